@@ -1,0 +1,420 @@
+/*
+ * DeepFusion keyframe optimisation -- FP64 CPU ORACLE (test infrastructure).
+ *
+ * This file is the slow, plain reference that the CUDA path is checked
+ * against. Only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg load it; the product path never calls it and shares no code, header or
+ * constant with it.
+ *
+ * What it computes (paper Section II-C, "Optimisation"):
+ *
+ *   c(d, s) = c_semi(d, s) + c_net(d) + c_grad(d)                       (Eq. 5)
+ *   r_semi,i = x_i - t - mu_s,i      on valid semi-dense pixels       (Eq. 6b)
+ *   r_net,i  = x_i - mu_n,i          on every pixel                   (Eq. 7b)
+ *   r_x,i    = x_{i+1} - x_i - gx_i  for columns u < W-1              (Eq. 8b)
+ *   r_y,i    = x_{i+W} - x_i - gy_i  for rows    v < H-1              (Eq. 8c)
+ *
+ * with x_i = ln d_i (the unknown log-depth), t = ln s (the log scale
+ * correction), every residual whitened by its variance (u = r / sqrt(V),
+ * Eqs. 6a, 7a, 8a) and each term passed through the Huber loss (end of
+ * Section II-C):  rho(u) = u^2 for |u| <= delta, 2 delta |u| - delta^2 beyond.
+ * delta <= 0 or non-finite selects plain least squares.
+ *
+ * The solve is 'n_gn' Gauss-Newton iterations that alternate between the
+ * scale and the depth (Section II-C, last paragraph). The Huber loss is
+ * handled by iteratively re-weighted least squares: each term's weight is
+ * omega(u)/V with omega(u) = rho'(u) / (2u) = min(1, delta/|u|) evaluated at
+ * the current (x, t). Within one GN iteration:
+ *   (i)  scale step: t <- sum w_i (x_i - mu_s,i) / sum w_i over the semi term
+ *        (left unchanged when the sum of weights is 0);
+ *   (ii) depth step: the normal equations A x = b of the re-weighted
+ *        quadratic in x (a 5-point stencil, symmetric positive definite
+ *        because the network term weights every pixel) are solved by
+ *        n_pcg iterations of Jacobi-preconditioned conjugate gradients that
+ *        start from the current x.
+ *
+ * Readings where the paper is silent (listed with reasons in the design
+ * notes): the Huber threshold is on the whitened residual; the x-term exists
+ * only for u < W-1 and the y-term only for v < H-1 (no wrap-around);
+ * a semi-dense pixel is valid iff its variance is finite and > 0 and its
+ * log-depth finite; PCG stops early when p.Ap <= 0 or r.z == 0, or (when
+ * tol > 0) when ||r|| < tol ||b||.
+ *
+ * Also here, for the variants that reuse the same cost:
+ *   - term selection (semi / network / gradient) for the ablations of
+ *     Tables II and III;
+ *   - the Tukey biweight as an alternative robust loss (Section IV);
+ *   - the semi-dense depth -> log-depth conversion of Section II-B
+ *     (first order: mu = ln d, V = sigma_d^2 / d^2).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared  (no FMA contraction, so
+ * x86 and Arm hosts give identical results).
+ *
+ * Parity status: every function below is pinned by the oracle tests
+ * (closed forms, dense Cholesky solves, a noise-free scene, invariances,
+ * scipy minimisation). The value of the Huber threshold and the order of the
+ * alternation are readings of the paper, not pinned by it.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Term-selection bits and robust-loss codes (the values are part of this
+ * file's C interface; the Python wrapper passes plain integers). */
+#define ORC_TERM_SEMI 1
+#define ORC_TERM_NET 2
+#define ORC_TERM_GRAD 4
+#define ORC_LOSS_HUBER 0
+#define ORC_LOSS_TUKEY 1
+
+#ifndef ORC_MUTANT
+#define ORC_MUTANT 0 /* >0 only in the tests' planted-mistake builds */
+#endif
+
+typedef struct {
+  int32_t width, height;
+  const double *mu_n, *var_n;   /* network log-depth and its variance (Eq. 7) */
+  const double *gx, *var_gx;    /* network x-gradient and variance (Eq. 8b) */
+  const double *gy, *var_gy;    /* network y-gradient and variance (Eq. 8c) */
+  const double *mu_s, *var_s;   /* semi-dense log-depth and variance (Eq. 6); may be NULL */
+} orc_problem;
+
+typedef struct {
+  int32_t n_gn;       /* Gauss-Newton iterations (10 in Section II-C) */
+  int32_t n_pcg;      /* PCG iterations per depth step */
+  double delta;       /* robust-loss threshold on whitened residuals */
+  double tol;         /* 0: fixed iteration count */
+  int32_t terms;      /* ORC_TERM_* bits */
+  int32_t loss;       /* ORC_LOSS_* */
+  int32_t scale_step; /* 1: run the scale half of each GN iteration */
+} orc_params;
+
+typedef struct {
+  double scale_log;  /* final t */
+  double res_norm;   /* ||r|| (recurrence residual) at the end of the last depth step */
+  int32_t iters_done;/* PCG iterations executed, summed over GN iterations */
+} orc_report;
+
+/* ---- robust loss -------------------------------------------------------- */
+
+static int robust_on(double delta) { return delta > 0.0 && isfinite(delta); }
+
+/* rho(u): squared whitened residual, or its robust replacement. */
+double orc_rho(double u, double delta, int32_t loss) {
+  if (!robust_on(delta)) return u * u;
+  double a = fabs(u);
+  if (loss == ORC_LOSS_TUKEY) {
+    if (a >= delta) return delta * delta / 3.0;
+    double q = 1.0 - (u / delta) * (u / delta);
+    return delta * delta / 3.0 * (1.0 - q * q * q);
+  }
+  if (a <= delta) return u * u;
+  return 2.0 * delta * a - delta * delta;
+}
+
+/* omega(u) = rho'(u) / (2u): the IRLS weight multiplying 1/V. */
+double orc_omega(double u, double delta, int32_t loss) {
+  if (!robust_on(delta)) return 1.0;
+  double a = fabs(u);
+  if (loss == ORC_LOSS_TUKEY) {
+    if (a >= delta) return 0.0;
+    double q = 1.0 - (u / delta) * (u / delta);
+    return q * q;
+  }
+  if (a <= delta) return 1.0;
+#if ORC_MUTANT == 5
+  return delta / (a * a);
+#else
+  return delta / a;
+#endif
+}
+
+/* A semi-dense pixel takes part in Eq. 6 iff its measurement is usable. */
+int orc_semi_valid(double mu, double var) {
+  return isfinite(mu) && isfinite(var) && var > 0.0;
+}
+
+static int semi_ok(const orc_problem *P, int i) {
+  return P->mu_s && P->var_s && orc_semi_valid(P->mu_s[i], P->var_s[i]);
+}
+
+/* ---- cost (Eq. 5 with the robust loss on every term) --------------------- */
+
+double orc_cost(const orc_problem *P, const double *x, double t, double delta,
+                int32_t terms, int32_t loss) {
+  const int W = P->width, H = P->height;
+  double c_semi = 0.0, c_net = 0.0, c_grad = 0.0;
+  for (int v = 0; v < H; ++v) {
+    for (int u = 0; u < W; ++u) {
+      const int i = v * W + u;
+      if ((terms & ORC_TERM_SEMI) && semi_ok(P, i)) {
+        double r = x[i] - t - P->mu_s[i];                          /* Eq. 6b */
+#if ORC_MUTANT == 9
+        c_semi += orc_rho(r / P->var_s[i], delta, loss);
+#else
+        c_semi += orc_rho(r / sqrt(P->var_s[i]), delta, loss);    /* Eq. 6a */
+#endif
+      }
+      if (terms & ORC_TERM_NET) {
+        double r = x[i] - P->mu_n[i];                              /* Eq. 7b */
+        c_net += orc_rho(r / sqrt(P->var_n[i]), delta, loss);     /* Eq. 7a */
+      }
+      if (terms & ORC_TERM_GRAD) {
+        if (u < W - 1) {
+#if ORC_MUTANT == 4
+          double r = x[i] - x[i + 1] - P->gx[i];
+#else
+          double r = x[i + 1] - x[i] - P->gx[i];                   /* Eq. 8b */
+#endif
+          c_grad += orc_rho(r / sqrt(P->var_gx[i]), delta, loss);
+        }
+        if (v < H - 1) {
+          double r = x[i + W] - x[i] - P->gy[i];                   /* Eq. 8c */
+          c_grad += orc_rho(r / sqrt(P->var_gy[i]), delta, loss);
+        }
+      }
+    }
+  }
+  return c_semi + c_net + c_grad;                                  /* Eq. 5 */
+}
+
+/* ---- scale half of a GN iteration --------------------------------------- */
+
+/* Minimise the re-weighted semi-dense term over t with x fixed:
+ * t = sum w_i (x_i - mu_s,i) / sum w_i,  w_i = omega(u_i) / Vs_i. */
+double orc_scale_step(const orc_problem *P, const double *x, double t,
+                      double delta, int32_t loss) {
+  const int N = P->width * P->height;
+  double sw = 0.0, swr = 0.0;
+  for (int i = 0; i < N; ++i) {
+    if (!semi_ok(P, i)) continue;
+    double r = x[i] - t - P->mu_s[i];
+    double w = orc_omega(r / sqrt(P->var_s[i]), delta, loss) / P->var_s[i];
+    sw += w;
+#if ORC_MUTANT == 6
+    swr += w * (P->mu_s[i] - x[i]);
+#else
+    swr += w * (x[i] - P->mu_s[i]);
+#endif
+  }
+  if (sw > 0.0) return swr / sw;
+  return t;
+}
+
+/* ---- depth half: normal equations of the re-weighted quadratic ---------- */
+
+/* A is stored as its diagonal 'diag', the east coupling wx (between i and
+ * i+1) and the south coupling wy (between i and i+W): A_{i,i+1} = -wx_i,
+ * A_{i,i+W} = -wy_i. Setting the gradient of
+ *   sum ws (x_i - t - mu_s)^2 + sum wn (x_i - mu_n)^2
+ *   + sum wx (x_{i+1} - x_i - gx)^2 + sum wy (x_{i+W} - x_i - gy)^2
+ * to zero gives, per pixel i,
+ *   diag_i = ws_i + wn_i + wx_i + wx_{i-1} + wy_i + wy_{i-W}
+ *   b_i    = ws_i (t + mu_s,i) + wn_i mu_n,i - wx_i gx_i + wx_{i-1} gx_{i-1}
+ *            - wy_i gy_i + wy_{i-W} gy_{i-W}.                            */
+void orc_assemble(const orc_problem *P, const double *x, double t, double delta,
+                  int32_t terms, int32_t loss, double *diag, double *wx,
+                  double *wy, double *b) {
+  const int W = P->width, H = P->height, N = W * H;
+  double *ws = (double *)calloc((size_t)N, sizeof(double));
+  double *wn = (double *)calloc((size_t)N, sizeof(double));
+  for (int v = 0; v < H; ++v) {
+    for (int u = 0; u < W; ++u) {
+      const int i = v * W + u;
+      ws[i] = wn[i] = wx[i] = wy[i] = 0.0;
+      if ((terms & ORC_TERM_SEMI) && semi_ok(P, i)) {
+        double r = x[i] - t - P->mu_s[i];
+        ws[i] = orc_omega(r / sqrt(P->var_s[i]), delta, loss) / P->var_s[i];
+      }
+      if (terms & ORC_TERM_NET) {
+        double r = x[i] - P->mu_n[i];
+        wn[i] = orc_omega(r / sqrt(P->var_n[i]), delta, loss) / P->var_n[i];
+      }
+      if (terms & ORC_TERM_GRAD) {
+        if (u < W - 1) {
+#if ORC_MUTANT == 3
+          double r = x[i + 1] - x[i] - P->gy[i];
+#else
+          double r = x[i + 1] - x[i] - P->gx[i];
+#endif
+          wx[i] = orc_omega(r / sqrt(P->var_gx[i]), delta, loss) / P->var_gx[i];
+        }
+        if (v < H - 1) {
+          double r = x[i + W] - x[i] - P->gy[i];
+          wy[i] = orc_omega(r / sqrt(P->var_gy[i]), delta, loss) / P->var_gy[i];
+        }
+      }
+    }
+  }
+  for (int v = 0; v < H; ++v) {
+    for (int u = 0; u < W; ++u) {
+      const int i = v * W + u;
+      double d = ws[i] + wn[i] + wx[i] + wy[i];
+      double bi = wn[i] * P->mu_n[i] - wx[i] * P->gx[i] - wy[i] * P->gy[i];
+      if (ws[i] != 0.0) bi += ws[i] * (t + P->mu_s[i]);
+      if (u > 0) {
+#if ORC_MUTANT != 1
+        d += wx[i - 1];
+#endif
+#if ORC_MUTANT == 2
+        bi -= wx[i - 1] * P->gx[i - 1];
+#else
+        bi += wx[i - 1] * P->gx[i - 1];
+#endif
+      }
+      if (v > 0) {
+#if ORC_MUTANT == 7
+        d += wy[i - 1 >= 0 ? i - 1 : 0];
+#else
+        d += wy[i - W];
+#endif
+        bi += wy[i - W] * P->gy[i - W];
+      }
+      diag[i] = d;
+      b[i] = bi;
+    }
+  }
+  free(ws);
+  free(wn);
+}
+
+/* q = A p for the 5-point operator (diag, wx, wy). */
+void orc_apply(int32_t W, int32_t H, const double *diag, const double *wx,
+               const double *wy, const double *p, double *q) {
+  for (int v = 0; v < H; ++v) {
+    for (int u = 0; u < W; ++u) {
+      const int i = v * W + u;
+      double s = diag[i] * p[i];
+      if (u < W - 1) s -= wx[i] * p[i + 1];
+      if (u > 0) s -= wx[i - 1] * p[i - 1];
+      if (v < H - 1) s -= wy[i] * p[i + W];
+      if (v > 0) s -= wy[i - W] * p[i - W];
+      q[i] = s;
+    }
+  }
+}
+
+static double dot(const double *a, const double *b, int n) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+/* Jacobi-preconditioned CG on A x = b, starting from x (updated in place).
+ * Returns the number of iterations executed; *res_norm = ||r|| at the end. */
+int32_t orc_pcg(int32_t W, int32_t H, const double *diag, const double *wx,
+                const double *wy, const double *b, double *x, int32_t n_pcg,
+                double tol, double *res_norm) {
+  const int N = W * H;
+  double *r = (double *)malloc(sizeof(double) * (size_t)N);
+  double *z = (double *)malloc(sizeof(double) * (size_t)N);
+  double *p = (double *)malloc(sizeof(double) * (size_t)N);
+  double *q = (double *)malloc(sizeof(double) * (size_t)N);
+  orc_apply(W, H, diag, wx, wy, x, q);
+  for (int i = 0; i < N; ++i) {
+    r[i] = b[i] - q[i];
+    z[i] = r[i] / diag[i];
+    p[i] = z[i];
+  }
+  double rho0 = dot(r, z, N);
+  double bnorm = tol > 0.0 ? sqrt(dot(b, b, N)) : 0.0;
+  int32_t it = 0;
+  int converged = tol > 0.0 && sqrt(dot(r, r, N)) < tol * bnorm;
+  for (int j = 0; j < n_pcg && !converged; ++j) {
+    orc_apply(W, H, diag, wx, wy, p, q);
+    double gamma = dot(p, q, N);
+    if (gamma <= 0.0 || rho0 == 0.0) break;
+    double alpha = rho0 / gamma;
+    for (int i = 0; i < N; ++i) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * q[i];
+    }
+    ++it;
+    if (tol > 0.0 && sqrt(dot(r, r, N)) < tol * bnorm) break;
+    for (int i = 0; i < N; ++i) z[i] = r[i] / diag[i];
+    double rho1 = dot(r, z, N);
+#if ORC_MUTANT == 8
+    double beta = rho0 / rho1;
+#else
+    double beta = rho1 / rho0;
+#endif
+    for (int i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    rho0 = rho1;
+  }
+  if (res_norm) *res_norm = sqrt(dot(r, r, N));
+  free(r);
+  free(z);
+  free(p);
+  free(q);
+  return it;
+}
+
+/* The whole per-frame solve: n_gn x (scale step, depth step). x and t are
+ * the warm start on entry and the result on exit. If cost_trace is not NULL
+ * it receives 2*n_gn+1 costs: at entry, after each scale step and after each
+ * depth step. */
+int32_t orc_optimise(const orc_problem *P, double *x, double *t,
+                     const orc_params *prm, orc_report *rep, double *cost_trace) {
+  const int W = P->width, H = P->height, N = W * H;
+  double *diag = (double *)malloc(sizeof(double) * (size_t)N);
+  double *wx = (double *)malloc(sizeof(double) * (size_t)N);
+  double *wy = (double *)malloc(sizeof(double) * (size_t)N);
+  double *b = (double *)malloc(sizeof(double) * (size_t)N);
+  int32_t iters = 0;
+  double rn = 0.0;
+  if (cost_trace) cost_trace[0] = orc_cost(P, x, *t, prm->delta, prm->terms, prm->loss);
+  for (int k = 0; k < prm->n_gn; ++k) {
+    if ((prm->terms & ORC_TERM_SEMI) && prm->scale_step)
+      *t = orc_scale_step(P, x, *t, prm->delta, prm->loss);
+    if (cost_trace)
+      cost_trace[2 * k + 1] = orc_cost(P, x, *t, prm->delta, prm->terms, prm->loss);
+    orc_assemble(P, x, *t, prm->delta, prm->terms, prm->loss, diag, wx, wy, b);
+    iters += orc_pcg(W, H, diag, wx, wy, b, x, prm->n_pcg, prm->tol, &rn);
+    if (cost_trace)
+      cost_trace[2 * k + 2] = orc_cost(P, x, *t, prm->delta, prm->terms, prm->loss);
+  }
+  if (rep) {
+    rep->scale_log = *t;
+    rep->res_norm = rn;
+    rep->iters_done = iters;
+  }
+  free(diag);
+  free(wx);
+  free(wy);
+  free(b);
+  return iters;
+}
+
+/* Output of the solve: metric depth d = exp(x) and scale s = exp(t). */
+void orc_depth(int64_t n, const double *x, double *d) {
+  for (int64_t i = 0; i < n; ++i) d[i] = exp(x[i]);
+}
+
+/* Section II-B, last sentence: semi-dense depth d with variance sigma_d^2 to
+ * log space, to first order: mu = ln d, V = sigma_d^2 / d^2. Invalid inputs
+ * (d <= 0, non-finite, variance <= 0) give mu = 0, V = 0. */
+void orc_semi_to_log(int64_t n, const double *d, const double *var_d, double *mu,
+                     double *var) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (isfinite(d[i]) && d[i] > 0.0 && isfinite(var_d[i]) && var_d[i] > 0.0) {
+      mu[i] = log(d[i]);
+      var[i] = var_d[i] / (d[i] * d[i]);
+    } else {
+      mu[i] = 0.0;
+      var[i] = 0.0;
+    }
+  }
+}
+
+/* Ablation of Table II: after a scale-ambiguous solve (semi + gradient terms,
+ * t fixed), fit the scale by least squares to the network log-depth:
+ * c = argmin sum_i (x_i + c - mu_n,i)^2 = mean(mu_n - x); x += c; t = c. */
+void orc_ls_scale_fit(const orc_problem *P, double *x, double *t) {
+  const int N = P->width * P->height;
+  double s = 0.0;
+  for (int i = 0; i < N; ++i) s += P->mu_n[i] - x[i];
+  double c = s / (double)N;
+  for (int i = 0; i < N; ++i) x[i] += c;
+  *t = *t + c;
+}

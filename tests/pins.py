@@ -1,0 +1,374 @@
+"""Pins for the FP64 oracle: checks against facts fixed by the paper's cost
+(Section II-C, Eqs. 5-8) and by mathematics, independent of the oracle's own
+code. Each function takes an ``oracle.Oracle`` and raises AssertionError on a
+mismatch, so the same pins run against the real oracle and against builds
+with a planted mistake (tests/test_oracle_mutants.py).
+
+What each pin fixes:
+  cost_closed_form     hand-derived cost of one-pixel / scale perturbations of
+                       a zero-residual state (every term, its whitening, its
+                       neighbour index, Huber and Tukey branches, term bits)
+  robust_weight        omega(u) = rho'(u) / (2u) by central differences
+  dense_hessian        A, b of the depth step = Hessian / gradient of the cost
+                       (second differences); PCG to convergence = Cholesky
+  joint_optimum        alternation converges to the bordered (x, t) Cholesky
+                       solution of the least-squares cost
+  prior_only           network term alone: x = mu_n bitwise; one Jacobi-PCG
+                       iteration from a perturbed start returns mu_n
+  planar_recovery      noise-free piecewise-planar scene: x = ln D, t = ln s
+  huber_scipy          robust cost: IRLS optimum = scipy BFGS optimum
+  invariances          shifts of mu_s, of (mu_n, mu_s), and transposition
+  monotone             cost never increases over scale and depth steps
+  no_pairwise          semi + network only: closed-form joint optimum
+  semi_to_log          first-order log conversion vs Monte Carlo
+"""
+from __future__ import annotations
+
+import types
+
+import numpy as np
+
+import oracle as orc
+from paper_2207_12244_gb300 import synth
+
+INF = float("inf")
+DELTA = orc.HUBER_DELTA
+TUKEY_C = 4.685
+
+
+def _planes(W, H, rng, xs, ts, mask_frac=0.5, garbage=True):
+    """A problem whose residuals all vanish at (xs, ts): mu_n = xs, g = exact
+    forward differences, mu_s = xs - ts on a random mask."""
+    kf = types.SimpleNamespace(width=W, height=H)
+    X = xs.reshape(H, W)
+    kf.mu_n = X.copy()
+    kf.gx = np.zeros((H, W))
+    kf.gy = np.zeros((H, W))
+    kf.gx[:, :-1] = X[:, 1:] - X[:, :-1]
+    kf.gy[:-1, :] = X[1:, :] - X[:-1, :]
+    if garbage:  # entries the method must ignore
+        kf.gx[:, -1] = 7.0
+        kf.gy[-1, :] = -5.0
+    kf.var_n = rng.uniform(0.1, 2.0, (H, W))
+    kf.var_gx = rng.uniform(0.1, 2.0, (H, W))
+    kf.var_gy = rng.uniform(0.1, 2.0, (H, W))
+    m = rng.random((H, W)) < mask_frac
+    kf.mu_s = np.where(m, X - ts, 0.0)
+    kf.var_s = np.where(m, rng.uniform(0.1, 2.0, (H, W)), 0.0)
+    if garbage:  # invalid semi-dense pixels in every encoding
+        bad = np.argwhere(~m)
+        for k, (v, u) in enumerate(bad):
+            kind = k % 4
+            if kind == 1:
+                kf.var_s[v, u] = -1.0
+                kf.mu_s[v, u] = 3.0
+            elif kind == 2:
+                kf.var_s[v, u] = np.nan
+            elif kind == 3:
+                kf.var_s[v, u] = 0.5
+                kf.mu_s[v, u] = np.inf
+    return kf, m
+
+
+def _touch_weights(kf, m, j, terms=orc.TERMS_ALL):
+    """Inverse variances of every term that contains pixel j (by hand)."""
+    W, H = kf.width, kf.height
+    v, u = divmod(j, W)
+    w = []
+    if terms & orc.TERM_SEMI and m[v, u]:
+        w.append(1.0 / kf.var_s[v, u])
+    if terms & orc.TERM_NET:
+        w.append(1.0 / kf.var_n[v, u])
+    if terms & orc.TERM_GRAD:
+        if u < W - 1:
+            w.append(1.0 / kf.var_gx[v, u])      # r_x at i   = x_{i+1} - x_i - gx_i
+        if u > 0:
+            w.append(1.0 / kf.var_gx[v, u - 1])  # r_x at i-1 = x_i - x_{i-1} - gx_{i-1}
+        if v < H - 1:
+            w.append(1.0 / kf.var_gy[v, u])
+        if v > 0:
+            w.append(1.0 / kf.var_gy[v - 1, u])
+    return np.array(w)
+
+
+def cost_closed_form(o):
+    rng = np.random.default_rng(11)
+    W, H = 5, 4
+    xs = rng.normal(0.0, 1.0, W * H)
+    ts = 0.3
+    kf, m = _planes(W, H, rng, xs, ts)
+    for delta in (INF, DELTA):
+        assert abs(o.cost(kf, xs, ts, delta)) < 1e-24
+    for j in range(W * H):
+        w = _touch_weights(kf, m, j)
+        # small step: every touched whitened residual is below delta
+        eps = 1e-3
+        x = xs.copy()
+        x[j] += eps
+        want = eps * eps * w.sum()
+        for delta in (INF, DELTA):
+            got = o.cost(kf, x, ts, delta)
+            assert np.isclose(got, want, rtol=1e-8, atol=0), (j, delta, got, want)
+        # large step: Huber's linear branch, 2 delta |u| - delta^2 per term
+        eps = 40.0
+        x = xs.copy()
+        x[j] -= eps
+        want = np.sum(2.0 * DELTA * eps * np.sqrt(w) - DELTA ** 2)
+        got = o.cost(kf, x, ts, DELTA)
+        assert np.isclose(got, want, rtol=1e-10), (j, got, want)
+        assert np.isclose(o.cost(kf, x, ts, INF), eps * eps * w.sum(), rtol=1e-10)
+        # Tukey saturates at c^2/3 per term
+        got = o.cost(kf, x, ts, TUKEY_C, loss=orc.LOSS_TUKEY)
+        assert np.isclose(got, len(w) * TUKEY_C ** 2 / 3.0, rtol=1e-12), (j, got)
+        # term selection
+        for terms in (orc.TERM_SEMI, orc.TERM_NET, orc.TERM_GRAD,
+                      orc.TERM_SEMI | orc.TERM_GRAD, orc.TERM_SEMI | orc.TERM_NET):
+            wt = _touch_weights(kf, m, j, terms)
+            x = xs.copy()
+            x[j] += 1e-3
+            got = o.cost(kf, x, ts, INF, terms=terms)
+            assert np.isclose(got, 1e-6 * wt.sum(), rtol=1e-8, atol=1e-30), (j, terms)
+    # the scale enters only the semi-dense term, with the opposite sign of x
+    sw = (1.0 / kf.var_s[m]).sum()
+    for tau in (1e-3, -0.7):
+        assert np.isclose(o.cost(kf, xs, ts + tau, INF), tau * tau * sw, rtol=1e-9)
+    x = xs + 0.25
+    assert np.isclose(o.cost(kf, x, ts + 0.25, INF, terms=orc.TERM_SEMI), 0.0, atol=1e-20)
+
+
+def robust_weight(o):
+    for loss, delta in ((orc.LOSS_HUBER, DELTA), (orc.LOSS_TUKEY, TUKEY_C)):
+        for u in (-9.0, -3.1, -1.0, -0.2, 0.3, 1.2, 1.4, 2.5, 4.0, 8.0):
+            h = 1e-6
+            d = (o.rho(u + h, delta, loss) - o.rho(u - h, delta, loss)) / (2 * h)
+            assert np.isclose(o.omega(u, delta, loss), d / (2 * u), rtol=1e-6, atol=1e-9), (loss, u)
+        # continuity at the threshold
+        a = o.rho(delta * (1 - 1e-12), delta, loss)
+        b = o.rho(delta * (1 + 1e-12), delta, loss)
+        assert abs(a - b) < 1e-9
+    for u in (-3.0, 0.5, 10.0):
+        assert o.omega(u, INF) == 1.0 and o.rho(u, INF) == u * u
+        assert o.omega(u, 0.0) == 1.0
+
+
+def _noisy(W, H, seed):
+    kf = synth.make_keyframe(W, H, seed)
+    return kf
+
+
+def _dense_quadratic(o, kf, t, x0, terms=orc.TERMS_ALL):
+    """Hessian/2 and -gradient/2 of the least-squares cost in x (t fixed),
+    by exact second differences of the cost (a quadratic)."""
+    N = kf.width * kf.height
+    c = lambda x: o.cost(kf, x, t, INF, terms=terms)
+    z = np.zeros(N)
+    c0 = c(z)
+    ce = np.empty(N)
+    cm = np.empty(N)
+    e = np.eye(N)
+    for j in range(N):
+        ce[j] = c(e[j])
+        cm[j] = c(-e[j])
+    A = np.empty((N, N))
+    for j in range(N):
+        for k in range(j, N):
+            if j == k:
+                A[j, j] = (c(2 * e[j]) - 2 * ce[j] + c0) / 2.0
+            else:
+                A[j, k] = A[k, j] = (c(e[j] + e[k]) - ce[j] - ce[k] + c0) / 2.0
+    b = -(ce - cm) / 4.0
+    return A, b
+
+
+def dense_hessian(o):
+    W, H = 6, 5
+    kf = _noisy(W, H, 3)
+    t = 0.2
+    rng = np.random.default_rng(5)
+    x0 = kf.mu_n.ravel().astype(np.float64) + rng.normal(0, 0.2, W * H)
+    A, b = _dense_quadratic(o, kf, t, x0)
+    diag, wx, wy, bb = o.assemble(kf, x0, t, INF)
+    scale = np.abs(A).max()
+    assert np.allclose(np.diag(A), diag, rtol=1e-7, atol=1e-9 * scale)
+    N = W * H
+    Ad = np.diag(diag)
+    for i in range(N):
+        v, u = divmod(i, W)
+        if u < W - 1:
+            Ad[i, i + 1] = Ad[i + 1, i] = -wx[i]
+        else:
+            assert wx[i] == 0.0
+        if v < H - 1:
+            Ad[i, i + W] = Ad[i + W, i] = -wy[i]
+        else:
+            assert wy[i] == 0.0
+    assert np.allclose(Ad, A, rtol=1e-7, atol=1e-8 * scale)
+    assert np.allclose(bb, b, rtol=1e-7, atol=1e-8 * np.abs(b).max())
+    Lc = np.linalg.cholesky(A)
+    xs = np.linalg.solve(Lc.T, np.linalg.solve(Lc, b))
+    x, it, rn = o.pcg(W, H, diag, wx, wy, bb, x0, 300)
+    assert np.allclose(x, xs, rtol=0, atol=1e-10 * np.abs(xs).max()), np.abs(x - xs).max()
+    # the same through the full schedule (scale step off, one GN iteration)
+    x2, t2, rep = o.optimise(kf, x0=x0, t0=t, n_gn=1, n_pcg=300, delta=INF, scale_step=False)
+    assert t2 == t
+    assert np.allclose(x2.ravel(), xs, rtol=0, atol=1e-10 * np.abs(xs).max())
+
+
+def joint_optimum(o):
+    W, H = 6, 5
+    kf = _noisy(W, H, 8)
+    N = W * H
+    # bordered Hessian over (x, t) by second differences of the L2 cost
+    c = lambda y: o.cost(kf, y[:N], y[N], INF)
+    n = N + 1
+    e = np.eye(n)
+    z = np.zeros(n)
+    c0 = c(z)
+    ce = np.array([c(e[j]) for j in range(n)])
+    cm = np.array([c(-e[j]) for j in range(n)])
+    A = np.empty((n, n))
+    for j in range(n):
+        for k in range(j, n):
+            if j == k:
+                A[j, j] = (c(2 * e[j]) - 2 * ce[j] + c0) / 2.0
+            else:
+                A[j, k] = A[k, j] = (c(e[j] + e[k]) - ce[j] - ce[k] + c0) / 2.0
+    b = -(ce - cm) / 4.0
+    ys = np.linalg.solve(A, b)
+    np.linalg.cholesky(A)  # positive definite: the minimiser is unique
+    x, t, rep = o.optimise(kf, n_gn=400, n_pcg=200, delta=INF)
+    assert abs(t - ys[N]) < 1e-9, (t, ys[N])
+    assert np.allclose(x.ravel(), ys[:N], rtol=0, atol=1e-9)
+
+
+def prior_only(o):
+    kf = _noisy(9, 7, 4)
+    x, t, rep = o.optimise(kf, n_gn=3, n_pcg=4, terms=orc.TERM_NET)
+    assert np.array_equal(x.ravel(), kf.mu_n.ravel().astype(np.float64))
+    assert t == 0.0 and rep.iters_done == 0
+    rng = np.random.default_rng(2)
+    x0 = kf.mu_n.ravel() + rng.normal(0, 0.5, kf.n_pixels)
+    for delta in (INF, DELTA):
+        x, t, rep = o.optimise(kf, x0=x0, n_gn=1, n_pcg=1, terms=orc.TERM_NET, delta=delta)
+        assert np.allclose(x.ravel(), kf.mu_n.ravel(), rtol=0, atol=1e-12)
+
+
+def planar_recovery(o):
+    W, H = 24, 16
+    base = synth.make_keyframe(W, H, 21)
+    L = base.log_depth_true
+    kf = types.SimpleNamespace(width=W, height=H, mu_n=L.copy(), var_n=base.var_n,
+                               var_gx=base.var_gx, var_gy=base.var_gy)
+    kf.gx = np.zeros((H, W))
+    kf.gy = np.zeros((H, W))
+    kf.gx[:, :-1] = L[:, 1:] - L[:, :-1]
+    kf.gy[:-1, :] = L[1:, :] - L[:-1, :]
+    m = base.var_s > 0
+    ts = base.scale_log_true
+    kf.mu_s = np.where(m, L - ts, 0.0)
+    kf.var_s = np.where(m, base.var_s, 0.0)
+    x0 = np.full(W * H, L.mean())
+    for delta in (INF, DELTA):
+        x, t, rep = o.optimise(kf, x0=x0, n_gn=1000, n_pcg=100, delta=delta)
+        assert abs(t - ts) < 1e-8, (delta, t, ts)
+        assert np.allclose(x, L, rtol=0, atol=1e-8), np.abs(x - L).max()
+
+
+def huber_scipy(o):
+    from scipy.optimize import minimize
+
+    W, H = 4, 4
+    kf = _noisy(W, H, 30)
+    kf.mu_n = kf.mu_n.astype(np.float64)
+    kf.mu_n[1, 2] += 1.5   # network outliers
+    kf.mu_n[3, 0] -= 1.2
+    kf.mu_s = kf.mu_s.astype(np.float64)
+    kf.var_s = kf.var_s.astype(np.float64)
+    kf.var_s[0, :] = 0.01
+    kf.mu_s[0, :] = kf.log_depth_true[0, :] - kf.scale_log_true
+    kf.mu_s[0, 1] += 0.8   # semi-dense outlier
+    kf.gx = kf.gx.astype(np.float64)
+    kf.gx[2, 1] += 0.9     # gradient outlier
+    N = W * H
+    f = lambda y: o.cost(kf, y[:N], y[N], DELTA)
+    x, t, rep = o.optimise(kf, n_gn=3000, n_pcg=60, delta=DELTA)
+    y_irls = np.concatenate([x.ravel(), [t]])
+    res = minimize(f, np.concatenate([kf.mu_n.ravel(), [0.0]]), method="BFGS",
+                   options={"gtol": 1e-10, "maxiter": 20000})
+    assert f(y_irls) <= res.fun + 1e-9 * max(1.0, abs(res.fun)), (f(y_irls), res.fun)
+    assert np.allclose(y_irls, res.x, rtol=0, atol=1e-5), np.abs(y_irls - res.x).max()
+    # Huber must actually be active somewhere for this pin to mean anything
+    assert abs(o.cost(kf, x, t, DELTA) - o.cost(kf, x, t, INF)) > 1e-3
+
+
+def invariances(o):
+    kf = _noisy(12, 9, 40)
+    for delta in (INF, DELTA):
+        x, t, _ = o.optimise(kf, n_gn=10, n_pcg=3, delta=delta)
+        c = 0.37
+        k1 = types.SimpleNamespace(**vars(kf))
+        k1.mu_s = kf.mu_s.astype(np.float64) + c
+        x1, t1, _ = o.optimise(k1, t0=-c, n_gn=10, n_pcg=3, delta=delta)
+        assert abs(t1 - (t - c)) < 1e-10 and np.allclose(x1, x, rtol=0, atol=1e-10)
+        k2 = types.SimpleNamespace(**vars(kf))
+        k2.mu_s = kf.mu_s.astype(np.float64) + c
+        k2.mu_n = kf.mu_n.astype(np.float64) + c
+        x2, t2, _ = o.optimise(k2, n_gn=10, n_pcg=3, delta=delta)
+        assert abs(t2 - t) < 1e-10 and np.allclose(x2, x + c, rtol=0, atol=1e-10)
+        k3 = types.SimpleNamespace(width=kf.height, height=kf.width)
+        for a, b in (("mu_n", "mu_n"), ("var_n", "var_n"), ("gx", "gy"), ("var_gx", "var_gy"),
+                     ("gy", "gx"), ("var_gy", "var_gx"), ("mu_s", "mu_s"), ("var_s", "var_s")):
+            setattr(k3, a, np.ascontiguousarray(getattr(kf, b).T))
+        x3, t3, _ = o.optimise(k3, n_gn=10, n_pcg=3, delta=delta)
+        assert abs(t3 - t) < 1e-10 and np.allclose(x3, x.T, rtol=0, atol=1e-10)
+
+
+def monotone(o):
+    kf = _noisy(32, 24, 50)
+    rng = np.random.default_rng(1)
+    for delta in (INF, DELTA):
+        for x0 in (None, kf.mu_n.ravel() + rng.normal(0, 0.3, kf.n_pixels)):
+            for npcg in (1, 3):
+                *_, tr = o.optimise(kf, x0=x0, n_gn=10, n_pcg=npcg, delta=delta, trace=True)
+                d = np.diff(tr)
+                assert np.all(d <= 1e-12 * tr[0]), (delta, npcg, d.max())
+                assert tr[-1] < tr[0]
+
+
+def no_pairwise(o):
+    kf = _noisy(10, 8, 60)
+    terms = orc.TERM_SEMI | orc.TERM_NET
+    mu_n = kf.mu_n.astype(np.float64).ravel()
+    vn = kf.var_n.astype(np.float64).ravel()
+    vs = kf.var_s.astype(np.float64).ravel()
+    mu_s = kf.mu_s.astype(np.float64).ravel()
+    valid = vs > 0
+    ws = np.where(valid, 1.0 / np.where(valid, vs, 1.0), 0.0)
+    wn = 1.0 / vn
+    h = ws * wn / (ws + wn)
+    ts = np.sum(h * (mu_n - mu_s)) / np.sum(h)
+    xs = (ws * (ts + mu_s) + wn * mu_n) / (ws + wn)
+    x, t, _ = o.optimise(kf, n_gn=20000, n_pcg=1, delta=INF, terms=terms)
+    assert abs(t - ts) < 1e-10, (t, ts)
+    assert np.allclose(x.ravel(), xs, rtol=0, atol=1e-10)
+    # one GN iteration: scale step from x = mu_n, then the exact per-pixel solve
+    t1 = np.sum(ws * (mu_n - mu_s)) / np.sum(ws)
+    x1 = (ws * (t1 + mu_s) + wn * mu_n) / (ws + wn)
+    x, t, _ = o.optimise(kf, n_gn=1, n_pcg=1, delta=INF, terms=terms)
+    assert abs(t - t1) < 1e-12 and np.allclose(x.ravel(), x1, rtol=0, atol=1e-12)
+
+
+def semi_to_log(o):
+    rng = np.random.default_rng(3)
+    d = np.array([0.5, 1.0, 2.0, 4.5, -1.0, 0.0, 2.0, np.nan])
+    sd = np.array([1e-3, 2e-3, 4e-3, 1e-2, 1e-3, 1e-3, -1.0, 1.0])
+    mu, var = o.semi_to_log(d, sd * np.abs(sd))
+    for i in range(4):
+        s = np.log(d[i] + sd[i] * rng.normal(size=400000))
+        assert abs(mu[i] - np.log(d[i])) < 1e-15
+        assert np.isclose(var[i], s.var(), rtol=0.01), (i, var[i], s.var())
+    assert np.all(mu[4:] == 0) and np.all(var[4:] == 0)
+
+
+ALL = [cost_closed_form, robust_weight, dense_hessian, joint_optimum, prior_only,
+       planar_recovery, huber_scipy, invariances, monotone, no_pairwise, semi_to_log]
