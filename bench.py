@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput of the per-frame keyframe re-optimisation on GB300.
+
+Workload (one "step"): a 640 x 480 FP32 keyframe re-optimised over a
+100-frame synthetic sequence. The semi-dense mask grows from 5 % to 40 % and
+variances shrink by Gaussian fusion. Each frame runs 10 Gauss-Newton x 5 PCG
+iterations. A step covers every stage of the path: keyframe (re)initialisation
+from the network planes, then per frame the semi-dense refresh, the solve
+(scale step, re-weighting / assembly, PCG) and the depth output.
+
+Metric: Mpixel.iter/s = sum over frames of H*W*n_gn*n_pcg / time / 1e6.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank solves its own sequence
+(weak scaling, no collective on the data path); value = all ranks' units /
+max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel·iter/s"
+WORKLOAD = "sequence-640x480-100f-10x5-fp32"
+ALG_BYTES_PER_PCG_PX = 56  # canonical streaming model of one PCG iteration
+ALG_BYTES_PER_GN_PX = 56   # scale step + re-weighting / assembly per GN iteration
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--solver", choices=["auto", "launches", "fused"], default="auto")
+    ap.add_argument("--width", type=int, default=640)
+    ap.add_argument("--height", type=int, default=480)
+    ap.add_argument("--frames", type=int, default=100)
+    ap.add_argument("--n-gn", type=int, default=10)
+    ap.add_argument("--n-pcg", type=int, default=5)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def lib_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2207_12244_gb300", "csrc")
+    for n in sorted(os.listdir(csrc)):
+        if n.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, n), "rb") as f:
+                h.update(n.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != lib_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"df_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    smax = float(c[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, c[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.remove(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args, ws, rank):
+    """The oracle (FP64 CPU) on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2207_12244_gb300 import synth
+
+    o = oracle.get()
+    kf, mus, vs = synth.make_sequence(args.width, args.height, args.seed, args.frames)
+    px_iters = args.width * args.height * args.n_gn * args.n_pcg
+    x = kf.mu_n.astype(np.float64).ravel()
+    t = 0.0
+    times = []
+    f = 0
+
+    class _V:
+        pass
+
+    view = _V()
+    for n in ("width", "height", "mu_n", "var_n", "gx", "var_gx", "gy", "var_gy"):
+        setattr(view, n, getattr(kf, n))
+    for step in range(args.warmup + args.steps):
+        view.mu_s, view.var_s = mus[f % args.frames], vs[f % args.frames]
+        t0 = time.perf_counter()
+        xr, t, _ = o.optimise(view, x0=x, t0=t, n_gn=args.n_gn, n_pcg=args.n_pcg)
+        dt = time.perf_counter() - t0
+        x = xr.ravel()
+        f += 1
+        if step >= args.warmup:
+            times.append(dt)
+    value = px_iters * len(times) / sum(times) / 1e6
+    sample = (f"{args.steps} timed frames (after {args.warmup} warm-up) of the "
+              f"{args.width}x{args.height} sequence, {args.n_gn}x{args.n_pcg} per frame, "
+              "warm-started; one frame per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "width": args.width, "height": args.height,
+                   "frames_per_step": 1, "n_gn": args.n_gn, "n_pcg": args.n_pcg},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args, kf, mus, vs):
+    import oracle
+
+    o = oracle.get()
+    x = kf.mu_n.astype(np.float64).ravel()
+    t = 0.0
+
+    class _V:
+        pass
+
+    view = _V()
+    for n in ("width", "height", "mu_n", "var_n", "gx", "var_gx", "gy", "var_gy"):
+        setattr(view, n, getattr(kf, n))
+    n = 0
+    t_start = time.perf_counter()
+    while True:
+        view.mu_s, view.var_s = mus[n % args.frames], vs[n % args.frames]
+        xr, t, _ = o.optimise(view, x0=x, t0=t, n_gn=args.n_gn, n_pcg=args.n_pcg)
+        x = xr.ravel()
+        n += 1
+        el = time.perf_counter() - t_start
+        if el >= args.cpu_seconds or n >= args.frames:
+            break
+    px_iters = args.width * args.height * args.n_gn * args.n_pcg * n
+    return {"value": px_iters / el / 1e6, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} frames of the same {args.width}x{args.height} sequence, "
+                      f"{args.n_gn}x{args.n_pcg} per frame, warm-started, {el:.1f} s single-thread"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2207_12244_gb300 import _build
+    from paper_2207_12244_gb300 import deepfusion as dfl
+    from paper_2207_12244_gb300 import synth
+
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        _build.build()
+    if ws > 1:
+        dist.barrier()
+    dfl.load()
+
+    W, H, F = args.width, args.height, args.frames
+    kf, mus, vs = synth.make_sequence(W, H, args.seed + 1000 * rank, F)
+    cnn_d = [torch.from_numpy(p).to(dev) for p in kf.cnn_planes]
+    mus_d = torch.from_numpy(mus).to(dev)
+    vs_d = torch.from_numpy(vs).to(dev)
+    out_d = torch.empty((F, H, W), dtype=torch.float32, device=dev)
+    solver = {"auto": dfl.DF_SOLVER_AUTO, "launches": dfl.DF_SOLVER_LAUNCHES,
+              "fused": dfl.DF_SOLVER_FUSED}[args.solver]
+    prm = dfl.df_default_params(n_gn=args.n_gn, n_pcg=args.n_pcg, solver=solver)
+    stream = torch.cuda.Stream(dev)
+    sptr = stream.cuda_stream
+    k = dfl.Keyframe(W, H, *cnn_d, stream=sptr)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    ev_opt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(F)]
+
+    def step(record_solve: bool):
+        k.reset(*cnn_d, stream=sptr)
+        for f in range(F):
+            k.frame_update(mus_d[f], vs_d[f], stream=sptr)
+            if record_solve:
+                ev_opt[f][0].record(stream)
+            k.optimise(prm, stream=sptr)
+            if record_solve:
+                ev_opt[f][1].record(stream)
+            k.fetch_depth(out_d[f], stream=sptr)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(False)
+    torch.cuda.synchronize()
+
+    step_ms, solve_ms = [], []
+    launches0 = dfl.df_kernel_launches()
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # evict the previous step's working set from L2
+            if ws > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                step(True)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            solve_ms.extend(a.elapsed_time(b) for a, b in ev_opt)
+    launches = dfl.df_kernel_launches() - launches0
+    clocks = clk.summary()
+    total_ms = sum(step_ms)
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    units_per_step = W * H * args.n_gn * args.n_pcg * F
+    value = units_per_step * args.steps * ws / (total_ms / 1e3) / 1e6
+
+    # dominant region: the solve of one frame (all its kernels)
+    solve_avg_s = statistics.mean(solve_ms) / 1e3
+    alg_bytes = W * H * (args.n_gn * args.n_pcg * ALG_BYTES_PER_PCG_PX +
+                         args.n_gn * ALG_BYTES_PER_GN_PX)
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / solve_avg_s / 1e9
+    kernel_key = f"solve_{args.solver}_{WORKLOAD}"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(kernel_key),
+                "peak_kind": peak_kind, "region": "df_optimise (one frame's solve)",
+                "alg_bytes_per_launch": alg_bytes}
+    lat = np.percentile(np.array(solve_ms), [50, 99])
+
+    # end to end through the public API with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        cnn_h = [torch.from_numpy(p).pin_memory() for p in kf.cnn_planes]
+        mus_h = torch.from_numpy(mus).pin_memory()
+        vs_h = torch.from_numpy(vs).pin_memory()
+        out_h = torch.empty((F, H, W), dtype=torch.float32).pin_memory()
+
+        def step_host():
+            k.reset(*cnn_h, stream=sptr)
+            for f in range(F):
+                k.frame_update(mus_h[f], vs_h[f], stream=sptr)
+                k.optimise(prm, stream=sptr)
+                k.fetch_depth(out_h[f], stream=sptr)
+
+        step_host()
+        torch.cuda.synchronize()
+        e2e_ms = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_host()
+            torch.cuda.synchronize()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        tot = sum(e2e_ms)
+        if ws > 1:
+            tt = torch.tensor([tot], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            tot = float(tt.item())
+        e2e = {"value": units_per_step * args.steps * ws / (tot / 1e3) / 1e6, "unit": METRIC,
+               "h2d_bytes_per_step": int(sum(p.nbytes for p in kf.cnn_planes) + mus.nbytes + vs.nbytes),
+               "d2h_bytes_per_step": int(F * H * W * 4), "ms_per_step": tot / args.steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args, kf, mus, vs)
+
+    k.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
+            "config": {"workload": WORKLOAD, "width": W, "height": H, "frames": F,
+                       "n_gn": args.n_gn, "n_pcg": args.n_pcg, "solver": args.solver,
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "flushed between steps (256 MB write)"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu,
+            "update_latency_ms": {"p50": float(lat[0]), "p99": float(lat[1]),
+                                  "what": "one frame's df_optimise, device time"},
+            "hbm_frac": roofline["frac"],
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * deepfusion.h -- C ABI of the GB300 (sm_103a) keyframe depth optimiser.
+ *
+ * The library solves, for each new frame, the fused keyframe log-depth
+ * problem of DeepFusion (Laidlow, Czarnowski, Leutenegger; Section II-C,
+ * "Optimisation"):
+ *
+ *   c(d, s) = c_semi(d, s) + c_net(d) + c_grad(d)                  (Eq. 5)
+ *
+ * over the per-pixel log-depth x_i = ln d_i and the log scale correction
+ * t = ln s, with the semi-dense unary term (Eq. 6), the network unary term
+ * (Eq. 7) and the network log-depth-gradient pairwise term (Eq. 8), each
+ * whitened by its variance and robustified by the Huber loss, by Gauss-Newton
+ * iterations that alternate between the scale and the depth (10 in the
+ * paper). The depth half solves the 5-point normal equations by
+ * Jacobi-preconditioned conjugate gradients.
+ *
+ * Conventions for every entry point:
+ *   - Images are H x W, row-major, dense (row stride = width elements);
+ *     pixel i = v * W + u (column u, row v), as in Eq. 8.
+ *   - 'ptrs_on_device' != 0: the buffers are device pointers on the current
+ *     CUDA device; otherwise host pointers (pinned memory gives asynchronous
+ *     copies, pageable memory is copied synchronously by the driver).
+ *   - 'stream' is a cudaStream_t (NULL = the legacy default stream). All work
+ *     is stream-ordered: the caller keeps ownership of its buffers and must
+ *     not modify or free them until the stream has passed the call.
+ *   - Every call returns a df_status; none aborts the process. On error the
+ *     keyframe is left as it was before the call and df_last_error() gives a
+ *     thread-local message.
+ *   - The library owns each keyframe's device memory (allocated at create,
+ *     released at destroy) and counts it against a process-wide budget.
+ */
+#ifndef DEEPFUSION_H
+#define DEEPFUSION_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DF_OK = 0,
+  DF_EINVAL = 1,    /* bad argument or invalid input values */
+  DF_ENOMEM = 2,    /* device allocation failed */
+  DF_EBUDGET = 3,   /* the memory budget would be exceeded */
+  DF_ECUDA = 4,     /* a CUDA runtime call failed */
+  DF_ETIMEOUT = 5,  /* a device-side wait gave up (the solve was abandoned) */
+  DF_ESTATE = 6,    /* the keyframe is in an unusable state */
+  DF_ENOTSUP = 7    /* not supported on this device / build */
+} df_status;
+
+/* Storage type of the six network planes (Section II-A outputs). */
+typedef enum { DF_F32 = 0, DF_BF16 = 1, DF_F16 = 2 } df_dtype;
+
+/* Cost terms (Eq. 5). Leaving some out gives the ablations of Tables II
+ * (semi + gradient, scale fitted afterwards) and III (no pairwise term). */
+enum { DF_TERM_SEMI = 1, DF_TERM_NET = 2, DF_TERM_GRAD = 4, DF_TERMS_ALL = 7 };
+
+/* Robust loss on every term: Huber (Section II-C) or Tukey's biweight
+ * (named as an alternative in Section IV). */
+enum { DF_LOSS_HUBER = 0, DF_LOSS_TUKEY = 1 };
+
+/* Which kernel schedule runs the solve. AUTO picks the fused persistent
+ * kernel when it fits, else the per-phase launches. */
+enum { DF_SOLVER_AUTO = 0, DF_SOLVER_LAUNCHES = 1, DF_SOLVER_FUSED = 2 };
+
+typedef struct {
+  int32_t width;      /* W >= 1 */
+  int32_t height;     /* H >= 1 */
+  int32_t cnn_dtype;  /* df_dtype of the six network planes */
+} df_keyframe_desc;
+
+typedef struct {
+  int32_t n_gn;       /* Gauss-Newton iterations; 10 in Section II-C */
+  int32_t n_pcg;      /* PCG iterations per depth step (>= 0) */
+  float delta;        /* robust threshold on whitened residuals;
+                         <= 0 or +inf gives plain least squares */
+  int32_t loss;       /* DF_LOSS_* */
+  int32_t terms;      /* DF_TERM_* bits; must include NET or GRAD */
+  int32_t scale_step; /* 1: solve the scale in each GN iteration (paper);
+                         0: keep t fixed (Table II's scale-ambiguous solve) */
+  int32_t solver;     /* DF_SOLVER_* */
+  double tol;         /* > 0: end a depth step once ||r|| < tol ||b||;
+                         0: fixed iteration count */
+} df_solve_params;
+
+typedef struct {
+  double scale_log;    /* t = ln s after the solve */
+  double res_norm;     /* ||r|| of the last depth step's PCG residual */
+  int32_t iters_done;  /* PCG iterations executed, summed over GN iterations */
+  int32_t flags;       /* device-side status bits (0 = clean) */
+} df_solve_report;
+
+typedef struct df_keyframe df_keyframe; /* opaque; owns its device memory */
+
+/* Fill 'p' with the paper's schedule: n_gn = 10 (Section II-C), n_pcg = 3,
+ * Huber with delta = 1.345, all terms, scale step on, AUTO solver, tol = 0. */
+void df_default_params(df_solve_params *p);
+
+/* Create a keyframe from the network's per-keyframe outputs (Section II:
+ * the CNN runs once per keyframe; Section II-A lists its outputs):
+ *   mu_net  = ln d_net (Eq. 7b),  var_net = R_net (Eq. 7a),
+ *   gx, var_gx = x-gradient of the log-depth and its variance (Eq. 8b),
+ *   gy, var_gy = y-gradient and its variance (Eq. 8c).
+ * Each is H x W of desc->cnn_dtype. gx in column W-1 and gy in row H-1 are
+ * ignored (those pairwise terms have no partner pixel). The state starts at
+ * x = mu_net, t = 0; there is no semi-dense term until df_frame_update.
+ * Variances must be finite and > 0 and means finite: with host pointers a
+ * violation returns DF_EINVAL and allocates nothing; with device pointers it
+ * is detected on the device, the keyframe is marked invalid (solves leave it
+ * unchanged) and df_keyframe_check() returns DF_EINVAL.
+ * Errors: DF_EINVAL (null/size/dtype), DF_EBUDGET, DF_ENOMEM, DF_ECUDA. */
+df_status df_keyframe_create(const df_keyframe_desc *desc, const void *mu_net,
+                             const void *var_net, const void *gx, const void *var_gx,
+                             const void *gy, const void *var_gy, int ptrs_on_device,
+                             void *stream, df_keyframe **out);
+
+/* Re-initialise an existing keyframe with new network outputs (same size and
+ * dtype): as df_keyframe_create, without allocating. */
+df_status df_keyframe_reset(df_keyframe *kf, const void *mu_net, const void *var_net,
+                            const void *gx, const void *var_gx, const void *gy,
+                            const void *var_gy, int ptrs_on_device, void *stream);
+
+/* Replace the semi-dense measurements of the current frame (Sections II and
+ * II-B: updated with every new frame, already in log space):
+ *   mu_semi = ln d_semi (Eq. 6b), var_semi = R_semi (Eq. 6a), both H x W f32.
+ * A pixel without a measurement has var_semi <= 0 or a non-finite value.
+ * Errors: DF_EINVAL (null kf/pointers), DF_ECUDA. */
+df_status df_frame_update(df_keyframe *kf, const float *mu_semi, const float *var_semi,
+                          int ptrs_on_device, void *stream);
+
+/* Run one frame's solve (Section II-C): params->n_gn iterations of
+ * { scale step; re-weighting; n_pcg Jacobi-PCG iterations on the depth },
+ * warm-started from the keyframe's current (x, t). 'params' NULL = defaults.
+ * 'report' NULL: fully asynchronous. Otherwise the call synchronises the
+ * stream and fills the report.
+ * Errors: DF_EINVAL (params out of range), DF_ESTATE (invalid keyframe),
+ * DF_ETIMEOUT (fused solver's device-side wait gave up), DF_ECUDA. */
+df_status df_optimise(df_keyframe *kf, const df_solve_params *params, void *stream,
+                      df_solve_report *report);
+
+/* Solve n keyframes of possibly different sizes together (one fused launch
+ * per group that fits the device). Each keyframe's result is the one
+ * df_optimise would give it alone. 'reports' may be NULL or hold n entries
+ * (then the call synchronises). Errors as df_optimise. */
+df_status df_optimise_batch(df_keyframe *const *kfs, int32_t n,
+                            const df_solve_params *params, void *stream,
+                            df_solve_report *reports);
+
+/* Write the keyframe's depth map d = exp(x) (Eq. 5's d; log_space != 0
+ * writes x = ln d instead) as H x W f32 into 'out'. */
+df_status df_fetch_depth(df_keyframe *kf, float *out, int log_space, int ptr_on_device,
+                         void *stream);
+
+/* Read / overwrite the solver state (log-depth x as H x W f32, log scale t).
+ * Used to checkpoint and resume a keyframe and to start a solve from a
+ * chosen point. 't_out' is written when the stream reaches the call (host
+ * pointer: the call synchronises). */
+df_status df_keyframe_get_state(df_keyframe *kf, float *x_out, double *t_out,
+                                int ptrs_on_device, void *stream);
+df_status df_keyframe_set_state(df_keyframe *kf, const float *x, double t,
+                                int ptrs_on_device, void *stream);
+
+/* Evaluate the robust cost c(x, t) of Eq. 5 at the current state with the
+ * given terms/loss/delta (FP64 reduction). Synchronises the stream. */
+df_status df_cost(df_keyframe *kf, const df_solve_params *params, void *stream,
+                  double *cost_out);
+
+/* Synchronise 'stream' and return DF_EINVAL if device-side input checks
+ * flagged the keyframe, DF_ETIMEOUT if a fused solve gave up, else DF_OK. */
+df_status df_keyframe_check(df_keyframe *kf, void *stream);
+
+/* Size / dtype of a keyframe and the device bytes it holds. */
+df_status df_keyframe_info(const df_keyframe *kf, df_keyframe_desc *desc,
+                           size_t *device_bytes);
+
+/* Release a keyframe (NULL-safe). Waits for the keyframe's pending work. */
+void df_keyframe_destroy(df_keyframe *kf);
+
+/* Device bytes a keyframe of this size and dtype will hold (for admission). */
+size_t df_keyframe_bytes(int32_t width, int32_t height, int32_t cnn_dtype);
+
+/* Process-wide device-memory budget for keyframes (0 = unlimited) and the
+ * bytes currently held. */
+df_status df_set_memory_budget(size_t bytes);
+size_t df_memory_in_use(void);
+
+/* Section II-B, last sentence: semi-dense depth d and its variance
+ * sigma_d^2 to log space, to first order: mu = ln d, var = sigma_d^2 / d^2.
+ * Invalid inputs (d <= 0, variance <= 0, non-finite) give mu = 0, var = 0.
+ * n elements; all four arrays on the same side (device or host). */
+df_status df_semi_to_log(const float *depth, const float *var_depth, float *mu_semi,
+                         float *var_semi, int64_t n, int ptrs_on_device, void *stream);
+
+/* Number of kernels this library has launched in this process (all devices);
+ * a diagnostic for counting device work inside a timed region. */
+uint64_t df_kernel_launches(void);
+
+const char *df_status_str(df_status s);
+const char *df_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEEPFUSION_H */

@@ -1,0 +1,588 @@
+// C ABI of the keyframe optimiser: keyframe state, memory budget, copies,
+// input validation and the solve driver. Declarations and the contract of
+// every entry point are in include/deepfusion.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+
+#include "df_fused.cuh"
+#include "df_internal.cuh"
+
+using df::Planes;
+using df::Scalars;
+using df::SolveCfg;
+
+struct df_keyframe {
+  int device;
+  int W, H, P, dtype;
+  size_t bytes;
+  void *mem;
+  Planes planes;
+  float *staging;  // dense H x W plane for host-side depth reads
+};
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<size_t> g_in_use{0};
+std::atomic<size_t> g_budget{0};
+std::atomic<uint64_t> g_launches{0};
+
+df_status fail(df_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+df_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(DF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define DF_CUDA(call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int elem_size(int dtype) { return dtype == DF_F32 ? 4 : 2; }
+
+int pitch_of(int W) { return (int)align_up((size_t)W, df::kPitchElems); }
+
+// Byte layout of one keyframe allocation (offsets are 256-B aligned).
+struct Layout {
+  size_t cnn[6], mu_s, var_s, x, diag, wx, wy, v[df::kWorkPlanes], staging, sc, partial, total;
+};
+
+Layout layout_of(int W, int H, int dtype) {
+  Layout L;
+  const size_t P = (size_t)pitch_of(W);
+  const size_t cnn_plane = align_up(P * H * elem_size(dtype), 256);
+  const size_t f32_plane = align_up(P * H * 4, 256);
+  size_t off = 0;
+  for (int j = 0; j < 6; ++j) { L.cnn[j] = off; off += cnn_plane; }
+  L.mu_s = off; off += f32_plane;
+  L.var_s = off; off += f32_plane;
+  L.x = off; off += f32_plane;
+  L.diag = off; off += f32_plane;
+  L.wx = off; off += f32_plane;
+  L.wy = off; off += f32_plane;
+  for (int j = 0; j < df::kWorkPlanes; ++j) { L.v[j] = off; off += f32_plane; }
+  L.staging = off; off += align_up((size_t)W * H * 4, 256);
+  L.sc = off; off += align_up(sizeof(Scalars), 256);
+  L.partial = off; off += align_up(sizeof(double) * df::kMaxPartialBlocks * df::kNumQ, 256);
+  L.total = off;
+  return L;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev) {
+      prev = cur;
+      cudaSetDevice(dev);
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+float half_bits_to_float(uint16_t h) {
+  const uint32_t sign = (uint32_t)(h >> 15) << 31;
+  const int exp = (h >> 10) & 0x1f;
+  uint32_t mant = h & 0x3ff;
+  uint32_t bits;
+  if (exp == 0x1f) {
+    bits = sign | 0x7f800000u | (mant << 13);
+  } else if (exp == 0) {
+    if (mant == 0) {
+      bits = sign;
+    } else {  // subnormal: renormalise
+      int e = -1;
+      do { ++e; mant <<= 1; } while ((mant & 0x400) == 0);
+      bits = sign | ((uint32_t)(127 - 15 - e) << 23) | ((mant & 0x3ff) << 13);
+    }
+  } else {
+    bits = sign | ((uint32_t)(exp - 15 + 127) << 23) | (mant << 13);
+  }
+  float f;
+  memcpy(&f, &bits, 4);
+  return f;
+}
+
+float host_elem(const void *p, size_t i, int dtype) {
+  if (dtype == DF_F32) return static_cast<const float *>(p)[i];
+  const uint16_t h = static_cast<const uint16_t *>(p)[i];
+  if (dtype == DF_BF16) {
+    const uint32_t bits = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &bits, 4);
+    return f;
+  }
+  return half_bits_to_float(h);
+}
+
+// Host-side check of the network planes: means finite, variances finite > 0
+// (gx / var_gx in the last column and gy / var_gy in the last row ignored).
+bool host_inputs_ok(const void *const cnn[6], int W, int H, int dtype, char *why, size_t n) {
+  for (int v = 0; v < H; ++v) {
+    for (int u = 0; u < W; ++u) {
+      const size_t i = (size_t)v * W + u;
+      for (int j = 0; j < 6; ++j) {
+        if ((j == 2 || j == 3) && u == W - 1) continue;
+        if ((j == 4 || j == 5) && v == H - 1) continue;
+        const float a = host_elem(cnn[j], i, dtype);
+        const bool is_var = (j & 1) == 1;
+        if (!isfinite(a) || (is_var && !(a > 0.0f))) {
+          static const char *names[6] = {"mu_net", "var_net", "gx", "var_gx", "gy", "var_gy"};
+          snprintf(why, n, "%s at (u=%d, v=%d) is %g", names[j], u, v, (double)a);
+          return false;
+        }
+      }
+    }
+  }
+  return true;
+}
+
+df_status copy_cnn(df_keyframe *kf, const void *const cnn[6], cudaStream_t s) {
+  const size_t es = elem_size(kf->dtype);
+  for (int j = 0; j < 6; ++j) {
+    DF_CUDA(cudaMemcpy2DAsync(const_cast<void *>(kf->planes.cnn[j]), kf->P * es, cnn[j],
+                              kf->W * es, kf->W * es, kf->H, cudaMemcpyDefault, s));
+  }
+  return DF_OK;
+}
+
+df_status load_cnn(df_keyframe *kf, const void *const cnn[6], int on_device, cudaStream_t s) {
+  df_status st = copy_cnn(kf, cnn, s);
+  if (st != DF_OK) return st;
+  DF_CUDA(cudaMemsetAsync(kf->planes.sc, 0, sizeof(Scalars), s));
+  DF_CUDA(df::launch_init_state(kf->planes, s));
+  if (on_device) DF_CUDA(df::launch_check_inputs(kf->planes, s));
+  return DF_OK;
+}
+
+df_status check_params(const df_solve_params *p) {
+  if (p->n_gn < 0 || p->n_pcg < 0) return fail(DF_EINVAL, "n_gn and n_pcg must be >= 0");
+  if (p->loss != DF_LOSS_HUBER && p->loss != DF_LOSS_TUKEY)
+    return fail(DF_EINVAL, "unknown loss %d", p->loss);
+  if ((p->terms & ~DF_TERMS_ALL) != 0 || (p->terms & (DF_TERM_NET | DF_TERM_GRAD)) == 0)
+    return fail(DF_EINVAL, "terms must be DF_TERM_* bits including NET or GRAD");
+  if (p->solver < DF_SOLVER_AUTO || p->solver > DF_SOLVER_FUSED)
+    return fail(DF_EINVAL, "unknown solver %d", p->solver);
+  if (!(p->tol >= 0.0) || !isfinite(p->tol)) return fail(DF_EINVAL, "tol must be finite >= 0");
+  if (isnan(p->delta)) return fail(DF_EINVAL, "delta is NaN");
+  return DF_OK;
+}
+
+SolveCfg cfg_of(const df_solve_params *p) {
+  SolveCfg c;
+  c.delta = p->delta;
+  c.loss = p->loss;
+  c.terms = p->terms;
+  c.scale_step = p->scale_step;
+  c.tol = p->tol;
+  return c;
+}
+
+df_status read_report(df_keyframe *kf, cudaStream_t s, df_solve_report *rep) {
+  Scalars h;
+  DF_CUDA(cudaMemcpyAsync(&h, kf->planes.sc, sizeof h, cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  rep->scale_log = h.t;
+  rep->res_norm = sqrt(h.rr);
+  rep->iters_done = h.iters;
+  rep->flags = h.flags;
+  if (h.flags & df::kFlagBadInput) return fail(DF_ESTATE, "keyframe inputs failed the device check");
+  if (h.flags & df::kFlagTimeout) return fail(DF_ETIMEOUT, "fused solve: a device-side wait gave up");
+  return DF_OK;
+}
+
+}  // namespace
+
+namespace df {
+void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace df
+
+extern "C" {
+
+uint64_t df_kernel_launches(void) { return g_launches.load(); }
+
+
+void df_default_params(df_solve_params *p) {
+  if (!p) return;
+  p->n_gn = 10;
+  p->n_pcg = 3;
+  p->delta = 1.345f;
+  p->loss = DF_LOSS_HUBER;
+  p->terms = DF_TERMS_ALL;
+  p->scale_step = 1;
+  p->solver = DF_SOLVER_AUTO;
+  p->tol = 0.0;
+}
+
+size_t df_keyframe_bytes(int32_t width, int32_t height, int32_t cnn_dtype) {
+  if (width < 1 || height < 1 || cnn_dtype < DF_F32 || cnn_dtype > DF_F16) return 0;
+  return layout_of(width, height, cnn_dtype).total;
+}
+
+df_status df_set_memory_budget(size_t bytes) {
+  g_budget.store(bytes);
+  return DF_OK;
+}
+
+size_t df_memory_in_use(void) { return g_in_use.load(); }
+
+df_status df_keyframe_create(const df_keyframe_desc *desc, const void *mu_net,
+                             const void *var_net, const void *gx, const void *var_gx,
+                             const void *gy, const void *var_gy, int ptrs_on_device,
+                             void *stream, df_keyframe **out) {
+  if (!out) return fail(DF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!desc) return fail(DF_EINVAL, "desc is NULL");
+  const int W = desc->width, H = desc->height, dt = desc->cnn_dtype;
+  if (W < 1 || H < 1) return fail(DF_EINVAL, "width and height must be >= 1");
+  if ((int64_t)W * H > (int64_t)1 << 30) return fail(DF_EINVAL, "keyframe too large");
+  if (dt != DF_F32 && dt != DF_BF16 && dt != DF_F16) return fail(DF_EINVAL, "bad cnn_dtype %d", dt);
+  const void *cnn[6] = {mu_net, var_net, gx, var_gx, gy, var_gy};
+  for (int j = 0; j < 6; ++j)
+    if (!cnn[j]) return fail(DF_EINVAL, "network plane %d is NULL", j);
+  if (!ptrs_on_device) {
+    char why[256];
+    if (!host_inputs_ok(cnn, W, H, dt, why, sizeof why))
+      return fail(DF_EINVAL, "invalid network input: %s", why);
+  }
+  const Layout L = layout_of(W, H, dt);
+  // reserve budget first
+  size_t cur = g_in_use.load();
+  for (;;) {
+    const size_t budget = g_budget.load();
+    if (budget != 0 && cur + L.total > budget)
+      return fail(DF_EBUDGET, "keyframe needs %zu bytes, %zu of %zu in use", L.total, cur, budget);
+    if (g_in_use.compare_exchange_weak(cur, cur + L.total)) break;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  void *mem = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&mem, L.total);
+  if (e != cudaSuccess) {
+    g_in_use.fetch_sub(L.total);
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? DF_ENOMEM : DF_ECUDA, "cudaMalloc(%zu): %s",
+                L.total, cudaGetErrorString(e));
+  }
+  df_keyframe *kf = new df_keyframe();
+  kf->device = dev;
+  kf->W = W;
+  kf->H = H;
+  kf->P = pitch_of(W);
+  kf->dtype = dt;
+  kf->bytes = L.total;
+  kf->mem = mem;
+  char *base = static_cast<char *>(mem);
+  Planes &k = kf->planes;
+  k.W = W;
+  k.H = H;
+  k.P = kf->P;
+  k.dtype = dt;
+  for (int j = 0; j < 6; ++j) k.cnn[j] = base + L.cnn[j];
+  k.mu_s = reinterpret_cast<float *>(base + L.mu_s);
+  k.var_s = reinterpret_cast<float *>(base + L.var_s);
+  k.x = reinterpret_cast<float *>(base + L.x);
+  k.diag = reinterpret_cast<float *>(base + L.diag);
+  k.wx = reinterpret_cast<float *>(base + L.wx);
+  k.wy = reinterpret_cast<float *>(base + L.wy);
+  for (int j = 0; j < df::kWorkPlanes; ++j) k.v[j] = reinterpret_cast<float *>(base + L.v[j]);
+  k.sc = reinterpret_cast<Scalars *>(base + L.sc);
+  k.partial = reinterpret_cast<double *>(base + L.partial);
+  kf->staging = reinterpret_cast<float *>(base + L.staging);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  df_status st = DF_OK;
+  e = cudaMemsetAsync(mem, 0, L.total, s);
+  if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync");
+  if (st == DF_OK) st = load_cnn(kf, cnn, ptrs_on_device, s);
+  if (st != DF_OK) {
+    cudaStreamSynchronize(s);
+    cudaFree(mem);
+    g_in_use.fetch_sub(L.total);
+    delete kf;
+    return st;
+  }
+  *out = kf;
+  return DF_OK;
+}
+
+df_status df_keyframe_reset(df_keyframe *kf, const void *mu_net, const void *var_net,
+                            const void *gx, const void *var_gx, const void *gy,
+                            const void *var_gy, int ptrs_on_device, void *stream) {
+  if (!kf) return fail(DF_EINVAL, "keyframe is NULL");
+  const void *cnn[6] = {mu_net, var_net, gx, var_gx, gy, var_gy};
+  for (int j = 0; j < 6; ++j)
+    if (!cnn[j]) return fail(DF_EINVAL, "network plane %d is NULL", j);
+  if (!ptrs_on_device) {
+    char why[256];
+    if (!host_inputs_ok(cnn, kf->W, kf->H, kf->dtype, why, sizeof why))
+      return fail(DF_EINVAL, "invalid network input: %s", why);
+  }
+  DeviceGuard g(kf->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // no semi-dense term until the next frame update
+  DF_CUDA(cudaMemsetAsync((void *)kf->planes.var_s, 0, (size_t)kf->P * kf->H * 4, s));
+  return load_cnn(kf, cnn, ptrs_on_device, s);
+}
+
+df_status df_frame_update(df_keyframe *kf, const float *mu_semi, const float *var_semi,
+                          int ptrs_on_device, void *stream) {
+  (void)ptrs_on_device;
+  if (!kf) return fail(DF_EINVAL, "keyframe is NULL");
+  if (!mu_semi || !var_semi) return fail(DF_EINVAL, "semi-dense plane is NULL");
+  DeviceGuard g(kf->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t row = (size_t)kf->W * 4, pitch = (size_t)kf->P * 4;
+  DF_CUDA(cudaMemcpy2DAsync((void *)kf->planes.mu_s, pitch, mu_semi, row, row, kf->H,
+                            cudaMemcpyDefault, s));
+  DF_CUDA(cudaMemcpy2DAsync((void *)kf->planes.var_s, pitch, var_semi, row, row, kf->H,
+                            cudaMemcpyDefault, s));
+  return DF_OK;
+}
+
+static df_status optimise_one(df_keyframe *kf, const df_solve_params *p, cudaStream_t s) {
+  const SolveCfg c = cfg_of(p);
+  DF_CUDA(cudaMemsetAsync(&kf->planes.sc->iters, 0, sizeof(int), s));
+  DF_CUDA(cudaMemsetAsync(&kf->planes.sc->stop, 0, sizeof(int), s));
+  int solver = p->solver;
+  if (solver == DF_SOLVER_AUTO) solver = df::fused_supported() ? DF_SOLVER_FUSED : DF_SOLVER_LAUNCHES;
+  if (solver == DF_SOLVER_FUSED) {
+    if (!df::fused_supported()) return fail(DF_ENOTSUP, "fused solver not available on this device");
+    const Planes *one = &kf->planes;
+    cudaError_t e = df::launch_solve_fused(&one, 1, c, p->n_gn, p->n_pcg, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fused solve launch");
+    return DF_OK;
+  }
+  DF_CUDA(df::launch_solve_launches(kf->planes, c, p->n_gn, p->n_pcg, s));
+  return DF_OK;
+}
+
+df_status df_optimise(df_keyframe *kf, const df_solve_params *params, void *stream,
+                      df_solve_report *report) {
+  if (!kf) return fail(DF_EINVAL, "keyframe is NULL");
+  df_solve_params p;
+  if (params) {
+    p = *params;
+  } else {
+    df_default_params(&p);
+  }
+  df_status st = check_params(&p);
+  if (st != DF_OK) return st;
+  DeviceGuard g(kf->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = optimise_one(kf, &p, s);
+  if (st != DF_OK) return st;
+  if (report) return read_report(kf, s, report);
+  return DF_OK;
+}
+
+df_status df_optimise_batch(df_keyframe *const *kfs, int32_t n, const df_solve_params *params,
+                            void *stream, df_solve_report *reports) {
+  if (n < 0 || (n > 0 && !kfs)) return fail(DF_EINVAL, "bad keyframe list");
+  df_solve_params p;
+  if (params) {
+    p = *params;
+  } else {
+    df_default_params(&p);
+  }
+  df_status st = check_params(&p);
+  if (st != DF_OK) return st;
+  for (int j = 0; j < n; ++j) {
+    if (!kfs[j]) return fail(DF_EINVAL, "keyframe %d is NULL", j);
+    for (int m = 0; m < j; ++m)
+      if (kfs[m] == kfs[j]) return fail(DF_EINVAL, "keyframe %d appears twice", j);
+    if (kfs[j]->device != kfs[0]->device) return fail(DF_EINVAL, "keyframes on different devices");
+  }
+  if (n == 0) return DF_OK;
+  DeviceGuard g(kfs[0]->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int solver = p.solver;
+  if (solver == DF_SOLVER_AUTO) solver = df::fused_supported() ? DF_SOLVER_FUSED : DF_SOLVER_LAUNCHES;
+  if (solver == DF_SOLVER_FUSED) {
+    if (!df::fused_supported()) return fail(DF_ENOTSUP, "fused solver not available on this device");
+    const SolveCfg c = cfg_of(&p);
+    const Planes *list[df::kMaxBatch];
+    for (int j0 = 0; j0 < n; j0 += df::kMaxBatch) {
+      const int m = (n - j0) < df::kMaxBatch ? (n - j0) : df::kMaxBatch;
+      for (int j = 0; j < m; ++j) {
+        list[j] = &kfs[j0 + j]->planes;
+        DF_CUDA(cudaMemsetAsync(&kfs[j0 + j]->planes.sc->iters, 0, sizeof(int), s));
+        DF_CUDA(cudaMemsetAsync(&kfs[j0 + j]->planes.sc->stop, 0, sizeof(int), s));
+      }
+      cudaError_t e = df::launch_solve_fused(list, m, c, p.n_gn, p.n_pcg, s);
+      if (e != cudaSuccess) return cuda_fail(e, "fused batch launch");
+    }
+  } else {
+    for (int j = 0; j < n; ++j) {
+      st = optimise_one(kfs[j], &p, s);
+      if (st != DF_OK) return st;
+    }
+  }
+  if (reports) {
+    df_status worst = DF_OK;
+    for (int j = 0; j < n; ++j) {
+      st = read_report(kfs[j], s, &reports[j]);
+      if (st != DF_OK && worst == DF_OK) worst = st;
+    }
+    return worst;
+  }
+  return DF_OK;
+}
+
+df_status df_fetch_depth(df_keyframe *kf, float *out, int log_space, int ptr_on_device,
+                         void *stream) {
+  if (!kf) return fail(DF_EINVAL, "keyframe is NULL");
+  if (!out) return fail(DF_EINVAL, "out is NULL");
+  DeviceGuard g(kf->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (ptr_on_device) {
+    DF_CUDA(df::launch_fetch(kf->planes, out, log_space, s));
+    return DF_OK;
+  }
+  DF_CUDA(df::launch_fetch(kf->planes, kf->staging, log_space, s));
+  DF_CUDA(cudaMemcpyAsync(out, kf->staging, (size_t)kf->W * kf->H * 4, cudaMemcpyDeviceToHost, s));
+  return DF_OK;
+}
+
+df_status df_keyframe_get_state(df_keyframe *kf, float *x_out, double *t_out,
+                                int ptrs_on_device, void *stream) {
+  if (!kf) return fail(DF_EINVAL, "keyframe is NULL");
+  DeviceGuard g(kf->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (x_out) {
+    DF_CUDA(cudaMemcpy2DAsync(x_out, (size_t)kf->W * 4, kf->planes.x, (size_t)kf->P * 4,
+                              (size_t)kf->W * 4, kf->H, cudaMemcpyDefault, s));
+  }
+  if (t_out) DF_CUDA(cudaMemcpyAsync(t_out, &kf->planes.sc->t, sizeof(double), cudaMemcpyDefault, s));
+  if (!ptrs_on_device) DF_CUDA(cudaStreamSynchronize(s));
+  return DF_OK;
+}
+
+df_status df_keyframe_set_state(df_keyframe *kf, const float *x, double t, int ptrs_on_device,
+                                void *stream) {
+  (void)ptrs_on_device;
+  if (!kf) return fail(DF_EINVAL, "keyframe is NULL");
+  if (!isfinite(t)) return fail(DF_EINVAL, "t must be finite");
+  DeviceGuard g(kf->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (x) {
+    DF_CUDA(cudaMemcpy2DAsync(kf->planes.x, (size_t)kf->P * 4, x, (size_t)kf->W * 4,
+                              (size_t)kf->W * 4, kf->H, cudaMemcpyDefault, s));
+  }
+  DF_CUDA(df::launch_set_scale(kf->planes, t, s));
+  return DF_OK;
+}
+
+df_status df_cost(df_keyframe *kf, const df_solve_params *params, void *stream, double *cost_out) {
+  if (!kf || !cost_out) return fail(DF_EINVAL, "NULL argument");
+  df_solve_params p;
+  if (params) {
+    p = *params;
+  } else {
+    df_default_params(&p);
+  }
+  df_status st = check_params(&p);
+  if (st != DF_OK) return st;
+  DeviceGuard g(kf->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DF_CUDA(df::launch_cost(kf->planes, cfg_of(&p), s));
+  DF_CUDA(cudaMemcpyAsync(cost_out, &kf->planes.sc->cost, sizeof(double), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  return DF_OK;
+}
+
+df_status df_keyframe_check(df_keyframe *kf, void *stream) {
+  if (!kf) return fail(DF_EINVAL, "keyframe is NULL");
+  DeviceGuard g(kf->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int flags = 0;
+  DF_CUDA(cudaMemcpyAsync(&flags, &kf->planes.sc->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  if (flags & df::kFlagBadInput) return fail(DF_EINVAL, "network inputs failed the device check");
+  if (flags & df::kFlagTimeout) return fail(DF_ETIMEOUT, "a fused solve gave up waiting");
+  return DF_OK;
+}
+
+df_status df_keyframe_info(const df_keyframe *kf, df_keyframe_desc *desc, size_t *device_bytes) {
+  if (!kf) return fail(DF_EINVAL, "keyframe is NULL");
+  if (desc) {
+    desc->width = kf->W;
+    desc->height = kf->H;
+    desc->cnn_dtype = kf->dtype;
+  }
+  if (device_bytes) *device_bytes = kf->bytes;
+  return DF_OK;
+}
+
+void df_keyframe_destroy(df_keyframe *kf) {
+  if (!kf) return;
+  {
+    DeviceGuard g(kf->device);
+    cudaFree(kf->mem);  // waits for the keyframe's pending work
+  }
+  g_in_use.fetch_sub(kf->bytes);
+  delete kf;
+}
+
+df_status df_semi_to_log(const float *depth, const float *var_depth, float *mu_semi,
+                         float *var_semi, int64_t n, int ptrs_on_device, void *stream) {
+  if (n < 0) return fail(DF_EINVAL, "n < 0");
+  if (n == 0) return DF_OK;
+  if (!depth || !var_depth || !mu_semi || !var_semi) return fail(DF_EINVAL, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (ptrs_on_device) {
+    DF_CUDA(df::launch_semi_to_log(depth, var_depth, mu_semi, var_semi, n, s));
+    return DF_OK;
+  }
+  // host arrays: stage through stream-ordered device memory, compute on the GPU
+  float *buf = nullptr;
+  const size_t bytes = (size_t)n * 4;
+  DF_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes * 4, s));
+  df_status st = DF_OK;
+  cudaError_t e = cudaMemcpyAsync(buf, depth, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf + n, var_depth, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = df::launch_semi_to_log(buf, buf + n, buf + 2 * n, buf + 3 * n, n, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mu_semi, buf + 2 * n, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(var_semi, buf + 3 * n, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) st = cuda_fail(e, "df_semi_to_log");
+  cudaFreeAsync(buf, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (st == DF_OK && e2 != cudaSuccess) st = cuda_fail(e2, "cudaStreamSynchronize");
+  return st;
+}
+
+const char *df_status_str(df_status s) {
+  switch (s) {
+    case DF_OK: return "DF_OK";
+    case DF_EINVAL: return "DF_EINVAL";
+    case DF_ENOMEM: return "DF_ENOMEM";
+    case DF_EBUDGET: return "DF_EBUDGET";
+    case DF_ECUDA: return "DF_ECUDA";
+    case DF_ETIMEOUT: return "DF_ETIMEOUT";
+    case DF_ESTATE: return "DF_ESTATE";
+    case DF_ENOTSUP: return "DF_ENOTSUP";
+  }
+  return "DF_UNKNOWN";
+}
+
+const char *df_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+// Internal declarations of the GB300 keyframe optimiser (not part of the ABI).
+//
+// Device layout of one keyframe (one allocation, every plane 256-B aligned,
+// rows padded to a pitch P that is a multiple of 32 elements so that every
+// row starts on a 128-B boundary and 16-B vector loads never straddle it):
+//
+//   network planes (Section II-A outputs, f32 / bf16 / f16):
+//     mu_n, var_n, gx, var_gx, gy, var_gy
+//   semi-dense planes (Section II-B, f32): mu_s, var_s
+//   state (f32): x = ln d
+//   solver workspace (f32): diag, wx, wy and kWorkPlanes vectors
+//   Scalars (FP64 scale t and CG scalars) + per-block FP64 partial sums
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "deepfusion.h"
+
+namespace df {
+
+constexpr int kPitchElems = 32;     // row pitch granularity (elements)
+constexpr int kWorkPlanes = 8;      // solver vectors beyond diag / wx / wy
+constexpr int kMaxPartialBlocks = 4096;
+constexpr int kNumQ = 4;            // FP64 quantities per partial slot
+
+enum : int { kFlagBadInput = 1, kFlagTimeout = 2, kFlagBreakdown = 4 };
+
+// Per-keyframe FP64 scalars, device resident for the whole life of the
+// keyframe, so a solve needs no host round trip.
+struct alignas(64) Scalars {
+  double t;       // log scale correction, t = ln s (Eq. 6b)
+  double rho;     // r.z of the current PCG iteration
+  double alpha;   // CG step
+  double beta;    // CG direction update
+  double rr;      // r.r (convergence norm / report)
+  double bb;      // b.b (relative tolerance)
+  double gamma;   // p.Ap
+  double cost;    // last cost evaluation
+  int stop;       // the current depth step has ended early
+  int iters;      // PCG iterations executed in the current solve
+  int flags;      // kFlag* bits, sticky
+  int valid;      // 1 once inputs passed the device-side check
+  unsigned int count;  // last-block-done counter for the launch path
+  unsigned int pad[3];
+};
+
+// Everything a kernel needs to address one keyframe.
+struct Planes {
+  int W, H, P;          // width, height, pitch (elements)
+  int dtype;            // df_dtype of cnn[]
+  const void *cnn[6];   // mu_n, var_n, gx, var_gx, gy, var_gy
+  const float *mu_s, *var_s;
+  float *x;
+  float *diag, *wx, *wy;
+  float *v[kWorkPlanes];  // solver vectors (meaning depends on the schedule)
+  Scalars *sc;
+  double *partial;      // [kMaxPartialBlocks * kNumQ]
+};
+
+struct SolveCfg {
+  float delta;      // robust threshold on whitened residuals (<= 0 or inf: L2)
+  int loss;         // DF_LOSS_*
+  int terms;        // DF_TERM_* bits
+  int scale_step;   // 1: scale half of each GN iteration
+  double tol;       // relative residual tolerance (0: fixed count)
+};
+
+// ---- element loads --------------------------------------------------------
+
+template <int DT>
+__device__ __forceinline__ float ld_cnn(const void *base, size_t i) {
+  if constexpr (DT == DF_BF16) {
+    return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[i]);
+  } else if constexpr (DT == DF_F16) {
+    return __half2float(reinterpret_cast<const __half *>(base)[i]);
+  } else {
+    return reinterpret_cast<const float *>(base)[i];
+  }
+}
+
+// ---- robust weights (Section II-C, last paragraphs) -----------------------
+//
+// The IRLS weight of a term with residual r and variance V is omega(u) / V,
+// u = r / sqrt(V): omega = 1 (least squares), min(1, delta/|u|) (Huber),
+// (1 - (u/delta)^2)^2 for |u| < delta else 0 (Tukey).
+__device__ __forceinline__ bool robust_active(float delta) {
+  return delta > 0.0f && delta < INFINITY;
+}
+
+__device__ __forceinline__ float robust_weight(float r, float V, float delta, int loss) {
+  const float iv = 1.0f / V;
+  if (!robust_active(delta)) return iv;
+  const float u = fabsf(r) / sqrtf(V);
+  if (loss == DF_LOSS_TUKEY) {
+    if (u >= delta) return 0.0f;
+    const float a = u / delta;
+    const float q = 1.0f - a * a;
+    return q * q * iv;
+  }
+  return (u <= delta) ? iv : (delta / u) * iv;
+}
+
+// Robust loss rho(u) (the cost of Eq. 5 with each squared whitened residual
+// replaced), in FP64 for the cost reduction.
+__device__ __forceinline__ double robust_rho(double r, double V, double delta, int loss) {
+  const double u = r / sqrt(V);
+  if (!(delta > 0.0 && delta < INFINITY)) return u * u;
+  const double a = fabs(u);
+  if (loss == DF_LOSS_TUKEY) {
+    if (a >= delta) return delta * delta / 3.0;
+    const double q = 1.0 - (u / delta) * (u / delta);
+    return delta * delta / 3.0 * (1.0 - q * q * q);
+  }
+  return a <= delta ? u * u : 2.0 * delta * a - delta * delta;
+}
+
+__device__ __forceinline__ bool semi_valid(float mu, float var) {
+  return isfinite(mu) && isfinite(var) && var > 0.0f;
+}
+
+// ---- reductions -----------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of NQ doubles in a fixed order; the result is valid in
+// thread 0. 'sm' must hold 32 * NQ doubles.
+template <int NQ>
+__device__ __forceinline__ void block_sum(double (&v)[NQ], double *sm) {
+  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int warp = tid >> 5;
+  const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
+  __syncthreads();
+  if ((tid & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sm[warp * NQ + q] = v[q];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = (lane < nwarps) ? sm[lane * NQ + q] : 0.0;
+      v[q] = warp_sum(s);
+    }
+  }
+  (void)lane;
+}
+
+// Grid-wide FP64 sum by "last block done": every block stores its partial,
+// the last block to arrive adds all partials in block order (so the result
+// does not depend on which block came last) and returns true in thread 0
+// with the totals in 'out'. The counter is left at zero for the next use.
+template <int NQ>
+__device__ bool grid_sum_last_block(double (&v)[NQ], double *partial, unsigned int *count,
+                                    double (&out)[NQ]) {
+  __shared__ double sm[32 * NQ];
+  __shared__ bool last;
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthr = blockDim.x * blockDim.y;
+  const int nblk = gridDim.x;
+  block_sum<NQ>(v, sm);
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) partial[blockIdx.x * NQ + q] = v[q];
+    __threadfence();
+    const unsigned int prev = atomicAdd(count, 1u);
+    last = (prev == (unsigned int)nblk - 1u);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) s[q] = 0.0;
+  for (int b = tid; b < nblk; b += nthr) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s[q] += __ldcg(partial + b * NQ + q);
+  }
+  block_sum<NQ>(s, sm);
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) out[q] = s[q];
+    *count = 0u;
+  }
+  return tid == 0;
+}
+
+// ---- host-side launch wrappers (launch path, df_launch.cu) ----------------
+
+// Counts kernel launches (df_kernel_launches); call once per launch.
+void count_launches(unsigned n);
+
+int launch_grid(int tiles);  // blocks for a grid-stride launch over 32x8 tiles
+
+cudaError_t launch_init_state(const Planes &k, cudaStream_t s);
+cudaError_t launch_check_inputs(const Planes &k, cudaStream_t s);
+cudaError_t launch_solve_launches(const Planes &k, const SolveCfg &c, int n_gn, int n_pcg,
+                                  cudaStream_t s);
+cudaError_t launch_fetch(const Planes &k, float *out, int log_space, cudaStream_t s);
+cudaError_t launch_cost(const Planes &k, const SolveCfg &c, cudaStream_t s);
+cudaError_t launch_set_x(const Planes &k, const float *x_dense, cudaStream_t s);
+cudaError_t launch_set_scale(const Planes &k, double t, cudaStream_t s);
+cudaError_t launch_semi_to_log(const float *d, const float *vd, float *mu, float *var,
+                               int64_t n, cudaStream_t s);
+
+}  // namespace df

@@ -1,0 +1,350 @@
+"""Thin ctypes binding of libdeepfusion (include/deepfusion.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+Functions keep the C names. Buffers may be torch tensors (CUDA or CPU,
+contiguous) or numpy arrays (host); device-ness is read from the tensor. The
+stream defaults to torch's current stream on the tensor's device.
+
+If the compiled library is missing, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdeepfusion.so")
+
+DF_OK, DF_EINVAL, DF_ENOMEM, DF_EBUDGET, DF_ECUDA, DF_ETIMEOUT, DF_ESTATE, DF_ENOTSUP = range(8)
+DF_F32, DF_BF16, DF_F16 = 0, 1, 2
+DF_TERM_SEMI, DF_TERM_NET, DF_TERM_GRAD = 1, 2, 4
+DF_TERMS_ALL = 7
+DF_LOSS_HUBER, DF_LOSS_TUKEY = 0, 1
+DF_SOLVER_AUTO, DF_SOLVER_LAUNCHES, DF_SOLVER_FUSED = 0, 1, 2
+
+
+class df_keyframe_desc(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("cnn_dtype", C.c_int32)]
+
+
+class df_solve_params(C.Structure):
+    _fields_ = [("n_gn", C.c_int32), ("n_pcg", C.c_int32), ("delta", C.c_float),
+                ("loss", C.c_int32), ("terms", C.c_int32), ("scale_step", C.c_int32),
+                ("solver", C.c_int32), ("tol", C.c_double)]
+
+
+class df_solve_report(C.Structure):
+    _fields_ = [("scale_log", C.c_double), ("res_norm", C.c_double),
+                ("iters_done", C.c_int32), ("flags", C.c_int32)]
+
+
+class DFError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {message}")
+
+
+_STATUS = {0: "DF_OK", 1: "DF_EINVAL", 2: "DF_ENOMEM", 3: "DF_EBUDGET", 4: "DF_ECUDA",
+           5: "DF_ETIMEOUT", 6: "DF_ESTATE", 7: "DF_ENOTSUP"}
+
+_lib = None
+
+
+def load(path: Optional[str] = None) -> C.CDLL:
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libdeepfusion.so not found at {p}: build it with "
+                           "paper_2207_12244_gb300._build.build() (CUDA toolkit required)")
+    L = C.CDLL(p)
+    vp, i32, st = C.c_void_p, C.c_int32, C.c_int
+    L.df_default_params.argtypes = [C.POINTER(df_solve_params)]
+    L.df_default_params.restype = None
+    L.df_keyframe_create.argtypes = [C.POINTER(df_keyframe_desc)] + [vp] * 6 + [C.c_int, vp,
+                                                                              C.POINTER(vp)]
+    L.df_keyframe_reset.argtypes = [vp] * 7 + [C.c_int, vp]
+    L.df_frame_update.argtypes = [vp, vp, vp, C.c_int, vp]
+    L.df_optimise.argtypes = [vp, C.POINTER(df_solve_params), vp, C.POINTER(df_solve_report)]
+    L.df_optimise_batch.argtypes = [C.POINTER(vp), i32, C.POINTER(df_solve_params), vp,
+                                     C.POINTER(df_solve_report)]
+    L.df_fetch_depth.argtypes = [vp, vp, C.c_int, C.c_int, vp]
+    L.df_keyframe_get_state.argtypes = [vp, vp, vp, C.c_int, vp]
+    L.df_keyframe_set_state.argtypes = [vp, vp, C.c_double, C.c_int, vp]
+    L.df_cost.argtypes = [vp, C.POINTER(df_solve_params), vp, C.POINTER(C.c_double)]
+    L.df_keyframe_check.argtypes = [vp, vp]
+    L.df_keyframe_info.argtypes = [vp, C.POINTER(df_keyframe_desc), C.POINTER(C.c_size_t)]
+    L.df_keyframe_destroy.argtypes = [vp]
+    L.df_keyframe_destroy.restype = None
+    L.df_keyframe_bytes.argtypes = [i32, i32, i32]
+    L.df_keyframe_bytes.restype = C.c_size_t
+    L.df_set_memory_budget.argtypes = [C.c_size_t]
+    L.df_memory_in_use.argtypes = []
+    L.df_memory_in_use.restype = C.c_size_t
+    L.df_semi_to_log.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, vp]
+    L.df_kernel_launches.argtypes = []
+    L.df_kernel_launches.restype = C.c_uint64
+    L.df_status_str.argtypes = [st]
+    L.df_status_str.restype = C.c_char_p
+    L.df_last_error.argtypes = []
+    L.df_last_error.restype = C.c_char_p
+    for name in ("df_keyframe_create", "df_keyframe_reset", "df_frame_update", "df_optimise",
+                 "df_optimise_batch", "df_fetch_depth", "df_keyframe_get_state",
+                 "df_keyframe_set_state", "df_cost", "df_keyframe_check", "df_keyframe_info",
+                 "df_set_memory_budget", "df_semi_to_log"):
+        getattr(L, name).restype = st
+    if path is None:
+        _lib = L
+    return L
+
+
+def header_functions(header: Optional[str] = None) -> list:
+    """Names of the functions declared in include/deepfusion.h."""
+    h = header or os.path.join(os.path.dirname(_HERE), "include", "deepfusion.h")
+    text = open(h).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(df_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(status: int, where: str):
+    if status != DF_OK:
+        msg = load().df_last_error().decode(errors="replace")
+        raise DFError(status, where, msg)
+
+
+# ---- buffer marshalling ---------------------------------------------------
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, want_device: Optional[bool] = None):
+    """(pointer, on_device) of a contiguous tensor / array."""
+    if a is None:
+        return None, False
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), bool(a.is_cuda)
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, False
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream(stream, like=None):
+    if stream is not None:
+        if isinstance(stream, int):
+            return stream
+        return int(getattr(stream, "cuda_stream", stream))
+    if like is not None and _is_torch(like) and like.is_cuda:
+        import torch
+        return torch.cuda.current_stream(like.device).cuda_stream
+    return 0
+
+
+def _same_side(bufs: Sequence, where: str) -> int:
+    sides = {_ptr(b)[1] for b in bufs if b is not None}
+    if len(sides) > 1:
+        raise ValueError(f"{where}: mix of host and device buffers")
+    return int(sides.pop()) if sides else 0
+
+
+def _dtype_code(a) -> int:
+    if _is_torch(a):
+        import torch
+        return {torch.float32: DF_F32, torch.bfloat16: DF_BF16, torch.float16: DF_F16}[a.dtype]
+    if a.dtype == np.float32:
+        return DF_F32
+    if a.dtype == np.float16:
+        return DF_F16
+    raise ValueError("numpy network planes must be float32 or float16 "
+                     "(pass bf16 as a torch.bfloat16 tensor or set cnn_dtype explicitly)")
+
+
+# ---- entry points ---------------------------------------------------------
+
+def df_default_params(**overrides) -> df_solve_params:
+    p = df_solve_params()
+    load().df_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def df_keyframe_create(width: int, height: int, mu_net, var_net, gx, var_gx, gy, var_gy,
+                       cnn_dtype: Optional[int] = None, stream=None) -> C.c_void_p:
+    planes = [mu_net, var_net, gx, var_gx, gy, var_gy]
+    on_dev = _same_side(planes, "df_keyframe_create")
+    for p in planes:
+        if _numel(p) != width * height:
+            raise ValueError("network plane size != width*height")
+    dt = _dtype_code(mu_net) if cnn_dtype is None else cnn_dtype
+    desc = df_keyframe_desc(width, height, dt)
+    out = C.c_void_p()
+    _check(load().df_keyframe_create(C.byref(desc), *[_ptr(p)[0] for p in planes], on_dev,
+                                     _stream(stream, mu_net), C.byref(out)), "df_keyframe_create")
+    return out
+
+
+def df_keyframe_reset(kf, mu_net, var_net, gx, var_gx, gy, var_gy, stream=None):
+    planes = [mu_net, var_net, gx, var_gx, gy, var_gy]
+    on_dev = _same_side(planes, "df_keyframe_reset")
+    _check(load().df_keyframe_reset(kf, *[_ptr(p)[0] for p in planes], on_dev,
+                                    _stream(stream, mu_net)), "df_keyframe_reset")
+
+
+def df_frame_update(kf, mu_semi, var_semi, stream=None):
+    on_dev = _same_side([mu_semi, var_semi], "df_frame_update")
+    _check(load().df_frame_update(kf, _ptr(mu_semi)[0], _ptr(var_semi)[0], on_dev,
+                                  _stream(stream, mu_semi)), "df_frame_update")
+
+
+def df_optimise(kf, params: Optional[df_solve_params] = None, stream=None,
+                report: bool = False) -> Optional[df_solve_report]:
+    rep = df_solve_report() if report else None
+    _check(load().df_optimise(kf, C.byref(params) if params is not None else None,
+                              _stream(stream), C.byref(rep) if report else None), "df_optimise")
+    return rep
+
+
+def df_optimise_batch(kfs: Sequence, params: Optional[df_solve_params] = None, stream=None,
+                      report: bool = False):
+    n = len(kfs)
+    arr = (C.c_void_p * max(n, 1))(*[k.value if isinstance(k, C.c_void_p) else k for k in kfs])
+    reps = (df_solve_report * max(n, 1))() if report else None
+    _check(load().df_optimise_batch(arr, n, C.byref(params) if params is not None else None,
+                                    _stream(stream), reps), "df_optimise_batch")
+    return list(reps)[:n] if report else None
+
+
+def df_fetch_depth(kf, out, log_space: bool = False, stream=None):
+    p, dev = _ptr(out)
+    _check(load().df_fetch_depth(kf, p, int(log_space), int(dev), _stream(stream, out)),
+           "df_fetch_depth")
+    return out
+
+
+def df_keyframe_get_state(kf, x_out=None, stream=None) -> float:
+    p, dev = _ptr(x_out)
+    t = C.c_double(0.0)
+    _check(load().df_keyframe_get_state(kf, p, C.addressof(t), 0, _stream(stream, x_out)),
+           "df_keyframe_get_state")
+    return t.value
+
+
+def df_keyframe_set_state(kf, x=None, t: float = 0.0, stream=None):
+    p, dev = _ptr(x)
+    _check(load().df_keyframe_set_state(kf, p, float(t), int(dev), _stream(stream, x)),
+           "df_keyframe_set_state")
+
+
+def df_cost(kf, params: Optional[df_solve_params] = None, stream=None) -> float:
+    c = C.c_double(0.0)
+    _check(load().df_cost(kf, C.byref(params) if params is not None else None, _stream(stream),
+                          C.byref(c)), "df_cost")
+    return c.value
+
+
+def df_keyframe_check(kf, stream=None):
+    _check(load().df_keyframe_check(kf, _stream(stream)), "df_keyframe_check")
+
+
+def df_keyframe_info(kf):
+    d = df_keyframe_desc()
+    n = C.c_size_t(0)
+    _check(load().df_keyframe_info(kf, C.byref(d), C.byref(n)), "df_keyframe_info")
+    return d.width, d.height, d.cnn_dtype, n.value
+
+
+def df_keyframe_destroy(kf):
+    load().df_keyframe_destroy(kf)
+
+
+def df_keyframe_bytes(width: int, height: int, cnn_dtype: int = DF_F32) -> int:
+    return int(load().df_keyframe_bytes(width, height, cnn_dtype))
+
+
+def df_set_memory_budget(nbytes: int):
+    _check(load().df_set_memory_budget(int(nbytes)), "df_set_memory_budget")
+
+
+def df_memory_in_use() -> int:
+    return int(load().df_memory_in_use())
+
+
+def df_semi_to_log(depth, var_depth, mu_out, var_out, stream=None):
+    on_dev = _same_side([depth, var_depth, mu_out, var_out], "df_semi_to_log")
+    _check(load().df_semi_to_log(_ptr(depth)[0], _ptr(var_depth)[0], _ptr(mu_out)[0],
+                                 _ptr(var_out)[0], _numel(depth), on_dev, _stream(stream, depth)),
+           "df_semi_to_log")
+
+
+def df_kernel_launches() -> int:
+    return int(load().df_kernel_launches())
+
+
+def df_status_str(s: int) -> str:
+    return load().df_status_str(s).decode()
+
+
+def df_last_error() -> str:
+    return load().df_last_error().decode(errors="replace")
+
+
+def _numel(a) -> int:
+    return int(a.numel()) if _is_torch(a) else int(a.size)
+
+
+class Keyframe:
+    """Owning handle around a df_keyframe (calls the entry points above)."""
+
+    def __init__(self, width, height, mu_net, var_net, gx, var_gx, gy, var_gy,
+                 cnn_dtype=None, stream=None):
+        self.width, self.height = width, height
+        self.handle = df_keyframe_create(width, height, mu_net, var_net, gx, var_gx, gy, var_gy,
+                                         cnn_dtype, stream)
+
+    def reset(self, *planes, stream=None):
+        df_keyframe_reset(self.handle, *planes, stream=stream)
+
+    def frame_update(self, mu_semi, var_semi, stream=None):
+        df_frame_update(self.handle, mu_semi, var_semi, stream)
+
+    def optimise(self, params=None, stream=None, report=False):
+        return df_optimise(self.handle, params, stream, report)
+
+    def fetch_depth(self, out, log_space=False, stream=None):
+        return df_fetch_depth(self.handle, out, log_space, stream)
+
+    def get_state(self, x_out=None, stream=None):
+        return df_keyframe_get_state(self.handle, x_out, stream)
+
+    def set_state(self, x=None, t=0.0, stream=None):
+        df_keyframe_set_state(self.handle, x, t, stream)
+
+    def cost(self, params=None, stream=None):
+        return df_cost(self.handle, params, stream)
+
+    def check(self, stream=None):
+        df_keyframe_check(self.handle, stream)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            df_keyframe_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,98 @@
+"""The C ABI library without a GPU: it loads, exports every declared entry
+point, and its host-side argument checks answer before touching the device."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2207_12244_gb300 import _build, deepfusion as dfl
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return dfl.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = dfl.header_functions()
+    assert len(names) >= 19
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_defaults(lib):
+    assert dfl.df_status_str(dfl.DF_EINVAL) == "DF_EINVAL"
+    assert dfl.df_status_str(dfl.DF_ETIMEOUT) == "DF_ETIMEOUT"
+    p = dfl.df_default_params()
+    assert (p.n_gn, p.n_pcg, p.loss, p.terms, p.scale_step, p.solver, p.tol) == (
+        10, 3, dfl.DF_LOSS_HUBER, dfl.DF_TERMS_ALL, 1, dfl.DF_SOLVER_AUTO, 0.0)
+    assert abs(p.delta - 1.345) < 1e-6
+
+
+def test_keyframe_bytes_and_budget(lib):
+    b32 = dfl.df_keyframe_bytes(640, 480, dfl.DF_F32)
+    b16 = dfl.df_keyframe_bytes(640, 480, dfl.DF_BF16)
+    assert b32 > b16 > 640 * 480 * 40
+    assert dfl.df_keyframe_bytes(0, 10) == 0 and dfl.df_keyframe_bytes(10, 10, 9) == 0
+    assert dfl.df_memory_in_use() == 0
+    dfl.df_set_memory_budget(1000)
+    W, H = 8, 4
+    z = np.zeros((H, W), np.float32)
+    o = np.ones((H, W), np.float32)
+    with pytest.raises(dfl.DFError) as e:
+        dfl.df_keyframe_create(W, H, z, o, z, o, z, o)
+    assert e.value.status == dfl.DF_EBUDGET
+    dfl.df_set_memory_budget(0)
+    assert dfl.df_memory_in_use() == 0
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    W, H = 6, 5
+    z = np.zeros((H, W), np.float32)
+    o = np.ones((H, W), np.float32)
+    bad = o.copy()
+    bad[2, 3] = -1.0
+    for planes in ([z, bad, z, o, z, o], [z, o, z, bad, z, o], [z, o, z, o, z, bad]):
+        with pytest.raises(dfl.DFError) as e:
+            dfl.df_keyframe_create(W, H, *planes)
+        assert e.value.status == dfl.DF_EINVAL
+        assert "invalid network input" in str(e.value)
+    nan = z.copy()
+    nan[0, 0] = np.nan
+    with pytest.raises(dfl.DFError) as e:
+        dfl.df_keyframe_create(W, H, nan, o, z, o, z, o)
+    assert e.value.status == dfl.DF_EINVAL
+    # the ignored last column of var_gx and last row of var_gy may hold anything
+    vx = o.copy()
+    vx[:, -1] = -3.0
+    vy = o.copy()
+    vy[-1, :] = np.nan
+    desc = dfl.df_keyframe_desc(0, H, 0)
+    out = C.c_void_p()
+    ptrs = [a.ctypes.data for a in (z, o, z, o, z, o)]
+    assert lib.df_keyframe_create(C.byref(desc), *ptrs, 0, None, C.byref(out)) == dfl.DF_EINVAL
+    desc = dfl.df_keyframe_desc(W, H, 7)
+    assert lib.df_keyframe_create(C.byref(desc), *ptrs, 0, None, C.byref(out)) == dfl.DF_EINVAL
+    assert lib.df_keyframe_create(None, *ptrs, 0, None, C.byref(out)) == dfl.DF_EINVAL
+    assert lib.df_keyframe_create(C.byref(dfl.df_keyframe_desc(W, H, 0)), None, *ptrs[1:], 0,
+                                  None, C.byref(out)) == dfl.DF_EINVAL
+    assert "NULL" in dfl.df_last_error()
+
+
+def test_null_keyframe_and_bad_params(lib):
+    assert lib.df_optimise(None, None, None, None) == dfl.DF_EINVAL
+    assert lib.df_frame_update(None, None, None, 0, None) == dfl.DF_EINVAL
+    assert lib.df_fetch_depth(None, None, 0, 0, None) == dfl.DF_EINVAL
+    lib.df_keyframe_destroy(None)  # NULL-safe
+    bad = [dict(n_gn=-1), dict(n_pcg=-2), dict(loss=5), dict(terms=0), dict(terms=1),
+           dict(terms=8), dict(solver=9), dict(tol=-1.0), dict(tol=float("inf")),
+           dict(delta=float("nan"))]
+    arr = (C.c_void_p * 1)(None)
+    for b in bad:
+        p = dfl.df_default_params(**b)
+        # batch checks the parameters before touching any keyframe
+        assert lib.df_optimise_batch(arr, 0, C.byref(p), None, None) == dfl.DF_EINVAL, b
+    assert lib.df_optimise_batch(None, 3, None, None, None) == dfl.DF_EINVAL
+    assert lib.df_semi_to_log(None, None, None, None, -1, 0, None) == dfl.DF_EINVAL
+    assert lib.df_semi_to_log(None, None, None, None, 0, 0, None) == dfl.DF_OK

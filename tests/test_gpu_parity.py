@@ -1,0 +1,279 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bar (FP32 storage and arithmetic, FP64 reductions): max relative depth error
+<= 1e-4 and |t_gpu - t_oracle| <= 1e-4 at equal iteration count.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import (DEPTH_RTOL, assert_parity, create, oracle_solve, params, solve,
+                      to_dev, torch_cuda)
+from paper_2207_12244_gb300 import deepfusion as dfl
+from paper_2207_12244_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SOLVERS = [dfl.DF_SOLVER_LAUNCHES, dfl.DF_SOLVER_FUSED]
+SOLVER_IDS = ["launches", "fused"]
+
+
+@pytest.fixture(scope="module")
+def o():
+    return oracle.get()
+
+
+@pytest.fixture(scope="module", params=SOLVERS, ids=SOLVER_IDS)
+def solver(request):
+    return request.param
+
+
+# The workload of the paper's network resolution: 256 x 192, 10 GN x 3 PCG.
+def test_config1_256x192(o, solver):
+    kf = synth.make_keyframe(256, 192, 0)
+    prm = params(n_gn=10, n_pcg=3, solver=solver)
+    x, t, rep = solve(kf, prm)
+    xo, to, ro = oracle_solve(o, kf, prm)
+    assert_parity(x, t, xo, to, what="256x192")
+    assert rep.iters_done == ro.iters_done == 30
+    assert rep.flags == 0
+    assert np.isclose(rep.res_norm, ro.res_norm, rtol=1e-2)
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (2, 2), (1, 17), (23, 1), (17, 13), (33, 9),
+                                  (100, 37), (129, 65), (31, 200)])
+def test_edge_sizes(o, solver, W, H):
+    kf = synth.make_keyframe(W, H, 100 + W * 7 + H)
+    prm = params(n_gn=4, n_pcg=4, solver=solver)
+    x, t, rep = solve(kf, prm)
+    xo, to, ro = oracle_solve(o, kf, prm)
+    assert_parity(x, t, xo, to, what=f"{W}x{H}")
+    assert rep.iters_done == ro.iters_done
+
+
+@pytest.mark.parametrize("mode", ["l2", "huber", "tukey", "semi+net", "net+grad", "semi+grad",
+                                  "no-scale-step"])
+def test_modes(o, solver, mode):
+    kf = synth.make_keyframe(96, 72, 7)
+    kw = dict(n_gn=6, n_pcg=5, solver=solver)
+    if mode == "l2":
+        kw["delta"] = float("inf")
+    elif mode == "tukey":
+        kw.update(loss=dfl.DF_LOSS_TUKEY, delta=4.685)
+    elif mode == "semi+net":
+        kw["terms"] = dfl.DF_TERM_SEMI | dfl.DF_TERM_NET
+    elif mode == "net+grad":
+        kw["terms"] = dfl.DF_TERM_NET | dfl.DF_TERM_GRAD
+    elif mode == "semi+grad":
+        kw.update(terms=dfl.DF_TERM_SEMI | dfl.DF_TERM_GRAD, scale_step=0)
+    elif mode == "no-scale-step":
+        kw["scale_step"] = 0
+    prm = params(**kw)
+    x, t, rep = solve(kf, prm)
+    xo, to, ro = oracle_solve(o, kf, prm)
+    assert_parity(x, t, xo, to, what=mode)
+    assert rep.iters_done == ro.iters_done
+
+
+def test_prior_only_returns_cnn_depth_bitwise(o, solver):
+    kf = synth.make_keyframe(64, 48, 9)
+    prm = params(terms=dfl.DF_TERM_NET, solver=solver)
+    x, t, rep = solve(kf, prm)
+    assert np.array_equal(x.astype(np.float32), kf.mu_n)
+    assert t == 0.0 and rep.iters_done == 0
+    # from a perturbed start one Jacobi-PCG iteration lands on mu_n
+    rng = np.random.default_rng(0)
+    x0 = kf.mu_n + rng.normal(0, 0.3, kf.mu_n.shape).astype(np.float32)
+    x, t, rep = solve(kf, params(terms=dfl.DF_TERM_NET, n_gn=1, n_pcg=1, solver=solver), x0=x0)
+    assert np.abs(x - kf.mu_n).max() < 1e-6
+
+
+def test_no_semi_frame(o, solver):
+    kf = synth.make_keyframe(80, 60, 11)
+    prm = params(solver=solver)
+    x, t, rep = solve(kf, prm, semi=False)
+    xo, to, _ = oracle_solve(o, kf, prm, semi=False)
+    assert t == 0.0 and to == 0.0
+    assert_parity(x, t, xo, to, what="no semi")
+
+
+def test_invalid_semi_pixels_are_missing(o, solver):
+    kf = synth.make_keyframe(70, 50, 12)
+    rng = np.random.default_rng(4)
+    idx = rng.choice(kf.n_pixels, 400, replace=False)
+    ms, vs = kf.mu_s.ravel().copy(), kf.var_s.ravel().copy()
+    ms[idx[:100]] = np.nan
+    vs[idx[100:200]] = np.inf
+    vs[idx[200:300]] = -1.0
+    ms[idx[300:]] = np.inf
+    vs[idx[300:]] = 1e-3
+    kf.mu_s, kf.var_s = ms.reshape(kf.mu_s.shape), vs.reshape(kf.var_s.shape)
+    prm = params(solver=solver)
+    x, t, _ = solve(kf, prm)
+    xo, to, _ = oracle_solve(o, kf, prm)
+    assert_parity(x, t, xo, to, what="invalid semi")
+
+
+def test_host_and_device_pointers_agree(solver):
+    kf = synth.make_keyframe(120, 90, 13)
+    prm = params(solver=solver)
+    xd, td, _ = solve(kf, prm, on_device=True)
+    xh, th, _ = solve(kf, prm, on_device=False)
+    assert np.array_equal(xd, xh) and td == th
+
+
+def test_deterministic(solver):
+    kf = synth.make_keyframe(200, 150, 14)
+    prm = params(n_gn=5, n_pcg=5, solver=solver)
+    a = solve(kf, prm)
+    b = solve(kf, prm)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+
+
+def test_tolerance_mode(o, solver):
+    kf = synth.make_keyframe(64, 64, 15)
+    prm = params(n_gn=5, n_pcg=200, tol=1e-3, solver=solver)
+    x, t, rep = solve(kf, prm)
+    xo, to, ro = oracle_solve(o, kf, prm)
+    assert rep.iters_done < 5 * 200
+    assert abs(rep.iters_done - ro.iters_done) <= 2
+    assert_parity(x, t, xo, to, rtol=5e-4, atol_t=5e-4, what="tol")
+
+
+def test_warm_started_sequence(o, solver):
+    """Config-2 recipe at reduced size: 100 frames, mask 5% -> 40%, 10 x 5."""
+    torch = torch_cuda()
+    kf, mus, vs = synth.make_sequence(128, 96, 21, n_frames=100)
+    prm = params(n_gn=10, n_pcg=5, solver=solver)
+    k = create(kf)
+    try:
+        dmu, dvs = to_dev(mus), to_dev(vs)
+        for f in range(mus.shape[0]):
+            k.frame_update(dmu[f], dvs[f])
+            k.optimise(prm)
+        out = torch.empty((kf.height, kf.width), dtype=torch.float32, device="cuda")
+        k.fetch_depth(out, log_space=True)
+        t = k.get_state()
+        x = out.double().cpu().numpy()
+    finally:
+        k.close()
+    xo, to = o.optimise_sequence(kf, mus, vs, n_gn=10, n_pcg=5, delta=prm.delta)
+    assert_parity(x, t, xo, to, what="sequence")
+
+
+def test_full_size_640x480_first_frames(o, solver):
+    """The benchmark's keyframe size (640 x 480) and schedule (10 x 5), first
+    frames of the sequence, every pixel compared."""
+    torch = torch_cuda()
+    kf, mus, vs = synth.make_sequence(640, 480, 1, n_frames=100)
+    prm = params(n_gn=10, n_pcg=5, solver=solver)
+    k = create(kf)
+    nf = 3
+    try:
+        for f in range(nf):
+            k.frame_update(to_dev(mus[f]), to_dev(vs[f]))
+            k.optimise(prm)
+        out = torch.empty((480, 640), dtype=torch.float32, device="cuda")
+        k.fetch_depth(out, log_space=True)
+        t = k.get_state()
+        x = out.double().cpu().numpy()
+    finally:
+        k.close()
+    xo, to = o.optimise_sequence(kf, mus, vs, n_gn=10, n_pcg=5, delta=prm.delta,
+                                 frames=range(nf))
+    assert_parity(x, t, xo, to, what="640x480")
+
+
+def test_cost_matches_oracle(o):
+    kf = synth.make_keyframe(90, 70, 16)
+    k = create(kf)
+    try:
+        k.frame_update(to_dev(kf.mu_s), to_dev(kf.var_s))
+        rng = np.random.default_rng(1)
+        x0 = (kf.mu_n + rng.normal(0, 0.05, kf.mu_n.shape)).astype(np.float32)
+        k.set_state(to_dev(x0), 0.3)
+        for delta, loss in ((1.345, 0), (float("inf"), 0), (4.685, 1)):
+            c = k.cost(params(delta=delta, loss=loss))
+            co = o.cost(kf, x0, 0.3, delta, loss=loss)
+            assert np.isclose(c, co, rtol=1e-5), (delta, loss, c, co)
+    finally:
+        k.close()
+
+
+def test_state_roundtrip_and_fetch_depth():
+    torch = torch_cuda()
+    kf = synth.make_keyframe(50, 40, 17)
+    k = create(kf)
+    try:
+        x = np.random.default_rng(2).normal(0, 1, (40, 50)).astype(np.float32)
+        k.set_state(x, -0.25)
+        xb = np.empty_like(x)
+        t = k.get_state(xb)
+        assert np.array_equal(xb, x) and t == -0.25
+        d = np.empty_like(x)
+        k.fetch_depth(d)  # host output
+        assert np.allclose(d, np.exp(x.astype(np.float64)), rtol=2e-7)
+        dd = torch.empty((40, 50), dtype=torch.float32, device="cuda")
+        k.fetch_depth(dd)
+        assert np.array_equal(dd.cpu().numpy(), d)
+    finally:
+        k.close()
+
+
+def test_semi_to_log_matches_oracle(o):
+    torch = torch_cuda()
+    rng = np.random.default_rng(5)
+    n = 100003
+    d = rng.uniform(0.3, 6.0, n).astype(np.float32)
+    vd = (0.01 * d ** 2) ** 2
+    vd = vd.astype(np.float32)
+    d[:50] = -1.0
+    vd[50:100] = 0.0
+    d[100] = np.nan
+    mu_o, var_o = o.semi_to_log(d, vd)
+    mu = torch.empty(n, device="cuda")
+    var = torch.empty(n, device="cuda")
+    dfl.df_semi_to_log(to_dev(d), to_dev(vd), mu, var)
+    assert np.allclose(mu.cpu().numpy(), mu_o, rtol=0, atol=2e-7)
+    assert np.allclose(var.cpu().numpy(), var_o, rtol=2e-6, atol=0)
+    mh, vh = np.empty(n, np.float32), np.empty(n, np.float32)
+    dfl.df_semi_to_log(d, vd, mh, vh)
+    assert np.array_equal(mh, mu.cpu().numpy()) and np.array_equal(vh, var.cpu().numpy())
+
+
+def test_device_input_check_marks_keyframe():
+    kf = synth.make_keyframe(40, 30, 18)
+    planes = [p.copy() for p in kf.cnn_planes]
+    planes[1][3, 4] = -0.5  # a negative network variance
+    k = dfl.Keyframe(40, 30, *[to_dev(p) for p in planes])
+    try:
+        with pytest.raises(dfl.DFError) as e:
+            k.check()
+        assert e.value.status == dfl.DF_EINVAL
+        with pytest.raises(dfl.DFError) as e:
+            k.optimise(params(), report=True)
+        assert e.value.status == dfl.DF_ESTATE
+        x = np.empty((30, 40), np.float32)
+        k.get_state(x)
+        assert np.array_equal(x, planes[0])  # solve left the state untouched
+    finally:
+        k.close()
+
+
+def test_budget_accounting_with_gpu():
+    kf = synth.make_keyframe(64, 48, 19)
+    need = dfl.df_keyframe_bytes(64, 48)
+    base = dfl.df_memory_in_use()
+    dfl.df_set_memory_budget(base + need + need // 2)
+    try:
+        a = create(kf)
+        assert dfl.df_memory_in_use() == base + need
+        with pytest.raises(dfl.DFError) as e:
+            create(kf)
+        assert e.value.status == dfl.DF_EBUDGET
+        a.close()
+        assert dfl.df_memory_in_use() == base
+        b = create(kf)
+        b.close()
+    finally:
+        dfl.df_set_memory_budget(0)
