@@ -23,7 +23,11 @@ struct df_keyframe {
   size_t bytes;
   void *mem;
   Planes planes;
-  float *staging;  // dense H x W plane for host-side depth reads
+  float *staging;   // dense H x W plane for host-side depth reads
+  void *plan;       // resident launch plan of the fused solver (single keyframe)
+  size_t plan_cap;  // bytes reserved for it
+  int plan_G = 0, plan_vec = 0;  // shape of the plan currently on the device (0: none)
+  df::FusedTuning plan_tune;
 };
 
 namespace {
@@ -32,6 +36,9 @@ thread_local std::string g_err;
 std::atomic<size_t> g_in_use{0};
 std::atomic<size_t> g_budget{0};
 std::atomic<uint64_t> g_launches{0};
+std::atomic<unsigned long long> g_spin_limit_ns{2000000000ull};
+std::mutex g_tune_mu;
+df::FusedTuning g_tune;
 
 df_status fail(df_status s, const char *fmt, ...) {
   char buf[512];
@@ -61,7 +68,8 @@ int pitch_of(int W) { return (int)align_up((size_t)W, df::kPitchElems); }
 
 // Byte layout of one keyframe allocation (offsets are 256-B aligned).
 struct Layout {
-  size_t cnn[6], mu_s, var_s, x, diag, wx, wy, v[df::kWorkPlanes], staging, sc, partial, total;
+  size_t cnn[6], mu_s, var_s, x, diag, wx, wy, v[df::kWorkPlanes], staging, sc, partial, plan,
+      plan_cap, total;
 };
 
 Layout layout_of(int W, int H, int dtype) {
@@ -81,6 +89,9 @@ Layout layout_of(int W, int H, int dtype) {
   L.staging = off; off += align_up((size_t)W * H * 4, 256);
   L.sc = off; off += align_up(sizeof(Scalars), 256);
   L.partial = off; off += align_up(sizeof(double) * df::kMaxPartialBlocks * df::kNumQ, 256);
+  L.plan = off;
+  L.plan_cap = df::fused_supported() ? align_up(df::fused_plan_bytes(1, df::fused_max_ctas()), 256) : 0;
+  off += L.plan_cap;
   L.total = off;
   return L;
 }
@@ -308,6 +319,8 @@ df_status df_keyframe_create(const df_keyframe_desc *desc, const void *mu_net,
   k.sc = reinterpret_cast<Scalars *>(base + L.sc);
   k.partial = reinterpret_cast<double *>(base + L.partial);
   kf->staging = reinterpret_cast<float *>(base + L.staging);
+  kf->plan = L.plan_cap ? base + L.plan : nullptr;
+  kf->plan_cap = L.plan_cap;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   df_status st = DF_OK;
   e = cudaMemsetAsync(mem, 0, L.total, s);
@@ -358,19 +371,79 @@ df_status df_frame_update(df_keyframe *kf, const float *mu_semi, const float *va
   return DF_OK;
 }
 
+static df::FusedTuning current_tuning() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune;
+}
+
+static bool same_tuning(const df::FusedTuning &a, const df::FusedTuning &b) {
+  return a.vec == b.vec && a.tile_rows == b.tile_rows && a.max_ctas == b.max_ctas;
+}
+
+static int pick_solver(int requested) {
+  if (requested != DF_SOLVER_AUTO) return requested;
+  return df::fused_supported() ? DF_SOLVER_FUSED : DF_SOLVER_LAUNCHES;
+}
+
+// Fused solve of one keyframe: its launch plan lives in the keyframe's own
+// allocation and is uploaded once per launch shape.
+static df_status fused_one(df_keyframe *kf, const SolveCfg &c, int n_gn, int n_pcg,
+                           cudaStream_t s) {
+  if (!df::fused_supported() || !kf->plan) return fail(DF_ENOTSUP, "fused solver not available on this device");
+  const df::FusedTuning tune = current_tuning();
+  if (kf->plan_G == 0 || !same_tuning(tune, kf->plan_tune)) {
+    std::vector<char> host;
+    int G = 0, vec = 0;
+    const Planes *one = &kf->planes;
+    if (!df::fused_build_plan(&one, 1, tune, host, G, vec))
+      return fail(DF_EINVAL, "fused solver: no launch plan for this keyframe");
+    if (host.size() > kf->plan_cap) return fail(DF_EINVAL, "fused plan larger than reserved");
+    DF_CUDA(cudaMemcpyAsync(kf->plan, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+    kf->plan_G = G;
+    kf->plan_vec = vec;
+    kf->plan_tune = tune;
+  }
+  DF_CUDA(df::fused_launch(kf->plan, kf->plan_G, kf->plan_vec, c, n_gn, n_pcg,
+                           g_spin_limit_ns.load(), s));
+  return DF_OK;
+}
+
+// Fused solve of a list of keyframes in as few launches as the plan allows
+// (a list whose tiles cannot share one grid is split in halves).
+static df_status fused_many(df_keyframe *const *kfs, int n, const SolveCfg &c, int n_gn,
+                            int n_pcg, cudaStream_t s) {
+  if (n <= 0) return DF_OK;
+  if (n == 1) return fused_one(kfs[0], c, n_gn, n_pcg, s);
+  if (n > df::kMaxBatch) {
+    df_status st = fused_many(kfs, df::kMaxBatch, c, n_gn, n_pcg, s);
+    if (st != DF_OK) return st;
+    return fused_many(kfs + df::kMaxBatch, n - df::kMaxBatch, c, n_gn, n_pcg, s);
+  }
+  std::vector<const Planes *> list(n);
+  for (int j = 0; j < n; ++j) list[j] = &kfs[j]->planes;
+  std::vector<char> host;
+  int G = 0, vec = 0;
+  if (!df::fused_build_plan(list.data(), n, current_tuning(), host, G, vec)) {
+    const int h = n / 2;
+    df_status st = fused_many(kfs, h, c, n_gn, n_pcg, s);
+    if (st != DF_OK) return st;
+    return fused_many(kfs + h, n - h, c, n_gn, n_pcg, s);
+  }
+  void *dplan = nullptr;
+  DF_CUDA(cudaMallocAsync(&dplan, host.size(), s));
+  cudaError_t e = cudaMemcpyAsync(dplan, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = df::fused_launch(dplan, G, vec, c, n_gn, n_pcg, g_spin_limit_ns.load(), s);
+  cudaError_t e2 = cudaFreeAsync(dplan, s);
+  if (e != cudaSuccess) return cuda_fail(e, "fused batch launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+  return DF_OK;
+}
+
 static df_status optimise_one(df_keyframe *kf, const df_solve_params *p, cudaStream_t s) {
   const SolveCfg c = cfg_of(p);
+  if (pick_solver(p->solver) == DF_SOLVER_FUSED) return fused_one(kf, c, p->n_gn, p->n_pcg, s);
   DF_CUDA(cudaMemsetAsync(&kf->planes.sc->iters, 0, sizeof(int), s));
   DF_CUDA(cudaMemsetAsync(&kf->planes.sc->stop, 0, sizeof(int), s));
-  int solver = p->solver;
-  if (solver == DF_SOLVER_AUTO) solver = df::fused_supported() ? DF_SOLVER_FUSED : DF_SOLVER_LAUNCHES;
-  if (solver == DF_SOLVER_FUSED) {
-    if (!df::fused_supported()) return fail(DF_ENOTSUP, "fused solver not available on this device");
-    const Planes *one = &kf->planes;
-    cudaError_t e = df::launch_solve_fused(&one, 1, c, p->n_gn, p->n_pcg, s);
-    if (e != cudaSuccess) return cuda_fail(e, "fused solve launch");
-    return DF_OK;
-  }
   DF_CUDA(df::launch_solve_launches(kf->planes, c, p->n_gn, p->n_pcg, s));
   return DF_OK;
 }
@@ -414,22 +487,9 @@ df_status df_optimise_batch(df_keyframe *const *kfs, int32_t n, const df_solve_p
   if (n == 0) return DF_OK;
   DeviceGuard g(kfs[0]->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int solver = p.solver;
-  if (solver == DF_SOLVER_AUTO) solver = df::fused_supported() ? DF_SOLVER_FUSED : DF_SOLVER_LAUNCHES;
-  if (solver == DF_SOLVER_FUSED) {
-    if (!df::fused_supported()) return fail(DF_ENOTSUP, "fused solver not available on this device");
-    const SolveCfg c = cfg_of(&p);
-    const Planes *list[df::kMaxBatch];
-    for (int j0 = 0; j0 < n; j0 += df::kMaxBatch) {
-      const int m = (n - j0) < df::kMaxBatch ? (n - j0) : df::kMaxBatch;
-      for (int j = 0; j < m; ++j) {
-        list[j] = &kfs[j0 + j]->planes;
-        DF_CUDA(cudaMemsetAsync(&kfs[j0 + j]->planes.sc->iters, 0, sizeof(int), s));
-        DF_CUDA(cudaMemsetAsync(&kfs[j0 + j]->planes.sc->stop, 0, sizeof(int), s));
-      }
-      cudaError_t e = df::launch_solve_fused(list, m, c, p.n_gn, p.n_pcg, s);
-      if (e != cudaSuccess) return cuda_fail(e, "fused batch launch");
-    }
+  if (pick_solver(p.solver) == DF_SOLVER_FUSED) {
+    st = fused_many(kfs, n, cfg_of(&p), p.n_gn, p.n_pcg, s);
+    if (st != DF_OK) return st;
   } else {
     for (int j = 0; j < n; ++j) {
       st = optimise_one(kfs[j], &p, s);

@@ -1,12 +1,985 @@
+// Fused persistent solver: one cooperative launch runs a whole per-frame
+// solve (Section II-C: n_gn Gauss-Newton iterations alternating scale and
+// depth) for one keyframe or a batch of keyframes of different sizes.
+//
+// Depth step: Jacobi-preconditioned CG in the Chronopoulos-Gear arrangement,
+// which has the iterates of textbook PCG in exact arithmetic but needs one
+// global reduction per iteration instead of two:
+//   u = r / diag,  w = A u,  gamma = (r, u),  delta = (w, u)
+//   beta  = gamma_i / gamma_{i-1},  alpha = gamma_i / (delta_i - beta gamma_i / alpha_{i-1})
+//   p = u + beta p,  s = w + beta s  (= A p),  x += alpha p,  r -= alpha s
+// The breakdown / stop rules are those of the textbook form: stop when
+// gamma = r.z = 0 or when p.Ap = delta - beta gamma / alpha <= 0, or (tol > 0)
+// when ||r|| < tol ||b||.
+//
+// Passes, each ended by one grid barrier:
+//   SCALE     scale-step partial sums (first GN iteration only)
+//   ASSEMBLE  IRLS weights of Eqs. 6-8 at (x, t), 5-point system, r0
+//   INIT      w0 = A u0
+//   ITER      one CG iteration (all but the last of a depth step)
+//   FINAL     last CG iteration's x update, plus the next GN iteration's
+//             scale-step sums taken at the new x
+//
+// Work: the planes are cut into tiles of (32 * VEC) columns x th rows; a warp
+// owns a tile and walks down its rows keeping the row above / below in
+// registers (5-point stencil), lanes exchange the left / right neighbours by
+// shuffles. Tiles are cut into contiguous ranges, one per CTA; a CTA's range
+// may span a few keyframes ("segments").
+//
+// Reductions: per tile a warp sums its FP32 per-lane partials in FP64, per
+// CTA the warps' sums are added in warp order into one slot per (CTA,
+// keyframe); after the barrier every CTA that needs a keyframe's scalar adds
+// that keyframe's slots in slot order. All CTAs therefore compute bitwise
+// identical scalars, and the result does not depend on timing.
+//
+// Barrier: a generation-counting grid barrier whose waits give up after a
+// time limit (%globaltimer); a CTA that gives up raises an abort word, every
+// CTA then skips the remaining passes, the keyframes are flagged
+// kFlagTimeout and the host reports DF_ETIMEOUT. The last CTA to exit resets
+// the barrier words, so the next launch starts clean either way.
+#include <math.h>
+
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include "df_fused.cuh"
 
 namespace df {
 
-bool fused_supported() { return false; }
+namespace {
 
-cudaError_t launch_solve_fused(const Planes *const *, int, const SolveCfg &, int, int,
-                               cudaStream_t) {
-  return cudaErrorNotSupported;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxSeg = 8;  // keyframes a CTA's tile range may span
+constexpr int kQ = 3;       // FP64 partial sums per slot
+
+enum PassKind : int { P_SCALE = 0, P_ASSEMBLE, P_INIT, P_ITER, P_FINAL };
+
+struct FusedKf {
+  Planes pl;
+  int tile_begin;  // first global tile index
+  int ntiles;
+  int tiles_x;     // column tiles per row band
+  int th;          // rows per tile
+  int slot_begin;  // this keyframe's slots: [slot_begin, slot_end)
+  int slot_end;
+  int writer_cta;  // the CTA that writes the final scalars back
+  int pad;
+};
+
+struct PlanHeader {
+  int nkf, G, ntiles, nslots;
+  int vec, pad0;
+  unsigned int bar_count, bar_gen, exit_count, abort;
+  long long off_cta_tile, off_cta_kf, off_cta_slot, off_kf, off_slots;
+  long long bytes;
+};
+
+// ---- small vector helpers ---------------------------------------------------
+
+template <int VEC>
+struct F {
+  float v[VEC];
+};
+
+template <int VEC>
+__device__ __forceinline__ F<VEC> fzero() {
+  F<VEC> a;
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) a.v[e] = 0.0f;
+  return a;
+}
+
+// coherent (L2) loads / stores for planes the kernel itself rewrites
+template <int VEC>
+__device__ __forceinline__ F<VEC> ldm(const float *p) {
+  F<VEC> a;
+  if constexpr (VEC == 4) {
+    const float4 q = __ldcg(reinterpret_cast<const float4 *>(p));
+    a.v[0] = q.x; a.v[1] = q.y; a.v[2] = q.z; a.v[3] = q.w;
+  } else {
+    a.v[0] = __ldcg(p);
+  }
+  return a;
+}
+
+template <int VEC>
+__device__ __forceinline__ void stm(float *p, const F<VEC> &a) {
+  if constexpr (VEC == 4) {
+    __stcg(reinterpret_cast<float4 *>(p), make_float4(a.v[0], a.v[1], a.v[2], a.v[3]));
+  } else {
+    __stcg(p, a.v[0]);
+  }
+}
+
+// read-only planes (network and semi-dense inputs) through the read-only path
+template <int VEC>
+__device__ __forceinline__ F<VEC> ldr(const float *p) {
+  F<VEC> a;
+  if constexpr (VEC == 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    a.v[0] = q.x; a.v[1] = q.y; a.v[2] = q.z; a.v[3] = q.w;
+  } else {
+    a.v[0] = __ldg(p);
+  }
+  return a;
+}
+
+template <int VEC, int DT>
+__device__ __forceinline__ F<VEC> ldc(const void *base, size_t i) {
+  if constexpr (DT == DF_F32) {
+    return ldr<VEC>(reinterpret_cast<const float *>(base) + i);
+  } else {
+    F<VEC> a;
+    if constexpr (VEC == 4) {
+      const uint2 q = __ldg(reinterpret_cast<const uint2 *>(
+          reinterpret_cast<const unsigned short *>(base) + i));
+      const unsigned short h[4] = {(unsigned short)(q.x & 0xffff), (unsigned short)(q.x >> 16),
+                                   (unsigned short)(q.y & 0xffff), (unsigned short)(q.y >> 16)};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if constexpr (DT == DF_BF16)
+          a.v[e] = __bfloat162float(__ushort_as_bfloat16(h[e]));
+        else
+          a.v[e] = __half2float(__ushort_as_half(h[e]));
+      }
+    } else {
+      a.v[0] = ld_cnn<DT>(base, i);
+    }
+    return a;
+  }
+}
+
+__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+__device__ __forceinline__ float safe_div(float r, float d) { return d > 0.0f ? r / d : 0.0f; }
+
+struct Geo {
+  int c0, r0, nrows, col;
+};
+
+template <int VEC>
+__device__ __forceinline__ Geo geo_of(const FusedKf &K, int lt) {
+  Geo g;
+  const int tx = lt % K.tiles_x, ty = lt / K.tiles_x;
+  g.c0 = tx * 32 * VEC;
+  g.r0 = ty * K.th;
+  g.nrows = min(K.th, K.pl.H - g.r0);
+  g.col = g.c0 + (threadIdx.x & 31) * VEC;
+  return g;
+}
+
+// ---- SCALE: partial sums of the scale step (Eq. 6 with x fixed) ------------
+template <int VEC>
+__device__ void scale_tile(const FusedKf &K, int lt, float t, const SolveCfg &c, float acc[kQ]) {
+  const Planes &k = K.pl;
+  const Geo g = geo_of<VEC>(K, lt);
+  for (int j = 0; j < g.nrows; ++j) {
+    const size_t i = (size_t)(g.r0 + j) * k.P + g.col;
+    const F<VEC> x = ldm<VEC>(k.x + i);
+    const F<VEC> ms = ldr<VEC>(k.mu_s + i), vs = ldr<VEC>(k.var_s + i);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      if (g.col + e < k.W && semi_valid(ms.v[e], vs.v[e])) {
+        const float w = robust_weight(x.v[e] - t - ms.v[e], vs.v[e], c.delta, c.loss);
+        acc[0] += w;
+        acc[1] += w * (x.v[e] - ms.v[e]);
+      }
+    }
+  }
+}
+
+// ---- ASSEMBLE: weights, 5-point system and r0 (see df_launch.cu) -----------
+template <int VEC, int DT>
+__device__ void assemble_tile(const FusedKf &K, int lt, float t, const SolveCfg &c,
+                              float acc[kQ]) {
+  const Planes &k = K.pl;
+  const Geo g = geo_of<VEC>(K, lt);
+  const int lane = threadIdx.x & 31;
+  const int W = k.W, H = k.H;
+  const size_t P = k.P;
+  const bool semi = c.terms & DF_TERM_SEMI, net = c.terms & DF_TERM_NET,
+             grad = c.terms & DF_TERM_GRAD;
+  float *r_out = k.v[1];
+  F<VEC> x_cur = ldm<VEC>(k.x + (size_t)g.r0 * P + g.col);
+  F<VEC> wy_up = fzero<VEC>(), ey_up = fzero<VEC>(), gy_up = fzero<VEC>();
+  if (grad && g.r0 > 0) {
+    const size_t iu = (size_t)(g.r0 - 1) * P + g.col;
+    const F<VEC> xu = ldm<VEC>(k.x + iu);
+    const F<VEC> gyu = ldc<VEC, DT>(k.cnn[4], iu), vyu = ldc<VEC, DT>(k.cnn[5], iu);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      if (g.col + e < W) {
+        gy_up.v[e] = gyu.v[e];
+        ey_up.v[e] = x_cur.v[e] - xu.v[e] - gyu.v[e];
+        wy_up.v[e] = robust_weight(ey_up.v[e], vyu.v[e], c.delta, c.loss);
+      }
+    }
+  }
+  for (int j = 0; j < g.nrows; ++j) {
+    const int v = g.r0 + j;
+    const size_t i = (size_t)v * P + g.col;
+    const F<VEC> x_dn = (v + 1 < H) ? ldm<VEC>(k.x + i + P) : fzero<VEC>();
+    // east neighbour of every element
+    F<VEC> x_e;
+#pragma unroll
+    for (int e = 0; e < VEC - 1; ++e) x_e.v[e] = x_cur.v[e + 1];
+    {
+      float xe = shfl_dn1(x_cur.v[0]);
+      if (lane == 31) xe = (g.col + VEC < W) ? __ldcg(k.x + i + VEC) : 0.0f;
+      x_e.v[VEC - 1] = xe;
+    }
+    // x-term at this pixel (pairs i, i+1) and y-term (pairs i, i+W)
+    F<VEC> wxv = fzero<VEC>(), exv = fzero<VEC>(), gxv = fzero<VEC>();
+    F<VEC> wyv = fzero<VEC>(), eyv = fzero<VEC>(), gyv = fzero<VEC>();
+    if (grad) {
+      const F<VEC> gxr = ldc<VEC, DT>(k.cnn[2], i), vxr = ldc<VEC, DT>(k.cnn[3], i);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        if (g.col + e < W - 1) {
+          gxv.v[e] = gxr.v[e];
+          exv.v[e] = x_e.v[e] - x_cur.v[e] - gxr.v[e];
+          wxv.v[e] = robust_weight(exv.v[e], vxr.v[e], c.delta, c.loss);
+        }
+      }
+      if (v < H - 1) {
+        const F<VEC> gyr = ldc<VEC, DT>(k.cnn[4], i), vyr = ldc<VEC, DT>(k.cnn[5], i);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          if (g.col + e < W) {
+            gyv.v[e] = gyr.v[e];
+            eyv.v[e] = x_dn.v[e] - x_cur.v[e] - gyr.v[e];
+            wyv.v[e] = robust_weight(eyv.v[e], vyr.v[e], c.delta, c.loss);
+          }
+        }
+      }
+    }
+    // x-term of the west pair (i-1, i)
+    F<VEC> wxw, exw, gxw;
+#pragma unroll
+    for (int e = 1; e < VEC; ++e) {
+      wxw.v[e] = wxv.v[e - 1];
+      exw.v[e] = exv.v[e - 1];
+      gxw.v[e] = gxv.v[e - 1];
+    }
+    {
+      float a = shfl_up1(wxv.v[VEC - 1]), b = shfl_up1(exv.v[VEC - 1]),
+            gg = shfl_up1(gxv.v[VEC - 1]);
+      if (lane == 0) {
+        a = b = gg = 0.0f;
+        if (grad && g.col > 0 && g.col < W) {
+          const float xw = __ldcg(k.x + i - 1);
+          gg = ld_cnn<DT>(k.cnn[2], i - 1);
+          b = x_cur.v[0] - xw - gg;
+          a = robust_weight(b, ld_cnn<DT>(k.cnn[3], i - 1), c.delta, c.loss);
+        }
+      }
+      wxw.v[0] = a;
+      exw.v[0] = b;
+      gxw.v[0] = gg;
+    }
+    const F<VEC> ms = ldr<VEC>(k.mu_s + i), vs = ldr<VEC>(k.var_s + i);
+    const F<VEC> mn = ldc<VEC, DT>(k.cnn[0], i), vn = ldc<VEC, DT>(k.cnn[1], i);
+    F<VEC> dd, rr_, wxo, wyo;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      float d = 0.0f, r = 0.0f, b = 0.0f;
+      if (g.col + e < W) {
+        const float xi = x_cur.v[e];
+        float ws = 0.0f, rs = 0.0f, bs = 0.0f;
+        if (semi && semi_valid(ms.v[e], vs.v[e])) {
+          ws = robust_weight(xi - t - ms.v[e], vs.v[e], c.delta, c.loss);
+          rs = ws * (t + ms.v[e] - xi);
+          bs = ws * (t + ms.v[e]);
+        }
+        float wn = 0.0f, m = 0.0f;
+        if (net) {
+          m = mn.v[e];
+          wn = robust_weight(xi - m, vn.v[e], c.delta, c.loss);
+        }
+        d = ws + wn + wxv.v[e] + wxw.v[e] + wyv.v[e] + wy_up.v[e];
+        r = rs + wn * (m - xi) + wxv.v[e] * exv.v[e] - wxw.v[e] * exw.v[e] +
+            wyv.v[e] * eyv.v[e] - wy_up.v[e] * ey_up.v[e];
+        b = bs + wn * m - wxv.v[e] * gxv.v[e] + wxw.v[e] * gxw.v[e] - wyv.v[e] * gyv.v[e] +
+            wy_up.v[e] * gy_up.v[e];
+      }
+      dd.v[e] = d;
+      rr_.v[e] = r;
+      wxo.v[e] = wxv.v[e];
+      wyo.v[e] = wyv.v[e];
+      acc[0] += r * safe_div(r, d);
+      acc[1] += r * r;
+      acc[2] += b * b;
+    }
+    stm<VEC>(k.diag + i, dd);
+    stm<VEC>(k.wx + i, wxo);
+    stm<VEC>(k.wy + i, wyo);
+    stm<VEC>(r_out + i, rr_);
+    wy_up = wyv;
+    ey_up = eyv;
+    gy_up = gyv;
+    x_cur = x_dn;
+  }
+}
+
+// ---- INIT / ITER: one CG pass over a tile ---------------------------------
+//
+// Values of the pass at one row (for this lane's VEC columns): the new
+// residual r' = r - alpha s_i, with s_i = w + beta s_prev (s_i = w in the first
+// iteration, s_i = 0 and r' = r for INIT), and u' = r' / diag.
+template <int VEC>
+struct RowNew {
+  F<VEC> d, r, s, u, r_in;  // diag, r', s_i, u', and the residual entering the pass
+};
+
+template <int VEC, int KIND>  // KIND: 0 INIT, 1 first iteration, 2 later iteration
+__device__ __forceinline__ RowNew<VEC> row_new(const float *r_cur, const float *s_prev,
+                                               const float *w_cur, const float *diag, size_t i,
+                                               float alpha, float beta) {
+  RowNew<VEC> o;
+  o.d = ldm<VEC>(diag + i);
+  const F<VEC> r = ldm<VEC>(r_cur + i);
+  o.r_in = r;
+  if constexpr (KIND == 0) {
+    o.r = r;
+    o.s = fzero<VEC>();
+  } else {
+    const F<VEC> w = ldm<VEC>(w_cur + i);
+    F<VEC> s;
+    if constexpr (KIND == 2) s = ldm<VEC>(s_prev + i);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      o.s.v[e] = (KIND == 2) ? w.v[e] + beta * s.v[e] : w.v[e];
+      o.r.v[e] = r.v[e] - alpha * o.s.v[e];
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) o.u.v[e] = safe_div(o.r.v[e], o.d.v[e]);
+  return o;
+}
+
+template <int KIND>
+__device__ __forceinline__ float col_new_u(const float *r_cur, const float *s_prev,
+                                           const float *w_cur, const float *diag, size_t i,
+                                           float alpha, float beta) {
+  const float d = __ldcg(diag + i);
+  float r = __ldcg(r_cur + i);
+  if constexpr (KIND != 0) {
+    float s = __ldcg(w_cur + i);
+    if constexpr (KIND == 2) s += beta * __ldcg(s_prev + i);
+    r -= alpha * s;
+  }
+  return safe_div(r, d);
+}
+
+template <int VEC, int KIND>
+__device__ void cg_tile(const FusedKf &K, int lt, float alpha, float beta, const float *r_cur,
+                        const float *s_prev, const float *w_cur, float *r_nxt, float *s_cur,
+                        float *w_nxt, float acc[kQ]) {
+  const Planes &k = K.pl;
+  const Geo g = geo_of<VEC>(K, lt);
+  const int lane = threadIdx.x & 31;
+  const int W = k.W, H = k.H;
+  const size_t P = k.P;
+  F<VEC> u_up = fzero<VEC>(), wy_up = fzero<VEC>();
+  if (g.r0 > 0) {
+    const size_t iu = (size_t)(g.r0 - 1) * P + g.col;
+    u_up = row_new<VEC, KIND>(r_cur, s_prev, w_cur, k.diag, iu, alpha, beta).u;
+    wy_up = ldm<VEC>(k.wy + iu);
+  }
+  size_t i = (size_t)g.r0 * P + g.col;
+  RowNew<VEC> cur = row_new<VEC, KIND>(r_cur, s_prev, w_cur, k.diag, i, alpha, beta);
+  for (int j = 0; j < g.nrows; ++j) {
+    const int v = g.r0 + j;
+    // the row below: owned (keep everything) or halo (u only)
+    RowNew<VEC> nxt;
+    F<VEC> u_dn = fzero<VEC>();
+    if (v + 1 < H) {
+      nxt = row_new<VEC, KIND>(r_cur, s_prev, w_cur, k.diag, i + P, alpha, beta);
+      u_dn = nxt.u;
+    }
+    const F<VEC> wxr = ldm<VEC>(k.wx + i), wyr = ldm<VEC>(k.wy + i);
+    // west / east neighbours of u and the west coupling
+    F<VEC> u_w, u_e, wx_w;
+#pragma unroll
+    for (int e = 1; e < VEC; ++e) {
+      u_w.v[e] = cur.u.v[e - 1];
+      wx_w.v[e] = wxr.v[e - 1];
+    }
+#pragma unroll
+    for (int e = 0; e < VEC - 1; ++e) u_e.v[e] = cur.u.v[e + 1];
+    {
+      float uw = shfl_up1(cur.u.v[VEC - 1]);
+      float wxl = shfl_up1(wxr.v[VEC - 1]);
+      float ue = shfl_dn1(cur.u.v[0]);
+      if (lane == 0) {
+        uw = 0.0f;
+        wxl = 0.0f;
+        if (g.col > 0 && g.col < W) {
+          uw = col_new_u<KIND>(r_cur, s_prev, w_cur, k.diag, i - 1, alpha, beta);
+          wxl = __ldcg(k.wx + i - 1);
+        }
+      }
+      if (lane == 31) {
+        ue = (g.col + VEC < W)
+                 ? col_new_u<KIND>(r_cur, s_prev, w_cur, k.diag, i + VEC, alpha, beta)
+                 : 0.0f;
+      }
+      u_w.v[0] = uw;
+      wx_w.v[0] = wxl;
+      u_e.v[VEC - 1] = ue;
+    }
+    F<VEC> w_new;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      w_new.v[e] = cur.d.v[e] * cur.u.v[e] - wxr.v[e] * u_e.v[e] - wx_w.v[e] * u_w.v[e] -
+                   wyr.v[e] * u_dn.v[e] - wy_up.v[e] * u_up.v[e];
+      acc[0] += cur.r.v[e] * cur.u.v[e];
+      acc[1] += w_new.v[e] * cur.u.v[e];
+      acc[2] += cur.r.v[e] * cur.r.v[e];
+    }
+    stm<VEC>(w_nxt + i, w_new);
+    if constexpr (KIND != 0) {
+      // p_i = u_i + beta p_{i-1} with u_i = r_i / diag (the residual entering
+      // this iteration), x += alpha p_i; r' and s_i go to the other buffers
+      const F<VEC> &r_old = cur.r_in;
+      F<VEC> p = (KIND == 2) ? ldm<VEC>(k.v[0] + i) : fzero<VEC>();
+      F<VEC> x = ldm<VEC>(k.x + i);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const float ui = safe_div(r_old.v[e], cur.d.v[e]);
+        p.v[e] = (KIND == 2) ? ui + beta * p.v[e] : ui;
+        x.v[e] += alpha * p.v[e];
+      }
+      stm<VEC>(k.v[0] + i, p);
+      stm<VEC>(k.x + i, x);
+      stm<VEC>(r_nxt + i, cur.r);
+      stm<VEC>(s_cur + i, cur.s);
+    }
+    u_up = cur.u;
+    wy_up = wyr;
+    cur = nxt;
+    i += P;
+  }
+}
+
+// ---- FINAL: last CG iteration (no stencil) + next scale-step sums ----------
+template <int VEC>
+__device__ void final_tile(const FusedKf &K, int lt, bool first, bool update, float alpha,
+                           float beta, bool scale, float t, const SolveCfg &c,
+                           const float *r_cur, const float *s_prev, const float *w_cur,
+                           float acc[kQ]) {
+  const Planes &k = K.pl;
+  const Geo g = geo_of<VEC>(K, lt);
+  for (int j = 0; j < g.nrows; ++j) {
+    const size_t i = (size_t)(g.r0 + j) * k.P + g.col;
+    F<VEC> x = ldm<VEC>(k.x + i);
+    if (update) {
+      const F<VEC> d = ldm<VEC>(k.diag + i), r = ldm<VEC>(r_cur + i), w = ldm<VEC>(w_cur + i);
+      const F<VEC> p = first ? fzero<VEC>() : ldm<VEC>(k.v[0] + i);
+      const F<VEC> s = first ? fzero<VEC>() : ldm<VEC>(s_prev + i);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const float ui = safe_div(r.v[e], d.v[e]);
+        const float pi = first ? ui : ui + beta * p.v[e];
+        x.v[e] += alpha * pi;
+        const float si = first ? w.v[e] : w.v[e] + beta * s.v[e];
+        const float rn = r.v[e] - alpha * si;
+        acc[0] += rn * rn;
+      }
+      stm<VEC>(k.x + i, x);
+    }
+    if (scale) {
+      const F<VEC> ms = ldr<VEC>(k.mu_s + i), vs = ldr<VEC>(k.var_s + i);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        if (g.col + e < k.W && semi_valid(ms.v[e], vs.v[e])) {
+          const float w = robust_weight(x.v[e] - t - ms.v[e], vs.v[e], c.delta, c.loss);
+          acc[1] += w;
+          acc[2] += w * (x.v[e] - ms.v[e]);
+        }
+      }
+    }
+  }
+}
+
+// ---- grid barrier with a time limit ----------------------------------------
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Returns false if this CTA gave up waiting or another CTA raised the abort
+// word; then the caller skips all remaining work.
+__device__ bool grid_sync(PlanHeader *h, int G, unsigned long long limit_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int gen = ld_acquire(&h->bar_gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&h->bar_count, 1u) + 1u;
+    if (arrived == (unsigned int)G) {
+      h->bar_count = 0u;
+      __threadfence();
+      atomicAdd(&h->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      unsigned int spins = 0;
+      while (ld_acquire(&h->bar_gen) == gen) {
+        if (((++spins) & 63u) == 0u) {
+          if (ld_acquire(&h->abort) != 0u || global_ns() - t0 > limit_ns) {
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    if (ok && ld_acquire(&h->abort) != 0u) ok = 0;
+    if (!ok) atomicExch(&h->abort, 1u);
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+struct Seg {
+  double t, gam, alpha, beta, bb, rr;
+  int stop, iters, active, pad;
+};
+
+template <int VEC>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_fused(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns) {
+  __shared__ FusedKf s_kf[kMaxSeg];
+  __shared__ Seg s_seg[kMaxSeg];
+  __shared__ double s_acc[kWarps][kMaxSeg][kQ];
+  __shared__ double s_tot[kMaxSeg][kQ];
+  __shared__ int s_nseg;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = h->G, nslots = h->nslots, nkf = h->nkf;
+  const char *hb = reinterpret_cast<const char *>(h);
+  const int *cta_tile = reinterpret_cast<const int *>(hb + h->off_cta_tile);
+  const int *cta_kf = reinterpret_cast<const int *>(hb + h->off_cta_kf);
+  const int *cta_slot = reinterpret_cast<const int *>(hb + h->off_cta_slot);
+  const FusedKf *kfs = reinterpret_cast<const FusedKf *>(hb + h->off_kf);
+  double *slots = reinterpret_cast<double *>(reinterpret_cast<char *>(h) + h->off_slots);
+  const int cta = blockIdx.x;
+  const int tb = cta_tile[cta], te = cta_tile[cta + 1];
+  const int slot0 = cta_slot[cta];
+
+  if (tid == 0) {
+    int n = 0;
+    for (int kk = cta_kf[cta]; kk < nkf && kfs[kk].tile_begin < te && n < kMaxSeg; ++kk) {
+      s_kf[n] = kfs[kk];
+      Seg &s = s_seg[n];
+      const Scalars *sc = kfs[kk].pl.sc;
+      s.t = sc->t;
+      s.gam = s.alpha = s.beta = s.bb = 0.0;
+      s.rr = sc->rr;
+      s.stop = 0;
+      s.iters = 0;
+      s.active = (sc->flags & kFlagBadInput) ? 0 : 1;
+      ++n;
+    }
+    s_nseg = n;
+  }
+  __syncthreads();
+  const int nseg = s_nseg;
+  const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step;
+  int parity = 0;
+  bool alive = true;
+
+  // One pass over the CTA's tiles, then slots, barrier and per-keyframe sums.
+  auto run_pass = [&](int kind, int it, bool final_scale) -> bool {
+    for (int q = tid; q < kWarps * kMaxSeg * kQ; q += kThreads) (&s_acc[0][0][0])[q] = 0.0;
+    __syncthreads();
+    int seg = 0;
+    for (int tile = tb + warp; tile < te; tile += kWarps) {
+      while (tile >= s_kf[seg].tile_begin + s_kf[seg].ntiles) ++seg;
+      const FusedKf &K = s_kf[seg];
+      const Seg &S = s_seg[seg];
+      if (!S.active) continue;
+      const int lt = tile - K.tile_begin;
+      float a[kQ] = {0.0f, 0.0f, 0.0f};
+      const float ft = (float)S.t, fa = (float)S.alpha, fb = (float)S.beta;
+      float *R0 = K.pl.v[1], *R1 = K.pl.v[2], *S0 = K.pl.v[3], *S1 = K.pl.v[4];
+      float *W0 = K.pl.v[5], *W1 = K.pl.v[6];
+      float *Rc = (it & 1) ? R1 : R0, *Rn = (it & 1) ? R0 : R1;
+      float *Sp = (it & 1) ? S1 : S0, *Sc = (it & 1) ? S0 : S1;
+      float *Wc = (it & 1) ? W1 : W0, *Wn = (it & 1) ? W0 : W1;
+      switch (kind) {
+        case P_SCALE:
+          scale_tile<VEC>(K, lt, ft, c, a);
+          break;
+        case P_ASSEMBLE:
+          if (K.pl.dtype == DF_BF16)
+            assemble_tile<VEC, DF_BF16>(K, lt, ft, c, a);
+          else if (K.pl.dtype == DF_F16)
+            assemble_tile<VEC, DF_F16>(K, lt, ft, c, a);
+          else
+            assemble_tile<VEC, DF_F32>(K, lt, ft, c, a);
+          break;
+        case P_INIT:
+          if (!S.stop) cg_tile<VEC, 0>(K, lt, 0.0f, 0.0f, R0, S0, W1, R1, S1, W0, a);
+          break;
+        case P_ITER:
+          if (!S.stop) {
+            if (it == 0)
+              cg_tile<VEC, 1>(K, lt, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
+            else
+              cg_tile<VEC, 2>(K, lt, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
+          }
+          break;
+        default:  // P_FINAL
+          final_tile<VEC>(K, lt, it == 0, !S.stop, fa, fb, final_scale, ft, c, Rc, Sp, Wc, a);
+          break;
+      }
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        const double dq = warp_sum((double)a[q]);
+        if (lane == 0) s_acc[warp][seg][q] += dq;
+      }
+    }
+    __syncthreads();
+    double *pslots = slots + (size_t)parity * nslots * kQ;
+    if (tid < nseg * kQ) {
+      const int sg = tid / kQ, q = tid % kQ;
+      double s = 0.0;
+      for (int w = 0; w < kWarps; ++w) s += s_acc[w][sg][q];
+      pslots[(size_t)(slot0 + sg) * kQ + q] = s;
+    }
+    if (!grid_sync(h, G, limit_ns)) return false;
+    if (warp < nseg) {
+      const FusedKf &K = s_kf[warp];
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        double s = 0.0;
+        for (int sl = K.slot_begin + lane; sl < K.slot_end; sl += 32)
+          s += __ldcg(pslots + (size_t)sl * kQ + q);
+        s = warp_sum(s);
+        if (lane == 0) s_tot[warp][q] = s;
+      }
+    }
+    __syncthreads();
+    parity ^= 1;
+    return true;
+  };
+
+  auto scale_update = [&](int qw, int qwr) {
+    if (tid < nseg) {
+      Seg &S = s_seg[tid];
+      if (S.active && s_tot[tid][qw] > 0.0) S.t = s_tot[tid][qwr] / s_tot[tid][qw];
+    }
+    __syncthreads();
+  };
+
+  bool scale_pending = false;
+  for (int gn = 0; gn < n_gn && alive; ++gn) {
+    if (do_scale) {
+      if (!scale_pending) {
+        alive = run_pass(P_SCALE, 0, false);
+        if (!alive) break;
+        scale_update(0, 1);
+      }
+      scale_pending = false;
+    }
+    alive = run_pass(P_ASSEMBLE, 0, false);
+    if (!alive) break;
+    if (tid < nseg) {
+      Seg &S = s_seg[tid];
+      S.gam = s_tot[tid][0];
+      S.rr = s_tot[tid][1];
+      S.bb = s_tot[tid][2];
+      S.stop = (c.tol > 0.0 && sqrt(S.rr) < c.tol * sqrt(S.bb)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (n_pcg == 0) continue;
+    alive = run_pass(P_INIT, 0, false);
+    if (!alive) break;
+    if (tid < nseg) {
+      Seg &S = s_seg[tid];
+      if (!S.stop) {
+        const double dl = s_tot[tid][1];
+        if (S.gam == 0.0 || !(dl > 0.0)) {
+          S.stop = 1;
+        } else {
+          S.alpha = S.gam / dl;
+          S.beta = 0.0;
+        }
+      }
+    }
+    __syncthreads();
+    for (int it = 0; it < n_pcg; ++it) {
+      if (it == n_pcg - 1) {
+        const bool fs = do_scale && gn + 1 < n_gn;
+        alive = run_pass(P_FINAL, it, fs);
+        if (!alive) break;
+        if (tid < nseg) {
+          Seg &S = s_seg[tid];
+          if (!S.stop) {
+            S.iters += 1;
+            S.rr = s_tot[tid][0];
+          }
+        }
+        __syncthreads();
+        if (fs) {
+          scale_update(1, 2);
+          scale_pending = true;
+        }
+      } else {
+        alive = run_pass(P_ITER, it, false);
+        if (!alive) break;
+        if (tid < nseg) {
+          Seg &S = s_seg[tid];
+          if (!S.stop) {
+            S.iters += 1;
+            S.rr = s_tot[tid][2];
+            const double gn_ = s_tot[tid][0], dl = s_tot[tid][1];
+            if (c.tol > 0.0 && sqrt(S.rr) < c.tol * sqrt(S.bb)) {
+              S.stop = 1;
+            } else {
+              const double beta = gn_ / S.gam;
+              const double denom = dl - beta * gn_ / S.alpha;
+              if (gn_ == 0.0 || !(denom > 0.0)) {
+                S.stop = 1;
+              } else {
+                S.beta = beta;
+                S.alpha = gn_ / denom;
+                S.gam = gn_;
+              }
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+
+  if (tid < nseg) {
+    const Seg &S = s_seg[tid];
+    const FusedKf &K = s_kf[tid];
+    Scalars *sc = K.pl.sc;
+    if (!alive) {
+      atomicOr(&sc->flags, kFlagTimeout);
+    } else if (S.active && K.writer_cta == cta) {
+      sc->t = S.t;
+      sc->rr = S.rr;
+      sc->rho = S.gam;
+      sc->iters = S.iters;
+      sc->stop = S.stop;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned int done = atomicAdd(&h->exit_count, 1u) + 1u;
+    if (done == (unsigned int)G) {  // last CTA out: leave the words clean
+      h->bar_count = 0u;
+      h->abort = 0u;
+      h->exit_count = 0u;
+      __threadfence();
+    }
+  }
+}
+
+struct DevInfo {
+  int sms = 0;
+  int occ[2] = {0, 0};  // resident CTAs per SM for VEC = 1, 4
+  bool coop = false;
+};
+
+DevInfo g_dev[64];
+bool g_dev_init[64] = {false};
+std::mutex g_dev_mu;
+
+const DevInfo &dev_info() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  if (dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (!g_dev_init[dev]) {
+    DevInfo d;
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    d.coop = coop != 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0], k_fused<1>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1], k_fused<4>, kThreads, 0);
+    cudaGetLastError();
+    g_dev[dev] = d;
+    g_dev_init[dev] = true;
+  }
+  return g_dev[dev];
+}
+
+size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+}  // namespace
+
+bool fused_supported() {
+  const DevInfo &d = dev_info();
+  return d.coop && d.sms > 0 && d.occ[0] > 0 && d.occ[1] > 0;
+}
+
+int fused_max_ctas() {
+  const DevInfo &d = dev_info();
+  return d.sms * std::max(1, std::min(d.occ[0], d.occ[1]));
+}
+
+size_t fused_plan_bytes(int nkf, int G) {
+  const int nslots = G + nkf;
+  size_t off = align16(sizeof(PlanHeader));
+  off += align16(sizeof(int) * (size_t)(G + 1));
+  off += align16(sizeof(int) * (size_t)G);
+  off += align16(sizeof(int) * (size_t)G);
+  off += align16(sizeof(FusedKf) * (size_t)nkf);
+  off += sizeof(double) * 2 * (size_t)nslots * kQ;
+  return off;
+}
+
+bool fused_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
+                      std::vector<char> &out, int &G_out, int &vec_out) {
+  const DevInfo &d = dev_info();
+  if (n < 1 || d.sms <= 0) return false;
+  const int occ = std::max(1, std::min(d.occ[0], d.occ[1]));
+  const int G_cap = std::max(1, std::min(tune.max_ctas > 0 ? tune.max_ctas : d.sms * occ,
+                                         d.sms * occ));
+  const long long warps = (long long)G_cap * kWarps;
+  long long rows4 = 0, rows1 = 0;
+  for (int k = 0; k < n; ++k) {
+    rows4 += (long long)((kfs[k]->W + 127) / 128) * kfs[k]->H;
+    rows1 += (long long)((kfs[k]->W + 31) / 32) * kfs[k]->H;
+  }
+  int vec = tune.vec;
+  if (vec != 1 && vec != 4) vec = (rows4 >= 4 * warps) ? 4 : 1;
+  const long long rows = vec == 4 ? rows4 : rows1;
+  int th = tune.tile_rows;
+  if (th <= 0) th = (int)std::max<long long>(1, std::min<long long>(32, rows / warps));
+  // tiles per keyframe
+  std::vector<int> tb(n + 1, 0), tx(n), nt(n);
+  for (int k = 0; k < n; ++k) {
+    tx[k] = (kfs[k]->W + 32 * vec - 1) / (32 * vec);
+    nt[k] = tx[k] * ((kfs[k]->H + th - 1) / th);
+    tb[k + 1] = tb[k] + nt[k];
+  }
+  const int T = tb[n];
+  int G = std::min(G_cap, std::max(1, (T + kWarps - 1) / kWarps));
+  if (tune.max_ctas > 0) G = std::min(G, tune.max_ctas);
+  // contiguous tile ranges, balanced, at most kMaxSeg keyframes each
+  std::vector<int> ct(G + 1, T), ck(G, 0);
+  {
+    int tile = 0, kf = 0;
+    for (int cI = 0; cI < G; ++cI) {
+      ct[cI] = tile;
+      while (kf < n && tb[kf + 1] <= tile) ++kf;
+      ck[cI] = kf;
+      const int left = T - tile, ctas_left = G - cI;
+      const int target = (left + ctas_left - 1) / ctas_left;
+      int end = std::min(T, tile + target);
+      // cap the number of keyframes touched
+      int kk = kf, segs = 0;
+      while (kk < n && tb[kk] < end) {
+        ++segs;
+        if (segs > kMaxSeg) {
+          end = tb[kk];
+          break;
+        }
+        ++kk;
+      }
+      tile = end;
+    }
+    if (tile != T) return false;  // does not fit: the caller splits the batch
+    ct[G] = T;
+  }
+  // drop empty trailing CTAs
+  while (G > 1 && ct[G - 1] == T) --G;
+  ct.resize(G + 1);
+  ct[G] = T;
+  ck.resize(G);
+  // slots: one per (CTA, keyframe segment), in CTA order
+  std::vector<int> cs(G);
+  std::vector<int> sb(n, -1), se(n, -1), wc(n, -1);
+  int ns = 0;
+  for (int cI = 0; cI < G; ++cI) {
+    cs[cI] = ns;
+    for (int kk = ck[cI]; kk < n && tb[kk] < ct[cI + 1]; ++kk) {
+      if (tb[kk + 1] <= ct[cI]) continue;
+      if (sb[kk] < 0) {
+        sb[kk] = ns;
+        wc[kk] = cI;
+      }
+      se[kk] = ns + 1;
+      ++ns;
+    }
+  }
+  for (int k = 0; k < n; ++k)
+    if (sb[k] < 0) return false;
+  const int nslots = G + n;  // bound used for the allocation
+  if (ns > nslots) return false;
+  out.assign(fused_plan_bytes(n, G), 0);
+  char *base = out.data();
+  PlanHeader *hd = reinterpret_cast<PlanHeader *>(base);
+  size_t off = align16(sizeof(PlanHeader));
+  hd->off_cta_tile = (long long)off;
+  off += align16(sizeof(int) * (size_t)(G + 1));
+  hd->off_cta_kf = (long long)off;
+  off += align16(sizeof(int) * (size_t)G);
+  hd->off_cta_slot = (long long)off;
+  off += align16(sizeof(int) * (size_t)G);
+  hd->off_kf = (long long)off;
+  off += align16(sizeof(FusedKf) * (size_t)n);
+  hd->off_slots = (long long)off;
+  hd->nkf = n;
+  hd->G = G;
+  hd->ntiles = T;
+  hd->nslots = nslots;
+  hd->vec = vec;
+  hd->bytes = (long long)out.size();
+  memcpy(base + hd->off_cta_tile, ct.data(), sizeof(int) * (G + 1));
+  memcpy(base + hd->off_cta_kf, ck.data(), sizeof(int) * G);
+  memcpy(base + hd->off_cta_slot, cs.data(), sizeof(int) * G);
+  FusedKf *fk = reinterpret_cast<FusedKf *>(base + hd->off_kf);
+  for (int k = 0; k < n; ++k) {
+    fk[k].pl = *kfs[k];
+    fk[k].tile_begin = tb[k];
+    fk[k].ntiles = nt[k];
+    fk[k].tiles_x = tx[k];
+    fk[k].th = th;
+    fk[k].slot_begin = sb[k];
+    fk[k].slot_end = se[k];
+    fk[k].writer_cta = wc[k];
+  }
+  G_out = G;
+  vec_out = vec;
+  return true;
+}
+
+cudaError_t fused_launch(void *dplan, int G, int vec, const SolveCfg &c, int n_gn, int n_pcg,
+                         unsigned long long limit_ns, cudaStream_t s) {
+  PlanHeader *h = static_cast<PlanHeader *>(dplan);
+  void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns};
+  count_launches(1);
+  const void *fn = vec == 4 ? reinterpret_cast<const void *>(k_fused<4>)
+                            : reinterpret_cast<const void *>(k_fused<1>);
+  return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args, 0, s);
 }
 
 }  // namespace df

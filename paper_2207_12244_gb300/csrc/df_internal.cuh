@@ -1,8 +1,9 @@
 // Internal declarations of the GB300 keyframe optimiser (not part of the ABI).
 //
 // Device layout of one keyframe (one allocation, every plane 256-B aligned,
-// rows padded to a pitch P that is a multiple of 32 elements so that every
-// row starts on a 128-B boundary and 16-B vector loads never straddle it):
+// rows padded to a pitch P that is a multiple of 128 elements so that every
+// row starts on a 256-B boundary and 16-B vector loads never straddle it;
+// the padding columns stay zero):
 //
 //   network planes (Section II-A outputs, f32 / bf16 / f16):
 //     mu_n, var_n, gx, var_gx, gy, var_gy
@@ -21,7 +22,8 @@
 
 namespace df {
 
-constexpr int kPitchElems = 32;     // row pitch granularity (elements)
+constexpr int kPitchElems = 128;    // row pitch granularity (elements): a warp's
+                                    // 32 x 4-element segment never crosses a row
 constexpr int kWorkPlanes = 8;      // solver vectors beyond diag / wx / wy
 constexpr int kMaxPartialBlocks = 4096;
 constexpr int kNumQ = 4;            // FP64 quantities per partial slot

@@ -72,7 +72,13 @@ def test_modes(o, solver, mode):
     x, t, rep = solve(kf, prm)
     xo, to, ro = oracle_solve(o, kf, prm)
     assert_parity(x, t, xo, to, what=mode)
-    assert rep.iters_done == ro.iters_done
+    if mode == "semi+net":
+        # diagonal system: Jacobi-PCG is exact after one iteration; later
+        # iterations run on rounding residue (1e-80 in FP64, exact zeros in
+        # FP32 stop earlier), so only the depth is comparable
+        assert 6 <= rep.iters_done <= ro.iters_done
+    else:
+        assert rep.iters_done == ro.iters_done
 
 
 def test_prior_only_returns_cnn_depth_bitwise(o, solver):
