@@ -194,6 +194,33 @@ size_t df_memory_in_use(void);
 df_status df_semi_to_log(const float *depth, const float *var_depth, float *mu_semi,
                          float *var_semi, int64_t n, int ptrs_on_device, void *stream);
 
+/* Launch shape of the fused solver (process-wide; paper counterpart: none,
+ * this is how the GB300 kernels are cut). A field of 0 means "choose from
+ * the problem size". Keyframes pick up a new setting at their next solve.
+ *   mode      0 auto (resident when the state fits in shared memory,
+ *             else streaming), 1 streaming only, 2 resident only
+ *   vec       streaming kernel: pixels per lane along a row, 1 or 4
+ *   tile_rows streaming kernel: rows per warp tile (1..64)
+ *   max_ctas  cap on the cooperative grid
+ *   debug_skip_cta  test only: >= 0 makes that CTA of the next fused launches
+ *             leave without arriving at its first grid barrier, so the
+ *             others' bounded waits run out (DF_ETIMEOUT); -1 = off. */
+typedef struct {
+  int32_t mode;
+  int32_t vec;
+  int32_t tile_rows;
+  int32_t max_ctas;
+  int32_t debug_skip_cta;
+} df_tuning;
+
+df_status df_set_tuning(const df_tuning *t); /* NULL restores the defaults */
+df_status df_get_tuning(df_tuning *t);
+
+/* Upper bound on every device-side wait of the fused solver (grid
+ * barriers), in nanoseconds; a wait that runs out abandons the solve and is
+ * reported as DF_ETIMEOUT. Default 2 s. */
+df_status df_set_spin_limit_ns(uint64_t ns);
+
 /* Number of kernels this library has launched in this process (all devices);
  * a diagnostic for counting device work inside a timed region. */
 uint64_t df_kernel_launches(void);

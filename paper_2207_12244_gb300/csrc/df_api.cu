@@ -26,7 +26,7 @@ struct df_keyframe {
   float *staging;   // dense H x W plane for host-side depth reads
   void *plan;       // resident launch plan of the fused solver (single keyframe)
   size_t plan_cap;  // bytes reserved for it
-  int plan_G = 0, plan_vec = 0;  // shape of the plan currently on the device (0: none)
+  df::LaunchShape plan_shape;    // shape of the plan currently on the device (kind -1: none)
   df::FusedTuning plan_tune;
 };
 
@@ -231,6 +231,42 @@ extern "C" {
 
 uint64_t df_kernel_launches(void) { return g_launches.load(); }
 
+df_status df_set_tuning(const df_tuning *t) {
+  df::FusedTuning n;
+  if (t) {
+    if (t->mode < 0 || t->mode > 2) return fail(DF_EINVAL, "tuning mode must be 0, 1 or 2");
+    if (t->vec != 0 && t->vec != 1 && t->vec != 4) return fail(DF_EINVAL, "vec must be 0, 1 or 4");
+    if (t->tile_rows < 0 || t->tile_rows > 64) return fail(DF_EINVAL, "tile_rows must be 0..64");
+    if (t->max_ctas < 0) return fail(DF_EINVAL, "max_ctas must be >= 0");
+    if (t->debug_skip_cta < -1) return fail(DF_EINVAL, "debug_skip_cta must be >= -1");
+    n.mode = t->mode;
+    n.vec = t->vec;
+    n.tile_rows = t->tile_rows;
+    n.max_ctas = t->max_ctas;
+    n.debug_skip_cta = t->debug_skip_cta;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune = n;
+  return DF_OK;
+}
+
+df_status df_get_tuning(df_tuning *t) {
+  if (!t) return fail(DF_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  t->mode = g_tune.mode;
+  t->vec = g_tune.vec;
+  t->tile_rows = g_tune.tile_rows;
+  t->max_ctas = g_tune.max_ctas;
+  t->debug_skip_cta = g_tune.debug_skip_cta;
+  return DF_OK;
+}
+
+df_status df_set_spin_limit_ns(uint64_t ns) {
+  if (ns == 0) return fail(DF_EINVAL, "spin limit must be > 0");
+  g_spin_limit_ns.store(ns);
+  return DF_OK;
+}
+
 
 void df_default_params(df_solve_params *p) {
   if (!p) return;
@@ -377,7 +413,8 @@ static df::FusedTuning current_tuning() {
 }
 
 static bool same_tuning(const df::FusedTuning &a, const df::FusedTuning &b) {
-  return a.vec == b.vec && a.tile_rows == b.tile_rows && a.max_ctas == b.max_ctas;
+  return a.mode == b.mode && a.vec == b.vec && a.tile_rows == b.tile_rows &&
+         a.max_ctas == b.max_ctas && a.debug_skip_cta == b.debug_skip_cta;
 }
 
 static int pick_solver(int requested) {
@@ -391,20 +428,18 @@ static df_status fused_one(df_keyframe *kf, const SolveCfg &c, int n_gn, int n_p
                            cudaStream_t s) {
   if (!df::fused_supported() || !kf->plan) return fail(DF_ENOTSUP, "fused solver not available on this device");
   const df::FusedTuning tune = current_tuning();
-  if (kf->plan_G == 0 || !same_tuning(tune, kf->plan_tune)) {
+  if (kf->plan_shape.kind < 0 || !same_tuning(tune, kf->plan_tune)) {
     std::vector<char> host;
-    int G = 0, vec = 0;
+    df::LaunchShape shape;
     const Planes *one = &kf->planes;
-    if (!df::fused_build_plan(&one, 1, tune, host, G, vec))
+    if (!df::fused_build_plan(&one, 1, tune, host, shape))
       return fail(DF_EINVAL, "fused solver: no launch plan for this keyframe");
     if (host.size() > kf->plan_cap) return fail(DF_EINVAL, "fused plan larger than reserved");
     DF_CUDA(cudaMemcpyAsync(kf->plan, host.data(), host.size(), cudaMemcpyHostToDevice, s));
-    kf->plan_G = G;
-    kf->plan_vec = vec;
+    kf->plan_shape = shape;
     kf->plan_tune = tune;
   }
-  DF_CUDA(df::fused_launch(kf->plan, kf->plan_G, kf->plan_vec, c, n_gn, n_pcg,
-                           g_spin_limit_ns.load(), s));
+  DF_CUDA(df::fused_launch(kf->plan, kf->plan_shape, c, n_gn, n_pcg, g_spin_limit_ns.load(), s));
   return DF_OK;
 }
 
@@ -422,8 +457,8 @@ static df_status fused_many(df_keyframe *const *kfs, int n, const SolveCfg &c, i
   std::vector<const Planes *> list(n);
   for (int j = 0; j < n; ++j) list[j] = &kfs[j]->planes;
   std::vector<char> host;
-  int G = 0, vec = 0;
-  if (!df::fused_build_plan(list.data(), n, current_tuning(), host, G, vec)) {
+  df::LaunchShape shape;
+  if (!df::fused_build_plan(list.data(), n, current_tuning(), host, shape)) {
     const int h = n / 2;
     df_status st = fused_many(kfs, h, c, n_gn, n_pcg, s);
     if (st != DF_OK) return st;
@@ -432,7 +467,7 @@ static df_status fused_many(df_keyframe *const *kfs, int n, const SolveCfg &c, i
   void *dplan = nullptr;
   DF_CUDA(cudaMallocAsync(&dplan, host.size(), s));
   cudaError_t e = cudaMemcpyAsync(dplan, host.data(), host.size(), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = df::fused_launch(dplan, G, vec, c, n_gn, n_pcg, g_spin_limit_ns.load(), s);
+  if (e == cudaSuccess) e = df::fused_launch(dplan, shape, c, n_gn, n_pcg, g_spin_limit_ns.load(), s);
   cudaError_t e2 = cudaFreeAsync(dplan, s);
   if (e != cudaSuccess) return cuda_fail(e, "fused batch launch");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");

@@ -46,6 +46,7 @@
 #include <vector>
 
 #include "df_fused.cuh"
+#include "df_sync.cuh"
 
 namespace df {
 
@@ -70,13 +71,7 @@ struct FusedKf {
   int pad;
 };
 
-struct PlanHeader {
-  int nkf, G, ntiles, nslots;
-  int vec, pad0;
-  unsigned int bar_count, bar_gen, exit_count, abort;
-  long long off_cta_tile, off_cta_kf, off_cta_slot, off_kf, off_slots;
-  long long bytes;
-};
+
 
 // ---- small vector helpers ---------------------------------------------------
 
@@ -507,55 +502,6 @@ __device__ void final_tile(const FusedKf &K, int lt, bool first, bool update, fl
   }
 }
 
-// ---- grid barrier with a time limit ----------------------------------------
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Returns false if this CTA gave up waiting or another CTA raised the abort
-// word; then the caller skips all remaining work.
-__device__ bool grid_sync(PlanHeader *h, int G, unsigned long long limit_ns) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned int gen = ld_acquire(&h->bar_gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&h->bar_count, 1u) + 1u;
-    if (arrived == (unsigned int)G) {
-      h->bar_count = 0u;
-      __threadfence();
-      atomicAdd(&h->bar_gen, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      unsigned int spins = 0;
-      while (ld_acquire(&h->bar_gen) == gen) {
-        if (((++spins) & 63u) == 0u) {
-          if (ld_acquire(&h->abort) != 0u || global_ns() - t0 > limit_ns) {
-            ok = 0;
-            break;
-          }
-        }
-      }
-    }
-    if (ok && ld_acquire(&h->abort) != 0u) ok = 0;
-    if (!ok) atomicExch(&h->abort, 1u);
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 struct Seg {
   double t, gam, alpha, beta, bb, rr;
   int stop, iters, active, pad;
@@ -784,17 +730,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       sc->stop = S.stop;
     }
   }
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    const unsigned int done = atomicAdd(&h->exit_count, 1u) + 1u;
-    if (done == (unsigned int)G) {  // last CTA out: leave the words clean
-      h->bar_count = 0u;
-      h->abort = 0u;
-      h->exit_count = 0u;
-      __threadfence();
-    }
-  }
+  grid_exit(h, G);
 }
 
 struct DevInfo {
@@ -834,17 +770,17 @@ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 }  // namespace
 
-bool fused_supported() {
+bool streaming_supported() {
   const DevInfo &d = dev_info();
   return d.coop && d.sms > 0 && d.occ[0] > 0 && d.occ[1] > 0;
 }
 
-int fused_max_ctas() {
+int streaming_max_ctas() {
   const DevInfo &d = dev_info();
   return d.sms * std::max(1, std::min(d.occ[0], d.occ[1]));
 }
 
-size_t fused_plan_bytes(int nkf, int G) {
+size_t streaming_plan_bytes(int nkf, int G) {
   const int nslots = G + nkf;
   size_t off = align16(sizeof(PlanHeader));
   off += align16(sizeof(int) * (size_t)(G + 1));
@@ -855,8 +791,8 @@ size_t fused_plan_bytes(int nkf, int G) {
   return off;
 }
 
-bool fused_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
-                      std::vector<char> &out, int &G_out, int &vec_out) {
+bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
+                          std::vector<char> &out, LaunchShape &shape) {
   const DevInfo &d = dev_info();
   if (n < 1 || d.sms <= 0) return false;
   const int occ = std::max(1, std::min(d.occ[0], d.occ[1]));
@@ -934,7 +870,7 @@ bool fused_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
     if (sb[k] < 0) return false;
   const int nslots = G + n;  // bound used for the allocation
   if (ns > nslots) return false;
-  out.assign(fused_plan_bytes(n, G), 0);
+  out.assign(streaming_plan_bytes(n, G), 0);
   char *base = out.data();
   PlanHeader *hd = reinterpret_cast<PlanHeader *>(base);
   size_t off = align16(sizeof(PlanHeader));
@@ -947,6 +883,8 @@ bool fused_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
   hd->off_kf = (long long)off;
   off += align16(sizeof(FusedKf) * (size_t)n);
   hd->off_slots = (long long)off;
+  hd->kind = kPlanStreaming;
+  hd->debug_skip_cta = tune.debug_skip_cta;
   hd->nkf = n;
   hd->G = G;
   hd->ntiles = T;
@@ -967,19 +905,45 @@ bool fused_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
     fk[k].slot_end = se[k];
     fk[k].writer_cta = wc[k];
   }
-  G_out = G;
-  vec_out = vec;
+  shape.kind = kPlanStreaming;
+  shape.G = G;
+  shape.vec = vec;
+  shape.smem = 0;
   return true;
 }
 
-cudaError_t fused_launch(void *dplan, int G, int vec, const SolveCfg &c, int n_gn, int n_pcg,
-                         unsigned long long limit_ns, cudaStream_t s) {
+cudaError_t streaming_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
+                             int n_pcg, unsigned long long limit_ns, cudaStream_t s) {
   PlanHeader *h = static_cast<PlanHeader *>(dplan);
+  const int G = shape.G, vec = shape.vec;
   void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns};
   count_launches(1);
   const void *fn = vec == 4 ? reinterpret_cast<const void *>(k_fused<4>)
                             : reinterpret_cast<const void *>(k_fused<1>);
   return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args, 0, s);
+}
+
+// ---- dispatch between the resident and the streaming kernels -------------
+
+bool fused_supported() { return streaming_supported(); }
+
+int fused_max_ctas() { return std::max(streaming_max_ctas(), resident_max_ctas()); }
+
+size_t fused_plan_bytes(int nkf, int G) {
+  return std::max(streaming_plan_bytes(nkf, G), resident_plan_bytes(nkf, G));
+}
+
+bool fused_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
+                      std::vector<char> &out, LaunchShape &shape) {
+  if (tune.mode != kModeStreaming && resident_build_plan(kfs, n, tune, out, shape)) return true;
+  if (tune.mode == kModeResident) return false;
+  return streaming_build_plan(kfs, n, tune, out, shape);
+}
+
+cudaError_t fused_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
+                         int n_pcg, unsigned long long limit_ns, cudaStream_t s) {
+  if (shape.kind == kPlanResident) return resident_launch(dplan, shape, c, n_gn, n_pcg, limit_ns, s);
+  return streaming_launch(dplan, shape, c, n_gn, n_pcg, limit_ns, s);
 }
 
 }  // namespace df

@@ -10,11 +10,23 @@ namespace df {
 
 constexpr int kMaxBatch = 256;  // keyframes per fused launch
 
-// Launch shape. 0 = chosen from the problem size.
+enum : int { kModeAuto = 0, kModeStreaming = 1, kModeResident = 2 };
+
+// Launch shape knobs. 0 = chosen from the problem size.
 struct FusedTuning {
-  int vec = 0;        // pixels per lane along a row: 1 or 4
-  int tile_rows = 0;  // rows per warp tile
-  int max_ctas = 0;   // cap on the cooperative grid
+  int mode = kModeAuto;  // resident if the state fits in shared memory, else streaming
+  int vec = 0;           // streaming: pixels per lane along a row (1 or 4)
+  int tile_rows = 0;     // streaming: rows per warp tile
+  int max_ctas = 0;      // cap on the cooperative grid
+  int debug_skip_cta = -1;  // test hook, see df_tuning
+};
+
+// What one fused launch looks like (filled by fused_build_plan).
+struct LaunchShape {
+  int kind = -1;  // kPlanStreaming / kPlanResident (df_sync.cuh)
+  int G = 0;      // CTAs
+  int vec = 0;    // streaming tile width selector
+  int smem = 0;   // dynamic shared memory per CTA (resident)
 };
 
 // True when the current device can run the fused solver.
@@ -30,11 +42,27 @@ size_t fused_plan_bytes(int nkf, int G);
 // words). Returns false if the keyframes cannot share one launch (then
 // split the batch).
 bool fused_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
-                      std::vector<char> &out, int &G, int &vec);
+                      std::vector<char> &out, LaunchShape &shape);
 
 // Launch on stream s with a plan already copied to device memory 'dplan'.
 // limit_ns bounds every grid-barrier wait.
-cudaError_t fused_launch(void *dplan, int G, int vec, const SolveCfg &c, int n_gn, int n_pcg,
-                         unsigned long long limit_ns, cudaStream_t s);
+cudaError_t fused_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
+                         int n_pcg, unsigned long long limit_ns, cudaStream_t s);
+
+// The two kernels behind fused_*: streaming (df_fused.cu) and resident
+// (df_resident.cu).
+bool streaming_supported();
+int streaming_max_ctas();
+size_t streaming_plan_bytes(int nkf, int G);
+bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
+                          std::vector<char> &out, LaunchShape &shape);
+cudaError_t streaming_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
+                             int n_pcg, unsigned long long limit_ns, cudaStream_t s);
+int resident_max_ctas();
+size_t resident_plan_bytes(int nkf, int G);
+bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
+                         std::vector<char> &out, LaunchShape &shape);
+cudaError_t resident_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
+                            int n_pcg, unsigned long long limit_ns, cudaStream_t s);
 
 }  // namespace df

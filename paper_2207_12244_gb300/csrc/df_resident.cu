@@ -1,0 +1,622 @@
+// Resident persistent solver: the same per-frame solve as df_fused.cu
+// (Section II-C: n_gn Gauss-Newton iterations alternating scale and depth;
+// Jacobi-PCG in the Chronopoulos-Gear arrangement, one grid barrier per
+// pass), for keyframes small enough that the whole solver state fits in the
+// GPU's shared memory.
+//
+// Each CTA owns a band of whole rows [rb, re) of one keyframe and keeps
+// x, r, p, s, w, diag, wx, wy and u of its band in shared memory for the
+// whole launch. Only the band's first and last rows cross CTAs: after each
+// pass a CTA writes them to the keyframe's global planes (L2), and the
+// neighbouring band recomputes the new u of those rows from them in the next
+// pass, exactly as the streaming kernel recomputes its tile halos. The global
+// planes are thus touched only at band edges, plus one read of the inputs per
+// Gauss-Newton iteration and one write of x at the end.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "df_fused.cuh"
+#include "df_sync.cuh"
+
+namespace df {
+
+namespace {
+
+constexpr int kRThreads = 512;
+constexpr int kRWarps = kRThreads / 32;
+constexpr int kRQ = 3;
+constexpr int kHalo = 5;  // halo rows of W floats kept in shared memory
+
+struct ResKf {
+  Planes pl;
+  int cta_begin, cta_end;  // CTAs (= reduction slots) of this keyframe
+};
+
+struct ResCta {
+  int kf, rb, re, pad;
+};
+
+struct ResSeg {
+  double t, gam, alpha, beta, bb, rr;
+  int stop, iters, active, pad;
+};
+
+__device__ __forceinline__ float sdiv(float r, float d) { return d > 0.0f ? r / d : 0.0f; }
+
+// The new residual's Jacobi-scaled value u' at one global pixel of a
+// neighbouring band, from that band's published r, s, w and diag.
+template <int KIND>  // 0: INIT (u = r / d), 1: first iteration, 2: later
+__device__ __forceinline__ float halo_u(const Planes &k, const float *Rc, const float *Sp,
+                                        const float *Wc, size_t i, float alpha, float beta) {
+  float r = __ldcg(Rc + i);
+  if constexpr (KIND != 0) {
+    float s = __ldcg(Wc + i);
+    if constexpr (KIND == 2) s += beta * __ldcg(Sp + i);
+    r -= alpha * s;
+  }
+  return sdiv(r, __ldcg(k.diag + i));
+}
+
+struct Smem {
+  float *X, *R, *P, *S, *Wv, *D, *WX, *WY, *U, *H0, *H1, *H2, *H3, *H4;
+};
+
+__device__ __forceinline__ Smem smem_of(float *base, int stride, int W) {
+  Smem m;
+  m.X = base;
+  m.R = m.X + stride;
+  m.P = m.R + stride;
+  m.S = m.P + stride;
+  m.Wv = m.S + stride;
+  m.D = m.Wv + stride;
+  m.WX = m.D + stride;
+  m.WY = m.WX + stride;
+  m.U = m.WY + stride;
+  m.H0 = m.U + stride;  // x above / u above
+  m.H1 = m.H0 + W;      // x below / u below
+  m.H2 = m.H1 + W;      // wy of the row above the band (kept through the CG passes)
+  m.H3 = m.H2 + W;      // ey of the row above the band
+  m.H4 = m.H3 + W;      // gy of the row above the band
+  return m;
+}
+
+// w = A u for the band (u in m.U, halo u in H0 / H1, north coupling of the
+// first row in H2); accumulates (r, u), (w, u), (r, r).
+__device__ __forceinline__ void apply_band(const Smem &m, int W, int nr, int bp, bool has_below,
+                                           float acc[kRQ]) {
+  for (int q = threadIdx.x; q < bp; q += kRThreads) {
+    const int v = q / W, u = q - v * W;
+    const float uq = m.U[q];
+    float w = m.D[q] * uq;
+    if (u < W - 1) w -= m.WX[q] * m.U[q + 1];
+    if (u > 0) w -= m.WX[q - 1] * m.U[q - 1];
+    if (v < nr - 1) {
+      w -= m.WY[q] * m.U[q + W];
+    } else if (has_below) {
+      w -= m.WY[q] * m.H1[u];
+    }
+    if (v > 0) {
+      w -= m.WY[q - W] * m.U[q - W];
+    } else {
+      w -= m.H2[u] * m.H0[u];
+    }
+    m.Wv[q] = w;
+    acc[0] += m.R[q] * uq;
+    acc[1] += w * uq;
+    acc[2] += m.R[q] * m.R[q];
+  }
+}
+
+// Write the band's first and last rows of a shared array to a global plane.
+__device__ __forceinline__ void publish_edges(const float *src, float *dst, int W, int nr, int rb,
+                                              size_t P) {
+  for (int u = threadIdx.x; u < W; u += kRThreads) {
+    __stcg(dst + (size_t)rb * P + u, src[u]);
+    if (nr > 1) __stcg(dst + (size_t)(rb + nr - 1) * P + u, src[(nr - 1) * W + u]);
+  }
+}
+
+template <int DT>
+__device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, float t,
+                              const SolveCfg &c, float acc[kRQ]) {
+  const int W = k.W, H = k.H, bp = nr * W;
+  const size_t P = k.P;
+  const bool semi = c.terms & DF_TERM_SEMI, net = c.terms & DF_TERM_NET,
+             grad = c.terms & DF_TERM_GRAD;
+  const bool has_above = rb > 0, has_below = rb + nr < H;
+  // halo x rows (published by the neighbours after their last x update)
+  for (int u = threadIdx.x; u < W; u += kRThreads) {
+    m.H0[u] = has_above ? __ldcg(k.x + (size_t)(rb - 1) * P + u) : 0.0f;
+    m.H1[u] = has_below ? __ldcg(k.x + (size_t)(rb + nr) * P + u) : 0.0f;
+  }
+  __syncthreads();
+  // step A: the band's own x- and y-terms, and the y-term above the band
+  for (int q = threadIdx.x; q < bp; q += kRThreads) {
+    const int v = q / W, u = q - v * W;
+    const size_t gi = (size_t)(rb + v) * P + u;
+    const float xq = m.X[q];
+    float wx = 0.0f, ex = 0.0f, wy = 0.0f, ey = 0.0f;
+    if (grad && u < W - 1) {
+      ex = m.X[q + 1] - xq - ld_cnn<DT>(k.cnn[2], gi);
+      wx = robust_weight(ex, ld_cnn<DT>(k.cnn[3], gi), c.delta, c.loss);
+    }
+    if (grad && rb + v < H - 1) {
+      const float xs = (v < nr - 1) ? m.X[q + W] : m.H1[u];
+      ey = xs - xq - ld_cnn<DT>(k.cnn[4], gi);
+      wy = robust_weight(ey, ld_cnn<DT>(k.cnn[5], gi), c.delta, c.loss);
+    }
+    m.WX[q] = wx;
+    m.WY[q] = wy;
+    m.P[q] = ex;  // p and s are free during assembly: hold ex, ey
+    m.S[q] = ey;
+  }
+  for (int u = threadIdx.x; u < W; u += kRThreads) {
+    float wy = 0.0f, ey = 0.0f, gy = 0.0f;
+    if (grad && has_above) {
+      const size_t gi = (size_t)(rb - 1) * P + u;
+      gy = ld_cnn<DT>(k.cnn[4], gi);
+      ey = m.X[u] - m.H0[u] - gy;
+      wy = robust_weight(ey, ld_cnn<DT>(k.cnn[5], gi), c.delta, c.loss);
+    }
+    m.H2[u] = wy;
+    m.H3[u] = ey;
+    m.H4[u] = gy;
+  }
+  __syncthreads();
+  // step B: unary terms, diagonal, residual r0 = b - A x in residual form
+  for (int q = threadIdx.x; q < bp; q += kRThreads) {
+    const int v = q / W, u = q - v * W;
+    const size_t gi = (size_t)(rb + v) * P + u;
+    const float xq = m.X[q];
+    float ws = 0.0f, rs = 0.0f, bs = 0.0f;
+    if (semi) {
+      const float ms = __ldg(k.mu_s + gi), vs = __ldg(k.var_s + gi);
+      if (semi_valid(ms, vs)) {
+        ws = robust_weight(xq - t - ms, vs, c.delta, c.loss);
+        rs = ws * (t + ms - xq);
+        bs = ws * (t + ms);
+      }
+    }
+    float wn = 0.0f, mn = 0.0f;
+    if (net) {
+      mn = ld_cnn<DT>(k.cnn[0], gi);
+      wn = robust_weight(xq - mn, ld_cnn<DT>(k.cnn[1], gi), c.delta, c.loss);
+    }
+    const float wx = m.WX[q], ex = m.P[q], wy = m.WY[q], ey = m.S[q];
+    const float wxl = u > 0 ? m.WX[q - 1] : 0.0f, exl = u > 0 ? m.P[q - 1] : 0.0f;
+    const float wyu = v > 0 ? m.WY[q - W] : m.H2[u], eyu = v > 0 ? m.S[q - W] : m.H3[u];
+    const float d = ws + wn + wx + wxl + wy + wyu;
+    const float r = rs + wn * (mn - xq) + wx * ex - wxl * exl + wy * ey - wyu * eyu;
+    m.D[q] = d;
+    m.R[q] = r;
+    acc[0] += r * sdiv(r, d);
+    acc[1] += r * r;
+    if (c.tol > 0.0) {
+      const float gx = (grad && u < W - 1) ? ld_cnn<DT>(k.cnn[2], gi) : 0.0f;
+      const float gxl = (grad && u > 0) ? ld_cnn<DT>(k.cnn[2], gi - 1) : 0.0f;
+      const float gy = (grad && rb + v < H - 1) ? ld_cnn<DT>(k.cnn[4], gi) : 0.0f;
+      const float gyu = v > 0 ? ((grad) ? ld_cnn<DT>(k.cnn[4], gi - P) : 0.0f) : m.H4[u];
+      const float b = bs + wn * mn - wx * gx + wxl * gxl - wy * gy + wyu * gyu;
+      acc[2] += b * b;
+    }
+  }
+}
+
+template <int VECDUMMY>
+__global__ void __launch_bounds__(kRThreads, 1)
+    k_resident(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns) {
+  extern __shared__ float4 dyn_smem[];
+  __shared__ double s_red[kRWarps][kRQ];
+  __shared__ double s_tot[kRQ];
+  __shared__ ResKf s_kf;
+  __shared__ ResSeg s_seg;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = h->G;
+  const char *hb = reinterpret_cast<const char *>(h);
+  const ResCta *ctas = reinterpret_cast<const ResCta *>(hb + h->off_cta_tile);
+  const ResKf *kfs = reinterpret_cast<const ResKf *>(hb + h->off_kf);
+  double *slots = reinterpret_cast<double *>(reinterpret_cast<char *>(h) + h->off_slots);
+  const ResCta me = ctas[blockIdx.x];
+  if (tid == 0) {
+    s_kf = kfs[me.kf];
+    const Scalars *sc = s_kf.pl.sc;
+    s_seg.t = sc->t;
+    s_seg.gam = s_seg.alpha = s_seg.beta = s_seg.bb = 0.0;
+    s_seg.rr = sc->rr;
+    s_seg.stop = 0;
+    s_seg.iters = 0;
+    s_seg.active = (sc->flags & kFlagBadInput) ? 0 : 1;
+  }
+  __syncthreads();
+  const Planes &k = s_kf.pl;
+  const int W = k.W, H = k.H;
+  const size_t P = k.P;
+  const int rb = me.rb, nr = me.re - me.rb, bp = nr * W;
+  const bool has_below = me.re < H;
+  const Smem m = smem_of(reinterpret_cast<float *>(dyn_smem), h->th, W);
+  float *Rg[2] = {k.v[1], k.v[2]}, *Sg[2] = {k.v[3], k.v[4]}, *Wg[2] = {k.v[5], k.v[6]};
+  const bool active = s_seg.active != 0;
+  const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step;
+  int parity = 0;
+  bool alive = true;
+
+  for (int q = tid; q < bp; q += kRThreads) {
+    const int v = q / W, u = q - v * W;
+    m.X[q] = __ldcg(k.x + (size_t)(rb + v) * P + u);
+  }
+  __syncthreads();
+
+  // partial sums of a pass -> slot -> barrier -> this keyframe's totals
+  auto end_pass = [&](float acc[kRQ]) -> bool {
+#pragma unroll
+    for (int q = 0; q < kRQ; ++q) {
+      const double dq = warp_sum((double)acc[q]);
+      if (lane == 0) s_red[warp][q] = dq;
+    }
+    __syncthreads();
+    double *pslots = slots + (size_t)parity * G * kRQ;
+    if (tid < kRQ) {
+      double s = 0.0;
+      for (int w = 0; w < kRWarps; ++w) s += s_red[w][tid];
+      pslots[(size_t)blockIdx.x * kRQ + tid] = s;
+    }
+    if (!grid_sync(h, G, limit_ns)) return false;
+    if (warp == 0) {
+#pragma unroll
+      for (int q = 0; q < kRQ; ++q) {
+        double s = 0.0;
+        for (int sl = s_kf.cta_begin + lane; sl < s_kf.cta_end; sl += 32)
+          s += __ldcg(pslots + (size_t)sl * kRQ + q);
+        s = warp_sum(s);
+        if (lane == 0) s_tot[q] = s;
+      }
+    }
+    __syncthreads();
+    parity ^= 1;
+    return true;
+  };
+
+  auto scale_partials = [&](float acc[kRQ], int q0, float t) {
+    for (int q = tid; q < bp; q += kRThreads) {
+      const int v = q / W, u = q - v * W;
+      const size_t gi = (size_t)(rb + v) * P + u;
+      const float ms = __ldg(k.mu_s + gi), vs = __ldg(k.var_s + gi);
+      if (semi_valid(ms, vs)) {
+        const float xq = m.X[q];
+        const float w = robust_weight(xq - t - ms, vs, c.delta, c.loss);
+        acc[q0] += w;
+        acc[q0 + 1] += w * (xq - ms);
+      }
+    }
+  };
+  auto scale_update = [&](int qw, int qwr) {
+    if (tid == 0 && s_seg.active && s_tot[qw] > 0.0) s_seg.t = s_tot[qwr] / s_tot[qw];
+    __syncthreads();
+  };
+
+  bool scale_pending = false;
+  for (int gn = 0; gn < n_gn && alive; ++gn) {
+    if (do_scale) {
+      if (!scale_pending) {
+        float acc[kRQ] = {0.0f, 0.0f, 0.0f};
+        if (active) scale_partials(acc, 0, (float)s_seg.t);
+        if (!(alive = end_pass(acc))) break;
+        scale_update(0, 1);
+      }
+      scale_pending = false;
+    }
+    {  // ASSEMBLE
+      float acc[kRQ] = {0.0f, 0.0f, 0.0f};
+      if (active) {
+        const float t = (float)s_seg.t;
+        if (k.dtype == DF_BF16)
+          assemble_band<DF_BF16>(m, k, rb, nr, t, c, acc);
+        else if (k.dtype == DF_F16)
+          assemble_band<DF_F16>(m, k, rb, nr, t, c, acc);
+        else
+          assemble_band<DF_F32>(m, k, rb, nr, t, c, acc);
+        __syncthreads();
+        publish_edges(m.R, Rg[0], W, nr, rb, P);
+        publish_edges(m.D, k.diag, W, nr, rb, P);
+      }
+      if (!(alive = end_pass(acc))) break;
+      if (tid == 0) {
+        s_seg.gam = s_tot[0];
+        s_seg.rr = s_tot[1];
+        s_seg.bb = s_tot[2];
+        s_seg.stop = (c.tol > 0.0 && sqrt(s_seg.rr) < c.tol * sqrt(s_seg.bb)) ? 1 : 0;
+      }
+      __syncthreads();
+    }
+    if (n_pcg == 0) continue;
+    {  // INIT: w0 = A u0
+      float acc[kRQ] = {0.0f, 0.0f, 0.0f};
+      if (active && !s_seg.stop) {
+        for (int u = tid; u < W; u += kRThreads) {
+          m.H0[u] = rb > 0 ? halo_u<0>(k, Rg[0], nullptr, nullptr, (size_t)(rb - 1) * P + u, 0.f, 0.f) : 0.0f;
+          m.H1[u] = has_below ? halo_u<0>(k, Rg[0], nullptr, nullptr, (size_t)(rb + nr) * P + u, 0.f, 0.f) : 0.0f;
+        }
+        for (int q = tid; q < bp; q += kRThreads) m.U[q] = sdiv(m.R[q], m.D[q]);
+        __syncthreads();
+        apply_band(m, W, nr, bp, has_below, acc);
+        __syncthreads();
+        publish_edges(m.Wv, Wg[0], W, nr, rb, P);
+      }
+      if (!(alive = end_pass(acc))) break;
+      if (tid == 0 && !s_seg.stop) {
+        const double dl = s_tot[1];
+        if (s_seg.gam == 0.0 || !(dl > 0.0)) {
+          s_seg.stop = 1;
+        } else {
+          s_seg.alpha = s_seg.gam / dl;
+          s_seg.beta = 0.0;
+        }
+      }
+      __syncthreads();
+    }
+    for (int it = 0; it < n_pcg && alive; ++it) {
+      const int cb = it & 1, nb = cb ^ 1;
+      const float fa = (float)s_seg.alpha, fb = (float)s_seg.beta;
+      const bool first = it == 0;
+      const bool run = active && !s_seg.stop;
+      float acc[kRQ] = {0.0f, 0.0f, 0.0f};
+      if (it == n_pcg - 1) {  // FINAL
+        const bool fs = do_scale && gn + 1 < n_gn;
+        if (run) {
+          for (int q = tid; q < bp; q += kRThreads) {
+            const float d = m.D[q], r = m.R[q];
+            const float ui = sdiv(r, d);
+            const float p = first ? ui : ui + fb * m.P[q];
+            m.X[q] += fa * p;
+            const float si = first ? m.Wv[q] : m.Wv[q] + fb * m.S[q];
+            const float rn = r - fa * si;
+            acc[0] += rn * rn;
+          }
+        }
+        if (active) {
+          // x may also have moved in earlier passes of a depth step that
+          // stopped early: the neighbours' next assembly needs the edges
+          __syncthreads();
+          publish_edges(m.X, k.x, W, nr, rb, P);
+        }
+        if (fs && active) scale_partials(acc, 1, (float)s_seg.t);
+        if (!(alive = end_pass(acc))) break;
+        if (tid == 0 && run) {
+          s_seg.iters += 1;
+          s_seg.rr = s_tot[0];
+        }
+        __syncthreads();
+        if (fs) {
+          scale_update(1, 2);
+          scale_pending = true;
+        }
+      } else {  // ITER
+        if (run) {
+          for (int u = tid; u < W; u += kRThreads) {
+            float a = 0.0f, b = 0.0f;
+            if (first) {
+              if (rb > 0) a = halo_u<1>(k, Rg[cb], Sg[cb], Wg[cb], (size_t)(rb - 1) * P + u, fa, fb);
+              if (has_below) b = halo_u<1>(k, Rg[cb], Sg[cb], Wg[cb], (size_t)(rb + nr) * P + u, fa, fb);
+            } else {
+              if (rb > 0) a = halo_u<2>(k, Rg[cb], Sg[cb], Wg[cb], (size_t)(rb - 1) * P + u, fa, fb);
+              if (has_below) b = halo_u<2>(k, Rg[cb], Sg[cb], Wg[cb], (size_t)(rb + nr) * P + u, fa, fb);
+            }
+            m.H0[u] = a;
+            m.H1[u] = b;
+          }
+          for (int q = tid; q < bp; q += kRThreads) {
+            const float d = m.D[q], r = m.R[q];
+            const float ui = sdiv(r, d);
+            const float p = first ? ui : ui + fb * m.P[q];
+            m.X[q] += fa * p;
+            m.P[q] = p;
+            const float si = first ? m.Wv[q] : m.Wv[q] + fb * m.S[q];
+            m.S[q] = si;
+            const float rn = r - fa * si;
+            m.R[q] = rn;
+            m.U[q] = sdiv(rn, d);
+          }
+          __syncthreads();
+          apply_band(m, W, nr, bp, has_below, acc);
+          __syncthreads();
+          publish_edges(m.R, Rg[nb], W, nr, rb, P);
+          publish_edges(m.S, Sg[nb], W, nr, rb, P);
+          publish_edges(m.Wv, Wg[nb], W, nr, rb, P);
+        }
+        if (!(alive = end_pass(acc))) break;
+        if (tid == 0 && run) {
+          s_seg.iters += 1;
+          s_seg.rr = s_tot[2];
+          const double gn_ = s_tot[0], dl = s_tot[1];
+          if (c.tol > 0.0 && sqrt(s_seg.rr) < c.tol * sqrt(s_seg.bb)) {
+            s_seg.stop = 1;
+          } else {
+            const double beta = gn_ / s_seg.gam;
+            const double denom = dl - beta * gn_ / s_seg.alpha;
+            if (gn_ == 0.0 || !(denom > 0.0)) {
+              s_seg.stop = 1;
+            } else {
+              s_seg.beta = beta;
+              s_seg.alpha = gn_ / denom;
+              s_seg.gam = gn_;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+
+  if (alive && active) {
+    for (int q = tid; q < bp; q += kRThreads) {
+      const int v = q / W, u = q - v * W;
+      __stcg(k.x + (size_t)(rb + v) * P + u, m.X[q]);
+    }
+  }
+  if (tid == 0) {
+    Scalars *sc = k.sc;
+    if (!alive) {
+      atomicOr(&sc->flags, kFlagTimeout);
+    } else if (active && s_kf.cta_begin == (int)blockIdx.x) {
+      sc->t = s_seg.t;
+      sc->rr = s_seg.rr;
+      sc->rho = s_seg.gam;
+      sc->iters = s_seg.iters;
+      sc->stop = s_seg.stop;
+    }
+  }
+  grid_exit(h, G);
+}
+
+size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+struct ResDev {
+  int sms = 0, smem_optin = 0, occ = 0, static_smem = 0;
+};
+ResDev g_rdev[64];
+bool g_rdev_init[64] = {false};
+std::mutex g_rdev_mu;
+
+const ResDev &rdev() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  if (dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> lk(g_rdev_mu);
+  if (!g_rdev_init[dev]) {
+    ResDev d;
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_resident<0>) == cudaSuccess) d.static_smem = (int)fa.sharedSizeBytes;
+    cudaGetLastError();
+    g_rdev[dev] = d;
+    g_rdev_init[dev] = true;
+  }
+  return g_rdev[dev];
+}
+
+}  // namespace
+
+size_t resident_plan_bytes(int nkf, int G) {
+  size_t off = align16(sizeof(PlanHeader));
+  off += align16(sizeof(ResCta) * (size_t)G);
+  off += align16(sizeof(ResKf) * (size_t)nkf);
+  off += sizeof(double) * 2 * (size_t)G * kRQ;
+  return off;
+}
+
+int resident_max_ctas() { return rdev().sms; }
+
+bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
+                         std::vector<char> &out, LaunchShape &shape) {
+  const ResDev &d = rdev();
+  if (n < 1 || d.sms <= 0 || d.smem_optin <= 0) return false;
+  int G_cap = d.sms;
+  if (tune.max_ctas > 0) G_cap = std::min(G_cap, tune.max_ctas);
+  const long long avail = (long long)d.smem_optin - d.static_smem - 1024;
+  long long total_px = 0;
+  int Wmax = 0;
+  for (int k = 0; k < n; ++k) {
+    total_px += (long long)kfs[k]->W * kfs[k]->H;
+    Wmax = std::max(Wmax, kfs[k]->W);
+  }
+  // rows a band may hold within the shared-memory budget, per keyframe
+  std::vector<int> nb(n), maxrows(n);
+  long long need = 0;
+  for (int k = 0; k < n; ++k) {
+    const long long Wk = kfs[k]->W;
+    const long long rows = (avail / 4 - (long long)kHalo * Wmax) / (9 * Wk);
+    if (rows < 1) return false;
+    maxrows[k] = (int)std::min<long long>(rows, kfs[k]->H);
+    nb[k] = (kfs[k]->H + maxrows[k] - 1) / maxrows[k];
+    need += nb[k];
+  }
+  if (need > G_cap) return false;
+  // hand the remaining CTAs out in proportion to pixels (more bands = less
+  // work per CTA), never more bands than rows
+  int spare = G_cap - (int)need;
+  while (spare > 0) {
+    int best = -1;
+    double best_load = 0.0;
+    for (int k = 0; k < n; ++k) {
+      if (nb[k] >= kfs[k]->H) continue;
+      const double load = (double)kfs[k]->W * kfs[k]->H / nb[k];
+      if (load > best_load) {
+        best_load = load;
+        best = k;
+      }
+    }
+    if (best < 0) break;
+    ++nb[best];
+    --spare;
+  }
+  int G = 0;
+  for (int k = 0; k < n; ++k) G += nb[k];
+  std::vector<ResCta> ctas(G);
+  std::vector<ResKf> rk(n);
+  int band_px_max = 0, cI = 0;
+  for (int k = 0; k < n; ++k) {
+    const int H = kfs[k]->H;
+    rk[k].pl = *kfs[k];
+    rk[k].cta_begin = cI;
+    for (int b = 0; b < nb[k]; ++b) {
+      const int r0 = (int)((long long)H * b / nb[k]), r1 = (int)((long long)H * (b + 1) / nb[k]);
+      ctas[cI].kf = k;
+      ctas[cI].rb = r0;
+      ctas[cI].re = r1;
+      band_px_max = std::max(band_px_max, (r1 - r0) * kfs[k]->W);
+      ++cI;
+    }
+    rk[k].cta_end = cI;
+  }
+  const int stride = (band_px_max + 3) & ~3;
+  const long long smem = (long long)(9LL * stride + (long long)kHalo * Wmax) * 4;
+  if (smem > avail) return false;
+  out.assign(resident_plan_bytes(n, G), 0);
+  char *base = out.data();
+  PlanHeader *hd = reinterpret_cast<PlanHeader *>(base);
+  size_t off = align16(sizeof(PlanHeader));
+  hd->off_cta_tile = (long long)off;
+  off += align16(sizeof(ResCta) * (size_t)G);
+  hd->off_kf = (long long)off;
+  off += align16(sizeof(ResKf) * (size_t)n);
+  hd->off_slots = (long long)off;
+  hd->kind = kPlanResident;
+  hd->debug_skip_cta = tune.debug_skip_cta;
+  hd->nkf = n;
+  hd->G = G;
+  hd->nslots = G;
+  hd->th = stride;  // shared-memory stride of one band array
+  hd->smem_bytes = (int)smem;
+  hd->bytes = (long long)out.size();
+  memcpy(base + hd->off_cta_tile, ctas.data(), sizeof(ResCta) * G);
+  memcpy(base + hd->off_kf, rk.data(), sizeof(ResKf) * n);
+  shape.kind = kPlanResident;
+  shape.G = G;
+  shape.vec = 0;
+  shape.smem = (int)smem;
+  (void)total_px;
+  return true;
+}
+
+cudaError_t resident_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
+                            int n_pcg, unsigned long long limit_ns, cudaStream_t s) {
+  PlanHeader *h = static_cast<PlanHeader *>(dplan);
+  cudaError_t e = cudaFuncSetAttribute(k_resident<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       shape.smem);
+  if (e != cudaSuccess) return e;
+  void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns};
+  count_launches(1);
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_resident<0>), dim3(shape.G),
+                                     dim3(kRThreads), args, (size_t)shape.smem, s);
+}
+
+}  // namespace df

@@ -42,6 +42,14 @@ class df_solve_report(C.Structure):
                 ("iters_done", C.c_int32), ("flags", C.c_int32)]
 
 
+class df_tuning(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("vec", C.c_int32), ("tile_rows", C.c_int32),
+                ("max_ctas", C.c_int32), ("debug_skip_cta", C.c_int32)]
+
+
+DF_MODE_AUTO, DF_MODE_STREAMING, DF_MODE_RESIDENT = 0, 1, 2
+
+
 class DFError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         self.status = status
@@ -88,6 +96,11 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.df_memory_in_use.argtypes = []
     L.df_memory_in_use.restype = C.c_size_t
     L.df_semi_to_log.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, vp]
+    L.df_set_tuning.argtypes = [C.POINTER(df_tuning)]
+    L.df_get_tuning.argtypes = [C.POINTER(df_tuning)]
+    L.df_set_spin_limit_ns.argtypes = [C.c_uint64]
+    for name in ("df_set_tuning", "df_get_tuning", "df_set_spin_limit_ns"):
+        getattr(L, name).restype = C.c_int
     L.df_kernel_launches.argtypes = []
     L.df_kernel_launches.restype = C.c_uint64
     L.df_status_str.argtypes = [st]
@@ -287,6 +300,22 @@ def df_semi_to_log(depth, var_depth, mu_out, var_out, stream=None):
     _check(load().df_semi_to_log(_ptr(depth)[0], _ptr(var_depth)[0], _ptr(mu_out)[0],
                                  _ptr(var_out)[0], _numel(depth), on_dev, _stream(stream, depth)),
            "df_semi_to_log")
+
+
+def df_set_tuning(mode: int = 0, vec: int = 0, tile_rows: int = 0, max_ctas: int = 0,
+                  debug_skip_cta: int = -1):
+    t = df_tuning(mode, vec, tile_rows, max_ctas, debug_skip_cta)
+    _check(load().df_set_tuning(C.byref(t)), "df_set_tuning")
+
+
+def df_get_tuning() -> df_tuning:
+    t = df_tuning()
+    _check(load().df_get_tuning(C.byref(t)), "df_get_tuning")
+    return t
+
+
+def df_set_spin_limit_ns(ns: int):
+    _check(load().df_set_spin_limit_ns(int(ns)), "df_set_spin_limit_ns")
 
 
 def df_kernel_launches() -> int:

@@ -14,8 +14,12 @@ from paper_2207_12244_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-SOLVERS = [dfl.DF_SOLVER_LAUNCHES, dfl.DF_SOLVER_FUSED]
-SOLVER_IDS = ["launches", "fused"]
+# (solver, fused kernel mode): the per-phase launches, the streaming fused
+# kernel and the shared-memory-resident fused kernel
+SOLVERS = [(dfl.DF_SOLVER_LAUNCHES, dfl.DF_MODE_AUTO),
+           (dfl.DF_SOLVER_FUSED, dfl.DF_MODE_STREAMING),
+           (dfl.DF_SOLVER_FUSED, dfl.DF_MODE_RESIDENT)]
+SOLVER_IDS = ["launches", "streaming", "resident"]
 
 
 @pytest.fixture(scope="module")
@@ -23,9 +27,12 @@ def o():
     return oracle.get()
 
 
-@pytest.fixture(scope="module", params=SOLVERS, ids=SOLVER_IDS)
+@pytest.fixture(params=SOLVERS, ids=SOLVER_IDS)
 def solver(request):
-    return request.param
+    sv, mode = request.param
+    dfl.df_set_tuning(mode=mode)
+    yield sv
+    dfl.df_set_tuning()
 
 
 # The workload of the paper's network resolution: 256 x 192, 10 GN x 3 PCG.
@@ -283,3 +290,52 @@ def test_budget_accounting_with_gpu():
         b.close()
     finally:
         dfl.df_set_memory_budget(0)
+
+
+@pytest.mark.parametrize("mode", [dfl.DF_MODE_STREAMING, dfl.DF_MODE_RESIDENT],
+                         ids=["streaming", "resident"])
+def test_streaming_tile_shapes(o, mode):
+    """Every tile shape of the streaming kernel (and grid caps for both
+    kernels) gives the same answer."""
+    kf = synth.make_keyframe(300, 140, 22)
+    prm = params(n_gn=3, n_pcg=4, solver=dfl.DF_SOLVER_FUSED)
+    xo, to, _ = oracle_solve(o, kf, prm)
+    shapes = ([(1, 1, 0), (1, 5, 0), (4, 3, 0), (4, 16, 0), (4, 64, 7), (1, 2, 1)]
+              if mode == dfl.DF_MODE_STREAMING else [(0, 0, 0), (0, 0, 3), (0, 0, 1)])
+    try:
+        for vec, th, cap in shapes:
+            dfl.df_set_tuning(mode=mode, vec=vec, tile_rows=th, max_ctas=cap)
+            x, t, rep = solve(kf, prm)
+            assert_parity(x, t, xo, to, what=f"mode {mode} vec {vec} th {th} cap {cap}")
+    finally:
+        dfl.df_set_tuning()
+
+
+@pytest.mark.parametrize("mode", [dfl.DF_MODE_STREAMING, dfl.DF_MODE_RESIDENT],
+                         ids=["streaming", "resident"])
+def test_barrier_wait_times_out_cleanly(mode):
+    """One CTA leaves without arriving at its first grid barrier (test
+    switch): the others' bounded waits run out, the solve reports
+    DF_ETIMEOUT, and the next solve on the same context is correct."""
+    kf = synth.make_keyframe(160, 120, 23)
+    prm = params(n_gn=2, n_pcg=3, solver=dfl.DF_SOLVER_FUSED)
+    ref = solve(kf, prm)
+    try:
+        dfl.df_set_spin_limit_ns(50_000_000)
+        dfl.df_set_tuning(mode=mode, debug_skip_cta=1, max_ctas=4)
+        k = create(kf)
+        try:
+            k.frame_update(to_dev(kf.mu_s), to_dev(kf.var_s))
+            with pytest.raises(dfl.DFError) as e:
+                k.optimise(prm, report=True)
+            assert e.value.status == dfl.DF_ETIMEOUT
+            with pytest.raises(dfl.DFError) as e:
+                k.check()
+            assert e.value.status == dfl.DF_ETIMEOUT
+        finally:
+            k.close()
+    finally:
+        dfl.df_set_tuning()
+        dfl.df_set_spin_limit_ns(2_000_000_000)
+    again = solve(kf, prm)
+    assert np.array_equal(again[0], ref[0]) and again[1] == ref[1]
