@@ -433,7 +433,7 @@ static df_status fused_one(df_keyframe *kf, const SolveCfg &c, int n_gn, int n_p
     df::LaunchShape shape;
     const Planes *one = &kf->planes;
     if (!df::fused_build_plan(&one, 1, tune, host, shape))
-      return fail(DF_EINVAL, "fused solver: no launch plan for this keyframe");
+      return fail(DF_ENOTSUP, "fused solver: this launch shape cannot hold the keyframe");
     if (host.size() > kf->plan_cap) return fail(DF_EINVAL, "fused plan larger than reserved");
     DF_CUDA(cudaMemcpyAsync(kf->plan, host.data(), host.size(), cudaMemcpyHostToDevice, s));
     kf->plan_shape = shape;

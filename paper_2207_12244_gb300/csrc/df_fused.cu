@@ -279,7 +279,7 @@ __device__ void assemble_tile(const FusedKf &K, int lt, float t, const SolveCfg 
     }
     const F<VEC> ms = ldr<VEC>(k.mu_s + i), vs = ldr<VEC>(k.var_s + i);
     const F<VEC> mn = ldc<VEC, DT>(k.cnn[0], i), vn = ldc<VEC, DT>(k.cnn[1], i);
-    F<VEC> dd, rr_, wxo, wyo;
+    F<VEC> dd, rr_, wxo, wyo;  // dd holds 1 / diag
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       float d = 0.0f, r = 0.0f, b = 0.0f;
@@ -302,11 +302,12 @@ __device__ void assemble_tile(const FusedKf &K, int lt, float t, const SolveCfg 
         b = bs + wn * m - wxv.v[e] * gxv.v[e] + wxw.v[e] * gxw.v[e] - wyv.v[e] * gyv.v[e] +
             wy_up.v[e] * gy_up.v[e];
       }
-      dd.v[e] = d;
+      const float id = d > 0.0f ? 1.0f / d : 0.0f;
+      dd.v[e] = id;
       rr_.v[e] = r;
       wxo.v[e] = wxv.v[e];
       wyo.v[e] = wyv.v[e];
-      acc[0] += r * safe_div(r, d);
+      acc[0] += r * (r * id);
       acc[1] += r * r;
       acc[2] += b * b;
     }
@@ -328,7 +329,7 @@ __device__ void assemble_tile(const FusedKf &K, int lt, float t, const SolveCfg 
 // iteration, s_i = 0 and r' = r for INIT), and u' = r' / diag.
 template <int VEC>
 struct RowNew {
-  F<VEC> d, r, s, u, r_in;  // diag, r', s_i, u', and the residual entering the pass
+  F<VEC> d, r, s, u, r_in;  // 1/diag, r', s_i, u', and the residual entering the pass
 };
 
 template <int VEC, int KIND>  // KIND: 0 INIT, 1 first iteration, 2 later iteration
@@ -353,7 +354,7 @@ __device__ __forceinline__ RowNew<VEC> row_new(const float *r_cur, const float *
     }
   }
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) o.u.v[e] = safe_div(o.r.v[e], o.d.v[e]);
+  for (int e = 0; e < VEC; ++e) o.u.v[e] = o.r.v[e] * o.d.v[e];
   return o;
 }
 
@@ -361,14 +362,14 @@ template <int KIND>
 __device__ __forceinline__ float col_new_u(const float *r_cur, const float *s_prev,
                                            const float *w_cur, const float *diag, size_t i,
                                            float alpha, float beta) {
-  const float d = __ldcg(diag + i);
+  const float id = __ldcg(diag + i);
   float r = __ldcg(r_cur + i);
   if constexpr (KIND != 0) {
     float s = __ldcg(w_cur + i);
     if constexpr (KIND == 2) s += beta * __ldcg(s_prev + i);
     r -= alpha * s;
   }
-  return safe_div(r, d);
+  return r * id;
 }
 
 template <int VEC, int KIND>
@@ -431,8 +432,9 @@ __device__ void cg_tile(const FusedKf &K, int lt, float alpha, float beta, const
     F<VEC> w_new;
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
-      w_new.v[e] = cur.d.v[e] * cur.u.v[e] - wxr.v[e] * u_e.v[e] - wx_w.v[e] * u_w.v[e] -
-                   wyr.v[e] * u_dn.v[e] - wy_up.v[e] * u_up.v[e];
+      // A u = r - N u (u = r / diag, A = diag - N)
+      w_new.v[e] = cur.r.v[e] - (wxr.v[e] * u_e.v[e] + wx_w.v[e] * u_w.v[e] +
+                                 wyr.v[e] * u_dn.v[e] + wy_up.v[e] * u_up.v[e]);
       acc[0] += cur.r.v[e] * cur.u.v[e];
       acc[1] += w_new.v[e] * cur.u.v[e];
       acc[2] += cur.r.v[e] * cur.r.v[e];
@@ -446,7 +448,7 @@ __device__ void cg_tile(const FusedKf &K, int lt, float alpha, float beta, const
       F<VEC> x = ldm<VEC>(k.x + i);
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
-        const float ui = safe_div(r_old.v[e], cur.d.v[e]);
+        const float ui = r_old.v[e] * cur.d.v[e];
         p.v[e] = (KIND == 2) ? ui + beta * p.v[e] : ui;
         x.v[e] += alpha * p.v[e];
       }
@@ -479,7 +481,7 @@ __device__ void final_tile(const FusedKf &K, int lt, bool first, bool update, fl
       const F<VEC> s = first ? fzero<VEC>() : ldm<VEC>(s_prev + i);
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
-        const float ui = safe_div(r.v[e], d.v[e]);
+        const float ui = r.v[e] * d.v[e];
         const float pi = first ? ui : ui + beta * p.v[e];
         x.v[e] += alpha * pi;
         const float si = first ? w.v[e] : w.v[e] + beta * s.v[e];
@@ -597,7 +599,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
-        const double dq = warp_sum((double)a[q]);
+        const double dq = (double)warp_sum_f(a[q]);
         if (lane == 0) s_acc[warp][seg][q] += dq;
       }
     }

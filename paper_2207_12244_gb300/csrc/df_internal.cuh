@@ -125,6 +125,16 @@ __device__ __forceinline__ bool semi_valid(float mu, float var) {
 
 // ---- reductions -----------------------------------------------------------
 
+// FP32 butterfly-free warp sum (lane 0 holds the result). Used for the
+// per-warp stage of the solver's inner products: GB300's FP64 rate is a tiny
+// fraction of FP32, so FP64 starts above the warp (cross-warp and cross-CTA
+// sums of a few hundred values).
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

@@ -29,7 +29,7 @@ namespace {
 constexpr int kRThreads = 512;
 constexpr int kRWarps = kRThreads / 32;
 constexpr int kRQ = 3;
-constexpr int kHalo = 5;  // halo rows of W floats kept in shared memory
+constexpr int kHalo = 9;  // halo arrays of W floats kept in shared memory
 
 struct ResKf {
   Planes pl;
@@ -45,69 +45,81 @@ struct ResSeg {
   int stop, iters, active, pad;
 };
 
-__device__ __forceinline__ float sdiv(float r, float d) { return d > 0.0f ? r / d : 0.0f; }
+// What the halo stage arrays are loaded with right after a barrier, for the
+// pass that follows it.
+enum HaloKind : int { HK_NONE = 0, HK_X, HK_INIT, HK_ITER };
 
-// The new residual's Jacobi-scaled value u' at one global pixel of a
-// neighbouring band, from that band's published r, s, w and diag.
-template <int KIND>  // 0: INIT (u = r / d), 1: first iteration, 2: later
-__device__ __forceinline__ float halo_u(const Planes &k, const float *Rc, const float *Sp,
-                                        const float *Wc, size_t i, float alpha, float beta) {
-  float r = __ldcg(Rc + i);
-  if constexpr (KIND != 0) {
-    float s = __ldcg(Wc + i);
-    if constexpr (KIND == 2) s += beta * __ldcg(Sp + i);
-    r -= alpha * s;
-  }
-  return sdiv(r, __ldcg(k.diag + i));
-}
-
+// Shared-memory arrays of one band (stride BS floats each): x, r, p, s, w,
+// 1/diag, wx, wy, u; then the halo arrays (W floats each): HA[0..3] the row
+// above the band, HA[4..7] the row below, WYT the y-coupling of the row above.
 struct Smem {
-  float *X, *R, *P, *S, *Wv, *D, *WX, *WY, *U, *H0, *H1, *H2, *H3, *H4;
+  float *X, *R, *P, *S, *Wv, *ID, *WX, *WY, *U;
+  float *HA[8];
+  float *WYT;
 };
 
 __device__ __forceinline__ Smem smem_of(float *base, int stride, int W) {
   Smem m;
-  m.X = base;
-  m.R = m.X + stride;
-  m.P = m.R + stride;
-  m.S = m.P + stride;
-  m.Wv = m.S + stride;
-  m.D = m.Wv + stride;
-  m.WX = m.D + stride;
-  m.WY = m.WX + stride;
-  m.U = m.WY + stride;
-  m.H0 = m.U + stride;  // x above / u above
-  m.H1 = m.H0 + W;      // x below / u below
-  m.H2 = m.H1 + W;      // wy of the row above the band (kept through the CG passes)
-  m.H3 = m.H2 + W;      // ey of the row above the band
-  m.H4 = m.H3 + W;      // gy of the row above the band
+  float *p = base;
+  m.X = p; p += stride;
+  m.R = p; p += stride;
+  m.P = p; p += stride;
+  m.S = p; p += stride;
+  m.Wv = p; p += stride;
+  m.ID = p; p += stride;
+  m.WX = p; p += stride;
+  m.WY = p; p += stride;
+  m.U = p; p += stride;
+  for (int j = 0; j < 8; ++j) { m.HA[j] = p; p += W; }
+  m.WYT = p;
   return m;
 }
 
-// w = A u for the band (u in m.U, halo u in H0 / H1, north coupling of the
-// first row in H2); accumulates (r, u), (w, u), (r, r).
+// Per-thread walk over the band's pixels q = tid, tid + T, ... with the row
+// and column kept incrementally (no integer division per pixel).
+struct Walk {
+  int q, v, u, dv, du, W;
+  __device__ __forceinline__ Walk(int W_) : W(W_) {
+    q = threadIdx.x;
+    v = q / W;
+    u = q - v * W;
+    dv = kRThreads / W;
+    du = kRThreads - dv * W;
+  }
+  __device__ __forceinline__ void next() {
+    q += kRThreads;
+    v += dv;
+    u += du;
+    if (u >= W) {
+      u -= W;
+      ++v;
+    }
+  }
+};
+
+// w = A u = r - N u for the band (A = diag - N; u = r / diag exactly, so
+// diag * u is r). Halo u: HA[0] above, HA[4] below; y-coupling of the row
+// above the band in WYT. Accumulates (r, u), (w, u), (r, r).
 __device__ __forceinline__ void apply_band(const Smem &m, int W, int nr, int bp, bool has_below,
                                            float acc[kRQ]) {
-  for (int q = threadIdx.x; q < bp; q += kRThreads) {
-    const int v = q / W, u = q - v * W;
+  for (Walk it(W); it.q < bp; it.next()) {
+    const int q = it.q, u = it.u, v = it.v;
     const float uq = m.U[q];
-    float w = m.D[q] * uq;
-    if (u < W - 1) w -= m.WX[q] * m.U[q + 1];
-    if (u > 0) w -= m.WX[q - 1] * m.U[q - 1];
+    float nu = 0.0f;
+    if (u < W - 1) nu += m.WX[q] * m.U[q + 1];
+    if (u > 0) nu += m.WX[q - 1] * m.U[q - 1];
     if (v < nr - 1) {
-      w -= m.WY[q] * m.U[q + W];
+      nu += m.WY[q] * m.U[q + W];
     } else if (has_below) {
-      w -= m.WY[q] * m.H1[u];
+      nu += m.WY[q] * m.HA[4][u];
     }
-    if (v > 0) {
-      w -= m.WY[q - W] * m.U[q - W];
-    } else {
-      w -= m.H2[u] * m.H0[u];
-    }
+    nu += (v > 0) ? m.WY[q - W] * m.U[q - W] : m.WYT[u] * m.HA[0][u];
+    const float r = m.R[q];
+    const float w = r - nu;
     m.Wv[q] = w;
-    acc[0] += m.R[q] * uq;
+    acc[0] += r * uq;
     acc[1] += w * uq;
-    acc[2] += m.R[q] * m.R[q];
+    acc[2] += r * r;
   }
 }
 
@@ -127,16 +139,11 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
   const size_t P = k.P;
   const bool semi = c.terms & DF_TERM_SEMI, net = c.terms & DF_TERM_NET,
              grad = c.terms & DF_TERM_GRAD;
-  const bool has_above = rb > 0, has_below = rb + nr < H;
-  // halo x rows (published by the neighbours after their last x update)
-  for (int u = threadIdx.x; u < W; u += kRThreads) {
-    m.H0[u] = has_above ? __ldcg(k.x + (size_t)(rb - 1) * P + u) : 0.0f;
-    m.H1[u] = has_below ? __ldcg(k.x + (size_t)(rb + nr) * P + u) : 0.0f;
-  }
-  __syncthreads();
+  const bool has_above = rb > 0;
+  // x of the rows above / below the band is in HA[0] / HA[4] (prefetched)
   // step A: the band's own x- and y-terms, and the y-term above the band
-  for (int q = threadIdx.x; q < bp; q += kRThreads) {
-    const int v = q / W, u = q - v * W;
+  for (Walk it(W); it.q < bp; it.next()) {
+    const int q = it.q, u = it.u, v = it.v;
     const size_t gi = (size_t)(rb + v) * P + u;
     const float xq = m.X[q];
     float wx = 0.0f, ex = 0.0f, wy = 0.0f, ey = 0.0f;
@@ -145,7 +152,7 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
       wx = robust_weight(ex, ld_cnn<DT>(k.cnn[3], gi), c.delta, c.loss);
     }
     if (grad && rb + v < H - 1) {
-      const float xs = (v < nr - 1) ? m.X[q + W] : m.H1[u];
+      const float xs = (v < nr - 1) ? m.X[q + W] : m.HA[4][u];
       ey = xs - xq - ld_cnn<DT>(k.cnn[4], gi);
       wy = robust_weight(ey, ld_cnn<DT>(k.cnn[5], gi), c.delta, c.loss);
     }
@@ -159,17 +166,17 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     if (grad && has_above) {
       const size_t gi = (size_t)(rb - 1) * P + u;
       gy = ld_cnn<DT>(k.cnn[4], gi);
-      ey = m.X[u] - m.H0[u] - gy;
+      ey = m.X[u] - m.HA[0][u] - gy;
       wy = robust_weight(ey, ld_cnn<DT>(k.cnn[5], gi), c.delta, c.loss);
     }
-    m.H2[u] = wy;
-    m.H3[u] = ey;
-    m.H4[u] = gy;
+    m.WYT[u] = wy;
+    m.HA[1][u] = ey;
+    m.HA[2][u] = gy;
   }
   __syncthreads();
   // step B: unary terms, diagonal, residual r0 = b - A x in residual form
-  for (int q = threadIdx.x; q < bp; q += kRThreads) {
-    const int v = q / W, u = q - v * W;
+  for (Walk it(W); it.q < bp; it.next()) {
+    const int q = it.q, u = it.u, v = it.v;
     const size_t gi = (size_t)(rb + v) * P + u;
     const float xq = m.X[q];
     float ws = 0.0f, rs = 0.0f, bs = 0.0f;
@@ -188,25 +195,25 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     }
     const float wx = m.WX[q], ex = m.P[q], wy = m.WY[q], ey = m.S[q];
     const float wxl = u > 0 ? m.WX[q - 1] : 0.0f, exl = u > 0 ? m.P[q - 1] : 0.0f;
-    const float wyu = v > 0 ? m.WY[q - W] : m.H2[u], eyu = v > 0 ? m.S[q - W] : m.H3[u];
+    const float wyu = v > 0 ? m.WY[q - W] : m.WYT[u], eyu = v > 0 ? m.S[q - W] : m.HA[1][u];
     const float d = ws + wn + wx + wxl + wy + wyu;
     const float r = rs + wn * (mn - xq) + wx * ex - wxl * exl + wy * ey - wyu * eyu;
-    m.D[q] = d;
+    const float id = d > 0.0f ? 1.0f / d : 0.0f;
+    m.ID[q] = id;
     m.R[q] = r;
-    acc[0] += r * sdiv(r, d);
+    acc[0] += r * (r * id);
     acc[1] += r * r;
     if (c.tol > 0.0) {
       const float gx = (grad && u < W - 1) ? ld_cnn<DT>(k.cnn[2], gi) : 0.0f;
       const float gxl = (grad && u > 0) ? ld_cnn<DT>(k.cnn[2], gi - 1) : 0.0f;
       const float gy = (grad && rb + v < H - 1) ? ld_cnn<DT>(k.cnn[4], gi) : 0.0f;
-      const float gyu = v > 0 ? ((grad) ? ld_cnn<DT>(k.cnn[4], gi - P) : 0.0f) : m.H4[u];
+      const float gyu = v > 0 ? ((grad) ? ld_cnn<DT>(k.cnn[4], gi - P) : 0.0f) : m.HA[2][u];
       const float b = bs + wn * mn - wx * gx + wxl * gxl - wy * gy + wyu * gyu;
       acc[2] += b * b;
     }
   }
 }
 
-template <int VECDUMMY>
 __global__ void __launch_bounds__(kRThreads, 1)
     k_resident(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns) {
   extern __shared__ float4 dyn_smem[];
@@ -237,26 +244,57 @@ __global__ void __launch_bounds__(kRThreads, 1)
   const int W = k.W, H = k.H;
   const size_t P = k.P;
   const int rb = me.rb, nr = me.re - me.rb, bp = nr * W;
-  const bool has_below = me.re < H;
+  const bool has_above = rb > 0, has_below = me.re < H;
   const Smem m = smem_of(reinterpret_cast<float *>(dyn_smem), h->th, W);
   float *Rg[2] = {k.v[1], k.v[2]}, *Sg[2] = {k.v[3], k.v[4]}, *Wg[2] = {k.v[5], k.v[6]};
+  float *IDg = k.diag;  // the fused kernels keep 1/diag in the diag plane
   const bool active = s_seg.active != 0;
   const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step;
   int parity = 0;
   bool alive = true;
 
-  for (int q = tid; q < bp; q += kRThreads) {
-    const int v = q / W, u = q - v * W;
-    m.X[q] = __ldcg(k.x + (size_t)(rb + v) * P + u);
-  }
-  __syncthreads();
+  for (Walk it(W); it.q < bp; it.next()) m.X[it.q] = __ldcg(k.x + (size_t)(rb + it.v) * P + it.u);
 
-  // partial sums of a pass -> slot -> barrier -> this keyframe's totals
-  auto end_pass = [&](float acc[kRQ]) -> bool {
+  // Load the halo rows the next pass needs (raw values; the new u of the
+  // rows above / below needs this pass's alpha, beta and is formed there).
+  auto prefetch_halo = [&](int kind, int cb) {
+    if (!active || kind == HK_NONE) return;
+    const size_t ia = (size_t)(rb - 1) * P, ib = (size_t)(rb + nr) * P;
+    for (int u = tid; u < W; u += kRThreads) {
+      if (kind == HK_X) {
+        m.HA[0][u] = has_above ? __ldcg(k.x + ia + u) : 0.0f;
+        m.HA[4][u] = has_below ? __ldcg(k.x + ib + u) : 0.0f;
+      } else {
+        const float *Rc = kind == HK_INIT ? Rg[0] : Rg[cb];
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+        if (has_above) {
+          a0 = __ldcg(Rc + ia + u);
+          a3 = __ldcg(IDg + ia + u);
+          if (kind == HK_ITER) {
+            a1 = __ldcg(Sg[cb] + ia + u);
+            a2 = __ldcg(Wg[cb] + ia + u);
+          }
+        }
+        if (has_below) {
+          b0 = __ldcg(Rc + ib + u);
+          b3 = __ldcg(IDg + ib + u);
+          if (kind == HK_ITER) {
+            b1 = __ldcg(Sg[cb] + ib + u);
+            b2 = __ldcg(Wg[cb] + ib + u);
+          }
+        }
+        m.HA[0][u] = a0; m.HA[1][u] = a1; m.HA[2][u] = a2; m.HA[3][u] = a3;
+        m.HA[4][u] = b0; m.HA[5][u] = b1; m.HA[6][u] = b2; m.HA[7][u] = b3;
+      }
+    }
+  };
+
+  // partial sums -> slot -> barrier -> prefetch next halo + this keyframe's totals
+  auto end_pass = [&](float acc[kRQ], int next_halo, int next_cb) -> bool {
 #pragma unroll
     for (int q = 0; q < kRQ; ++q) {
-      const double dq = warp_sum((double)acc[q]);
-      if (lane == 0) s_red[warp][q] = dq;
+      const float s = warp_sum_f(acc[q]);
+      if (lane == 0) s_red[warp][q] = (double)s;
     }
     __syncthreads();
     double *pslots = slots + (size_t)parity * G * kRQ;
@@ -266,6 +304,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
       pslots[(size_t)blockIdx.x * kRQ + tid] = s;
     }
     if (!grid_sync(h, G, limit_ns)) return false;
+    prefetch_halo(next_halo, next_cb);
     if (warp == 0) {
 #pragma unroll
       for (int q = 0; q < kRQ; ++q) {
@@ -282,12 +321,11 @@ __global__ void __launch_bounds__(kRThreads, 1)
   };
 
   auto scale_partials = [&](float acc[kRQ], int q0, float t) {
-    for (int q = tid; q < bp; q += kRThreads) {
-      const int v = q / W, u = q - v * W;
-      const size_t gi = (size_t)(rb + v) * P + u;
+    for (Walk it(W); it.q < bp; it.next()) {
+      const size_t gi = (size_t)(rb + it.v) * P + it.u;
       const float ms = __ldg(k.mu_s + gi), vs = __ldg(k.var_s + gi);
       if (semi_valid(ms, vs)) {
-        const float xq = m.X[q];
+        const float xq = m.X[it.q];
         const float w = robust_weight(xq - t - ms, vs, c.delta, c.loss);
         acc[q0] += w;
         acc[q0 + 1] += w * (xq - ms);
@@ -299,13 +337,18 @@ __global__ void __launch_bounds__(kRThreads, 1)
     __syncthreads();
   };
 
+  // the first pass is either the scale step or the assembly; both need the
+  // x halo, which is current in global memory at launch
+  prefetch_halo(HK_X, 0);
+  __syncthreads();
+
   bool scale_pending = false;
   for (int gn = 0; gn < n_gn && alive; ++gn) {
     if (do_scale) {
       if (!scale_pending) {
         float acc[kRQ] = {0.0f, 0.0f, 0.0f};
         if (active) scale_partials(acc, 0, (float)s_seg.t);
-        if (!(alive = end_pass(acc))) break;
+        if (!(alive = end_pass(acc, HK_X, 0))) break;
         scale_update(0, 1);
       }
       scale_pending = false;
@@ -322,9 +365,9 @@ __global__ void __launch_bounds__(kRThreads, 1)
           assemble_band<DF_F32>(m, k, rb, nr, t, c, acc);
         __syncthreads();
         publish_edges(m.R, Rg[0], W, nr, rb, P);
-        publish_edges(m.D, k.diag, W, nr, rb, P);
+        publish_edges(m.ID, IDg, W, nr, rb, P);
       }
-      if (!(alive = end_pass(acc))) break;
+      if (!(alive = end_pass(acc, n_pcg > 0 ? HK_INIT : HK_X, 0))) break;
       if (tid == 0) {
         s_seg.gam = s_tot[0];
         s_seg.rr = s_tot[1];
@@ -333,21 +376,21 @@ __global__ void __launch_bounds__(kRThreads, 1)
       }
       __syncthreads();
     }
-    if (n_pcg == 0) continue;
+    if (n_pcg == 0) continue;  // no depth update in this GN iteration
     {  // INIT: w0 = A u0
       float acc[kRQ] = {0.0f, 0.0f, 0.0f};
       if (active && !s_seg.stop) {
         for (int u = tid; u < W; u += kRThreads) {
-          m.H0[u] = rb > 0 ? halo_u<0>(k, Rg[0], nullptr, nullptr, (size_t)(rb - 1) * P + u, 0.f, 0.f) : 0.0f;
-          m.H1[u] = has_below ? halo_u<0>(k, Rg[0], nullptr, nullptr, (size_t)(rb + nr) * P + u, 0.f, 0.f) : 0.0f;
+          m.HA[0][u] = m.HA[0][u] * m.HA[3][u];
+          m.HA[4][u] = m.HA[4][u] * m.HA[7][u];
         }
-        for (int q = tid; q < bp; q += kRThreads) m.U[q] = sdiv(m.R[q], m.D[q]);
+        for (Walk it(W); it.q < bp; it.next()) m.U[it.q] = m.R[it.q] * m.ID[it.q];
         __syncthreads();
         apply_band(m, W, nr, bp, has_below, acc);
         __syncthreads();
         publish_edges(m.Wv, Wg[0], W, nr, rb, P);
       }
-      if (!(alive = end_pass(acc))) break;
+      if (!(alive = end_pass(acc, n_pcg > 1 ? HK_ITER : HK_NONE, 0))) break;
       if (tid == 0 && !s_seg.stop) {
         const double dl = s_tot[1];
         if (s_seg.gam == 0.0 || !(dl > 0.0)) {
@@ -368,10 +411,10 @@ __global__ void __launch_bounds__(kRThreads, 1)
       if (it == n_pcg - 1) {  // FINAL
         const bool fs = do_scale && gn + 1 < n_gn;
         if (run) {
-          for (int q = tid; q < bp; q += kRThreads) {
-            const float d = m.D[q], r = m.R[q];
-            const float ui = sdiv(r, d);
-            const float p = first ? ui : ui + fb * m.P[q];
+          for (Walk w(W); w.q < bp; w.next()) {
+            const int q = w.q;
+            const float id = m.ID[q], r = m.R[q];
+            const float p = first ? r * id : r * id + fb * m.P[q];
             m.X[q] += fa * p;
             const float si = first ? m.Wv[q] : m.Wv[q] + fb * m.S[q];
             const float rn = r - fa * si;
@@ -385,7 +428,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
           publish_edges(m.X, k.x, W, nr, rb, P);
         }
         if (fs && active) scale_partials(acc, 1, (float)s_seg.t);
-        if (!(alive = end_pass(acc))) break;
+        if (!(alive = end_pass(acc, HK_X, 0))) break;
         if (tid == 0 && run) {
           s_seg.iters += 1;
           s_seg.rr = s_tot[0];
@@ -398,28 +441,23 @@ __global__ void __launch_bounds__(kRThreads, 1)
       } else {  // ITER
         if (run) {
           for (int u = tid; u < W; u += kRThreads) {
-            float a = 0.0f, b = 0.0f;
-            if (first) {
-              if (rb > 0) a = halo_u<1>(k, Rg[cb], Sg[cb], Wg[cb], (size_t)(rb - 1) * P + u, fa, fb);
-              if (has_below) b = halo_u<1>(k, Rg[cb], Sg[cb], Wg[cb], (size_t)(rb + nr) * P + u, fa, fb);
-            } else {
-              if (rb > 0) a = halo_u<2>(k, Rg[cb], Sg[cb], Wg[cb], (size_t)(rb - 1) * P + u, fa, fb);
-              if (has_below) b = halo_u<2>(k, Rg[cb], Sg[cb], Wg[cb], (size_t)(rb + nr) * P + u, fa, fb);
-            }
-            m.H0[u] = a;
-            m.H1[u] = b;
+            // r' = r - alpha (w + beta s), u' = r' / diag at the halo rows
+            const float sa = first ? m.HA[2][u] : m.HA[2][u] + fb * m.HA[1][u];
+            m.HA[0][u] = (m.HA[0][u] - fa * sa) * m.HA[3][u];
+            const float sb = first ? m.HA[6][u] : m.HA[6][u] + fb * m.HA[5][u];
+            m.HA[4][u] = (m.HA[4][u] - fa * sb) * m.HA[7][u];
           }
-          for (int q = tid; q < bp; q += kRThreads) {
-            const float d = m.D[q], r = m.R[q];
-            const float ui = sdiv(r, d);
-            const float p = first ? ui : ui + fb * m.P[q];
+          for (Walk w(W); w.q < bp; w.next()) {
+            const int q = w.q;
+            const float id = m.ID[q], r = m.R[q];
+            const float p = first ? r * id : r * id + fb * m.P[q];
             m.X[q] += fa * p;
             m.P[q] = p;
             const float si = first ? m.Wv[q] : m.Wv[q] + fb * m.S[q];
             m.S[q] = si;
             const float rn = r - fa * si;
             m.R[q] = rn;
-            m.U[q] = sdiv(rn, d);
+            m.U[q] = rn * id;
           }
           __syncthreads();
           apply_band(m, W, nr, bp, has_below, acc);
@@ -428,7 +466,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
           publish_edges(m.S, Sg[nb], W, nr, rb, P);
           publish_edges(m.Wv, Wg[nb], W, nr, rb, P);
         }
-        if (!(alive = end_pass(acc))) break;
+        const int next_kind = (it + 1 < n_pcg - 1) ? HK_ITER : HK_NONE;
+        if (!(alive = end_pass(acc, next_kind, nb))) break;
         if (tid == 0 && run) {
           s_seg.iters += 1;
           s_seg.rr = s_tot[2];
@@ -453,10 +492,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
   }
 
   if (alive && active) {
-    for (int q = tid; q < bp; q += kRThreads) {
-      const int v = q / W, u = q - v * W;
-      __stcg(k.x + (size_t)(rb + v) * P + u, m.X[q]);
-    }
+    for (Walk it(W); it.q < bp; it.next())
+      __stcg(k.x + (size_t)(rb + it.v) * P + it.u, m.X[it.q]);
   }
   if (tid == 0) {
     Scalars *sc = k.sc;
@@ -495,7 +532,7 @@ const ResDev &rdev() {
     cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_resident<0>) == cudaSuccess) d.static_smem = (int)fa.sharedSizeBytes;
+    if (cudaFuncGetAttributes(&fa, k_resident) == cudaSuccess) d.static_smem = (int)fa.sharedSizeBytes;
     cudaGetLastError();
     g_rdev[dev] = d;
     g_rdev_init[dev] = true;
@@ -610,12 +647,12 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
 cudaError_t resident_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
                             int n_pcg, unsigned long long limit_ns, cudaStream_t s) {
   PlanHeader *h = static_cast<PlanHeader *>(dplan);
-  cudaError_t e = cudaFuncSetAttribute(k_resident<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        shape.smem);
   if (e != cudaSuccess) return e;
   void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns};
   count_launches(1);
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_resident<0>), dim3(shape.G),
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_resident), dim3(shape.G),
                                      dim3(kRThreads), args, (size_t)shape.smem, s);
 }
 

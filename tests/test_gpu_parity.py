@@ -301,12 +301,18 @@ def test_streaming_tile_shapes(o, mode):
     prm = params(n_gn=3, n_pcg=4, solver=dfl.DF_SOLVER_FUSED)
     xo, to, _ = oracle_solve(o, kf, prm)
     shapes = ([(1, 1, 0), (1, 5, 0), (4, 3, 0), (4, 16, 0), (4, 64, 7), (1, 2, 1)]
-              if mode == dfl.DF_MODE_STREAMING else [(0, 0, 0), (0, 0, 3), (0, 0, 1)])
+              if mode == dfl.DF_MODE_STREAMING else [(0, 0, 0), (0, 0, 40), (0, 0, 9)])
     try:
         for vec, th, cap in shapes:
             dfl.df_set_tuning(mode=mode, vec=vec, tile_rows=th, max_ctas=cap)
             x, t, rep = solve(kf, prm)
             assert_parity(x, t, xo, to, what=f"mode {mode} vec {vec} th {th} cap {cap}")
+        if mode == dfl.DF_MODE_RESIDENT:
+            # one CTA's shared memory cannot hold a 300 x 140 keyframe
+            dfl.df_set_tuning(mode=mode, max_ctas=1)
+            with pytest.raises(dfl.DFError) as e:
+                solve(kf, prm)
+            assert e.value.status == dfl.DF_ENOTSUP
     finally:
         dfl.df_set_tuning()
 
