@@ -151,7 +151,6 @@ __device__ __forceinline__ F<VEC> ldc(const void *base, size_t i) {
 __device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 
-__device__ __forceinline__ float safe_div(float r, float d) { return d > 0.0f ? r / d : 0.0f; }
 
 struct Geo {
   int c0, r0, nrows, col;
@@ -517,6 +516,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   __shared__ double s_acc[kWarps][kMaxSeg][kQ];
   __shared__ double s_tot[kMaxSeg][kQ];
   __shared__ int s_nseg;
+  __shared__ unsigned int s_epoch;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = h->G, nslots = h->nslots, nkf = h->nkf;
@@ -545,6 +545,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       ++n;
     }
     s_nseg = n;
+    s_epoch = 0u;
   }
   __syncthreads();
   const int nseg = s_nseg;
@@ -611,16 +612,14 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int w = 0; w < kWarps; ++w) s += s_acc[w][sg][q];
       pslots[(size_t)(slot0 + sg) * kQ + q] = s;
     }
-    if (!grid_sync(h, G, limit_ns)) return false;
+    if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
     if (warp < nseg) {
       const FusedKf &K = s_kf[warp];
+      double tot[kQ];
+      warp_slot_sum<kQ>(pslots, K.slot_begin, K.slot_end, tot);
+      if (lane == 0) {
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) {
-        double s = 0.0;
-        for (int sl = K.slot_begin + lane; sl < K.slot_end; sl += 32)
-          s += __ldcg(pslots + (size_t)sl * kQ + q);
-        s = warp_sum(s);
-        if (lane == 0) s_tot[warp][q] = s;
+        for (int q = 0; q < kQ; ++q) s_tot[warp][q] = tot[q];
       }
     }
     __syncthreads();

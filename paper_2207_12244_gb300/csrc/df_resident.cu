@@ -217,8 +217,9 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
 __global__ void __launch_bounds__(kRThreads, 1)
     k_resident(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns) {
   extern __shared__ float4 dyn_smem[];
-  __shared__ double s_red[kRWarps][kRQ];
+  __shared__ float s_red[32 * kRQ];
   __shared__ double s_tot[kRQ];
+  __shared__ unsigned int s_epoch;
   __shared__ ResKf s_kf;
   __shared__ ResSeg s_seg;
 
@@ -238,6 +239,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
     s_seg.stop = 0;
     s_seg.iters = 0;
     s_seg.active = (sc->flags & kFlagBadInput) ? 0 : 1;
+    s_epoch = 0u;
   }
   __syncthreads();
   const Planes &k = s_kf.pl;
@@ -257,10 +259,11 @@ __global__ void __launch_bounds__(kRThreads, 1)
 
   // Load the halo rows the next pass needs (raw values; the new u of the
   // rows above / below needs this pass's alpha, beta and is formed there).
-  auto prefetch_halo = [&](int kind, int cb) {
+  // called by threads [t0, kRThreads)
+  auto prefetch_halo = [&](int kind, int cb, int t0 = 32) {
     if (!active || kind == HK_NONE) return;
     const size_t ia = (size_t)(rb - 1) * P, ib = (size_t)(rb + nr) * P;
-    for (int u = tid; u < W; u += kRThreads) {
+    for (int u = tid - t0; u < W; u += kRThreads - t0) {
       if (kind == HK_X) {
         m.HA[0][u] = has_above ? __ldcg(k.x + ia + u) : 0.0f;
         m.HA[4][u] = has_below ? __ldcg(k.x + ib + u) : 0.0f;
@@ -291,29 +294,26 @@ __global__ void __launch_bounds__(kRThreads, 1)
 
   // partial sums -> slot -> barrier -> prefetch next halo + this keyframe's totals
   auto end_pass = [&](float acc[kRQ], int next_halo, int next_cb) -> bool {
-#pragma unroll
-    for (int q = 0; q < kRQ; ++q) {
-      const float s = warp_sum_f(acc[q]);
-      if (lane == 0) s_red[warp][q] = (double)s;
-    }
-    __syncthreads();
     double *pslots = slots + (size_t)parity * G * kRQ;
-    if (tid < kRQ) {
-      double s = 0.0;
-      for (int w = 0; w < kRWarps; ++w) s += s_red[w][tid];
-      pslots[(size_t)blockIdx.x * kRQ + tid] = s;
-    }
-    if (!grid_sync(h, G, limit_ns)) return false;
-    prefetch_halo(next_halo, next_cb);
-    if (warp == 0) {
+    {
+      float a3[kRQ] = {acc[0], acc[1], acc[2]};
+      double cs[kRQ];
+      cta_partial_sum<kRQ>(a3, s_red, cs);
+      if (tid == 0) {
 #pragma unroll
-      for (int q = 0; q < kRQ; ++q) {
-        double s = 0.0;
-        for (int sl = s_kf.cta_begin + lane; sl < s_kf.cta_end; sl += 32)
-          s += __ldcg(pslots + (size_t)sl * kRQ + q);
-        s = warp_sum(s);
-        if (lane == 0) s_tot[q] = s;
+        for (int q = 0; q < kRQ; ++q) pslots[(size_t)blockIdx.x * kRQ + q] = cs[q];
       }
+    }
+    if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
+    if (warp == 0) {
+      double tot[kRQ];
+      warp_slot_sum<kRQ>(pslots, s_kf.cta_begin, s_kf.cta_end, tot);
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < kRQ; ++q) s_tot[q] = tot[q];
+      }
+    } else {
+      prefetch_halo(next_halo, next_cb);
     }
     __syncthreads();
     parity ^= 1;
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
 
   // the first pass is either the scale step or the assembly; both need the
   // x halo, which is current in global memory at launch
-  prefetch_halo(HK_X, 0);
+  prefetch_halo(HK_X, 0, 0);
   __syncthreads();
 
   bool scale_pending = false;
