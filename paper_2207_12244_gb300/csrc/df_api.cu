@@ -90,7 +90,7 @@ Layout layout_of(int W, int H, int dtype) {
   L.sc = off; off += align_up(sizeof(Scalars), 256);
   L.partial = off; off += align_up(sizeof(double) * df::kMaxPartialBlocks * df::kNumQ, 256);
   L.plan = off;
-  L.plan_cap = df::fused_supported() ? align_up(df::fused_plan_bytes(1, df::fused_max_ctas()), 256) : 0;
+  L.plan_cap = df::fused_supported() ? align_up(df::fused_plan_cap_single(), 256) : 0;
   off += L.plan_cap;
   L.total = off;
   return L;

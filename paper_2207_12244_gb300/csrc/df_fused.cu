@@ -69,6 +69,7 @@ struct FusedKf {
   int slot_end;
   int writer_cta;  // the CTA that writes the final scalars back
   int pad;
+  long long inbox0;  // first double of its readers' inboxes (within a parity)
 };
 
 
@@ -605,18 +606,33 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
     __syncthreads();
-    double *pslots = slots + (size_t)parity * nslots * kQ;
+    // Push the CTA's sum for each keyframe into the inbox of every CTA of
+    // that keyframe (one slot per writer), then read only the own inbox
+    // after the barrier: no cache line is read by more than one CTA.
+    double *pbox = slots + (size_t)parity * h->slot_stride;
     if (tid < nseg * kQ) {
       const int sg = tid / kQ, q = tid % kQ;
       double s = 0.0;
       for (int w = 0; w < kWarps; ++w) s += s_acc[w][sg][q];
-      pslots[(size_t)(slot0 + sg) * kQ + q] = s;
+      s_tot[sg][q] = s;  // reused below as the push buffer
+    }
+    __syncthreads();
+    for (int sg = 0; sg < nseg; ++sg) {
+      const FusedKf &K = s_kf[sg];
+      const int nk = K.slot_end - K.slot_begin, l = slot0 + sg - K.slot_begin;
+      double *box = pbox + K.inbox0;
+      for (int j = tid; j < nk; j += kThreads) {
+        double *dst = box + ((size_t)j * nk + l) * kQ;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) __stcg(dst + q, s_tot[sg][q]);
+      }
     }
     if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
     if (warp < nseg) {
       const FusedKf &K = s_kf[warp];
+      const int nk = K.slot_end - K.slot_begin, l = slot0 + warp - K.slot_begin;
       double tot[kQ];
-      warp_slot_sum<kQ>(pslots, K.slot_begin, K.slot_end, tot);
+      warp_slot_sum<kQ>(pbox + K.inbox0 + (size_t)l * nk * kQ, 0, nk, tot);
       if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < kQ; ++q) s_tot[warp][q] = tot[q];
@@ -781,15 +797,21 @@ int streaming_max_ctas() {
   return d.sms * std::max(1, std::min(d.occ[0], d.occ[1]));
 }
 
-size_t streaming_plan_bytes(int nkf, int G) {
-  const int nslots = G + nkf;
+static size_t streaming_bytes(int nkf, int G, size_t inbox) {
   size_t off = align16(sizeof(PlanHeader));
   off += align16(sizeof(int) * (size_t)(G + 1));
   off += align16(sizeof(int) * (size_t)G);
   off += align16(sizeof(int) * (size_t)G);
   off += align16(sizeof(FusedKf) * (size_t)nkf);
-  off += sizeof(double) * 2 * (size_t)nslots * kQ;
+  off += sizeof(double) * 2 * inbox;
   return off;
+}
+
+// Upper bound: the inboxes hold sum over keyframes of (slots)^2 * kQ
+// doubles per parity, at most (G + nkf)^2 * kQ.
+size_t streaming_plan_bytes(int nkf, int G) {
+  const size_t m = (size_t)G + nkf;
+  return streaming_bytes(nkf, G, m * m * kQ);
 }
 
 bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
@@ -869,9 +891,10 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   }
   for (int k = 0; k < n; ++k)
     if (sb[k] < 0) return false;
-  const int nslots = G + n;  // bound used for the allocation
-  if (ns > nslots) return false;
-  out.assign(streaming_plan_bytes(n, G), 0);
+  const int nslots = ns;
+  size_t inbox = 0;
+  for (int k = 0; k < n; ++k) inbox += (size_t)(se[k] - sb[k]) * (se[k] - sb[k]) * kQ;
+  out.assign(streaming_bytes(n, G, inbox), 0);
   char *base = out.data();
   PlanHeader *hd = reinterpret_cast<PlanHeader *>(base);
   size_t off = align16(sizeof(PlanHeader));
@@ -890,13 +913,17 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   hd->G = G;
   hd->ntiles = T;
   hd->nslots = nslots;
+  hd->slot_stride = (long long)inbox;
   hd->vec = vec;
   hd->bytes = (long long)out.size();
   memcpy(base + hd->off_cta_tile, ct.data(), sizeof(int) * (G + 1));
   memcpy(base + hd->off_cta_kf, ck.data(), sizeof(int) * G);
   memcpy(base + hd->off_cta_slot, cs.data(), sizeof(int) * G);
   FusedKf *fk = reinterpret_cast<FusedKf *>(base + hd->off_kf);
+  long long ib = 0;
   for (int k = 0; k < n; ++k) {
+    fk[k].inbox0 = ib;
+    ib += (long long)(se[k] - sb[k]) * (se[k] - sb[k]) * kQ;
     fk[k].pl = *kfs[k];
     fk[k].tile_begin = tb[k];
     fk[k].ntiles = nt[k];
@@ -932,6 +959,11 @@ int fused_max_ctas() { return std::max(streaming_max_ctas(), resident_max_ctas()
 
 size_t fused_plan_bytes(int nkf, int G) {
   return std::max(streaming_plan_bytes(nkf, G), resident_plan_bytes(nkf, G));
+}
+
+size_t fused_plan_cap_single() {
+  return std::max(streaming_plan_bytes(1, streaming_max_ctas()),
+                  resident_plan_bytes(1, resident_max_ctas()));
 }
 
 bool fused_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,

@@ -38,6 +38,9 @@ int fused_max_ctas();
 // Bytes of a launch plan for nkf keyframes and a grid of G CTAs.
 size_t fused_plan_bytes(int nkf, int G);
 
+// Bytes a single keyframe reserves for its own launch plan (either kernel).
+size_t fused_plan_cap_single();
+
 // Host-side plan of one launch (tiles, CTA ranges, reduction slots, barrier
 // words). Returns false if the keyframes cannot share one launch (then
 // split the batch).

@@ -33,7 +33,8 @@ constexpr int kHalo = 9;  // halo arrays of W floats kept in shared memory
 
 struct ResKf {
   Planes pl;
-  int cta_begin, cta_end;  // CTAs (= reduction slots) of this keyframe
+  int cta_begin, cta_end;  // CTAs of this keyframe
+  long long inbox0;        // first double of its CTAs' inboxes (within a parity)
 };
 
 struct ResCta {
@@ -293,21 +294,32 @@ __global__ void __launch_bounds__(kRThreads, 1)
   };
 
   // partial sums -> slot -> barrier -> prefetch next halo + this keyframe's totals
+  // Reductions: every CTA pushes its FP64 partials into the inbox of each
+  // CTA of its keyframe (one slot per writer); after the barrier a CTA adds
+  // its own inbox in slot order. No two CTAs read the same lines, so the
+  // sums cost one uncontended L2 round trip and are identical everywhere.
+  const int nk = s_kf.cta_end - s_kf.cta_begin;
+  const int lk = (int)blockIdx.x - s_kf.cta_begin;
   auto end_pass = [&](float acc[kRQ], int next_halo, int next_cb) -> bool {
-    double *pslots = slots + (size_t)parity * G * kRQ;
+    double *box = slots + (size_t)parity * h->slot_stride + s_kf.inbox0;
     {
       float a3[kRQ] = {acc[0], acc[1], acc[2]};
       double cs[kRQ];
       cta_partial_sum<kRQ>(a3, s_red, cs);
-      if (tid == 0) {
+      if (warp == 0) {
 #pragma unroll
-        for (int q = 0; q < kRQ; ++q) pslots[(size_t)blockIdx.x * kRQ + q] = cs[q];
+        for (int q = 0; q < kRQ; ++q) cs[q] = __shfl_sync(0xffffffffu, cs[q], 0);
+        for (int j = lane; j < nk; j += 32) {
+          double *dst = box + ((size_t)j * nk + lk) * kRQ;
+#pragma unroll
+          for (int q = 0; q < kRQ; ++q) __stcg(dst + q, cs[q]);
+        }
       }
     }
     if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
     if (warp == 0) {
       double tot[kRQ];
-      warp_slot_sum<kRQ>(pslots, s_kf.cta_begin, s_kf.cta_end, tot);
+      warp_slot_sum<kRQ>(box + (size_t)lk * nk * kRQ, 0, nk, tot);
       if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < kRQ; ++q) s_tot[q] = tot[q];
@@ -542,12 +554,25 @@ const ResDev &rdev() {
 
 }  // namespace
 
-size_t resident_plan_bytes(int nkf, int G) {
+// Inbox doubles per parity for keyframes with nk[k] CTAs: sum nk^2 * kRQ.
+static size_t inbox_doubles(const std::vector<int> &nk) {
+  size_t s = 0;
+  for (int n : nk) s += (size_t)n * n * kRQ;
+  return s;
+}
+
+static size_t resident_bytes(int nkf, int G, size_t inbox) {
   size_t off = align16(sizeof(PlanHeader));
   off += align16(sizeof(ResCta) * (size_t)G);
   off += align16(sizeof(ResKf) * (size_t)nkf);
-  off += sizeof(double) * 2 * (size_t)G * kRQ;
+  off += sizeof(double) * 2 * inbox;
+  (void)G;
   return off;
+}
+
+// Upper bound (all G CTAs on one keyframe has the largest inboxes).
+size_t resident_plan_bytes(int nkf, int G) {
+  return resident_bytes(nkf, G, (size_t)G * G * kRQ);
 }
 
 int resident_max_ctas() { return rdev().sms; }
@@ -614,10 +639,18 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
     }
     rk[k].cta_end = cI;
   }
+  {
+    long long ib = 0;
+    for (int k = 0; k < n; ++k) {
+      rk[k].inbox0 = ib;
+      ib += (long long)nb[k] * nb[k] * kRQ;
+    }
+  }
   const int stride = (band_px_max + 3) & ~3;
   const long long smem = (long long)(9LL * stride + (long long)kHalo * Wmax) * 4;
   if (smem > avail) return false;
-  out.assign(resident_plan_bytes(n, G), 0);
+  const size_t inbox = inbox_doubles(nb);
+  out.assign(resident_bytes(n, G, inbox), 0);
   char *base = out.data();
   PlanHeader *hd = reinterpret_cast<PlanHeader *>(base);
   size_t off = align16(sizeof(PlanHeader));
@@ -631,6 +664,7 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
   hd->nkf = n;
   hd->G = G;
   hd->nslots = G;
+  hd->slot_stride = (long long)inbox;
   hd->th = stride;  // shared-memory stride of one band array
   hd->smem_bytes = (int)smem;
   hd->bytes = (long long)out.size();

@@ -20,6 +20,7 @@ struct PlanHeader {
   long long bytes;
   int smem_bytes;  // dynamic shared memory per CTA (resident plans)
   int pad1;
+  long long slot_stride;  // doubles per parity of the reduction slots / inboxes
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
