@@ -69,7 +69,7 @@ struct FusedKf {
   int slot_end;
   int writer_cta;  // the CTA that writes the final scalars back
   int pad;
-  long long inbox0;  // first double of its readers' inboxes (within a parity)
+  long long inbox0;  // first slot of its readers' inboxes (within a parity)
 };
 
 
@@ -514,7 +514,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     k_fused(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns) {
   __shared__ FusedKf s_kf[kMaxSeg];
   __shared__ Seg s_seg[kMaxSeg];
-  __shared__ double s_acc[kWarps][kMaxSeg][kQ];
+  __shared__ ff2 s_acc[kWarps][kMaxSeg][kQ];
+  __shared__ Slot s_push[kMaxSeg];
   __shared__ double s_tot[kMaxSeg][kQ];
   __shared__ int s_nseg;
   __shared__ unsigned int s_epoch;
@@ -526,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int *cta_kf = reinterpret_cast<const int *>(hb + h->off_cta_kf);
   const int *cta_slot = reinterpret_cast<const int *>(hb + h->off_cta_slot);
   const FusedKf *kfs = reinterpret_cast<const FusedKf *>(hb + h->off_kf);
-  double *slots = reinterpret_cast<double *>(reinterpret_cast<char *>(h) + h->off_slots);
+  Slot *slots = reinterpret_cast<Slot *>(reinterpret_cast<char *>(h) + h->off_slots);
   const int cta = blockIdx.x;
   const int tb = cta_tile[cta], te = cta_tile[cta + 1];
   const int slot0 = cta_slot[cta];
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   // One pass over the CTA's tiles, then slots, barrier and per-keyframe sums.
   auto run_pass = [&](int kind, int it, bool final_scale) -> bool {
-    for (int q = tid; q < kWarps * kMaxSeg * kQ; q += kThreads) (&s_acc[0][0][0])[q] = 0.0;
+    for (int q = tid; q < kWarps * kMaxSeg * kQ; q += kThreads) (&s_acc[0][0][0])[q] = ff2{0.0f, 0.0f};
     __syncthreads();
     int seg = 0;
     for (int tile = tb + warp; tile < te; tile += kWarps) {
@@ -601,30 +602,33 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
-        const double dq = (double)warp_sum_f(a[q]);
-        if (lane == 0) s_acc[warp][seg][q] += dq;
+        const ff2 dq = warp_sum_ff(ff2{a[q], 0.0f});
+        if (lane == 0) s_acc[warp][seg][q] = ff_add(s_acc[warp][seg][q], dq);
       }
     }
     __syncthreads();
     // Push the CTA's sum for each keyframe into the inbox of every CTA of
     // that keyframe (one slot per writer), then read only the own inbox
     // after the barrier: no cache line is read by more than one CTA.
-    double *pbox = slots + (size_t)parity * h->slot_stride;
-    if (tid < nseg * kQ) {
-      const int sg = tid / kQ, q = tid % kQ;
-      double s = 0.0;
-      for (int w = 0; w < kWarps; ++w) s += s_acc[w][sg][q];
-      s_tot[sg][q] = s;  // reused below as the push buffer
+    Slot *pbox = slots + (size_t)parity * h->slot_stride;
+    if (tid < nseg * 4) {
+      const int sg = tid >> 2, q = tid & 3;
+      ff2 s = ff2{0.0f, 0.0f};
+      if (q < kQ)
+        for (int w = 0; w < kWarps; ++w) s = ff_add(s, s_acc[w][sg][q]);
+      s_push[sg].v[q] = s;
     }
     __syncthreads();
     for (int sg = 0; sg < nseg; ++sg) {
       const FusedKf &K = s_kf[sg];
       const int nk = K.slot_end - K.slot_begin, l = slot0 + sg - K.slot_begin;
-      double *box = pbox + K.inbox0;
+      const int np = inbox_slots(nk);
+      Slot *box = pbox + K.inbox0;
+      const float4 *src = reinterpret_cast<const float4 *>(&s_push[sg]);
       for (int j = tid; j < nk; j += kThreads) {
-        double *dst = box + ((size_t)j * nk + l) * kQ;
-#pragma unroll
-        for (int q = 0; q < kQ; ++q) __stcg(dst + q, s_tot[sg][q]);
+        float4 *dst = reinterpret_cast<float4 *>(box + (size_t)j * np + l);
+        __stcg(dst, src[0]);
+        __stcg(dst + 1, src[1]);
       }
     }
     if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
@@ -632,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       const FusedKf &K = s_kf[warp];
       const int nk = K.slot_end - K.slot_begin, l = slot0 + warp - K.slot_begin;
       double tot[kQ];
-      warp_slot_sum<kQ>(pbox + K.inbox0 + (size_t)l * nk * kQ, 0, nk, tot);
+      warp_inbox_sum<kQ>(pbox + K.inbox0 + (size_t)l * inbox_slots(nk), nk, tot);
       if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < kQ; ++q) s_tot[warp][q] = tot[q];
@@ -803,15 +807,16 @@ static size_t streaming_bytes(int nkf, int G, size_t inbox) {
   off += align16(sizeof(int) * (size_t)G);
   off += align16(sizeof(int) * (size_t)G);
   off += align16(sizeof(FusedKf) * (size_t)nkf);
-  off += sizeof(double) * 2 * inbox;
+  off = (off + 255) & ~(size_t)255;
+  off += sizeof(Slot) * 2 * inbox;
   return off;
 }
 
-// Upper bound: the inboxes hold sum over keyframes of (slots)^2 * kQ
-// doubles per parity, at most (G + nkf)^2 * kQ.
+// Upper bound: per parity the inboxes hold, for every keyframe with m slots,
+// m inboxes of inbox_slots(m) slots; at most (G + nkf) * inbox_slots(G + nkf).
 size_t streaming_plan_bytes(int nkf, int G) {
-  const size_t m = (size_t)G + nkf;
-  return streaming_bytes(nkf, G, m * m * kQ);
+  const int m = G + nkf;
+  return streaming_bytes(nkf, G, (size_t)m * inbox_slots(m));
 }
 
 bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
@@ -893,7 +898,7 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
     if (sb[k] < 0) return false;
   const int nslots = ns;
   size_t inbox = 0;
-  for (int k = 0; k < n; ++k) inbox += (size_t)(se[k] - sb[k]) * (se[k] - sb[k]) * kQ;
+  for (int k = 0; k < n; ++k) inbox += (size_t)(se[k] - sb[k]) * inbox_slots(se[k] - sb[k]);
   out.assign(streaming_bytes(n, G, inbox), 0);
   char *base = out.data();
   PlanHeader *hd = reinterpret_cast<PlanHeader *>(base);
@@ -906,6 +911,7 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   off += align16(sizeof(int) * (size_t)G);
   hd->off_kf = (long long)off;
   off += align16(sizeof(FusedKf) * (size_t)n);
+  off = (off + 255) & ~(size_t)255;
   hd->off_slots = (long long)off;
   hd->kind = kPlanStreaming;
   hd->debug_skip_cta = tune.debug_skip_cta;
@@ -923,7 +929,7 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   long long ib = 0;
   for (int k = 0; k < n; ++k) {
     fk[k].inbox0 = ib;
-    ib += (long long)(se[k] - sb[k]) * (se[k] - sb[k]) * kQ;
+    ib += (long long)(se[k] - sb[k]) * inbox_slots(se[k] - sb[k]);
     fk[k].pl = *kfs[k];
     fk[k].tile_begin = tb[k];
     fk[k].ntiles = nt[k];

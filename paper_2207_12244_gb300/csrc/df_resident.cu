@@ -34,7 +34,7 @@ constexpr int kHalo = 9;  // halo arrays of W floats kept in shared memory
 struct ResKf {
   Planes pl;
   int cta_begin, cta_end;  // CTAs of this keyframe
-  long long inbox0;        // first double of its CTAs' inboxes (within a parity)
+  long long inbox0;        // first slot of its CTAs' inboxes (within a parity)
 };
 
 struct ResCta {
@@ -218,7 +218,7 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
 __global__ void __launch_bounds__(kRThreads, 1)
     k_resident(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns) {
   extern __shared__ float4 dyn_smem[];
-  __shared__ float s_red[32 * kRQ];
+  __shared__ ff2 s_red[32 * kRQ];
   __shared__ double s_tot[kRQ];
   __shared__ unsigned int s_epoch;
   __shared__ ResKf s_kf;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
   const char *hb = reinterpret_cast<const char *>(h);
   const ResCta *ctas = reinterpret_cast<const ResCta *>(hb + h->off_cta_tile);
   const ResKf *kfs = reinterpret_cast<const ResKf *>(hb + h->off_kf);
-  double *slots = reinterpret_cast<double *>(reinterpret_cast<char *>(h) + h->off_slots);
+  Slot *slots = reinterpret_cast<Slot *>(reinterpret_cast<char *>(h) + h->off_slots);
   const ResCta me = ctas[blockIdx.x];
   if (tid == 0) {
     s_kf = kfs[me.kf];
@@ -301,25 +301,33 @@ __global__ void __launch_bounds__(kRThreads, 1)
   const int nk = s_kf.cta_end - s_kf.cta_begin;
   const int lk = (int)blockIdx.x - s_kf.cta_begin;
   auto end_pass = [&](float acc[kRQ], int next_halo, int next_cb) -> bool {
-    double *box = slots + (size_t)parity * h->slot_stride + s_kf.inbox0;
+    const int np = inbox_slots(nk);
+    Slot *box = slots + (size_t)parity * h->slot_stride + s_kf.inbox0;
     {
-      float a3[kRQ] = {acc[0], acc[1], acc[2]};
-      double cs[kRQ];
+      const float a3[kRQ] = {acc[0], acc[1], acc[2]};
+      ff2 cs[kRQ];
       cta_partial_sum<kRQ>(a3, s_red, cs);
       if (warp == 0) {
-#pragma unroll
-        for (int q = 0; q < kRQ; ++q) cs[q] = __shfl_sync(0xffffffffu, cs[q], 0);
+        float4 lo, hi;
+        lo.x = __shfl_sync(0xffffffffu, cs[0].hi, 0);
+        lo.y = __shfl_sync(0xffffffffu, cs[0].lo, 0);
+        lo.z = __shfl_sync(0xffffffffu, cs[1].hi, 0);
+        lo.w = __shfl_sync(0xffffffffu, cs[1].lo, 0);
+        hi.x = __shfl_sync(0xffffffffu, cs[2].hi, 0);
+        hi.y = __shfl_sync(0xffffffffu, cs[2].lo, 0);
+        hi.z = 0.0f;
+        hi.w = 0.0f;
         for (int j = lane; j < nk; j += 32) {
-          double *dst = box + ((size_t)j * nk + lk) * kRQ;
-#pragma unroll
-          for (int q = 0; q < kRQ; ++q) __stcg(dst + q, cs[q]);
+          float4 *dst = reinterpret_cast<float4 *>(box + (size_t)j * np + lk);
+          __stcg(dst, lo);
+          __stcg(dst + 1, hi);
         }
       }
     }
     if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
     if (warp == 0) {
       double tot[kRQ];
-      warp_slot_sum<kRQ>(box + (size_t)lk * nk * kRQ, 0, nk, tot);
+      warp_inbox_sum<kRQ>(box + (size_t)lk * np, nk, tot);
       if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < kRQ; ++q) s_tot[q] = tot[q];
@@ -554,10 +562,11 @@ const ResDev &rdev() {
 
 }  // namespace
 
-// Inbox doubles per parity for keyframes with nk[k] CTAs: sum nk^2 * kRQ.
-static size_t inbox_doubles(const std::vector<int> &nk) {
+// Inbox slots per parity for keyframes with nk[k] CTAs: each of a
+// keyframe's CTAs has an inbox with one slot per CTA of that keyframe.
+static size_t inbox_total(const std::vector<int> &nk) {
   size_t s = 0;
-  for (int n : nk) s += (size_t)n * n * kRQ;
+  for (int n : nk) s += (size_t)n * inbox_slots(n);
   return s;
 }
 
@@ -565,14 +574,14 @@ static size_t resident_bytes(int nkf, int G, size_t inbox) {
   size_t off = align16(sizeof(PlanHeader));
   off += align16(sizeof(ResCta) * (size_t)G);
   off += align16(sizeof(ResKf) * (size_t)nkf);
-  off += sizeof(double) * 2 * inbox;
-  (void)G;
+  off = (off + 255) & ~(size_t)255;
+  off += sizeof(Slot) * 2 * inbox;
   return off;
 }
 
 // Upper bound (all G CTAs on one keyframe has the largest inboxes).
 size_t resident_plan_bytes(int nkf, int G) {
-  return resident_bytes(nkf, G, (size_t)G * G * kRQ);
+  return resident_bytes(nkf, G, (size_t)G * inbox_slots(G));
 }
 
 int resident_max_ctas() { return rdev().sms; }
@@ -643,13 +652,13 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
     long long ib = 0;
     for (int k = 0; k < n; ++k) {
       rk[k].inbox0 = ib;
-      ib += (long long)nb[k] * nb[k] * kRQ;
+      ib += (long long)nb[k] * inbox_slots(nb[k]);
     }
   }
   const int stride = (band_px_max + 3) & ~3;
   const long long smem = (long long)(9LL * stride + (long long)kHalo * Wmax) * 4;
   if (smem > avail) return false;
-  const size_t inbox = inbox_doubles(nb);
+  const size_t inbox = inbox_total(nb);
   out.assign(resident_bytes(n, G, inbox), 0);
   char *base = out.data();
   PlanHeader *hd = reinterpret_cast<PlanHeader *>(base);
@@ -658,6 +667,7 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
   off += align16(sizeof(ResCta) * (size_t)G);
   hd->off_kf = (long long)off;
   off += align16(sizeof(ResKf) * (size_t)n);
+  off = (off + 255) & ~(size_t)255;
   hd->off_slots = (long long)off;
   hd->kind = kPlanResident;
   hd->debug_skip_cta = tune.debug_skip_cta;

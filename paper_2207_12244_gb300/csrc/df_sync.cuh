@@ -74,54 +74,103 @@ __device__ __forceinline__ bool grid_sync(PlanHeader *h, int G, unsigned long lo
   return s_ok != 0;
 }
 
-// Deterministic FP64 sum of this keyframe's slots [sb, se) (kQ values each)
-// by one warp: every lane issues all its loads before adding, so the whole
-// reduction costs one L2 round trip; lanes add in slot order, then a fixed
-// shuffle tree. Result in lane 0.
-template <int kQ>
-__device__ __forceinline__ void warp_slot_sum(const double *pslots, int sb, int se,
-                                              double (&out)[kQ]) {
-  const int lane = threadIdx.x & 31;
-  constexpr int kU = 8;  // slots per lane loaded at once
-  double acc[kQ];
+// ---- double-float reductions ------------------------------------------------
+//
+// GB300 executes FP64 adds at about 2 per clock per SM, 64x below FP32, so an
+// FP64 shuffle tree over a CTA costs microseconds. The solver's inner
+// products are therefore carried as an unevaluated sum of two floats
+// (hi + lo, about 44 significant bits) from the warp level up, combined by
+// the error-free TwoSum transformation (Knuth / Dekker) in a fixed order, and
+// turned into one double per scalar at the very end. All operations are
+// FP32 adds, so the reduction is deterministic and as cheap as an FP32 one.
+struct ff2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff2 ff_add(ff2 a, ff2 b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return ff2{hi, e - (hi - s)};
+}
+
+__device__ __forceinline__ ff2 ff_shfl_down(ff2 a, int o) {
+  return ff2{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+
+// fixed-order warp tree; result in lane 0
+__device__ __forceinline__ ff2 warp_sum_ff(ff2 a) {
 #pragma unroll
-  for (int q = 0; q < kQ; ++q) acc[q] = 0.0;
-  for (int base = sb; base < se; base += 32 * kU) {
-    double v[kU][kQ];
+  for (int o = 16; o > 0; o >>= 1) a = ff_add(a, ff_shfl_down(a, o));
+  return a;
+}
+
+__device__ __forceinline__ double ff_to_double(ff2 a) { return (double)a.hi + (double)a.lo; }
+
+// Reduction slot: kQ double-float values padded to 32 bytes (kQ <= 4).
+struct alignas(32) Slot {
+  ff2 v[4];
+};
+
+// Slots a reader's inbox holds for n writers: padded to whole warps so that
+// every lane loads whole slots without bounds checks (padding stays zero).
+__host__ __device__ __forceinline__ int inbox_slots(int n) { return (n + 31) & ~31; }
+
+// Sum of one inbox of n writers (slot order, then a fixed warp tree) by one
+// warp: every lane issues all its loads before adding. Result in lane 0.
+template <int kQ>
+__device__ __forceinline__ void warp_inbox_sum(const Slot *box, int n, double (&out)[kQ]) {
+  const int lane = threadIdx.x & 31;
+  const int np = inbox_slots(n);
+  constexpr int kU = 8;
+  ff2 acc[kQ];
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) acc[q] = ff2{0.0f, 0.0f};
+  for (int base = 0; base < np; base += 32 * kU) {
+    float4 v[kU][2];
 #pragma unroll
     for (int j = 0; j < kU; ++j) {
       const int sl = base + lane + 32 * j;
-#pragma unroll
-      for (int q = 0; q < kQ; ++q) v[j][q] = sl < se ? __ldcg(pslots + (size_t)sl * kQ + q) : 0.0;
+      const float4 *p = reinterpret_cast<const float4 *>(box + sl);
+      if (base + 32 * j < np) {
+        v[j][0] = __ldcg(p);
+        v[j][1] = __ldcg(p + 1);
+      } else {
+        v[j][0] = v[j][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
 #pragma unroll
     for (int j = 0; j < kU; ++j) {
+      const ff2 s[4] = {ff2{v[j][0].x, v[j][0].y}, ff2{v[j][0].z, v[j][0].w},
+                        ff2{v[j][1].x, v[j][1].y}, ff2{v[j][1].z, v[j][1].w}};
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) acc[q] += v[j][q];
+      for (int q = 0; q < kQ; ++q) acc[q] = ff_add(acc[q], s[q]);
     }
   }
 #pragma unroll
-  for (int q = 0; q < kQ; ++q) out[q] = warp_sum(acc[q]);
+  for (int q = 0; q < kQ; ++q) out[q] = ff_to_double(warp_sum_ff(acc[q]));
 }
 
-// A CTA's FP32 per-thread partials -> FP64 CTA total (fixed order) in
-// thread 0's 'out'. red must hold 32 * kQ floats.
+// A CTA's FP32 per-thread partials -> double-float CTA total (fixed order),
+// valid in warp 0 lane 0. red must hold 32 * kQ ff2.
 template <int kQ>
-__device__ __forceinline__ void cta_partial_sum(const float (&acc)[kQ], float *red,
-                                                double (&out)[kQ]) {
+__device__ __forceinline__ void cta_partial_sum(const float (&acc)[kQ], ff2 *red,
+                                                ff2 (&out)[kQ]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
 #pragma unroll
   for (int q = 0; q < kQ; ++q) {
-    const float s = warp_sum_f(acc[q]);
+    const ff2 s = warp_sum_ff(ff2{acc[q], 0.0f});
     if (lane == 0) red[warp * kQ + q] = s;
   }
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
-      double x = lane < nwarps ? (double)red[lane * kQ + q] : 0.0;
-      out[q] = warp_sum(x);
+      const ff2 x = lane < nwarps ? red[lane * kQ + q] : ff2{0.0f, 0.0f};
+      out[q] = warp_sum_ff(x);
     }
   }
 }
