@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--mode", choices=["auto", "streaming", "resident"], default="auto",
+                    help="fused kernel (launch shape)")
+    ap.add_argument("--max-ctas", type=int, default=0, help="cap on the fused kernel's grid")
+    ap.add_argument("--vec", type=int, default=0)
+    ap.add_argument("--tile-rows", type=int, default=0)
     return ap.parse_args()
 
 
@@ -266,6 +271,8 @@ def main():
     solver = {"auto": dfl.DF_SOLVER_AUTO, "launches": dfl.DF_SOLVER_LAUNCHES,
               "fused": dfl.DF_SOLVER_FUSED}[args.solver]
     prm = dfl.df_default_params(n_gn=args.n_gn, n_pcg=args.n_pcg, solver=solver)
+    dfl.df_set_tuning(mode={"auto": 0, "streaming": 1, "resident": 2}[args.mode],
+                      vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas)
     stream = torch.cuda.Stream(dev)
     sptr = stream.cuda_stream
     k = dfl.Keyframe(W, H, *cnn_d, stream=sptr)
@@ -377,6 +384,7 @@ def main():
             "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
             "config": {"workload": WORKLOAD, "width": W, "height": H, "frames": F,
                        "n_gn": args.n_gn, "n_pcg": args.n_pcg, "solver": args.solver,
+                       "kernel_mode": args.mode, "max_ctas": args.max_ctas,
                        "parallelism": f"replicas x{ws}",
                        "l2": "flushed between steps (256 MB write)"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
