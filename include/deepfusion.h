@@ -194,6 +194,42 @@ size_t df_memory_in_use(void);
 df_status df_semi_to_log(const float *depth, const float *var_depth, float *mu_semi,
                          float *var_semi, int64_t n, int ptrs_on_device, void *stream);
 
+/* Largest keyframe (in pixels) df_optimise_noalloc accepts: 196608, i.e.
+ * 512 x 384, or four times the 256 x 192 resolution of Section II-A. */
+#define DF_NOALLOC_MAX_PIXELS 196608
+
+/* The per-frame solve of df_optimise for callers that cannot allocate device
+ * memory: code running where cudaMalloc is forbidden or unavailable, such as
+ * inside a CUDA graph being captured by someone else, a real-time loop with a
+ * no-allocation rule, or a host whose device memory is owned by another
+ * allocator. The paper has no counterpart; this is an interface of this
+ * library.
+ *
+ * Arguments: H x W = height x width (at most DF_NOALLOC_MAX_PIXELS pixels),
+ * dense row-major f32 DEVICE buffers owned by the caller: the six network
+ * planes as in df_keyframe_create, the semi-dense planes as in
+ * df_frame_update (both NULL = no semi-dense term), the log-depth x (read as
+ * the warm start, overwritten with the result) and the log scale t (one
+ * device double, read and overwritten). params: as df_optimise (NULL =
+ * defaults; the solver field is ignored: this always runs the per-phase
+ * launch schedule). Inputs are not checked on the device.
+ *
+ * It allocates nothing: its working memory (the solver vectors, FP64 partial
+ * sums and scalars) is one static device array of the library, about 5.6 MB,
+ * that every GPU which loads the library holds until the process exits. All
+ * calls on a device share that array and it keeps the last call's contents,
+ * so calls whose work overlaps on the GPU (other streams, other host
+ * threads) race with each other: serialise them. The first call on each
+ * device looks the array's device address up (cudaGetSymbolAddress); make
+ * that first call before any stream capture. Asynchronous on 'stream'.
+ * Errors: DF_EINVAL (sizes above the limit, NULL pointers, parameters),
+ * DF_ECUDA. */
+df_status df_optimise_noalloc(int32_t width, int32_t height, const float *mu_net,
+                              const float *var_net, const float *gx, const float *var_gx,
+                              const float *gy, const float *var_gy, const float *mu_semi,
+                              const float *var_semi, float *x_inout, double *scale_log_inout,
+                              const df_solve_params *params, void *stream);
+
 /* Launch shape of the fused solver (process-wide; paper counterpart: none,
  * this is how the GB300 kernels are cut). A field of 0 means "choose from
  * the problem size". Keyframes pick up a new setting at their next solve.

@@ -225,6 +225,20 @@ df_status read_report(df_keyframe *kf, cudaStream_t s, df_solve_report *rep) {
 
 namespace df {
 void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+df_status report(df_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+df_status check_solve_params(const df_solve_params *p) { return check_params(p); }
+
+SolveCfg solve_cfg(const df_solve_params *p) { return cfg_of(p); }
 }  // namespace df
 
 extern "C" {

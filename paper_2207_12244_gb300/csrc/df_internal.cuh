@@ -211,6 +211,12 @@ __device__ bool grid_sum_last_block(double (&v)[NQ], double *partial, unsigned i
 // Counts kernel launches (df_kernel_launches); call once per launch.
 void count_launches(unsigned n);
 
+// Shared with the entry points outside df_api.cu: record an error message
+// for df_last_error() and return the status; check / convert solve params.
+df_status report(df_status s, const char *fmt, ...);
+df_status check_solve_params(const df_solve_params *p);
+SolveCfg solve_cfg(const df_solve_params *p);
+
 int launch_grid(int tiles);  // blocks for a grid-stride launch over 32x8 tiles
 
 cudaError_t launch_init_state(const Planes &k, cudaStream_t s);

@@ -96,6 +96,9 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.df_memory_in_use.argtypes = []
     L.df_memory_in_use.restype = C.c_size_t
     L.df_semi_to_log.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, vp]
+    L.df_optimise_noalloc.argtypes = [C.c_int32, C.c_int32] + [vp] * 10 + [
+        C.POINTER(df_solve_params), vp]
+    L.df_optimise_noalloc.restype = C.c_int
     L.df_set_tuning.argtypes = [C.POINTER(df_tuning)]
     L.df_get_tuning.argtypes = [C.POINTER(df_tuning)]
     L.df_set_spin_limit_ns.argtypes = [C.c_uint64]
@@ -300,6 +303,26 @@ def df_semi_to_log(depth, var_depth, mu_out, var_out, stream=None):
     _check(load().df_semi_to_log(_ptr(depth)[0], _ptr(var_depth)[0], _ptr(mu_out)[0],
                                  _ptr(var_out)[0], _numel(depth), on_dev, _stream(stream, depth)),
            "df_semi_to_log")
+
+
+DF_NOALLOC_MAX_PIXELS = 196608
+
+
+def df_optimise_noalloc(width: int, height: int, mu_net, var_net, gx, var_gx, gy, var_gy,
+                        mu_semi, var_semi, x_inout, scale_log_inout,
+                        params: Optional[df_solve_params] = None, stream=None):
+    """The solve without device allocation: every buffer is the caller's
+    (CUDA tensors; scale_log_inout a one-element float64 tensor)."""
+    bufs = [mu_net, var_net, gx, var_gx, gy, var_gy, mu_semi, var_semi, x_inout, scale_log_inout]
+    ptrs = []
+    for b in bufs:
+        p, dev = _ptr(b)
+        if b is not None and not dev:
+            raise ValueError("df_optimise_noalloc takes device buffers only")
+        ptrs.append(p)
+    _check(load().df_optimise_noalloc(int(width), int(height), *ptrs,
+                                      C.byref(params) if params is not None else None,
+                                      _stream(stream, x_inout)), "df_optimise_noalloc")
 
 
 def df_set_tuning(mode: int = 0, vec: int = 0, tile_rows: int = 0, max_ctas: int = 0,
