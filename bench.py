@@ -248,6 +248,7 @@ def main():
 
     from paper_2207_12244_gb300 import _build
     from paper_2207_12244_gb300 import deepfusion as dfl
+    from paper_2207_12244_gb300 import replicas
     from paper_2207_12244_gb300 import synth
 
     if ws > 1:
@@ -263,7 +264,7 @@ def main():
     dfl.load()
 
     W, H, F = args.width, args.height, args.frames
-    kf, mus, vs = synth.make_sequence(W, H, args.seed + 1000 * rank, F)
+    kf, mus, vs = synth.make_sequence(W, H, replicas.rank_seed(args.seed, rank), F)
     cnn_d = [torch.from_numpy(p).to(dev) for p in kf.cnn_planes]
     mus_d = torch.from_numpy(mus).to(dev)
     vs_d = torch.from_numpy(vs).to(dev)
@@ -316,11 +317,7 @@ def main():
             solve_ms.extend(a.elapsed_time(b) for a, b in ev_opt)
     launches = dfl.df_kernel_launches() - launches0
     clocks = clk.summary()
-    total_ms = sum(step_ms)
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = replicas.max_over_ranks(sum(step_ms), device=dev)
     units_per_step = W * H * args.n_gn * args.n_pcg * F
     value = units_per_step * args.steps * ws / (total_ms / 1e3) / 1e6
 
@@ -362,11 +359,7 @@ def main():
             step_host()
             torch.cuda.synchronize()
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        tot = sum(e2e_ms)
-        if ws > 1:
-            tt = torch.tensor([tot], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            tot = float(tt.item())
+        tot = replicas.max_over_ranks(sum(e2e_ms), device=dev)
         e2e = {"value": units_per_step * args.steps * ws / (tot / 1e3) / 1e6, "unit": METRIC,
                "h2d_bytes_per_step": int(sum(p.nbytes for p in kf.cnn_planes) + mus.nbytes + vs.nbytes),
                "d2h_bytes_per_step": int(F * H * W * 4), "ms_per_step": tot / args.steps}
