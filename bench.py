@@ -59,6 +59,15 @@ def parse():
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on the fused kernel's grid")
     ap.add_argument("--vec", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--workload", choices=["sequence", "batch64", "precision", "serving"],
+                    default="sequence",
+                    help="sequence: 640x480 keyframe over 100 frames (default); batch64: 64 "
+                         "keyframes of uneven sizes in one batched solve; precision: one "
+                         "1920x1440 keyframe with reduced-precision network planes")
+    ap.add_argument("--cnn-dtype", choices=["f32", "bf16", "f16"], default="bf16",
+                    help="network-plane storage for --workload precision")
+    ap.add_argument("--rate", type=float, default=600.0, help="serving: frames/s offered")
+    ap.add_argument("--requests", type=int, default=1200, help="serving: frames per run")
     return ap.parse_args()
 
 
@@ -236,6 +245,203 @@ def cpu_baseline(args, kf, mus, vs):
                       f"{args.n_gn}x{args.n_pcg} per frame, warm-started, {el:.1f} s single-thread"}
 
 
+def run_serving(args, ws, rank, dev, torch, dfl, replicas, synth):
+    """32 camera streams (16 at 640x480, 16 at 1280x960), Poisson frame
+    arrivals at --rate frames/s, device-resident keyframes admitted under a
+    40 GB budget, 10 GN x 5 PCG per frame: continuous batching vs one launch
+    per frame, same arrival schedule."""
+    from paper_2207_12244_gb300 import serving
+
+    sizes = [(640, 480)] * 16 + [(1280, 960)] * 16
+    my = replicas.shard(len(sizes), rank, ws)
+    F = 8
+    seqs = [synth.make_sequence(W, H, replicas.rank_seed(args.seed, 0) + 31 * i, n_frames=F)
+            for i, (W, H) in enumerate(sizes) if i in my]
+    frames = [[(torch.from_numpy(m[f]).to(dev), torch.from_numpy(v[f]).to(dev)) for f in range(F)]
+              for _, m, v in seqs]
+    cnn = [[torch.from_numpy(p).to(dev) for p in kf.cnn_planes] for kf, _, _ in seqs]
+    prm = dfl.df_default_params(n_gn=10, n_pcg=5)
+    n_req = max(1, args.requests * len(my) // len(sizes))
+    rate = args.rate * len(my) / len(sizes)
+    t, s = serving.poisson_schedule(n_req, rate, len(my), seed=args.seed + rank)
+    px = np.array([kf.width * kf.height for kf, _, _ in seqs])
+    results = {}
+    for mode in ("batched", "plain"):
+        srv = dfl.df_server_create(memory_budget=40 << 30, max_batch=64, max_inflight=2,
+                                   batching=(mode == "batched"), params=prm)
+        try:
+            sids = [dfl.df_server_open_stream(srv, kf.width, kf.height, *c)
+                    for (kf, _, _), c in zip(seqs, cnn)]
+            # warm-up: one frame per stream
+            ws_t, ws_s = serving.poisson_schedule(len(sids), 1e6, len(sids), seed=1)
+            serving.run(srv, sids, frames, ws_t, np.arange(len(sids)))
+            torch.cuda.synchronize()
+            st = serving.run(srv, sids, frames, t, s)
+        finally:
+            dfl.df_server_destroy(srv)
+        units = float(px[s].sum()) * 50
+        results[mode] = {"p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
+                         "max_ms": st.max_ms, "mean_batch": st.mean_batch,
+                         "frames_per_s": st.throughput_rps,
+                         "mpx_iter_per_s": units / st.wall_s / 1e6, "wall_s": st.wall_s}
+    # job-wide: slowest rank's wall time, everybody's work
+    wall = replicas.max_over_ranks(results["batched"]["wall_s"], device=dev)
+    units_all = replicas.sum_over_ranks(float(px[s].sum()) * 50, device=dev)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": units_all / wall / 1e6, "unit": METRIC, "n_gpus": ws,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
+            "config": {"workload": "serving-32streams-640x480+1280x960-poisson-10x5",
+                       "offered_frames_per_s": args.rate, "frames": args.requests,
+                       "budget_bytes": 40 << 30, "parallelism": f"replicas x{ws}"},
+            "update_latency_ms": {"batched": results["batched"], "plain": results["plain"],
+                                  "what": "arrival (submit) to finished (event seen), host clock"},
+            "e2e": None, "roofline": None, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
+    """Batched / large-keyframe workloads: one solve of all keyframes per step."""
+    if args.workload == "batch64":
+        shapes = synth.batch_shapes(64, replicas.rank_seed(args.seed, rank))
+        dt_name, n_gn, n_pcg = "f32", 10, 3
+        name = "batch64-uneven-10x3-fp32"
+    else:
+        shapes = [(1920, 1440)]
+        dt_name, n_gn, n_pcg = args.cnn_dtype, 10, 3
+        name = f"keyframe-1920x1440-10x3-{dt_name}"
+    code = {"f32": dfl.DF_F32, "bf16": dfl.DF_BF16, "f16": dfl.DF_F16}[dt_name]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dt_name]
+    base = replicas.rank_seed(args.seed, rank)
+    kfs = [synth.make_keyframe(W, H, base + 17 * i) for i, (W, H) in enumerate(shapes)]
+    cnn_d = [[torch.from_numpy(p).to(tdt).to(dev) for p in kf.cnn_planes] for kf in kfs]
+    semi_d = [(torch.from_numpy(kf.mu_s).to(dev), torch.from_numpy(kf.var_s).to(dev)) for kf in kfs]
+    outs = [torch.empty((kf.height, kf.width), dtype=torch.float32, device=dev) for kf in kfs]
+    solver = {"auto": dfl.DF_SOLVER_AUTO, "launches": dfl.DF_SOLVER_LAUNCHES,
+              "fused": dfl.DF_SOLVER_FUSED}[args.solver]
+    prm = dfl.df_default_params(n_gn=n_gn, n_pcg=n_pcg, solver=solver)
+    stream = torch.cuda.Stream(dev)
+    sptr = stream.cuda_stream
+    ks = [dfl.Keyframe(kf.width, kf.height, *c, cnn_dtype=code, stream=sptr)
+          for kf, c in zip(kfs, cnn_d)]
+    handles = [k.handle for k in ks]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def step(record):
+        for k, c, (ms, vs) in zip(ks, cnn_d, semi_d):
+            k.reset(*c, stream=sptr)
+            k.frame_update(ms, vs, stream=sptr)
+        if record:
+            ev[0].record(stream)
+        dfl.df_optimise_batch(handles, prm, stream=sptr)
+        if record:
+            ev[1].record(stream)
+        for k, o in zip(ks, outs):
+            k.fetch_depth(o, stream=sptr)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(False)
+    torch.cuda.synchronize()
+    step_ms, solve_ms = [], []
+    launches0 = dfl.df_kernel_launches()
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                step(True)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            solve_ms.append(ev[0].elapsed_time(ev[1]))
+    launches = dfl.df_kernel_launches() - launches0
+    clocks = clk.summary()
+    total_ms = replicas.max_over_ranks(sum(step_ms), device=dev)
+    px = sum(W * H for W, H in shapes)
+    units = px * n_gn * n_pcg
+    value = units * args.steps * ws / (total_ms / 1e3) / 1e6
+    gn_bytes = ALG_BYTES_PER_GN_PX if code == dfl.DF_F32 else ALG_BYTES_PER_GN_PX - 12
+    alg = px * (n_gn * n_pcg * ALG_BYTES_PER_PCG_PX + n_gn * gn_bytes)
+    peak, peak_kind = peaks()
+    solve_s = statistics.mean(solve_ms) / 1e3
+    achieved = alg / solve_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(f"solve_{args.solver}_{name}"),
+                "peak_kind": peak_kind, "region": "df_optimise_batch (all keyframes, one frame)",
+                "alg_bytes_per_launch": alg}
+    e2e = None
+    if not args.no_e2e:
+        cnn_h = [[torch.from_numpy(p).to(tdt).pin_memory() for p in kf.cnn_planes] for kf in kfs]
+        semi_h = [(torch.from_numpy(kf.mu_s).pin_memory(), torch.from_numpy(kf.var_s).pin_memory())
+                  for kf in kfs]
+        outs_h = [torch.empty((kf.height, kf.width), dtype=torch.float32).pin_memory() for kf in kfs]
+
+        def step_host():
+            for k, c, (ms, vs) in zip(ks, cnn_h, semi_h):
+                k.reset(*c, stream=sptr)
+                k.frame_update(ms, vs, stream=sptr)
+            dfl.df_optimise_batch(handles, prm, stream=sptr)
+            for k, o in zip(ks, outs_h):
+                k.fetch_depth(o, stream=sptr)
+
+        step_host()
+        torch.cuda.synchronize()
+        tms = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_host()
+            torch.cuda.synchronize()
+            tms.append(1e3 * (time.perf_counter() - t0))
+        tot = replicas.max_over_ranks(sum(tms), device=dev)
+        esz = 4 if code == dfl.DF_F32 else 2
+        e2e = {"value": units * args.steps * ws / (tot / 1e3) / 1e6, "unit": METRIC,
+               "h2d_bytes_per_step": int(px * (6 * esz + 8)), "d2h_bytes_per_step": int(px * 4),
+               "ms_per_step": tot / args.steps}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+
+        o = oracle.get()
+        kf = kfs[0]
+        t0 = time.perf_counter()
+        o.optimise(kf, n_gn=n_gn, n_pcg=n_pcg)
+        el = time.perf_counter() - t0
+        cpu = {"value": kf.width * kf.height * n_gn * n_pcg / el / 1e6, "unit": METRIC,
+               "cores": 1, "kind": "oracle",
+               "sample": f"one {kf.width}x{kf.height} keyframe of the workload, {n_gn}x{n_pcg}, "
+                         f"{el:.1f} s single-thread (FP64 on the FP32 inputs)"}
+    for k in ks:
+        k.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
+            "config": {"workload": name, "keyframes": len(shapes), "pixels": px,
+                       "cnn_dtype": dt_name, "n_gn": n_gn, "n_pcg": n_pcg, "solver": args.solver,
+                       "kernel_mode": args.mode, "max_ctas": args.max_ctas,
+                       "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MB write)"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu,
+            "update_latency_ms": {"p50": float(np.percentile(solve_ms, 50)),
+                                  "p99": float(np.percentile(solve_ms, 99)),
+                                  "what": "one batched solve, device time"},
+            "hbm_frac": roofline["frac"],
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -262,6 +468,20 @@ def main():
     if ws > 1:
         dist.barrier()
     dfl.load()
+    dfl.df_set_tuning(mode={"auto": 0, "streaming": 1, "resident": 2}[args.mode],
+                      vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas)
+    if args.workload == "serving":
+        run_serving(args, ws, rank, dev, torch, dfl, replicas, synth)
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    if args.workload != "sequence":
+        run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth)
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     W, H, F = args.width, args.height, args.frames
     kf, mus, vs = synth.make_sequence(W, H, replicas.rank_seed(args.seed, rank), F)

@@ -194,6 +194,70 @@ size_t df_memory_in_use(void);
 df_status df_semi_to_log(const float *depth, const float *var_depth, float *mu_semi,
                          float *var_semi, int64_t n, int ptrs_on_device, void *stream);
 
+/* ---- serving: many camera streams, continuous batching --------------------
+ *
+ * A server keeps one keyframe per camera stream resident on the device
+ * (Section II: the keyframe is re-optimised with every new frame) and
+ * solves the frame updates that callers submit. Streams are admitted
+ * against the memory budget; submitted frames queue per stream; every
+ * df_server_progress call retires the batches that have finished and, in
+ * batching mode, launches ONE batched solve (df_optimise_batch) over every
+ * stream that has a frame waiting and is not already on the GPU. Batches run
+ * on a pool of CUDA streams, so frames that arrive while others are being
+ * solved are admitted at the next call and overlap on the device. With
+ * batching = 0 every frame is solved by its own df_optimise launch in
+ * arrival order (the plain baseline). Not thread-safe: one host thread
+ * drives a server. Paper counterpart: none (a serving layer of this
+ * library). */
+typedef struct df_server df_server;
+
+typedef struct {
+  size_t memory_budget;   /* device bytes for the streams' keyframes; 0 = unlimited */
+  int32_t max_batch;      /* keyframes per batched launch, 1..256 */
+  int32_t max_inflight;   /* launches in flight at once (CUDA streams), 1..16 */
+  int32_t batching;       /* 1: continuous batching; 0: one launch per frame */
+  int32_t pad;
+  df_solve_params params; /* solve of every frame */
+} df_server_config;
+
+/* One finished frame update. Times are host steady-clock nanoseconds. */
+typedef struct {
+  uint64_t tag;          /* the caller's tag from df_server_submit */
+  int32_t stream_id;
+  int32_t status;        /* df_status of the solve */
+  int64_t t_submit_ns;   /* df_server_submit returned */
+  int64_t t_launch_ns;   /* its batch was launched */
+  int64_t t_done_ns;     /* its batch was seen finished */
+  int32_t batch_size;    /* keyframes in its launch */
+  int32_t pad;
+} df_completion;
+
+df_status df_server_create(const df_server_config *cfg, df_server **out);
+/* Waits for all work, releases every stream. NULL-safe. */
+void df_server_destroy(df_server *srv);
+/* Admit a camera stream: create its keyframe from the network planes as
+ * df_keyframe_create does. DF_EBUDGET when the budget cannot hold it. */
+df_status df_server_open_stream(df_server *srv, const df_keyframe_desc *desc,
+                                const void *mu_net, const void *var_net, const void *gx,
+                                const void *var_gx, const void *gy, const void *var_gy,
+                                int ptrs_on_device, int32_t *stream_id);
+/* Release a stream (waits for its pending work); its memory returns to the
+ * budget. */
+df_status df_server_close_stream(df_server *srv, int32_t stream_id);
+/* Queue a frame update (semi-dense log-depth / variance, H x W f32, as
+ * df_frame_update). The buffers must stay valid and unchanged until the
+ * frame's completion has been returned. */
+df_status df_server_submit(df_server *srv, int32_t stream_id, const float *mu_semi,
+                           const float *var_semi, int ptrs_on_device, uint64_t tag);
+/* Non-blocking scheduler step: retire finished launches, start new ones,
+ * write up to 'cap' completions to 'out' and their number to *n_out. */
+df_status df_server_progress(df_server *srv, df_completion *out, int32_t cap, int32_t *n_out);
+/* Frames submitted but not yet returned by df_server_progress. */
+int32_t df_server_pending(const df_server *srv);
+/* The stream's current depth (as df_fetch_depth; synchronises). */
+df_status df_server_fetch_depth(df_server *srv, int32_t stream_id, float *out, int log_space,
+                                int ptr_on_device);
+
 /* Largest keyframe (in pixels) df_optimise_noalloc accepts: 196608, i.e.
  * 512 x 384, or four times the 256 x 192 resolution of Section II-A. */
 #define DF_NOALLOC_MAX_PIXELS 196608

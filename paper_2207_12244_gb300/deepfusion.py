@@ -50,6 +50,18 @@ class df_tuning(C.Structure):
 DF_MODE_AUTO, DF_MODE_STREAMING, DF_MODE_RESIDENT = 0, 1, 2
 
 
+class df_server_config(C.Structure):
+    _fields_ = [("memory_budget", C.c_size_t), ("max_batch", C.c_int32),
+                ("max_inflight", C.c_int32), ("batching", C.c_int32), ("pad", C.c_int32),
+                ("params", df_solve_params)]
+
+
+class df_completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("stream_id", C.c_int32), ("status", C.c_int32),
+                ("t_submit_ns", C.c_int64), ("t_launch_ns", C.c_int64), ("t_done_ns", C.c_int64),
+                ("batch_size", C.c_int32), ("pad", C.c_int32)]
+
+
 class DFError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         self.status = status
@@ -99,6 +111,21 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.df_optimise_noalloc.argtypes = [C.c_int32, C.c_int32] + [vp] * 10 + [
         C.POINTER(df_solve_params), vp]
     L.df_optimise_noalloc.restype = C.c_int
+    L.df_server_create.argtypes = [C.POINTER(df_server_config), C.POINTER(vp)]
+    L.df_server_destroy.argtypes = [vp]
+    L.df_server_destroy.restype = None
+    L.df_server_open_stream.argtypes = [vp, C.POINTER(df_keyframe_desc)] + [vp] * 6 + [
+        C.c_int, C.POINTER(C.c_int32)]
+    L.df_server_close_stream.argtypes = [vp, C.c_int32]
+    L.df_server_submit.argtypes = [vp, C.c_int32, vp, vp, C.c_int, C.c_uint64]
+    L.df_server_progress.argtypes = [vp, C.POINTER(df_completion), C.c_int32,
+                                     C.POINTER(C.c_int32)]
+    L.df_server_pending.argtypes = [vp]
+    L.df_server_pending.restype = C.c_int32
+    L.df_server_fetch_depth.argtypes = [vp, C.c_int32, vp, C.c_int, C.c_int]
+    for name in ("df_server_create", "df_server_open_stream", "df_server_close_stream",
+                 "df_server_submit", "df_server_progress", "df_server_fetch_depth"):
+        getattr(L, name).restype = C.c_int
     L.df_set_tuning.argtypes = [C.POINTER(df_tuning)]
     L.df_get_tuning.argtypes = [C.POINTER(df_tuning)]
     L.df_set_spin_limit_ns.argtypes = [C.c_uint64]
@@ -306,6 +333,59 @@ def df_semi_to_log(depth, var_depth, mu_out, var_out, stream=None):
 
 
 DF_NOALLOC_MAX_PIXELS = 196608
+
+
+def df_server_create(memory_budget: int = 0, max_batch: int = 64, max_inflight: int = 2,
+                     batching: bool = True, params: Optional[df_solve_params] = None):
+    cfg = df_server_config(int(memory_budget), int(max_batch), int(max_inflight),
+                           1 if batching else 0, 0, params or df_default_params())
+    out = C.c_void_p()
+    _check(load().df_server_create(C.byref(cfg), C.byref(out)), "df_server_create")
+    return out
+
+
+def df_server_destroy(srv):
+    load().df_server_destroy(srv)
+
+
+def df_server_open_stream(srv, width, height, mu_net, var_net, gx, var_gx, gy, var_gy,
+                          cnn_dtype: Optional[int] = None) -> int:
+    planes = [mu_net, var_net, gx, var_gx, gy, var_gy]
+    on_dev = _same_side(planes, "df_server_open_stream")
+    dt = _dtype_code(mu_net) if cnn_dtype is None else cnn_dtype
+    desc = df_keyframe_desc(width, height, dt)
+    sid = C.c_int32(-1)
+    _check(load().df_server_open_stream(srv, C.byref(desc), *[_ptr(p)[0] for p in planes],
+                                        on_dev, C.byref(sid)), "df_server_open_stream")
+    return sid.value
+
+
+def df_server_close_stream(srv, sid: int):
+    _check(load().df_server_close_stream(srv, int(sid)), "df_server_close_stream")
+
+
+def df_server_submit(srv, sid: int, mu_semi, var_semi, tag: int):
+    on_dev = _same_side([mu_semi, var_semi], "df_server_submit")
+    _check(load().df_server_submit(srv, int(sid), _ptr(mu_semi)[0], _ptr(var_semi)[0], on_dev,
+                                   int(tag)), "df_server_submit")
+
+
+def df_server_progress(srv, cap: int = 256):
+    buf = (df_completion * cap)()
+    n = C.c_int32(0)
+    _check(load().df_server_progress(srv, buf, cap, C.byref(n)), "df_server_progress")
+    return [buf[i] for i in range(n.value)]
+
+
+def df_server_pending(srv) -> int:
+    return int(load().df_server_pending(srv))
+
+
+def df_server_fetch_depth(srv, sid: int, out, log_space: bool = False):
+    p, dev = _ptr(out)
+    _check(load().df_server_fetch_depth(srv, int(sid), p, int(log_space), int(dev)),
+           "df_server_fetch_depth")
+    return out
 
 
 def df_optimise_noalloc(width: int, height: int, mu_net, var_net, gx, var_gx, gy, var_gy,

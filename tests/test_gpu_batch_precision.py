@@ -1,0 +1,174 @@
+"""Batched uneven keyframes and reduced-precision network planes vs the oracle.
+
+* Batches: several keyframes of different sizes solved by one fused launch
+  (df_optimise_batch) match the oracle keyframe by keyframe, and each
+  result is the one df_optimise gives that keyframe alone (same bar).
+* BF16 / FP16 network planes: against the oracle run on the same rounded
+  inputs the bar is the FP32 one (the arithmetic is identical); against the
+  oracle on the original FP32 inputs the error is the rounding's, stated and
+  bounded.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_parity, create, depth_rel_err, oracle_solve, params, solve, to_dev, \
+    torch_cuda
+from paper_2207_12244_gb300 import deepfusion as dfl
+from paper_2207_12244_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MODES = [dfl.DF_MODE_STREAMING, dfl.DF_MODE_RESIDENT, dfl.DF_MODE_AUTO]
+MODE_IDS = ["streaming", "resident", "auto"]
+
+
+@pytest.fixture(scope="module")
+def o():
+    return oracle.get()
+
+
+@pytest.fixture(params=MODES, ids=MODE_IDS)
+def mode(request):
+    dfl.df_set_tuning(mode=request.param)
+    yield request.param
+    dfl.df_set_tuning()
+
+
+def _fetch(k, kf):
+    torch = torch_cuda()
+    out = torch.empty((kf.height, kf.width), dtype=torch.float32, device="cuda")
+    k.fetch_depth(out, log_space=True)
+    t = k.get_state()
+    return out.double().cpu().numpy(), t
+
+
+def _batch(kfs, prm):
+    ks = [create(kf) for kf in kfs]
+    try:
+        for k, kf in zip(ks, kfs):
+            k.frame_update(to_dev(kf.mu_s), to_dev(kf.var_s))
+        reps = dfl.df_optimise_batch([k.handle for k in ks], prm, report=True)
+        return [_fetch(k, kf) for k, kf in zip(ks, kfs)], reps
+    finally:
+        for k in ks:
+            k.close()
+
+
+SHAPES = [(64, 48), (37, 29), (100, 70), (16, 16), (128, 96), (1, 40), (200, 3)]
+
+
+def test_batch_uneven_matches_oracle_and_alone(o, mode):
+    kfs = [synth.make_keyframe(W, H, 500 + i) for i, (W, H) in enumerate(SHAPES)]
+    prm = params(n_gn=6, n_pcg=4, solver=dfl.DF_SOLVER_FUSED)
+    res, reps = _batch(kfs, prm)
+    for i, (kf, (x, t), rep) in enumerate(zip(kfs, res, reps)):
+        xo, to, ro = oracle_solve(o, kf, prm)
+        assert_parity(x, t, xo, to, what=f"batch item {i} {kf.width}x{kf.height}")
+        assert rep.iters_done == ro.iters_done
+        xa, ta, _ = solve(kf, prm)  # the same keyframe alone
+        assert_parity(x, t, xa, ta, what=f"alone vs batch {i}")
+
+
+def test_many_small_keyframes_share_ctas(o):
+    """More keyframes than a CTA's segment capacity: the streaming plan
+    splits or caps segments, every result still matches."""
+    rng = np.random.default_rng(9)
+    kfs = [synth.make_keyframe(int(rng.integers(8, 40)), int(rng.integers(4, 30)), 700 + i)
+           for i in range(40)]
+    prm = params(n_gn=3, n_pcg=3, solver=dfl.DF_SOLVER_FUSED)
+    try:
+        for m, cap in ((dfl.DF_MODE_STREAMING, 4), (dfl.DF_MODE_STREAMING, 0),
+                       (dfl.DF_MODE_RESIDENT, 0)):
+            dfl.df_set_tuning(mode=m, max_ctas=cap)
+            res, _ = _batch(kfs, prm)
+            for i, (kf, (x, t)) in enumerate(zip(kfs, res)):
+                xo, to, _ = oracle_solve(o, kf, prm)
+                assert_parity(x, t, xo, to, what=f"mode {m} cap {cap} item {i}")
+    finally:
+        dfl.df_set_tuning()
+
+
+def test_batch_with_launch_schedule_and_bad_lists(o):
+    kfs = [synth.make_keyframe(W, H, 800 + i) for i, (W, H) in enumerate(SHAPES[:3])]
+    prm = params(n_gn=4, n_pcg=3, solver=dfl.DF_SOLVER_LAUNCHES)
+    res, _ = _batch(kfs, prm)
+    for kf, (x, t) in zip(kfs, res):
+        xo, to, _ = oracle_solve(o, kf, prm)
+        assert_parity(x, t, xo, to, what="launch batch")
+    k = create(kfs[0])
+    try:
+        with pytest.raises(dfl.DFError) as e:
+            dfl.df_optimise_batch([k.handle, k.handle], prm)
+        assert e.value.status == dfl.DF_EINVAL
+        assert dfl.df_optimise_batch([], prm) is None
+    finally:
+        k.close()
+
+
+def _rounded(kf, torch_dtype):
+    """The network planes rounded to torch_dtype on the CPU (round to nearest
+    even) and a copy of the keyframe whose planes are those values in FP32."""
+    import copy
+
+    torch = torch_cuda()
+    planes = [torch.from_numpy(np.ascontiguousarray(p)).to(torch_dtype) for p in kf.cnn_planes]
+    kr = copy.copy(kf)
+    names = ("mu_n", "var_n", "gx", "var_gx", "gy", "var_gy")
+    for n, p in zip(names, planes):
+        setattr(kr, n, p.float().numpy())
+    return planes, kr
+
+
+@pytest.mark.parametrize("dt", [dfl.DF_BF16, dfl.DF_F16], ids=["bf16", "fp16"])
+@pytest.mark.parametrize("sv", [(dfl.DF_SOLVER_LAUNCHES, 0), (dfl.DF_SOLVER_FUSED, 1),
+                                (dfl.DF_SOLVER_FUSED, 2)], ids=["launches", "streaming", "resident"])
+def test_reduced_precision_network_planes(o, dt, sv):
+    torch = torch_cuda()
+    solver, m = sv
+    kf = synth.make_keyframe(160, 120, 901)
+    td = torch.bfloat16 if dt == dfl.DF_BF16 else torch.float16
+    planes, kr = _rounded(kf, td)
+    prm = params(n_gn=10, n_pcg=3, solver=solver)
+    dfl.df_set_tuning(mode=m)
+    try:
+        k = dfl.Keyframe(kf.width, kf.height, *[p.cuda() for p in planes], cnn_dtype=dt)
+        try:
+            k.frame_update(to_dev(kf.mu_s), to_dev(kf.var_s))
+            k.optimise(prm)
+            x, t = _fetch(k, kf)
+        finally:
+            k.close()
+    finally:
+        dfl.df_set_tuning()
+    # same rounded inputs: the FP32 bar
+    xr, tr, _ = oracle_solve(o, kr, prm)
+    assert_parity(x, t, xr, tr, what="rounded inputs")
+    # original FP32 inputs: the rounding's own error, stated
+    xo, to, _ = oracle_solve(o, kf, prm)
+    e = depth_rel_err(x, xo)
+    bound = 2e-2 if dt == dfl.DF_BF16 else 3e-3
+    print(f"{'bf16' if dt == dfl.DF_BF16 else 'fp16'}: vs FP32-input oracle max {e.max():.3g} "
+          f"mean {e.mean():.3g}, |dt| {abs(t - to):.3g}")
+    assert e.max() < bound and abs(t - to) < bound
+
+
+def test_reduced_precision_host_pointers():
+    """BF16 codes from the host go through the same host-side checks."""
+    torch = torch_cuda()
+    kf = synth.make_keyframe(48, 32, 902)
+    planes = [torch.from_numpy(np.ascontiguousarray(p)).to(torch.bfloat16) for p in kf.cnn_planes]
+    xd = solve(kf, params(), cnn_dtype=dfl.DF_BF16)  # device pointers
+    k = dfl.Keyframe(kf.width, kf.height, *planes, cnn_dtype=dfl.DF_BF16)  # host pointers
+    try:
+        k.frame_update(np.ascontiguousarray(kf.mu_s), np.ascontiguousarray(kf.var_s))
+        k.optimise(params())
+        x, t = _fetch(k, kf)
+    finally:
+        k.close()
+    assert np.array_equal(x, xd[0])
+    bad = [p.clone() for p in planes]
+    bad[1][0, 0] = -1.0
+    with pytest.raises(dfl.DFError) as e:
+        dfl.Keyframe(kf.width, kf.height, *bad, cnn_dtype=dfl.DF_BF16)
+    assert e.value.status == dfl.DF_EINVAL
