@@ -168,6 +168,13 @@ df_status df_keyframe_set_state(df_keyframe *kf, const float *x, double t,
 df_status df_cost(df_keyframe *kf, const df_solve_params *params, void *stream,
                   double *cost_out);
 
+/* The scale estimate of the ablation of Table II (Section III-C, "Scale
+ * Optimisation Evaluation"): after a scale-ambiguous solve (terms =
+ * SEMI | GRAD, scale_step = 0), fit the scale to the network prediction by
+ * least squares in log space: c = mean(mu_n - x), then x += c and t += c
+ * (the semi-dense residuals x - t - mu_s are unchanged). Asynchronous. */
+df_status df_scale_fit_ls(df_keyframe *kf, void *stream);
+
 /* Synchronise 'stream' and return DF_EINVAL if device-side input checks
  * flagged the keyframe, DF_ETIMEOUT if a fused solve gave up, else DF_OK. */
 df_status df_keyframe_check(df_keyframe *kf, void *stream);
@@ -302,6 +309,9 @@ df_status df_optimise_noalloc(int32_t width, int32_t height, const float *mu_net
  *   vec       streaming kernel: pixels per lane along a row, 1 or 4
  *   tile_rows streaming kernel: rows per warp tile (1..64)
  *   max_ctas  cap on the cooperative grid
+ *   gn_per_launch  Gauss-Newton iterations per fused launch (0 = all of
+ *             them in one launch); the solve is split into launches of
+ *             whole GN iterations with the same result
  *   debug_skip_cta  test only: >= 0 makes that CTA of the next fused launches
  *             leave without arriving at its first grid barrier, so the
  *             others' bounded waits run out (DF_ETIMEOUT); -1 = off. */
@@ -310,11 +320,24 @@ typedef struct {
   int32_t vec;
   int32_t tile_rows;
   int32_t max_ctas;
+  int32_t gn_per_launch;
   int32_t debug_skip_cta;
 } df_tuning;
 
 df_status df_set_tuning(const df_tuning *t); /* NULL restores the defaults */
 df_status df_get_tuning(df_tuning *t);
+
+/* Autotuner (paper counterpart: none): time the fused solver's candidate
+ * launch shapes -- the resident kernel with all GN iterations in one launch
+ * or one per launch, the streaming kernel with 1 or 4 pixels per lane and
+ * 2..32 rows per warp tile -- on these keyframes (solved together as by
+ * df_optimise_batch, or alone when n = 1) with 'params'. Every trial starts
+ * from the keyframes' current state, which is restored at the end. The
+ * fastest shape becomes the current tuning (df_set_tuning) and is written to
+ * *best, its time per solve to *best_ms. Synchronises; allocates a snapshot
+ * of the keyframes' log-depth for the duration of the call. */
+df_status df_autotune(df_keyframe *const *kfs, int32_t n, const df_solve_params *params,
+                      void *stream, df_tuning *best, float *best_ms);
 
 /* Upper bound on every device-side wait of the fused solver (grid
  * barriers), in nanoseconds; a wait that runs out abandons the solve and is

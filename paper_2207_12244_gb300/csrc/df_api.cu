@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -257,6 +258,8 @@ df_status df_set_tuning(const df_tuning *t) {
     n.vec = t->vec;
     n.tile_rows = t->tile_rows;
     n.max_ctas = t->max_ctas;
+    if (t->gn_per_launch < 0) return fail(DF_EINVAL, "gn_per_launch must be >= 0");
+    n.gn_per_launch = t->gn_per_launch;
     n.debug_skip_cta = t->debug_skip_cta;
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -271,6 +274,7 @@ df_status df_get_tuning(df_tuning *t) {
   t->vec = g_tune.vec;
   t->tile_rows = g_tune.tile_rows;
   t->max_ctas = g_tune.max_ctas;
+  t->gn_per_launch = g_tune.gn_per_launch;
   t->debug_skip_cta = g_tune.debug_skip_cta;
   return DF_OK;
 }
@@ -428,7 +432,8 @@ static df::FusedTuning current_tuning() {
 
 static bool same_tuning(const df::FusedTuning &a, const df::FusedTuning &b) {
   return a.mode == b.mode && a.vec == b.vec && a.tile_rows == b.tile_rows &&
-         a.max_ctas == b.max_ctas && a.debug_skip_cta == b.debug_skip_cta;
+         a.max_ctas == b.max_ctas && a.debug_skip_cta == b.debug_skip_cta;  // gn_per_launch
+                                                                            // does not shape plans
 }
 
 static int pick_solver(int requested) {
@@ -453,7 +458,13 @@ static df_status fused_one(df_keyframe *kf, const SolveCfg &c, int n_gn, int n_p
     kf->plan_shape = shape;
     kf->plan_tune = tune;
   }
-  DF_CUDA(df::fused_launch(kf->plan, kf->plan_shape, c, n_gn, n_pcg, g_spin_limit_ns.load(), s));
+  const int chunk = tune.gn_per_launch > 0 ? tune.gn_per_launch : (n_gn > 0 ? n_gn : 1);
+  for (int g0 = 0, first = 1; g0 < n_gn || first; g0 += chunk, first = 0) {
+    const int m = std::min(chunk, n_gn - g0);
+    DF_CUDA(df::fused_launch(kf->plan, kf->plan_shape, c, m < 0 ? 0 : m, n_pcg,
+                             g_spin_limit_ns.load(), s, first));
+    if (n_gn == 0) break;
+  }
   return DF_OK;
 }
 
@@ -481,7 +492,13 @@ static df_status fused_many(df_keyframe *const *kfs, int n, const SolveCfg &c, i
   void *dplan = nullptr;
   DF_CUDA(cudaMallocAsync(&dplan, host.size(), s));
   cudaError_t e = cudaMemcpyAsync(dplan, host.data(), host.size(), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = df::fused_launch(dplan, shape, c, n_gn, n_pcg, g_spin_limit_ns.load(), s);
+  const df::FusedTuning tune = current_tuning();
+  const int chunk = tune.gn_per_launch > 0 ? tune.gn_per_launch : (n_gn > 0 ? n_gn : 1);
+  for (int g0 = 0, first = 1; e == cudaSuccess && (g0 < n_gn || first); g0 += chunk, first = 0) {
+    const int m = std::min(chunk, n_gn - g0);
+    e = df::fused_launch(dplan, shape, c, m < 0 ? 0 : m, n_pcg, g_spin_limit_ns.load(), s, first);
+    if (n_gn == 0) break;
+  }
   cudaError_t e2 = cudaFreeAsync(dplan, s);
   if (e != cudaSuccess) return cuda_fail(e, "fused batch launch");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
@@ -615,6 +632,14 @@ df_status df_cost(df_keyframe *kf, const df_solve_params *params, void *stream, 
   DF_CUDA(df::launch_cost(kf->planes, cfg_of(&p), s));
   DF_CUDA(cudaMemcpyAsync(cost_out, &kf->planes.sc->cost, sizeof(double), cudaMemcpyDeviceToHost, s));
   DF_CUDA(cudaStreamSynchronize(s));
+  return DF_OK;
+}
+
+df_status df_scale_fit_ls(df_keyframe *kf, void *stream) {
+  if (!kf) return fail(DF_EINVAL, "keyframe is NULL");
+  DeviceGuard g(kf->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DF_CUDA(df::launch_ls_scale_fit(kf->planes, s));
   return DF_OK;
 }
 

@@ -1,0 +1,113 @@
+// Autotuner of the fused solver's launch shape (df_autotune): times
+// candidate shapes on the caller's own keyframes, each trial starting from
+// the same state, and keeps the fastest.
+#include <vector>
+
+#include "df_internal.cuh"
+
+namespace {
+
+struct Snapshot {
+  std::vector<float *> x;
+  std::vector<double> t;
+};
+
+}  // namespace
+
+extern "C" df_status df_autotune(df_keyframe *const *kfs, int32_t n, const df_solve_params *params,
+                                 void *stream, df_tuning *best, float *best_ms) {
+  if (!kfs || n < 1 || !best) return df::report(DF_EINVAL, "bad arguments");
+  df_solve_params p;
+  if (params) {
+    p = *params;
+  } else {
+    df_default_params(&p);
+  }
+  p.solver = DF_SOLVER_FUSED;
+  df_status st = df::check_solve_params(&p);
+  if (st != DF_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  df_tuning saved;
+  df_get_tuning(&saved);
+  // snapshot every keyframe's (x, t)
+  Snapshot snap;
+  for (int32_t j = 0; j < n; ++j) {
+    df_keyframe_desc d;
+    size_t bytes = 0;
+    st = df_keyframe_info(kfs[j], &d, &bytes);
+    if (st != DF_OK) return st;
+    float *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, (size_t)d.width * d.height * sizeof(float));
+    if (e != cudaSuccess) {
+      for (float *q : snap.x) cudaFree(q);
+      return df::report(DF_ENOMEM, "autotune snapshot: %s", cudaGetErrorString(e));
+    }
+    snap.x.push_back(buf);
+    double t = 0.0;
+    st = df_keyframe_get_state(kfs[j], buf, &t, 0, stream);
+    if (st != DF_OK) break;
+    snap.t.push_back(t);
+  }
+  auto restore = [&]() -> df_status {
+    for (int32_t j = 0; j < n; ++j) {
+      df_status r = df_keyframe_set_state(kfs[j], snap.x[j], snap.t[j], 1, stream);
+      if (r != DF_OK) return r;
+    }
+    return DF_OK;
+  };
+  auto solve = [&]() -> df_status {
+    return n == 1 ? df_optimise(kfs[0], &p, stream, nullptr)
+                  : df_optimise_batch(kfs, n, &p, stream, nullptr);
+  };
+  std::vector<df_tuning> cand;
+  for (int g : {0, 1}) cand.push_back(df_tuning{2, 0, 0, 0, g, -1});
+  for (int vec : {1, 4})
+    for (int th : {2, 4, 8, 16, 32}) cand.push_back(df_tuning{1, vec, th, 0, 0, -1});
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_t = 0.0f;
+  bool have = false;
+  if (st == DF_OK) {
+    for (const df_tuning &c : cand) {
+      df_set_tuning(&c);
+      if (restore() != DF_OK) continue;
+      if (solve() != DF_OK) {  // e.g. the resident kernel cannot hold these keyframes
+        cudaStreamSynchronize(s);
+        continue;
+      }
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        restore();
+        cudaEventRecord(e0, s);
+        if (solve() != DF_OK) break;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < tmin) tmin = ms;
+      }
+      if (tmin < 1e29f && (!have || tmin < best_t)) {
+        best_t = tmin;
+        *best = c;
+        have = true;
+      }
+    }
+  }
+  df_status rs = restore();
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (float *q : snap.x) cudaFree(q);
+  if (st != DF_OK) {
+    df_set_tuning(&saved);
+    return st;
+  }
+  if (!have) {
+    df_set_tuning(&saved);
+    return df::report(DF_ENOTSUP, "no launch shape could solve these keyframes");
+  }
+  df_set_tuning(best);
+  if (best_ms) *best_ms = best_t;
+  return rs;
+}

@@ -511,7 +511,8 @@ struct Seg {
 
 template <int VEC>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_fused(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns) {
+    k_fused(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns,
+            int first) {
   __shared__ FusedKf s_kf[kMaxSeg];
   __shared__ Seg s_seg[kMaxSeg];
   __shared__ ff2 s_acc[kWarps][kMaxSeg][kQ];
@@ -542,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       s.gam = s.alpha = s.beta = s.bb = 0.0;
       s.rr = sc->rr;
       s.stop = 0;
-      s.iters = 0;
+      s.iters = first ? 0 : sc->iters;
       s.active = (sc->flags & kFlagBadInput) ? 0 : 1;
       ++n;
     }
@@ -947,10 +948,10 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
 }
 
 cudaError_t streaming_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
-                             int n_pcg, unsigned long long limit_ns, cudaStream_t s) {
+                             int n_pcg, unsigned long long limit_ns, cudaStream_t s, int first) {
   PlanHeader *h = static_cast<PlanHeader *>(dplan);
   const int G = shape.G, vec = shape.vec;
-  void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns};
+  void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns, &first};
   count_launches(1);
   const void *fn = vec == 4 ? reinterpret_cast<const void *>(k_fused<4>)
                             : reinterpret_cast<const void *>(k_fused<1>);
@@ -980,9 +981,10 @@ bool fused_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
 }
 
 cudaError_t fused_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
-                         int n_pcg, unsigned long long limit_ns, cudaStream_t s) {
-  if (shape.kind == kPlanResident) return resident_launch(dplan, shape, c, n_gn, n_pcg, limit_ns, s);
-  return streaming_launch(dplan, shape, c, n_gn, n_pcg, limit_ns, s);
+                         int n_pcg, unsigned long long limit_ns, cudaStream_t s, int first) {
+  if (shape.kind == kPlanResident)
+    return resident_launch(dplan, shape, c, n_gn, n_pcg, limit_ns, s, first);
+  return streaming_launch(dplan, shape, c, n_gn, n_pcg, limit_ns, s, first);
 }
 
 }  // namespace df

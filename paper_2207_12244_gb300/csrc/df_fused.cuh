@@ -18,6 +18,7 @@ struct FusedTuning {
   int vec = 0;           // streaming: pixels per lane along a row (1 or 4)
   int tile_rows = 0;     // streaming: rows per warp tile
   int max_ctas = 0;      // cap on the cooperative grid
+  int gn_per_launch = 0; // GN iterations per launch (0: all)
   int debug_skip_cta = -1;  // test hook, see df_tuning
 };
 
@@ -49,8 +50,10 @@ bool fused_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
 
 // Launch on stream s with a plan already copied to device memory 'dplan'.
 // limit_ns bounds every grid-barrier wait.
+// 'first' = 1 for the first launch of a solve (the reported PCG iteration
+// count starts at 0), 0 for later launches of the same solve.
 cudaError_t fused_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
-                         int n_pcg, unsigned long long limit_ns, cudaStream_t s);
+                         int n_pcg, unsigned long long limit_ns, cudaStream_t s, int first = 1);
 
 // The two kernels behind fused_*: streaming (df_fused.cu) and resident
 // (df_resident.cu).
@@ -60,12 +63,12 @@ size_t streaming_plan_bytes(int nkf, int G);
 bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
                           std::vector<char> &out, LaunchShape &shape);
 cudaError_t streaming_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
-                             int n_pcg, unsigned long long limit_ns, cudaStream_t s);
+                             int n_pcg, unsigned long long limit_ns, cudaStream_t s, int first);
 int resident_max_ctas();
 size_t resident_plan_bytes(int nkf, int G);
 bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
                          std::vector<char> &out, LaunchShape &shape);
 cudaError_t resident_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
-                            int n_pcg, unsigned long long limit_ns, cudaStream_t s);
+                            int n_pcg, unsigned long long limit_ns, cudaStream_t s, int first);
 
 }  // namespace df

@@ -227,6 +227,7 @@ cudaError_t launch_fetch(const Planes &k, float *out, int log_space, cudaStream_
 cudaError_t launch_cost(const Planes &k, const SolveCfg &c, cudaStream_t s);
 cudaError_t launch_set_x(const Planes &k, const float *x_dense, cudaStream_t s);
 cudaError_t launch_set_scale(const Planes &k, double t, cudaStream_t s);
+cudaError_t launch_ls_scale_fit(const Planes &k, cudaStream_t s);
 cudaError_t launch_semi_to_log(const float *d, const float *vd, float *mu, float *var,
                                int64_t n, cudaStream_t s);
 

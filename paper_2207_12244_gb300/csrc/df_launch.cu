@@ -287,6 +287,38 @@ __global__ void k_set_x(Planes k, const float *xd) {
 
 __global__ void k_set_scale(Scalars *sc, double t) { sc->t = t; }
 
+// ---- Table II's least-squares scale fit (Section III-C) -------------------
+// After a scale-ambiguous solve, the log offset c minimising
+// sum_i (x_i + c - mu_n,i)^2 is mean(mu_n - x); x += c and t += c keep the
+// semi-dense residuals x - t - mu_s unchanged.
+template <int DT>
+__global__ void k_lsfit_sum(Planes k) {
+  TileIter it(k.W, k.H);
+  float acc = 0.0f;
+  for (int tile = blockIdx.x; tile < it.ntiles; tile += gridDim.x) {
+    int u, v;
+    if (!pixel_of(tile, it.tiles_x, k.W, k.H, u, v)) continue;
+    const size_t i = (size_t)v * k.P + u;
+    acc += ld_cnn<DT>(k.cnn[0], i) - k.x[i];
+  }
+  double a[1] = {(double)acc}, out[1];
+  if (grid_sum_last_block<1>(a, k.partial, &k.sc->count, out)) {
+    const double c = out[0] / ((double)k.W * (double)k.H);
+    k.sc->gamma = c;  // the shift, read by k_lsfit_shift
+    k.sc->t += c;
+  }
+}
+
+__global__ void k_lsfit_shift(Planes k) {
+  TileIter it(k.W, k.H);
+  const float c = (float)k.sc->gamma;
+  for (int tile = blockIdx.x; tile < it.ntiles; tile += gridDim.x) {
+    int u, v;
+    if (!pixel_of(tile, it.tiles_x, k.W, k.H, u, v)) continue;
+    k.x[(size_t)v * k.P + u] += c;
+  }
+}
+
 // ---- cost c(x, t) of Eq. 5 with the robust loss (FP64) --------------------
 template <int DT>
 __global__ void k_cost(Planes k, SolveCfg c) {
@@ -429,6 +461,19 @@ cudaError_t launch_set_x(const Planes &k, const float *xd, cudaStream_t s) {
 cudaError_t launch_set_scale(const Planes &k, double t, cudaStream_t s) {
   count_launches(1);
   k_set_scale<<<1, 1, 0, s>>>(k.sc, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ls_scale_fit(const Planes &k, cudaStream_t s) {
+  count_launches(2);
+  const dim3 blk(TX, TY), grd(launch_grid(tiles_of(k)));
+  if (k.dtype == DF_BF16)
+    k_lsfit_sum<DF_BF16><<<grd, blk, 0, s>>>(k);
+  else if (k.dtype == DF_F16)
+    k_lsfit_sum<DF_F16><<<grd, blk, 0, s>>>(k);
+  else
+    k_lsfit_sum<DF_F32><<<grd, blk, 0, s>>>(k);
+  k_lsfit_shift<<<grd, blk, 0, s>>>(k);
   return cudaGetLastError();
 }
 

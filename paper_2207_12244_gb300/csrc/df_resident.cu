@@ -216,7 +216,8 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
 }
 
 __global__ void __launch_bounds__(kRThreads, 1)
-    k_resident(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns) {
+    k_resident(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns,
+               int first) {
   extern __shared__ float4 dyn_smem[];
   __shared__ ff2 s_red[32 * kRQ];
   __shared__ double s_tot[kRQ];
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
     s_seg.gam = s_seg.alpha = s_seg.beta = s_seg.bb = 0.0;
     s_seg.rr = sc->rr;
     s_seg.stop = 0;
-    s_seg.iters = 0;
+    s_seg.iters = first ? 0 : sc->iters;
     s_seg.active = (sc->flags & kFlagBadInput) ? 0 : 1;
     s_epoch = 0u;
   }
@@ -689,12 +690,12 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
 }
 
 cudaError_t resident_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
-                            int n_pcg, unsigned long long limit_ns, cudaStream_t s) {
+                            int n_pcg, unsigned long long limit_ns, cudaStream_t s, int first) {
   PlanHeader *h = static_cast<PlanHeader *>(dplan);
   cudaError_t e = cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        shape.smem);
   if (e != cudaSuccess) return e;
-  void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns};
+  void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns, &first};
   count_launches(1);
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_resident), dim3(shape.G),
                                      dim3(kRThreads), args, (size_t)shape.smem, s);

@@ -44,7 +44,8 @@ class df_solve_report(C.Structure):
 
 class df_tuning(C.Structure):
     _fields_ = [("mode", C.c_int32), ("vec", C.c_int32), ("tile_rows", C.c_int32),
-                ("max_ctas", C.c_int32), ("debug_skip_cta", C.c_int32)]
+                ("max_ctas", C.c_int32), ("gn_per_launch", C.c_int32),
+                ("debug_skip_cta", C.c_int32)]
 
 
 DF_MODE_AUTO, DF_MODE_STREAMING, DF_MODE_RESIDENT = 0, 1, 2
@@ -99,6 +100,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.df_keyframe_set_state.argtypes = [vp, vp, C.c_double, C.c_int, vp]
     L.df_cost.argtypes = [vp, C.POINTER(df_solve_params), vp, C.POINTER(C.c_double)]
     L.df_keyframe_check.argtypes = [vp, vp]
+    L.df_scale_fit_ls.argtypes = [vp, vp]
+    L.df_scale_fit_ls.restype = C.c_int
     L.df_keyframe_info.argtypes = [vp, C.POINTER(df_keyframe_desc), C.POINTER(C.c_size_t)]
     L.df_keyframe_destroy.argtypes = [vp]
     L.df_keyframe_destroy.restype = None
@@ -126,6 +129,9 @@ def load(path: Optional[str] = None) -> C.CDLL:
     for name in ("df_server_create", "df_server_open_stream", "df_server_close_stream",
                  "df_server_submit", "df_server_progress", "df_server_fetch_depth"):
         getattr(L, name).restype = C.c_int
+    L.df_autotune.argtypes = [C.POINTER(vp), C.c_int32, C.POINTER(df_solve_params), vp,
+                              C.POINTER(df_tuning), C.POINTER(C.c_float)]
+    L.df_autotune.restype = C.c_int
     L.df_set_tuning.argtypes = [C.POINTER(df_tuning)]
     L.df_get_tuning.argtypes = [C.POINTER(df_tuning)]
     L.df_set_spin_limit_ns.argtypes = [C.c_uint64]
@@ -298,6 +304,10 @@ def df_cost(kf, params: Optional[df_solve_params] = None, stream=None) -> float:
     return c.value
 
 
+def df_scale_fit_ls(kf, stream=None):
+    _check(load().df_scale_fit_ls(kf, _stream(stream)), "df_scale_fit_ls")
+
+
 def df_keyframe_check(kf, stream=None):
     _check(load().df_keyframe_check(kf, _stream(stream)), "df_keyframe_check")
 
@@ -406,9 +416,21 @@ def df_optimise_noalloc(width: int, height: int, mu_net, var_net, gx, var_gx, gy
 
 
 def df_set_tuning(mode: int = 0, vec: int = 0, tile_rows: int = 0, max_ctas: int = 0,
-                  debug_skip_cta: int = -1):
-    t = df_tuning(mode, vec, tile_rows, max_ctas, debug_skip_cta)
+                  debug_skip_cta: int = -1, gn_per_launch: int = 0):
+    t = df_tuning(mode, vec, tile_rows, max_ctas, gn_per_launch, debug_skip_cta)
     _check(load().df_set_tuning(C.byref(t)), "df_set_tuning")
+
+
+def df_autotune(kfs: Sequence, params: Optional[df_solve_params] = None, stream=None):
+    """Time the fused solver's launch shapes on these keyframes; the fastest
+    becomes current. Returns (df_tuning, ms per solve)."""
+    n = len(kfs)
+    arr = (C.c_void_p * max(n, 1))(*[k.value if isinstance(k, C.c_void_p) else k for k in kfs])
+    best = df_tuning()
+    ms = C.c_float(0.0)
+    _check(load().df_autotune(arr, n, C.byref(params) if params is not None else None,
+                              _stream(stream), C.byref(best), C.byref(ms)), "df_autotune")
+    return best, ms.value
 
 
 def df_get_tuning() -> df_tuning:
@@ -469,6 +491,9 @@ class Keyframe:
 
     def check(self, stream=None):
         df_keyframe_check(self.handle, stream)
+
+    def scale_fit_ls(self, stream=None):
+        df_scale_fit_ls(self.handle, stream)
 
     def close(self):
         if self.handle is not None and self.handle.value:

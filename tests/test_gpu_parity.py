@@ -345,3 +345,133 @@ def test_barrier_wait_times_out_cleanly(mode):
         dfl.df_set_spin_limit_ns(2_000_000_000)
     again = solve(kf, prm)
     assert np.array_equal(again[0], ref[0]) and again[1] == ref[1]
+
+
+def test_table2_scale_ambiguous_solve_then_ls_fit(o, solver):
+    """Table II variant: semi + gradient terms with t fixed, then the
+    least-squares scale fit to the network log-depth."""
+    torch = torch_cuda()
+    kf = synth.make_keyframe(120, 90, 24)
+    prm = params(n_gn=6, n_pcg=6, terms=dfl.DF_TERM_SEMI | dfl.DF_TERM_GRAD, scale_step=0,
+                 solver=solver)
+    k = create(kf)
+    try:
+        k.frame_update(to_dev(kf.mu_s), to_dev(kf.var_s))
+        k.optimise(prm)
+        k.scale_fit_ls()
+        out = torch.empty((kf.height, kf.width), dtype=torch.float32, device="cuda")
+        k.fetch_depth(out, log_space=True)
+        t = k.get_state()
+        x = out.double().cpu().numpy()
+    finally:
+        k.close()
+    xo, to, _ = oracle_solve(o, kf, prm)
+    xo, to = o.ls_scale_fit(kf, xo, to)
+    assert_parity(x, t, xo, to, what="table II")
+    assert abs(np.mean(kf.mu_n.astype(np.float64) - x)) < 1e-5  # the fit's defining property
+
+
+@pytest.mark.parametrize("mode", [dfl.DF_MODE_STREAMING, dfl.DF_MODE_RESIDENT],
+                         ids=["streaming", "resident"])
+def test_gn_iterations_split_over_launches(o, mode):
+    kf = synth.make_keyframe(140, 100, 25)
+    prm = params(n_gn=6, n_pcg=4, solver=dfl.DF_SOLVER_FUSED)
+    xo, to, ro = oracle_solve(o, kf, prm)
+    try:
+        for g in (1, 2, 4, 6):
+            dfl.df_set_tuning(mode=mode, gn_per_launch=g)
+            x, t, rep = solve(kf, prm)
+            assert_parity(x, t, xo, to, what=f"gn_per_launch {g}")
+            assert rep.iters_done == ro.iters_done == 24
+    finally:
+        dfl.df_set_tuning()
+
+
+def test_autotune_picks_a_shape_and_restores_state(o):
+    torch = torch_cuda()
+    kfs = [synth.make_keyframe(W, H, 300 + i) for i, (W, H) in enumerate([(160, 120), (96, 64)])]
+    prm = params(n_gn=4, n_pcg=3, solver=dfl.DF_SOLVER_FUSED)
+    ks = [create(kf) for kf in kfs]
+    try:
+        for k, kf in zip(ks, kfs):
+            k.frame_update(to_dev(kf.mu_s), to_dev(kf.var_s))
+        before = [k.get_state(np.empty((kf.height, kf.width), np.float32)) for k, kf in zip(ks, kfs)]
+        xs_before = []
+        for k, kf in zip(ks, kfs):
+            xb = np.empty((kf.height, kf.width), np.float32)
+            k.get_state(xb)
+            xs_before.append(xb)
+        best, ms = dfl.df_autotune([k.handle for k in ks], prm)
+        assert ms > 0 and best.mode in (1, 2)
+        cur = dfl.df_get_tuning()
+        assert (cur.mode, cur.vec, cur.tile_rows, cur.gn_per_launch) == (
+            best.mode, best.vec, best.tile_rows, best.gn_per_launch)
+        for k, kf, xb, tb in zip(ks, kfs, xs_before, before):
+            xa = np.empty_like(xb)
+            ta = k.get_state(xa)
+            assert np.array_equal(xa, xb) and ta == tb  # the state is as before
+        dfl.df_optimise_batch([k.handle for k in ks], prm, report=True)
+        for k, kf in zip(ks, kfs):
+            out = torch.empty((kf.height, kf.width), dtype=torch.float32, device="cuda")
+            k.fetch_depth(out, log_space=True)
+            t = k.get_state()
+            xo, to, _ = oracle_solve(o, kf, prm)
+            assert_parity(out.double().cpu().numpy(), t, xo, to, what="after autotune")
+    finally:
+        for k in ks:
+            k.close()
+        dfl.df_set_tuning()
+
+
+@pytest.mark.parametrize("sv", [(dfl.DF_SOLVER_LAUNCHES, 0), (dfl.DF_SOLVER_FUSED, 2),
+                                (dfl.DF_SOLVER_FUSED, 1)], ids=["launches", "resident", "streaming"])
+def test_frame_captured_in_a_cuda_graph(sv):
+    """A frame's work (semi-dense update, solve, depth output) captured once
+    in a CUDA graph and replayed gives the eager result."""
+    torch = torch_cuda()
+    solver, mode = sv
+    kf, mus, vs = synth.make_sequence(96, 72, 26, n_frames=3)
+    prm = params(n_gn=4, n_pcg=3, solver=solver)
+    dfl.df_set_tuning(mode=mode)
+    try:
+        dmu, dvs = to_dev(mus), to_dev(vs)
+        out = torch.empty((72, 96), dtype=torch.float32, device="cuda")
+        eager = create(kf)
+        try:
+            for f in range(3):
+                eager.frame_update(dmu[f], dvs[f])
+                eager.optimise(prm)
+            eager.fetch_depth(out, log_space=True)
+            ref = out.clone()
+        finally:
+            eager.close()
+        k = create(kf)
+        try:
+            mu_in = torch.empty_like(dmu[0])
+            var_in = torch.empty_like(dvs[0])
+            # warm-up outside the capture (uploads the fused kernel's plan)
+            mu_in.copy_(dmu[0])
+            var_in.copy_(dvs[0])
+            k.set_state(to_dev(kf.mu_n), 0.0)
+            k.optimise(prm)
+            k.set_state(to_dev(kf.mu_n), 0.0)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(g, stream=s):
+                    k.frame_update(mu_in, var_in)
+                    k.optimise(prm)
+                    k.fetch_depth(out, log_space=True)
+            torch.cuda.current_stream().wait_stream(s)
+            for f in range(3):
+                mu_in.copy_(dmu[f])
+                var_in.copy_(dvs[f])
+                g.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref)
+        finally:
+            k.close()
+    finally:
+        dfl.df_set_tuning()
