@@ -189,13 +189,20 @@ def _ptr(a, want_device: Optional[bool] = None):
 
 
 def _stream(stream, like=None):
+    """The cudaStream_t to pass: the given one, else torch's current stream
+    (on the tensor's device if one is given), else the legacy default."""
     if stream is not None:
         if isinstance(stream, int):
             return stream
         return int(getattr(stream, "cuda_stream", stream))
-    if like is not None and _is_torch(like) and like.is_cuda:
+    try:
         import torch
+    except ImportError:
+        return 0
+    if like is not None and _is_torch(like) and like.is_cuda:
         return torch.cuda.current_stream(like.device).cuda_stream
+    if torch.cuda.is_available() and torch.cuda.is_initialized():
+        return torch.cuda.current_stream().cuda_stream
     return 0
 
 
