@@ -47,6 +47,7 @@
 
 #include "df_fused.cuh"
 #include "df_sync.cuh"
+#include "df_tma.cuh"
 
 namespace df {
 
@@ -504,15 +505,496 @@ __device__ void final_tile(const FusedKf &K, int lt, bool first, bool update, fl
   }
 }
 
+// ---- VEC = 4 tiles fed by bulk copies (df_tma.cuh) --------------------------
+//
+// Same arithmetic as the tiles above; the rows of a tile (one halo row above
+// and below where they exist) are staged in the warp's ring, kStages rows in
+// flight, and every value, including the tile's west / east neighbour
+// columns, is read from shared memory. Each function returns false if a wait
+// for staged rows ran out of time.
+
+__device__ __forceinline__ F<4> f4v(float4 q) {
+  F<4> a;
+  a.v[0] = q.x; a.v[1] = q.y; a.v[2] = q.z; a.v[3] = q.w;
+  return a;
+}
+
+template <int DT>
+__device__ __forceinline__ F<4> cnn4(const RowRing &ring, int s, int p) {
+  if constexpr (DT == DF_F32) {
+    return f4v(ring.f4(s, p));
+  } else {
+    const uint2 q = ring.h4(s, p);
+    const unsigned short h[4] = {(unsigned short)(q.x & 0xffff), (unsigned short)(q.x >> 16),
+                                 (unsigned short)(q.y & 0xffff), (unsigned short)(q.y >> 16)};
+    F<4> a;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if constexpr (DT == DF_BF16)
+        a.v[e] = __bfloat162float(__ushort_as_bfloat16(h[e]));
+      else
+        a.v[e] = __half2float(__ushort_as_half(h[e]));
+    }
+    return a;
+  }
+}
+
+template <int DT>
+__device__ __forceinline__ float cnn1(const RowRing &ring, int s, int p, int idx32) {
+  // idx32: slot index of an f32 plane (3 = west, 132 = east); 16-bit planes
+  // carry 8 halo elements, hence the shift by 4
+  if constexpr (DT == DF_F32) {
+    return ring.f1(s, p, idx32);
+  } else {
+    const unsigned short h = ring.h1(s, p, idx32 + 4);
+    if constexpr (DT == DF_BF16)
+      return __bfloat162float(__ushort_as_bfloat16(h));
+    else
+      return __half2float(__ushort_as_half(h));
+  }
+}
+
+template <int DT>
+__device__ __forceinline__ void store4(float *p, const F<4> &a) {
+  __stcg(reinterpret_cast<float4 *>(p), make_float4(a.v[0], a.v[1], a.v[2], a.v[3]));
+}
+
+// Rows jb..je of a tile go through the ring in order; 'ensure(k)' waits for
+// the k-th of them, 'release()' frees the oldest waited row's stage and
+// stages the next row of the tile.
+struct TileRows {
+  RowRing &ring;
+  const StagePlane *pl;
+  int np, c0, P, jb, R, issued = 0, waited = 0, released = 0;
+  bool ok = true;
+  __device__ TileRows(RowRing &r, const StagePlane *pl_, int np_, int c0_, int P_, int jb_, int R_)
+      : ring(r), pl(pl_), np(np_), c0(c0_), P(P_), jb(jb_), R(R_) {
+    if ((threadIdx.x & 31) == 0) fence_proxy_async_global();  // see the previous pass's stores
+    while (issued < R && issued < kStages) issue_one();
+  }
+  __device__ __forceinline__ void issue_one() {
+    __syncwarp();
+    ring.issue(issued % kStages, pl, np, (size_t)(jb + issued), c0, P);
+    ++issued;
+  }
+  __device__ __forceinline__ int stage(int k) const { return k % kStages; }
+  __device__ __forceinline__ bool ensure(int k) {
+    while (ok && waited <= k) {
+      ok = ring.wait(stage(waited));
+      ++waited;
+    }
+    return ok;
+  }
+  __device__ __forceinline__ void release() {
+    ++released;
+    if (issued < R) issue_one();
+  }
+};
+
+template <int KIND>
+struct CgIdx {
+  static constexpr int R = 0;
+  static constexpr int S = KIND == 2 ? 1 : 0;
+  static constexpr int W = KIND == 0 ? 0 : (KIND == 1 ? 1 : 2);
+  static constexpr int ID = KIND == 0 ? 1 : (KIND == 1 ? 2 : 3);
+  static constexpr int P = KIND == 2 ? 4 : 0;
+  static constexpr int X = KIND == 0 ? 0 : (KIND == 1 ? 3 : 5);
+  static constexpr int WX = KIND == 0 ? 2 : (KIND == 1 ? 4 : 6);
+  static constexpr int WY = KIND == 0 ? 3 : (KIND == 1 ? 5 : 7);
+  static constexpr int NP = KIND == 0 ? 4 : (KIND == 1 ? 6 : 8);
+};
+
+template <int KIND>
+__device__ __forceinline__ RowNew<4> ring_row_new(const RowRing &ring, int s, float alpha,
+                                                  float beta) {
+  using I = CgIdx<KIND>;
+  RowNew<4> o;
+  o.d = f4v(ring.f4(s, I::ID));
+  const F<4> r = f4v(ring.f4(s, I::R));
+  o.r_in = r;
+  if constexpr (KIND == 0) {
+    o.r = r;
+    o.s = fzero<4>();
+  } else {
+    const F<4> w = f4v(ring.f4(s, I::W));
+    F<4> sp;
+    if constexpr (KIND == 2) sp = f4v(ring.f4(s, I::S));
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      o.s.v[e] = (KIND == 2) ? w.v[e] + beta * sp.v[e] : w.v[e];
+      o.r.v[e] = r.v[e] - alpha * o.s.v[e];
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) o.u.v[e] = o.r.v[e] * o.d.v[e];
+  return o;
+}
+
+template <int KIND>
+__device__ __forceinline__ float ring_col_u(const RowRing &ring, int s, int idx, float alpha,
+                                            float beta) {
+  using I = CgIdx<KIND>;
+  const float id = ring.f1(s, I::ID, idx);
+  float r = ring.f1(s, I::R, idx);
+  if constexpr (KIND != 0) {
+    float w = ring.f1(s, I::W, idx);
+    if constexpr (KIND == 2) w += beta * ring.f1(s, I::S, idx);
+    r -= alpha * w;
+  }
+  return r * id;
+}
+
+template <int KIND>
+__device__ bool tma_cg_tile(RowRing &ring, const FusedKf &K, int lt, float alpha, float beta,
+                            const float *r_cur, const float *s_prev, const float *w_cur,
+                            float *r_nxt, float *s_cur, float *w_nxt, float acc[kQ]) {
+  using I = CgIdx<KIND>;
+  const Planes &k = K.pl;
+  const Geo g = geo_of<4>(K, lt);
+  const int lane = threadIdx.x & 31;
+  const int W = k.W, H = k.H;
+  const size_t P = k.P;
+  StagePlane pl[8];
+  pl[I::R] = {r_cur, 4};
+  if constexpr (KIND == 2) pl[I::S] = {s_prev, 4};
+  if constexpr (KIND != 0) pl[I::W] = {w_cur, 4};
+  pl[I::ID] = {k.diag, 4};
+  if constexpr (KIND == 2) pl[I::P] = {k.v[0], 4};
+  if constexpr (KIND != 0) pl[I::X] = {k.x, 4};
+  pl[I::WX] = {k.wx, 4};
+  pl[I::WY] = {k.wy, 4};
+  const int jb = g.r0 > 0 ? g.r0 - 1 : g.r0;
+  const int je = min(g.r0 + g.nrows, H - 1);
+  TileRows rows(ring, pl, I::NP, g.c0, (int)P, jb, je - jb + 1);
+  F<4> u_up = fzero<4>(), wy_up = fzero<4>();
+  int kc = 0;
+  if (g.r0 > 0) {
+    if (!rows.ensure(0)) return false;
+    u_up = ring_row_new<KIND>(ring, rows.stage(0), alpha, beta).u;
+    wy_up = f4v(ring.f4(rows.stage(0), I::WY));
+    rows.release();
+    kc = 1;
+  }
+  if (!rows.ensure(kc)) return false;
+  RowNew<4> cur = ring_row_new<KIND>(ring, rows.stage(kc), alpha, beta);
+  size_t i = (size_t)g.r0 * P + g.col;
+  for (int j = 0; j < g.nrows; ++j) {
+    const int v = g.r0 + j;
+    const int sc = rows.stage(kc);
+    RowNew<4> nxt;
+    F<4> u_dn = fzero<4>();
+    if (v + 1 < H) {
+      if (!rows.ensure(kc + 1)) return false;
+      nxt = ring_row_new<KIND>(ring, rows.stage(kc + 1), alpha, beta);
+      u_dn = nxt.u;
+    }
+    const F<4> wxr = f4v(ring.f4(sc, I::WX)), wyr = f4v(ring.f4(sc, I::WY));
+    F<4> u_w, u_e, wx_w;
+#pragma unroll
+    for (int e = 1; e < 4; ++e) {
+      u_w.v[e] = cur.u.v[e - 1];
+      wx_w.v[e] = wxr.v[e - 1];
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) u_e.v[e] = cur.u.v[e + 1];
+    {
+      float uw = shfl_up1(cur.u.v[3]);
+      float wxl = shfl_up1(wxr.v[3]);
+      float ue = shfl_dn1(cur.u.v[0]);
+      if (lane == 0) {
+        const bool west = g.col > 0;
+        uw = west ? ring_col_u<KIND>(ring, sc, 3, alpha, beta) : 0.0f;
+        wxl = west ? ring.f1(sc, I::WX, 3) : 0.0f;
+      }
+      if (lane == 31) ue = (g.col + 4 < W) ? ring_col_u<KIND>(ring, sc, 132, alpha, beta) : 0.0f;
+      u_w.v[0] = uw;
+      wx_w.v[0] = wxl;
+      u_e.v[3] = ue;
+    }
+    F<4> w_new;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      w_new.v[e] = cur.r.v[e] - (wxr.v[e] * u_e.v[e] + wx_w.v[e] * u_w.v[e] +
+                                 wyr.v[e] * u_dn.v[e] + wy_up.v[e] * u_up.v[e]);
+      acc[0] += cur.r.v[e] * cur.u.v[e];
+      acc[1] += w_new.v[e] * cur.u.v[e];
+      acc[2] += cur.r.v[e] * cur.r.v[e];
+    }
+    stm<4>(w_nxt + i, w_new);
+    if constexpr (KIND != 0) {
+      F<4> p = (KIND == 2) ? f4v(ring.f4(sc, I::P)) : fzero<4>();
+      F<4> x = f4v(ring.f4(sc, I::X));
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float ui = cur.r_in.v[e] * cur.d.v[e];
+        p.v[e] = (KIND == 2) ? ui + beta * p.v[e] : ui;
+        x.v[e] += alpha * p.v[e];
+      }
+      stm<4>(k.v[0] + i, p);
+      stm<4>(k.x + i, x);
+      stm<4>(r_nxt + i, cur.r);
+      stm<4>(s_cur + i, cur.s);
+    }
+    rows.release();
+    u_up = cur.u;
+    wy_up = wyr;
+    cur = nxt;
+    ++kc;
+    i += P;
+  }
+  // the halo row below was waited for but is not needed any more
+  return rows.ensure(rows.R - 1);
+}
+
+__device__ bool tma_final_tile(RowRing &ring, const FusedKf &K, int lt, bool first, bool update,
+                               float alpha, float beta, bool scale, float t, const SolveCfg &c,
+                               const float *r_cur, const float *s_prev, const float *w_cur,
+                               float acc[kQ]) {
+  const Planes &k = K.pl;
+  const Geo g = geo_of<4>(K, lt);
+  StagePlane pl[8];
+  int np = 0, iR = -1, iS = -1, iW = -1, iD = -1, iP = -1, iMS = -1, iVS = -1;
+  const int iX = np;
+  pl[np++] = {k.x, 4};
+  if (update) {
+    iR = np; pl[np++] = {r_cur, 4};
+    iW = np; pl[np++] = {w_cur, 4};
+    iD = np; pl[np++] = {k.diag, 4};
+    if (!first) {
+      iS = np; pl[np++] = {s_prev, 4};
+      iP = np; pl[np++] = {k.v[0], 4};
+    }
+  }
+  if (scale) {
+    iMS = np; pl[np++] = {k.mu_s, 4};
+    iVS = np; pl[np++] = {k.var_s, 4};
+  }
+  TileRows rows(ring, pl, np, g.c0, k.P, g.r0, g.nrows);
+  size_t i = (size_t)g.r0 * k.P + g.col;
+  for (int j = 0; j < g.nrows; ++j) {
+    if (!rows.ensure(j)) return false;
+    const int s = rows.stage(j);
+    F<4> x = f4v(ring.f4(s, iX));
+    if (update) {
+      const F<4> d = f4v(ring.f4(s, iD)), r = f4v(ring.f4(s, iR)), w = f4v(ring.f4(s, iW));
+      const F<4> p = first ? fzero<4>() : f4v(ring.f4(s, iP));
+      const F<4> sp = first ? fzero<4>() : f4v(ring.f4(s, iS));
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float ui = r.v[e] * d.v[e];
+        const float pi = first ? ui : ui + beta * p.v[e];
+        x.v[e] += alpha * pi;
+        const float si = first ? w.v[e] : w.v[e] + beta * sp.v[e];
+        const float rn = r.v[e] - alpha * si;
+        acc[0] += rn * rn;
+      }
+      stm<4>(k.x + i, x);
+    }
+    if (scale) {
+      const F<4> ms = f4v(ring.f4(s, iMS)), vs = f4v(ring.f4(s, iVS));
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (g.col + e < k.W && semi_valid(ms.v[e], vs.v[e])) {
+          const float w = robust_weight(x.v[e] - t - ms.v[e], vs.v[e], c.delta, c.loss);
+          acc[1] += w;
+          acc[2] += w * (x.v[e] - ms.v[e]);
+        }
+      }
+    }
+    rows.release();
+    i += k.P;
+  }
+  return true;
+}
+
+__device__ bool tma_scale_tile(RowRing &ring, const FusedKf &K, int lt, float t,
+                               const SolveCfg &c, float acc[kQ]) {
+  const Planes &k = K.pl;
+  const Geo g = geo_of<4>(K, lt);
+  const StagePlane pl[3] = {{k.x, 4}, {k.mu_s, 4}, {k.var_s, 4}};
+  TileRows rows(ring, pl, 3, g.c0, k.P, g.r0, g.nrows);
+  for (int j = 0; j < g.nrows; ++j) {
+    if (!rows.ensure(j)) return false;
+    const int s = rows.stage(j);
+    const F<4> x = f4v(ring.f4(s, 0)), ms = f4v(ring.f4(s, 1)), vs = f4v(ring.f4(s, 2));
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (g.col + e < k.W && semi_valid(ms.v[e], vs.v[e])) {
+        const float w = robust_weight(x.v[e] - t - ms.v[e], vs.v[e], c.delta, c.loss);
+        acc[0] += w;
+        acc[1] += w * (x.v[e] - ms.v[e]);
+      }
+    }
+    rows.release();
+  }
+  return true;
+}
+
+// planes of the assembly: x, mu_s, var_s (f32) and the six network planes
+enum : int { A_X = 0, A_MS, A_VS, A_MN, A_VN, A_GX, A_VX, A_GY, A_VY, A_NP };
+
+template <int DT>
+__device__ bool tma_assemble_tile(RowRing &ring, const FusedKf &K, int lt, float t,
+                                  const SolveCfg &c, float acc[kQ]) {
+  const Planes &k = K.pl;
+  const Geo g = geo_of<4>(K, lt);
+  const int lane = threadIdx.x & 31;
+  const int W = k.W, H = k.H;
+  const size_t P = k.P;
+  const bool semi = c.terms & DF_TERM_SEMI, net = c.terms & DF_TERM_NET,
+             grad = c.terms & DF_TERM_GRAD;
+  const int es = DT == DF_F32 ? 4 : 2;
+  const StagePlane pl[A_NP] = {{k.x, 4},      {k.mu_s, 4},   {k.var_s, 4},
+                               {k.cnn[0], es}, {k.cnn[1], es}, {k.cnn[2], es},
+                               {k.cnn[3], es}, {k.cnn[4], es}, {k.cnn[5], es}};
+  float *r_out = k.v[1];
+  const int jb = g.r0 > 0 ? g.r0 - 1 : g.r0;
+  const int je = min(g.r0 + g.nrows, H - 1);
+  TileRows rows(ring, pl, A_NP, g.c0, (int)P, jb, je - jb + 1);
+  int kc = 0;
+  F<4> wy_up = fzero<4>(), ey_up = fzero<4>(), gy_up = fzero<4>();
+  if (g.r0 > 0) {
+    if (!rows.ensure(1)) return false;
+    const int s0 = rows.stage(0), s1 = rows.stage(1);
+    if (grad) {
+      const F<4> xu = f4v(ring.f4(s0, A_X)), xc = f4v(ring.f4(s1, A_X));
+      const F<4> gyu = cnn4<DT>(ring, s0, A_GY), vyu = cnn4<DT>(ring, s0, A_VY);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (g.col + e < W) {
+          gy_up.v[e] = gyu.v[e];
+          ey_up.v[e] = xc.v[e] - xu.v[e] - gyu.v[e];
+          wy_up.v[e] = robust_weight(ey_up.v[e], vyu.v[e], c.delta, c.loss);
+        }
+      }
+    }
+    rows.release();
+    kc = 1;
+  }
+  size_t i = (size_t)g.r0 * P + g.col;
+  for (int j = 0; j < g.nrows; ++j) {
+    const int v = g.r0 + j;
+    if (!rows.ensure(kc)) return false;
+    const int sc = rows.stage(kc);
+    const F<4> x_cur = f4v(ring.f4(sc, A_X));
+    F<4> x_dn = fzero<4>();
+    if (v + 1 < H) {
+      if (!rows.ensure(kc + 1)) return false;
+      x_dn = f4v(ring.f4(rows.stage(kc + 1), A_X));
+    }
+    F<4> x_e;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) x_e.v[e] = x_cur.v[e + 1];
+    {
+      float xe = shfl_dn1(x_cur.v[0]);
+      if (lane == 31) xe = (g.col + 4 < W) ? ring.f1(sc, A_X, 132) : 0.0f;
+      x_e.v[3] = xe;
+    }
+    F<4> wxv = fzero<4>(), exv = fzero<4>(), gxv = fzero<4>();
+    F<4> wyv = fzero<4>(), eyv = fzero<4>(), gyv = fzero<4>();
+    if (grad) {
+      const F<4> gxr = cnn4<DT>(ring, sc, A_GX), vxr = cnn4<DT>(ring, sc, A_VX);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (g.col + e < W - 1) {
+          gxv.v[e] = gxr.v[e];
+          exv.v[e] = x_e.v[e] - x_cur.v[e] - gxr.v[e];
+          wxv.v[e] = robust_weight(exv.v[e], vxr.v[e], c.delta, c.loss);
+        }
+      }
+      if (v < H - 1) {
+        const F<4> gyr = cnn4<DT>(ring, sc, A_GY), vyr = cnn4<DT>(ring, sc, A_VY);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (g.col + e < W) {
+            gyv.v[e] = gyr.v[e];
+            eyv.v[e] = x_dn.v[e] - x_cur.v[e] - gyr.v[e];
+            wyv.v[e] = robust_weight(eyv.v[e], vyr.v[e], c.delta, c.loss);
+          }
+        }
+      }
+    }
+    F<4> wxw, exw, gxw;
+#pragma unroll
+    for (int e = 1; e < 4; ++e) {
+      wxw.v[e] = wxv.v[e - 1];
+      exw.v[e] = exv.v[e - 1];
+      gxw.v[e] = gxv.v[e - 1];
+    }
+    {
+      float a = shfl_up1(wxv.v[3]), b = shfl_up1(exv.v[3]), gg = shfl_up1(gxv.v[3]);
+      if (lane == 0) {
+        a = b = gg = 0.0f;
+        if (grad && g.col > 0 && g.col < W) {
+          const float xw = ring.f1(sc, A_X, 3);
+          gg = cnn1<DT>(ring, sc, A_GX, 3);
+          b = x_cur.v[0] - xw - gg;
+          a = robust_weight(b, cnn1<DT>(ring, sc, A_VX, 3), c.delta, c.loss);
+        }
+      }
+      wxw.v[0] = a;
+      exw.v[0] = b;
+      gxw.v[0] = gg;
+    }
+    const F<4> ms = f4v(ring.f4(sc, A_MS)), vs = f4v(ring.f4(sc, A_VS));
+    const F<4> mn = cnn4<DT>(ring, sc, A_MN), vn = cnn4<DT>(ring, sc, A_VN);
+    F<4> dd, rr_;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.0f, r = 0.0f, b = 0.0f;
+      if (g.col + e < W) {
+        const float xi = x_cur.v[e];
+        float ws = 0.0f, rs = 0.0f, bs = 0.0f;
+        if (semi && semi_valid(ms.v[e], vs.v[e])) {
+          ws = robust_weight(xi - t - ms.v[e], vs.v[e], c.delta, c.loss);
+          rs = ws * (t + ms.v[e] - xi);
+          bs = ws * (t + ms.v[e]);
+        }
+        float wn = 0.0f, m = 0.0f;
+        if (net) {
+          m = mn.v[e];
+          wn = robust_weight(xi - m, vn.v[e], c.delta, c.loss);
+        }
+        d = ws + wn + wxv.v[e] + wxw.v[e] + wyv.v[e] + wy_up.v[e];
+        r = rs + wn * (m - xi) + wxv.v[e] * exv.v[e] - wxw.v[e] * exw.v[e] +
+            wyv.v[e] * eyv.v[e] - wy_up.v[e] * ey_up.v[e];
+        b = bs + wn * m - wxv.v[e] * gxv.v[e] + wxw.v[e] * gxw.v[e] - wyv.v[e] * gyv.v[e] +
+            wy_up.v[e] * gy_up.v[e];
+      }
+      const float id = d > 0.0f ? 1.0f / d : 0.0f;
+      dd.v[e] = id;
+      rr_.v[e] = r;
+      acc[0] += r * (r * id);
+      acc[1] += r * r;
+      acc[2] += b * b;
+    }
+    stm<4>(k.diag + i, dd);
+    stm<4>(k.wx + i, wxv);
+    stm<4>(k.wy + i, wyv);
+    stm<4>(r_out + i, rr_);
+    rows.release();
+    wy_up = wyv;
+    ey_up = eyv;
+    gy_up = gyv;
+    ++kc;
+    i += P;
+  }
+  return rows.ensure(rows.R - 1);
+}
+
 struct Seg {
   double t, gam, alpha, beta, bb, rr;
   int stop, iters, active, pad;
 };
 
+// dynamic shared memory of the VEC = 4 kernel: the warps' row rings + mbarriers
+constexpr int kRingSmem = kWarps * kWarpStageBytes + kWarps * kStages * 8;
+
 template <int VEC>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     k_fused(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns,
             int first) {
+  extern __shared__ __align__(128) char dyn_ring[];
   __shared__ FusedKf s_kf[kMaxSeg];
   __shared__ Seg s_seg[kMaxSeg];
   __shared__ ff2 s_acc[kWarps][kMaxSeg][kQ];
@@ -550,6 +1032,18 @@ __global__ void __launch_bounds__(kThreads, 2)
     s_nseg = n;
     s_epoch = 0u;
   }
+  RowRing ring;
+  if constexpr (VEC == 4) {
+    ring.smem = dyn_ring + warp * kWarpStageBytes;
+    ring.bars = reinterpret_cast<uint64_t *>(dyn_ring + kWarps * kWarpStageBytes) + warp * kStages;
+    ring.parity = 0u;
+    ring.pending = 0u;
+    ring.limit_ns = limit_ns;
+    if (lane == 0) {
+      for (int st = 0; st < kStages; ++st) mbar_init(&ring.bars[st], 1u);
+      mbar_fence_init();
+    }
+  }
   __syncthreads();
   const int nseg = s_nseg;
   const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step;
@@ -574,6 +1068,41 @@ __global__ void __launch_bounds__(kThreads, 2)
       float *Rc = (it & 1) ? R1 : R0, *Rn = (it & 1) ? R0 : R1;
       float *Sp = (it & 1) ? S1 : S0, *Sc = (it & 1) ? S0 : S1;
       float *Wc = (it & 1) ? W1 : W0, *Wn = (it & 1) ? W0 : W1;
+      if constexpr (VEC == 4) {
+        bool ok = true;
+        switch (kind) {
+          case P_SCALE:
+            ok = tma_scale_tile(ring, K, lt, ft, c, a);
+            break;
+          case P_ASSEMBLE:
+            if (K.pl.dtype == DF_BF16)
+              ok = tma_assemble_tile<DF_BF16>(ring, K, lt, ft, c, a);
+            else if (K.pl.dtype == DF_F16)
+              ok = tma_assemble_tile<DF_F16>(ring, K, lt, ft, c, a);
+            else
+              ok = tma_assemble_tile<DF_F32>(ring, K, lt, ft, c, a);
+            break;
+          case P_INIT:
+            if (!S.stop) ok = tma_cg_tile<0>(ring, K, lt, 0.0f, 0.0f, R0, S0, W1, R1, S1, W0, a);
+            break;
+          case P_ITER:
+            if (!S.stop) {
+              if (it == 0)
+                ok = tma_cg_tile<1>(ring, K, lt, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
+              else
+                ok = tma_cg_tile<2>(ring, K, lt, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
+            }
+            break;
+          default:  // P_FINAL
+            ok = tma_final_tile(ring, K, lt, it == 0, !S.stop, fa, fb, final_scale, ft, c, Rc, Sp,
+                                Wc, a);
+            break;
+        }
+        if (!ok) {  // a staged row never arrived: give up the launch
+          if (lane == 0) atomicExch(&h->abort, 1u);
+          break;
+        }
+      } else {
       switch (kind) {
         case P_SCALE:
           scale_tile<VEC>(K, lt, ft, c, a);
@@ -600,6 +1129,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         default:  // P_FINAL
           final_tile<VEC>(K, lt, it == 0, !S.stop, fa, fb, final_scale, ft, c, Rc, Sp, Wc, a);
           break;
+      }
       }
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
@@ -752,6 +1282,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       sc->stop = S.stop;
     }
   }
+  if constexpr (VEC == 4) ring.drain();
   grid_exit(h, G);
 }
 
@@ -780,7 +1311,8 @@ const DevInfo &dev_info() {
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     d.coop = coop != 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0], k_fused<1>, kThreads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1], k_fused<4>, kThreads, 0);
+    cudaFuncSetAttribute(k_fused<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1], k_fused<4>, kThreads, kRingSmem);
     cudaGetLastError();
     g_dev[dev] = d;
     g_dev_init[dev] = true;
@@ -799,7 +1331,7 @@ bool streaming_supported() {
 
 int streaming_max_ctas() {
   const DevInfo &d = dev_info();
-  return d.sms * std::max(1, std::min(d.occ[0], d.occ[1]));
+  return d.sms * std::max(1, std::max(d.occ[0], d.occ[1]));
 }
 
 static size_t streaming_bytes(int nkf, int G, size_t inbox) {
@@ -824,25 +1356,33 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
                           std::vector<char> &out, LaunchShape &shape) {
   const DevInfo &d = dev_info();
   if (n < 1 || d.sms <= 0) return false;
-  const int occ = std::max(1, std::min(d.occ[0], d.occ[1]));
-  const int G_cap = std::max(1, std::min(tune.max_ctas > 0 ? tune.max_ctas : d.sms * occ,
-                                         d.sms * occ));
-  const long long warps = (long long)G_cap * kWarps;
   long long rows4 = 0, rows1 = 0;
   for (int k = 0; k < n; ++k) {
     rows4 += (long long)((kfs[k]->W + 127) / 128) * kfs[k]->H;
     rows1 += (long long)((kfs[k]->W + 31) / 32) * kfs[k]->H;
   }
+  const int cap_of[2] = {d.sms * std::max(1, d.occ[0]), d.sms * std::max(1, d.occ[1])};
   int vec = tune.vec;
-  if (vec != 1 && vec != 4) vec = (rows4 >= 4 * warps) ? 4 : 1;
+  if (vec != 1 && vec != 4) vec = (rows4 >= 8LL * cap_of[1] * kWarps) ? 4 : 1;
+  const int G_cap = std::max(1, std::min(tune.max_ctas > 0 ? tune.max_ctas : cap_of[vec == 4],
+                                         cap_of[vec == 4]));
+  const long long warps = (long long)G_cap * kWarps;
   const long long rows = vec == 4 ? rows4 : rows1;
   int th = tune.tile_rows;
-  if (th <= 0) th = (int)std::max<long long>(1, std::min<long long>(32, rows / warps));
-  // tiles per keyframe
-  std::vector<int> tb(n + 1, 0), tx(n), nt(n);
+  if (th <= 0) {
+    // about one tile per warp; VEC = 4 tiles walk long columns (their halo
+    // rows cost 2 / th), VEC = 1 tiles stay short (latency-bound sizes)
+    th = (int)(vec == 4 ? std::max<long long>(4, std::min<long long>(256, rows / warps))
+                        : std::max<long long>(1, std::min<long long>(32, rows / warps)));
+  }
+  // tiles per keyframe: rows split into bands of near-equal height ~th
+  std::vector<int> tb(n + 1, 0), tx(n), nt(n), thk(n);
   for (int k = 0; k < n; ++k) {
+    const int H = kfs[k]->H;
+    const int nty = std::max(1, (H + th / 2) / th);
+    thk[k] = (H + nty - 1) / nty;
     tx[k] = (kfs[k]->W + 32 * vec - 1) / (32 * vec);
-    nt[k] = tx[k] * ((kfs[k]->H + th - 1) / th);
+    nt[k] = tx[k] * ((H + thk[k] - 1) / thk[k]);
     tb[k + 1] = tb[k] + nt[k];
   }
   const int T = tb[n];
@@ -935,7 +1475,7 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
     fk[k].tile_begin = tb[k];
     fk[k].ntiles = nt[k];
     fk[k].tiles_x = tx[k];
-    fk[k].th = th;
+    fk[k].th = thk[k];
     fk[k].slot_begin = sb[k];
     fk[k].slot_end = se[k];
     fk[k].writer_cta = wc[k];
@@ -955,7 +1495,8 @@ cudaError_t streaming_launch(void *dplan, const LaunchShape &shape, const SolveC
   count_launches(1);
   const void *fn = vec == 4 ? reinterpret_cast<const void *>(k_fused<4>)
                             : reinterpret_cast<const void *>(k_fused<1>);
-  return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args, 0, s);
+  return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args,
+                                     vec == 4 ? (size_t)kRingSmem : 0, s);
 }
 
 // ---- dispatch between the resident and the streaming kernels -------------
