@@ -62,10 +62,9 @@ enum PassKind : int { P_SCALE = 0, P_ASSEMBLE, P_INIT, P_ITER, P_FINAL };
 
 struct FusedKf {
   Planes pl;
-  int tile_begin;  // first global tile index
-  int ntiles;
-  int tiles_x;     // column tiles per row band
-  int th;          // rows per tile
+  int row_begin;   // first row of its strips in the plan's concatenated row list
+  int rows;        // strips * H: a strip is one column tile (32 * VEC columns) over all rows
+  int pad0, pad1;
   int slot_begin;  // this keyframe's slots: [slot_begin, slot_end)
   int slot_end;
   int writer_cta;  // the CTA that writes the final scalars back
@@ -159,21 +158,19 @@ struct Geo {
 };
 
 template <int VEC>
-__device__ __forceinline__ Geo geo_of(const FusedKf &K, int lt) {
+__device__ __forceinline__ Geo geo_of(int c0, int r0, int nrows) {
   Geo g;
-  const int tx = lt % K.tiles_x, ty = lt / K.tiles_x;
-  g.c0 = tx * 32 * VEC;
-  g.r0 = ty * K.th;
-  g.nrows = min(K.th, K.pl.H - g.r0);
-  g.col = g.c0 + (threadIdx.x & 31) * VEC;
+  g.c0 = c0;
+  g.r0 = r0;
+  g.nrows = nrows;
+  g.col = c0 + (threadIdx.x & 31) * VEC;
   return g;
 }
 
 // ---- SCALE: partial sums of the scale step (Eq. 6 with x fixed) ------------
 template <int VEC>
-__device__ void scale_tile(const FusedKf &K, int lt, float t, const SolveCfg &c, float acc[kQ]) {
+__device__ void scale_tile(const FusedKf &K, const Geo &g, float t, const SolveCfg &c, float acc[kQ]) {
   const Planes &k = K.pl;
-  const Geo g = geo_of<VEC>(K, lt);
   for (int j = 0; j < g.nrows; ++j) {
     const size_t i = (size_t)(g.r0 + j) * k.P + g.col;
     const F<VEC> x = ldm<VEC>(k.x + i);
@@ -191,10 +188,9 @@ __device__ void scale_tile(const FusedKf &K, int lt, float t, const SolveCfg &c,
 
 // ---- ASSEMBLE: weights, 5-point system and r0 (see df_launch.cu) -----------
 template <int VEC, int DT>
-__device__ void assemble_tile(const FusedKf &K, int lt, float t, const SolveCfg &c,
+__device__ void assemble_tile(const FusedKf &K, const Geo &g, float t, const SolveCfg &c,
                               float acc[kQ]) {
   const Planes &k = K.pl;
-  const Geo g = geo_of<VEC>(K, lt);
   const int lane = threadIdx.x & 31;
   const int W = k.W, H = k.H;
   const size_t P = k.P;
@@ -374,11 +370,10 @@ __device__ __forceinline__ float col_new_u(const float *r_cur, const float *s_pr
 }
 
 template <int VEC, int KIND>
-__device__ void cg_tile(const FusedKf &K, int lt, float alpha, float beta, const float *r_cur,
+__device__ void cg_tile(const FusedKf &K, const Geo &g, float alpha, float beta, const float *r_cur,
                         const float *s_prev, const float *w_cur, float *r_nxt, float *s_cur,
                         float *w_nxt, float acc[kQ]) {
   const Planes &k = K.pl;
-  const Geo g = geo_of<VEC>(K, lt);
   const int lane = threadIdx.x & 31;
   const int W = k.W, H = k.H;
   const size_t P = k.P;
@@ -467,12 +462,11 @@ __device__ void cg_tile(const FusedKf &K, int lt, float alpha, float beta, const
 
 // ---- FINAL: last CG iteration (no stencil) + next scale-step sums ----------
 template <int VEC>
-__device__ void final_tile(const FusedKf &K, int lt, bool first, bool update, float alpha,
+__device__ void final_tile(const FusedKf &K, const Geo &g, bool first, bool update, float alpha,
                            float beta, bool scale, float t, const SolveCfg &c,
                            const float *r_cur, const float *s_prev, const float *w_cur,
                            float acc[kQ]) {
   const Planes &k = K.pl;
-  const Geo g = geo_of<VEC>(K, lt);
   for (int j = 0; j < g.nrows; ++j) {
     const size_t i = (size_t)(g.r0 + j) * k.P + g.col;
     F<VEC> x = ldm<VEC>(k.x + i);
@@ -561,20 +555,47 @@ __device__ __forceinline__ void store4(float *p, const F<4> &a) {
 
 // Rows jb..je of a tile go through the ring in order; 'ensure(k)' waits for
 // the k-th of them, 'release()' frees the oldest waited row's stage and
-// stages the next row of the tile.
+// stages the next row of the tile. Rows at index 0 (when has_above) and
+// R - 1 (when has_below) are halo rows and stage only the planes of
+// 'halo_mask'; the others stage those of 'mask'.
+template <int NP>
 struct TileRows {
   RowRing &ring;
-  const StagePlane *pl;
-  int np, c0, P, jb, R, issued = 0, waited = 0, released = 0;
-  bool ok = true;
-  __device__ TileRows(RowRing &r, const StagePlane *pl_, int np_, int c0_, int P_, int jb_, int R_)
-      : ring(r), pl(pl_), np(np_), c0(c0_), P(P_), jb(jb_), R(R_) {
+  const char *src[NP];  // next row's copy start per plane
+  uint32_t half = 0;    // bit p: plane p holds 16-bit values
+  uint32_t b4, d4, b2, d2, rb4, rb2;
+  uint32_t mask, halo_mask;
+  int R, issued = 0, waited = 0;
+  bool has_above, has_below, ok = true;
+  __device__ TileRows(RowRing &r, const StagePlane (&pl)[NP], uint32_t mask_, uint32_t halo_mask_,
+                      int c0, int P, int jb, int R_, bool above, bool below)
+      : ring(r), mask(mask_), halo_mask(halo_mask_), R(R_), has_above(above), has_below(below) {
+    // column range [cs, ce) of a staged row: the tile's 128 columns and
+    // 16 bytes on each side, clipped to the padded row
+    const int cs4 = c0 - 4 > 0 ? c0 - 4 : 0, ce4 = c0 + 132 < P ? c0 + 132 : P;
+    const int cs2 = c0 - 8 > 0 ? c0 - 8 : 0, ce2 = c0 + 136 < P ? c0 + 136 : P;
+    b4 = (uint32_t)(ce4 - cs4) * 4u;
+    d4 = (uint32_t)(cs4 - (c0 - 4)) * 4u;
+    b2 = (uint32_t)(ce2 - cs2) * 2u;
+    d2 = (uint32_t)(cs2 - (c0 - 8)) * 2u;
+    rb4 = (uint32_t)P * 4u;
+    rb2 = (uint32_t)P * 2u;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const bool h = pl[p].esize == 2;
+      half |= (uint32_t)h << p;
+      src[p] = static_cast<const char *>(pl[p].base) + (size_t)jb * (h ? rb2 : rb4) +
+               (size_t)(h ? cs2 * 2 : cs4 * 4);
+    }
     if ((threadIdx.x & 31) == 0) fence_proxy_async_global();  // see the previous pass's stores
     while (issued < R && issued < kStages) issue_one();
   }
   __device__ __forceinline__ void issue_one() {
     __syncwarp();
-    ring.issue(issued % kStages, pl, np, (size_t)(jb + issued), c0, P);
+    const bool halo = (has_above && issued == 0) || (has_below && issued == R - 1);
+    ring.issue<NP>(issued % kStages, src, half, b4, d4, b2, d2, halo ? halo_mask : mask);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) src[p] += ((half >> p) & 1u) ? rb2 : rb4;
     ++issued;
   }
   __device__ __forceinline__ int stage(int k) const { return k % kStages; }
@@ -586,21 +607,23 @@ struct TileRows {
     return ok;
   }
   __device__ __forceinline__ void release() {
-    ++released;
     if (issued < R) issue_one();
   }
 };
 
+// Plane order of a CG pass's staged rows: the planes a halo row needs
+// (r, s, w, 1/diag, wy) first, then wx, p, x of the own rows.
 template <int KIND>
 struct CgIdx {
   static constexpr int R = 0;
   static constexpr int S = KIND == 2 ? 1 : 0;
   static constexpr int W = KIND == 0 ? 0 : (KIND == 1 ? 1 : 2);
   static constexpr int ID = KIND == 0 ? 1 : (KIND == 1 ? 2 : 3);
-  static constexpr int P = KIND == 2 ? 4 : 0;
-  static constexpr int X = KIND == 0 ? 0 : (KIND == 1 ? 3 : 5);
-  static constexpr int WX = KIND == 0 ? 2 : (KIND == 1 ? 4 : 6);
-  static constexpr int WY = KIND == 0 ? 3 : (KIND == 1 ? 5 : 7);
+  static constexpr int WY = KIND == 0 ? 2 : (KIND == 1 ? 3 : 4);
+  static constexpr int NH = WY + 1;
+  static constexpr int WX = NH;
+  static constexpr int P = KIND == 2 ? WX + 1 : 0;
+  static constexpr int X = KIND == 0 ? 0 : (KIND == 1 ? WX + 1 : WX + 2);
   static constexpr int NP = KIND == 0 ? 4 : (KIND == 1 ? 6 : 8);
 };
 
@@ -645,16 +668,15 @@ __device__ __forceinline__ float ring_col_u(const RowRing &ring, int s, int idx,
 }
 
 template <int KIND>
-__device__ bool tma_cg_tile(RowRing &ring, const FusedKf &K, int lt, float alpha, float beta,
+__device__ __forceinline__ bool tma_cg_tile(RowRing &ring, const FusedKf &K, const Geo &g, float alpha, float beta,
                             const float *r_cur, const float *s_prev, const float *w_cur,
                             float *r_nxt, float *s_cur, float *w_nxt, float acc[kQ]) {
   using I = CgIdx<KIND>;
   const Planes &k = K.pl;
-  const Geo g = geo_of<4>(K, lt);
   const int lane = threadIdx.x & 31;
   const int W = k.W, H = k.H;
   const size_t P = k.P;
-  StagePlane pl[8];
+  StagePlane pl[I::NP];
   pl[I::R] = {r_cur, 4};
   if constexpr (KIND == 2) pl[I::S] = {s_prev, 4};
   if constexpr (KIND != 0) pl[I::W] = {w_cur, 4};
@@ -665,7 +687,8 @@ __device__ bool tma_cg_tile(RowRing &ring, const FusedKf &K, int lt, float alpha
   pl[I::WY] = {k.wy, 4};
   const int jb = g.r0 > 0 ? g.r0 - 1 : g.r0;
   const int je = min(g.r0 + g.nrows, H - 1);
-  TileRows rows(ring, pl, I::NP, g.c0, (int)P, jb, je - jb + 1);
+  TileRows<I::NP> rows(ring, pl, (1u << I::NP) - 1, (1u << I::NH) - 1, g.c0, (int)P, jb,
+                       je - jb + 1, g.r0 > 0, g.r0 + g.nrows < H);
   F<4> u_up = fzero<4>(), wy_up = fzero<4>();
   int kc = 0;
   if (g.r0 > 0) {
@@ -746,30 +769,20 @@ __device__ bool tma_cg_tile(RowRing &ring, const FusedKf &K, int lt, float alpha
   return rows.ensure(rows.R - 1);
 }
 
-__device__ bool tma_final_tile(RowRing &ring, const FusedKf &K, int lt, bool first, bool update,
+__device__ __forceinline__ bool tma_final_tile(RowRing &ring, const FusedKf &K, const Geo &g, bool first, bool update,
                                float alpha, float beta, bool scale, float t, const SolveCfg &c,
                                const float *r_cur, const float *s_prev, const float *w_cur,
                                float acc[kQ]) {
   const Planes &k = K.pl;
-  const Geo g = geo_of<4>(K, lt);
-  StagePlane pl[8];
-  int np = 0, iR = -1, iS = -1, iW = -1, iD = -1, iP = -1, iMS = -1, iVS = -1;
-  const int iX = np;
-  pl[np++] = {k.x, 4};
-  if (update) {
-    iR = np; pl[np++] = {r_cur, 4};
-    iW = np; pl[np++] = {w_cur, 4};
-    iD = np; pl[np++] = {k.diag, 4};
-    if (!first) {
-      iS = np; pl[np++] = {s_prev, 4};
-      iP = np; pl[np++] = {k.v[0], 4};
-    }
-  }
-  if (scale) {
-    iMS = np; pl[np++] = {k.mu_s, 4};
-    iVS = np; pl[np++] = {k.var_s, 4};
-  }
-  TileRows rows(ring, pl, np, g.c0, k.P, g.r0, g.nrows);
+  // fixed plane slots; a launch stages only the ones its pass reads
+  enum : int { iX = 0, iR, iW, iD, iS, iP, iMS, iVS };
+  const StagePlane pl[8] = {{k.x, 4},    {r_cur, 4},  {w_cur, 4},   {k.diag, 4},
+                            {s_prev, 4}, {k.v[0], 4}, {k.mu_s, 4}, {k.var_s, 4}};
+  uint32_t mask = 1u << iX;
+  if (update) mask |= (1u << iR) | (1u << iW) | (1u << iD);
+  if (update && !first) mask |= (1u << iS) | (1u << iP);
+  if (scale) mask |= (1u << iMS) | (1u << iVS);
+  TileRows<8> rows(ring, pl, mask, mask, g.c0, k.P, g.r0, g.nrows, false, false);
   size_t i = (size_t)g.r0 * k.P + g.col;
   for (int j = 0; j < g.nrows; ++j) {
     if (!rows.ensure(j)) return false;
@@ -807,12 +820,11 @@ __device__ bool tma_final_tile(RowRing &ring, const FusedKf &K, int lt, bool fir
   return true;
 }
 
-__device__ bool tma_scale_tile(RowRing &ring, const FusedKf &K, int lt, float t,
+__device__ __forceinline__ bool tma_scale_tile(RowRing &ring, const FusedKf &K, const Geo &g, float t,
                                const SolveCfg &c, float acc[kQ]) {
   const Planes &k = K.pl;
-  const Geo g = geo_of<4>(K, lt);
   const StagePlane pl[3] = {{k.x, 4}, {k.mu_s, 4}, {k.var_s, 4}};
-  TileRows rows(ring, pl, 3, g.c0, k.P, g.r0, g.nrows);
+  TileRows<3> rows(ring, pl, 7u, 7u, g.c0, k.P, g.r0, g.nrows, false, false);
   for (int j = 0; j < g.nrows; ++j) {
     if (!rows.ensure(j)) return false;
     const int s = rows.stage(j);
@@ -830,27 +842,28 @@ __device__ bool tma_scale_tile(RowRing &ring, const FusedKf &K, int lt, float t,
   return true;
 }
 
-// planes of the assembly: x, mu_s, var_s (f32) and the six network planes
-enum : int { A_X = 0, A_MS, A_VS, A_MN, A_VN, A_GX, A_VX, A_GY, A_VY, A_NP };
+// planes of the assembly: the halo rows need x, gy, var_gy (staged first);
+// the own rows also mu_s, var_s (f32) and the other network planes
+enum : int { A_X = 0, A_GY, A_VY, A_MS, A_VS, A_MN, A_VN, A_GX, A_VX, A_NP };
 
 template <int DT>
-__device__ bool tma_assemble_tile(RowRing &ring, const FusedKf &K, int lt, float t,
+__device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &K, const Geo &g, float t,
                                   const SolveCfg &c, float acc[kQ]) {
   const Planes &k = K.pl;
-  const Geo g = geo_of<4>(K, lt);
   const int lane = threadIdx.x & 31;
   const int W = k.W, H = k.H;
   const size_t P = k.P;
   const bool semi = c.terms & DF_TERM_SEMI, net = c.terms & DF_TERM_NET,
              grad = c.terms & DF_TERM_GRAD;
   const int es = DT == DF_F32 ? 4 : 2;
-  const StagePlane pl[A_NP] = {{k.x, 4},      {k.mu_s, 4},   {k.var_s, 4},
-                               {k.cnn[0], es}, {k.cnn[1], es}, {k.cnn[2], es},
-                               {k.cnn[3], es}, {k.cnn[4], es}, {k.cnn[5], es}};
+  const StagePlane pl[A_NP] = {{k.x, 4},       {k.cnn[4], es}, {k.cnn[5], es},
+                               {k.mu_s, 4},    {k.var_s, 4},   {k.cnn[0], es},
+                               {k.cnn[1], es}, {k.cnn[2], es}, {k.cnn[3], es}};
   float *r_out = k.v[1];
   const int jb = g.r0 > 0 ? g.r0 - 1 : g.r0;
   const int je = min(g.r0 + g.nrows, H - 1);
-  TileRows rows(ring, pl, A_NP, g.c0, (int)P, jb, je - jb + 1);
+  TileRows<A_NP> rows(ring, pl, (1u << A_NP) - 1, (1u << A_GY) | (1u << A_VY) | (1u << A_X),
+                       g.c0, (int)P, jb, je - jb + 1, g.r0 > 0, g.r0 + g.nrows < H);
   int kc = 0;
   F<4> wy_up = fzero<4>(), ey_up = fzero<4>(), gy_up = fzero<4>();
   if (g.r0 > 0) {
@@ -1006,18 +1019,20 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = h->G, nslots = h->nslots, nkf = h->nkf;
   const char *hb = reinterpret_cast<const char *>(h);
-  const int *cta_tile = reinterpret_cast<const int *>(hb + h->off_cta_tile);
+  const int *warp_row = reinterpret_cast<const int *>(hb + h->off_cta_work);
   const int *cta_kf = reinterpret_cast<const int *>(hb + h->off_cta_kf);
   const int *cta_slot = reinterpret_cast<const int *>(hb + h->off_cta_slot);
   const FusedKf *kfs = reinterpret_cast<const FusedKf *>(hb + h->off_kf);
   Slot *slots = reinterpret_cast<Slot *>(reinterpret_cast<char *>(h) + h->off_slots);
   const int cta = blockIdx.x;
-  const int tb = cta_tile[cta], te = cta_tile[cta + 1];
+  const int re = warp_row[(cta + 1) * kWarps];  // end of the CTA's rows
+  const int wb = warp_row[cta * kWarps + warp], we = warp_row[cta * kWarps + warp + 1];
+  const int th_max = h->th;
   const int slot0 = cta_slot[cta];
 
   if (tid == 0) {
     int n = 0;
-    for (int kk = cta_kf[cta]; kk < nkf && kfs[kk].tile_begin < te && n < kMaxSeg; ++kk) {
+    for (int kk = cta_kf[cta]; kk < nkf && kfs[kk].row_begin < re && n < kMaxSeg; ++kk) {
       s_kf[n] = kfs[kk];
       Seg &s = s_seg[n];
       const Scalars *sc = kfs[kk].pl.sc;
@@ -1051,16 +1066,23 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
   bool alive = true;
 
   // One pass over the CTA's tiles, then slots, barrier and per-keyframe sums.
-  auto run_pass = [&](int kind, int it, bool final_scale) -> bool {
+  auto run_pass = [&](int kind, int it, bool final_scale) __attribute__((always_inline)) -> bool {
     for (int q = tid; q < kWarps * kMaxSeg * kQ; q += kThreads) (&s_acc[0][0][0])[q] = ff2{0.0f, 0.0f};
     __syncthreads();
     int seg = 0;
-    for (int tile = tb + warp; tile < te; tile += kWarps) {
-      while (tile >= s_kf[seg].tile_begin + s_kf[seg].ntiles) ++seg;
+    RowRing rg = ring;  // the ring's phase bits stay in registers for the pass
+    // the warp walks its share [wb, we) of the concatenated strip rows in
+    // pieces that end at a strip's last row (or after th_max rows)
+    for (int pos = wb; pos < we;) {
+      while (pos >= s_kf[seg].row_begin + s_kf[seg].rows) ++seg;
       const FusedKf &K = s_kf[seg];
+      const int H = K.pl.H, rel = pos - K.row_begin, sx = rel / H, r0 = rel - sx * H;
+      int nrows = min(H - r0, we - pos);
+      if (th_max > 0) nrows = min(nrows, th_max);
+      pos += nrows;
       const Seg &S = s_seg[seg];
       if (!S.active) continue;
-      const int lt = tile - K.tile_begin;
+      const Geo g = geo_of<VEC>(sx * 32 * VEC, r0, nrows);
       float a[kQ] = {0.0f, 0.0f, 0.0f};
       const float ft = (float)S.t, fa = (float)S.alpha, fb = (float)S.beta;
       float *R0 = K.pl.v[1], *R1 = K.pl.v[2], *S0 = K.pl.v[3], *S1 = K.pl.v[4];
@@ -1072,29 +1094,29 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
         bool ok = true;
         switch (kind) {
           case P_SCALE:
-            ok = tma_scale_tile(ring, K, lt, ft, c, a);
+            ok = tma_scale_tile(rg, K, g, ft, c, a);
             break;
           case P_ASSEMBLE:
             if (K.pl.dtype == DF_BF16)
-              ok = tma_assemble_tile<DF_BF16>(ring, K, lt, ft, c, a);
+              ok = tma_assemble_tile<DF_BF16>(rg, K, g, ft, c, a);
             else if (K.pl.dtype == DF_F16)
-              ok = tma_assemble_tile<DF_F16>(ring, K, lt, ft, c, a);
+              ok = tma_assemble_tile<DF_F16>(rg, K, g, ft, c, a);
             else
-              ok = tma_assemble_tile<DF_F32>(ring, K, lt, ft, c, a);
+              ok = tma_assemble_tile<DF_F32>(rg, K, g, ft, c, a);
             break;
           case P_INIT:
-            if (!S.stop) ok = tma_cg_tile<0>(ring, K, lt, 0.0f, 0.0f, R0, S0, W1, R1, S1, W0, a);
+            if (!S.stop) ok = tma_cg_tile<0>(rg, K, g, 0.0f, 0.0f, R0, S0, W1, R1, S1, W0, a);
             break;
           case P_ITER:
             if (!S.stop) {
               if (it == 0)
-                ok = tma_cg_tile<1>(ring, K, lt, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
+                ok = tma_cg_tile<1>(rg, K, g, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
               else
-                ok = tma_cg_tile<2>(ring, K, lt, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
+                ok = tma_cg_tile<2>(rg, K, g, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
             }
             break;
           default:  // P_FINAL
-            ok = tma_final_tile(ring, K, lt, it == 0, !S.stop, fa, fb, final_scale, ft, c, Rc, Sp,
+            ok = tma_final_tile(rg, K, g, it == 0, !S.stop, fa, fb, final_scale, ft, c, Rc, Sp,
                                 Wc, a);
             break;
         }
@@ -1105,29 +1127,29 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       } else {
       switch (kind) {
         case P_SCALE:
-          scale_tile<VEC>(K, lt, ft, c, a);
+          scale_tile<VEC>(K, g, ft, c, a);
           break;
         case P_ASSEMBLE:
           if (K.pl.dtype == DF_BF16)
-            assemble_tile<VEC, DF_BF16>(K, lt, ft, c, a);
+            assemble_tile<VEC, DF_BF16>(K, g, ft, c, a);
           else if (K.pl.dtype == DF_F16)
-            assemble_tile<VEC, DF_F16>(K, lt, ft, c, a);
+            assemble_tile<VEC, DF_F16>(K, g, ft, c, a);
           else
-            assemble_tile<VEC, DF_F32>(K, lt, ft, c, a);
+            assemble_tile<VEC, DF_F32>(K, g, ft, c, a);
           break;
         case P_INIT:
-          if (!S.stop) cg_tile<VEC, 0>(K, lt, 0.0f, 0.0f, R0, S0, W1, R1, S1, W0, a);
+          if (!S.stop) cg_tile<VEC, 0>(K, g, 0.0f, 0.0f, R0, S0, W1, R1, S1, W0, a);
           break;
         case P_ITER:
           if (!S.stop) {
             if (it == 0)
-              cg_tile<VEC, 1>(K, lt, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
+              cg_tile<VEC, 1>(K, g, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
             else
-              cg_tile<VEC, 2>(K, lt, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
+              cg_tile<VEC, 2>(K, g, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
           }
           break;
         default:  // P_FINAL
-          final_tile<VEC>(K, lt, it == 0, !S.stop, fa, fb, final_scale, ft, c, Rc, Sp, Wc, a);
+          final_tile<VEC>(K, g, it == 0, !S.stop, fa, fb, final_scale, ft, c, Rc, Sp, Wc, a);
           break;
       }
       }
@@ -1137,6 +1159,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
         if (lane == 0) s_acc[warp][seg][q] = ff_add(s_acc[warp][seg][q], dq);
       }
     }
+    ring = rg;
     __syncthreads();
     // Push the CTA's sum for each keyframe into the inbox of every CTA of
     // that keyframe (one slot per writer), then read only the own inbox
@@ -1336,7 +1359,7 @@ int streaming_max_ctas() {
 
 static size_t streaming_bytes(int nkf, int G, size_t inbox) {
   size_t off = align16(sizeof(PlanHeader));
-  off += align16(sizeof(int) * (size_t)(G + 1));
+  off += align16(sizeof(int) * ((size_t)G * kWarps + 1));
   off += align16(sizeof(int) * (size_t)G);
   off += align16(sizeof(int) * (size_t)G);
   off += align16(sizeof(FusedKf) * (size_t)nkf);
@@ -1366,58 +1389,50 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   if (vec != 1 && vec != 4) vec = (rows4 >= 8LL * cap_of[1] * kWarps) ? 4 : 1;
   const int G_cap = std::max(1, std::min(tune.max_ctas > 0 ? tune.max_ctas : cap_of[vec == 4],
                                          cap_of[vec == 4]));
-  const long long warps = (long long)G_cap * kWarps;
-  const long long rows = vec == 4 ? rows4 : rows1;
-  int th = tune.tile_rows;
-  if (th <= 0) {
-    // about one tile per warp; VEC = 4 tiles walk long columns (their halo
-    // rows cost 2 / th), VEC = 1 tiles stay short (latency-bound sizes)
-    th = (int)(vec == 4 ? std::max<long long>(4, std::min<long long>(256, rows / warps))
-                        : std::max<long long>(1, std::min<long long>(32, rows / warps)));
-  }
-  // tiles per keyframe: rows split into bands of near-equal height ~th
-  std::vector<int> tb(n + 1, 0), tx(n), nt(n), thk(n);
-  for (int k = 0; k < n; ++k) {
-    const int H = kfs[k]->H;
-    const int nty = std::max(1, (H + th / 2) / th);
-    thk[k] = (H + nty - 1) / nty;
-    tx[k] = (kfs[k]->W + 32 * vec - 1) / (32 * vec);
-    nt[k] = tx[k] * ((H + thk[k] - 1) / thk[k]);
-    tb[k + 1] = tb[k] + nt[k];
-  }
-  const int T = tb[n];
-  int G = std::min(G_cap, std::max(1, (T + kWarps - 1) / kWarps));
+  // Work list: every keyframe's strips (one column tile of 32 * VEC
+  // columns over all H rows) concatenated in keyframe order. Each CTA takes
+  // a contiguous share of these rows and splits it evenly over its warps, so
+  // every warp walks about the same number of rows whatever the keyframes'
+  // shapes; a piece of a warp ends at a strip's last row (or after
+  // tile_rows rows, when set).
+  std::vector<long long> rb(n + 1, 0);
+  for (int k = 0; k < n; ++k)
+    rb[k + 1] = rb[k] + (long long)((kfs[k]->W + 32 * vec - 1) / (32 * vec)) * kfs[k]->H;
+  const long long R = rb[n];
+  if (R > (long long)INT32_MAX / 2) return false;
+  const int th_max = tune.tile_rows > 0 ? tune.tile_rows : 0;
+  // at least min_rows rows per warp: fewer CTAs for small work (a cheaper
+  // grid barrier); VEC = 4 warps need a few rows to fill their copy ring
+  const long long min_rows = std::max<long long>(vec == 4 ? 4 : 1, th_max);
+  int G = (int)std::min<long long>(G_cap, std::max<long long>(1, (R + min_rows * kWarps - 1) /
+                                                                      (min_rows * kWarps)));
   if (tune.max_ctas > 0) G = std::min(G, tune.max_ctas);
-  // contiguous tile ranges, balanced, at most kMaxSeg keyframes each
-  std::vector<int> ct(G + 1, T), ck(G, 0);
+  std::vector<int> wr((size_t)G * kWarps + 1, (int)R), ck(G, n);
   {
-    int tile = 0, kf = 0;
+    long long pos = 0;
+    int kf = 0;
     for (int cI = 0; cI < G; ++cI) {
-      ct[cI] = tile;
-      while (kf < n && tb[kf + 1] <= tile) ++kf;
+      while (kf < n && rb[kf + 1] <= pos) ++kf;
       ck[cI] = kf;
-      const int left = T - tile, ctas_left = G - cI;
-      const int target = (left + ctas_left - 1) / ctas_left;
-      int end = std::min(T, tile + target);
-      // cap the number of keyframes touched
-      int kk = kf, segs = 0;
-      while (kk < n && tb[kk] < end) {
-        ++segs;
-        if (segs > kMaxSeg) {
-          end = tb[kk];
+      const long long left = R - pos, ctas_left = G - cI;
+      long long end = std::min(R, pos + (left + ctas_left - 1) / ctas_left);
+      // cap the number of keyframes a CTA touches
+      int segs = 0;
+      for (int kk = kf; kk < n && rb[kk] < end; ++kk) {
+        if (++segs > kMaxSeg) {
+          end = rb[kk];
           break;
         }
-        ++kk;
       }
-      tile = end;
+      for (int w = 0; w < kWarps; ++w) wr[(size_t)cI * kWarps + w] = (int)(pos + (end - pos) * w / kWarps);
+      pos = end;
     }
-    if (tile != T) return false;  // does not fit: the caller splits the batch
-    ct[G] = T;
+    if (pos != R) return false;  // does not fit: the caller splits the batch
   }
   // drop empty trailing CTAs
-  while (G > 1 && ct[G - 1] == T) --G;
-  ct.resize(G + 1);
-  ct[G] = T;
+  while (G > 1 && wr[(size_t)(G - 1) * kWarps] == R) --G;
+  wr.resize((size_t)G * kWarps + 1);
+  wr[(size_t)G * kWarps] = (int)R;
   ck.resize(G);
   // slots: one per (CTA, keyframe segment), in CTA order
   std::vector<int> cs(G);
@@ -1425,8 +1440,9 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   int ns = 0;
   for (int cI = 0; cI < G; ++cI) {
     cs[cI] = ns;
-    for (int kk = ck[cI]; kk < n && tb[kk] < ct[cI + 1]; ++kk) {
-      if (tb[kk + 1] <= ct[cI]) continue;
+    const long long c_beg = wr[(size_t)cI * kWarps], c_end = wr[(size_t)(cI + 1) * kWarps];
+    for (int kk = ck[cI]; kk < n && rb[kk] < c_end; ++kk) {
+      if (rb[kk + 1] <= c_beg) continue;
       if (sb[kk] < 0) {
         sb[kk] = ns;
         wc[kk] = cI;
@@ -1444,8 +1460,8 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   char *base = out.data();
   PlanHeader *hd = reinterpret_cast<PlanHeader *>(base);
   size_t off = align16(sizeof(PlanHeader));
-  hd->off_cta_tile = (long long)off;
-  off += align16(sizeof(int) * (size_t)(G + 1));
+  hd->off_cta_work = (long long)off;
+  off += align16(sizeof(int) * ((size_t)G * kWarps + 1));
   hd->off_cta_kf = (long long)off;
   off += align16(sizeof(int) * (size_t)G);
   hd->off_cta_slot = (long long)off;
@@ -1458,12 +1474,13 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   hd->debug_skip_cta = tune.debug_skip_cta;
   hd->nkf = n;
   hd->G = G;
-  hd->ntiles = T;
+  hd->ntiles = (int)R;  // rows of the work list
+  hd->th = th_max;
   hd->nslots = nslots;
   hd->slot_stride = (long long)inbox;
   hd->vec = vec;
   hd->bytes = (long long)out.size();
-  memcpy(base + hd->off_cta_tile, ct.data(), sizeof(int) * (G + 1));
+  memcpy(base + hd->off_cta_work, wr.data(), sizeof(int) * wr.size());
   memcpy(base + hd->off_cta_kf, ck.data(), sizeof(int) * G);
   memcpy(base + hd->off_cta_slot, cs.data(), sizeof(int) * G);
   FusedKf *fk = reinterpret_cast<FusedKf *>(base + hd->off_kf);
@@ -1472,10 +1489,8 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
     fk[k].inbox0 = ib;
     ib += (long long)(se[k] - sb[k]) * inbox_slots(se[k] - sb[k]);
     fk[k].pl = *kfs[k];
-    fk[k].tile_begin = tb[k];
-    fk[k].ntiles = nt[k];
-    fk[k].tiles_x = tx[k];
-    fk[k].th = thk[k];
+    fk[k].row_begin = (int)rb[k];
+    fk[k].rows = (int)(rb[k + 1] - rb[k]);
     fk[k].slot_begin = sb[k];
     fk[k].slot_end = se[k];
     fk[k].writer_cta = wc[k];

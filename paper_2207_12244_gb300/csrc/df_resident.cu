@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = h->G;
   const char *hb = reinterpret_cast<const char *>(h);
-  const ResCta *ctas = reinterpret_cast<const ResCta *>(hb + h->off_cta_tile);
+  const ResCta *ctas = reinterpret_cast<const ResCta *>(hb + h->off_cta_work);
   const ResKf *kfs = reinterpret_cast<const ResKf *>(hb + h->off_kf);
   Slot *slots = reinterpret_cast<Slot *>(reinterpret_cast<char *>(h) + h->off_slots);
   const ResCta me = ctas[blockIdx.x];
@@ -664,7 +664,7 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
   char *base = out.data();
   PlanHeader *hd = reinterpret_cast<PlanHeader *>(base);
   size_t off = align16(sizeof(PlanHeader));
-  hd->off_cta_tile = (long long)off;
+  hd->off_cta_work = (long long)off;
   off += align16(sizeof(ResCta) * (size_t)G);
   hd->off_kf = (long long)off;
   off += align16(sizeof(ResKf) * (size_t)n);
@@ -679,7 +679,7 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
   hd->th = stride;  // shared-memory stride of one band array
   hd->smem_bytes = (int)smem;
   hd->bytes = (long long)out.size();
-  memcpy(base + hd->off_cta_tile, ctas.data(), sizeof(ResCta) * G);
+  memcpy(base + hd->off_cta_work, ctas.data(), sizeof(ResCta) * G);
   memcpy(base + hd->off_kf, rk.data(), sizeof(ResKf) * n);
   shape.kind = kPlanResident;
   shape.G = G;

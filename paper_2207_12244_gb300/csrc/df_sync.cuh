@@ -13,10 +13,14 @@ enum : int { kPlanStreaming = 0, kPlanResident = 1 };
 struct PlanHeader {
   int kind;        // kPlanStreaming / kPlanResident
   int nkf, G, ntiles, nslots;
-  int vec, th;
+  int vec;
+  int th;  // streaming: longest piece a warp walks at once (0: no limit);
+           // resident: shared-memory stride of a band array
   int debug_skip_cta;  // test hook: this CTA leaves without arriving (-1: none)
   unsigned int bar_count, bar_gen, exit_count, abort;
-  long long off_cta_tile, off_cta_kf, off_cta_slot, off_kf, off_slots;
+  // off_cta_work: per-CTA work table (streaming: the G * 8 + 1 warp row
+  // starts; resident: one band descriptor per CTA)
+  long long off_cta_work, off_cta_kf, off_cta_slot, off_kf, off_slots;
   long long bytes;
   int smem_bytes;  // dynamic shared memory per CTA (resident plans)
   int pad1;

@@ -87,26 +87,23 @@ struct RowRing {
     return smem + s * kStageBytes + p * kSlotBytes;
   }
 
-  // Stage row 'row' of the tile starting at column c0 (pitch P elements).
-  __device__ __forceinline__ void issue(int s, const StagePlane *pl, int np, size_t row, int c0,
-                                        int P) {
+  // Stage the planes of 'mask' (bit p: plane p) of a row: plane p's copy
+  // starts at src[p]; planes of 'half' (16-bit) copy b2 bytes to slot
+  // offset d2, the others (f32) b4 bytes to offset d4.
+  template <int NP>
+  __device__ __forceinline__ void issue(int s, const char *const (&src)[NP], uint32_t half,
+                                        uint32_t b4, uint32_t d4, uint32_t b2, uint32_t d2,
+                                        uint32_t mask) {
     if ((threadIdx.x & 31) == 0) {
-      uint32_t total = 0;
-      int cs[kMaxStagePlanes], ce[kMaxStagePlanes];
-      for (int p = 0; p < np; ++p) {
-        const int he = 16 / pl[p].esize;
-        cs[p] = c0 - he > 0 ? c0 - he : 0;
-        ce[p] = c0 + 128 + he < P ? c0 + 128 + he : P;
-        total += (uint32_t)((ce[p] - cs[p]) * pl[p].esize);
-      }
+      const uint32_t n2 = __popc(mask & half), n4 = __popc(mask & ~half);
       fence_proxy_async_shared();  // earlier generic reads of this stage come first
-      mbar_arrive_expect_tx(&bars[s], total);
-      for (int p = 0; p < np; ++p) {
-        const int he = 16 / pl[p].esize;
-        const char *src = static_cast<const char *>(pl[p].base) +
-                          (row * (size_t)P + (size_t)cs[p]) * pl[p].esize;
-        char *dst = slot(s, p) + (cs[p] - (c0 - he)) * pl[p].esize;
-        bulk_copy_g2s(dst, src, (uint32_t)((ce[p] - cs[p]) * pl[p].esize), &bars[s]);
+      mbar_arrive_expect_tx(&bars[s], n4 * b4 + n2 * b2);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        if (mask & (1u << p)) {
+          const bool h = (half >> p) & 1u;
+          bulk_copy_g2s(slot(s, p) + (h ? d2 : d4), src[p], h ? b2 : b4, &bars[s]);
+        }
       }
     }
     pending |= 1u << s;
