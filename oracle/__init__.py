@@ -27,6 +27,7 @@ _LOCK = threading.Lock()
 TERM_SEMI, TERM_NET, TERM_GRAD = 1, 2, 4
 TERMS_ALL = TERM_SEMI | TERM_NET | TERM_GRAD
 LOSS_HUBER, LOSS_TUKEY = 0, 1
+SCALE_FIXED, SCALE_ALTERNATE, SCALE_JOINT = 0, 1, 2
 HUBER_DELTA = 1.345
 
 
@@ -169,8 +170,12 @@ class Oracle:
     # -- the per-frame solve -------------------------------------------------
     def optimise(self, kf, x0=None, t0: float = 0.0, n_gn: int = 10, n_pcg: int = 3,
                  delta: float = HUBER_DELTA, tol: float = 0.0, terms: int = TERMS_ALL,
-                 loss: int = LOSS_HUBER, scale_step: bool = True, trace: bool = False):
+                 loss: int = LOSS_HUBER, scale_step: int = SCALE_ALTERNATE, trace: bool = False):
         """Run the schedule from (x0, t0); x0 defaults to mu_n (keyframe init).
+
+        scale_step: SCALE_FIXED (t kept), SCALE_ALTERNATE (scale half, then
+        depth half, per GN iteration) or SCALE_JOINT (bordered PCG in (x, t));
+        True / False mean SCALE_ALTERNATE / SCALE_FIXED.
 
         Returns (x [H, W] float64, t, Report[, cost trace of 2*n_gn+1 values]).
         """
@@ -178,7 +183,7 @@ class Oracle:
         x = _f64(kf.mu_n if x0 is None else x0).copy()
         t = C.c_double(float(t0))
         prm = _Params(int(n_gn), int(n_pcg), float(delta), float(tol), int(terms),
-                      int(loss), 1 if scale_step else 0)
+                      int(loss), int(scale_step))
         rep = _Report()
         tr = np.zeros(2 * int(n_gn) + 1) if trace else None
         self.lib.orc_optimise(C.byref(prob), _dp(x), C.byref(t), C.byref(prm), C.byref(rep),

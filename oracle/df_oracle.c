@@ -44,6 +44,8 @@
  *   - term selection (semi / network / gradient) for the ablations of
  *     Tables II and III;
  *   - the Tukey biweight as an alternative robust loss (Section IV);
+ *   - a joint variant of each GN iteration: instead of alternating, one
+ *     Jacobi-PCG solve of the bordered normal equations in (x, t);
  *   - the semi-dense depth -> log-depth conversion of Section II-B
  *     (first order: mu = ln d, V = sigma_d^2 / d^2).
  *
@@ -87,7 +89,8 @@ typedef struct {
   double tol;         /* 0: fixed iteration count */
   int32_t terms;      /* ORC_TERM_* bits */
   int32_t loss;       /* ORC_LOSS_* */
-  int32_t scale_step; /* 1: run the scale half of each GN iteration */
+  int32_t scale_step; /* 0: t fixed; 1: scale half, then depth half, in each GN
+                         iteration; 2: one PCG on the bordered system in (x, t) */
 } orc_params;
 
 typedef struct {
@@ -350,6 +353,104 @@ int32_t orc_pcg(int32_t W, int32_t H, const double *diag, const double *wx,
   return it;
 }
 
+/* Joint variant of the depth step (scale_step = 2): with the weights fixed,
+ * the re-weighted quadratic in y = (x, t) has the bordered normal equations
+ *
+ *   [  A     -ws ] [x]   [ b - ws t ]
+ *   [ -ws^T   S  ] [t] = [ -ws.mu_s ],     S = sum_i ws_i,
+ *
+ * (A, b as in orc_assemble, whose b includes ws (t + mu_s); ws the semi
+ * weights). Jacobi-preconditioned CG on this (N+1)-system from the current
+ * (x, t), with preconditioner diag(A, S); when S = 0 the last row is empty
+ * and t keeps its value. Dot products run over all N+1 components. */
+int32_t orc_pcg_joint(int32_t W, int32_t H, const double *diag, const double *wx,
+                      const double *wy, const double *ws, const double *mu_s,
+                      const double *b, double *x, double *t, int32_t n_pcg, double tol,
+                      double *res_norm) {
+  const int N = W * H;
+  double *r = (double *)malloc(sizeof(double) * (size_t)N);
+  double *z = (double *)malloc(sizeof(double) * (size_t)N);
+  double *p = (double *)malloc(sizeof(double) * (size_t)N);
+  double *q = (double *)malloc(sizeof(double) * (size_t)N);
+  double S = 0.0, bt = 0.0, bb = 0.0;
+  for (int i = 0; i < N; ++i) {
+    if (ws[i] == 0.0) continue;
+    S += ws[i];
+    bt -= ws[i] * mu_s[i];
+  }
+  /* r = rhs - K y */
+  orc_apply(W, H, diag, wx, wy, x, q);
+  double rt = bt - S * (*t);
+  for (int i = 0; i < N; ++i) {
+    r[i] = b[i] - q[i];             /* (b - ws t) - (A x - ws t) */
+    if (ws[i] != 0.0) rt += ws[i] * x[i];
+    const double b0 = b[i] - ws[i] * (*t);
+    bb += b0 * b0;
+  }
+  bb += bt * bt;
+  const double bnorm = tol > 0.0 ? sqrt(bb) : 0.0;
+  for (int i = 0; i < N; ++i) {
+    z[i] = r[i] / diag[i];
+    p[i] = z[i];
+  }
+  double zt = S > 0.0 ? rt / S : 0.0, pt = zt;
+  double rho0 = dot(r, z, N) + rt * zt;
+  int32_t it = 0;
+  int converged = tol > 0.0 && sqrt(dot(r, r, N) + rt * rt) < tol * bnorm;
+  for (int j = 0; j < n_pcg && !converged; ++j) {
+    /* q = K p */
+    orc_apply(W, H, diag, wx, wy, p, q);
+    double wp = 0.0;
+    for (int i = 0; i < N; ++i) {
+#if ORC_MUTANT == 10
+      q[i] += ws[i] * pt;
+#else
+      q[i] -= ws[i] * pt;
+#endif
+      wp += ws[i] * p[i];
+    }
+    const double qt = -wp + S * pt;
+    const double gamma = dot(p, q, N) + pt * qt;
+    if (gamma <= 0.0 || rho0 == 0.0) break;
+    const double alpha = rho0 / gamma;
+    for (int i = 0; i < N; ++i) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * q[i];
+    }
+    *t += alpha * pt;
+    rt -= alpha * qt;
+    ++it;
+    if (tol > 0.0 && sqrt(dot(r, r, N) + rt * rt) < tol * bnorm) break;
+    for (int i = 0; i < N; ++i) z[i] = r[i] / diag[i];
+    zt = S > 0.0 ? rt / S : 0.0;
+    const double rho1 = dot(r, z, N) + rt * zt;
+    const double beta = rho1 / rho0;
+    for (int i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    pt = zt + beta * pt;
+    rho0 = rho1;
+  }
+  if (res_norm) *res_norm = sqrt(dot(r, r, N) + rt * rt);
+  free(r);
+  free(z);
+  free(p);
+  free(q);
+  return it;
+}
+
+/* Semi-dense weights ws_i = omega(u_i)/Vs_i at (x, t) (0 off the mask or when
+ * the semi term is off): the same weights orc_assemble puts on its diagonal. */
+static void semi_weights(const orc_problem *P, const double *x, double t, double delta,
+                         int32_t terms, int32_t loss, double *ws) {
+  const int N = P->width * P->height;
+  for (int i = 0; i < N; ++i) {
+    ws[i] = 0.0;
+    if ((terms & ORC_TERM_SEMI) && semi_ok(P, i)) {
+      double r = x[i] - t - P->mu_s[i];
+      ws[i] = orc_omega(r / sqrt(P->var_s[i]), delta, loss) / P->var_s[i];
+    }
+  }
+}
+
 /* The whole per-frame solve: n_gn x (scale step, depth step). x and t are
  * the warm start on entry and the result on exit. If cost_trace is not NULL
  * it receives 2*n_gn+1 costs: at entry, after each scale step and after each
@@ -364,13 +465,20 @@ int32_t orc_optimise(const orc_problem *P, double *x, double *t,
   int32_t iters = 0;
   double rn = 0.0;
   if (cost_trace) cost_trace[0] = orc_cost(P, x, *t, prm->delta, prm->terms, prm->loss);
+  const int joint = prm->scale_step == 2 && (prm->terms & ORC_TERM_SEMI);
+  double *ws = joint ? (double *)malloc(sizeof(double) * (size_t)N) : NULL;
   for (int k = 0; k < prm->n_gn; ++k) {
-    if ((prm->terms & ORC_TERM_SEMI) && prm->scale_step)
+    if ((prm->terms & ORC_TERM_SEMI) && prm->scale_step == 1)
       *t = orc_scale_step(P, x, *t, prm->delta, prm->loss);
     if (cost_trace)
       cost_trace[2 * k + 1] = orc_cost(P, x, *t, prm->delta, prm->terms, prm->loss);
     orc_assemble(P, x, *t, prm->delta, prm->terms, prm->loss, diag, wx, wy, b);
-    iters += orc_pcg(W, H, diag, wx, wy, b, x, prm->n_pcg, prm->tol, &rn);
+    if (joint) {
+      semi_weights(P, x, *t, prm->delta, prm->terms, prm->loss, ws);
+      iters += orc_pcg_joint(W, H, diag, wx, wy, ws, P->mu_s, b, x, t, prm->n_pcg, prm->tol, &rn);
+    } else {
+      iters += orc_pcg(W, H, diag, wx, wy, b, x, prm->n_pcg, prm->tol, &rn);
+    }
     if (cost_trace)
       cost_trace[2 * k + 2] = orc_cost(P, x, *t, prm->delta, prm->terms, prm->loss);
   }
@@ -379,6 +487,7 @@ int32_t orc_optimise(const orc_problem *P, double *x, double *t,
     rep->res_norm = rn;
     rep->iters_done = iters;
   }
+  free(ws);
   free(diag);
   free(wx);
   free(wy);

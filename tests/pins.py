@@ -214,11 +214,10 @@ def dense_hessian(o):
     assert np.allclose(x2.ravel(), xs, rtol=0, atol=1e-10 * np.abs(xs).max())
 
 
-def joint_optimum(o):
-    W, H = 6, 5
-    kf = _noisy(W, H, 8)
-    N = W * H
-    # bordered Hessian over (x, t) by second differences of the L2 cost
+def _bordered(o, kf):
+    """Hessian/2 and -gradient/2 at 0 of the least-squares cost over (x, t),
+    by exact second differences of the cost (a quadratic)."""
+    N = kf.width * kf.height
     c = lambda y: o.cost(kf, y[:N], y[N], INF)
     n = N + 1
     e = np.eye(n)
@@ -234,11 +233,60 @@ def joint_optimum(o):
             else:
                 A[j, k] = A[k, j] = (c(e[j] + e[k]) - ce[j] - ce[k] + c0) / 2.0
     b = -(ce - cm) / 4.0
+    return A, b
+
+
+def joint_optimum(o):
+    W, H = 6, 5
+    kf = _noisy(W, H, 8)
+    N = W * H
+    A, b = _bordered(o, kf)
     ys = np.linalg.solve(A, b)
     np.linalg.cholesky(A)  # positive definite: the minimiser is unique
     x, t, rep = o.optimise(kf, n_gn=400, n_pcg=200, delta=INF)
     assert abs(t - ys[N]) < 1e-9, (t, ys[N])
     assert np.allclose(x.ravel(), ys[:N], rtol=0, atol=1e-9)
+
+
+def joint_bordered(o):
+    """The joint variant runs Jacobi-PCG on the bordered system itself: its
+    first iterations equal textbook PCG on the (x, t) Hessian of the cost
+    (built here from the cost alone), and it reaches that system's solution."""
+    W, H = 6, 5
+    kf = _noisy(W, H, 12)
+    N = W * H
+    K, b = _bordered(o, kf)
+    ys = np.linalg.solve(K, b)
+    rng = np.random.default_rng(4)
+    y0 = np.concatenate([kf.mu_n.ravel().astype(np.float64) + rng.normal(0, 0.1, N), [0.3]])
+    m = np.diag(K).copy()
+    y, r = y0.copy(), b - K @ y0
+    zv = r / m
+    p = zv.copy()
+    rho = r @ zv
+    for j in range(1, 4):
+        q = K @ p
+        a = rho / (p @ q)
+        y = y + a * p
+        r = r - a * q
+        x1, t1, rep = o.optimise(kf, x0=y0[:N], t0=y0[N], n_gn=1, n_pcg=j, delta=INF,
+                                 scale_step=orc.SCALE_JOINT)
+        assert rep.iters_done == j
+        assert abs(t1 - y[N]) < 1e-10, (j, t1, y[N])
+        assert np.allclose(x1.ravel(), y[:N], rtol=0, atol=1e-10), (j, np.abs(x1.ravel() - y[:N]).max())
+        zv = r / m
+        rho1 = r @ zv
+        p = zv + (rho1 / rho) * p
+        rho = rho1
+    x, t, rep = o.optimise(kf, x0=y0[:N], t0=y0[N], n_gn=1, n_pcg=4 * (N + 1), delta=INF,
+                           scale_step=orc.SCALE_JOINT)
+    assert abs(t - ys[N]) < 1e-10 and np.allclose(x.ravel(), ys[:N], rtol=0, atol=1e-10)
+    # without semi-dense pixels the border row is empty and t stays put
+    k0 = types.SimpleNamespace(**vars(kf))
+    k0.var_s = np.zeros_like(kf.var_s)
+    x0j, t0j, _ = o.optimise(k0, t0=0.25, n_gn=2, n_pcg=5, delta=INF, scale_step=orc.SCALE_JOINT)
+    x0a, t0a, _ = o.optimise(k0, t0=0.25, n_gn=2, n_pcg=5, delta=INF, scale_step=orc.SCALE_FIXED)
+    assert t0j == 0.25 and np.allclose(x0j, x0a, rtol=0, atol=1e-13)
 
 
 def prior_only(o):
@@ -297,6 +345,11 @@ def huber_scipy(o):
                    options={"gtol": 1e-10, "maxiter": 20000})
     assert f(y_irls) <= res.fun + 1e-9 * max(1.0, abs(res.fun)), (f(y_irls), res.fun)
     assert np.allclose(y_irls, res.x, rtol=0, atol=1e-5), np.abs(y_irls - res.x).max()
+    # the joint (x, t) variant of the GN iteration reaches the same minimiser
+    xj, tj, _ = o.optimise(kf, n_gn=400, n_pcg=60, delta=DELTA, scale_step=orc.SCALE_JOINT)
+    yj = np.concatenate([xj.ravel(), [tj]])
+    assert f(yj) <= res.fun + 1e-9 * max(1.0, abs(res.fun)), (f(yj), res.fun)
+    assert np.allclose(yj, res.x, rtol=0, atol=1e-5), np.abs(yj - res.x).max()
     # Huber must actually be active somewhere for this pin to mean anything
     assert abs(o.cost(kf, x, t, DELTA) - o.cost(kf, x, t, INF)) > 1e-3
 
@@ -329,10 +382,12 @@ def monotone(o):
     for delta in (INF, DELTA):
         for x0 in (None, kf.mu_n.ravel() + rng.normal(0, 0.3, kf.n_pixels)):
             for npcg in (1, 3):
-                *_, tr = o.optimise(kf, x0=x0, n_gn=10, n_pcg=npcg, delta=delta, trace=True)
-                d = np.diff(tr)
-                assert np.all(d <= 1e-12 * tr[0]), (delta, npcg, d.max())
-                assert tr[-1] < tr[0]
+                for mode in (orc.SCALE_ALTERNATE, orc.SCALE_JOINT):
+                    *_, tr = o.optimise(kf, x0=x0, n_gn=10, n_pcg=npcg, delta=delta, trace=True,
+                                        scale_step=mode)
+                    d = np.diff(tr)
+                    assert np.all(d <= 1e-12 * tr[0]), (delta, npcg, mode, d.max())
+                    assert tr[-1] < tr[0]
 
 
 def no_pairwise(o):
@@ -370,5 +425,5 @@ def semi_to_log(o):
     assert np.all(mu[4:] == 0) and np.all(var[4:] == 0)
 
 
-ALL = [cost_closed_form, robust_weight, dense_hessian, joint_optimum, prior_only,
+ALL = [cost_closed_form, robust_weight, dense_hessian, joint_optimum, joint_bordered, prior_only,
        planar_recovery, huber_scipy, invariances, monotone, no_pairwise, semi_to_log]

@@ -5,7 +5,8 @@ that plants a plausible error: a dropped neighbour weight on the diagonal,
 a flipped sign in b, the wrong gradient plane in a weight, a reversed
 gradient residual, a wrong Huber weight, a flipped scale step, a wrong
 neighbour index, an inverted CG beta, a residual divided by the variance
-instead of the standard deviation.
+instead of the standard deviation, a flipped sign of the x-t coupling in
+the joint solve.
 """
 import pytest
 
@@ -22,6 +23,7 @@ MUTANTS = {
     7: "south neighbour indexed i-1",
     8: "CG beta inverted",
     9: "semi residual divided by V",
+    10: "joint PCG couples x and t with the wrong sign",
 }
 
 
