@@ -72,6 +72,24 @@ typedef struct {
   int32_t cnn_dtype;  /* df_dtype of the six network planes */
 } df_keyframe_desc;
 
+/* df_solve_params.scale_step: how the log scale t = ln s is solved.
+ *  DF_SCALE_FIXED     t is kept (Table II's scale-ambiguous solve);
+ *  DF_SCALE_ALTERNATE each GN iteration first solves t with x fixed, then
+ *                     x with t fixed (Section II-C, last paragraph: the
+ *                     paper's alternation);
+ *  DF_SCALE_JOINT     each GN iteration runs Jacobi-PCG on the bordered
+ *                     normal equations in (x, t)
+ *                       [A, -ws; -ws^T, sum ws] [x; t] = [b - ws t; -ws.mu_s]
+ *                     (A, b: the depth step's 5-point system; ws: the
+ *                     semi-dense weights), preconditioned by diag(A) and
+ *                     sum ws. Not in the paper: a solver variant that needs
+ *                     no alternation. Runs on the launch solver only: with
+ *                     DF_SOLVER_FUSED the solve returns DF_ENOTSUP, with
+ *                     DF_SOLVER_AUTO it takes the launch solver. */
+#define DF_SCALE_FIXED 0
+#define DF_SCALE_ALTERNATE 1
+#define DF_SCALE_JOINT 2
+
 typedef struct {
   int32_t n_gn;       /* Gauss-Newton iterations; 10 in Section II-C */
   int32_t n_pcg;      /* PCG iterations per depth step (>= 0) */
@@ -79,8 +97,7 @@ typedef struct {
                          <= 0 or +inf gives plain least squares */
   int32_t loss;       /* DF_LOSS_* */
   int32_t terms;      /* DF_TERM_* bits; must include NET or GRAD */
-  int32_t scale_step; /* 1: solve the scale in each GN iteration (paper);
-                         0: keep t fixed (Table II's scale-ambiguous solve) */
+  int32_t scale_step; /* DF_SCALE_*: how t is solved (see below) */
   int32_t solver;     /* DF_SOLVER_* */
   double tol;         /* > 0: end a depth step once ||r|| < tol ||b||;
                          0: fixed iteration count */
@@ -174,6 +191,17 @@ df_status df_cost(df_keyframe *kf, const df_solve_params *params, void *stream,
  * least squares in log space: c = mean(mu_n - x), then x += c and t += c
  * (the semi-dense residuals x - t - mu_s are unchanged). Asynchronous. */
 df_status df_scale_fit_ls(df_keyframe *kf, void *stream);
+
+/* Accuracy metric of Section III-B (the measure of Tables I-III): counts
+ * the pixels whose estimated depth d = exp(x) lies within rel_tol of the
+ * ground truth, |d - d_true| <= rel_tol * d_true (rel_tol = 0.1 in the
+ * paper), among the pixels with a finite d_true > 0 (*n_valid); the paper's
+ * percentage is 100 * n_within / n_valid. depth_true: dense row-major H x W
+ * FP32 metric depth, host or device (ptr_on_device), caller-owned, read
+ * before return. The within decision is taken in FP64. Synchronous.
+ * Errors: DF_EINVAL for NULL pointers or a negative / non-finite rel_tol. */
+df_status df_depth_accuracy(df_keyframe *kf, const float *depth_true, int ptr_on_device,
+                            double rel_tol, void *stream, int64_t *n_within, int64_t *n_valid);
 
 /* Synchronise 'stream' and return DF_EINVAL if device-side input checks
  * flagged the keyframe, DF_ETIMEOUT if a fused solve gave up, else DF_OK. */

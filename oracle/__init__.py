@@ -108,6 +108,9 @@ class Oracle:
         L.orc_semi_to_log.argtypes = [C.c_int64, D, D, D, D]
         L.orc_ls_scale_fit.restype = None
         L.orc_ls_scale_fit.argtypes = [P, D, D]
+        L.orc_within.restype = None
+        L.orc_within.argtypes = [C.c_int64, D, D, C.c_double, C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int64)]
         self.lib = L
 
     # -- problem marshalling ------------------------------------------------
@@ -193,7 +196,8 @@ class Oracle:
         return out + (tr,) if trace else out
 
     def optimise_sequence(self, kf, mu_s_frames, var_s_frames, n_gn: int = 10, n_pcg: int = 5,
-                          delta: float = HUBER_DELTA, frames=None):
+                          delta: float = HUBER_DELTA, frames=None,
+                          scale_step: int = SCALE_ALTERNATE):
         """Warm-started per-frame re-optimisation (Section II, every new frame).
 
         Returns the (x, t) after the last processed frame.
@@ -208,9 +212,17 @@ class Oracle:
         idx = range(len(mu_s_frames)) if frames is None else frames
         for f in idx:
             v.mu_s, v.var_s = mu_s_frames[f], var_s_frames[f]
-            x, t, _ = self.optimise(v, x0=x, t0=t, n_gn=n_gn, n_pcg=n_pcg, delta=delta)
+            x, t, _ = self.optimise(v, x0=x, t0=t, n_gn=n_gn, n_pcg=n_pcg, delta=delta,
+                                    scale_step=scale_step)
             x = x.ravel()
         return x.reshape(kf.height, kf.width), t
+
+    def within(self, x, d_true, rel_tol: float = 0.1):
+        """(n_within, n_valid) of Section III-B's accuracy measure."""
+        xx, dd = _f64(x).ravel(), _f64(d_true).ravel()
+        a, b = C.c_int64(0), C.c_int64(0)
+        self.lib.orc_within(xx.size, _dp(xx), _dp(dd), float(rel_tol), C.byref(a), C.byref(b))
+        return a.value, b.value
 
     def depth(self, x) -> np.ndarray:
         xx = _f64(x)

@@ -527,3 +527,20 @@ void orc_ls_scale_fit(const orc_problem *P, double *x, double *t) {
   for (int i = 0; i < N; ++i) x[i] += c;
   *t = *t + c;
 }
+
+/* Accuracy measure of Section III-B (Tables I-III): among the pixels with a
+ * finite ground-truth depth g > 0 (*n_valid), count those whose estimate
+ * d = exp(x) satisfies |d - g| <= rel_tol * g (*n_within); the paper reports
+ * 100 * n_within / n_valid with rel_tol = 0.1. */
+void orc_within(int64_t n, const double *x, const double *d_true, double rel_tol,
+                int64_t *n_within, int64_t *n_valid) {
+  int64_t a = 0, b = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double g = d_true[i];
+    if (!(g > 0.0) || !isfinite(g)) continue;
+    ++b;
+    if (fabs(exp(x[i]) - g) <= rel_tol * g) ++a;
+  }
+  *n_within = a;
+  *n_valid = b;
+}

@@ -194,6 +194,8 @@ df_status check_params(const df_solve_params *p) {
     return fail(DF_EINVAL, "terms must be DF_TERM_* bits including NET or GRAD");
   if (p->solver < DF_SOLVER_AUTO || p->solver > DF_SOLVER_FUSED)
     return fail(DF_EINVAL, "unknown solver %d", p->solver);
+  if (p->scale_step < DF_SCALE_FIXED || p->scale_step > DF_SCALE_JOINT)
+    return fail(DF_EINVAL, "unknown scale_step %d", p->scale_step);
   if (!(p->tol >= 0.0) || !isfinite(p->tol)) return fail(DF_EINVAL, "tol must be finite >= 0");
   if (isnan(p->delta)) return fail(DF_EINVAL, "delta is NaN");
   return DF_OK;
@@ -436,9 +438,16 @@ static bool same_tuning(const df::FusedTuning &a, const df::FusedTuning &b) {
                                                                             // does not shape plans
 }
 
-static int pick_solver(int requested) {
-  if (requested != DF_SOLVER_AUTO) return requested;
+static int pick_solver(const df_solve_params &p) {
+  if (p.solver != DF_SOLVER_AUTO) return p.solver;
+  if (p.scale_step == DF_SCALE_JOINT) return DF_SOLVER_LAUNCHES;  // joint: launch solver only
   return df::fused_supported() ? DF_SOLVER_FUSED : DF_SOLVER_LAUNCHES;
+}
+
+static df_status check_joint(const df_solve_params &p) {
+  if (p.scale_step == DF_SCALE_JOINT && p.solver == DF_SOLVER_FUSED)
+    return fail(DF_ENOTSUP, "DF_SCALE_JOINT runs on the launch solver only");
+  return DF_OK;
 }
 
 // Fused solve of one keyframe: its launch plan lives in the keyframe's own
@@ -507,7 +516,7 @@ static df_status fused_many(df_keyframe *const *kfs, int n, const SolveCfg &c, i
 
 static df_status optimise_one(df_keyframe *kf, const df_solve_params *p, cudaStream_t s) {
   const SolveCfg c = cfg_of(p);
-  if (pick_solver(p->solver) == DF_SOLVER_FUSED) return fused_one(kf, c, p->n_gn, p->n_pcg, s);
+  if (pick_solver(*p) == DF_SOLVER_FUSED) return fused_one(kf, c, p->n_gn, p->n_pcg, s);
   DF_CUDA(cudaMemsetAsync(&kf->planes.sc->iters, 0, sizeof(int), s));
   DF_CUDA(cudaMemsetAsync(&kf->planes.sc->stop, 0, sizeof(int), s));
   DF_CUDA(df::launch_solve_launches(kf->planes, c, p->n_gn, p->n_pcg, s));
@@ -524,6 +533,7 @@ df_status df_optimise(df_keyframe *kf, const df_solve_params *params, void *stre
     df_default_params(&p);
   }
   df_status st = check_params(&p);
+  if (st == DF_OK) st = check_joint(p);
   if (st != DF_OK) return st;
   DeviceGuard g(kf->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -543,6 +553,7 @@ df_status df_optimise_batch(df_keyframe *const *kfs, int32_t n, const df_solve_p
     df_default_params(&p);
   }
   df_status st = check_params(&p);
+  if (st == DF_OK) st = check_joint(p);
   if (st != DF_OK) return st;
   for (int j = 0; j < n; ++j) {
     if (!kfs[j]) return fail(DF_EINVAL, "keyframe %d is NULL", j);
@@ -553,7 +564,7 @@ df_status df_optimise_batch(df_keyframe *const *kfs, int32_t n, const df_solve_p
   if (n == 0) return DF_OK;
   DeviceGuard g(kfs[0]->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (pick_solver(p.solver) == DF_SOLVER_FUSED) {
+  if (pick_solver(p) == DF_SOLVER_FUSED) {
     st = fused_many(kfs, n, cfg_of(&p), p.n_gn, p.n_pcg, s);
     if (st != DF_OK) return st;
   } else {
@@ -632,6 +643,27 @@ df_status df_cost(df_keyframe *kf, const df_solve_params *params, void *stream, 
   DF_CUDA(df::launch_cost(kf->planes, cfg_of(&p), s));
   DF_CUDA(cudaMemcpyAsync(cost_out, &kf->planes.sc->cost, sizeof(double), cudaMemcpyDeviceToHost, s));
   DF_CUDA(cudaStreamSynchronize(s));
+  return DF_OK;
+}
+
+df_status df_depth_accuracy(df_keyframe *kf, const float *depth_true, int ptr_on_device,
+                            double rel_tol, void *stream, int64_t *n_within, int64_t *n_valid) {
+  if (!kf || !depth_true || !n_within || !n_valid) return fail(DF_EINVAL, "NULL argument");
+  if (!(rel_tol >= 0.0) || !isfinite(rel_tol)) return fail(DF_EINVAL, "rel_tol must be finite >= 0");
+  DeviceGuard g(kf->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const float *dt = depth_true;
+  if (!ptr_on_device) {
+    DF_CUDA(cudaMemcpyAsync(kf->staging, depth_true, (size_t)kf->W * kf->H * 4,
+                            cudaMemcpyHostToDevice, s));
+    dt = kf->staging;
+  }
+  DF_CUDA(df::launch_accuracy(kf->planes, dt, rel_tol, s));
+  double h[2];
+  DF_CUDA(cudaMemcpyAsync(h, &kf->planes.sc->acc_in, sizeof h, cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  *n_within = (int64_t)h[0];
+  *n_valid = (int64_t)h[1];
   return DF_OK;
 }
 

@@ -1061,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
   }
   __syncthreads();
   const int nseg = s_nseg;
-  const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step;
+  const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step == DF_SCALE_ALTERNATE;
   int parity = 0;
   bool alive = true;
 

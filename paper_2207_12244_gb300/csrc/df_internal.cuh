@@ -26,7 +26,7 @@ constexpr int kPitchElems = 128;    // row pitch granularity (elements): a warp'
                                     // 32 x 4-element segment never crosses a row
 constexpr int kWorkPlanes = 8;      // solver vectors beyond diag / wx / wy
 constexpr int kMaxPartialBlocks = 4096;
-constexpr int kNumQ = 4;            // FP64 quantities per partial slot
+constexpr int kNumQ = 6;            // FP64 quantities per partial slot
 
 enum : int { kFlagBadInput = 1, kFlagTimeout = 2, kFlagBreakdown = 4 };
 
@@ -41,6 +41,12 @@ struct alignas(64) Scalars {
   double bb;      // b.b (relative tolerance)
   double gamma;   // p.Ap
   double cost;    // last cost evaluation
+  // joint (x, t) solve: the t components of the bordered PCG
+  double j_s;     // S = sum of the semi-dense weights (the border's diagonal)
+  double j_rt;    // residual
+  double j_pt;    // direction
+  double j_qt;    // operator applied to the direction
+  double acc_in, acc_valid;  // last accuracy count (df_depth_accuracy)
   int stop;       // the current depth step has ended early
   int iters;      // PCG iterations executed in the current solve
   int flags;      // kFlag* bits, sticky
@@ -66,7 +72,7 @@ struct SolveCfg {
   float delta;      // robust threshold on whitened residuals (<= 0 or inf: L2)
   int loss;         // DF_LOSS_*
   int terms;        // DF_TERM_* bits
-  int scale_step;   // 1: scale half of each GN iteration
+  int scale_step;   // DF_SCALE_*
   double tol;       // relative residual tolerance (0: fixed count)
 };
 
@@ -225,6 +231,7 @@ cudaError_t launch_solve_launches(const Planes &k, const SolveCfg &c, int n_gn, 
                                   cudaStream_t s);
 cudaError_t launch_fetch(const Planes &k, float *out, int log_space, cudaStream_t s);
 cudaError_t launch_cost(const Planes &k, const SolveCfg &c, cudaStream_t s);
+cudaError_t launch_accuracy(const Planes &k, const float *d_true, double rel_tol, cudaStream_t s);
 cudaError_t launch_set_x(const Planes &k, const float *x_dense, cudaStream_t s);
 cudaError_t launch_set_scale(const Planes &k, double t, cudaStream_t s);
 cudaError_t launch_ls_scale_fit(const Planes &k, cudaStream_t s);

@@ -114,7 +114,15 @@ __global__ void k_scale(Planes k, SolveCfg c) {
 // cancellation of forming b and A x separately:
 //   r_i = ws (t + mu_s - x_i) + wn (mu_n - x_i) + wx_i ex_i - wx_{i-1} ex_{i-1}
 //         + wy_i ey_i - wy_{i-W} ey_{i-W}.
-template <int DT>
+//
+// Joint variant (JOINT, scale_step = DF_SCALE_JOINT): the same weights give
+// the bordered system in y = (x, t)
+//   [ A     -ws ] [x]   [ b - ws t  ]
+//   [ -ws^T  S  ] [t] = [ -ws.mu_s  ],   S = sum ws,
+// whose residual at (x, t) is r (above) for the x rows and
+// r_t = sum ws (x - t - mu_s) for the border; ws is kept in v[4] for the
+// operator, and the preconditioner is diag(A) and S.
+template <int DT, bool JOINT>
 __global__ void k_assemble(Planes k, SolveCfg c) {
   if (k.sc->flags & kFlagBadInput) return;
   TileIter it(k.W, k.H);
@@ -123,6 +131,7 @@ __global__ void k_assemble(Planes k, SolveCfg c) {
              grad = c.terms & DF_TERM_GRAD;
   const size_t P = k.P;
   float rz = 0.0f, rr = 0.0f, bb = 0.0f;
+  float js = 0.0f, jrt = 0.0f, jbt = 0.0f;  // joint: sum ws, r_t, sum ws mu_s
   float *r_out = k.v[0];
   for (int tile = blockIdx.x; tile < it.ntiles; tile += gridDim.x) {
     int u, v;
@@ -135,7 +144,12 @@ __global__ void k_assemble(Planes k, SolveCfg c) {
       if (semi_valid(ms, vs)) {
         ws = robust_weight(xi - t - ms, vs, c.delta, c.loss);
         rs = ws * (t + ms - xi);
-        bs = ws * (t + ms);
+        bs = JOINT ? ws * ms : ws * (t + ms);
+        if (JOINT) {
+          js += ws;
+          jrt -= rs;
+          jbt += ws * ms;
+        }
       }
     }
     float wn = 0.0f, mn = 0.0f;
@@ -173,6 +187,7 @@ __global__ void k_assemble(Planes k, SolveCfg c) {
     k.wx[i] = wxi;
     k.wy[i] = wyi;
     r_out[i] = r;
+    if (JOINT) k.v[4][i] = ws;
     const float z = d > 0.0f ? r / d : 0.0f;
     rz += r * z;
     rr += r * r;
@@ -181,23 +196,48 @@ __global__ void k_assemble(Planes k, SolveCfg c) {
       bb += b * b;
     }
   }
-  double a[3] = {(double)rz, (double)rr, (double)bb}, out[3];
-  if (grid_sum_last_block<3>(a, k.partial, &k.sc->count, out)) {
-    k.sc->rho = out[0];
-    k.sc->rr = out[1];
-    k.sc->bb = out[2];
-    k.sc->stop = (c.tol > 0.0 && sqrt(out[1]) < c.tol * sqrt(out[2])) ? 1 : 0;
+  if constexpr (!JOINT) {
+    double a[3] = {(double)rz, (double)rr, (double)bb}, out[3];
+    if (grid_sum_last_block<3>(a, k.partial, &k.sc->count, out)) {
+      k.sc->rho = out[0];
+      k.sc->rr = out[1];
+      k.sc->bb = out[2];
+      k.sc->stop = (c.tol > 0.0 && sqrt(out[1]) < c.tol * sqrt(out[2])) ? 1 : 0;
+    }
+  } else {
+    double a[6] = {(double)rz, (double)rr, (double)bb, (double)js, (double)jrt, (double)jbt},
+           out[6];
+    if (grid_sum_last_block<6>(a, k.partial, &k.sc->count, out)) {
+      const double S = out[3], rt = out[4], zt = S > 0.0 ? rt / S : 0.0;
+      k.sc->j_s = S;
+      k.sc->j_rt = rt;
+      k.sc->rho = out[0] + rt * zt;
+      k.sc->rr = out[1] + rt * rt;
+      k.sc->bb = out[2] + out[5] * out[5];
+      k.sc->stop =
+          (c.tol > 0.0 && sqrt(k.sc->rr) < c.tol * sqrt(k.sc->bb)) ? 1 : 0;
+    }
   }
 }
 
 // ---- PCG direction: p_new = z + beta p_old (z = r / diag), q = A p_new -----
 // p_new at the four neighbours is recomputed from their r, diag, p_old, so
 // one launch both updates p and applies the stencil (p is double-buffered).
+// Joint: the direction's border component p_t = z_t + beta p_t (z_t = r_t / S)
+// enters q_x = A p_x - ws p_t, and q_t = S p_t - ws.p_x follows from one more
+// sum.
+template <bool JOINT>
 __global__ void k_pcg_dir(Planes k, int first, const float *__restrict__ p_old,
                           float *__restrict__ p_new) {
   if (k.sc->stop || (k.sc->flags & kFlagBadInput)) return;
   TileIter it(k.W, k.H);
   const float beta = first ? 0.0f : (float)k.sc->beta;
+  double pt = 0.0;
+  if (JOINT) {
+    const double S = k.sc->j_s, zt = S > 0.0 ? k.sc->j_rt / S : 0.0;
+    pt = first ? zt : zt + k.sc->beta * k.sc->j_pt;
+  }
+  const float ptf = (float)pt;
   const float *r = k.v[0];
   float *q = k.v[3];
   const size_t P = k.P;
@@ -206,7 +246,7 @@ __global__ void k_pcg_dir(Planes k, int first, const float *__restrict__ p_old,
     const float z = d > 0.0f ? r[j] / d : 0.0f;
     return first ? z : z + beta * p_old[j];
   };
-  float pq = 0.0f;
+  float pq = 0.0f, wp = 0.0f;
   for (int tile = blockIdx.x; tile < it.ntiles; tile += gridDim.x) {
     int u, v;
     if (!pixel_of(tile, it.tiles_x, k.W, k.H, u, v)) continue;
@@ -217,22 +257,36 @@ __global__ void k_pcg_dir(Planes k, int first, const float *__restrict__ p_old,
     if (u > 0) a -= k.wx[i - 1] * pn(i - 1);
     if (v < k.H - 1) a -= k.wy[i] * pn(i + P);
     if (v > 0) a -= k.wy[i - P] * pn(i - P);
+    if (JOINT) {
+      const float ws = k.v[4][i];
+      a -= ws * ptf;
+      wp += ws * pc;
+    }
     p_new[i] = pc;
     q[i] = a;
     pq += pc * a;
   }
-  double s[1] = {(double)pq}, out[1];
-  if (grid_sum_last_block<1>(s, k.partial, &k.sc->count, out)) {
-    k.sc->gamma = out[0];
-    if (out[0] <= 0.0 || k.sc->rho == 0.0) {
+  double s[2] = {(double)pq, (double)wp}, out[2];
+  if (grid_sum_last_block<2>(s, k.partial, &k.sc->count, out)) {
+    double gamma = out[0];
+    if (JOINT) {
+      const double qt = k.sc->j_s * pt - out[1];
+      k.sc->j_pt = pt;
+      k.sc->j_qt = qt;
+      gamma += pt * qt;
+    }
+    k.sc->gamma = gamma;
+    if (gamma <= 0.0 || k.sc->rho == 0.0) {
       k.sc->stop = 1;  // breakdown or exact solution: this depth step ends
     } else {
-      k.sc->alpha = k.sc->rho / out[0];
+      k.sc->alpha = k.sc->rho / gamma;
     }
   }
 }
 
 // ---- PCG step: x += alpha p, r -= alpha q, new r.z -----------------------
+// Joint: the last block also moves t and the border residual.
+template <bool JOINT>
 __global__ void k_pcg_step(Planes k, double tol, const float *__restrict__ p) {
   if (k.sc->stop || (k.sc->flags & kFlagBadInput)) return;
   TileIter it(k.W, k.H);
@@ -255,6 +309,14 @@ __global__ void k_pcg_step(Planes k, double tol, const float *__restrict__ p) {
   double s[2] = {(double)rz, (double)rr}, out[2];
   if (grid_sum_last_block<2>(s, k.partial, &k.sc->count, out)) {
     k.sc->iters += 1;
+    if (JOINT) {
+      const double a = k.sc->alpha, S = k.sc->j_s;
+      k.sc->t += a * k.sc->j_pt;
+      const double rt = k.sc->j_rt - a * k.sc->j_qt;
+      k.sc->j_rt = rt;
+      out[0] += S > 0.0 ? rt * (rt / S) : 0.0;
+      out[1] += rt * rt;
+    }
     k.sc->rr = out[1];
     if (tol > 0.0 && sqrt(out[1]) < tol * sqrt(k.sc->bb)) {
       k.sc->stop = 1;
@@ -351,6 +413,29 @@ __global__ void k_cost(Planes k, SolveCfg c) {
   if (grid_sum_last_block<1>(s, k.partial, &k.sc->count, out)) k.sc->cost = out[0];
 }
 
+// ---- accuracy metric of Section III-B: depth within rel_tol of the truth ---
+// Counts, over the pixels with a finite ground truth g > 0, those with
+// |exp(x) - g| <= rel_tol * g (decided in FP64). Counts are summed as
+// doubles, exact below 2^53.
+__global__ void k_accuracy(Planes k, const float *__restrict__ d_true, double rel_tol) {
+  TileIter it(k.W, k.H);
+  double n_in = 0.0, n_valid = 0.0;
+  for (int tile = blockIdx.x; tile < it.ntiles; tile += gridDim.x) {
+    int u, v;
+    if (!pixel_of(tile, it.tiles_x, k.W, k.H, u, v)) continue;
+    const double g = d_true[(size_t)v * k.W + u];
+    if (!(g > 0.0) || !isfinite(g)) continue;
+    n_valid += 1.0;
+    const double d = exp((double)k.x[(size_t)v * k.P + u]);
+    if (fabs(d - g) <= rel_tol * g) n_in += 1.0;
+  }
+  double s[2] = {n_in, n_valid}, out[2];
+  if (grid_sum_last_block<2>(s, k.partial, &k.sc->count, out)) {
+    k.sc->acc_in = out[0];
+    k.sc->acc_valid = out[1];
+  }
+}
+
 // ---- Section II-B: semi-dense depth / variance to log space ---------------
 __global__ void k_semi_to_log(const float *d, const float *vd, float *mu, float *var,
                               int64_t n) {
@@ -421,28 +506,37 @@ cudaError_t launch_check_inputs(const Planes &k, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve_launches(const Planes &k, const SolveCfg &c, int n_gn, int n_pcg,
-                                  cudaStream_t s) {
-  const dim3 blk(TX, TY), grd(launch_grid(tiles_of(k)));
-  cudaError_t e = cudaSuccess;
-  const bool scale = (c.terms & DF_TERM_SEMI) && c.scale_step;
-  count_launches((unsigned)(n_gn * ((scale ? 2 : 1) + 2 * n_pcg)));
+template <bool JOINT>
+static void solve_launches(const Planes &k, const SolveCfg &c, int n_gn, int n_pcg, bool scale,
+                           dim3 grd, dim3 blk, cudaStream_t s) {
   for (int g = 0; g < n_gn; ++g) {
     if (scale) k_scale<<<grd, blk, 0, s>>>(k, c);
     if (k.dtype == DF_BF16)
-      k_assemble<DF_BF16><<<grd, blk, 0, s>>>(k, c);
+      k_assemble<DF_BF16, JOINT><<<grd, blk, 0, s>>>(k, c);
     else if (k.dtype == DF_F16)
-      k_assemble<DF_F16><<<grd, blk, 0, s>>>(k, c);
+      k_assemble<DF_F16, JOINT><<<grd, blk, 0, s>>>(k, c);
     else
-      k_assemble<DF_F32><<<grd, blk, 0, s>>>(k, c);
+      k_assemble<DF_F32, JOINT><<<grd, blk, 0, s>>>(k, c);
     for (int j = 0; j < n_pcg; ++j) {
       float *p_old = k.v[1 + (j & 1)];
       float *p_new = k.v[1 + ((j + 1) & 1)];
-      k_pcg_dir<<<grd, blk, 0, s>>>(k, j == 0, p_old, p_new);
-      k_pcg_step<<<grd, blk, 0, s>>>(k, c.tol, p_new);
+      k_pcg_dir<JOINT><<<grd, blk, 0, s>>>(k, j == 0, p_old, p_new);
+      k_pcg_step<JOINT><<<grd, blk, 0, s>>>(k, c.tol, p_new);
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+}
+
+cudaError_t launch_solve_launches(const Planes &k, const SolveCfg &c, int n_gn, int n_pcg,
+                                  cudaStream_t s) {
+  const dim3 blk(TX, TY), grd(launch_grid(tiles_of(k)));
+  const bool semi = (c.terms & DF_TERM_SEMI) != 0;
+  const bool joint = semi && c.scale_step == DF_SCALE_JOINT;
+  const bool scale = semi && c.scale_step == DF_SCALE_ALTERNATE;
+  count_launches((unsigned)(n_gn * ((scale ? 2 : 1) + 2 * n_pcg)));
+  if (joint)
+    solve_launches<true>(k, c, n_gn, n_pcg, scale, grd, blk, s);
+  else
+    solve_launches<false>(k, c, n_gn, n_pcg, scale, grd, blk, s);
   return cudaGetLastError();
 }
 
@@ -474,6 +568,14 @@ cudaError_t launch_ls_scale_fit(const Planes &k, cudaStream_t s) {
   else
     k_lsfit_sum<DF_F32><<<grd, blk, 0, s>>>(k);
   k_lsfit_shift<<<grd, blk, 0, s>>>(k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accuracy(const Planes &k, const float *d_true, double rel_tol,
+                            cudaStream_t s) {
+  count_launches(1);
+  const dim3 blk(TX, TY), grd(launch_grid(tiles_of(k)));
+  k_accuracy<<<grd, blk, 0, s>>>(k, d_true, rel_tol);
   return cudaGetLastError();
 }
 

@@ -71,6 +71,8 @@ extern "C" df_status df_optimise_noalloc(int32_t width, int32_t height, const fl
   }
   df_status st = check_solve_params(&p);
   if (st != DF_OK) return st;
+  if (p.scale_step == DF_SCALE_JOINT)
+    return report(DF_ENOTSUP, "df_optimise_noalloc has no scratch plane for DF_SCALE_JOINT");
   if (!mu_semi) p.terms &= ~DF_TERM_SEMI;
   if ((p.terms & (DF_TERM_NET | DF_TERM_GRAD)) == 0)
     return report(DF_EINVAL, "terms must include NET or GRAD");

@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
   float *Rg[2] = {k.v[1], k.v[2]}, *Sg[2] = {k.v[3], k.v[4]}, *Wg[2] = {k.v[5], k.v[6]};
   float *IDg = k.diag;  // the fused kernels keep 1/diag in the diag plane
   const bool active = s_seg.active != 0;
-  const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step;
+  const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step == DF_SCALE_ALTERNATE;
   int parity = 0;
   bool alive = true;
 

@@ -25,6 +25,7 @@ DF_TERM_SEMI, DF_TERM_NET, DF_TERM_GRAD = 1, 2, 4
 DF_TERMS_ALL = 7
 DF_LOSS_HUBER, DF_LOSS_TUKEY = 0, 1
 DF_SOLVER_AUTO, DF_SOLVER_LAUNCHES, DF_SOLVER_FUSED = 0, 1, 2
+DF_SCALE_FIXED, DF_SCALE_ALTERNATE, DF_SCALE_JOINT = 0, 1, 2
 
 
 class df_keyframe_desc(C.Structure):
@@ -101,6 +102,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.df_cost.argtypes = [vp, C.POINTER(df_solve_params), vp, C.POINTER(C.c_double)]
     L.df_keyframe_check.argtypes = [vp, vp]
     L.df_scale_fit_ls.argtypes = [vp, vp]
+    L.df_depth_accuracy.argtypes = [vp, vp, C.c_int, C.c_double, vp, C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64)]
     L.df_scale_fit_ls.restype = C.c_int
     L.df_keyframe_info.argtypes = [vp, C.POINTER(df_keyframe_desc), C.POINTER(C.c_size_t)]
     L.df_keyframe_destroy.argtypes = [vp]
@@ -315,6 +318,16 @@ def df_scale_fit_ls(kf, stream=None):
     _check(load().df_scale_fit_ls(kf, _stream(stream)), "df_scale_fit_ls")
 
 
+def df_depth_accuracy(kf, depth_true, rel_tol: float = 0.1, stream=None):
+    """(n_within, n_valid): pixels whose depth is within rel_tol of the truth
+    (Section III-B's accuracy measure) and pixels with a valid truth."""
+    p, dev = _ptr(depth_true)
+    a, b = C.c_int64(0), C.c_int64(0)
+    _check(load().df_depth_accuracy(kf, p, int(dev), float(rel_tol), _stream(stream, depth_true),
+                                    C.byref(a), C.byref(b)), "df_depth_accuracy")
+    return a.value, b.value
+
+
 def df_keyframe_check(kf, stream=None):
     _check(load().df_keyframe_check(kf, _stream(stream)), "df_keyframe_check")
 
@@ -501,6 +514,9 @@ class Keyframe:
 
     def scale_fit_ls(self, stream=None):
         df_scale_fit_ls(self.handle, stream)
+
+    def depth_accuracy(self, depth_true, rel_tol=0.1, stream=None):
+        return df_depth_accuracy(self.handle, depth_true, rel_tol, stream)
 
     def close(self):
         if self.handle is not None and self.handle.value:

@@ -425,5 +425,20 @@ def semi_to_log(o):
     assert np.all(mu[4:] == 0) and np.all(var[4:] == 0)
 
 
+def within_10pct(o):
+    """Section III-B's accuracy measure on a hand-made list: estimates at known
+    relative offsets from the truth (well away from the 10% edge), and truths
+    that do not count (zero, negative, NaN, infinite)."""
+    g = np.array([1.0, 2.0, 0.7, 4.2, 3.0, 1.5, 2.5, 0.9, 0.0, -1.0, np.nan, np.inf, 5.0])
+    off = np.array([0.0, 0.05, -0.05, 0.098, -0.098, 0.102, -0.11, 0.3, 0.0, 0.0, 0.0, 0.0, -0.5])
+    with np.errstate(invalid="ignore", divide="ignore"):
+        x = np.log(np.abs(g) * (1.0 + off))
+    x[~np.isfinite(x)] = 0.0
+    assert o.within(x, g, 0.1) == (5, 9)
+    assert o.within(x, g, 0.2) == (7, 9)
+    assert o.within(x, g, 0.0) == (1, 9)   # only g = 1, x = 0 is exact
+    assert o.within(np.zeros(0), np.zeros(0), 0.1) == (0, 0)
+
+
 ALL = [cost_closed_form, robust_weight, dense_hessian, joint_optimum, joint_bordered, prior_only,
-       planar_recovery, huber_scipy, invariances, monotone, no_pairwise, semi_to_log]
+       planar_recovery, huber_scipy, invariances, monotone, no_pairwise, semi_to_log, within_10pct]

@@ -65,3 +65,15 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
         dfl.df_optimise_noalloc(W, H, z, z, z, z, z, z, None, None, z, t, params())
     assert e.value.status == dfl.DF_EINVAL
     assert "no-allocation limit" in str(e.value)
+
+
+def test_noalloc_refuses_the_joint_variant():
+    """Its scratch has no plane for the semi-dense weights the joint (x, t)
+    solve keeps; the call is refused before anything runs."""
+    torch = torch_cuda()
+    z = torch.ones((8, 8), device="cuda")
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(dfl.DFError) as e:
+        dfl.df_optimise_noalloc(8, 8, z, z, z, z, z, z, z, z, z, t,
+                                params(scale_step=dfl.DF_SCALE_JOINT))
+    assert e.value.status == dfl.DF_ENOTSUP
