@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mpixel·iter/s"
 WORKLOAD = "sequence-640x480-100f-10x5-fp32"
+SCALE_STEPS = {"fixed": 0, "alternate": 1, "joint": 2}  # DF_SCALE_* values
 ALG_BYTES_PER_PCG_PX = 56  # canonical streaming model of one PCG iteration
 ALG_BYTES_PER_GN_PX = 56   # scale step + re-weighting / assembly per GN iteration
 
@@ -45,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--solver", choices=["auto", "launches", "fused"], default="auto")
+    ap.add_argument("--scale-step", choices=["alternate", "joint", "fixed"], default="alternate",
+                    help="how t is solved: the paper's alternation, the joint (x, t) PCG, or fixed")
     ap.add_argument("--width", type=int, default=640)
     ap.add_argument("--height", type=int, default=480)
     ap.add_argument("--frames", type=int, default=100)
@@ -192,7 +195,8 @@ def run_reference(args, ws, rank):
     for step in range(args.warmup + args.steps):
         view.mu_s, view.var_s = mus[f % args.frames], vs[f % args.frames]
         t0 = time.perf_counter()
-        xr, t, _ = o.optimise(view, x0=x, t0=t, n_gn=args.n_gn, n_pcg=args.n_pcg)
+        xr, t, _ = o.optimise(view, x0=x, t0=t, n_gn=args.n_gn, n_pcg=args.n_pcg,
+                               scale_step=SCALE_STEPS[args.scale_step])
         dt = time.perf_counter() - t0
         x = xr.ravel()
         f += 1
@@ -208,7 +212,8 @@ def run_reference(args, ws, rank):
         "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "width": args.width, "height": args.height,
-                   "frames_per_step": 1, "n_gn": args.n_gn, "n_pcg": args.n_pcg},
+                   "frames_per_step": 1, "n_gn": args.n_gn, "n_pcg": args.n_pcg,
+                   "scale_step": args.scale_step},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -233,7 +238,8 @@ def cpu_baseline(args, kf, mus, vs):
     t_start = time.perf_counter()
     while True:
         view.mu_s, view.var_s = mus[n % args.frames], vs[n % args.frames]
-        xr, t, _ = o.optimise(view, x0=x, t0=t, n_gn=args.n_gn, n_pcg=args.n_pcg)
+        xr, t, _ = o.optimise(view, x0=x, t0=t, n_gn=args.n_gn, n_pcg=args.n_pcg,
+                               scale_step=SCALE_STEPS[args.scale_step])
         x = xr.ravel()
         n += 1
         el = time.perf_counter() - t_start
@@ -491,7 +497,10 @@ def main():
     out_d = torch.empty((F, H, W), dtype=torch.float32, device=dev)
     solver = {"auto": dfl.DF_SOLVER_AUTO, "launches": dfl.DF_SOLVER_LAUNCHES,
               "fused": dfl.DF_SOLVER_FUSED}[args.solver]
-    prm = dfl.df_default_params(n_gn=args.n_gn, n_pcg=args.n_pcg, solver=solver)
+    scale_step = {"alternate": dfl.DF_SCALE_ALTERNATE, "joint": dfl.DF_SCALE_JOINT,
+                  "fixed": dfl.DF_SCALE_FIXED}[args.scale_step]
+    prm = dfl.df_default_params(n_gn=args.n_gn, n_pcg=args.n_pcg, solver=solver,
+                                scale_step=scale_step)
     dfl.df_set_tuning(mode={"auto": 0, "streaming": 1, "resident": 2}[args.mode],
                       vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas)
     stream = torch.cuda.Stream(dev)
@@ -584,6 +593,18 @@ def main():
                "h2d_bytes_per_step": int(sum(p.nbytes for p in kf.cnn_planes) + mus.nbytes + vs.nbytes),
                "d2h_bytes_per_step": int(F * H * W * 4), "ms_per_step": tot / args.steps}
 
+    # accuracy of the fused depth after the last frame (Section III-B's
+    # measure, outside the timed region), next to the network prior alone
+    truth_d = torch.from_numpy(np.exp(kf.log_depth_true).astype(np.float32)).to(dev)
+    with torch.cuda.stream(stream):
+        step(False)
+    n_in, n_valid = k.depth_accuracy(truth_d, 0.1, stream=sptr)
+    k.reset(*cnn_d, stream=sptr)
+    n_in0, _ = k.depth_accuracy(truth_d, 0.1, stream=sptr)
+    accuracy = {"within_10pct": n_in / n_valid, "cnn_prior_within_10pct": n_in0 / n_valid,
+                "what": "fraction of pixels within 10% of the synthetic ground-truth depth "
+                        "after the last frame (Section III-B measure)"}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(args, kf, mus, vs)
@@ -597,11 +618,12 @@ def main():
             "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
             "config": {"workload": WORKLOAD, "width": W, "height": H, "frames": F,
                        "n_gn": args.n_gn, "n_pcg": args.n_pcg, "solver": args.solver,
+                       "scale_step": args.scale_step,
                        "kernel_mode": args.mode, "max_ctas": args.max_ctas,
                        "parallelism": f"replicas x{ws}",
                        "l2": "flushed between steps (256 MB write)"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "accuracy": accuracy,
             "update_latency_ms": {"p50": float(lat[0]), "p99": float(lat[1]),
                                   "what": "one frame's df_optimise, device time"},
             "hbm_frac": roofline["frac"],

@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "df_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "df_mvs.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LOCK = threading.Lock()
 
@@ -36,6 +37,24 @@ class _Problem(C.Structure):
         (n, C.POINTER(C.c_double))
         for n in ("mu_n", "var_n", "gx", "var_gx", "gy", "var_gy", "mu_s", "var_s")
     ]
+
+
+class _Camera(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("fx", "fy", "cx", "cy")]
+
+
+class _Pose(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3)]
+
+
+class _MvsParams(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("grad_min", "d_min", "d_max", "sigma_range",
+                                           "ssd_max", "photo_var")] + [("max_steps", C.c_int32)]
+
+
+MVS_DEFAULTS = dict(grad_min=20.0, d_min=0.3, d_max=10.0, sigma_range=2.0, ssd_max=5 * 20.0 ** 2,
+                    photo_var=1.0, max_steps=512)
+MVS_OK, MVS_FLAT, MVS_INTERVAL, MVS_LINE, MVS_NOSTEP, MVS_SSD, MVS_NEIGHBOUR = range(7)
 
 
 class _Params(C.Structure):
@@ -62,10 +81,11 @@ def build(mutant: int = 0, force: bool = False) -> str:
     name = "liboracle.so" if mutant == 0 else f"liboracle_m{mutant}.so"
     out = os.path.join(_BUILD, name)
     with _LOCK:
-        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        newest = max(os.path.getmtime(p) for p in _SRCS)
+        if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
             tmp = out + f".{os.getpid()}.tmp"
             cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                   f"-DORC_MUTANT={int(mutant)}", _SRC, "-o", tmp, "-lm"]
+                   f"-DORC_MUTANT={int(mutant)}", *_SRCS, "-o", tmp, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, out)
     return out
@@ -108,6 +128,10 @@ class Oracle:
         L.orc_semi_to_log.argtypes = [C.c_int64, D, D, D, D]
         L.orc_ls_scale_fit.restype = None
         L.orc_ls_scale_fit.argtypes = [P, D, D]
+        L.orc_semi_dense.restype = C.c_int64
+        L.orc_semi_dense.argtypes = [I, I, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                     C.POINTER(_Camera), C.POINTER(_Pose), C.POINTER(_MvsParams),
+                                     D, D, C.POINTER(C.c_int32), C.POINTER(C.c_int32), D]
         L.orc_within.restype = None
         L.orc_within.argtypes = [C.c_int64, D, D, C.c_double, C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int64)]
@@ -216,6 +240,33 @@ class Oracle:
                                     scale_step=scale_step)
             x = x.ravel()
         return x.reshape(kf.height, kf.width), t
+
+    def semi_dense(self, img_key, img_ref, cam, R, t, depth=None, var=None, **params):
+        """One stereo update (Section II-B). Returns (depth, var, status,
+        best_step, margin, n_measured); depth / var start from the given
+        estimate (None: no estimate anywhere)."""
+        H, W = np.shape(img_key)
+        ik = np.ascontiguousarray(img_key, dtype=np.float32)
+        ir = np.ascontiguousarray(img_ref, dtype=np.float32)
+        d = np.zeros(H * W) if depth is None else _f64(depth).copy()
+        vv = np.zeros(H * W) if var is None else _f64(var).copy()
+        st = np.zeros(H * W, np.int32)
+        bs = np.zeros(H * W, np.int32)
+        mg = np.zeros(H * W)
+        p = dict(MVS_DEFAULTS)
+        p.update(params)
+        prm = _MvsParams(*[float(p[k]) for k in ("grad_min", "d_min", "d_max", "sigma_range",
+                                                 "ssd_max", "photo_var")], int(p["max_steps"]))
+        camc = _Camera(*[float(c) for c in cam])
+        pose = _Pose((C.c_double * 9)(*np.asarray(R, np.float64).ravel()),
+                     (C.c_double * 3)(*np.asarray(t, np.float64).ravel()))
+        fp = C.POINTER(C.c_float)
+        ip = C.POINTER(C.c_int32)
+        n = self.lib.orc_semi_dense(W, H, ik.ctypes.data_as(fp), ir.ctypes.data_as(fp),
+                                    C.byref(camc), C.byref(pose), C.byref(prm), _dp(d), _dp(vv),
+                                    st.ctypes.data_as(ip), bs.ctypes.data_as(ip), _dp(mg))
+        sh = (H, W)
+        return d.reshape(sh), vv.reshape(sh), st.reshape(sh), bs.reshape(sh), mg.reshape(sh), int(n)
 
     def within(self, x, d_true, rel_tol: float = 0.1):
         """(n_within, n_valid) of Section III-B's accuracy measure."""

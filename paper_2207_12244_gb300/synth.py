@@ -78,7 +78,16 @@ def _intrinsics(W: int, H: int):
 
 def make_scene(W: int, H: int, rng: np.random.Generator, n_planes: int = 3):
     """Return (ln D float64 [H, W], labels int32 [H, W])."""
+    log_d, labels, _ = _scene_planes(W, H, rng, n_planes)
+    return log_d, labels
+
+
+def _scene_planes(W: int, H: int, rng: np.random.Generator, n_planes: int = 3):
+    """The scene of make_scene plus each plane as (n, dist) with n.X = dist in
+    the keyframe's camera coordinates (a fronto-parallel fallback plane has
+    n = (0, 0, 1))."""
     fx, fy, cx, cy = _intrinsics(W, H)
+    planes = [(np.array([0.0, 0.0, 1.0]), 1.0)] * n_planes
     u = np.arange(W, dtype=np.float64)[None, :]
     v = np.arange(H, dtype=np.float64)[:, None]
     su = rng.integers(0, W, size=n_planes)
@@ -106,11 +115,14 @@ def make_scene(W: int, H: int, rng: np.random.Generator, n_planes: int = 3):
             vals = cand[region] if cand.shape == region.shape else np.broadcast_to(cand, region.shape)[region]
             if np.all(vals > 0) and np.all(1.0 / vals >= 0.5) and np.all(1.0 / vals <= 5.0):
                 inv_d[region] = np.broadcast_to(cand, (H, W))[region]
+                planes[k] = (n.copy(), dist)
                 ok = True
                 break
         if not ok:  # fronto-parallel plane at a valid depth
-            inv_d[region] = 1.0 / rng.uniform(0.8, 4.0)
-    return np.log(1.0 / inv_d), labels
+            dfp = rng.uniform(0.8, 4.0)
+            inv_d[region] = 1.0 / dfp
+            planes[k] = (np.array([0.0, 0.0, 1.0]), dfp)
+    return np.log(1.0 / inv_d), labels, planes
 
 
 def _candidates(labels: np.ndarray, rng: np.random.Generator) -> np.ndarray:
@@ -253,3 +265,119 @@ def to_f16(a: np.ndarray) -> np.ndarray:
 
 def f16_to_f32(codes: np.ndarray) -> np.ndarray:
     return codes.view(np.float16).astype(np.float32)
+
+
+# ---- two views of a textured piecewise-planar scene (semi-dense input) -----
+#
+# The semi-dense stereo step (Section II-B) needs images: a keyframe image
+# and a reference image of the same scene from a known relative pose. The
+# planes of _scene_planes carry an aperiodic texture fixed to the surface
+# (value noise over plane coordinates, two octaves), so both views see the
+# same surface pattern. The reference view is ray-cast: a ray meets plane k
+# where that point falls inside plane k's region of the keyframe image; the
+# nearest such hit is seen, else a far background plane.
+
+@dataclass
+class StereoPair:
+    width: int
+    height: int
+    img_key: np.ndarray   # float32 [H, W], intensities in [0, 255]
+    img_ref: np.ndarray   # float32 [H, W]
+    cam: Tuple[float, float, float, float]  # fx, fy, cx, cy (both views)
+    R: np.ndarray         # float64 3 x 3: X_ref = R X_key + t
+    t: np.ndarray         # float64 3
+    depth_true: np.ndarray  # float64 [H, W], keyframe depth (metres)
+    labels: np.ndarray = field(repr=False, default=None)
+
+
+def _hash01(i: np.ndarray, j: np.ndarray, salt: int) -> np.ndarray:
+    """Deterministic pseudo-random values in [0, 1) per integer lattice point."""
+    h = (i.astype(np.int64) * 73856093) ^ (j.astype(np.int64) * 19349663) ^ (salt * 83492791)
+    h = (h ^ (h >> 13)) * 1274126177
+    h = h ^ (h >> 16)
+    return (h & 0xFFFFFF).astype(np.float64) / float(1 << 24)
+
+
+def _value_noise(a: np.ndarray, b: np.ndarray, cell: float, salt: int) -> np.ndarray:
+    x, y = a / cell, b / cell
+    i, j = np.floor(x), np.floor(y)
+    fx, fy = x - i, y - j
+    wx, wy = fx * fx * (3 - 2 * fx), fy * fy * (3 - 2 * fy)  # smoothstep
+    v00, v10 = _hash01(i, j, salt), _hash01(i + 1, j, salt)
+    v01, v11 = _hash01(i, j + 1, salt), _hash01(i + 1, j + 1, salt)
+    return (v00 * (1 - wx) + v10 * wx) * (1 - wy) + (v01 * (1 - wx) + v11 * wx) * wy
+
+
+def _texture(X: np.ndarray, n: np.ndarray, salt: int, cell: float) -> np.ndarray:
+    """Intensity of surface points X (..., 3) on a plane with normal n."""
+    helper = np.array([1.0, 0.0, 0.0]) if abs(n[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = np.cross(n, helper)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(n, e1)
+    a, b = X @ e1, X @ e2
+    v = 0.65 * _value_noise(a, b, cell, salt) + 0.35 * _value_noise(a, b, cell * 0.5, salt + 7)
+    return 255.0 * v
+
+
+def _rotation(axis: np.ndarray, angle: float) -> np.ndarray:
+    axis = axis / np.linalg.norm(axis)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + np.sin(angle) * K + (1 - np.cos(angle)) * (K @ K)
+
+
+def make_stereo_pair(W: int, H: int, seed: int, baseline: float = 0.04, rot_deg: float = 0.5,
+                     cell: float = 0.025, noise: float = 0.0) -> StereoPair:
+    """Keyframe and reference images of one seeded scene (the scene of
+    make_keyframe(W, H, seed)) from a relative pose with the given baseline
+    (metres, mostly sideways) and a small rotation; optional Gaussian image
+    noise (intensity units)."""
+    rng = np.random.default_rng(seed)
+    log_d, labels, planes = _scene_planes(W, H, rng)
+    fx, fy, cx, cy = _intrinsics(W, H)
+    prng = np.random.default_rng([seed, 104729])
+    R = _rotation(prng.normal(size=3), np.deg2rad(rot_deg))
+    d = prng.normal(size=3)
+    d[2] *= 0.2  # mostly sideways motion
+    t = baseline * d / np.linalg.norm(d)
+    D = np.exp(log_d)
+    u = np.arange(W, dtype=np.float64)[None, :]
+    v = np.arange(H, dtype=np.float64)[:, None]
+    rays = np.stack(np.broadcast_arrays((u - cx) / fx, (v - cy) / fy, np.ones((H, W))), axis=-1)
+    Xk = rays * D[..., None]
+    img_key = np.zeros((H, W))
+    for k, (n, dist) in enumerate(planes):
+        m = labels == k
+        img_key[m] = _texture(Xk[m], n, 1000 * seed + k, cell)
+    # reference view: X_key = R^T (X_ref - t) along reference rays X_ref = lam r
+    Rt = R.T
+    dir_k = rays @ R  # (R^T r) for every reference ray r
+    orig_k = -Rt @ t
+    best = np.full((H, W), np.inf)
+    img_ref = np.zeros((H, W))
+    for k, (n, dist) in enumerate(planes):
+        den = dir_k @ n
+        with np.errstate(divide="ignore", invalid="ignore"):
+            lam = (dist - orig_k @ n) / den
+        X = orig_k + lam[..., None] * dir_k
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u0 = fx * X[..., 0] / X[..., 2] + cx
+            v0 = fy * X[..., 1] / X[..., 2] + cy
+        ok = (lam > 0) & (X[..., 2] > 0) & np.isfinite(u0) & np.isfinite(v0)
+        iu = np.clip(np.rint(np.where(ok, u0, 0)), 0, W - 1).astype(int)
+        iv = np.clip(np.rint(np.where(ok, v0, 0)), 0, H - 1).astype(int)
+        ok &= (u0 > -0.5) & (u0 < W - 0.5) & (v0 > -0.5) & (v0 < H - 0.5)
+        ok &= labels[iv, iu] == k
+        take = ok & (lam < best)
+        best[take] = lam[take]
+        img_ref[take] = _texture(X[take], n, 1000 * seed + k, cell)
+    bg = ~np.isfinite(best)
+    if bg.any():  # far fronto-parallel background in the keyframe frame
+        nb = np.array([0.0, 0.0, 1.0])
+        lam = (10.0 - orig_k @ nb) / (dir_k[bg] @ nb)
+        img_ref[bg] = _texture(orig_k + lam[:, None] * dir_k[bg], nb, 1000 * seed + 99, cell)
+    if noise > 0:
+        nrng = np.random.default_rng([seed, 7919])
+        img_key = img_key + nrng.normal(0, noise, img_key.shape)
+        img_ref = img_ref + nrng.normal(0, noise, img_ref.shape)
+    return StereoPair(W, H, img_key.astype(np.float32), img_ref.astype(np.float32),
+                      (fx, fy, cx, cy), R, t, D, labels)

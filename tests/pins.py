@@ -440,5 +440,92 @@ def within_10pct(o):
     assert o.within(np.zeros(0), np.zeros(0), 0.1) == (0, 0)
 
 
+def _rectified(delta_true, tx=0.2, fx=50.0, W=64, H=32):
+    """Fronto-parallel plane, reference camera shifted along x (X_ref = X_key +
+    (tx, 0, 0)), linear-ramp images: a keyframe point at depth Z appears
+    fx tx / Z pixels further along x (the textbook disparity relation)."""
+    cam = (fx, fx, W / 2.0, H / 2.0)
+    u = np.arange(W, dtype=np.float64)[None, :]
+    v = np.arange(H, dtype=np.float64)[:, None]
+    img_key = (3.0 * u + 0.5 * v + 10.0) * np.ones((H, W))
+    img_ref = img_key - 3.0 * delta_true
+    return cam, img_key.astype(np.float32), img_ref.astype(np.float32), np.eye(3), np.array([tx, 0.0, 0.0])
+
+
+def mvs_rectified(o):
+    """Section II-B on rectified stereo in closed form: depth steps are
+    disparities fx tx / d_min - j (1 px apart); with ramp images the error of
+    every sample is 3 (disparity - true disparity), so the best step, its
+    neighbour, the linearised sub-pixel fraction and sigma^2 = (J^T J)^-1
+    are known exactly."""
+    fx, tx = 50.0, 0.2
+    B = fx * tx  # disparity x depth
+    prm = dict(grad_min=1.0, d_min=0.5, d_max=10.0, ssd_max=1e9, max_steps=512)
+    for dstar, (da_disp, db_disp) in ((8.0, (8.0, 9.0)), (8.3, (8.0, 9.0)), (7.8, (8.0, 7.0))):
+        cam, ik, ir, R, t = _rectified(dstar, tx, fx)
+        d, var, st, bs, mg, n = o.semi_dense(ik, ir, cam, R, t, **prm)
+        da, db = B / da_disp, B / db_disp
+        ea, eb = 3.0 * (da_disp - dstar), 3.0 * (db_disp - dstar)
+        s = min(1.0, max(0.0, -ea / (eb - ea)))
+        want_d = da + s * (db - da)
+        want_var = (db - da) ** 2 / (5.0 * (eb - ea) ** 2)
+        for (yy, xx) in ((16, 20), (10, 30), (20, 35)):
+            assert st[yy, xx] == orc.MVS_OK, (dstar, st[yy, xx])
+            assert bs[yy, xx] == int(round(B / prm["d_min"] - da_disp)), (dstar, bs[yy, xx])
+            # the images are stored in float32 (values ~100 carry ~4e-6 rounding)
+            assert abs(d[yy, xx] - want_d) < 1e-6 * want_d, (dstar, d[yy, xx], want_d)
+            assert abs(var[yy, xx] - want_var) < 1e-5 * want_var, (dstar, var[yy, xx], want_var)
+        # pixels whose samples leave the image, and the border rows, are not measured
+        assert st[0, 20] == orc.MVS_FLAT and st[16, 63] == orc.MVS_FLAT
+        assert st[16, 62] != orc.MVS_OK
+    # too little texture: nothing is measured
+    cam, ik, ir, R, t = _rectified(8.0, tx, fx)
+    _, _, st, _, _, n = o.semi_dense(ik, ir, cam, R, t, **dict(prm, grad_min=4.0))
+    assert n == 0 and np.all(st == orc.MVS_FLAT)
+
+
+def mvs_fusion_and_interval(o):
+    """A current estimate narrows the search to d +- 2 sigma and is fused with
+    the measurement by the Gaussian product; an estimate wide enough to cover
+    the whole range leaves the measurement unchanged before fusion."""
+    fx, tx = 50.0, 0.2
+    cam, ik, ir, R, t = _rectified(8.3, tx, fx)
+    prm = dict(grad_min=1.0, d_min=0.5, d_max=10.0, ssd_max=1e9, max_steps=512)
+    d0, v0, st0, _, _, _ = o.semi_dense(ik, ir, cam, R, t, **prm)
+    H, W = ik.shape
+    prior_d = np.full((H, W), 2.0)
+    prior_v = np.full((H, W), 100.0)  # +-20 m: the whole range
+    d1, v1, st1, _, _, _ = o.semi_dense(ik, ir, cam, R, t, depth=prior_d, var=prior_v, **prm)
+    m = st0 == orc.MVS_OK
+    assert np.array_equal(st1 == orc.MVS_OK, m)
+    want_v = prior_v[m] * v0[m] / (prior_v[m] + v0[m])
+    want_d = (prior_d[m] * v0[m] + d0[m] * prior_v[m]) / (prior_v[m] + v0[m])
+    assert np.allclose(v1[m], want_v, rtol=1e-12) and np.allclose(d1[m], want_d, rtol=1e-12)
+    # a tight estimate far from the truth: the measurement stays near it
+    pd, pv = np.full((H, W), 1.6), np.full((H, W), 0.01 ** 2)
+    d2, v2, st2, _, _, _ = o.semi_dense(ik, ir, cam, R, t, depth=pd, var=pv, **prm)
+    k = st2 == orc.MVS_OK
+    assert k.sum() > 0
+    step = fx * tx / 1.6 ** 2  # pixels of disparity per metre of depth at 1.6 m
+    assert np.all(np.abs(d2[k] - 1.6) <= 0.02 + 2.0 / step)
+    # pixels without texture keep their estimate
+    assert np.array_equal(d2[~k & (st2 == orc.MVS_FLAT)], pd[~k & (st2 == orc.MVS_FLAT)])
+
+
+def mvs_scene(o):
+    """On a noise-free textured scene (two views, known pose) the measured
+    depths agree with the scene's true depth: most within 10 %, the median
+    within a few per cent, and the stated sigma is not wildly optimistic."""
+    sp = synth.make_stereo_pair(320, 240, 5)
+    d, var, st, bs, mg, n = o.semi_dense(sp.img_key, sp.img_ref, sp.cam, sp.R, sp.t)
+    m = st == orc.MVS_OK
+    assert m.mean() > 0.15, m.mean()
+    rel = np.abs(d[m] / sp.depth_true[m] - 1.0)
+    assert np.median(rel) < 0.03 and np.mean(rel < 0.1) > 0.8, (np.median(rel), np.mean(rel < 0.1))
+    z = np.abs(d[m] - sp.depth_true[m]) / np.sqrt(var[m])
+    assert np.median(z) < 10.0
+
+
 ALL = [cost_closed_form, robust_weight, dense_hessian, joint_optimum, joint_bordered, prior_only,
-       planar_recovery, huber_scipy, invariances, monotone, no_pairwise, semi_to_log, within_10pct]
+       planar_recovery, huber_scipy, invariances, monotone, no_pairwise, semi_to_log, within_10pct,
+       mvs_rectified, mvs_fusion_and_interval, mvs_scene]

@@ -6,7 +6,8 @@ a flipped sign in b, the wrong gradient plane in a weight, a reversed
 gradient residual, a wrong Huber weight, a flipped scale step, a wrong
 neighbour index, an inverted CG beta, a residual divided by the variance
 instead of the standard deviation, a flipped sign of the x-t coupling in
-the joint solve.
+the joint solve, a stereo variance with the wrong power of the depth step,
+a stereo sub-pixel fraction with the wrong sign.
 """
 import pytest
 
@@ -24,6 +25,8 @@ MUTANTS = {
     8: "CG beta inverted",
     9: "semi residual divided by V",
     10: "joint PCG couples x and t with the wrong sign",
+    11: "stereo variance uses |dd| instead of dd^2",
+    12: "stereo sub-pixel fraction has the wrong sign",
 }
 
 
