@@ -222,6 +222,86 @@ size_t df_keyframe_bytes(int32_t width, int32_t height, int32_t cnn_dtype);
 df_status df_set_memory_budget(size_t bytes);
 size_t df_memory_in_use(void);
 
+/* ---- semi-dense two-view depth (Section II-B) -----------------------------
+ *
+ * The step that produces the optimisation's semi-dense input each frame:
+ * for every keyframe pixel with enough texture, a search along its epipolar
+ * line in a reference image for the depth that minimises the SSD of five
+ * equally spaced points (Eq. 2), a sub-pixel fit between the best 1-pixel
+ * step and its better neighbour, the measurement variance
+ * sigma^2 = photo_var (J^T J)^-1 with J the finite-difference Jacobian of the
+ * 5-vector error along the depth (Eqs. 3, 4), and the Gaussian fusion of the
+ * measurement with the pixel's current estimate. Details the paper leaves
+ * open are fixed as follows:
+ *  - texture: central-difference gradient magnitude of the keyframe image
+ *    >= grad_min (the image border is never measured);
+ *  - search interval: [d - sigma_range sigma, d + sigma_range sigma] with a
+ *    current estimate (sigma_range = 2 in the paper), else [d_min, d_max],
+ *    clipped to [d_min, d_max]; the projections of its ends span a segment of
+ *    length L in the reference image, walked in floor(L) + 1 steps of 1 px
+ *    from the near end (segments of more than max_steps steps are skipped);
+ *  - samples: keyframe points x + s e0 (s = -2..2, e0 the unit direction of
+ *    the keyframe's epipolar line at x), each compared with its projection
+ *    into the reference image at the step's depth; bilinear interpolation;
+ *    a step with any sample outside the image is invalid;
+ *  - the first minimum wins; the neighbour is the step before or after the
+ *    best one (evaluated even just beyond the interval) with the smaller SSD,
+ *    the one before on ties; the error is linearised between the two and
+ *    minimised over the segment between them;
+ *  - no measurement when the best SSD exceeds ssd_max. */
+typedef struct {
+  float fx, fy, cx, cy; /* pinhole intrinsics, pixels (both images) */
+} df_camera;
+
+typedef struct {
+  float R[9]; /* row-major rotation, keyframe camera -> reference camera */
+  float t[3]; /* X_ref = R X_key + t (metres) */
+} df_pose;
+
+typedef struct {
+  float grad_min;    /* texture threshold, intensity units per pixel (default 20) */
+  float d_min, d_max;/* search range without an estimate (default 0.3, 10 m) */
+  float sigma_range; /* half-width of the interval in sigmas (default 2) */
+  float ssd_max;     /* largest accepted best SSD (default 5 * 20^2) */
+  float photo_var;   /* image noise variance in sigma^2 (default 1) */
+  int32_t max_steps; /* longest walk, steps (default 512) */
+} df_mvs_params;
+
+/* per-pixel outcome codes of df_mvs_update's status plane */
+#define DF_MVS_OK 0        /* measured and fused */
+#define DF_MVS_FLAT 1      /* border pixel or too little texture */
+#define DF_MVS_INTERVAL 2  /* empty search interval */
+#define DF_MVS_LINE 3      /* degenerate / too long segment, keyframe samples outside */
+#define DF_MVS_NOSTEP 4    /* no step with all samples inside the reference image */
+#define DF_MVS_SSD 5       /* best SSD above ssd_max */
+#define DF_MVS_NEIGHBOUR 6 /* no usable neighbour for the sub-pixel fit */
+
+typedef struct df_mvs df_mvs;
+
+void df_mvs_default_params(df_mvs_params *p);
+
+/* Work space for images of width x height (a device list of candidate
+ * pixels and a counter), on the current device. */
+df_status df_mvs_create(int32_t width, int32_t height, df_mvs **out);
+void df_mvs_destroy(df_mvs *m); /* NULL-safe */
+
+/* One stereo update of a keyframe's semi-dense estimate, asynchronous on
+ * 'stream'. img_key, img_ref: dense row-major H x W FP32 intensities on the
+ * device. depth, var: dense H x W FP32 device planes holding the current
+ * estimate (metres, metres^2; var <= 0 or non-finite: no estimate), updated
+ * in place where a measurement is made. status, best_step: optional dense
+ * H x W int32 device planes (NULL to skip) receiving DF_MVS_* and the best
+ * step index (-1 when there was none). All buffers are caller-owned and
+ * must not be written until the stream has passed the call. The result goes
+ * to log space with df_semi_to_log and into the solve with df_frame_update.
+ * Errors: DF_EINVAL for NULL required pointers, a size other than the
+ * context's, or invalid parameters (d_min <= 0, d_max <= d_min, max_steps <
+ * 1, negative thresholds). */
+df_status df_mvs_update(df_mvs *m, const float *img_key, const float *img_ref,
+                        const df_camera *cam, const df_pose *key_to_ref,
+                        const df_mvs_params *params, float *depth, float *var,
+                        int32_t *status, int32_t *best_step, void *stream);
+
 /* Section II-B, last sentence: semi-dense depth d and its variance
  * sigma_d^2 to log space, to first order: mu = ln d, var = sigma_d^2 / d^2.
  * Invalid inputs (d <= 0, variance <= 0, non-finite) give mu = 0, var = 0.

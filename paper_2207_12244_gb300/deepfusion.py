@@ -64,6 +64,23 @@ class df_completion(C.Structure):
                 ("batch_size", C.c_int32), ("pad", C.c_int32)]
 
 
+class df_camera(C.Structure):
+    _fields_ = [(n, C.c_float) for n in ("fx", "fy", "cx", "cy")]
+
+
+class df_pose(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3)]
+
+
+class df_mvs_params(C.Structure):
+    _fields_ = [(n, C.c_float) for n in ("grad_min", "d_min", "d_max", "sigma_range", "ssd_max",
+                                         "photo_var")] + [("max_steps", C.c_int32)]
+
+
+DF_MVS_OK, DF_MVS_FLAT, DF_MVS_INTERVAL, DF_MVS_LINE, DF_MVS_NOSTEP, DF_MVS_SSD, \
+    DF_MVS_NEIGHBOUR = range(7)
+
+
 class DFError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         self.status = status
@@ -117,6 +134,13 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.df_optimise_noalloc.argtypes = [C.c_int32, C.c_int32] + [vp] * 10 + [
         C.POINTER(df_solve_params), vp]
     L.df_optimise_noalloc.restype = C.c_int
+    L.df_mvs_default_params.argtypes = [C.POINTER(df_mvs_params)]
+    L.df_mvs_default_params.restype = None
+    L.df_mvs_create.argtypes = [i32, i32, C.POINTER(vp)]
+    L.df_mvs_destroy.argtypes = [vp]
+    L.df_mvs_destroy.restype = None
+    L.df_mvs_update.argtypes = [vp, vp, vp, C.POINTER(df_camera), C.POINTER(df_pose),
+                                C.POINTER(df_mvs_params), vp, vp, vp, vp, vp]
     L.df_server_create.argtypes = [C.POINTER(df_server_config), C.POINTER(vp)]
     L.df_server_destroy.argtypes = [vp]
     L.df_server_destroy.restype = None
@@ -477,6 +501,69 @@ def df_last_error() -> str:
 
 def _numel(a) -> int:
     return int(a.numel()) if _is_torch(a) else int(a.size)
+
+
+def df_mvs_default_params(**overrides) -> df_mvs_params:
+    p = df_mvs_params()
+    load().df_mvs_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def df_mvs_create(width: int, height: int) -> C.c_void_p:
+    out = C.c_void_p()
+    _check(load().df_mvs_create(int(width), int(height), C.byref(out)), "df_mvs_create")
+    return out
+
+
+def df_mvs_destroy(m):
+    load().df_mvs_destroy(m)
+
+
+def df_mvs_update(m, img_key, img_ref, cam, R, t, depth, var, status=None, best_step=None,
+                  params: Optional[df_mvs_params] = None, stream=None):
+    """One stereo update (Section II-B) of depth / var in place; all planes
+    are contiguous H x W device tensors (status / best_step int32, optional)."""
+    c = df_camera(*[float(v) for v in cam])
+    pose = df_pose((C.c_float * 9)(*[float(v) for v in np.asarray(R, np.float64).ravel()]),
+                   (C.c_float * 3)(*[float(v) for v in np.asarray(t, np.float64).ravel()]))
+    ptrs = []
+    for a in (img_key, img_ref, depth, var, status, best_step):
+        p, dev = _ptr(a)
+        if a is not None and not dev:
+            raise ValueError("df_mvs_update takes device buffers")
+        ptrs.append(p)
+    _check(load().df_mvs_update(m, ptrs[0], ptrs[1], C.byref(c), C.byref(pose),
+                                C.byref(params) if params is not None else None, ptrs[2],
+                                ptrs[3], ptrs[4], ptrs[5], _stream(stream, depth)),
+           "df_mvs_update")
+
+
+class SemiDense:
+    """Owner of a df_mvs work space for images of one size."""
+
+    def __init__(self, width: int, height: int):
+        self.width, self.height = width, height
+        self.handle = df_mvs_create(width, height)
+
+    def update(self, img_key, img_ref, cam, R, t, depth, var, status=None, best_step=None,
+               params=None, stream=None):
+        df_mvs_update(self.handle, img_key, img_ref, cam, R, t, depth, var, status, best_step,
+                      params, stream)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            df_mvs_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Keyframe:
