@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on the fused kernel's grid")
     ap.add_argument("--vec", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
-    ap.add_argument("--workload", choices=["sequence", "batch64", "precision", "serving"],
+    ap.add_argument("--workload", choices=["sequence", "batch64", "precision", "serving", "mvs"],
                     default="sequence",
                     help="sequence: 640x480 keyframe over 100 frames (default); batch64: 64 "
                          "keyframes of uneven sizes in one batched solve; precision: one "
@@ -309,6 +309,142 @@ def run_serving(args, ws, rank, dev, torch, dfl, replicas, synth):
         print(json.dumps(line), flush=True)
 
 
+# FP32 operations of one epipolar step of the stereo search, counted from
+# the kernel source: the step's depth (9), and per sample (x5) the projection
+# (12 + 6), the bilinear read (14), the error and its square (3).
+MVS_FLOPS_PER_STEP = 9 + 5 * (12 + 6 + 14 + 3)
+# nominal FP32 FMA peak of the part: SMs x 128 lanes x 2 flops x max clock
+FP32_LANES_PER_SM = 128
+
+
+def run_mvs(args, ws, rank, dev, torch, dfl, replicas, synth):
+    """Semi-dense stereo (Section II-B): one step = a keyframe image against
+    a run of reference views, one df_mvs_update each (search + fusion),
+    starting from no estimate."""
+    W, H, F = args.width, args.height, min(args.frames, 8)
+    seed = replicas.rank_seed(args.seed, rank)
+    pairs = [synth.make_stereo_pair(W, H, seed, baseline=0.03 + 0.01 * (v % 4), view=v)
+             for v in range(F)]
+    name = f"mvs-{W}x{H}-{F}views"
+    key_d = torch.from_numpy(pairs[0].img_key).to(dev)
+    refs_d = [torch.from_numpy(p.img_ref).to(dev) for p in pairs]
+    depth = torch.zeros((H, W), dtype=torch.float32, device=dev)
+    var = torch.zeros((H, W), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    sptr = stream.cuda_stream
+    m = dfl.SemiDense(W, H)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(F)]
+
+    def step(record, key, refs, d, v):
+        d.zero_()
+        v.zero_()
+        for f, p in enumerate(pairs):
+            if record:
+                evs[f][0].record(stream)
+            m.update(key, refs[f], p.cam, p.R, p.t, d, v, stream=sptr)
+            if record:
+                evs[f][1].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(False, key_d, refs_d, depth, var)
+    torch.cuda.synchronize()
+    # work count of one step (outside the timed region)
+    steps_per_update = []
+    with torch.cuda.stream(stream):
+        depth.zero_()
+        var.zero_()
+        for f, p in enumerate(pairs):
+            m.update(key_d, refs_d[f], p.cam, p.R, p.t, depth, var, stream=sptr)
+            steps_per_update.append(m.last_steps(stream=sptr))
+    step_ms, upd_ms = [], []
+    launches0 = dfl.df_kernel_launches()
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                step(True, key_d, refs_d, depth, var)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            upd_ms.extend(a.elapsed_time(b) for a, b in evs)
+    launches = dfl.df_kernel_launches() - launches0
+    clocks = clk.summary()
+    total_ms = replicas.max_over_ranks(sum(step_ms), device=dev)
+    units = W * H * F
+    value = units * args.steps * ws / (total_ms / 1e3) / 1e6
+    flops = MVS_FLOPS_PER_STEP * float(np.mean(steps_per_update))
+    upd_s = statistics.mean(upd_ms) / 1e3
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+    achieved = flops / upd_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_kind": "derived: SMs x 128 FP32 lanes x 2 x 2.07 GHz (nominal FMA rate)",
+                "region": "df_mvs_update (one reference view)",
+                "alg_flops_per_launch": flops, "steps_per_launch": float(np.mean(steps_per_update))}
+    e2e = None
+    if not args.no_e2e:
+        key_h = torch.from_numpy(pairs[0].img_key).pin_memory()
+        refs_h = [torch.from_numpy(p.img_ref).pin_memory() for p in pairs]
+        out_h = torch.empty((2, H, W), dtype=torch.float32).pin_memory()
+        kd = torch.empty_like(key_d)
+        rd = [torch.empty_like(r) for r in refs_d]
+        tms = []
+        for it in range(args.steps + 1):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                kd.copy_(key_h, non_blocking=True)
+                for r, h in zip(rd, refs_h):
+                    r.copy_(h, non_blocking=True)
+                step(False, kd, rd, depth, var)
+                out_h[0].copy_(depth, non_blocking=True)
+                out_h[1].copy_(var, non_blocking=True)
+            torch.cuda.synchronize()
+            if it:
+                tms.append(1e3 * (time.perf_counter() - t0))
+        tot = replicas.max_over_ranks(sum(tms), device=dev)
+        e2e = {"value": units * args.steps * ws / (tot / 1e3) / 1e6, "unit": "Mpixel/s",
+               "h2d_bytes_per_step": int(4 * W * H * (F + 1)), "d2h_bytes_per_step": int(8 * W * H),
+               "ms_per_step": tot / args.steps}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+
+        o = oracle.get()
+        p = pairs[0]
+        t0 = time.perf_counter()
+        o.semi_dense(p.img_key, p.img_ref, p.cam, p.R, p.t)
+        el = time.perf_counter() - t0
+        cpu = {"value": W * H / el / 1e6, "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+               "sample": f"one {W}x{H} update (first reference view), {el:.2f} s single-thread FP64"}
+    m.close()
+    if rank == 0:
+        line = {
+            "metric": "Mpixel/s", "value": value, "unit": "Mpixel/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (two rendered views of a textured piecewise-planar scene)",
+            "config": {"workload": name, "width": W, "height": H, "views": F,
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "flushed between steps (256 MB write)"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu,
+            "update_latency_ms": {"p50": float(np.percentile(upd_ms, 50)),
+                                  "p99": float(np.percentile(upd_ms, 99)),
+                                  "what": "one df_mvs_update, device time"},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     """Batched / large-keyframe workloads: one solve of all keyframes per step."""
     if args.workload == "batch64":
@@ -478,6 +614,12 @@ def main():
                       vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas)
     if args.workload == "serving":
         run_serving(args, ws, rank, dev, torch, dfl, replicas, synth)
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    if args.workload == "mvs":
+        run_mvs(args, ws, rank, dev, torch, dfl, replicas, synth)
         if ws > 1:
             dist.barrier()
             dist.destroy_process_group()

@@ -302,6 +302,11 @@ df_status df_mvs_update(df_mvs *m, const float *img_key, const float *img_ref,
                         const df_mvs_params *params, float *depth, float *var,
                         int32_t *status, int32_t *best_step, void *stream);
 
+/* Epipolar steps the last df_mvs_update evaluated (each walked step plus
+ * the three steps recomputed for the sub-pixel fit, summed over pixels):
+ * the work count of the update. Synchronises 'stream'. */
+df_status df_mvs_last_steps(df_mvs *m, void *stream, uint64_t *steps);
+
 /* Section II-B, last sentence: semi-dense depth d and its variance
  * sigma_d^2 to log space, to first order: mu = ln d, var = sigma_d^2 / d^2.
  * Invalid inputs (d <= 0, variance <= 0, non-finite) give mu = 0, var = 0.

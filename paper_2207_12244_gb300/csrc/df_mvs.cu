@@ -26,6 +26,7 @@ struct df_mvs {
   int device;
   int *list;   // W * H candidate pixel indices
   int *count;  // number of listed pixels
+  unsigned long long *steps;  // epipolar steps evaluated by the last update
 };
 
 namespace df {
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kSearchThreads)
                  const float *__restrict__ img_ref, MvsGeo g, MvsCfg p,
                  const int *__restrict__ list, const int *__restrict__ count,
                  float *__restrict__ depth, float *__restrict__ var, int *__restrict__ status,
-                 int *__restrict__ best_step) {
+                 int *__restrict__ best_step, unsigned long long *__restrict__ steps) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -219,6 +220,7 @@ __global__ void __launch_bounds__(kSearchThreads)
         ok = bilin(img_key, W, H, uf + (float)s * e0x, vf + (float)s * e0y, &w.key[s + 2]);
     }
     if (ok) {
+      if (lane == 0) atomicAdd(steps, (unsigned long long)(w.n + 3));  // walk + 3 recomputed
       // the walk: lane-strided steps, then a warp argmin (first minimum)
       float best = INFINITY;
       int bj = 0x7fffffff;
@@ -326,6 +328,7 @@ df_status df_mvs_create(int32_t width, int32_t height, df_mvs **out) {
   cudaGetDevice(&m->device);
   cudaError_t e = cudaMalloc(&m->list, sizeof(int) * ((size_t)width * height + 1));
   if (e == cudaSuccess) e = cudaMalloc(&m->count, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&m->steps, sizeof(unsigned long long));
   if (e != cudaSuccess) {
     cudaGetLastError();
     df_mvs_destroy(m);
@@ -339,6 +342,7 @@ void df_mvs_destroy(df_mvs *m) {
   if (!m) return;
   if (m->list) cudaFree(m->list);
   if (m->count) cudaFree(m->count);
+  if (m->steps) cudaFree(m->steps);
   delete m;
 }
 
@@ -376,6 +380,7 @@ df_status df_mvs_update(df_mvs *m, const float *img_key, const float *img_ref,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n = m->W * m->H;
   cudaError_t e = cudaMemsetAsync(m->count, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->steps, 0, sizeof(unsigned long long), s);
   if (e == cudaSuccess) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
@@ -385,11 +390,23 @@ df_status df_mvs_update(df_mvs *m, const float *img_key, const float *img_ref,
     k_mvs_select<<<sel_blocks, kSelThreads, 0, s>>>(m->W, m->H, img_key, depth, var, c, m->list,
                                                      m->count, status, best_step);
     k_mvs_search<<<sms * 8, kSearchThreads, 0, s>>>(m->W, m->H, img_key, img_ref, g, c, m->list,
-                                                     m->count, depth, var, status, best_step);
+                                                     m->count, depth, var, status, best_step,
+                                                     m->steps);
     e = cudaGetLastError();
   }
   if (cur != m->device) cudaSetDevice(cur);
   if (e != cudaSuccess) return report(DF_ECUDA, "df_mvs_update: %s", cudaGetErrorString(e));
+  return DF_OK;
+}
+
+df_status df_mvs_last_steps(df_mvs *m, void *stream, uint64_t *steps) {
+  if (!m || !steps) return df::report(DF_EINVAL, "NULL argument");
+  unsigned long long h = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&h, m->steps, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return df::report(DF_ECUDA, "df_mvs_last_steps: %s", cudaGetErrorString(e));
+  *steps = (uint64_t)h;
   return DF_OK;
 }
 

@@ -139,6 +139,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.df_mvs_create.argtypes = [i32, i32, C.POINTER(vp)]
     L.df_mvs_destroy.argtypes = [vp]
     L.df_mvs_destroy.restype = None
+    L.df_mvs_last_steps.argtypes = [vp, vp, C.POINTER(C.c_uint64)]
     L.df_mvs_update.argtypes = [vp, vp, vp, C.POINTER(df_camera), C.POINTER(df_pose),
                                 C.POINTER(df_mvs_params), vp, vp, vp, vp, vp]
     L.df_server_create.argtypes = [C.POINTER(df_server_config), C.POINTER(vp)]
@@ -542,6 +543,12 @@ def df_mvs_update(m, img_key, img_ref, cam, R, t, depth, var, status=None, best_
            "df_mvs_update")
 
 
+def df_mvs_last_steps(m, stream=None) -> int:
+    n = C.c_uint64(0)
+    _check(load().df_mvs_last_steps(m, _stream(stream), C.byref(n)), "df_mvs_last_steps")
+    return n.value
+
+
 class SemiDense:
     """Owner of a df_mvs work space for images of one size."""
 
@@ -553,6 +560,9 @@ class SemiDense:
                params=None, stream=None):
         df_mvs_update(self.handle, img_key, img_ref, cam, R, t, depth, var, status, best_step,
                       params, stream)
+
+    def last_steps(self, stream=None) -> int:
+        return df_mvs_last_steps(self.handle, stream)
 
     def close(self):
         if self.handle is not None and self.handle.value:

@@ -326,15 +326,16 @@ def _rotation(axis: np.ndarray, angle: float) -> np.ndarray:
 
 
 def make_stereo_pair(W: int, H: int, seed: int, baseline: float = 0.04, rot_deg: float = 0.5,
-                     cell: float = 0.025, noise: float = 0.0) -> StereoPair:
+                     cell: float = 0.025, noise: float = 0.0, view: int = 0) -> StereoPair:
     """Keyframe and reference images of one seeded scene (the scene of
     make_keyframe(W, H, seed)) from a relative pose with the given baseline
     (metres, mostly sideways) and a small rotation; optional Gaussian image
-    noise (intensity units)."""
+    noise (intensity units). 'view' draws another reference pose of the same
+    keyframe (the keyframe image does not depend on it)."""
     rng = np.random.default_rng(seed)
     log_d, labels, planes = _scene_planes(W, H, rng)
     fx, fy, cx, cy = _intrinsics(W, H)
-    prng = np.random.default_rng([seed, 104729])
+    prng = np.random.default_rng([seed, 104729] + ([view] if view else []))
     R = _rotation(prng.normal(size=3), np.deg2rad(rot_deg))
     d = prng.normal(size=3)
     d[2] *= 0.2  # mostly sideways motion
@@ -376,7 +377,7 @@ def make_stereo_pair(W: int, H: int, seed: int, baseline: float = 0.04, rot_deg:
         lam = (10.0 - orig_k @ nb) / (dir_k[bg] @ nb)
         img_ref[bg] = _texture(orig_k + lam[:, None] * dir_k[bg], nb, 1000 * seed + 99, cell)
     if noise > 0:
-        nrng = np.random.default_rng([seed, 7919])
+        nrng = np.random.default_rng([seed, 7919, view])
         img_key = img_key + nrng.normal(0, noise, img_key.shape)
         img_ref = img_ref + nrng.normal(0, noise, img_ref.shape)
     return StereoPair(W, H, img_key.astype(np.float32), img_ref.astype(np.float32),
