@@ -69,6 +69,10 @@ def parse():
                          "1920x1440 keyframe with reduced-precision network planes")
     ap.add_argument("--cnn-dtype", choices=["f32", "bf16", "f16"], default="bf16",
                     help="network-plane storage for --workload precision")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="batch64: launch the batched solve eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batch64: keep the default launch shape instead of autotuning it")
     ap.add_argument("--rate", type=float, default=600.0, help="serving: frames/s offered")
     ap.add_argument("--requests", type=int, default=1200, help="serving: frames per run")
     return ap.parse_args()
@@ -473,13 +477,23 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
 
+    graph = None
+    graph_launches = 0
+    tuning = None
+
+    def solve():
+        if graph is not None:
+            graph.replay()
+        else:
+            dfl.df_optimise_batch(handles, prm, stream=sptr)
+
     def step(record):
         for k, c, (ms, vs) in zip(ks, cnn_d, semi_d):
             k.reset(*c, stream=sptr)
             k.frame_update(ms, vs, stream=sptr)
         if record:
             ev[0].record(stream)
-        dfl.df_optimise_batch(handles, prm, stream=sptr)
+        solve()
         if record:
             ev[1].record(stream)
         for k, o in zip(ks, outs):
@@ -489,6 +503,33 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
         for _ in range(args.warmup):
             step(False)
     torch.cuda.synchronize()
+    use_graph = args.workload == "batch64" and not args.no_graph and args.solver != "launches"
+    if args.workload == "batch64" and not args.no_autotune and args.solver != "launches" \
+            and args.mode == "auto" and not (args.vec or args.tile_rows or args.max_ctas):
+        # launch shape (kernel, tile rows, vector width, GN iterations per
+        # launch) picked by timing the candidates on this batch
+        best, best_ms = dfl.df_autotune(handles, prm, stream=sptr)
+        tuning = {"mode": best.mode, "vec": best.vec, "tile_rows": best.tile_rows,
+                  "max_ctas": best.max_ctas, "gn_per_launch": best.gn_per_launch,
+                  "autotune_ms": best_ms}
+    if use_graph:
+        # the batched solve captured once in a CUDA graph, replayed per step
+        dfl.df_batch_prepare(handles, stream=sptr)
+        with torch.cuda.stream(stream):
+            step(False)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        cap0 = dfl.df_kernel_launches()
+        with torch.cuda.stream(stream):
+            with torch.cuda.graph(g, stream=stream):
+                dfl.df_optimise_batch(handles, prm, stream=sptr)
+        torch.cuda.synchronize()
+        graph_launches = dfl.df_kernel_launches() - cap0  # kernels in the graph
+        graph = g
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step(False)
+        torch.cuda.synchronize()
     step_ms, solve_ms = [], []
     launches0 = dfl.df_kernel_launches()
     with ClockSampler(dev.index) as clk:
@@ -504,7 +545,9 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             solve_ms.append(ev[0].elapsed_time(ev[1]))
-    launches = dfl.df_kernel_launches() - launches0
+    # the library counts its own launches; a replayed graph's kernels are
+    # counted from the capture, once per timed replay
+    launches = dfl.df_kernel_launches() - launches0 + graph_launches * args.steps
     clocks = clk.summary()
     total_ms = replicas.max_over_ranks(sum(step_ms), device=dev)
     px = sum(W * H for W, H in shapes)
@@ -530,7 +573,7 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
             for k, c, (ms, vs) in zip(ks, cnn_h, semi_h):
                 k.reset(*c, stream=sptr)
                 k.frame_update(ms, vs, stream=sptr)
-            dfl.df_optimise_batch(handles, prm, stream=sptr)
+            solve()
             for k, o in zip(ks, outs_h):
                 k.fetch_depth(o, stream=sptr)
 
@@ -562,6 +605,12 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
                "cores": 1, "kind": "oracle",
                "sample": f"one {kf.width}x{kf.height} keyframe of the workload, {n_gn}x{n_pcg}, "
                          f"{el:.1f} s single-thread (FP64 on the FP32 inputs)"}
+    used_graph = graph is not None
+    if used_graph:
+        graph = None
+        dfl.df_batch_release(handles)
+    dfl.df_set_tuning(mode={"auto": 0, "streaming": 1, "resident": 2}[args.mode],
+                      vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas)
     for k in ks:
         k.close()
     if rank == 0:
@@ -572,6 +621,7 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
             "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
             "config": {"workload": name, "keyframes": len(shapes), "pixels": px,
                        "cnn_dtype": dt_name, "n_gn": n_gn, "n_pcg": n_pcg, "solver": args.solver,
+                       "cuda_graph": used_graph, "autotuned": tuning,
                        "kernel_mode": args.mode, "max_ctas": args.max_ctas,
                        "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MB write)"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,

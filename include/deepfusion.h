@@ -166,6 +166,20 @@ df_status df_optimise_batch(df_keyframe *const *kfs, int32_t n,
                             const df_solve_params *params, void *stream,
                             df_solve_report *reports);
 
+/* Prepare a keyframe list for repeated batched solves and for capture in a
+ * CUDA graph: builds the fused solver's launch plans for exactly this list
+ * (in this order) and the current tuning, and keeps them on the device
+ * (synchronises 'stream'). df_optimise_batch on the same list then uses
+ * them with no host work or allocation; a batched solve under stream capture
+ * requires them (DF_ENOTSUP otherwise). Plans live until df_batch_release
+ * names one of their keyframes or one of them is destroyed; graphs that
+ * captured a solve must not be replayed after that. Lists of one keyframe
+ * need nothing (each keyframe keeps its own plan). Not in the paper: launch
+ * management. Errors: DF_EINVAL (NULL / repeated / cross-device keyframes),
+ * DF_ENOTSUP (no fused solver on this device). */
+df_status df_batch_prepare(df_keyframe *const *kfs, int32_t n, void *stream);
+df_status df_batch_release(df_keyframe *const *kfs, int32_t n);
+
 /* Write the keyframe's depth map d = exp(x) (Eq. 5's d; log_space != 0
  * writes x = ln d instead) as H x W f32 into 'out'. */
 df_status df_fetch_depth(df_keyframe *kf, float *out, int log_space, int ptr_on_device,

@@ -477,6 +477,65 @@ static df_status fused_one(df_keyframe *kf, const SolveCfg &c, int n_gn, int n_p
   return DF_OK;
 }
 
+// Launch plans of keyframe lists prepared for repeated solves and for CUDA
+// graphs (df_batch_prepare): kept on the device, keyed by the ordered
+// keyframe list, the tuning and the device, and freed by df_batch_release
+// or when one of their keyframes is destroyed. A list without a prepared
+// plan gets a stream-ordered temporary one per solve.
+struct BatchPlan {
+  std::vector<df_keyframe *> kfs;
+  df::FusedTuning tune;
+  int device = 0;
+  df::LaunchShape shape;
+  void *dplan = nullptr;
+};
+static std::mutex g_bp_mu;
+static std::vector<BatchPlan> g_bp;
+
+static void drop_batch_plans_if(const std::vector<df_keyframe *> &any_of) {
+  std::lock_guard<std::mutex> lk(g_bp_mu);
+  for (size_t j = 0; j < g_bp.size();) {
+    bool hit = false;
+    for (df_keyframe *k : any_of)
+      hit = hit || std::find(g_bp[j].kfs.begin(), g_bp[j].kfs.end(), k) != g_bp[j].kfs.end();
+    if (hit) {
+      cudaFree(g_bp[j].dplan);  // synchronising: no launch still reads it
+      g_bp.erase(g_bp.begin() + j);
+    } else {
+      ++j;
+    }
+  }
+}
+
+static bool find_batch_plan(df_keyframe *const *kfs, int n, const df::FusedTuning &tune,
+                            void **dplan, df::LaunchShape *shape) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_bp_mu);
+  for (const BatchPlan &b : g_bp) {
+    if (b.device == dev && (int)b.kfs.size() == n && same_tuning(b.tune, tune) &&
+        std::equal(b.kfs.begin(), b.kfs.end(), kfs)) {
+      *dplan = b.dplan;
+      *shape = b.shape;
+      return true;
+    }
+  }
+  return false;
+}
+
+static df_status fused_launches(void *dplan, const df::LaunchShape &shape,
+                                const df::FusedTuning &tune, const SolveCfg &c, int n_gn,
+                                int n_pcg, cudaStream_t s) {
+  const int chunk = tune.gn_per_launch > 0 ? tune.gn_per_launch : (n_gn > 0 ? n_gn : 1);
+  for (int g0 = 0, first = 1; g0 < n_gn || first; g0 += chunk, first = 0) {
+    const int m = std::min(chunk, n_gn - g0);
+    DF_CUDA(df::fused_launch(dplan, shape, c, m < 0 ? 0 : m, n_pcg, g_spin_limit_ns.load(), s,
+                             first));
+    if (n_gn == 0) break;
+  }
+  return DF_OK;
+}
+
 // Fused solve of a list of keyframes in as few launches as the plan allows
 // (a list whose tiles cannot share one grid is split in halves).
 static df_status fused_many(df_keyframe *const *kfs, int n, const SolveCfg &c, int n_gn,
@@ -488,29 +547,70 @@ static df_status fused_many(df_keyframe *const *kfs, int n, const SolveCfg &c, i
     if (st != DF_OK) return st;
     return fused_many(kfs + df::kMaxBatch, n - df::kMaxBatch, c, n_gn, n_pcg, s);
   }
+  const df::FusedTuning tune = current_tuning();
+  void *dplan = nullptr;
+  df::LaunchShape shape;
+  if (find_batch_plan(kfs, n, tune, &dplan, &shape))
+    return fused_launches(dplan, shape, tune, c, n_gn, n_pcg, s);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(DF_ENOTSUP, "batched solve under stream capture needs df_batch_prepare on "
+                            "this keyframe list first");
   std::vector<const Planes *> list(n);
   for (int j = 0; j < n; ++j) list[j] = &kfs[j]->planes;
   std::vector<char> host;
-  df::LaunchShape shape;
-  if (!df::fused_build_plan(list.data(), n, current_tuning(), host, shape)) {
+  if (!df::fused_build_plan(list.data(), n, tune, host, shape)) {
     const int h = n / 2;
     df_status st = fused_many(kfs, h, c, n_gn, n_pcg, s);
     if (st != DF_OK) return st;
     return fused_many(kfs + h, n - h, c, n_gn, n_pcg, s);
   }
-  void *dplan = nullptr;
   DF_CUDA(cudaMallocAsync(&dplan, host.size(), s));
   cudaError_t e = cudaMemcpyAsync(dplan, host.data(), host.size(), cudaMemcpyHostToDevice, s);
-  const df::FusedTuning tune = current_tuning();
-  const int chunk = tune.gn_per_launch > 0 ? tune.gn_per_launch : (n_gn > 0 ? n_gn : 1);
-  for (int g0 = 0, first = 1; e == cudaSuccess && (g0 < n_gn || first); g0 += chunk, first = 0) {
-    const int m = std::min(chunk, n_gn - g0);
-    e = df::fused_launch(dplan, shape, c, m < 0 ? 0 : m, n_pcg, g_spin_limit_ns.load(), s, first);
-    if (n_gn == 0) break;
-  }
+  df_status st = e == cudaSuccess ? fused_launches(dplan, shape, tune, c, n_gn, n_pcg, s)
+                                  : cuda_fail(e, "batch plan upload");
   cudaError_t e2 = cudaFreeAsync(dplan, s);
-  if (e != cudaSuccess) return cuda_fail(e, "fused batch launch");
+  if (st != DF_OK) return st;
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+  return DF_OK;
+}
+
+// df_batch_prepare: the plans fused_many would build for this list, kept.
+static df_status prepare_many(df_keyframe *const *kfs, int n, cudaStream_t s) {
+  if (n <= 1) return DF_OK;  // a single keyframe keeps its own plan
+  if (n > df::kMaxBatch) {
+    df_status st = prepare_many(kfs, df::kMaxBatch, s);
+    if (st != DF_OK) return st;
+    return prepare_many(kfs + df::kMaxBatch, n - df::kMaxBatch, s);
+  }
+  const df::FusedTuning tune = current_tuning();
+  void *dp = nullptr;
+  df::LaunchShape shape;
+  if (find_batch_plan(kfs, n, tune, &dp, &shape)) return DF_OK;
+  std::vector<const Planes *> list(n);
+  for (int j = 0; j < n; ++j) list[j] = &kfs[j]->planes;
+  std::vector<char> host;
+  if (!df::fused_build_plan(list.data(), n, tune, host, shape)) {
+    const int h = n / 2;
+    df_status st = prepare_many(kfs, h, s);
+    if (st != DF_OK) return st;
+    return prepare_many(kfs + h, n - h, s);
+  }
+  BatchPlan b;
+  DF_CUDA(cudaMalloc(&b.dplan, host.size()));
+  cudaError_t e = cudaMemcpyAsync(b.dplan, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(b.dplan);
+    return cuda_fail(e, "batch plan upload");
+  }
+  b.kfs.assign(kfs, kfs + n);
+  b.tune = tune;
+  cudaGetDevice(&b.device);
+  b.shape = shape;
+  std::lock_guard<std::mutex> lk(g_bp_mu);
+  g_bp.push_back(std::move(b));
   return DF_OK;
 }
 
@@ -581,6 +681,27 @@ df_status df_optimise_batch(df_keyframe *const *kfs, int32_t n, const df_solve_p
     }
     return worst;
   }
+  return DF_OK;
+}
+
+df_status df_batch_prepare(df_keyframe *const *kfs, int32_t n, void *stream) {
+  if (n < 0 || (n > 0 && !kfs)) return fail(DF_EINVAL, "bad keyframe list");
+  for (int j = 0; j < n; ++j) {
+    if (!kfs[j]) return fail(DF_EINVAL, "keyframe %d is NULL", j);
+    for (int m = 0; m < j; ++m)
+      if (kfs[m] == kfs[j]) return fail(DF_EINVAL, "keyframe %d appears twice", j);
+    if (kfs[j]->device != kfs[0]->device) return fail(DF_EINVAL, "keyframes on different devices");
+  }
+  if (n < 2) return DF_OK;
+  if (!df::fused_supported()) return fail(DF_ENOTSUP, "fused solver not available on this device");
+  DeviceGuard g(kfs[0]->device);
+  return prepare_many(kfs, n, static_cast<cudaStream_t>(stream));
+}
+
+df_status df_batch_release(df_keyframe *const *kfs, int32_t n) {
+  if (n < 0 || (n > 0 && !kfs)) return fail(DF_EINVAL, "bad keyframe list");
+  std::vector<df_keyframe *> v(kfs, kfs + n);
+  drop_batch_plans_if(v);
   return DF_OK;
 }
 
@@ -702,6 +823,7 @@ void df_keyframe_destroy(df_keyframe *kf) {
   if (!kf) return;
   {
     DeviceGuard g(kf->device);
+    drop_batch_plans_if({kf});
     cudaFree(kf->mem);  // waits for the keyframe's pending work
   }
   g_in_use.fetch_sub(kf->bytes);

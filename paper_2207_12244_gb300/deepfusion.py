@@ -134,6 +134,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.df_optimise_noalloc.argtypes = [C.c_int32, C.c_int32] + [vp] * 10 + [
         C.POINTER(df_solve_params), vp]
     L.df_optimise_noalloc.restype = C.c_int
+    L.df_batch_prepare.argtypes = [C.POINTER(vp), i32, vp]
+    L.df_batch_release.argtypes = [C.POINTER(vp), i32]
     L.df_mvs_default_params.argtypes = [C.POINTER(df_mvs_params)]
     L.df_mvs_default_params.restype = None
     L.df_mvs_create.argtypes = [i32, i32, C.POINTER(vp)]
@@ -309,6 +311,23 @@ def df_optimise_batch(kfs: Sequence, params: Optional[df_solve_params] = None, s
     _check(load().df_optimise_batch(arr, n, C.byref(params) if params is not None else None,
                                     _stream(stream), reps), "df_optimise_batch")
     return list(reps)[:n] if report else None
+
+
+def _kf_array(kfs):
+    n = len(kfs)
+    return (C.c_void_p * max(n, 1))(*[k.value if isinstance(k, C.c_void_p) else k for k in kfs]), n
+
+
+def df_batch_prepare(kfs: Sequence, stream=None):
+    """Keep the launch plans of this keyframe list (for repeated batched
+    solves and CUDA graph capture)."""
+    arr, n = _kf_array(kfs)
+    _check(load().df_batch_prepare(arr, n, _stream(stream)), "df_batch_prepare")
+
+
+def df_batch_release(kfs: Sequence):
+    arr, n = _kf_array(kfs)
+    _check(load().df_batch_release(arr, n), "df_batch_release")
 
 
 def df_fetch_depth(kf, out, log_space: bool = False, stream=None):

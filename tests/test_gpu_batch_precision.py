@@ -106,6 +106,62 @@ def test_batch_with_launch_schedule_and_bad_lists(o):
         k.close()
 
 
+@pytest.mark.parametrize("mode", [dfl.DF_MODE_STREAMING, dfl.DF_MODE_RESIDENT],
+                         ids=["streaming", "resident"])
+def test_prepared_batch_captured_in_a_cuda_graph(o, mode):
+    """A batched solve of uneven keyframes, prepared once and captured in a
+    CUDA graph, replays to the eager result bitwise; capturing an unprepared
+    batch is refused without touching the capture."""
+    torch = torch_cuda()
+    kfs = [synth.make_keyframe(W, H, 900 + i) for i, (W, H) in enumerate(SHAPES[:5])]
+    prm = params(n_gn=4, n_pcg=3, solver=dfl.DF_SOLVER_FUSED)
+    dfl.df_set_tuning(mode=mode)
+    ks = [create(kf) for kf in kfs]
+    try:
+        semi = [(to_dev(kf.mu_s), to_dev(kf.var_s)) for kf in kfs]
+        handles = [k.handle for k in ks]
+
+        def frame():
+            for k, (m, v) in zip(ks, semi):
+                k.frame_update(m, v)
+            dfl.df_optimise_batch(handles, prm)
+
+        frame()
+        eager = [_fetch(k, kf) for k, kf in zip(ks, kfs)]
+        for k, kf in zip(ks, kfs):
+            k.set_state(to_dev(kf.mu_n), 0.0)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g0 = torch.cuda.CUDAGraph()
+        refused = None
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g0, stream=s):
+                try:
+                    dfl.df_optimise_batch(handles, prm)
+                except dfl.DFError as e:
+                    refused = e.status
+        assert refused == dfl.DF_ENOTSUP
+        dfl.df_batch_prepare(handles)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                frame()
+        torch.cuda.current_stream().wait_stream(s)
+        g.replay()
+        torch.cuda.synchronize()
+        got = [_fetch(k, kf) for k, kf in zip(ks, kfs)]
+        for i, ((xe, te), (xg, tg)) in enumerate(zip(eager, got)):
+            assert np.array_equal(xe, xg) and te == tg, f"item {i}"
+            xo, to, _ = oracle_solve(o, kfs[i], prm)
+            assert_parity(xg, tg, xo, to, what=f"graph item {i}")
+        dfl.df_batch_release(handles)
+    finally:
+        for k in ks:
+            k.close()
+        dfl.df_set_tuning()
+
+
 def _rounded(kf, torch_dtype):
     """The network planes rounded to torch_dtype on the CPU (round to nearest
     even) and a copy of the keyframe whose planes are those values in FP32."""
