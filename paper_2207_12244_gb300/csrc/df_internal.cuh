@@ -98,17 +98,22 @@ __device__ __forceinline__ bool robust_active(float delta) {
   return delta > 0.0f && delta < INFINITY;
 }
 
+// IRLS weight omega(u) / V of a residual r with variance V, u = r / sqrt(V).
+// Huber: 1 / V inside the threshold (u^2 <= delta^2, i.e. r^2 <= delta^2 V,
+// no root needed), delta / (|r| sqrt(V)) beyond it. Tukey: (1 - (u/delta)^2)^2
+// / V inside, 0 beyond. The reciprocals use the hardware approximations
+// (rsqrtf, __fdividef: a few ulp), far inside the solve's tolerance; the
+// branch decisions use exact products.
 __device__ __forceinline__ float robust_weight(float r, float V, float delta, int loss) {
-  const float iv = 1.0f / V;
+  const float iv = __fdividef(1.0f, V);
   if (!robust_active(delta)) return iv;
-  const float u = fabsf(r) / sqrtf(V);
+  const float r2 = r * r, d2v = delta * delta * V;
   if (loss == DF_LOSS_TUKEY) {
-    if (u >= delta) return 0.0f;
-    const float a = u / delta;
-    const float q = 1.0f - a * a;
+    if (r2 >= d2v) return 0.0f;
+    const float q = 1.0f - __fdividef(r2, d2v);
     return q * q * iv;
   }
-  return (u <= delta) ? iv : (delta / u) * iv;
+  return (r2 <= d2v) ? iv : __fdividef(delta * rsqrtf(V), fabsf(r));
 }
 
 // Robust loss rho(u) (the cost of Eq. 5 with each squared whitened residual
