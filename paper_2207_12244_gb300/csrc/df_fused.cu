@@ -555,21 +555,23 @@ __device__ __forceinline__ void store4(float *p, const F<4> &a) {
 
 // Rows jb..je of a tile go through the ring in order; 'ensure(k)' waits for
 // the k-th of them, 'release()' frees the oldest waited row's stage and
-// stages the next row of the tile. Rows at index 0 (when has_above) and
-// R - 1 (when has_below) are halo rows and stage only the planes of
-// 'halo_mask'; the others stage those of 'mask'.
-template <int NP>
+// stages the next row of the tile. Planes 0..NP-1; bit p of HALF marks a
+// 16-bit plane. Rows at index 0 (when has_above) and R - 1 (when has_below)
+// are halo rows and stage only planes 0..NH-1; the others stage the planes
+// of 'mask' (all NP unless a pass leaves some out). Plane counts and widths
+// are compile-time, so a row's copies are a straight run of instructions.
+template <int NP, int NH, uint32_t HALF>
 struct TileRows {
   RowRing &ring;
   const char *src[NP];  // next row's copy start per plane
-  uint32_t half = 0;    // bit p: plane p holds 16-bit values
   uint32_t b4, d4, b2, d2, rb4, rb2;
-  uint32_t mask, halo_mask;
+  uint32_t mask;
   int R, issued = 0, waited = 0;
   bool has_above, has_below, ok = true;
-  __device__ TileRows(RowRing &r, const StagePlane (&pl)[NP], uint32_t mask_, uint32_t halo_mask_,
-                      int c0, int P, int jb, int R_, bool above, bool below)
-      : ring(r), mask(mask_), halo_mask(halo_mask_), R(R_), has_above(above), has_below(below) {
+  static constexpr uint32_t kAll = (NP >= 32) ? 0xffffffffu : ((1u << NP) - 1u);
+  __device__ TileRows(RowRing &r, const StagePlane (&pl)[NP], int c0, int P, int jb, int R_,
+                      bool above, bool below, uint32_t mask_ = kAll)
+      : ring(r), mask(mask_), R(R_), has_above(above), has_below(below) {
     // column range [cs, ce) of a staged row: the tile's 128 columns and
     // 16 bytes on each side, clipped to the padded row
     const int cs4 = c0 - 4 > 0 ? c0 - 4 : 0, ce4 = c0 + 132 < P ? c0 + 132 : P;
@@ -582,8 +584,8 @@ struct TileRows {
     rb2 = (uint32_t)P * 2u;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      const bool h = pl[p].esize == 2;
-      half |= (uint32_t)h << p;
+      constexpr uint32_t H = HALF;
+      const bool h = (H >> p) & 1u;
       src[p] = static_cast<const char *>(pl[p].base) + (size_t)jb * (h ? rb2 : rb4) +
                (size_t)(h ? cs2 * 2 : cs4 * 4);
     }
@@ -593,9 +595,48 @@ struct TileRows {
   __device__ __forceinline__ void issue_one() {
     __syncwarp();
     const bool halo = (has_above && issued == 0) || (has_below && issued == R - 1);
-    ring.issue<NP>(issued % kStages, src, half, b4, d4, b2, d2, halo ? halo_mask : mask);
+    const int s = issued % kStages;
+    if ((threadIdx.x & 31) == 0) {
+      char *base = ring.smem + s * kStageBytes;
+      uint64_t *bar = &ring.bars[s];
+      fence_proxy_async_shared();  // earlier generic reads of this stage come first
+      if (halo) {
+        constexpr uint32_t hm = (1u << NH) - 1u;
+        constexpr int n2 = __builtin_popcount(HALF & hm), n4 = NH - n2;
+        mbar_arrive_expect_tx(bar, (uint32_t)n4 * b4 + (uint32_t)n2 * b2);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) src[p] += ((half >> p) & 1u) ? rb2 : rb4;
+        for (int p = 0; p < NH; ++p) {
+          constexpr uint32_t H = HALF;
+          const bool h = (H >> p) & 1u;
+          bulk_copy_g2s(base + p * kSlotBytes + (h ? d2 : d4), src[p], h ? b2 : b4, bar);
+        }
+      } else if (mask == kAll) {
+        constexpr int n2 = __builtin_popcount(HALF & kAll), n4 = NP - n2;
+        mbar_arrive_expect_tx(bar, (uint32_t)n4 * b4 + (uint32_t)n2 * b2);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          constexpr uint32_t H = HALF;
+          const bool h = (H >> p) & 1u;
+          bulk_copy_g2s(base + p * kSlotBytes + (h ? d2 : d4), src[p], h ? b2 : b4, bar);
+        }
+      } else {
+        const uint32_t n2 = __popc(mask & HALF), n4 = __popc(mask & ~HALF);
+        mbar_arrive_expect_tx(bar, n4 * b4 + n2 * b2);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          constexpr uint32_t H = HALF;
+          const bool h = (H >> p) & 1u;
+          if (mask & (1u << p))
+            bulk_copy_g2s(base + p * kSlotBytes + (h ? d2 : d4), src[p], h ? b2 : b4, bar);
+        }
+      }
+    }
+    ring.pending |= 1u << s;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      constexpr uint32_t H = HALF;
+      src[p] += ((H >> p) & 1u) ? rb2 : rb4;
+    }
     ++issued;
   }
   __device__ __forceinline__ int stage(int k) const { return k % kStages; }
@@ -687,8 +728,8 @@ __device__ __forceinline__ bool tma_cg_tile(RowRing &ring, const FusedKf &K, con
   pl[I::WY] = {k.wy, 4};
   const int jb = g.r0 > 0 ? g.r0 - 1 : g.r0;
   const int je = min(g.r0 + g.nrows, H - 1);
-  TileRows<I::NP> rows(ring, pl, (1u << I::NP) - 1, (1u << I::NH) - 1, g.c0, (int)P, jb,
-                       je - jb + 1, g.r0 > 0, g.r0 + g.nrows < H);
+  TileRows<I::NP, I::NH, 0u> rows(ring, pl, g.c0, (int)P, jb, je - jb + 1, g.r0 > 0,
+                                  g.r0 + g.nrows < H);
   F<4> u_up = fzero<4>(), wy_up = fzero<4>();
   int kc = 0;
   if (g.r0 > 0) {
@@ -782,7 +823,7 @@ __device__ __forceinline__ bool tma_final_tile(RowRing &ring, const FusedKf &K, 
   if (update) mask |= (1u << iR) | (1u << iW) | (1u << iD);
   if (update && !first) mask |= (1u << iS) | (1u << iP);
   if (scale) mask |= (1u << iMS) | (1u << iVS);
-  TileRows<8> rows(ring, pl, mask, mask, g.c0, k.P, g.r0, g.nrows, false, false);
+  TileRows<8, 8, 0u> rows(ring, pl, g.c0, k.P, g.r0, g.nrows, false, false, mask);
   size_t i = (size_t)g.r0 * k.P + g.col;
   for (int j = 0; j < g.nrows; ++j) {
     if (!rows.ensure(j)) return false;
@@ -824,7 +865,7 @@ __device__ __forceinline__ bool tma_scale_tile(RowRing &ring, const FusedKf &K, 
                                const SolveCfg &c, float acc[kQ]) {
   const Planes &k = K.pl;
   const StagePlane pl[3] = {{k.x, 4}, {k.mu_s, 4}, {k.var_s, 4}};
-  TileRows<3> rows(ring, pl, 7u, 7u, g.c0, k.P, g.r0, g.nrows, false, false);
+  TileRows<3, 3, 0u> rows(ring, pl, g.c0, k.P, g.r0, g.nrows, false, false);
   for (int j = 0; j < g.nrows; ++j) {
     if (!rows.ensure(j)) return false;
     const int s = rows.stage(j);
@@ -862,8 +903,13 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
   float *r_out = k.v[1];
   const int jb = g.r0 > 0 ? g.r0 - 1 : g.r0;
   const int je = min(g.r0 + g.nrows, H - 1);
-  TileRows<A_NP> rows(ring, pl, (1u << A_NP) - 1, (1u << A_GY) | (1u << A_VY) | (1u << A_X),
-                       g.c0, (int)P, jb, je - jb + 1, g.r0 > 0, g.r0 + g.nrows < H);
+  // 16-bit planes: the network planes when DT is BF16 / FP16
+  constexpr uint32_t kHalf =
+      DT == DF_F32 ? 0u
+                   : ((1u << A_GY) | (1u << A_VY) | (1u << A_MN) | (1u << A_VN) | (1u << A_GX) |
+                      (1u << A_VX));
+  TileRows<A_NP, 3, kHalf> rows(ring, pl, g.c0, (int)P, jb, je - jb + 1, g.r0 > 0,
+                                g.r0 + g.nrows < H);
   int kc = 0;
   F<4> wy_up = fzero<4>(), ey_up = fzero<4>(), gy_up = fzero<4>();
   if (g.r0 > 0) {

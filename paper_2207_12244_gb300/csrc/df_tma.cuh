@@ -75,7 +75,8 @@ struct StagePlane {
   int esize;
 };
 
-// A warp's ring of row stages. Lane 0 issues, every lane waits and reads.
+// A warp's ring of row stages. Lane 0 issues the copies (the tile's row
+// walker does), every lane waits and reads.
 struct RowRing {
   char *smem;         // kWarpStageBytes of this warp
   uint64_t *bars;     // kStages mbarriers
@@ -85,28 +86,6 @@ struct RowRing {
 
   __device__ __forceinline__ char *slot(int s, int p) const {
     return smem + s * kStageBytes + p * kSlotBytes;
-  }
-
-  // Stage the planes of 'mask' (bit p: plane p) of a row: plane p's copy
-  // starts at src[p]; planes of 'half' (16-bit) copy b2 bytes to slot
-  // offset d2, the others (f32) b4 bytes to offset d4.
-  template <int NP>
-  __device__ __forceinline__ void issue(int s, const char *const (&src)[NP], uint32_t half,
-                                        uint32_t b4, uint32_t d4, uint32_t b2, uint32_t d2,
-                                        uint32_t mask) {
-    if ((threadIdx.x & 31) == 0) {
-      const uint32_t n2 = __popc(mask & half), n4 = __popc(mask & ~half);
-      fence_proxy_async_shared();  // earlier generic reads of this stage come first
-      mbar_arrive_expect_tx(&bars[s], n4 * b4 + n2 * b2);
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        if (mask & (1u << p)) {
-          const bool h = (half >> p) & 1u;
-          bulk_copy_g2s(slot(s, p) + (h ? d2 : d4), src[p], h ? b2 : b4, &bars[s]);
-        }
-      }
-    }
-    pending |= 1u << s;
   }
 
   // Wait until stage s has landed; false if the wait ran out of time.
