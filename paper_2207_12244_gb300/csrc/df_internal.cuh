@@ -98,22 +98,22 @@ __device__ __forceinline__ bool robust_active(float delta) {
   return delta > 0.0f && delta < INFINITY;
 }
 
-// IRLS weight omega(u) / V of a residual r with variance V, u = r / sqrt(V).
-// Huber: 1 / V inside the threshold (u^2 <= delta^2, i.e. r^2 <= delta^2 V,
-// no root needed), delta / (|r| sqrt(V)) beyond it. Tukey: (1 - (u/delta)^2)^2
-// / V inside, 0 beyond. The reciprocals use the hardware approximations
-// (rsqrtf, __fdividef: a few ulp), far inside the solve's tolerance; the
-// branch decisions use exact products.
+// IRLS weight omega(u) / V of a residual r with variance V, u^2 = r^2 / V.
+// Huber: omega = min(1, delta / |u|), written min(1, delta rsqrt(u^2)) (1
+// at u = 0, where rsqrt gives +inf). Tukey: omega = (1 - u^2 / delta^2)^2
+// for u^2 < delta^2, else 0. Both are continuous at the threshold, so no
+// result hinges on a comparison; the reciprocals use the hardware
+// approximations (rsqrtf, __fdividef: a few ulp, far inside the solve's
+// tolerance).
 __device__ __forceinline__ float robust_weight(float r, float V, float delta, int loss) {
   const float iv = __fdividef(1.0f, V);
   if (!robust_active(delta)) return iv;
-  const float r2 = r * r, d2v = delta * delta * V;
+  const float u2 = r * r * iv;
   if (loss == DF_LOSS_TUKEY) {
-    if (r2 >= d2v) return 0.0f;
-    const float q = 1.0f - __fdividef(r2, d2v);
-    return q * q * iv;
+    const float q = 1.0f - __fdividef(u2, delta * delta);
+    return u2 < delta * delta ? q * q * iv : 0.0f;
   }
-  return (r2 <= d2v) ? iv : __fdividef(delta * rsqrtf(V), fabsf(r));
+  return iv * fminf(1.0f, delta * rsqrtf(u2));
 }
 
 // Robust loss rho(u) (the cost of Eq. 5 with each squared whitened residual
