@@ -5,11 +5,12 @@
 //  1. k_mvs_select (one thread per pixel): texture and interval tests; the
 //     candidates are appended to a compact list (one atomic per warp), the
 //     others get their status.
-//  2. k_mvs_search (one warp per listed pixel): the lanes split the 1-pixel
-//     steps of the epipolar segment, each computing the 5-sample error
-//     (Eq. 2) of its steps; a warp argmin (first minimum on ties) picks the
-//     best step; three lanes recompute the best step and its two neighbours,
-//     and lane 0 fits the sub-pixel depth between the best step and its
+//  2. k_mvs_search (a group of kGroup lanes per listed pixel): the lanes
+//     split the 1-pixel steps of the epipolar segment, each computing the
+//     5-sample error (Eq. 2) of its steps; a group argmin (first minimum on
+//     ties) picks the best step; three lanes recompute the best step and its
+//     two neighbours, and the group's first lane fits the sub-pixel depth
+//     between the best step and its
 //     better neighbour, sets sigma^2 = photo_var (J^T J)^-1 (Eqs. 3, 4) and
 //     fuses the measurement with the current estimate.
 //
@@ -152,18 +153,30 @@ __device__ __forceinline__ bool step_error(const Walk &w, const MvsGeo &g,
   return true;
 }
 
+// Lanes per listed pixel: a warp serves 32 / kGroup pixels at once. With an
+// estimate the search interval spans only a few steps, so a whole warp per
+// pixel would leave most lanes idle; long walks take more rounds per pixel
+// but as many steps per warp and round.
+constexpr int kGroup = 8;
+
 __global__ void __launch_bounds__(kSearchThreads)
     k_mvs_search(int W, int H, const float *__restrict__ img_key,
                  const float *__restrict__ img_ref, MvsGeo g, MvsCfg p,
                  const int *__restrict__ list, const int *__restrict__ count,
                  float *__restrict__ depth, float *__restrict__ var, int *__restrict__ status,
                  int *__restrict__ best_step, unsigned long long *__restrict__ steps) {
-  const int lane = threadIdx.x & 31;
+  constexpr int kPerWarp = 32 / kGroup;
+  const int wl = threadIdx.x & 31;
+  const int grp = wl / kGroup, lane = wl % kGroup, g0 = grp * kGroup;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int total = *count;
-  for (int e = warp; e < total; e += nwarps) {
-    const int i = list[e];
+  // every lane runs every round (the shuffles span the warp); groups past
+  // the end of the list compute nothing and write nothing
+  for (int base = warp * kPerWarp; base < total; base += nwarps * kPerWarp) {
+    const int e = base + grp;
+    const bool live = e < total;
+    const int i = live ? list[e] : list[base];
     const int v = i / W, u = i - v * W;
     const float uf = (float)u, vf = (float)v;
     const float dp = depth[i], vp = var[i];
@@ -219,12 +232,14 @@ __global__ void __launch_bounds__(kSearchThreads)
       for (int s = -2; s <= 2 && ok; ++s)
         ok = bilin(img_key, W, H, uf + (float)s * e0x, vf + (float)s * e0y, &w.key[s + 2]);
     }
-    if (ok) {
-      if (lane == 0) atomicAdd(steps, (unsigned long long)(w.n + 3));  // walk + 3 recomputed
-      // the walk: lane-strided steps, then a warp argmin (first minimum)
+    ok = ok && live;
+    if (live && ok && lane == 0) atomicAdd(steps, (unsigned long long)(w.n + 3));  // + 3 recomputed
+    {
+      // the walk: group-strided steps, then a group argmin (first minimum)
       float best = INFINITY;
       int bj = 0x7fffffff;
-      for (int j = lane; j < w.n; j += 32) {
+      const int n = ok ? w.n : 0;
+      for (int j = lane; j < n; j += kGroup) {
         float ev[5], ssd, dj;
         if (step_error(w, g, img_ref, W, H, j, ev, &ssd, &dj) && ssd < best) {
           best = ssd;
@@ -232,7 +247,7 @@ __global__ void __launch_bounds__(kSearchThreads)
         }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = kGroup / 2; o > 0; o >>= 1) {  // xor below kGroup stays in the group
         const float ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
         if (ob < best || (ob == best && oj < bj)) {
@@ -240,57 +255,63 @@ __global__ void __launch_bounds__(kSearchThreads)
           bj = oj;
         }
       }
-      st = DF_MVS_NOSTEP;
-      if (bj != 0x7fffffff) {
+      // the sub-pixel fit: lanes 0, 1, 2 of the group evaluate steps
+      // bj - 1, bj, bj + 1; every lane runs the shuffles that gather them
+      const bool have = ok && bj != 0x7fffffff;
+      const bool fit = have && best <= p.ssd_max;
+      float ev[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, ssd = 0.0f, dj = 0.0f;
+      bool okj = false;
+      if (fit && lane < 3) okj = step_error(w, g, img_ref, W, H, bj - 1 + lane, ev, &ssd, &dj);
+      float em[5], ea[5], ep[5];
+#pragma unroll
+      for (int s = 0; s < 5; ++s) {
+        em[s] = __shfl_sync(0xffffffffu, ev[s], g0);
+        ea[s] = __shfl_sync(0xffffffffu, ev[s], g0 + 1);
+        ep[s] = __shfl_sync(0xffffffffu, ev[s], g0 + 2);
+      }
+      const float sm = __shfl_sync(0xffffffffu, ssd, g0), sq = __shfl_sync(0xffffffffu, ssd, g0 + 2);
+      const float dm = __shfl_sync(0xffffffffu, dj, g0), da = __shfl_sync(0xffffffffu, dj, g0 + 1),
+                  dq = __shfl_sync(0xffffffffu, dj, g0 + 2);
+      const bool okm = __shfl_sync(0xffffffffu, okj, g0), okp = __shfl_sync(0xffffffffu, okj, g0 + 2);
+      if (!ok) {
+        st = DF_MVS_LINE;
+      } else if (!have) {
+        st = DF_MVS_NOSTEP;
+      } else if (!fit) {
         bk = bj;
         st = DF_MVS_SSD;
-        if (best <= p.ssd_max) {
-          // lanes 0, 1, 2: steps bj - 1, bj, bj + 1
-          float ev[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, ssd = 0.0f, dj = 0.0f;
-          bool okj = false;
-          if (lane < 3) okj = step_error(w, g, img_ref, W, H, bj - 1 + lane, ev, &ssd, &dj);
-          float em[5], ea[5], ep[5];
+      } else {
+        bk = bj;
+        st = DF_MVS_NEIGHBOUR;
+        if (okm || okp) {
+          const bool take_m = okm && (!okp || sm <= sq);
+          float D2 = 0.0f, ade = 0.0f;
 #pragma unroll
           for (int s = 0; s < 5; ++s) {
-            em[s] = __shfl_sync(0xffffffffu, ev[s], 0);
-            ea[s] = __shfl_sync(0xffffffffu, ev[s], 1);
-            ep[s] = __shfl_sync(0xffffffffu, ev[s], 2);
+            const float de = (take_m ? em[s] : ep[s]) - ea[s];
+            D2 += de * de;
+            ade += ea[s] * de;
           }
-          const float sm = __shfl_sync(0xffffffffu, ssd, 0), sq = __shfl_sync(0xffffffffu, ssd, 2);
-          const float dm = __shfl_sync(0xffffffffu, dj, 0), da = __shfl_sync(0xffffffffu, dj, 1),
-                      dq = __shfl_sync(0xffffffffu, dj, 2);
-          const bool okm = __shfl_sync(0xffffffffu, okj, 0), okp = __shfl_sync(0xffffffffu, okj, 2);
-          st = DF_MVS_NEIGHBOUR;
-          if (okm || okp) {
-            const bool take_m = okm && (!okp || sm <= sq);
-            float D2 = 0.0f, ade = 0.0f;
-#pragma unroll
-            for (int s = 0; s < 5; ++s) {
-              const float de = (take_m ? em[s] : ep[s]) - ea[s];
-              D2 += de * de;
-              ade += ea[s] * de;
-            }
-            if (D2 > 0.0f) {
-              const float sstar = fminf(fmaxf(-ade / D2, 0.0f), 1.0f);
-              const float dd = (take_m ? dm : dq) - da;
-              const float d_obs = da + sstar * dd;
-              const float v_obs = p.photo_var * dd * dd / D2;
-              if (v_obs > 0.0f && isfinite(v_obs)) {
-                if (has) {
-                  d_new = (dp * v_obs + d_obs * vp) / (vp + v_obs);
-                  v_new = vp * v_obs / (vp + v_obs);
-                } else {
-                  d_new = d_obs;
-                  v_new = v_obs;
-                }
-                st = DF_MVS_OK;
+          if (D2 > 0.0f) {
+            const float sstar = fminf(fmaxf(-ade / D2, 0.0f), 1.0f);
+            const float dd = (take_m ? dm : dq) - da;
+            const float d_obs = da + sstar * dd;
+            const float v_obs = p.photo_var * dd * dd / D2;
+            if (v_obs > 0.0f && isfinite(v_obs)) {
+              if (has) {
+                d_new = (dp * v_obs + d_obs * vp) / (vp + v_obs);
+                v_new = vp * v_obs / (vp + v_obs);
+              } else {
+                d_new = d_obs;
+                v_new = v_obs;
               }
+              st = DF_MVS_OK;
             }
           }
         }
       }
     }
-    if (lane == 0) {
+    if (live && lane == 0) {
       if (st == DF_MVS_OK) {
         depth[i] = d_new;
         var[i] = v_new;
