@@ -38,6 +38,7 @@ constexpr int kSearchThreads = 256;  // 8 warps, one pixel each at a time
 
 struct MvsGeo {
   float fx, fy, cx, cy;
+  float ifx, ify;  // 1 / fx, 1 / fy
   float R[9], t[3];
   float C[3];  // reference camera centre in keyframe coordinates, -R^T t
 };
@@ -127,10 +128,10 @@ __device__ __forceinline__ bool step_error(const Walk &w, const MvsGeo &g,
   // d (q~ a0_z - a0_x) = t_x - q~ t_z (or the y row)
   float d;
   if (w.use_x) {
-    const float qt = (qx - g.cx) / g.fx;
+    const float qt = (qx - g.cx) * g.ifx;
     d = (g.t[0] - qt * g.t[2]) / (qt * w.a0[2] - w.a0[0]);
   } else {
-    const float qt = (qy - g.cy) / g.fy;
+    const float qt = (qy - g.cy) * g.ify;
     d = (g.t[1] - qt * g.t[2]) / (qt * w.a0[2] - w.a0[1]);
   }
   if (!(d > 0.0f) || !isfinite(d)) return false;
@@ -142,7 +143,8 @@ __device__ __forceinline__ bool step_error(const Walk &w, const MvsGeo &g,
     const float Y1 = d * (w.a0[1] + sf * w.a1[1]) + g.t[1];
     const float Y2 = d * (w.a0[2] + sf * w.a1[2]) + g.t[2];
     if (!(Y2 > 0.0f)) return false;
-    const float pu = g.fx * Y0 / Y2 + g.cx, pv = g.fy * Y1 / Y2 + g.cy;
+    const float iz = 1.0f / Y2;  // one exact reciprocal for both coordinates
+    const float pu = g.fx * Y0 * iz + g.cx, pv = g.fy * Y1 * iz + g.cy;
     float val;
     if (!bilin(I1, W, H, pu, pv, &val)) return false;
     e[s + 2] = val - w.key[s + 2];
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kSearchThreads)
     float d_new = dp, v_new = vp;
     Walk w;
     // keyframe ray and epipolar direction (x - epipole, scaled by C_z)
-    const float r0 = (uf - g.cx) / g.fx, r1 = (vf - g.cy) / g.fy;
+    const float r0 = (uf - g.cx) * g.ifx, r1 = (vf - g.cy) * g.ify;
 #pragma unroll
     for (int k = 0; k < 3; ++k) w.a0[k] = g.R[3 * k] * r0 + g.R[3 * k + 1] * r1 + g.R[3 * k + 2];
     float e0x = g.C[2] * (uf - g.cx) - g.fx * g.C[0];
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kSearchThreads)
     if (ok) {
       e0x /= ne;
       e0y /= ne;
-      const float s0 = e0x / g.fx, s1 = e0y / g.fy;
+      const float s0 = e0x * g.ifx, s1 = e0y * g.ify;
 #pragma unroll
       for (int k = 0; k < 3; ++k) w.a1[k] = g.R[3 * k] * s0 + g.R[3 * k + 1] * s1;
 #pragma unroll
@@ -391,6 +393,8 @@ df_status df_mvs_update(df_mvs *m, const float *img_key, const float *img_ref,
   g.fy = cam->fy;
   g.cx = cam->cx;
   g.cy = cam->cy;
+  g.ifx = 1.0f / cam->fx;
+  g.ify = 1.0f / cam->fy;
   for (int k = 0; k < 9; ++k) g.R[k] = key_to_ref->R[k];
   for (int k = 0; k < 3; ++k) g.t[k] = key_to_ref->t[k];
   for (int r = 0; r < 3; ++r)
