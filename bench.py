@@ -282,9 +282,10 @@ def run_serving(args, ws, rank, dev, torch, dfl, replicas, synth):
         try:
             sids = [dfl.df_server_open_stream(srv, kf.width, kf.height, *c)
                     for (kf, _, _), c in zip(seqs, cnn)]
-            # warm-up: one frame per stream
-            ws_t, ws_s = serving.poisson_schedule(len(sids), 1e6, len(sids), seed=1)
-            serving.run(srv, sids, frames, ws_t, np.arange(len(sids)))
+            # warm-up: args.warmup rounds of one frame per stream
+            for _ in range(max(1, args.warmup)):
+                ws_t, ws_s = serving.poisson_schedule(len(sids), 1e6, len(sids), seed=1)
+                serving.run(srv, sids, frames, ws_t, np.arange(len(sids)))
             torch.cuda.synchronize()
             st = serving.run(srv, sids, frames, t, s)
         finally:
@@ -300,7 +301,8 @@ def run_serving(args, ws, rank, dev, torch, dfl, replicas, synth):
     if rank == 0:
         line = {
             "metric": METRIC, "value": units_all / wall / 1e6, "unit": METRIC, "n_gpus": ws,
-            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall, "higher_is_better": True,
+            "steps": 1, "warmup": max(1, args.warmup), "ms_per_step": 1e3 * wall,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
             "config": {"workload": "serving-32streams-640x480+1280x960-poisson-10x5",
@@ -748,7 +750,8 @@ def main():
                          args.n_gn * ALG_BYTES_PER_GN_PX)
     peak, peak_kind = peaks()
     achieved = alg_bytes / solve_avg_s / 1e9
-    kernel_key = f"solve_{args.solver}_{WORKLOAD}"
+    kernel_key = f"solve_{args.solver}_{WORKLOAD}" + (
+        "" if args.scale_step == "alternate" else f"_{args.scale_step}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": ncu_traffic(kernel_key),
                 "peak_kind": peak_kind, "region": "df_optimise (one frame's solve)",
