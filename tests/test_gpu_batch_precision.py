@@ -228,3 +228,40 @@ def test_reduced_precision_host_pointers():
     with pytest.raises(dfl.DFError) as e:
         dfl.Keyframe(kf.width, kf.height, *bad, cnn_dtype=dfl.DF_BF16)
     assert e.value.status == dfl.DF_EINVAL
+
+
+@pytest.mark.parametrize("mode", [dfl.DF_MODE_STREAMING, dfl.DF_MODE_RESIDENT],
+                         ids=["streaming", "resident"])
+def test_batch_of_mixed_network_precisions(o, mode):
+    """One fused launch over keyframes whose network planes are stored in
+    FP32, BF16 and FP16: each keyframe meets the FP32 bar against the oracle
+    on its own (rounded) inputs."""
+    torch = torch_cuda()
+    shapes = [(96, 72), (50, 37), (128, 40), (33, 90)]
+    dts = [dfl.DF_F32, dfl.DF_BF16, dfl.DF_F16, dfl.DF_BF16]
+    kfs = [synth.make_keyframe(W, H, 1100 + i) for i, (W, H) in enumerate(shapes)]
+    prm = params(n_gn=6, n_pcg=4, solver=dfl.DF_SOLVER_FUSED)
+    dfl.df_set_tuning(mode=mode)
+    ks, refs = [], []
+    try:
+        for kf, dt in zip(kfs, dts):
+            if dt == dfl.DF_F32:
+                ks.append(create(kf))
+                refs.append(kf)
+            else:
+                td = torch.bfloat16 if dt == dfl.DF_BF16 else torch.float16
+                planes, kr = _rounded(kf, td)
+                ks.append(dfl.Keyframe(kf.width, kf.height, *[p.cuda() for p in planes],
+                                       cnn_dtype=dt))
+                refs.append(kr)
+        for k, kf in zip(ks, kfs):
+            k.frame_update(to_dev(kf.mu_s), to_dev(kf.var_s))
+        dfl.df_optimise_batch([k.handle for k in ks], prm)
+        for i, (k, kf, kr) in enumerate(zip(ks, kfs, refs)):
+            x, t = _fetch(k, kf)
+            xo, to, _ = oracle_solve(o, kr, prm)
+            assert_parity(x, t, xo, to, what=f"mixed batch item {i} dtype {dts[i]}")
+    finally:
+        for k in ks:
+            k.close()
+        dfl.df_set_tuning()
