@@ -71,6 +71,9 @@ def parse():
                     help="network-plane storage for --workload precision")
     ap.add_argument("--no-graph", action="store_true",
                     help="batch64: launch the batched solve eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--graph", action="store_true",
+                    help="sequence: replay each frame's work (semi-dense update, solve, depth "
+                         "output) from a CUDA graph captured once")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batch64: keep the default launch shape instead of autotuning it")
     ap.add_argument("--rate", type=float, default=600.0, help="serving: frames/s offered")
@@ -705,21 +708,58 @@ def main():
     ev_opt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(F)]
 
+    # one frame's work (semi-dense update, solve, depth output) captured once
+    # in a CUDA graph on fixed buffers and replayed per frame
+    graph = None
+    graph_launches = 0
+    mu_in = torch.empty_like(mus_d[0])
+    var_in = torch.empty_like(vs_d[0])
+    out_fix = torch.empty((H, W), dtype=torch.float32, device=dev)
+
+    def frame_eager(f):
+        k.frame_update(mus_d[f], vs_d[f], stream=sptr)
+        k.optimise(prm, stream=sptr)
+
     def step(record_solve: bool):
         k.reset(*cnn_d, stream=sptr)
         for f in range(F):
-            k.frame_update(mus_d[f], vs_d[f], stream=sptr)
-            if record_solve:
-                ev_opt[f][0].record(stream)
-            k.optimise(prm, stream=sptr)
-            if record_solve:
-                ev_opt[f][1].record(stream)
-            k.fetch_depth(out_d[f], stream=sptr)
+            if graph is not None:
+                mu_in.copy_(mus_d[f], non_blocking=True)
+                var_in.copy_(vs_d[f], non_blocking=True)
+                if record_solve:
+                    ev_opt[f][0].record(stream)
+                graph.replay()
+                if record_solve:
+                    ev_opt[f][1].record(stream)
+                out_d[f].copy_(out_fix, non_blocking=True)
+            else:
+                k.frame_update(mus_d[f], vs_d[f], stream=sptr)
+                if record_solve:
+                    ev_opt[f][0].record(stream)
+                k.optimise(prm, stream=sptr)
+                if record_solve:
+                    ev_opt[f][1].record(stream)
+                k.fetch_depth(out_d[f], stream=sptr)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step(False)
     torch.cuda.synchronize()
+    if args.graph:
+        g = torch.cuda.CUDAGraph()
+        cap0 = dfl.df_kernel_launches()
+        with torch.cuda.stream(stream):
+            with torch.cuda.graph(g, stream=stream):
+                k.frame_update(mu_in, var_in, stream=sptr)
+                k.optimise(prm, stream=sptr)
+                k.fetch_depth(out_fix, stream=sptr)
+        torch.cuda.synchronize()
+        graph_launches = dfl.df_kernel_launches() - cap0
+        graph = g
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step(False)
+        torch.cuda.synchronize()
 
     step_ms, solve_ms = [], []
     launches0 = dfl.df_kernel_launches()
@@ -738,7 +778,8 @@ def main():
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             solve_ms.extend(a.elapsed_time(b) for a, b in ev_opt)
-    launches = dfl.df_kernel_launches() - launches0
+    # a replayed graph's kernels are counted from its capture, once per frame
+    launches = dfl.df_kernel_launches() - launches0 + graph_launches * F * args.steps
     clocks = clk.summary()
     total_ms = replicas.max_over_ranks(sum(step_ms), device=dev)
     units_per_step = W * H * args.n_gn * args.n_pcg * F
@@ -793,6 +834,8 @@ def main():
     truth_d = torch.from_numpy(np.exp(kf.log_depth_true).astype(np.float32)).to(dev)
     with torch.cuda.stream(stream):
         step(False)
+    torch.cuda.synchronize()
+    graph = None  # the accuracy check and the host-buffer leg run eagerly
     n_in, n_valid = k.depth_accuracy(truth_d, 0.1, stream=sptr)
     k.reset(*cnn_d, stream=sptr)
     n_in0, _ = k.depth_accuracy(truth_d, 0.1, stream=sptr)
@@ -813,7 +856,7 @@ def main():
             "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
             "config": {"workload": WORKLOAD, "width": W, "height": H, "frames": F,
                        "n_gn": args.n_gn, "n_pcg": args.n_pcg, "solver": args.solver,
-                       "scale_step": args.scale_step,
+                       "scale_step": args.scale_step, "cuda_graph": bool(args.graph),
                        "kernel_mode": args.mode, "max_ctas": args.max_ctas,
                        "parallelism": f"replicas x{ws}",
                        "l2": "flushed between steps (256 MB write)"},
