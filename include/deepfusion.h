@@ -83,9 +83,12 @@ typedef struct {
  *                     (A, b: the depth step's 5-point system; ws: the
  *                     semi-dense weights), preconditioned by diag(A) and
  *                     sum ws. Not in the paper: a solver variant that needs
- *                     no alternation. Runs on the launch solver only: with
- *                     DF_SOLVER_FUSED the solve returns DF_ENOTSUP, with
- *                     DF_SOLVER_AUTO it takes the launch solver. */
+ *                     no alternation. Runs on the launch solver and, with a
+ *                     fixed iteration count (tol = 0), on the fused solver
+ *                     when the keyframe's launch shape is shared-memory
+ *                     resident; otherwise DF_SOLVER_AUTO takes the launch
+ *                     solver and DF_SOLVER_FUSED returns DF_ENOTSUP. Batches
+ *                     are solved keyframe by keyframe. */
 #define DF_SCALE_FIXED 0
 #define DF_SCALE_ALTERNATE 1
 #define DF_SCALE_JOINT 2

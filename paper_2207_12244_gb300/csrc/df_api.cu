@@ -12,6 +12,7 @@
 #include <string>
 
 #include "df_fused.cuh"
+#include "df_sync.cuh"
 #include "df_internal.cuh"
 
 using df::Planes;
@@ -440,20 +441,23 @@ static bool same_tuning(const df::FusedTuning &a, const df::FusedTuning &b) {
 
 static int pick_solver(const df_solve_params &p) {
   if (p.solver != DF_SOLVER_AUTO) return p.solver;
-  if (p.scale_step == DF_SCALE_JOINT) return DF_SOLVER_LAUNCHES;  // joint: launch solver only
+  // the joint solve with a tolerance runs on the launch solver only
+  if (p.scale_step == DF_SCALE_JOINT && p.tol > 0.0) return DF_SOLVER_LAUNCHES;
   return df::fused_supported() ? DF_SOLVER_FUSED : DF_SOLVER_LAUNCHES;
 }
 
 static df_status check_joint(const df_solve_params &p) {
-  if (p.scale_step == DF_SCALE_JOINT && p.solver == DF_SOLVER_FUSED)
-    return fail(DF_ENOTSUP, "DF_SCALE_JOINT runs on the launch solver only");
+  if (p.scale_step == DF_SCALE_JOINT && p.solver == DF_SOLVER_FUSED && p.tol > 0.0)
+    return fail(DF_ENOTSUP, "DF_SCALE_JOINT with tol > 0 runs on the launch solver only");
   return DF_OK;
 }
 
 // Fused solve of one keyframe: its launch plan lives in the keyframe's own
 // allocation and is uploaded once per launch shape.
+// need_resident: the solve runs only on a shared-memory resident plan (the
+// joint (x, t) solve); DF_ENOTSUP otherwise, before anything is launched.
 static df_status fused_one(df_keyframe *kf, const SolveCfg &c, int n_gn, int n_pcg,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool need_resident = false) {
   if (!df::fused_supported() || !kf->plan) return fail(DF_ENOTSUP, "fused solver not available on this device");
   const df::FusedTuning tune = current_tuning();
   if (kf->plan_shape.kind < 0 || !same_tuning(tune, kf->plan_tune)) {
@@ -467,6 +471,9 @@ static df_status fused_one(df_keyframe *kf, const SolveCfg &c, int n_gn, int n_p
     kf->plan_shape = shape;
     kf->plan_tune = tune;
   }
+  if (need_resident && kf->plan_shape.kind != df::kPlanResident)
+    return fail(DF_ENOTSUP, "the joint (x, t) solve needs a shared-memory resident plan; this "
+                            "keyframe's launch shape streams");
   const int chunk = tune.gn_per_launch > 0 ? tune.gn_per_launch : (n_gn > 0 ? n_gn : 1);
   for (int g0 = 0, first = 1; g0 < n_gn || first; g0 += chunk, first = 0) {
     const int m = std::min(chunk, n_gn - g0);
@@ -616,7 +623,12 @@ static df_status prepare_many(df_keyframe *const *kfs, int n, cudaStream_t s) {
 
 static df_status optimise_one(df_keyframe *kf, const df_solve_params *p, cudaStream_t s) {
   const SolveCfg c = cfg_of(p);
-  if (pick_solver(*p) == DF_SOLVER_FUSED) return fused_one(kf, c, p->n_gn, p->n_pcg, s);
+  const bool joint = p->scale_step == DF_SCALE_JOINT;
+  if (pick_solver(*p) == DF_SOLVER_FUSED) {
+    df_status st = fused_one(kf, c, p->n_gn, p->n_pcg, s, joint);
+    // the joint solve on a streaming launch shape: the launch solver serves AUTO
+    if (!(joint && st == DF_ENOTSUP && p->solver == DF_SOLVER_AUTO)) return st;
+  }
   DF_CUDA(cudaMemsetAsync(&kf->planes.sc->iters, 0, sizeof(int), s));
   DF_CUDA(cudaMemsetAsync(&kf->planes.sc->stop, 0, sizeof(int), s));
   DF_CUDA(df::launch_solve_launches(kf->planes, c, p->n_gn, p->n_pcg, s));
@@ -664,10 +676,10 @@ df_status df_optimise_batch(df_keyframe *const *kfs, int32_t n, const df_solve_p
   if (n == 0) return DF_OK;
   DeviceGuard g(kfs[0]->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (pick_solver(p) == DF_SOLVER_FUSED) {
+  if (pick_solver(p) == DF_SOLVER_FUSED && p.scale_step != DF_SCALE_JOINT) {
     st = fused_many(kfs, n, cfg_of(&p), p.n_gn, p.n_pcg, s);
     if (st != DF_OK) return st;
-  } else {
+  } else {  // the launch solver, or the joint solve (keyframe by keyframe)
     for (int j = 0; j < n; ++j) {
       st = optimise_one(kfs[j], &p, s);
       if (st != DF_OK) return st;

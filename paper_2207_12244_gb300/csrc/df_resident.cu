@@ -19,6 +19,8 @@
 #include <mutex>
 #include <vector>
 
+#include <type_traits>
+
 #include "df_fused.cuh"
 #include "df_sync.cuh"
 
@@ -28,7 +30,7 @@ namespace {
 
 constexpr int kRThreads = 512;
 constexpr int kRWarps = kRThreads / 32;
-constexpr int kRQ = 3;
+constexpr int kRQ = 4;
 constexpr int kHalo = 9;  // halo arrays of W floats kept in shared memory
 
 struct ResKf {
@@ -43,6 +45,8 @@ struct ResCta {
 
 struct ResSeg {
   double t, gam, alpha, beta, bb, rr;
+  // joint (x, t) solve: the border components of the CG vectors
+  double jS, jrt, jut, jwt, jpt, jst;
   int stop, iters, active, pad;
 };
 
@@ -124,6 +128,34 @@ __device__ __forceinline__ void apply_band(const Smem &m, int W, int nr, int bp,
   }
 }
 
+// Joint (x, t) variant of apply_band: w = A u - ws u_t with u = r / diag
+// formed on the fly (the U array holds ws, the semi-dense weights). Halo u as
+// in apply_band. Accumulates (r, u), (w, u), (r, r) and (ws, u).
+__device__ __forceinline__ void apply_band_joint(const Smem &m, int W, int nr, int bp,
+                                                 bool has_below, float ut, float acc[kRQ]) {
+  for (Walk it(W); it.q < bp; it.next()) {
+    const int q = it.q, u = it.u, v = it.v;
+    const float r = m.R[q];
+    const float uq = r * m.ID[q];
+    float nu = 0.0f;
+    if (u < W - 1) nu += m.WX[q] * (m.R[q + 1] * m.ID[q + 1]);
+    if (u > 0) nu += m.WX[q - 1] * (m.R[q - 1] * m.ID[q - 1]);
+    if (v < nr - 1) {
+      nu += m.WY[q] * (m.R[q + W] * m.ID[q + W]);
+    } else if (has_below) {
+      nu += m.WY[q] * m.HA[4][u];
+    }
+    nu += (v > 0) ? m.WY[q - W] * (m.R[q - W] * m.ID[q - W]) : m.WYT[u] * m.HA[0][u];
+    const float ws = m.U[q];
+    const float w = r - nu - ws * ut;
+    m.Wv[q] = w;
+    acc[0] += r * uq;
+    acc[1] += w * uq;
+    acc[2] += r * r;
+    acc[3] += ws * uq;
+  }
+}
+
 // Write the band's first and last rows of a shared array to a global plane.
 __device__ __forceinline__ void publish_edges(const float *src, float *dst, int W, int nr, int rb,
                                               size_t P) {
@@ -133,7 +165,10 @@ __device__ __forceinline__ void publish_edges(const float *src, float *dst, int 
   }
 }
 
-template <int DT>
+// JOINT: also keep ws in the U array and sum the border's S = sum ws and
+// r_t = sum ws (x - t - mu_s) into acc[2], acc[3] (b.b is not formed: the
+// joint solve runs with a fixed iteration count here).
+template <int DT, bool JOINT>
 __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, float t,
                               const SolveCfg &c, float acc[kRQ]) {
   const int W = k.W, H = k.H, bp = nr * W;
@@ -204,7 +239,11 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     m.R[q] = r;
     acc[0] += r * (r * id);
     acc[1] += r * r;
-    if (c.tol > 0.0) {
+    if (JOINT) {
+      m.U[q] = ws;
+      acc[2] += ws;
+      acc[3] -= rs;  // ws (x - t - mu_s)
+    } else if (c.tol > 0.0) {
       const float gx = (grad && u < W - 1) ? ld_cnn<DT>(k.cnn[2], gi) : 0.0f;
       const float gxl = (grad && u > 0) ? ld_cnn<DT>(k.cnn[2], gi - 1) : 0.0f;
       const float gy = (grad && rb + v < H - 1) ? ld_cnn<DT>(k.cnn[4], gi) : 0.0f;
@@ -215,6 +254,12 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
   }
 }
 
+template <int N>
+using IC = std::integral_constant<int, N>;
+
+// JOINT: the joint (x, t) variant (c.scale_step == DF_SCALE_JOINT with the
+// semi-dense term); the alternating solve is the other instance.
+template <bool JOINT>
 __global__ void __launch_bounds__(kRThreads, 1)
     k_resident(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns,
                int first) {
@@ -254,6 +299,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
   float *IDg = k.diag;  // the fused kernels keep 1/diag in the diag plane
   const bool active = s_seg.active != 0;
   const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step == DF_SCALE_ALTERNATE;
+  constexpr bool joint = JOINT;
   int parity = 0;
   bool alive = true;
 
@@ -301,37 +347,41 @@ __global__ void __launch_bounds__(kRThreads, 1)
   // sums cost one uncontended L2 round trip and are identical everywhere.
   const int nk = s_kf.cta_end - s_kf.cta_begin;
   const int lk = (int)blockIdx.x - s_kf.cta_begin;
-  auto end_pass = [&](float acc[kRQ], int next_halo, int next_cb) -> bool {
+  // nq: std::integral_constant with the number of sums this pass needs
+  // (acc[0 .. NQ-1]); narrower slots store and load half as much.
+  auto end_pass = [&](auto nq, const float *acc, int next_halo, int next_cb) -> bool {
+    constexpr int NQ = decltype(nq)::value;
     const int np = inbox_slots(nk);
     Slot *box = slots + (size_t)parity * h->slot_stride + s_kf.inbox0;
     {
-      const float a3[kRQ] = {acc[0], acc[1], acc[2]};
-      ff2 cs[kRQ];
-      cta_partial_sum<kRQ>(a3, s_red, cs);
+      float an[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) an[q] = acc[q];
+      ff2 cs[NQ];
+      cta_partial_sum<NQ>(an, s_red, cs);
       if (warp == 0) {
-        float4 lo, hi;
-        lo.x = __shfl_sync(0xffffffffu, cs[0].hi, 0);
-        lo.y = __shfl_sync(0xffffffffu, cs[0].lo, 0);
-        lo.z = __shfl_sync(0xffffffffu, cs[1].hi, 0);
-        lo.w = __shfl_sync(0xffffffffu, cs[1].lo, 0);
-        hi.x = __shfl_sync(0xffffffffu, cs[2].hi, 0);
-        hi.y = __shfl_sync(0xffffffffu, cs[2].lo, 0);
-        hi.z = 0.0f;
-        hi.w = 0.0f;
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          v[2 * q] = q < NQ ? __shfl_sync(0xffffffffu, cs[q < NQ ? q : 0].hi, 0) : 0.0f;
+          v[2 * q + 1] = q < NQ ? __shfl_sync(0xffffffffu, cs[q < NQ ? q : 0].lo, 0) : 0.0f;
+        }
+        const float4 lo = make_float4(v[0], v[1], v[2], v[3]);
+        const float4 hi = make_float4(v[4], v[5], v[6], v[7]);
         for (int j = lane; j < nk; j += 32) {
           float4 *dst = reinterpret_cast<float4 *>(box + (size_t)j * np + lk);
           __stcg(dst, lo);
-          __stcg(dst + 1, hi);
+          if (NQ > 2) __stcg(dst + 1, hi);
         }
       }
     }
     if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
     if (warp == 0) {
-      double tot[kRQ];
-      warp_inbox_sum<kRQ>(box + (size_t)lk * np, nk, tot);
+      double tot[NQ];
+      warp_inbox_sum<NQ>(box + (size_t)lk * np, nk, tot);
       if (lane == 0) {
 #pragma unroll
-        for (int q = 0; q < kRQ; ++q) s_tot[q] = tot[q];
+        for (int q = 0; q < NQ; ++q) s_tot[q] = tot[q];
       }
     } else {
       prefetch_halo(next_halo, next_cb);
@@ -367,53 +417,102 @@ __global__ void __launch_bounds__(kRThreads, 1)
   for (int gn = 0; gn < n_gn && alive; ++gn) {
     if (do_scale) {
       if (!scale_pending) {
-        float acc[kRQ] = {0.0f, 0.0f, 0.0f};
+        float acc[kRQ] = {};
         if (active) scale_partials(acc, 0, (float)s_seg.t);
-        if (!(alive = end_pass(acc, HK_X, 0))) break;
+        if (!(alive = end_pass(IC<2>{}, acc, HK_X, 0))) break;
         scale_update(0, 1);
       }
       scale_pending = false;
     }
     {  // ASSEMBLE
-      float acc[kRQ] = {0.0f, 0.0f, 0.0f};
+      float acc[kRQ] = {};
       if (active) {
         const float t = (float)s_seg.t;
-        if (k.dtype == DF_BF16)
-          assemble_band<DF_BF16>(m, k, rb, nr, t, c, acc);
-        else if (k.dtype == DF_F16)
-          assemble_band<DF_F16>(m, k, rb, nr, t, c, acc);
-        else
-          assemble_band<DF_F32>(m, k, rb, nr, t, c, acc);
+        if constexpr (JOINT) {
+          if (k.dtype == DF_BF16)
+            assemble_band<DF_BF16, true>(m, k, rb, nr, t, c, acc);
+          else if (k.dtype == DF_F16)
+            assemble_band<DF_F16, true>(m, k, rb, nr, t, c, acc);
+          else
+            assemble_band<DF_F32, true>(m, k, rb, nr, t, c, acc);
+        } else {
+          if (k.dtype == DF_BF16)
+            assemble_band<DF_BF16, false>(m, k, rb, nr, t, c, acc);
+          else if (k.dtype == DF_F16)
+            assemble_band<DF_F16, false>(m, k, rb, nr, t, c, acc);
+          else
+            assemble_band<DF_F32, false>(m, k, rb, nr, t, c, acc);
+        }
         __syncthreads();
         publish_edges(m.R, Rg[0], W, nr, rb, P);
         publish_edges(m.ID, IDg, W, nr, rb, P);
       }
-      if (!(alive = end_pass(acc, n_pcg > 0 ? HK_INIT : HK_X, 0))) break;
+      // sums needed: r.z; r.r and b.b only for a tolerance or a report
+      // without CG iterations; the joint solve also S and r_t
+      const int next_a = n_pcg > 0 ? HK_INIT : HK_X;
+      const bool wide = c.tol > 0.0 || n_pcg == 0;
+      if constexpr (JOINT) {
+        alive = end_pass(IC<4>{}, acc, next_a, 0);
+      } else {
+        alive = wide ? end_pass(IC<3>{}, acc, next_a, 0) : end_pass(IC<1>{}, acc, next_a, 0);
+      }
+      if (!alive) break;
       if (tid == 0) {
-        s_seg.gam = s_tot[0];
-        s_seg.rr = s_tot[1];
-        s_seg.bb = s_tot[2];
-        s_seg.stop = (c.tol > 0.0 && sqrt(s_seg.rr) < c.tol * sqrt(s_seg.bb)) ? 1 : 0;
+        if constexpr (JOINT) {
+          // border of the bordered system: S = sum ws, r_t, u_t = r_t / S
+          const double S = s_tot[2], rt = s_tot[3], ut = S > 0.0 ? rt / S : 0.0;
+          s_seg.jS = S;
+          s_seg.jrt = rt;
+          s_seg.jut = ut;
+          s_seg.gam = s_tot[0] + rt * ut;
+          s_seg.rr = s_tot[1] + rt * rt;
+          s_seg.stop = 0;
+        } else {
+          s_seg.gam = s_tot[0];
+          s_seg.stop = 0;
+          if (wide) {
+            s_seg.rr = s_tot[1];
+            s_seg.bb = s_tot[2];
+            s_seg.stop = (c.tol > 0.0 && sqrt(s_seg.rr) < c.tol * sqrt(s_seg.bb)) ? 1 : 0;
+          }
+        }
       }
       __syncthreads();
     }
     if (n_pcg == 0) continue;  // no depth update in this GN iteration
     {  // INIT: w0 = A u0
-      float acc[kRQ] = {0.0f, 0.0f, 0.0f};
+      float acc[kRQ] = {};
       if (active && !s_seg.stop) {
         for (int u = tid; u < W; u += kRThreads) {
           m.HA[0][u] = m.HA[0][u] * m.HA[3][u];
           m.HA[4][u] = m.HA[4][u] * m.HA[7][u];
         }
-        for (Walk it(W); it.q < bp; it.next()) m.U[it.q] = m.R[it.q] * m.ID[it.q];
-        __syncthreads();
-        apply_band(m, W, nr, bp, has_below, acc);
+        if constexpr (JOINT) {
+          __syncthreads();
+          apply_band_joint(m, W, nr, bp, has_below, (float)s_seg.jut, acc);
+        } else {
+          for (Walk it(W); it.q < bp; it.next()) m.U[it.q] = m.R[it.q] * m.ID[it.q];
+          __syncthreads();
+          apply_band(m, W, nr, bp, has_below, acc);
+        }
         __syncthreads();
         publish_edges(m.Wv, Wg[0], W, nr, rb, P);
       }
-      if (!(alive = end_pass(acc, n_pcg > 1 ? HK_ITER : HK_NONE, 0))) break;
+      // sums needed: (w0, u0); the joint solve also (ws, u0)
+      const int next_i = n_pcg > 1 ? HK_ITER : HK_NONE;
+      if constexpr (JOINT) {
+        const float a2[2] = {acc[1], acc[3]};
+        alive = end_pass(IC<2>{}, a2, next_i, 0);
+      } else {
+        alive = end_pass(IC<1>{}, acc + 1, next_i, 0);
+      }
+      if (!alive) break;
       if (tid == 0 && !s_seg.stop) {
-        const double dl = s_tot[1];
+        double dl = s_tot[0];
+        if constexpr (JOINT) {  // w_t = S u_t - (ws, u); (w, u) gains w_t u_t
+          s_seg.jwt = s_seg.jS * s_seg.jut - s_tot[1];
+          dl += s_seg.jwt * s_seg.jut;
+        }
         if (s_seg.gam == 0.0 || !(dl > 0.0)) {
           s_seg.stop = 1;
         } else {
@@ -428,7 +527,21 @@ __global__ void __launch_bounds__(kRThreads, 1)
       const float fa = (float)s_seg.alpha, fb = (float)s_seg.beta;
       const bool first = it == 0;
       const bool run = active && !s_seg.stop;
-      float acc[kRQ] = {0.0f, 0.0f, 0.0f};
+      float acc[kRQ] = {};
+      if constexpr (JOINT) {
+        // the border moves with the same alpha, beta: p_t = u_t + beta p_t,
+        // s_t = w_t + beta s_t, t += alpha p_t, r_t -= alpha s_t
+        __syncthreads();
+        if (tid == 0 && run) {
+          const double a = s_seg.alpha, b = first ? 0.0 : s_seg.beta;
+          s_seg.jpt = s_seg.jut + b * s_seg.jpt;
+          s_seg.jst = s_seg.jwt + b * s_seg.jst;
+          s_seg.t += a * s_seg.jpt;
+          s_seg.jrt -= a * s_seg.jst;
+          s_seg.jut = s_seg.jS > 0.0 ? s_seg.jrt / s_seg.jS : 0.0;
+        }
+        __syncthreads();
+      }
       if (it == n_pcg - 1) {  // FINAL
         const bool fs = do_scale && gn + 1 < n_gn;
         if (run) {
@@ -449,10 +562,12 @@ __global__ void __launch_bounds__(kRThreads, 1)
           publish_edges(m.X, k.x, W, nr, rb, P);
         }
         if (fs && active) scale_partials(acc, 1, (float)s_seg.t);
-        if (!(alive = end_pass(acc, HK_X, 0))) break;
+        // sums needed: r.r, and the next scale step's two sums
+        alive = fs ? end_pass(IC<3>{}, acc, HK_X, 0) : end_pass(IC<1>{}, acc, HK_X, 0);
+        if (!alive) break;
         if (tid == 0 && run) {
           s_seg.iters += 1;
-          s_seg.rr = s_tot[0];
+          s_seg.rr = s_tot[0] + (joint ? s_seg.jrt * s_seg.jrt : 0.0);
         }
         __syncthreads();
         if (fs) {
@@ -478,21 +593,39 @@ __global__ void __launch_bounds__(kRThreads, 1)
             m.S[q] = si;
             const float rn = r - fa * si;
             m.R[q] = rn;
-            m.U[q] = rn * id;
+            if (!joint) m.U[q] = rn * id;
           }
           __syncthreads();
-          apply_band(m, W, nr, bp, has_below, acc);
+          if constexpr (JOINT)
+            apply_band_joint(m, W, nr, bp, has_below, (float)s_seg.jut, acc);
+          else
+            apply_band(m, W, nr, bp, has_below, acc);
           __syncthreads();
           publish_edges(m.R, Rg[nb], W, nr, rb, P);
           publish_edges(m.S, Sg[nb], W, nr, rb, P);
           publish_edges(m.Wv, Wg[nb], W, nr, rb, P);
         }
         const int next_kind = (it + 1 < n_pcg - 1) ? HK_ITER : HK_NONE;
-        if (!(alive = end_pass(acc, next_kind, nb))) break;
+        // sums needed: (r, u), (w, u); (r, r) for a tolerance; the joint
+        // solve also (ws, u)
+        if constexpr (JOINT) {
+          const float a3[3] = {acc[0], acc[1], acc[3]};
+          alive = end_pass(IC<3>{}, a3, next_kind, nb);
+        } else {
+          alive = c.tol > 0.0 ? end_pass(IC<3>{}, acc, next_kind, nb)
+                              : end_pass(IC<2>{}, acc, next_kind, nb);
+        }
+        if (!alive) break;
         if (tid == 0 && run) {
           s_seg.iters += 1;
-          s_seg.rr = s_tot[2];
-          const double gn_ = s_tot[0], dl = s_tot[1];
+          double gn_ = s_tot[0], dl = s_tot[1];
+          if constexpr (JOINT) {  // border terms of (r, u) and (w, u)
+            s_seg.jwt = s_seg.jS * s_seg.jut - s_tot[2];
+            gn_ += s_seg.jrt * s_seg.jut;
+            dl += s_seg.jwt * s_seg.jut;
+          } else if (c.tol > 0.0) {
+            s_seg.rr = s_tot[2];
+          }
           if (c.tol > 0.0 && sqrt(s_seg.rr) < c.tol * sqrt(s_seg.bb)) {
             s_seg.stop = 1;
           } else {
@@ -553,7 +686,8 @@ const ResDev &rdev() {
     cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_resident) == cudaSuccess) d.static_smem = (int)fa.sharedSizeBytes;
+    if (cudaFuncGetAttributes(&fa, k_resident<true>) == cudaSuccess)
+      d.static_smem = (int)fa.sharedSizeBytes;  // the larger of the two instances
     cudaGetLastError();
     g_rdev[dev] = d;
     g_rdev_init[dev] = true;
@@ -692,13 +826,15 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
 cudaError_t resident_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
                             int n_pcg, unsigned long long limit_ns, cudaStream_t s, int first) {
   PlanHeader *h = static_cast<PlanHeader *>(dplan);
-  cudaError_t e = cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       shape.smem);
+  const bool joint = (c.terms & DF_TERM_SEMI) && c.scale_step == DF_SCALE_JOINT;
+  const void *fn = joint ? reinterpret_cast<const void *>(k_resident<true>)
+                         : reinterpret_cast<const void *>(k_resident<false>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, shape.smem);
   if (e != cudaSuccess) return e;
   void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns, &first};
   count_launches(1);
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_resident), dim3(shape.G),
-                                     dim3(kRThreads), args, (size_t)shape.smem, s);
+  return cudaLaunchCooperativeKernel(fn, dim3(shape.G), dim3(kRThreads), args, (size_t)shape.smem,
+                                     s);
 }
 
 }  // namespace df

@@ -140,7 +140,8 @@ __device__ __forceinline__ void warp_inbox_sum(const Slot *box, int n, double (&
       const float4 *p = reinterpret_cast<const float4 *>(box + sl);
       if (base + 32 * j < np) {
         v[j][0] = __ldcg(p);
-        v[j][1] = __ldcg(p + 1);
+        // slots of one or two sums are written without their second half
+        v[j][1] = kQ > 2 ? __ldcg(p + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
       } else {
         v[j][0] = v[j][1] = make_float4(0.f, 0.f, 0.f, 0.f);
       }

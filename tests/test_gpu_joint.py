@@ -20,11 +20,15 @@ def o():
     return orc.get()
 
 
+SOLVERS = [dfl.DF_SOLVER_LAUNCHES, dfl.DF_SOLVER_FUSED]
+
+
+@pytest.mark.parametrize("solver", SOLVERS, ids=["launches", "resident"])
 @pytest.mark.parametrize("W,H", [(256, 192), (37, 23), (1, 1), (129, 3), (3, 130)])
 @pytest.mark.parametrize("delta", [1.345, float("inf")], ids=["huber", "l2"])
-def test_joint_matches_oracle(o, W, H, delta):
+def test_joint_matches_oracle(o, W, H, delta, solver):
     kf = synth.make_keyframe(W, H, 300 + W + H)
-    prm = params(n_gn=10, n_pcg=3, delta=delta, scale_step=JOINT)
+    prm = params(n_gn=10, n_pcg=3, delta=delta, scale_step=JOINT, solver=solver)
     x, t, rep = solve(kf, prm)
     xo, to, ro = oracle_solve(o, kf, prm)
     assert rep.iters_done == ro.iters_done
@@ -33,13 +37,25 @@ def test_joint_matches_oracle(o, W, H, delta):
         assert abs(t) > 1e-3  # the border moved t
 
 
-def test_joint_auto_takes_launch_solver_and_fused_is_refused(o):
+def test_joint_routing(o):
+    """AUTO runs the joint solve on the resident kernel, or on the launch
+    solver where the launch shape streams or a tolerance is set; FUSED is
+    refused in those cases."""
     kf = synth.make_keyframe(96, 72, 7)
-    x, t, rep = solve(kf, params(n_gn=5, n_pcg=4, scale_step=JOINT, solver=dfl.DF_SOLVER_AUTO))
-    xo, to, _ = oracle_solve(o, kf, params(n_gn=5, n_pcg=4, scale_step=JOINT))
-    assert_parity(x, t, xo, to, what="joint auto")
+    want = oracle_solve(o, kf, params(n_gn=5, n_pcg=4, scale_step=JOINT))
+    x, t, _ = solve(kf, params(n_gn=5, n_pcg=4, scale_step=JOINT, solver=dfl.DF_SOLVER_AUTO))
+    assert_parity(x, t, want[0], want[1], what="joint auto")
+    dfl.df_set_tuning(mode=dfl.DF_MODE_STREAMING)
+    try:
+        x, t, _ = solve(kf, params(n_gn=5, n_pcg=4, scale_step=JOINT, solver=dfl.DF_SOLVER_AUTO))
+        assert_parity(x, t, want[0], want[1], what="joint auto, streaming shape")
+        with pytest.raises(dfl.DFError) as e:
+            solve(kf, params(scale_step=JOINT, solver=dfl.DF_SOLVER_FUSED))
+        assert e.value.status == dfl.DF_ENOTSUP
+    finally:
+        dfl.df_set_tuning()
     with pytest.raises(dfl.DFError) as e:
-        solve(kf, params(scale_step=JOINT, solver=dfl.DF_SOLVER_FUSED))
+        solve(kf, params(scale_step=JOINT, solver=dfl.DF_SOLVER_FUSED, tol=1e-3))
     assert e.value.status == dfl.DF_ENOTSUP
     with pytest.raises(dfl.DFError) as e:
         solve(kf, params(scale_step=3))
@@ -73,10 +89,11 @@ def test_long_runs_of_both_variants(o):
     assert abs(tj - tstar) < 0.1 * abs(ta - tstar)
 
 
-def test_joint_warm_started_sequence(o):
+@pytest.mark.parametrize("solver", SOLVERS, ids=["launches", "resident"])
+def test_joint_warm_started_sequence(o, solver):
     torch = torch_cuda()
     kf, mus, vs = synth.make_sequence(128, 96, 23, n_frames=30)
-    prm = params(n_gn=10, n_pcg=5, scale_step=JOINT)
+    prm = params(n_gn=10, n_pcg=5, scale_step=JOINT, solver=solver)
     k = create(kf)
     try:
         dmu, dvs = to_dev(mus), to_dev(vs)
