@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
                int first) {
   extern __shared__ float4 dyn_smem[];
   __shared__ ff2 s_red[32 * kRQ];
+  __shared__ ff2 s_cs[kRQ];
   __shared__ double s_tot[kRQ];
   __shared__ unsigned int s_epoch;
   __shared__ ResKf s_kf;
@@ -357,14 +358,14 @@ __global__ void __launch_bounds__(kRThreads, 1)
       float an[NQ];
 #pragma unroll
       for (int q = 0; q < NQ; ++q) an[q] = acc[q];
-      ff2 cs[NQ];
-      cta_partial_sum<NQ>(an, s_red, cs);
+      cta_partial_sum_split<NQ>(an, s_red, s_cs);
+      __syncthreads();
       if (warp == 0) {
         float v[8];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          v[2 * q] = q < NQ ? __shfl_sync(0xffffffffu, cs[q < NQ ? q : 0].hi, 0) : 0.0f;
-          v[2 * q + 1] = q < NQ ? __shfl_sync(0xffffffffu, cs[q < NQ ? q : 0].lo, 0) : 0.0f;
+          v[2 * q] = q < NQ ? s_cs[q].hi : 0.0f;
+          v[2 * q + 1] = q < NQ ? s_cs[q].lo : 0.0f;
         }
         const float4 lo = make_float4(v[0], v[1], v[2], v[3]);
         const float4 hi = make_float4(v[4], v[5], v[6], v[7]);
@@ -376,15 +377,12 @@ __global__ void __launch_bounds__(kRThreads, 1)
       }
     }
     if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
-    if (warp == 0) {
-      double tot[NQ];
-      warp_inbox_sum<NQ>(box + (size_t)lk * np, nk, tot);
-      if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) s_tot[q] = tot[q];
-      }
+    // warp q adds quantity q of the inbox; the other warps load the halo
+    if (warp < NQ) {
+      const double tot = warp_inbox_sum_q(box + (size_t)lk * np, nk, warp);
+      if (lane == 0) s_tot[warp] = tot;
     } else {
-      prefetch_halo(next_halo, next_cb);
+      prefetch_halo(next_halo, next_cb, 32 * NQ);
     }
     __syncthreads();
     parity ^= 1;

@@ -180,6 +180,49 @@ __device__ __forceinline__ void cta_partial_sum(const float (&acc)[kQ], ff2 *red
   }
 }
 
+// As cta_partial_sum, with the second level split over warps: warp q adds
+// quantity q (same order, same result), so the kQ trees run side by side.
+// The totals land in shared memory out[0..kQ-1] (valid after the caller's
+// next __syncthreads).
+template <int kQ>
+__device__ __forceinline__ void cta_partial_sum_split(const float (&acc)[kQ], ff2 *red,
+                                                      ff2 *out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const ff2 s = warp_sum_ff(ff2{acc[q], 0.0f});
+    if (lane == 0) red[warp * kQ + q] = s;
+  }
+  __syncthreads();
+  if (warp < kQ) {
+    const ff2 x = lane < nwarps ? red[lane * kQ + warp] : ff2{0.0f, 0.0f};
+    const ff2 t = warp_sum_ff(x);
+    if (lane == 0) out[warp] = t;
+  }
+}
+
+// One quantity q of an inbox of n writers, summed by one warp in the order of
+// warp_inbox_sum (slot order per lane, then a fixed warp tree).
+__device__ __forceinline__ double warp_inbox_sum_q(const Slot *box, int n, int q) {
+  const int lane = threadIdx.x & 31;
+  const int np = inbox_slots(n);
+  constexpr int kU = 8;
+  ff2 acc = ff2{0.0f, 0.0f};
+  for (int base = 0; base < np; base += 32 * kU) {
+    float2 v[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      const int sl = base + lane + 32 * j;
+      v[j] = (base + 32 * j < np) ? __ldcg(reinterpret_cast<const float2 *>(&box[sl].v[q]))
+                                  : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < kU; ++j) acc = ff_add(acc, ff2{v[j].x, v[j].y});
+  }
+  return ff_to_double(warp_sum_ff(acc));
+}
+
 // Called once by every CTA as its last action: the last CTA out resets the
 // barrier words (also after an abort, since every CTA does exit).
 __device__ __forceinline__ void grid_exit(PlanHeader *h, int G) {
