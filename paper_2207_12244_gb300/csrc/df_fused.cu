@@ -1113,6 +1113,16 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
 
   // One pass over the CTA's tiles, then slots, barrier and per-keyframe sums.
   auto run_pass = [&](int kind, int it, bool final_scale) __attribute__((always_inline)) -> bool {
+    // the sums this pass's consumers use: a[q0 .. q0 + nq) of the tiles'
+    // accumulators, reduced into s_tot[.][0 .. nq)
+    int q0 = 0, nq = kQ;
+    switch (kind) {
+      case P_SCALE: nq = 2; break;                                      // sum w, sum w (x - mu_s)
+      case P_ASSEMBLE: nq = (c.tol > 0.0 || n_pcg == 0) ? 3 : 1; break;  // r.z (r.r, b.b)
+      case P_INIT: q0 = 1; nq = 1; break;                                // (w, u)
+      case P_ITER: nq = c.tol > 0.0 ? 3 : 2; break;                      // (r, u), (w, u) (r.r)
+      default: nq = final_scale ? 3 : 1; break;                          // r.r (scale sums)
+    }
     for (int q = tid; q < kWarps * kMaxSeg * kQ; q += kThreads) (&s_acc[0][0][0])[q] = ff2{0.0f, 0.0f};
     __syncthreads();
     int seg = 0;
@@ -1201,8 +1211,10 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       }
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
-        const ff2 dq = warp_sum_ff(ff2{a[q], 0.0f});
-        if (lane == 0) s_acc[warp][seg][q] = ff_add(s_acc[warp][seg][q], dq);
+        if (q < nq) {
+          const ff2 dq = warp_sum_ff(ff2{a[q0 + q < kQ ? q0 + q : 0], 0.0f});
+          if (lane == 0) s_acc[warp][seg][q] = ff_add(s_acc[warp][seg][q], dq);
+        }
       }
     }
     ring = rg;
@@ -1228,19 +1240,17 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       for (int j = tid; j < nk; j += kThreads) {
         float4 *dst = reinterpret_cast<float4 *>(box + (size_t)j * np + l);
         __stcg(dst, src[0]);
-        __stcg(dst + 1, src[1]);
+        if (nq > 2) __stcg(dst + 1, src[1]);
       }
     }
     if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
-    if (warp < nseg) {
-      const FusedKf &K = s_kf[warp];
-      const int nk = K.slot_end - K.slot_begin, l = slot0 + warp - K.slot_begin;
-      double tot[kQ];
-      warp_inbox_sum<kQ>(pbox + K.inbox0 + (size_t)l * inbox_slots(nk), nk, tot);
-      if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < kQ; ++q) s_tot[warp][q] = tot[q];
-      }
+    // one warp per (keyframe, sum): the trees run side by side
+    for (int pq = warp; pq < nseg * nq; pq += kWarps) {
+      const int sg = pq / nq, q = pq - sg * nq;
+      const FusedKf &K = s_kf[sg];
+      const int nk = K.slot_end - K.slot_begin, l = slot0 + sg - K.slot_begin;
+      const double tot = warp_inbox_sum_q(pbox + K.inbox0 + (size_t)l * inbox_slots(nk), nk, q);
+      if (lane == 0) s_tot[sg][q] = tot;
     }
     __syncthreads();
     parity ^= 1;
@@ -1270,9 +1280,12 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     if (tid < nseg) {
       Seg &S = s_seg[tid];
       S.gam = s_tot[tid][0];
-      S.rr = s_tot[tid][1];
-      S.bb = s_tot[tid][2];
-      S.stop = (c.tol > 0.0 && sqrt(S.rr) < c.tol * sqrt(S.bb)) ? 1 : 0;
+      S.stop = 0;
+      if (c.tol > 0.0 || n_pcg == 0) {
+        S.rr = s_tot[tid][1];
+        S.bb = s_tot[tid][2];
+        S.stop = (c.tol > 0.0 && sqrt(S.rr) < c.tol * sqrt(S.bb)) ? 1 : 0;
+      }
     }
     __syncthreads();
     if (n_pcg == 0) continue;
@@ -1281,7 +1294,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     if (tid < nseg) {
       Seg &S = s_seg[tid];
       if (!S.stop) {
-        const double dl = s_tot[tid][1];
+        const double dl = s_tot[tid][0];  // (w0, u0)
         if (S.gam == 0.0 || !(dl > 0.0)) {
           S.stop = 1;
         } else {
@@ -1315,7 +1328,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
           Seg &S = s_seg[tid];
           if (!S.stop) {
             S.iters += 1;
-            S.rr = s_tot[tid][2];
+            if (c.tol > 0.0) S.rr = s_tot[tid][2];
             const double gn_ = s_tot[tid][0], dl = s_tot[tid][1];
             if (c.tol > 0.0 && sqrt(S.rr) < c.tol * sqrt(S.bb)) {
               S.stop = 1;
