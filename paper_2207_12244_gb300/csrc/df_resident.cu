@@ -560,16 +560,26 @@ __global__ void __launch_bounds__(kRThreads, 1)
           publish_edges(m.X, k.x, W, nr, rb, P);
         }
         if (fs && active) scale_partials(acc, 1, (float)s_seg.t);
-        // sums needed: r.r, and the next scale step's two sums
-        alive = fs ? end_pass(IC<3>{}, acc, HK_X, 0) : end_pass(IC<1>{}, acc, HK_X, 0);
+        // sums needed: the next scale step's two; r.r for a tolerance and
+        // for the report after the last Gauss-Newton iteration
+        const bool need_rr = c.tol > 0.0 || gn + 1 == n_gn;
+        if (fs && need_rr)
+          alive = end_pass(IC<3>{}, acc, HK_X, 0);
+        else if (fs)
+          alive = end_pass(IC<2>{}, acc + 1, HK_X, 0);
+        else
+          alive = end_pass(IC<1>{}, acc, HK_X, 0);
         if (!alive) break;
         if (tid == 0 && run) {
           s_seg.iters += 1;
-          s_seg.rr = s_tot[0] + (joint ? s_seg.jrt * s_seg.jrt : 0.0);
+          if (need_rr || !fs) s_seg.rr = s_tot[0] + (joint ? s_seg.jrt * s_seg.jrt : 0.0);
         }
         __syncthreads();
         if (fs) {
-          scale_update(1, 2);
+          if (need_rr)
+            scale_update(1, 2);
+          else
+            scale_update(0, 1);
           scale_pending = true;
         }
       } else {  // ITER
