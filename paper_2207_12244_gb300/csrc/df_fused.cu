@@ -57,6 +57,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSeg = 8;  // keyframes a CTA's tile range may span
 constexpr int kQ = 3;       // FP64 partial sums per slot
+static_assert(kQ == 3, "a pass's reduction selects among three accumulators");
 
 enum PassKind : int { P_SCALE = 0, P_ASSEMBLE, P_INIT, P_ITER, P_FINAL };
 
@@ -168,7 +169,7 @@ __device__ __forceinline__ Geo geo_of(int c0, int r0, int nrows) {
 }
 
 // ---- SCALE: partial sums of the scale step (Eq. 6 with x fixed) ------------
-template <int VEC>
+template <int VEC, int LK>
 __device__ void scale_tile(const FusedKf &K, const Geo &g, float t, const SolveCfg &c, float acc[kQ]) {
   const Planes &k = K.pl;
   for (int j = 0; j < g.nrows; ++j) {
@@ -178,7 +179,7 @@ __device__ void scale_tile(const FusedKf &K, const Geo &g, float t, const SolveC
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       if (g.col + e < k.W && semi_valid(ms.v[e], vs.v[e])) {
-        const float w = robust_weight(x.v[e] - t - ms.v[e], vs.v[e], c.delta, c.loss);
+        const float w = robust_weight_k<LK>(x.v[e] - t - ms.v[e], vs.v[e], c.delta);
         acc[0] += w;
         acc[1] += w * (x.v[e] - ms.v[e]);
       }
@@ -187,7 +188,7 @@ __device__ void scale_tile(const FusedKf &K, const Geo &g, float t, const SolveC
 }
 
 // ---- ASSEMBLE: weights, 5-point system and r0 (see df_launch.cu) -----------
-template <int VEC, int DT>
+template <int VEC, int DT, int LK>
 __device__ void assemble_tile(const FusedKf &K, const Geo &g, float t, const SolveCfg &c,
                               float acc[kQ]) {
   const Planes &k = K.pl;
@@ -208,7 +209,7 @@ __device__ void assemble_tile(const FusedKf &K, const Geo &g, float t, const Sol
       if (g.col + e < W) {
         gy_up.v[e] = gyu.v[e];
         ey_up.v[e] = x_cur.v[e] - xu.v[e] - gyu.v[e];
-        wy_up.v[e] = robust_weight(ey_up.v[e], vyu.v[e], c.delta, c.loss);
+        wy_up.v[e] = robust_weight_k<LK>(ey_up.v[e], vyu.v[e], c.delta);
       }
     }
   }
@@ -235,7 +236,7 @@ __device__ void assemble_tile(const FusedKf &K, const Geo &g, float t, const Sol
         if (g.col + e < W - 1) {
           gxv.v[e] = gxr.v[e];
           exv.v[e] = x_e.v[e] - x_cur.v[e] - gxr.v[e];
-          wxv.v[e] = robust_weight(exv.v[e], vxr.v[e], c.delta, c.loss);
+          wxv.v[e] = robust_weight_k<LK>(exv.v[e], vxr.v[e], c.delta);
         }
       }
       if (v < H - 1) {
@@ -245,7 +246,7 @@ __device__ void assemble_tile(const FusedKf &K, const Geo &g, float t, const Sol
           if (g.col + e < W) {
             gyv.v[e] = gyr.v[e];
             eyv.v[e] = x_dn.v[e] - x_cur.v[e] - gyr.v[e];
-            wyv.v[e] = robust_weight(eyv.v[e], vyr.v[e], c.delta, c.loss);
+            wyv.v[e] = robust_weight_k<LK>(eyv.v[e], vyr.v[e], c.delta);
           }
         }
       }
@@ -267,7 +268,7 @@ __device__ void assemble_tile(const FusedKf &K, const Geo &g, float t, const Sol
           const float xw = __ldcg(k.x + i - 1);
           gg = ld_cnn<DT>(k.cnn[2], i - 1);
           b = x_cur.v[0] - xw - gg;
-          a = robust_weight(b, ld_cnn<DT>(k.cnn[3], i - 1), c.delta, c.loss);
+          a = robust_weight_k<LK>(b, ld_cnn<DT>(k.cnn[3], i - 1), c.delta);
         }
       }
       wxw.v[0] = a;
@@ -284,14 +285,14 @@ __device__ void assemble_tile(const FusedKf &K, const Geo &g, float t, const Sol
         const float xi = x_cur.v[e];
         float ws = 0.0f, rs = 0.0f, bs = 0.0f;
         if (semi && semi_valid(ms.v[e], vs.v[e])) {
-          ws = robust_weight(xi - t - ms.v[e], vs.v[e], c.delta, c.loss);
+          ws = robust_weight_k<LK>(xi - t - ms.v[e], vs.v[e], c.delta);
           rs = ws * (t + ms.v[e] - xi);
           bs = ws * (t + ms.v[e]);
         }
         float wn = 0.0f, m = 0.0f;
         if (net) {
           m = mn.v[e];
-          wn = robust_weight(xi - m, vn.v[e], c.delta, c.loss);
+          wn = robust_weight_k<LK>(xi - m, vn.v[e], c.delta);
         }
         d = ws + wn + wxv.v[e] + wxw.v[e] + wyv.v[e] + wy_up.v[e];
         r = rs + wn * (m - xi) + wxv.v[e] * exv.v[e] - wxw.v[e] * exw.v[e] +
@@ -461,7 +462,7 @@ __device__ void cg_tile(const FusedKf &K, const Geo &g, float alpha, float beta,
 }
 
 // ---- FINAL: last CG iteration (no stencil) + next scale-step sums ----------
-template <int VEC>
+template <int VEC, int LK>
 __device__ void final_tile(const FusedKf &K, const Geo &g, bool first, bool update, float alpha,
                            float beta, bool scale, float t, const SolveCfg &c,
                            const float *r_cur, const float *s_prev, const float *w_cur,
@@ -490,7 +491,7 @@ __device__ void final_tile(const FusedKf &K, const Geo &g, bool first, bool upda
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
         if (g.col + e < k.W && semi_valid(ms.v[e], vs.v[e])) {
-          const float w = robust_weight(x.v[e] - t - ms.v[e], vs.v[e], c.delta, c.loss);
+          const float w = robust_weight_k<LK>(x.v[e] - t - ms.v[e], vs.v[e], c.delta);
           acc[1] += w;
           acc[2] += w * (x.v[e] - ms.v[e]);
         }
@@ -810,8 +811,9 @@ __device__ __forceinline__ bool tma_cg_tile(RowRing &ring, const FusedKf &K, con
   return rows.ensure(rows.R - 1);
 }
 
+template <int LK>
 __device__ __forceinline__ bool tma_final_tile(RowRing &ring, const FusedKf &K, const Geo &g, bool first, bool update,
-                               float alpha, float beta, bool scale, float t, const SolveCfg &c,
+                               float alpha, float beta, bool scale, bool rr, float t, const SolveCfg &c,
                                const float *r_cur, const float *s_prev, const float *w_cur,
                                float acc[kQ]) {
   const Planes &k = K.pl;
@@ -821,7 +823,8 @@ __device__ __forceinline__ bool tma_final_tile(RowRing &ring, const FusedKf &K, 
                             {s_prev, 4}, {k.v[0], 4}, {k.mu_s, 4}, {k.var_s, 4}};
   uint32_t mask = 1u << iX;
   if (update) mask |= (1u << iR) | (1u << iW) | (1u << iD);
-  if (update && !first) mask |= (1u << iS) | (1u << iP);
+  if (update && !first) mask |= 1u << iP;
+  if (update && !first && rr) mask |= 1u << iS;
   if (scale) mask |= (1u << iMS) | (1u << iVS);
   TileRows<8, 8, 0u> rows(ring, pl, g.c0, k.P, g.r0, g.nrows, false, false, mask);
   size_t i = (size_t)g.r0 * k.P + g.col;
@@ -832,15 +835,17 @@ __device__ __forceinline__ bool tma_final_tile(RowRing &ring, const FusedKf &K, 
     if (update) {
       const F<4> d = f4v(ring.f4(s, iD)), r = f4v(ring.f4(s, iR)), w = f4v(ring.f4(s, iW));
       const F<4> p = first ? fzero<4>() : f4v(ring.f4(s, iP));
-      const F<4> sp = first ? fzero<4>() : f4v(ring.f4(s, iS));
+      const F<4> sp = first || !rr ? fzero<4>() : f4v(ring.f4(s, iS));
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float ui = r.v[e] * d.v[e];
         const float pi = first ? ui : ui + beta * p.v[e];
         x.v[e] += alpha * pi;
-        const float si = first ? w.v[e] : w.v[e] + beta * sp.v[e];
-        const float rn = r.v[e] - alpha * si;
-        acc[0] += rn * rn;
+        if (rr) {
+          const float si = first ? w.v[e] : w.v[e] + beta * sp.v[e];
+          const float rn = r.v[e] - alpha * si;
+          acc[0] += rn * rn;
+        }
       }
       stm<4>(k.x + i, x);
     }
@@ -849,7 +854,7 @@ __device__ __forceinline__ bool tma_final_tile(RowRing &ring, const FusedKf &K, 
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         if (g.col + e < k.W && semi_valid(ms.v[e], vs.v[e])) {
-          const float w = robust_weight(x.v[e] - t - ms.v[e], vs.v[e], c.delta, c.loss);
+          const float w = robust_weight_k<LK>(x.v[e] - t - ms.v[e], vs.v[e], c.delta);
           acc[1] += w;
           acc[2] += w * (x.v[e] - ms.v[e]);
         }
@@ -861,6 +866,7 @@ __device__ __forceinline__ bool tma_final_tile(RowRing &ring, const FusedKf &K, 
   return true;
 }
 
+template <int LK>
 __device__ __forceinline__ bool tma_scale_tile(RowRing &ring, const FusedKf &K, const Geo &g, float t,
                                const SolveCfg &c, float acc[kQ]) {
   const Planes &k = K.pl;
@@ -873,7 +879,7 @@ __device__ __forceinline__ bool tma_scale_tile(RowRing &ring, const FusedKf &K, 
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (g.col + e < k.W && semi_valid(ms.v[e], vs.v[e])) {
-        const float w = robust_weight(x.v[e] - t - ms.v[e], vs.v[e], c.delta, c.loss);
+        const float w = robust_weight_k<LK>(x.v[e] - t - ms.v[e], vs.v[e], c.delta);
         acc[0] += w;
         acc[1] += w * (x.v[e] - ms.v[e]);
       }
@@ -887,9 +893,9 @@ __device__ __forceinline__ bool tma_scale_tile(RowRing &ring, const FusedKf &K, 
 // the own rows also mu_s, var_s (f32) and the other network planes
 enum : int { A_X = 0, A_GY, A_VY, A_MS, A_VS, A_MN, A_VN, A_GX, A_VX, A_NP };
 
-template <int DT>
+template <int DT, int LK>
 __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &K, const Geo &g, float t,
-                                  const SolveCfg &c, float acc[kQ]) {
+                                  const SolveCfg &c, bool wide, float acc[kQ]) {
   const Planes &k = K.pl;
   const int lane = threadIdx.x & 31;
   const int W = k.W, H = k.H;
@@ -923,7 +929,7 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
         if (g.col + e < W) {
           gy_up.v[e] = gyu.v[e];
           ey_up.v[e] = xc.v[e] - xu.v[e] - gyu.v[e];
-          wy_up.v[e] = robust_weight(ey_up.v[e], vyu.v[e], c.delta, c.loss);
+          wy_up.v[e] = robust_weight_k<LK>(ey_up.v[e], vyu.v[e], c.delta);
         }
       }
     }
@@ -958,7 +964,7 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
         if (g.col + e < W - 1) {
           gxv.v[e] = gxr.v[e];
           exv.v[e] = x_e.v[e] - x_cur.v[e] - gxr.v[e];
-          wxv.v[e] = robust_weight(exv.v[e], vxr.v[e], c.delta, c.loss);
+          wxv.v[e] = robust_weight_k<LK>(exv.v[e], vxr.v[e], c.delta);
         }
       }
       if (v < H - 1) {
@@ -968,7 +974,7 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
           if (g.col + e < W) {
             gyv.v[e] = gyr.v[e];
             eyv.v[e] = x_dn.v[e] - x_cur.v[e] - gyr.v[e];
-            wyv.v[e] = robust_weight(eyv.v[e], vyr.v[e], c.delta, c.loss);
+            wyv.v[e] = robust_weight_k<LK>(eyv.v[e], vyr.v[e], c.delta);
           }
         }
       }
@@ -988,7 +994,7 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
           const float xw = ring.f1(sc, A_X, 3);
           gg = cnn1<DT>(ring, sc, A_GX, 3);
           b = x_cur.v[0] - xw - gg;
-          a = robust_weight(b, cnn1<DT>(ring, sc, A_VX, 3), c.delta, c.loss);
+          a = robust_weight_k<LK>(b, cnn1<DT>(ring, sc, A_VX, 3), c.delta);
         }
       }
       wxw.v[0] = a;
@@ -1005,27 +1011,30 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
         const float xi = x_cur.v[e];
         float ws = 0.0f, rs = 0.0f, bs = 0.0f;
         if (semi && semi_valid(ms.v[e], vs.v[e])) {
-          ws = robust_weight(xi - t - ms.v[e], vs.v[e], c.delta, c.loss);
+          ws = robust_weight_k<LK>(xi - t - ms.v[e], vs.v[e], c.delta);
           rs = ws * (t + ms.v[e] - xi);
           bs = ws * (t + ms.v[e]);
         }
         float wn = 0.0f, m = 0.0f;
         if (net) {
           m = mn.v[e];
-          wn = robust_weight(xi - m, vn.v[e], c.delta, c.loss);
+          wn = robust_weight_k<LK>(xi - m, vn.v[e], c.delta);
         }
         d = ws + wn + wxv.v[e] + wxw.v[e] + wyv.v[e] + wy_up.v[e];
         r = rs + wn * (m - xi) + wxv.v[e] * exv.v[e] - wxw.v[e] * exw.v[e] +
             wyv.v[e] * eyv.v[e] - wy_up.v[e] * ey_up.v[e];
-        b = bs + wn * m - wxv.v[e] * gxv.v[e] + wxw.v[e] * gxw.v[e] - wyv.v[e] * gyv.v[e] +
-            wy_up.v[e] * gy_up.v[e];
+        if (wide)  // b only for the norms a tolerance or a report reads
+          b = bs + wn * m - wxv.v[e] * gxv.v[e] + wxw.v[e] * gxw.v[e] - wyv.v[e] * gyv.v[e] +
+              wy_up.v[e] * gy_up.v[e];
       }
       const float id = d > 0.0f ? __fdividef(1.0f, d) : 0.0f;
       dd.v[e] = id;
       rr_.v[e] = r;
       acc[0] += r * (r * id);
-      acc[1] += r * r;
-      acc[2] += b * b;
+      if (wide) {
+        acc[1] += r * r;
+        acc[2] += b * b;
+      }
     }
     stm<4>(k.diag + i, dd);
     stm<4>(k.wx + i, wxv);
@@ -1049,7 +1058,7 @@ struct Seg {
 // dynamic shared memory of the VEC = 4 kernel: the warps' row rings + mbarriers
 constexpr int kRingSmem = kWarps * kWarpStageBytes + kWarps * kStages * 8;
 
-template <int VEC>
+template <int VEC, int LK>
 __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     k_fused(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns,
             int first) {
@@ -1110,18 +1119,23 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
   const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step == DF_SCALE_ALTERNATE;
   int parity = 0;
   bool alive = true;
+  const bool wide = c.tol > 0.0 || n_pcg == 0;  // the assembly's r.r and b.b are read
 
   // One pass over the CTA's tiles, then slots, barrier and per-keyframe sums.
-  auto run_pass = [&](int kind, int it, bool final_scale) __attribute__((always_inline)) -> bool {
+  // fin (the last x update only): bit 0 the next scale step's sums, bit 1 r.r
+  auto run_pass = [&](int kind, int it, int fin) __attribute__((always_inline)) -> bool {
     // the sums this pass's consumers use: a[q0 .. q0 + nq) of the tiles'
     // accumulators, reduced into s_tot[.][0 .. nq)
     int q0 = 0, nq = kQ;
     switch (kind) {
       case P_SCALE: nq = 2; break;                                      // sum w, sum w (x - mu_s)
-      case P_ASSEMBLE: nq = (c.tol > 0.0 || n_pcg == 0) ? 3 : 1; break;  // r.z (r.r, b.b)
+      case P_ASSEMBLE: nq = wide ? 3 : 1; break;                         // r.z (r.r, b.b)
       case P_INIT: q0 = 1; nq = 1; break;                                // (w, u)
       case P_ITER: nq = c.tol > 0.0 ? 3 : 2; break;                      // (r, u), (w, u) (r.r)
-      default: nq = final_scale ? 3 : 1; break;                          // r.r (scale sums)
+      default:                                                           // (r.r) (scale sums)
+        q0 = (fin & 2) ? 0 : 1;
+        nq = ((fin & 2) ? 1 : 0) + ((fin & 1) ? 2 : 0);
+        break;
     }
     for (int q = tid; q < kWarps * kMaxSeg * kQ; q += kThreads) (&s_acc[0][0][0])[q] = ff2{0.0f, 0.0f};
     __syncthreads();
@@ -1150,15 +1164,15 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
         bool ok = true;
         switch (kind) {
           case P_SCALE:
-            ok = tma_scale_tile(rg, K, g, ft, c, a);
+            ok = tma_scale_tile<LK>(rg, K, g, ft, c, a);
             break;
           case P_ASSEMBLE:
             if (K.pl.dtype == DF_BF16)
-              ok = tma_assemble_tile<DF_BF16>(rg, K, g, ft, c, a);
+              ok = tma_assemble_tile<DF_BF16, LK>(rg, K, g, ft, c, wide, a);
             else if (K.pl.dtype == DF_F16)
-              ok = tma_assemble_tile<DF_F16>(rg, K, g, ft, c, a);
+              ok = tma_assemble_tile<DF_F16, LK>(rg, K, g, ft, c, wide, a);
             else
-              ok = tma_assemble_tile<DF_F32>(rg, K, g, ft, c, a);
+              ok = tma_assemble_tile<DF_F32, LK>(rg, K, g, ft, c, wide, a);
             break;
           case P_INIT:
             if (!S.stop) ok = tma_cg_tile<0>(rg, K, g, 0.0f, 0.0f, R0, S0, W1, R1, S1, W0, a);
@@ -1172,7 +1186,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
             }
             break;
           default:  // P_FINAL
-            ok = tma_final_tile(rg, K, g, it == 0, !S.stop, fa, fb, final_scale, ft, c, Rc, Sp,
+            ok = tma_final_tile<LK>(rg, K, g, it == 0, !S.stop, fa, fb, fin & 1, fin & 2, ft, c, Rc, Sp,
                                 Wc, a);
             break;
         }
@@ -1183,15 +1197,15 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       } else {
       switch (kind) {
         case P_SCALE:
-          scale_tile<VEC>(K, g, ft, c, a);
+          scale_tile<VEC, LK>(K, g, ft, c, a);
           break;
         case P_ASSEMBLE:
           if (K.pl.dtype == DF_BF16)
-            assemble_tile<VEC, DF_BF16>(K, g, ft, c, a);
+            assemble_tile<VEC, DF_BF16, LK>(K, g, ft, c, a);
           else if (K.pl.dtype == DF_F16)
-            assemble_tile<VEC, DF_F16>(K, g, ft, c, a);
+            assemble_tile<VEC, DF_F16, LK>(K, g, ft, c, a);
           else
-            assemble_tile<VEC, DF_F32>(K, g, ft, c, a);
+            assemble_tile<VEC, DF_F32, LK>(K, g, ft, c, a);
           break;
         case P_INIT:
           if (!S.stop) cg_tile<VEC, 0>(K, g, 0.0f, 0.0f, R0, S0, W1, R1, S1, W0, a);
@@ -1205,14 +1219,16 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
           }
           break;
         default:  // P_FINAL
-          final_tile<VEC>(K, g, it == 0, !S.stop, fa, fb, final_scale, ft, c, Rc, Sp, Wc, a);
+          final_tile<VEC, LK>(K, g, it == 0, !S.stop, fa, fb, fin & 1, ft, c, Rc, Sp, Wc, a);
           break;
       }
       }
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
         if (q < nq) {
-          const ff2 dq = warp_sum_ff(ff2{a[q0 + q < kQ ? q0 + q : 0], 0.0f});
+          const int qa = q0 + q;  // selects, not a dynamic index into a[]
+          const float aq = qa == 0 ? a[0] : (qa == 1 ? a[1] : a[2]);
+          const ff2 dq = warp_sum_ff(ff2{aq, 0.0f});
           if (lane == 0) s_acc[warp][seg][q] = ff_add(s_acc[warp][seg][q], dq);
         }
       }
@@ -1223,7 +1239,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     // that keyframe (one slot per writer), then read only the own inbox
     // after the barrier: no cache line is read by more than one CTA.
     Slot *pbox = slots + (size_t)parity * h->slot_stride;
-    if (tid < nseg * 4) {
+    if (nq > 0 && tid < nseg * 4) {
       const int sg = tid >> 2, q = tid & 3;
       ff2 s = ff2{0.0f, 0.0f};
       if (q < kQ)
@@ -1231,7 +1247,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       s_push[sg].v[q] = s;
     }
     __syncthreads();
-    for (int sg = 0; sg < nseg; ++sg) {
+    for (int sg = 0; sg < nseg && nq > 0; ++sg) {
       const FusedKf &K = s_kf[sg];
       const int nk = K.slot_end - K.slot_begin, l = slot0 + sg - K.slot_begin;
       const int np = inbox_slots(nk);
@@ -1269,13 +1285,13 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
   for (int gn = 0; gn < n_gn && alive; ++gn) {
     if (do_scale) {
       if (!scale_pending) {
-        alive = run_pass(P_SCALE, 0, false);
+        alive = run_pass(P_SCALE, 0, 0);
         if (!alive) break;
         scale_update(0, 1);
       }
       scale_pending = false;
     }
-    alive = run_pass(P_ASSEMBLE, 0, false);
+    alive = run_pass(P_ASSEMBLE, 0, 0);
     if (!alive) break;
     if (tid < nseg) {
       Seg &S = s_seg[tid];
@@ -1289,7 +1305,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     }
     __syncthreads();
     if (n_pcg == 0) continue;
-    alive = run_pass(P_INIT, 0, false);
+    alive = run_pass(P_INIT, 0, 0);
     if (!alive) break;
     if (tid < nseg) {
       Seg &S = s_seg[tid];
@@ -1306,23 +1322,27 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     __syncthreads();
     for (int it = 0; it < n_pcg; ++it) {
       if (it == n_pcg - 1) {
+        // sums needed: the next scale step's two; r.r for a tolerance and
+        // for the report after the launch's last GN iteration
         const bool fs = do_scale && gn + 1 < n_gn;
-        alive = run_pass(P_FINAL, it, fs);
+        const bool rr = c.tol > 0.0 || gn + 1 == n_gn;
+        alive = run_pass(P_FINAL, it, (fs ? 1 : 0) | (rr ? 2 : 0));
         if (!alive) break;
         if (tid < nseg) {
           Seg &S = s_seg[tid];
           if (!S.stop) {
             S.iters += 1;
-            S.rr = s_tot[tid][0];
+            if (rr) S.rr = s_tot[tid][0];
           }
         }
         __syncthreads();
         if (fs) {
-          scale_update(1, 2);
+          if (rr) scale_update(1, 2);
+          else scale_update(0, 1);
           scale_pending = true;
         }
       } else {
-        alive = run_pass(P_ITER, it, false);
+        alive = run_pass(P_ITER, it, 0);
         if (!alive) break;
         if (tid < nseg) {
           Seg &S = s_seg[tid];
@@ -1378,6 +1398,18 @@ DevInfo g_dev[64];
 bool g_dev_init[64] = {false};
 std::mutex g_dev_mu;
 
+// The kernel instance of a vector width and a loss kind.
+const void *fused_fn(int vec, int lk) {
+  if (vec == 4) {
+    if (lk == LK_LSQ) return reinterpret_cast<const void *>(k_fused<4, LK_LSQ>);
+    if (lk == LK_TUKEY) return reinterpret_cast<const void *>(k_fused<4, LK_TUKEY>);
+    return reinterpret_cast<const void *>(k_fused<4, LK_HUBER>);
+  }
+  if (lk == LK_LSQ) return reinterpret_cast<const void *>(k_fused<1, LK_LSQ>);
+  if (lk == LK_TUKEY) return reinterpret_cast<const void *>(k_fused<1, LK_TUKEY>);
+  return reinterpret_cast<const void *>(k_fused<1, LK_HUBER>);
+}
+
 const DevInfo &dev_info() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -1392,9 +1424,18 @@ const DevInfo &dev_info() {
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     d.coop = coop != 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[0], k_fused<1>, kThreads, 0);
-    cudaFuncSetAttribute(k_fused<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[1], k_fused<4>, kThreads, kRingSmem);
+    // the instances of one vector width differ only in the loss: the grid
+    // follows the least resident of them
+    d.occ[0] = d.occ[1] = 1 << 20;
+    for (int lk = LK_LSQ; lk <= LK_TUKEY; ++lk) {
+      int o1 = 0, o4 = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, fused_fn(1, lk), kThreads, 0);
+      cudaFuncSetAttribute(fused_fn(4, lk), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kRingSmem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o4, fused_fn(4, lk), kThreads, kRingSmem);
+      d.occ[0] = std::min(d.occ[0], o1);
+      d.occ[1] = std::min(d.occ[1], o4);
+    }
     cudaGetLastError();
     g_dev[dev] = d;
     g_dev_init[dev] = true;
@@ -1567,8 +1608,7 @@ cudaError_t streaming_launch(void *dplan, const LaunchShape &shape, const SolveC
   const int G = shape.G, vec = shape.vec;
   void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns, &first};
   count_launches(1);
-  const void *fn = vec == 4 ? reinterpret_cast<const void *>(k_fused<4>)
-                            : reinterpret_cast<const void *>(k_fused<1>);
+  const void *fn = fused_fn(vec, loss_kind(c.loss, c.delta));
   return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args,
                                      vec == 4 ? (size_t)kRingSmem : 0, s);
 }

@@ -105,15 +105,38 @@ __device__ __forceinline__ bool robust_active(float delta) {
 // result hinges on a comparison; the reciprocals use the hardware
 // approximations (rsqrtf, __fdividef: a few ulp, far inside the solve's
 // tolerance).
-__device__ __forceinline__ float robust_weight(float r, float V, float delta, int loss) {
+//
+// The fused kernels fix the loss at compile time (one instance per loss
+// kind), so their inner loops carry no branch on it; robust_weight picks the
+// same arithmetic at run time for the other kernels.
+enum : int { LK_LSQ = 0, LK_HUBER = 1, LK_TUKEY = 2 };
+
+__host__ __device__ inline int loss_kind(int loss, float delta) {
+  if (!(delta > 0.0f && delta < INFINITY)) return LK_LSQ;
+  return loss == DF_LOSS_TUKEY ? LK_TUKEY : LK_HUBER;
+}
+
+template <int LK>
+__device__ __forceinline__ float robust_weight_k(float r, float V, float delta) {
   const float iv = __fdividef(1.0f, V);
-  if (!robust_active(delta)) return iv;
-  const float u2 = r * r * iv;
-  if (loss == DF_LOSS_TUKEY) {
+  if constexpr (LK == LK_LSQ) {
+    return iv;
+  } else if constexpr (LK == LK_TUKEY) {
+    const float u2 = r * r * iv;
     const float q = 1.0f - __fdividef(u2, delta * delta);
     return u2 < delta * delta ? q * q * iv : 0.0f;
+  } else {
+    const float u2 = r * r * iv;
+    return iv * fminf(1.0f, delta * rsqrtf(u2));
   }
-  return iv * fminf(1.0f, delta * rsqrtf(u2));
+}
+
+__device__ __forceinline__ float robust_weight(float r, float V, float delta, int loss) {
+  switch (loss_kind(loss, delta)) {
+    case LK_LSQ: return robust_weight_k<LK_LSQ>(r, V, delta);
+    case LK_TUKEY: return robust_weight_k<LK_TUKEY>(r, V, delta);
+    default: return robust_weight_k<LK_HUBER>(r, V, delta);
+  }
 }
 
 // Robust loss rho(u) (the cost of Eq. 5 with each squared whitened residual

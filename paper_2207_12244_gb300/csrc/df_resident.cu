@@ -168,7 +168,7 @@ __device__ __forceinline__ void publish_edges(const float *src, float *dst, int 
 // JOINT: also keep ws in the U array and sum the border's S = sum ws and
 // r_t = sum ws (x - t - mu_s) into acc[2], acc[3] (b.b is not formed: the
 // joint solve runs with a fixed iteration count here).
-template <int DT, bool JOINT>
+template <int DT, bool JOINT, int LK>
 __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, float t,
                               const SolveCfg &c, float acc[kRQ]) {
   const int W = k.W, H = k.H, bp = nr * W;
@@ -185,12 +185,12 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     float wx = 0.0f, ex = 0.0f, wy = 0.0f, ey = 0.0f;
     if (grad && u < W - 1) {
       ex = m.X[q + 1] - xq - ld_cnn<DT>(k.cnn[2], gi);
-      wx = robust_weight(ex, ld_cnn<DT>(k.cnn[3], gi), c.delta, c.loss);
+      wx = robust_weight_k<LK>(ex, ld_cnn<DT>(k.cnn[3], gi), c.delta);
     }
     if (grad && rb + v < H - 1) {
       const float xs = (v < nr - 1) ? m.X[q + W] : m.HA[4][u];
       ey = xs - xq - ld_cnn<DT>(k.cnn[4], gi);
-      wy = robust_weight(ey, ld_cnn<DT>(k.cnn[5], gi), c.delta, c.loss);
+      wy = robust_weight_k<LK>(ey, ld_cnn<DT>(k.cnn[5], gi), c.delta);
     }
     m.WX[q] = wx;
     m.WY[q] = wy;
@@ -203,7 +203,7 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
       const size_t gi = (size_t)(rb - 1) * P + u;
       gy = ld_cnn<DT>(k.cnn[4], gi);
       ey = m.X[u] - m.HA[0][u] - gy;
-      wy = robust_weight(ey, ld_cnn<DT>(k.cnn[5], gi), c.delta, c.loss);
+      wy = robust_weight_k<LK>(ey, ld_cnn<DT>(k.cnn[5], gi), c.delta);
     }
     m.WYT[u] = wy;
     m.HA[1][u] = ey;
@@ -219,7 +219,7 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     if (semi) {
       const float ms = __ldg(k.mu_s + gi), vs = __ldg(k.var_s + gi);
       if (semi_valid(ms, vs)) {
-        ws = robust_weight(xq - t - ms, vs, c.delta, c.loss);
+        ws = robust_weight_k<LK>(xq - t - ms, vs, c.delta);
         rs = ws * (t + ms - xq);
         bs = ws * (t + ms);
       }
@@ -227,7 +227,7 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     float wn = 0.0f, mn = 0.0f;
     if (net) {
       mn = ld_cnn<DT>(k.cnn[0], gi);
-      wn = robust_weight(xq - mn, ld_cnn<DT>(k.cnn[1], gi), c.delta, c.loss);
+      wn = robust_weight_k<LK>(xq - mn, ld_cnn<DT>(k.cnn[1], gi), c.delta);
     }
     const float wx = m.WX[q], ex = m.P[q], wy = m.WY[q], ey = m.S[q];
     const float wxl = u > 0 ? m.WX[q - 1] : 0.0f, exl = u > 0 ? m.P[q - 1] : 0.0f;
@@ -258,8 +258,9 @@ template <int N>
 using IC = std::integral_constant<int, N>;
 
 // JOINT: the joint (x, t) variant (c.scale_step == DF_SCALE_JOINT with the
-// semi-dense term); the alternating solve is the other instance.
-template <bool JOINT>
+// semi-dense term); the alternating solve is the other instance. LK: the
+// loss kind (least squares, Huber, Tukey), fixed per instance.
+template <bool JOINT, int LK>
 __global__ void __launch_bounds__(kRThreads, 1)
     k_resident(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns,
                int first) {
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
       const float ms = __ldg(k.mu_s + gi), vs = __ldg(k.var_s + gi);
       if (semi_valid(ms, vs)) {
         const float xq = m.X[it.q];
-        const float w = robust_weight(xq - t - ms, vs, c.delta, c.loss);
+        const float w = robust_weight_k<LK>(xq - t - ms, vs, c.delta);
         acc[q0] += w;
         acc[q0 + 1] += w * (xq - ms);
       }
@@ -428,18 +429,18 @@ __global__ void __launch_bounds__(kRThreads, 1)
         const float t = (float)s_seg.t;
         if constexpr (JOINT) {
           if (k.dtype == DF_BF16)
-            assemble_band<DF_BF16, true>(m, k, rb, nr, t, c, acc);
+            assemble_band<DF_BF16, true, LK>(m, k, rb, nr, t, c, acc);
           else if (k.dtype == DF_F16)
-            assemble_band<DF_F16, true>(m, k, rb, nr, t, c, acc);
+            assemble_band<DF_F16, true, LK>(m, k, rb, nr, t, c, acc);
           else
-            assemble_band<DF_F32, true>(m, k, rb, nr, t, c, acc);
+            assemble_band<DF_F32, true, LK>(m, k, rb, nr, t, c, acc);
         } else {
           if (k.dtype == DF_BF16)
-            assemble_band<DF_BF16, false>(m, k, rb, nr, t, c, acc);
+            assemble_band<DF_BF16, false, LK>(m, k, rb, nr, t, c, acc);
           else if (k.dtype == DF_F16)
-            assemble_band<DF_F16, false>(m, k, rb, nr, t, c, acc);
+            assemble_band<DF_F16, false, LK>(m, k, rb, nr, t, c, acc);
           else
-            assemble_band<DF_F32, false>(m, k, rb, nr, t, c, acc);
+            assemble_band<DF_F32, false, LK>(m, k, rb, nr, t, c, acc);
         }
         __syncthreads();
         publish_edges(m.R, Rg[0], W, nr, rb, P);
@@ -672,6 +673,18 @@ __global__ void __launch_bounds__(kRThreads, 1)
   grid_exit(h, G);
 }
 
+// The kernel instance of a variant and a loss kind.
+static const void *resident_fn(bool joint, int lk) {
+  if (joint) {
+    if (lk == LK_LSQ) return reinterpret_cast<const void *>(k_resident<true, LK_LSQ>);
+    if (lk == LK_TUKEY) return reinterpret_cast<const void *>(k_resident<true, LK_TUKEY>);
+    return reinterpret_cast<const void *>(k_resident<true, LK_HUBER>);
+  }
+  if (lk == LK_LSQ) return reinterpret_cast<const void *>(k_resident<false, LK_LSQ>);
+  if (lk == LK_TUKEY) return reinterpret_cast<const void *>(k_resident<false, LK_TUKEY>);
+  return reinterpret_cast<const void *>(k_resident<false, LK_HUBER>);
+}
+
 size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 struct ResDev {
@@ -694,8 +707,10 @@ const ResDev &rdev() {
     cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_resident<true>) == cudaSuccess)
-      d.static_smem = (int)fa.sharedSizeBytes;  // the larger of the two instances
+    for (int v = 0; v < 2; ++v)  // the largest static share of the instances
+      for (int lk = LK_LSQ; lk <= LK_TUKEY; ++lk)
+        if (cudaFuncGetAttributes(&fa, resident_fn(v == 1, lk)) == cudaSuccess)
+          d.static_smem = std::max(d.static_smem, (int)fa.sharedSizeBytes);
     cudaGetLastError();
     g_rdev[dev] = d;
     g_rdev_init[dev] = true;
@@ -835,8 +850,7 @@ cudaError_t resident_launch(void *dplan, const LaunchShape &shape, const SolveCf
                             int n_pcg, unsigned long long limit_ns, cudaStream_t s, int first) {
   PlanHeader *h = static_cast<PlanHeader *>(dplan);
   const bool joint = (c.terms & DF_TERM_SEMI) && c.scale_step == DF_SCALE_JOINT;
-  const void *fn = joint ? reinterpret_cast<const void *>(k_resident<true>)
-                         : reinterpret_cast<const void *>(k_resident<false>);
+  const void *fn = resident_fn(joint, loss_kind(c.loss, c.delta));
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, shape.smem);
   if (e != cudaSuccess) return e;
   void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns, &first};
