@@ -556,88 +556,73 @@ __device__ __forceinline__ void store4(float *p, const F<4> &a) {
 
 // Rows jb..je of a tile go through the ring in order; 'ensure(k)' waits for
 // the k-th of them, 'release()' frees the oldest waited row's stage and
-// stages the next row of the tile. Planes 0..NP-1; bit p of HALF marks a
-// 16-bit plane. Rows at index 0 (when has_above) and R - 1 (when has_below)
-// are halo rows and stage only planes 0..NH-1; the others stage the planes
-// of 'mask' (all NP unless a pass leaves some out). Plane counts and widths
-// are compile-time, so a row's copies are a straight run of instructions.
+// stages the next row of the tile. Each plane is
+// one bulk copy per row: the tile's 128 columns plus 16 bytes on each side,
+// clipped to the padded row; element size 4, or 2 for the planes in HALF
+// (16-bit network planes). Rows at index 0 (when has_above) and R - 1 (when
+// has_below) are halo rows and stage only planes 0..NH-1; the others stage
+// the planes of 'mask' (all NP unless a pass leaves some out). Lane p owns
+// plane p: it keeps that plane's source pointer, size and slot, so a row's
+// NP copies leave as one warp instruction (lane 0 posts the row's byte count
+// on the stage's mbarrier first).
 template <int NP, int NH, uint32_t HALF>
 struct TileRows {
+  static_assert(NP <= 32 && NH <= NP, "one lane per staged plane");
   RowRing &ring;
-  const char *src[NP];  // next row's copy start per plane
-  uint32_t b4, d4, b2, d2, rb4, rb2;
-  uint32_t mask;
+  const char *src = nullptr;  // this lane's plane: the next row's copy start
+  uint32_t bytes = 0;         // this lane's copy size
+  uint32_t dst = 0;           // shared address of this lane's slot in stage 0
+  uint32_t step = 0;          // row pitch of this lane's plane, bytes
+  uint32_t tx_full = 0, tx_halo = 0;  // bytes a full / halo row brings
   int R, issued = 0, waited = 0;
   bool has_above, has_below, ok = true;
+  bool mine_full = false, mine_halo = false;  // this lane copies in a full / halo row
   static constexpr uint32_t kAll = (NP >= 32) ? 0xffffffffu : ((1u << NP) - 1u);
   __device__ TileRows(RowRing &r, const StagePlane (&pl)[NP], int c0, int P, int jb, int R_,
-                      bool above, bool below, uint32_t mask_ = kAll)
-      : ring(r), mask(mask_), R(R_), has_above(above), has_below(below) {
+                      bool above, bool below, uint32_t mask = kAll)
+      : ring(r), R(R_), has_above(above), has_below(below) {
+    const int lane = threadIdx.x & 31;
     // column range [cs, ce) of a staged row: the tile's 128 columns and
     // 16 bytes on each side, clipped to the padded row
     const int cs4 = c0 - 4 > 0 ? c0 - 4 : 0, ce4 = c0 + 132 < P ? c0 + 132 : P;
     const int cs2 = c0 - 8 > 0 ? c0 - 8 : 0, ce2 = c0 + 136 < P ? c0 + 136 : P;
-    b4 = (uint32_t)(ce4 - cs4) * 4u;
-    d4 = (uint32_t)(cs4 - (c0 - 4)) * 4u;
-    b2 = (uint32_t)(ce2 - cs2) * 2u;
-    d2 = (uint32_t)(cs2 - (c0 - 8)) * 2u;
-    rb4 = (uint32_t)P * 4u;
-    rb2 = (uint32_t)P * 2u;
+    const uint32_t b4 = (uint32_t)(ce4 - cs4) * 4u, d4 = (uint32_t)(cs4 - (c0 - 4)) * 4u;
+    const uint32_t b2 = (uint32_t)(ce2 - cs2) * 2u, d2 = (uint32_t)(cs2 - (c0 - 8)) * 2u;
+    const uint32_t rb4 = (uint32_t)P * 4u, rb2 = (uint32_t)P * 2u;
+    const uint32_t s0 = smem_addr(ring.smem);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       constexpr uint32_t H = HALF;
       const bool h = (H >> p) & 1u;
-      src[p] = static_cast<const char *>(pl[p].base) + (size_t)jb * (h ? rb2 : rb4) +
-               (size_t)(h ? cs2 * 2 : cs4 * 4);
+      const uint32_t bp = h ? b2 : b4;
+      if (p < NH) tx_halo += bp;
+      if ((mask >> p) & 1u) tx_full += bp;
+      if (p == lane) {
+        src = static_cast<const char *>(pl[p].base) + (size_t)jb * (h ? rb2 : rb4) +
+              (size_t)(h ? cs2 * 2 : cs4 * 4);
+        bytes = bp;
+        dst = s0 + (uint32_t)(p * kSlotBytes) + (h ? d2 : d4);
+        step = h ? rb2 : rb4;
+        mine_halo = p < NH;
+        mine_full = (mask >> p) & 1u;
+      }
     }
-    if ((threadIdx.x & 31) == 0) fence_proxy_async_global();  // see the previous pass's stores
+    if (mine_full || mine_halo) fence_proxy_async_global();  // see the previous pass's stores
     while (issued < R && issued < kStages) issue_one();
   }
   __device__ __forceinline__ void issue_one() {
     __syncwarp();
     const bool halo = (has_above && issued == 0) || (has_below && issued == R - 1);
     const int s = issued % kStages;
-    if ((threadIdx.x & 31) == 0) {
-      char *base = ring.smem + s * kStageBytes;
-      uint64_t *bar = &ring.bars[s];
+    uint64_t *bar = &ring.bars[s];
+    if ((threadIdx.x & 31) == 0) mbar_arrive_expect_tx(bar, halo ? tx_halo : tx_full);
+    __syncwarp();
+    if (halo ? mine_halo : mine_full) {
       fence_proxy_async_shared();  // earlier generic reads of this stage come first
-      if (halo) {
-        constexpr uint32_t hm = (1u << NH) - 1u;
-        constexpr int n2 = __builtin_popcount(HALF & hm), n4 = NH - n2;
-        mbar_arrive_expect_tx(bar, (uint32_t)n4 * b4 + (uint32_t)n2 * b2);
-#pragma unroll
-        for (int p = 0; p < NH; ++p) {
-          constexpr uint32_t H = HALF;
-          const bool h = (H >> p) & 1u;
-          bulk_copy_g2s(base + p * kSlotBytes + (h ? d2 : d4), src[p], h ? b2 : b4, bar);
-        }
-      } else if (mask == kAll) {
-        constexpr int n2 = __builtin_popcount(HALF & kAll), n4 = NP - n2;
-        mbar_arrive_expect_tx(bar, (uint32_t)n4 * b4 + (uint32_t)n2 * b2);
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          constexpr uint32_t H = HALF;
-          const bool h = (H >> p) & 1u;
-          bulk_copy_g2s(base + p * kSlotBytes + (h ? d2 : d4), src[p], h ? b2 : b4, bar);
-        }
-      } else {
-        const uint32_t n2 = __popc(mask & HALF), n4 = __popc(mask & ~HALF);
-        mbar_arrive_expect_tx(bar, n4 * b4 + n2 * b2);
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          constexpr uint32_t H = HALF;
-          const bool h = (H >> p) & 1u;
-          if (mask & (1u << p))
-            bulk_copy_g2s(base + p * kSlotBytes + (h ? d2 : d4), src[p], h ? b2 : b4, bar);
-        }
-      }
+      bulk_copy_g2s_a(dst + (uint32_t)(s * kStageBytes), src, bytes, smem_addr(bar));
     }
     ring.pending |= 1u << s;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      constexpr uint32_t H = HALF;
-      src[p] += ((H >> p) & 1u) ? rb2 : rb4;
-    }
+    src += step;
     ++issued;
   }
   __device__ __forceinline__ int stage(int k) const { return k % kStages; }

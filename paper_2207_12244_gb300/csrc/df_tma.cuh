@@ -62,6 +62,17 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
 }
 
 // generic-proxy accesses before async-proxy accesses of the same memory
+// The same with the shared addresses of the destination and the mbarrier
+// already converted.
+__device__ __forceinline__ void bulk_copy_g2s_a(uint32_t dst, const void *src, uint32_t bytes,
+                                                uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
