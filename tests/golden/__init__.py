@@ -1,0 +1,51 @@
+"""Reader of the golden fixtures (written by make_golden.py from the FP64 oracle)."""
+from __future__ import annotations
+
+import glob
+import os
+import types
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+LOSSES = {"huber": 0, "tukey": 1}
+SCALE_STEPS = {"fixed": 0, "alternate": 1, "joint": 2}
+
+
+def paths():
+    return sorted(glob.glob(os.path.join(HERE, "*.txt")))
+
+
+def load(path):
+    """One fixture as a namespace: the keyframe planes (float32 [H, W]), the
+    solve's parameters and the expected x (float64 [H, W]), t and iterations."""
+    g = types.SimpleNamespace(name=os.path.basename(path)[:-4])
+    planes = {}
+    with open(path) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            key, _, rest = line.strip().partition(" ")
+            if key == "plane":
+                pname, _, vals = rest.partition(" ")
+                planes[pname] = [float.fromhex(v) for v in vals.split()]
+            elif key == "expect_x":
+                g.x = np.array([float.fromhex(v) for v in rest.split()], np.float64)
+            elif key in ("W", "H", "n_gn", "n_pcg", "terms", "expect_iters"):
+                setattr(g, key, int(rest))
+            elif key in ("delta", "expect_t"):
+                setattr(g, key, float.fromhex(rest))
+            elif key == "loss":
+                g.loss = LOSSES[rest]
+            elif key == "scale_step":
+                g.scale_step = SCALE_STEPS[rest]
+            else:
+                raise ValueError(f"{path}: unknown key {key}")
+    g.width, g.height = g.W, g.H
+    for n, v in planes.items():
+        a = np.array(v, np.float32).reshape(g.H, g.W)
+        setattr(g, n, a)
+    g.x = g.x.reshape(g.H, g.W)
+    g.cnn_planes = tuple(getattr(g, n) for n in ("mu_n", "var_n", "gx", "var_gx", "gy", "var_gy"))
+    return g
