@@ -108,6 +108,22 @@ def lib_source_hash():
     return h.hexdigest()[:16]
 
 
+def traffic_key(args, workload: str) -> str:
+    """Key of a workload's dominant-kernel entry in profiles/traffic.json:
+    the solver, the workload and every launch-shape or method flag that
+    changes which kernel runs (a forced mode, grid cap, tile shape, the joint
+    scale step)."""
+    key = f"solve_{args.solver}_{workload}"
+    if getattr(args, "scale_step", "alternate") != "alternate":
+        key += f"_{args.scale_step}"
+    if args.mode != "auto":
+        key += f"_{args.mode}"
+    for flag in ("max_ctas", "vec", "tile_rows"):
+        if getattr(args, flag, 0):
+            key += f"_{flag}{getattr(args, flag)}"
+    return key
+
+
 def ncu_traffic(kernel_key: str):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu
     summary, if it was taken on the current kernel sources."""
@@ -564,7 +580,7 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     solve_s = statistics.mean(solve_ms) / 1e3
     achieved = alg / solve_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(f"solve_{args.solver}_{name}"),
+                "frac": achieved / peak, "traffic": ncu_traffic(traffic_key(args, name)),
                 "peak_kind": peak_kind, "region": "df_optimise_batch (all keyframes, one frame)",
                 "alg_bytes_per_launch": alg}
     e2e = None
@@ -791,8 +807,7 @@ def main():
                          args.n_gn * ALG_BYTES_PER_GN_PX)
     peak, peak_kind = peaks()
     achieved = alg_bytes / solve_avg_s / 1e9
-    kernel_key = f"solve_{args.solver}_{WORKLOAD}" + (
-        "" if args.scale_step == "alternate" else f"_{args.scale_step}")
+    kernel_key = traffic_key(args, WORKLOAD)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": ncu_traffic(kernel_key),
                 "peak_kind": peak_kind, "region": "df_optimise (one frame's solve)",
