@@ -1036,7 +1036,8 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
 }
 
 struct Seg {
-  double t, gam, alpha, beta, bb, rr;
+  double t, bb, rr;
+  ff2 gam, alpha, beta;  // CG scalars (double-float)
   int stop, iters, active, pad;
 };
 
@@ -1052,7 +1053,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
   __shared__ Seg s_seg[kMaxSeg];
   __shared__ ff2 s_acc[kWarps][kMaxSeg][kQ];
   __shared__ Slot s_push[kMaxSeg];
-  __shared__ double s_tot[kMaxSeg][kQ];
+  __shared__ ff2 s_tot[kMaxSeg][kQ];  // this pass's totals
   __shared__ int s_nseg;
   __shared__ unsigned int s_epoch;
 
@@ -1077,7 +1078,8 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       Seg &s = s_seg[n];
       const Scalars *sc = kfs[kk].pl.sc;
       s.t = sc->t;
-      s.gam = s.alpha = s.beta = s.bb = 0.0;
+      s.gam = s.alpha = s.beta = ff2{0.0f, 0.0f};
+      s.bb = 0.0;
       s.rr = sc->rr;
       s.stop = 0;
       s.iters = first ? 0 : sc->iters;
@@ -1139,7 +1141,8 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       if (!S.active) continue;
       const Geo g = geo_of<VEC>(sx * 32 * VEC, r0, nrows);
       float a[kQ] = {0.0f, 0.0f, 0.0f};
-      const float ft = (float)S.t, fa = (float)S.alpha, fb = (float)S.beta;
+      // hi is the float nearest to a double-float value
+      const float ft = (float)S.t, fa = S.alpha.hi, fb = S.beta.hi;
       float *R0 = K.pl.v[1], *R1 = K.pl.v[2], *S0 = K.pl.v[3], *S1 = K.pl.v[4];
       float *W0 = K.pl.v[5], *W1 = K.pl.v[6];
       float *Rc = (it & 1) ? R1 : R0, *Rn = (it & 1) ? R0 : R1;
@@ -1250,7 +1253,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       const int sg = pq / nq, q = pq - sg * nq;
       const FusedKf &K = s_kf[sg];
       const int nk = K.slot_end - K.slot_begin, l = slot0 + sg - K.slot_begin;
-      const double tot = warp_inbox_sum_q(pbox + K.inbox0 + (size_t)l * inbox_slots(nk), nk, q);
+      const ff2 tot = warp_inbox_sum_q(pbox + K.inbox0 + (size_t)l * inbox_slots(nk), nk, q);
       if (lane == 0) s_tot[sg][q] = tot;
     }
     __syncthreads();
@@ -1261,7 +1264,8 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
   auto scale_update = [&](int qw, int qwr) {
     if (tid < nseg) {
       Seg &S = s_seg[tid];
-      if (S.active && s_tot[tid][qw] > 0.0) S.t = s_tot[tid][qwr] / s_tot[tid][qw];
+      if (S.active && s_tot[tid][qw].hi > 0.0f)
+        S.t = ff_to_double(ff_div(s_tot[tid][qwr], s_tot[tid][qw]));
     }
     __syncthreads();
   };
@@ -1283,8 +1287,8 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       S.gam = s_tot[tid][0];
       S.stop = 0;
       if (c.tol > 0.0 || n_pcg == 0) {
-        S.rr = s_tot[tid][1];
-        S.bb = s_tot[tid][2];
+        S.rr = ff_to_double(s_tot[tid][1]);
+        S.bb = ff_to_double(s_tot[tid][2]);
         S.stop = (c.tol > 0.0 && sqrt(S.rr) < c.tol * sqrt(S.bb)) ? 1 : 0;
       }
     }
@@ -1295,12 +1299,12 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     if (tid < nseg) {
       Seg &S = s_seg[tid];
       if (!S.stop) {
-        const double dl = s_tot[tid][0];  // (w0, u0)
-        if (S.gam == 0.0 || !(dl > 0.0)) {
+        const ff2 dl = s_tot[tid][0];  // (w0, u0)
+        if (S.gam.hi == 0.0f || !(dl.hi > 0.0f)) {
           S.stop = 1;
         } else {
-          S.alpha = S.gam / dl;
-          S.beta = 0.0;
+          S.alpha = ff_div(S.gam, dl);
+          S.beta = ff2{0.0f, 0.0f};
         }
       }
     }
@@ -1317,7 +1321,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
           Seg &S = s_seg[tid];
           if (!S.stop) {
             S.iters += 1;
-            if (rr) S.rr = s_tot[tid][0];
+            if (rr) S.rr = ff_to_double(s_tot[tid][0]);
           }
         }
         __syncthreads();
@@ -1333,18 +1337,19 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
           Seg &S = s_seg[tid];
           if (!S.stop) {
             S.iters += 1;
-            if (c.tol > 0.0) S.rr = s_tot[tid][2];
-            const double gn_ = s_tot[tid][0], dl = s_tot[tid][1];
+            if (c.tol > 0.0) S.rr = ff_to_double(s_tot[tid][2]);
+            const ff2 gn_ = s_tot[tid][0], dl = s_tot[tid][1];
             if (c.tol > 0.0 && sqrt(S.rr) < c.tol * sqrt(S.bb)) {
               S.stop = 1;
             } else {
-              const double beta = gn_ / S.gam;
-              const double denom = dl - beta * gn_ / S.alpha;
-              if (gn_ == 0.0 || !(denom > 0.0)) {
+              // beta = gamma / gamma_prev; p.Ap = delta - beta gamma / alpha_prev
+              const ff2 beta = ff_div(gn_, S.gam);
+              const ff2 denom = ff_sub(dl, ff_div(ff_mul(beta, gn_), S.alpha));
+              if (gn_.hi == 0.0f || !(denom.hi > 0.0f)) {
                 S.stop = 1;
               } else {
                 S.beta = beta;
-                S.alpha = gn_ / denom;
+                S.alpha = ff_div(gn_, denom);
                 S.gam = gn_;
               }
             }
@@ -1364,7 +1369,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     } else if (S.active && K.writer_cta == cta) {
       sc->t = S.t;
       sc->rr = S.rr;
-      sc->rho = S.gam;
+      sc->rho = ff_to_double(S.gam);
       sc->iters = S.iters;
       sc->stop = S.stop;
     }

@@ -44,7 +44,8 @@ struct ResCta {
 };
 
 struct ResSeg {
-  double t, gam, alpha, beta, bb, rr;
+  double t, bb, rr;
+  ff2 gam, alpha, beta;  // CG scalars (double-float)
   // joint (x, t) solve: the border components of the CG vectors
   double jS, jrt, jut, jwt, jpt, jst;
   int stop, iters, active, pad;
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
   extern __shared__ float4 dyn_smem[];
   __shared__ ff2 s_red[32 * kRQ];
   __shared__ ff2 s_cs[kRQ];
-  __shared__ double s_tot[kRQ];
+  __shared__ ff2 s_tot[kRQ];  // this pass's totals
   __shared__ unsigned int s_epoch;
   __shared__ ResKf s_kf;
   __shared__ ResSeg s_seg;
@@ -283,7 +284,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
     s_kf = kfs[me.kf];
     const Scalars *sc = s_kf.pl.sc;
     s_seg.t = sc->t;
-    s_seg.gam = s_seg.alpha = s_seg.beta = s_seg.bb = 0.0;
+    s_seg.gam = s_seg.alpha = s_seg.beta = ff2{0.0f, 0.0f};
+    s_seg.bb = 0.0;
     s_seg.rr = sc->rr;
     s_seg.stop = 0;
     s_seg.iters = first ? 0 : sc->iters;
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
     if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
     // warp q adds quantity q of the inbox; the other warps load the halo
     if (warp < NQ) {
-      const double tot = warp_inbox_sum_q(box + (size_t)lk * np, nk, warp);
+      const ff2 tot = warp_inbox_sum_q(box + (size_t)lk * np, nk, warp);
       if (lane == 0) s_tot[warp] = tot;
     } else {
       prefetch_halo(next_halo, next_cb, 32 * NQ);
@@ -403,7 +405,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
     }
   };
   auto scale_update = [&](int qw, int qwr) {
-    if (tid == 0 && s_seg.active && s_tot[qw] > 0.0) s_seg.t = s_tot[qwr] / s_tot[qw];
+    if (tid == 0 && s_seg.active && s_tot[qw].hi > 0.0f)
+      s_seg.t = ff_to_double(ff_div(s_tot[qwr], s_tot[qw]));
     __syncthreads();
   };
 
@@ -459,19 +462,20 @@ __global__ void __launch_bounds__(kRThreads, 1)
       if (tid == 0) {
         if constexpr (JOINT) {
           // border of the bordered system: S = sum ws, r_t, u_t = r_t / S
-          const double S = s_tot[2], rt = s_tot[3], ut = S > 0.0 ? rt / S : 0.0;
+          const double S = ff_to_double(s_tot[2]), rt = ff_to_double(s_tot[3]);
+          const double ut = S > 0.0 ? rt / S : 0.0;
           s_seg.jS = S;
           s_seg.jrt = rt;
           s_seg.jut = ut;
-          s_seg.gam = s_tot[0] + rt * ut;
-          s_seg.rr = s_tot[1] + rt * rt;
+          s_seg.gam = ff_from_double(ff_to_double(s_tot[0]) + rt * ut);
+          s_seg.rr = ff_to_double(s_tot[1]) + rt * rt;
           s_seg.stop = 0;
         } else {
           s_seg.gam = s_tot[0];
           s_seg.stop = 0;
           if (wide) {
-            s_seg.rr = s_tot[1];
-            s_seg.bb = s_tot[2];
+            s_seg.rr = ff_to_double(s_tot[1]);
+            s_seg.bb = ff_to_double(s_tot[2]);
             s_seg.stop = (c.tol > 0.0 && sqrt(s_seg.rr) < c.tol * sqrt(s_seg.bb)) ? 1 : 0;
           }
         }
@@ -507,23 +511,24 @@ __global__ void __launch_bounds__(kRThreads, 1)
       }
       if (!alive) break;
       if (tid == 0 && !s_seg.stop) {
-        double dl = s_tot[0];
+        ff2 dl = s_tot[0];
         if constexpr (JOINT) {  // w_t = S u_t - (ws, u); (w, u) gains w_t u_t
-          s_seg.jwt = s_seg.jS * s_seg.jut - s_tot[1];
-          dl += s_seg.jwt * s_seg.jut;
+          s_seg.jwt = s_seg.jS * s_seg.jut - ff_to_double(s_tot[1]);
+          dl = ff_from_double(ff_to_double(dl) + s_seg.jwt * s_seg.jut);
         }
-        if (s_seg.gam == 0.0 || !(dl > 0.0)) {
+        if (s_seg.gam.hi == 0.0f || !(dl.hi > 0.0f)) {
           s_seg.stop = 1;
         } else {
-          s_seg.alpha = s_seg.gam / dl;
-          s_seg.beta = 0.0;
+          s_seg.alpha = ff_div(s_seg.gam, dl);
+          s_seg.beta = ff2{0.0f, 0.0f};
         }
       }
       __syncthreads();
     }
     for (int it = 0; it < n_pcg && alive; ++it) {
       const int cb = it & 1, nb = cb ^ 1;
-      const float fa = (float)s_seg.alpha, fb = (float)s_seg.beta;
+      // hi is the float nearest to a double-float value
+      const float fa = s_seg.alpha.hi, fb = s_seg.beta.hi;
       const bool first = it == 0;
       const bool run = active && !s_seg.stop;
       float acc[kRQ] = {};
@@ -532,7 +537,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
         // s_t = w_t + beta s_t, t += alpha p_t, r_t -= alpha s_t
         __syncthreads();
         if (tid == 0 && run) {
-          const double a = s_seg.alpha, b = first ? 0.0 : s_seg.beta;
+          const double a = ff_to_double(s_seg.alpha), b = first ? 0.0 : ff_to_double(s_seg.beta);
           s_seg.jpt = s_seg.jut + b * s_seg.jpt;
           s_seg.jst = s_seg.jwt + b * s_seg.jst;
           s_seg.t += a * s_seg.jpt;
@@ -573,7 +578,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
         if (!alive) break;
         if (tid == 0 && run) {
           s_seg.iters += 1;
-          if (need_rr || !fs) s_seg.rr = s_tot[0] + (joint ? s_seg.jrt * s_seg.jrt : 0.0);
+          if (need_rr || !fs)
+            s_seg.rr = ff_to_double(s_tot[0]) + (joint ? s_seg.jrt * s_seg.jrt : 0.0);
         }
         __syncthreads();
         if (fs) {
@@ -627,24 +633,25 @@ __global__ void __launch_bounds__(kRThreads, 1)
         if (!alive) break;
         if (tid == 0 && run) {
           s_seg.iters += 1;
-          double gn_ = s_tot[0], dl = s_tot[1];
+          ff2 gn_ = s_tot[0], dl = s_tot[1];
           if constexpr (JOINT) {  // border terms of (r, u) and (w, u)
-            s_seg.jwt = s_seg.jS * s_seg.jut - s_tot[2];
-            gn_ += s_seg.jrt * s_seg.jut;
-            dl += s_seg.jwt * s_seg.jut;
+            s_seg.jwt = s_seg.jS * s_seg.jut - ff_to_double(s_tot[2]);
+            gn_ = ff_from_double(ff_to_double(gn_) + s_seg.jrt * s_seg.jut);
+            dl = ff_from_double(ff_to_double(dl) + s_seg.jwt * s_seg.jut);
           } else if (c.tol > 0.0) {
-            s_seg.rr = s_tot[2];
+            s_seg.rr = ff_to_double(s_tot[2]);
           }
           if (c.tol > 0.0 && sqrt(s_seg.rr) < c.tol * sqrt(s_seg.bb)) {
             s_seg.stop = 1;
           } else {
-            const double beta = gn_ / s_seg.gam;
-            const double denom = dl - beta * gn_ / s_seg.alpha;
-            if (gn_ == 0.0 || !(denom > 0.0)) {
+            // beta = gamma / gamma_prev; p.Ap = delta - beta gamma / alpha_prev
+            const ff2 beta = ff_div(gn_, s_seg.gam);
+            const ff2 denom = ff_sub(dl, ff_div(ff_mul(beta, gn_), s_seg.alpha));
+            if (gn_.hi == 0.0f || !(denom.hi > 0.0f)) {
               s_seg.stop = 1;
             } else {
               s_seg.beta = beta;
-              s_seg.alpha = gn_ / denom;
+              s_seg.alpha = ff_div(gn_, denom);
               s_seg.gam = gn_;
             }
           }
@@ -665,7 +672,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
     } else if (active && s_kf.cta_begin == (int)blockIdx.x) {
       sc->t = s_seg.t;
       sc->rr = s_seg.rr;
-      sc->rho = s_seg.gam;
+      sc->rho = ff_to_double(s_seg.gam);
       sc->iters = s_seg.iters;
       sc->stop = s_seg.stop;
     }

@@ -84,9 +84,10 @@ __device__ __forceinline__ bool grid_sync(PlanHeader *h, int G, unsigned long lo
 // FP64 shuffle tree over a CTA costs microseconds. The solver's inner
 // products are therefore carried as an unevaluated sum of two floats
 // (hi + lo, about 44 significant bits) from the warp level up, combined by
-// the error-free TwoSum transformation (Knuth / Dekker) in a fixed order, and
-// turned into one double per scalar at the very end. All operations are
-// FP32 adds, so the reduction is deterministic and as cheap as an FP32 one.
+// the error-free TwoSum transformation (Knuth / Dekker) in a fixed order; the
+// totals stay double-float for the CG scalars and become doubles only where
+// an FP64 value is stored or reported. All operations are FP32 adds, so the
+// reduction is deterministic and as cheap as an FP32 one.
 struct ff2 {
   float hi, lo;
 };
@@ -113,6 +114,58 @@ __device__ __forceinline__ ff2 warp_sum_ff(ff2 a) {
 
 __device__ __forceinline__ double ff_to_double(ff2 a) { return (double)a.hi + (double)a.lo; }
 
+// ---- double-float scalar arithmetic -----------------------------------------
+//
+// The CG scalars (gamma = r.z, alpha, beta, and p.Ap = delta - beta gamma /
+// alpha_prev) are formed from the double-float sums above by one thread
+// between two CTA barriers, so their latency is on every pass's critical
+// path. On GB300 a dependent FP64 operation takes ~64 cycles and an FP64
+// division ~550, so three divisions cost ~0.8 us per pass. The same
+// quantities in double-float arithmetic (Dekker, "A floating-point technique
+// for extending the available precision", Numer. Math. 18, 1971: the exact
+// product of two floats by one fused multiply-add, and the double-length
+// quotient q1 + q2 with q2 the correction from the exact remainder) take a
+// few FP32 operations each and keep ~44 significant bits, the precision of
+// the sums they come from.
+
+// a + b for |a| >= |b| (or a == 0), exactly as hi + lo
+__device__ __forceinline__ ff2 ff_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return ff2{s, b - (s - a)};
+}
+
+__device__ __forceinline__ ff2 ff_neg(ff2 a) { return ff2{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ ff2 ff_sub(ff2 a, ff2 b) { return ff_add(a, ff_neg(b)); }
+
+// a * b: the float product and its exact rounding error (fma), plus the
+// cross terms of the low parts
+__device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return ff_fast_two_sum(p, e);
+}
+
+// a / b: q1 from the hardware reciprocal of b.hi, the remainder a - q1 b with
+// q1 b.hi split exactly, q2 = remainder / b.hi. b.hi must be finite and
+// non-zero (callers test the denominator's sign first).
+__device__ __forceinline__ ff2 ff_div(ff2 a, ff2 b) {
+  const float rb = __fdividef(1.0f, b.hi);
+  const float q1 = a.hi * rb;
+  const float p = q1 * b.hi;
+  const float pe = fmaf(q1, b.hi, -p);
+  const float r = (((a.hi - p) - pe) + a.lo) - q1 * b.lo;
+  return ff_fast_two_sum(q1, r * rb);
+}
+
+// a double as hi + lo (for the FP64 values of the joint solve's border)
+__device__ __forceinline__ ff2 ff_from_double(double d) {
+  const float hi = (float)d;
+  return ff2{hi, (float)(d - (double)hi)};
+}
+
 // Reduction slot: kQ double-float values padded to 32 bytes (kQ <= 4).
 struct alignas(32) Slot {
   ff2 v[4];
@@ -122,66 +175,9 @@ struct alignas(32) Slot {
 // every lane loads whole slots without bounds checks (padding stays zero).
 __host__ __device__ __forceinline__ int inbox_slots(int n) { return (n + 31) & ~31; }
 
-// Sum of one inbox of n writers (slot order, then a fixed warp tree) by one
-// warp: every lane issues all its loads before adding. Result in lane 0.
-template <int kQ>
-__device__ __forceinline__ void warp_inbox_sum(const Slot *box, int n, double (&out)[kQ]) {
-  const int lane = threadIdx.x & 31;
-  const int np = inbox_slots(n);
-  constexpr int kU = 8;
-  ff2 acc[kQ];
-#pragma unroll
-  for (int q = 0; q < kQ; ++q) acc[q] = ff2{0.0f, 0.0f};
-  for (int base = 0; base < np; base += 32 * kU) {
-    float4 v[kU][2];
-#pragma unroll
-    for (int j = 0; j < kU; ++j) {
-      const int sl = base + lane + 32 * j;
-      const float4 *p = reinterpret_cast<const float4 *>(box + sl);
-      if (base + 32 * j < np) {
-        v[j][0] = __ldcg(p);
-        // slots of one or two sums are written without their second half
-        v[j][1] = kQ > 2 ? __ldcg(p + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-      } else {
-        v[j][0] = v[j][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kU; ++j) {
-      const ff2 s[4] = {ff2{v[j][0].x, v[j][0].y}, ff2{v[j][0].z, v[j][0].w},
-                        ff2{v[j][1].x, v[j][1].y}, ff2{v[j][1].z, v[j][1].w}};
-#pragma unroll
-      for (int q = 0; q < kQ; ++q) acc[q] = ff_add(acc[q], s[q]);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < kQ; ++q) out[q] = ff_to_double(warp_sum_ff(acc[q]));
-}
-
-// A CTA's FP32 per-thread partials -> double-float CTA total (fixed order),
-// valid in warp 0 lane 0. red must hold 32 * kQ ff2.
-template <int kQ>
-__device__ __forceinline__ void cta_partial_sum(const float (&acc)[kQ], ff2 *red,
-                                                ff2 (&out)[kQ]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-#pragma unroll
-  for (int q = 0; q < kQ; ++q) {
-    const ff2 s = warp_sum_ff(ff2{acc[q], 0.0f});
-    if (lane == 0) red[warp * kQ + q] = s;
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int q = 0; q < kQ; ++q) {
-      const ff2 x = lane < nwarps ? red[lane * kQ + q] : ff2{0.0f, 0.0f};
-      out[q] = warp_sum_ff(x);
-    }
-  }
-}
-
-// As cta_partial_sum, with the second level split over warps: warp q adds
-// quantity q (same order, same result), so the kQ trees run side by side.
+// A CTA's FP32 per-thread partials -> double-float CTA totals in a fixed
+// order: a warp tree per quantity, then warp q adds quantity q over the warps
+// (the kQ second-level trees run side by side).
 // The totals land in shared memory out[0..kQ-1] (valid after the caller's
 // next __syncthreads).
 template <int kQ>
@@ -202,9 +198,10 @@ __device__ __forceinline__ void cta_partial_sum_split(const float (&acc)[kQ], ff
   }
 }
 
-// One quantity q of an inbox of n writers, summed by one warp in the order of
-// warp_inbox_sum (slot order per lane, then a fixed warp tree).
-__device__ __forceinline__ double warp_inbox_sum_q(const Slot *box, int n, int q) {
+// One quantity q of an inbox of n writers, summed by one warp: every lane
+// adds its slots in slot order (issuing all its loads first), then a fixed
+// warp tree. The total is valid in lane 0, as a double-float.
+__device__ __forceinline__ ff2 warp_inbox_sum_q(const Slot *box, int n, int q) {
   const int lane = threadIdx.x & 31;
   const int np = inbox_slots(n);
   constexpr int kU = 8;
@@ -220,7 +217,7 @@ __device__ __forceinline__ double warp_inbox_sum_q(const Slot *box, int n, int q
 #pragma unroll
     for (int j = 0; j < kU; ++j) acc = ff_add(acc, ff2{v[j].x, v[j].y});
   }
-  return ff_to_double(warp_sum_ff(acc));
+  return warp_sum_ff(acc);
 }
 
 // Called once by every CTA as its last action: the last CTA out resets the
