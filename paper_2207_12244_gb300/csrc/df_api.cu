@@ -147,9 +147,46 @@ float host_elem(const void *p, size_t i, int dtype) {
   return half_bits_to_float(h);
 }
 
+// Validity of one network plane from the bit patterns of its elements:
+// finite (any sign) for a mean, finite and > 0 for a variance. Integer tests
+// over whole rows, so the loop is a plain streaming pass (the caller's planes
+// are megabytes and this runs before every host-pointer keyframe load).
+//   float: |bits| < 0x7f800000 is finite; 0 < bits < 0x7f800000 is finite > 0
+//   bf16:  the same on the upper 16 bits (0x7f80)
+//   fp16:  exponent field all ones (0x7c00) is Inf / NaN
+template <class T>
+bool plane_ok(const T *p, int W, int rows, int cols, bool is_var, uint32_t inf_bits) {
+  constexpr uint32_t kSign = sizeof(T) == 4 ? 0x80000000u : 0x8000u;
+  for (int v = 0; v < rows; ++v) {
+    const T *row = p + (size_t)v * W;
+    uint32_t bad = 0;
+    if (is_var) {
+      for (int u = 0; u < cols; ++u) bad |= (uint32_t)((uint32_t)row[u] - 1u >= inf_bits - 1u);
+    } else {
+      for (int u = 0; u < cols; ++u) bad |= (uint32_t)(((uint32_t)row[u] & ~kSign) >= inf_bits);
+    }
+    if (bad) return false;
+  }
+  return true;
+}
+
 // Host-side check of the network planes: means finite, variances finite > 0
 // (gx / var_gx in the last column and gy / var_gy in the last row ignored).
+// A fast pass over each plane's bits; only when it fails does the
+// element-by-element walk below look for the first bad pixel (row, column,
+// then plane order) to report.
 bool host_inputs_ok(const void *const cnn[6], int W, int H, int dtype, char *why, size_t n) {
+  bool fast_ok = true;
+  for (int j = 0; j < 6 && fast_ok; ++j) {
+    const int cols = (j == 2 || j == 3) ? W - 1 : W, rows = (j == 4 || j == 5) ? H - 1 : H;
+    const bool is_var = (j & 1) == 1;
+    if (dtype == DF_F32)
+      fast_ok = plane_ok(static_cast<const uint32_t *>(cnn[j]), W, rows, cols, is_var, 0x7f800000u);
+    else
+      fast_ok = plane_ok(static_cast<const uint16_t *>(cnn[j]), W, rows, cols, is_var,
+                         dtype == DF_BF16 ? 0x7f80u : 0x7c00u);
+  }
+  if (fast_ok) return true;
   for (int v = 0; v < H; ++v) {
     for (int u = 0; u < W; ++u) {
       const size_t i = (size_t)v * W + u;

@@ -56,15 +56,22 @@ struct ResSeg {
 enum HaloKind : int { HK_NONE = 0, HK_X, HK_INIT, HK_ITER };
 
 // Shared-memory arrays of one band (stride BS floats each): x, r, p, s, w,
-// 1/diag, wx, wy, u; then the halo arrays (W floats each): HA[0..3] the row
-// above the band, HA[4..7] the row below, WYT the y-coupling of the row above.
+// 1/diag, wx, wy, u; when the plan stages the inputs, IN[0..7] = mu_n,
+// var_n, gx, var_gx, gy, var_gy, mu_s, var_s of the band (as f32). Then the
+// halo arrays (W floats each): HA[0..3] the row above the band, HA[4..7] the
+// row below, WYT the y-coupling of the row above, and with staged inputs
+// GYT / VYT, gy and var_gy of the row above.
+constexpr int kIn = 8;  // staged input planes
+enum : int { I_MN = 0, I_VN, I_GX, I_VX, I_GY, I_VY, I_MS, I_VS };
+
 struct Smem {
   float *X, *R, *P, *S, *Wv, *ID, *WX, *WY, *U;
+  float *IN[kIn];
   float *HA[8];
-  float *WYT;
+  float *WYT, *GYT, *VYT;
 };
 
-__device__ __forceinline__ Smem smem_of(float *base, int stride, int W) {
+__device__ __forceinline__ Smem smem_of(float *base, int stride, int W, bool in_smem) {
   Smem m;
   float *p = base;
   m.X = p; p += stride;
@@ -76,8 +83,15 @@ __device__ __forceinline__ Smem smem_of(float *base, int stride, int W) {
   m.WX = p; p += stride;
   m.WY = p; p += stride;
   m.U = p; p += stride;
+  for (int j = 0; j < kIn; ++j) {
+    m.IN[j] = in_smem ? p : nullptr;
+    if (in_smem) p += stride;
+  }
   for (int j = 0; j < 8; ++j) { m.HA[j] = p; p += W; }
-  m.WYT = p;
+  m.WYT = p; p += W;
+  m.GYT = in_smem ? p : nullptr;
+  if (in_smem) p += W;
+  m.VYT = in_smem ? p : nullptr;
   return m;
 }
 
@@ -103,30 +117,63 @@ struct Walk {
   }
 };
 
+// Walks the band two pixels per step: eval(q, u, v, out) only loads from
+// shared memory, commit(q, out) stores, so the two pixels' load and
+// arithmetic chains overlap (a store between them would order every later
+// shared-memory load after it). Per thread the pixels are committed in walk
+// order, so every per-thread partial sum is added in the same order as a
+// one-pixel walk.
+template <class T, class Eval, class Commit>
+__device__ __forceinline__ void walk_pairs(int W, int bp, Eval &&eval, Commit &&commit) {
+  Walk it(W);
+  for (; it.q + kRThreads < bp;) {
+    const int qa = it.q, ua = it.u, va = it.v;
+    it.next();
+    const int qb = it.q, ub = it.u, vb = it.v;
+    it.next();
+    T a, b;
+    eval(qa, ua, va, a);
+    eval(qb, ub, vb, b);
+    commit(qa, a);
+    commit(qb, b);
+  }
+  if (it.q < bp) {
+    T a;
+    eval(it.q, it.u, it.v, a);
+    commit(it.q, a);
+  }
+}
+
 // w = A u = r - N u for the band (A = diag - N; u = r / diag exactly, so
 // diag * u is r). Halo u: HA[0] above, HA[4] below; y-coupling of the row
 // above the band in WYT. Accumulates (r, u), (w, u), (r, r).
 __device__ __forceinline__ void apply_band(const Smem &m, int W, int nr, int bp, bool has_below,
                                            float acc[kRQ]) {
-  for (Walk it(W); it.q < bp; it.next()) {
-    const int q = it.q, u = it.u, v = it.v;
-    const float uq = m.U[q];
-    float nu = 0.0f;
-    if (u < W - 1) nu += m.WX[q] * m.U[q + 1];
-    if (u > 0) nu += m.WX[q - 1] * m.U[q - 1];
-    if (v < nr - 1) {
-      nu += m.WY[q] * m.U[q + W];
-    } else if (has_below) {
-      nu += m.WY[q] * m.HA[4][u];
-    }
-    nu += (v > 0) ? m.WY[q - W] * m.U[q - W] : m.WYT[u] * m.HA[0][u];
-    const float r = m.R[q];
-    const float w = r - nu;
-    m.Wv[q] = w;
-    acc[0] += r * uq;
-    acc[1] += w * uq;
-    acc[2] += r * r;
-  }
+  struct Px {
+    float r, uq, w;
+  };
+  walk_pairs<Px>(
+      W, bp,
+      [&](int q, int u, int v, Px &o) {
+        o.uq = m.U[q];
+        float nu = 0.0f;
+        if (u < W - 1) nu += m.WX[q] * m.U[q + 1];
+        if (u > 0) nu += m.WX[q - 1] * m.U[q - 1];
+        if (v < nr - 1) {
+          nu += m.WY[q] * m.U[q + W];
+        } else if (has_below) {
+          nu += m.WY[q] * m.HA[4][u];
+        }
+        nu += (v > 0) ? m.WY[q - W] * m.U[q - W] : m.WYT[u] * m.HA[0][u];
+        o.r = m.R[q];
+        o.w = o.r - nu;
+      },
+      [&](int q, const Px &o) {
+        m.Wv[q] = o.w;
+        acc[0] += o.r * o.uq;
+        acc[1] += o.w * o.uq;
+        acc[2] += o.r * o.r;
+      });
 }
 
 // Joint (x, t) variant of apply_band: w = A u - ws u_t with u = r / diag
@@ -166,10 +213,47 @@ __device__ __forceinline__ void publish_edges(const float *src, float *dst, int 
   }
 }
 
+// Input plane j (I_MN .. I_VS) at band pixel q / global index gi: from the
+// band's staged copy (SM) or from the keyframe's planes.
+template <bool SM, int DT>
+__device__ __forceinline__ float band_in(const Smem &m, const Planes &k, int j, int q, size_t gi) {
+  if constexpr (SM) {
+    return m.IN[j][q];
+  } else {
+    if (j == I_MS) return __ldg(k.mu_s + gi);
+    if (j == I_VS) return __ldg(k.var_s + gi);
+    return ld_cnn<DT>(k.cnn[j], gi);
+  }
+}
+
+// Copy the band's input planes (and gy, var_gy of the row above) into shared
+// memory, as f32; they are constant for the whole launch.
+template <int DT>
+__device__ void stage_inputs(const Smem &m, const Planes &k, int rb, int bp, bool has_above) {
+  const int W = k.W;
+  const size_t P = k.P;
+  for (Walk it(W); it.q < bp; it.next()) {
+    const size_t gi = (size_t)(rb + it.v) * P + it.u;
+    float v[kIn];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) v[j] = ld_cnn<DT>(k.cnn[j], gi);
+    v[I_MS] = __ldg(k.mu_s + gi);
+    v[I_VS] = __ldg(k.var_s + gi);
+#pragma unroll
+    for (int j = 0; j < kIn; ++j) m.IN[j][it.q] = v[j];
+  }
+  for (int u = threadIdx.x; u < W; u += kRThreads) {
+    const size_t gi = (size_t)(rb - 1) * P + u;
+    m.GYT[u] = has_above ? ld_cnn<DT>(k.cnn[I_GY], gi) : 0.0f;
+    m.VYT[u] = has_above ? ld_cnn<DT>(k.cnn[I_VY], gi) : 1.0f;
+  }
+}
+
 // JOINT: also keep ws in the U array and sum the border's S = sum ws and
 // r_t = sum ws (x - t - mu_s) into acc[2], acc[3] (b.b is not formed: the
-// joint solve runs with a fixed iteration count here).
-template <int DT, bool JOINT, int LK>
+// joint solve runs with a fixed iteration count here). SM: the inputs are
+// staged in shared memory (DT is then unused).
+template <int DT, bool JOINT, int LK, bool SM>
 __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, float t,
                               const SolveCfg &c, float acc[kRQ]) {
   const int W = k.W, H = k.H, bp = nr * W;
@@ -177,6 +261,7 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
   const bool semi = c.terms & DF_TERM_SEMI, net = c.terms & DF_TERM_NET,
              grad = c.terms & DF_TERM_GRAD;
   const bool has_above = rb > 0;
+  auto in = [&](int j, int q, size_t gi) { return band_in<SM, DT>(m, k, j, q, gi); };
   // x of the rows above / below the band is in HA[0] / HA[4] (prefetched)
   // step A: the band's own x- and y-terms, and the y-term above the band
   for (Walk it(W); it.q < bp; it.next()) {
@@ -185,13 +270,13 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     const float xq = m.X[q];
     float wx = 0.0f, ex = 0.0f, wy = 0.0f, ey = 0.0f;
     if (grad && u < W - 1) {
-      ex = m.X[q + 1] - xq - ld_cnn<DT>(k.cnn[2], gi);
-      wx = robust_weight_k<LK>(ex, ld_cnn<DT>(k.cnn[3], gi), c.delta);
+      ex = m.X[q + 1] - xq - in(I_GX, q, gi);
+      wx = robust_weight_k<LK>(ex, in(I_VX, q, gi), c.delta);
     }
     if (grad && rb + v < H - 1) {
       const float xs = (v < nr - 1) ? m.X[q + W] : m.HA[4][u];
-      ey = xs - xq - ld_cnn<DT>(k.cnn[4], gi);
-      wy = robust_weight_k<LK>(ey, ld_cnn<DT>(k.cnn[5], gi), c.delta);
+      ey = xs - xq - in(I_GY, q, gi);
+      wy = robust_weight_k<LK>(ey, in(I_VY, q, gi), c.delta);
     }
     m.WX[q] = wx;
     m.WY[q] = wy;
@@ -202,9 +287,16 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     float wy = 0.0f, ey = 0.0f, gy = 0.0f;
     if (grad && has_above) {
       const size_t gi = (size_t)(rb - 1) * P + u;
-      gy = ld_cnn<DT>(k.cnn[4], gi);
+      float vy;
+      if constexpr (SM) {
+        gy = m.GYT[u];
+        vy = m.VYT[u];
+      } else {
+        gy = ld_cnn<DT>(k.cnn[I_GY], gi);
+        vy = ld_cnn<DT>(k.cnn[I_VY], gi);
+      }
       ey = m.X[u] - m.HA[0][u] - gy;
-      wy = robust_weight_k<LK>(ey, ld_cnn<DT>(k.cnn[5], gi), c.delta);
+      wy = robust_weight_k<LK>(ey, vy, c.delta);
     }
     m.WYT[u] = wy;
     m.HA[1][u] = ey;
@@ -218,7 +310,7 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     const float xq = m.X[q];
     float ws = 0.0f, rs = 0.0f, bs = 0.0f;
     if (semi) {
-      const float ms = __ldg(k.mu_s + gi), vs = __ldg(k.var_s + gi);
+      const float ms = in(I_MS, q, gi), vs = in(I_VS, q, gi);
       if (semi_valid(ms, vs)) {
         ws = robust_weight_k<LK>(xq - t - ms, vs, c.delta);
         rs = ws * (t + ms - xq);
@@ -227,8 +319,8 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     }
     float wn = 0.0f, mn = 0.0f;
     if (net) {
-      mn = ld_cnn<DT>(k.cnn[0], gi);
-      wn = robust_weight_k<LK>(xq - mn, ld_cnn<DT>(k.cnn[1], gi), c.delta);
+      mn = in(I_MN, q, gi);
+      wn = robust_weight_k<LK>(xq - mn, in(I_VN, q, gi), c.delta);
     }
     const float wx = m.WX[q], ex = m.P[q], wy = m.WY[q], ey = m.S[q];
     const float wxl = u > 0 ? m.WX[q - 1] : 0.0f, exl = u > 0 ? m.P[q - 1] : 0.0f;
@@ -245,10 +337,10 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
       acc[2] += ws;
       acc[3] -= rs;  // ws (x - t - mu_s)
     } else if (c.tol > 0.0) {
-      const float gx = (grad && u < W - 1) ? ld_cnn<DT>(k.cnn[2], gi) : 0.0f;
-      const float gxl = (grad && u > 0) ? ld_cnn<DT>(k.cnn[2], gi - 1) : 0.0f;
-      const float gy = (grad && rb + v < H - 1) ? ld_cnn<DT>(k.cnn[4], gi) : 0.0f;
-      const float gyu = v > 0 ? ((grad) ? ld_cnn<DT>(k.cnn[4], gi - P) : 0.0f) : m.HA[2][u];
+      const float gx = (grad && u < W - 1) ? in(I_GX, q, gi) : 0.0f;
+      const float gxl = (grad && u > 0) ? in(I_GX, q - 1, gi - 1) : 0.0f;
+      const float gy = (grad && rb + v < H - 1) ? in(I_GY, q, gi) : 0.0f;
+      const float gyu = v > 0 ? ((grad) ? in(I_GY, q - W, gi - P) : 0.0f) : m.HA[2][u];
       const float b = bs + wn * mn - wx * gx + wxl * gxl - wy * gy + wyu * gyu;
       acc[2] += b * b;
     }
@@ -298,7 +390,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
   const size_t P = k.P;
   const int rb = me.rb, nr = me.re - me.rb, bp = nr * W;
   const bool has_above = rb > 0, has_below = me.re < H;
-  const Smem m = smem_of(reinterpret_cast<float *>(dyn_smem), h->th, W);
+  const bool in_sm = h->in_smem != 0;
+  const Smem m = smem_of(reinterpret_cast<float *>(dyn_smem), h->th, W, in_sm);
   float *Rg[2] = {k.v[1], k.v[2]}, *Sg[2] = {k.v[3], k.v[4]}, *Wg[2] = {k.v[5], k.v[6]};
   float *IDg = k.diag;  // the fused kernels keep 1/diag in the diag plane
   const bool active = s_seg.active != 0;
@@ -308,6 +401,14 @@ __global__ void __launch_bounds__(kRThreads, 1)
   bool alive = true;
 
   for (Walk it(W); it.q < bp; it.next()) m.X[it.q] = __ldcg(k.x + (size_t)(rb + it.v) * P + it.u);
+  if (in_sm && active) {
+    if (k.dtype == DF_BF16)
+      stage_inputs<DF_BF16>(m, k, rb, bp, has_above);
+    else if (k.dtype == DF_F16)
+      stage_inputs<DF_F16>(m, k, rb, bp, has_above);
+    else
+      stage_inputs<DF_F32>(m, k, rb, bp, has_above);
+  }
 
   // Load the halo rows the next pass needs (raw values; the new u of the
   // rows above / below needs this pass's alpha, beta and is formed there).
@@ -395,7 +496,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
   auto scale_partials = [&](float acc[kRQ], int q0, float t) {
     for (Walk it(W); it.q < bp; it.next()) {
       const size_t gi = (size_t)(rb + it.v) * P + it.u;
-      const float ms = __ldg(k.mu_s + gi), vs = __ldg(k.var_s + gi);
+      const float ms = in_sm ? m.IN[I_MS][it.q] : __ldg(k.mu_s + gi);
+      const float vs = in_sm ? m.IN[I_VS][it.q] : __ldg(k.var_s + gi);
       if (semi_valid(ms, vs)) {
         const float xq = m.X[it.q];
         const float w = robust_weight_k<LK>(xq - t - ms, vs, c.delta);
@@ -430,21 +532,14 @@ __global__ void __launch_bounds__(kRThreads, 1)
       float acc[kRQ] = {};
       if (active) {
         const float t = (float)s_seg.t;
-        if constexpr (JOINT) {
-          if (k.dtype == DF_BF16)
-            assemble_band<DF_BF16, true, LK>(m, k, rb, nr, t, c, acc);
-          else if (k.dtype == DF_F16)
-            assemble_band<DF_F16, true, LK>(m, k, rb, nr, t, c, acc);
-          else
-            assemble_band<DF_F32, true, LK>(m, k, rb, nr, t, c, acc);
-        } else {
-          if (k.dtype == DF_BF16)
-            assemble_band<DF_BF16, false, LK>(m, k, rb, nr, t, c, acc);
-          else if (k.dtype == DF_F16)
-            assemble_band<DF_F16, false, LK>(m, k, rb, nr, t, c, acc);
-          else
-            assemble_band<DF_F32, false, LK>(m, k, rb, nr, t, c, acc);
-        }
+        if (in_sm)
+          assemble_band<DF_F32, JOINT, LK, true>(m, k, rb, nr, t, c, acc);
+        else if (k.dtype == DF_BF16)
+          assemble_band<DF_BF16, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
+        else if (k.dtype == DF_F16)
+          assemble_band<DF_F16, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
+        else
+          assemble_band<DF_F32, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
         __syncthreads();
         publish_edges(m.R, Rg[0], W, nr, rb, P);
         publish_edges(m.ID, IDg, W, nr, rb, P);
@@ -494,7 +589,9 @@ __global__ void __launch_bounds__(kRThreads, 1)
           __syncthreads();
           apply_band_joint(m, W, nr, bp, has_below, (float)s_seg.jut, acc);
         } else {
-          for (Walk it(W); it.q < bp; it.next()) m.U[it.q] = m.R[it.q] * m.ID[it.q];
+          walk_pairs<float>(
+              W, bp, [&](int q, int, int, float &o) { o = m.R[q] * m.ID[q]; },
+              [&](int q, float o) { m.U[q] = o; });
           __syncthreads();
           apply_band(m, W, nr, bp, has_below, acc);
         }
@@ -549,15 +646,22 @@ __global__ void __launch_bounds__(kRThreads, 1)
       if (it == n_pcg - 1) {  // FINAL
         const bool fs = do_scale && gn + 1 < n_gn;
         if (run) {
-          for (Walk w(W); w.q < bp; w.next()) {
-            const int q = w.q;
-            const float id = m.ID[q], r = m.R[q];
-            const float p = first ? r * id : r * id + fb * m.P[q];
-            m.X[q] += fa * p;
-            const float si = first ? m.Wv[q] : m.Wv[q] + fb * m.S[q];
-            const float rn = r - fa * si;
-            acc[0] += rn * rn;
-          }
+          struct Fin {
+            float x, rn;
+          };
+          walk_pairs<Fin>(
+              W, bp,
+              [&](int q, int, int, Fin &o) {
+                const float id = m.ID[q], r = m.R[q];
+                const float p = first ? r * id : r * id + fb * m.P[q];
+                o.x = m.X[q] + fa * p;
+                const float si = first ? m.Wv[q] : m.Wv[q] + fb * m.S[q];
+                o.rn = r - fa * si;
+              },
+              [&](int q, const Fin &o) {
+                m.X[q] = o.x;
+                acc[0] += o.rn * o.rn;
+              });
         }
         if (active) {
           // x may also have moved in earlier passes of a depth step that
@@ -598,18 +702,26 @@ __global__ void __launch_bounds__(kRThreads, 1)
             const float sb = first ? m.HA[6][u] : m.HA[6][u] + fb * m.HA[5][u];
             m.HA[4][u] = (m.HA[4][u] - fa * sb) * m.HA[7][u];
           }
-          for (Walk w(W); w.q < bp; w.next()) {
-            const int q = w.q;
-            const float id = m.ID[q], r = m.R[q];
-            const float p = first ? r * id : r * id + fb * m.P[q];
-            m.X[q] += fa * p;
-            m.P[q] = p;
-            const float si = first ? m.Wv[q] : m.Wv[q] + fb * m.S[q];
-            m.S[q] = si;
-            const float rn = r - fa * si;
-            m.R[q] = rn;
-            if (!joint) m.U[q] = rn * id;
-          }
+          struct Upd {
+            float x, p, s, r, id;
+          };
+          walk_pairs<Upd>(
+              W, bp,
+              [&](int q, int, int, Upd &o) {
+                o.id = m.ID[q];
+                const float r = m.R[q];
+                o.p = first ? r * o.id : r * o.id + fb * m.P[q];
+                o.x = m.X[q] + fa * o.p;
+                o.s = first ? m.Wv[q] : m.Wv[q] + fb * m.S[q];
+                o.r = r - fa * o.s;
+              },
+              [&](int q, const Upd &o) {
+                m.X[q] = o.x;
+                m.P[q] = o.p;
+                m.S[q] = o.s;
+                m.R[q] = o.r;
+                if (!joint) m.U[q] = o.r * o.id;
+              });
           __syncthreads();
           if constexpr (JOINT)
             apply_band_joint(m, W, nr, bp, has_below, (float)s_seg.jut, acc);
@@ -751,10 +863,24 @@ size_t resident_plan_bytes(int nkf, int G) {
 
 int resident_max_ctas() { return rdev().sms; }
 
+// The plan with or without the input planes staged in shared memory; false
+// if the keyframes' bands do not fit the CTAs / shared memory that way.
+static bool resident_build_plan_with(const Planes *const *kfs, int n, const FusedTuning &tune,
+                                     bool in_smem, std::vector<char> &out, LaunchShape &shape);
+
 bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
                          std::vector<char> &out, LaunchShape &shape) {
+  // the input planes stay in shared memory for the launch where the bands
+  // still fit with them; otherwise the assembly reads them from L2 / HBM
+  return resident_build_plan_with(kfs, n, tune, true, out, shape) ||
+         resident_build_plan_with(kfs, n, tune, false, out, shape);
+}
+
+static bool resident_build_plan_with(const Planes *const *kfs, int n, const FusedTuning &tune,
+                                     bool in_smem, std::vector<char> &out, LaunchShape &shape) {
   const ResDev &d = rdev();
   if (n < 1 || d.sms <= 0 || d.smem_optin <= 0) return false;
+  const long long arrays = in_smem ? 9 + kIn : 9, halo = in_smem ? kHalo + 2 : kHalo;
   int G_cap = d.sms;
   if (tune.max_ctas > 0) G_cap = std::min(G_cap, tune.max_ctas);
   const long long avail = (long long)d.smem_optin - d.static_smem - 1024;
@@ -769,7 +895,7 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
   long long need = 0;
   for (int k = 0; k < n; ++k) {
     const long long Wk = kfs[k]->W;
-    const long long rows = (avail / 4 - (long long)kHalo * Wmax) / (9 * Wk);
+    const long long rows = (avail / 4 - halo * Wmax) / (arrays * Wk);
     if (rows < 1) return false;
     maxrows[k] = (int)std::min<long long>(rows, kfs[k]->H);
     nb[k] = (kfs[k]->H + maxrows[k] - 1) / maxrows[k];
@@ -821,7 +947,7 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
     }
   }
   const int stride = (band_px_max + 3) & ~3;
-  const long long smem = (long long)(9LL * stride + (long long)kHalo * Wmax) * 4;
+  const long long smem = (arrays * stride + halo * Wmax) * 4;
   if (smem > avail) return false;
   const size_t inbox = inbox_total(nb);
   out.assign(resident_bytes(n, G, inbox), 0);
@@ -842,6 +968,7 @@ bool resident_build_plan(const Planes *const *kfs, int n, const FusedTuning &tun
   hd->slot_stride = (long long)inbox;
   hd->th = stride;  // shared-memory stride of one band array
   hd->smem_bytes = (int)smem;
+  hd->in_smem = in_smem ? 1 : 0;
   hd->bytes = (long long)out.size();
   memcpy(base + hd->off_cta_work, ctas.data(), sizeof(ResCta) * G);
   memcpy(base + hd->off_kf, rk.data(), sizeof(ResKf) * n);

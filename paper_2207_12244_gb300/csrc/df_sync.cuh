@@ -23,7 +23,8 @@ struct PlanHeader {
   long long off_cta_work, off_cta_kf, off_cta_slot, off_kf, off_slots;
   long long bytes;
   int smem_bytes;  // dynamic shared memory per CTA (resident plans)
-  int pad1;
+  int in_smem;     // resident plans: 1 = each band's input planes are staged
+                   // in shared memory for the whole launch
   long long slot_stride;  // doubles per parity of the reduction slots / inboxes
 };
 

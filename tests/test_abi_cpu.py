@@ -96,3 +96,52 @@ def test_null_keyframe_and_bad_params(lib):
     assert lib.df_optimise_batch(None, 3, None, None, None) == dfl.DF_EINVAL
     assert lib.df_semi_to_log(None, None, None, None, -1, 0, None) == dfl.DF_EINVAL
     assert lib.df_semi_to_log(None, None, None, None, 0, 0, None) == dfl.DF_OK
+
+
+def _codes(a, dtype):
+    """float32 values as the element bits the library reads for each dtype."""
+    a = np.asarray(a, np.float32)
+    if dtype == dfl.DF_F32:
+        return a
+    if dtype == dfl.DF_F16:
+        return a.astype(np.float16)
+    return (a.view(np.uint32) >> 16).astype(np.uint16)  # bf16: upper half (exact here)
+
+
+@pytest.mark.parametrize("dtype", [dfl.DF_F32, dfl.DF_BF16, dfl.DF_F16], ids=["f32", "bf16", "f16"])
+def test_host_validation_matches_the_rule(lib, dtype):
+    """The host check accepts exactly the planes whose means are finite and
+    whose variances are finite and > 0, ignoring gx / var_gx in the last
+    column and gy / var_gy in the last row; a rejection names the plane and
+    the pixel."""
+    W, H = 37, 11
+    rng = np.random.default_rng(5)
+    specials = [np.nan, np.inf, -np.inf, 0.0, -0.0, -2.0, 2.0 ** -130, 3.0]
+    names = ["mu_net", "var_net", "gx", "var_gx", "gy", "var_gy"]
+    base = [np.full((H, W), 0.5 if j % 2 == 0 else 1.5, np.float32) for j in range(6)]
+    n_reject = 0
+    for j in range(6):
+        for val in specials:
+            for (v, u) in [(int(rng.integers(H)), int(rng.integers(W))), (H - 1, W - 1),
+                           (0, W - 1), (H - 1, 0)]:
+                planes = [b.copy() for b in base]
+                planes[j][v, u] = val
+                fv = float(_codes(np.float32(val), dtype).astype(np.float32)) \
+                    if dtype != dfl.DF_BF16 else float(np.float32(val))
+                ignored = (j in (2, 3) and u == W - 1) or (j in (4, 5) and v == H - 1)
+                ok_val = np.isfinite(fv) and (j % 2 == 0 or fv > 0.0)
+                expect_reject = not ok_val and not ignored
+                desc = dfl.df_keyframe_desc(W, H, dtype)
+                out = C.c_void_p()
+                codes = [np.ascontiguousarray(_codes(p, dtype)) for p in planes]
+                st = lib.df_keyframe_create(C.byref(desc), *[c.ctypes.data for c in codes], 0,
+                                            None, C.byref(out))
+                if st == dfl.DF_OK:
+                    lib.df_keyframe_destroy(out)
+                msg = dfl.df_last_error()
+                rejected = st == dfl.DF_EINVAL and "invalid network input" in msg
+                assert rejected == expect_reject, (names[j], val, v, u, st, msg)
+                if rejected:
+                    n_reject += 1
+                    assert f"{names[j]} at (u={u}, v={v})" in msg, msg
+    assert n_reject > 50
