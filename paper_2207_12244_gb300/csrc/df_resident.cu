@@ -46,8 +46,9 @@ struct ResCta {
 struct ResSeg {
   double t, bb, rr;
   ff2 gam, alpha, beta;  // CG scalars (double-float)
-  // joint (x, t) solve: the border components of the CG vectors
-  double jS, jrt, jut, jwt, jpt, jst;
+  // joint (x, t) solve: the border components of the CG vectors and the
+  // change of t during the current depth step (folded into t at its end)
+  ff2 jS, jrt, jut, jwt, jpt, jst, jdt;
   int stop, iters, active, pad;
 };
 
@@ -377,6 +378,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
     const Scalars *sc = s_kf.pl.sc;
     s_seg.t = sc->t;
     s_seg.gam = s_seg.alpha = s_seg.beta = ff2{0.0f, 0.0f};
+    s_seg.jS = s_seg.jrt = s_seg.jut = s_seg.jwt = s_seg.jpt = s_seg.jst = s_seg.jdt =
+        ff2{0.0f, 0.0f};
     s_seg.bb = 0.0;
     s_seg.rr = sc->rr;
     s_seg.stop = 0;
@@ -512,6 +515,18 @@ __global__ void __launch_bounds__(kRThreads, 1)
     __syncthreads();
   };
 
+  // The border of the joint solve moves with the iteration's alpha, beta
+  // (thread 0, right after they are formed): p_t = u_t + beta p_t,
+  // s_t = w_t + beta s_t, t += alpha p_t, r_t -= alpha s_t, u_t = r_t / S.
+  auto joint_border_step = [&](bool first_it) {
+    const ff2 a = s_seg.alpha;
+    s_seg.jpt = first_it ? s_seg.jut : ff_add(s_seg.jut, ff_mul(s_seg.beta, s_seg.jpt));
+    s_seg.jst = first_it ? s_seg.jwt : ff_add(s_seg.jwt, ff_mul(s_seg.beta, s_seg.jst));
+    s_seg.jdt = ff_add(s_seg.jdt, ff_mul(a, s_seg.jpt));
+    s_seg.jrt = ff_sub(s_seg.jrt, ff_mul(a, s_seg.jst));
+    s_seg.jut = s_seg.jS.hi > 0.0f ? ff_div(s_seg.jrt, s_seg.jS) : ff2{0.0f, 0.0f};
+  };
+
   // the first pass is either the scale step or the assembly; both need the
   // x halo, which is current in global memory at launch
   prefetch_halo(HK_X, 0, 0);
@@ -557,13 +572,14 @@ __global__ void __launch_bounds__(kRThreads, 1)
       if (tid == 0) {
         if constexpr (JOINT) {
           // border of the bordered system: S = sum ws, r_t, u_t = r_t / S
-          const double S = ff_to_double(s_tot[2]), rt = ff_to_double(s_tot[3]);
-          const double ut = S > 0.0 ? rt / S : 0.0;
+          const ff2 S = s_tot[2], rt = s_tot[3];
+          const ff2 ut = S.hi > 0.0f ? ff_div(rt, S) : ff2{0.0f, 0.0f};
           s_seg.jS = S;
           s_seg.jrt = rt;
           s_seg.jut = ut;
-          s_seg.gam = ff_from_double(ff_to_double(s_tot[0]) + rt * ut);
-          s_seg.rr = ff_to_double(s_tot[1]) + rt * rt;
+          s_seg.jdt = ff2{0.0f, 0.0f};
+          s_seg.gam = ff_add(s_tot[0], ff_mul(rt, ut));
+          s_seg.rr = ff_to_double(ff_add(s_tot[1], ff_mul(rt, rt)));
           s_seg.stop = 0;
         } else {
           s_seg.gam = s_tot[0];
@@ -587,7 +603,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
         }
         if constexpr (JOINT) {
           __syncthreads();
-          apply_band_joint(m, W, nr, bp, has_below, (float)s_seg.jut, acc);
+          apply_band_joint(m, W, nr, bp, has_below, s_seg.jut.hi, acc);
         } else {
           walk_pairs<float>(
               W, bp, [&](int q, int, int, float &o) { o = m.R[q] * m.ID[q]; },
@@ -610,14 +626,15 @@ __global__ void __launch_bounds__(kRThreads, 1)
       if (tid == 0 && !s_seg.stop) {
         ff2 dl = s_tot[0];
         if constexpr (JOINT) {  // w_t = S u_t - (ws, u); (w, u) gains w_t u_t
-          s_seg.jwt = s_seg.jS * s_seg.jut - ff_to_double(s_tot[1]);
-          dl = ff_from_double(ff_to_double(dl) + s_seg.jwt * s_seg.jut);
+          s_seg.jwt = ff_sub(ff_mul(s_seg.jS, s_seg.jut), s_tot[1]);
+          dl = ff_add(dl, ff_mul(s_seg.jwt, s_seg.jut));
         }
         if (s_seg.gam.hi == 0.0f || !(dl.hi > 0.0f)) {
           s_seg.stop = 1;
         } else {
           s_seg.alpha = ff_div(s_seg.gam, dl);
           s_seg.beta = ff2{0.0f, 0.0f};
+          if constexpr (JOINT) joint_border_step(true);
         }
       }
       __syncthreads();
@@ -629,20 +646,6 @@ __global__ void __launch_bounds__(kRThreads, 1)
       const bool first = it == 0;
       const bool run = active && !s_seg.stop;
       float acc[kRQ] = {};
-      if constexpr (JOINT) {
-        // the border moves with the same alpha, beta: p_t = u_t + beta p_t,
-        // s_t = w_t + beta s_t, t += alpha p_t, r_t -= alpha s_t
-        __syncthreads();
-        if (tid == 0 && run) {
-          const double a = ff_to_double(s_seg.alpha), b = first ? 0.0 : ff_to_double(s_seg.beta);
-          s_seg.jpt = s_seg.jut + b * s_seg.jpt;
-          s_seg.jst = s_seg.jwt + b * s_seg.jst;
-          s_seg.t += a * s_seg.jpt;
-          s_seg.jrt -= a * s_seg.jst;
-          s_seg.jut = s_seg.jS > 0.0 ? s_seg.jrt / s_seg.jS : 0.0;
-        }
-        __syncthreads();
-      }
       if (it == n_pcg - 1) {  // FINAL
         const bool fs = do_scale && gn + 1 < n_gn;
         if (run) {
@@ -680,10 +683,17 @@ __global__ void __launch_bounds__(kRThreads, 1)
         else
           alive = end_pass(IC<1>{}, acc, HK_X, 0);
         if (!alive) break;
-        if (tid == 0 && run) {
-          s_seg.iters += 1;
-          if (need_rr || !fs)
-            s_seg.rr = ff_to_double(s_tot[0]) + (joint ? s_seg.jrt * s_seg.jrt : 0.0);
+        if (tid == 0) {
+          if constexpr (JOINT) {  // the depth step's change of t
+            s_seg.t += ff_to_double(s_seg.jdt);
+            s_seg.jdt = ff2{0.0f, 0.0f};
+          }
+          if (run) {
+            s_seg.iters += 1;
+            if (need_rr || !fs)
+              s_seg.rr = ff_to_double(joint ? ff_add(s_tot[0], ff_mul(s_seg.jrt, s_seg.jrt))
+                                            : s_tot[0]);
+          }
         }
         __syncthreads();
         if (fs) {
@@ -724,7 +734,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
               });
           __syncthreads();
           if constexpr (JOINT)
-            apply_band_joint(m, W, nr, bp, has_below, (float)s_seg.jut, acc);
+            apply_band_joint(m, W, nr, bp, has_below, s_seg.jut.hi, acc);
           else
             apply_band(m, W, nr, bp, has_below, acc);
           __syncthreads();
@@ -747,9 +757,9 @@ __global__ void __launch_bounds__(kRThreads, 1)
           s_seg.iters += 1;
           ff2 gn_ = s_tot[0], dl = s_tot[1];
           if constexpr (JOINT) {  // border terms of (r, u) and (w, u)
-            s_seg.jwt = s_seg.jS * s_seg.jut - ff_to_double(s_tot[2]);
-            gn_ = ff_from_double(ff_to_double(gn_) + s_seg.jrt * s_seg.jut);
-            dl = ff_from_double(ff_to_double(dl) + s_seg.jwt * s_seg.jut);
+            s_seg.jwt = ff_sub(ff_mul(s_seg.jS, s_seg.jut), s_tot[2]);
+            gn_ = ff_add(gn_, ff_mul(s_seg.jrt, s_seg.jut));
+            dl = ff_add(dl, ff_mul(s_seg.jwt, s_seg.jut));
           } else if (c.tol > 0.0) {
             s_seg.rr = ff_to_double(s_tot[2]);
           }
@@ -765,6 +775,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
               s_seg.beta = beta;
               s_seg.alpha = ff_div(gn_, denom);
               s_seg.gam = gn_;
+              if constexpr (JOINT) joint_border_step(false);
             }
           }
         }
