@@ -1,4 +1,6 @@
 import os
+
+import pytest
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -11,3 +13,12 @@ if HERE not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _library_built():
+    """Build the CUDA library once per session (a no-op when the in-tree build
+    is current), so that any subset of the tests can run first."""
+    from paper_2207_12244_gb300 import _build
+
+    _build.build()
