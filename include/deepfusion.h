@@ -424,7 +424,8 @@ df_status df_server_fetch_depth(df_server *srv, int32_t stream_id, float *out, i
  * device looks the array's device address up (cudaGetSymbolAddress); make
  * that first call before any stream capture. Asynchronous on 'stream'.
  * Errors: DF_EINVAL (sizes above the limit, NULL pointers, parameters),
- * DF_ECUDA. */
+ * DF_ENOTSUP (the joint (x, t) variant, whose extra scratch plane the array
+ * does not hold; a device index beyond 63), DF_ECUDA. */
 df_status df_optimise_noalloc(int32_t width, int32_t height, const float *mu_net,
                               const float *var_net, const float *gx, const float *var_gx,
                               const float *gy, const float *var_gy, const float *mu_semi,
