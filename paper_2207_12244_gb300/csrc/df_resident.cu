@@ -733,13 +733,16 @@ __global__ void __launch_bounds__(kRThreads, 1)
                 if (!joint) m.U[q] = o.r * o.id;
               });
           __syncthreads();
+          // r and s of the band's edge rows are final: their stores drain
+          // while the stencil runs (the next pass reads them after the
+          // barrier; this pass reads only the other parity's planes)
+          publish_edges(m.R, Rg[nb], W, nr, rb, P);
+          publish_edges(m.S, Sg[nb], W, nr, rb, P);
           if constexpr (JOINT)
             apply_band_joint(m, W, nr, bp, has_below, s_seg.jut.hi, acc);
           else
             apply_band(m, W, nr, bp, has_below, acc);
           __syncthreads();
-          publish_edges(m.R, Rg[nb], W, nr, rb, P);
-          publish_edges(m.S, Sg[nb], W, nr, rb, P);
           publish_edges(m.Wv, Wg[nb], W, nr, rb, P);
         }
         const int next_kind = (it + 1 < n_pcg - 1) ? HK_ITER : HK_NONE;
