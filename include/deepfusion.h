@@ -147,6 +147,12 @@ df_status df_keyframe_reset(df_keyframe *kf, const void *mu_net, const void *var
  * II-B: updated with every new frame, already in log space):
  *   mu_semi = ln d_semi (Eq. 6b), var_semi = R_semi (Eq. 6a), both H x W f32.
  * A pixel without a measurement has var_semi <= 0 or a non-finite value.
+ * Ordered on 'stream' like every call; the buffers are read before the
+ * stream passes the call. Host buffers (ptrs_on_device = 0) are uploaded on
+ * the keyframe's own copy stream into a staging pair of the keyframe, so
+ * that the upload overlaps the work 'stream' runs before the call (the
+ * previous frame's solve); 'stream' then waits for it and moves the planes
+ * into place. Under stream capture the upload goes on 'stream' itself.
  * Errors: DF_EINVAL (null kf/pointers), DF_ECUDA. */
 df_status df_frame_update(df_keyframe *kf, const float *mu_semi, const float *var_semi,
                           int ptrs_on_device, void *stream);

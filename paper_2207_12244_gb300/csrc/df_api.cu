@@ -26,6 +26,12 @@ struct df_keyframe {
   void *mem;
   Planes planes;
   float *staging;   // dense H x W plane for host-side depth reads
+  // host-pointer frame updates: dense H x W mu / var staging planes, filled
+  // on the keyframe's own copy stream so that the upload of a frame overlaps
+  // the solve of the previous one (stream and events made on first use)
+  float *semi_stage;
+  cudaStream_t copy_stream;
+  cudaEvent_t ev_staged, ev_free;
   void *plan;       // resident launch plan of the fused solver (single keyframe)
   size_t plan_cap;  // bytes reserved for it
   df::LaunchShape plan_shape;    // shape of the plan currently on the device (kind -1: none)
@@ -70,8 +76,8 @@ int pitch_of(int W) { return (int)align_up((size_t)W, df::kPitchElems); }
 
 // Byte layout of one keyframe allocation (offsets are 256-B aligned).
 struct Layout {
-  size_t cnn[6], mu_s, var_s, x, diag, wx, wy, v[df::kWorkPlanes], staging, sc, partial, plan,
-      plan_cap, total;
+  size_t cnn[6], mu_s, var_s, x, diag, wx, wy, v[df::kWorkPlanes], staging, semi_stage, sc,
+      partial, plan, plan_cap, total;
 };
 
 Layout layout_of(int W, int H, int dtype) {
@@ -89,6 +95,7 @@ Layout layout_of(int W, int H, int dtype) {
   L.wy = off; off += f32_plane;
   for (int j = 0; j < df::kWorkPlanes; ++j) { L.v[j] = off; off += f32_plane; }
   L.staging = off; off += align_up((size_t)W * H * 4, 256);
+  L.semi_stage = off; off += 2 * align_up((size_t)W * H * 4, 256);
   L.sc = off; off += align_up(sizeof(Scalars), 256);
   L.partial = off; off += align_up(sizeof(double) * df::kMaxPartialBlocks * df::kNumQ, 256);
   L.plan = off;
@@ -413,6 +420,9 @@ df_status df_keyframe_create(const df_keyframe_desc *desc, const void *mu_net,
   k.sc = reinterpret_cast<Scalars *>(base + L.sc);
   k.partial = reinterpret_cast<double *>(base + L.partial);
   kf->staging = reinterpret_cast<float *>(base + L.staging);
+  kf->semi_stage = reinterpret_cast<float *>(base + L.semi_stage);
+  kf->copy_stream = nullptr;
+  kf->ev_staged = kf->ev_free = nullptr;
   kf->plan = L.plan_cap ? base + L.plan : nullptr;
   kf->plan_cap = L.plan_cap;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -450,14 +460,56 @@ df_status df_keyframe_reset(df_keyframe *kf, const void *mu_net, const void *var
   return load_cnn(kf, cnn, ptrs_on_device, s);
 }
 
+// The keyframe's copy stream and its two events, made on first use; false
+// (and no error left pending) if the runtime cannot make them.
+static bool ensure_copy_stream(df_keyframe *kf) {
+  if (kf->copy_stream) return true;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+      cudaEventCreateWithFlags(&a, cudaEventDisableTiming) == cudaSuccess &&
+      cudaEventCreateWithFlags(&b, cudaEventDisableTiming) == cudaSuccess) {
+    kf->copy_stream = cs;
+    kf->ev_staged = a;
+    kf->ev_free = b;
+    return true;
+  }
+  cudaGetLastError();
+  if (b) cudaEventDestroy(b);
+  if (a) cudaEventDestroy(a);
+  if (cs) cudaStreamDestroy(cs);
+  return false;
+}
+
 df_status df_frame_update(df_keyframe *kf, const float *mu_semi, const float *var_semi,
                           int ptrs_on_device, void *stream) {
-  (void)ptrs_on_device;
   if (!kf) return fail(DF_EINVAL, "keyframe is NULL");
   if (!mu_semi || !var_semi) return fail(DF_EINVAL, "semi-dense plane is NULL");
   DeviceGuard g(kf->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t row = (size_t)kf->W * 4, pitch = (size_t)kf->P * 4;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (!ptrs_on_device && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+      cap == cudaStreamCaptureStatusNone && ensure_copy_stream(kf)) {
+    // Upload on the copy stream once the previous update's staging has been
+    // consumed; 's' waits for the upload and moves the planes into place, so
+    // the call is still ordered on 's' and the host buffers are read before
+    // 's' passes it. The upload itself overlaps whatever 's' runs before.
+    const size_t n = (size_t)kf->W * kf->H * 4;
+    float *st_mu = kf->semi_stage;
+    float *st_var = reinterpret_cast<float *>(reinterpret_cast<char *>(st_mu) + align_up(n, 256));
+    DF_CUDA(cudaStreamWaitEvent(kf->copy_stream, kf->ev_free, 0));
+    DF_CUDA(cudaMemcpyAsync(st_mu, mu_semi, n, cudaMemcpyDefault, kf->copy_stream));
+    DF_CUDA(cudaMemcpyAsync(st_var, var_semi, n, cudaMemcpyDefault, kf->copy_stream));
+    DF_CUDA(cudaEventRecord(kf->ev_staged, kf->copy_stream));
+    DF_CUDA(cudaStreamWaitEvent(s, kf->ev_staged, 0));
+    DF_CUDA(cudaMemcpy2DAsync((void *)kf->planes.mu_s, pitch, st_mu, row, row, kf->H,
+                              cudaMemcpyDeviceToDevice, s));
+    DF_CUDA(cudaMemcpy2DAsync((void *)kf->planes.var_s, pitch, st_var, row, row, kf->H,
+                              cudaMemcpyDeviceToDevice, s));
+    DF_CUDA(cudaEventRecord(kf->ev_free, s));
+    return DF_OK;
+  }
   DF_CUDA(cudaMemcpy2DAsync((void *)kf->planes.mu_s, pitch, mu_semi, row, row, kf->H,
                             cudaMemcpyDefault, s));
   DF_CUDA(cudaMemcpy2DAsync((void *)kf->planes.var_s, pitch, var_semi, row, row, kf->H,
@@ -873,6 +925,10 @@ void df_keyframe_destroy(df_keyframe *kf) {
   {
     DeviceGuard g(kf->device);
     drop_batch_plans_if({kf});
+    // released by the runtime once their pending work is done
+    if (kf->ev_staged) cudaEventDestroy(kf->ev_staged);
+    if (kf->ev_free) cudaEventDestroy(kf->ev_free);
+    if (kf->copy_stream) cudaStreamDestroy(kf->copy_stream);
     cudaFree(kf->mem);  // waits for the keyframe's pending work
   }
   g_in_use.fetch_sub(kf->bytes);

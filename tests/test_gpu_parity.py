@@ -135,6 +135,44 @@ def test_host_and_device_pointers_agree(solver):
     assert np.array_equal(xd, xh) and td == th
 
 
+def test_host_frame_updates_overlap_and_agree(solver):
+    """Frame updates from host buffers (pageable arrays and pinned tensors)
+    are uploaded on the keyframe's copy stream while the previous frame is
+    solved; a warm-started sequence issued without any synchronisation
+    between frames gives bitwise the device-pointer result."""
+    torch = torch_cuda()
+    kf, mus, vs = synth.make_sequence(96, 64, 21, n_frames=6)
+    prm = params(n_gn=4, n_pcg=3, solver=solver)
+
+    def run(kind):
+        # every buffer stays alive until the stream has passed its call
+        if kind == "device":
+            src = [(to_dev(m), to_dev(v)) for m, v in zip(mus, vs)]
+        elif kind == "pinned":
+            src = [(torch.from_numpy(m).pin_memory(), torch.from_numpy(v).pin_memory())
+                   for m, v in zip(mus, vs)]
+        else:
+            src = [(np.ascontiguousarray(m), np.ascontiguousarray(v)) for m, v in zip(mus, vs)]
+        k = create(kf)
+        try:
+            outs = []
+            for f in range(len(mus)):
+                k.frame_update(*src[f])
+                k.optimise(prm)
+                out = torch.empty((kf.height, kf.width), dtype=torch.float32, device="cuda")
+                k.fetch_depth(out, log_space=True)
+                outs.append(out)
+            torch.cuda.synchronize()
+            return [o.cpu().numpy() for o in outs], k.get_state()
+        finally:
+            k.close()
+
+    xd, td = run("device")
+    for kind in ("pinned", "pageable"):
+        xh, th = run(kind)
+        assert all(np.array_equal(a, b) for a, b in zip(xd, xh)) and td == th, kind
+
+
 def test_deterministic(solver):
     kf = synth.make_keyframe(200, 150, 14)
     prm = params(n_gn=5, n_pcg=5, solver=solver)
