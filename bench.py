@@ -97,14 +97,42 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and with whitespace runs collapsed (string
+    and character literals kept), so that comment or layout edits do not
+    change the hash of the kernels' code."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def lib_source_hash():
+    """Hash of the CUDA library's code (comments and whitespace excluded):
+    the key under which profiles/traffic.json records the ncu DRAM bytes."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_12244_gb300", "csrc")
     for n in sorted(os.listdir(csrc)):
         if n.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, n), "rb") as f:
+            with open(os.path.join(csrc, n), encoding="utf-8") as f:
                 h.update(n.encode())
-                h.update(f.read())
+                h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

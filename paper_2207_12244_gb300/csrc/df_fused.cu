@@ -26,11 +26,13 @@
 // shuffles. Tiles are cut into contiguous ranges, one per CTA; a CTA's range
 // may span a few keyframes ("segments").
 //
-// Reductions: per tile a warp sums its FP32 per-lane partials in FP64, per
-// CTA the warps' sums are added in warp order into one slot per (CTA,
-// keyframe); after the barrier every CTA that needs a keyframe's scalar adds
-// that keyframe's slots in slot order. All CTAs therefore compute bitwise
-// identical scalars, and the result does not depend on timing.
+// Reductions: per tile a warp sums its FP32 per-lane partials as a
+// double-float (df_sync.cuh), per CTA the warps' sums are added in warp order
+// into one slot per (CTA, keyframe), pushed into the inbox of every CTA of
+// that keyframe; after the barrier each CTA adds its own inbox in slot
+// order. All CTAs therefore compute bitwise identical scalars, and the
+// result does not depend on timing. The CG scalars formed from the sums are
+// double-float too.
 //
 // Barrier: a generation-counting grid barrier whose waits give up after a
 // time limit (%globaltimer); a CTA that gives up raises an abort word, every
@@ -56,7 +58,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSeg = 8;  // keyframes a CTA's tile range may span
-constexpr int kQ = 3;       // FP64 partial sums per slot
+constexpr int kQ = 3;       // double-float partial sums per slot
 static_assert(kQ == 3, "a pass's reduction selects among three accumulators");
 
 enum PassKind : int { P_SCALE = 0, P_ASSEMBLE, P_INIT, P_ITER, P_FINAL };

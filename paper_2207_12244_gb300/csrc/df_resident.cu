@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
   };
 
   // partial sums -> slot -> barrier -> prefetch next halo + this keyframe's totals
-  // Reductions: every CTA pushes its FP64 partials into the inbox of each
+  // Reductions: every CTA pushes its double-float partials into the inbox of each
   // CTA of its keyframe (one slot per writer); after the barrier a CTA adds
   // its own inbox in slot order. No two CTAs read the same lines, so the
   // sums cost one uncontended L2 round trip and are identical everywhere.
