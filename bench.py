@@ -123,13 +123,19 @@ def _code_only(text: str) -> str:
     return " ".join("".join(out).split())
 
 
+# The sources of the fused solvers, whose launches profiles/traffic.json
+# records: the kernels, their launch plans and the device headers they use.
+FUSED_SOURCES = ("df_fused.cu", "df_fused.cuh", "df_internal.cuh", "df_resident.cu",
+                 "df_sync.cuh", "df_tma.cuh")
+
+
 def lib_source_hash():
-    """Hash of the CUDA library's code (comments and whitespace excluded):
+    """Hash of the fused solvers' code (comments and whitespace excluded):
     the key under which profiles/traffic.json records the ncu DRAM bytes."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_12244_gb300", "csrc")
     for n in sorted(os.listdir(csrc)):
-        if n.endswith((".cu", ".cuh")):
+        if n in FUSED_SOURCES:
             with open(os.path.join(csrc, n), encoding="utf-8") as f:
                 h.update(n.encode())
                 h.update(_code_only(f.read()).encode())

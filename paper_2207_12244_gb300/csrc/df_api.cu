@@ -10,6 +10,8 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "df_fused.cuh"
 #include "df_sync.cuh"
@@ -183,17 +185,40 @@ bool plane_ok(const T *p, int W, int rows, int cols, bool is_var, uint32_t inf_b
 // element-by-element walk below look for the first bad pixel (row, column,
 // then plane order) to report.
 bool host_inputs_ok(const void *const cnn[6], int W, int H, int dtype, char *why, size_t n) {
-  bool fast_ok = true;
-  for (int j = 0; j < 6 && fast_ok; ++j) {
-    const int cols = (j == 2 || j == 3) ? W - 1 : W, rows = (j == 4 || j == 5) ? H - 1 : H;
-    const bool is_var = (j & 1) == 1;
-    if (dtype == DF_F32)
-      fast_ok = plane_ok(static_cast<const uint32_t *>(cnn[j]), W, rows, cols, is_var, 0x7f800000u);
-    else
-      fast_ok = plane_ok(static_cast<const uint16_t *>(cnn[j]), W, rows, cols, is_var,
-                         dtype == DF_BF16 ? 0x7f80u : 0x7c00u);
+  // the fast pass: row blocks of every plane, split over host threads when
+  // the planes are large (a batch of keyframes reloads hundreds of MB)
+  std::atomic<bool> fast_ok{true};
+  auto check_rows = [&](int part, int parts) {
+    for (int j = 0; j < 6 && fast_ok.load(std::memory_order_relaxed); ++j) {
+      const int cols = (j == 2 || j == 3) ? W - 1 : W, rows = (j == 4 || j == 5) ? H - 1 : H;
+      const int r0 = (int)((long long)rows * part / parts);
+      const int r1 = (int)((long long)rows * (part + 1) / parts);
+      const bool is_var = (j & 1) == 1;
+      bool ok;
+      if (dtype == DF_F32)
+        ok = plane_ok(static_cast<const uint32_t *>(cnn[j]) + (size_t)r0 * W, W, r1 - r0, cols,
+                      is_var, 0x7f800000u);
+      else
+        ok = plane_ok(static_cast<const uint16_t *>(cnn[j]) + (size_t)r0 * W, W, r1 - r0, cols,
+                      is_var, dtype == DF_BF16 ? 0x7f80u : 0x7c00u);
+      if (!ok) fast_ok.store(false, std::memory_order_relaxed);
+    }
+  };
+  const long long elems = 6LL * W * H;
+  unsigned parts = 1;
+  if (elems >= (1LL << 22)) {
+    const unsigned hc = std::thread::hardware_concurrency();
+    parts = std::max(1u, std::min(16u, std::min(hc, (unsigned)H)));
   }
-  if (fast_ok) return true;
+  std::vector<std::thread> helpers;
+  try {
+    for (unsigned t = 1; t < parts; ++t) helpers.emplace_back(check_rows, (int)t, (int)parts);
+  } catch (...) {  // no threads to be had: the caller's thread checks the rest
+    for (unsigned t = (unsigned)helpers.size() + 1; t < parts; ++t) check_rows((int)t, (int)parts);
+  }
+  check_rows(0, (int)parts);
+  for (std::thread &th : helpers) th.join();
+  if (fast_ok.load()) return true;
   for (int v = 0; v < H; ++v) {
     for (int u = 0; u < W; ++u) {
       const size_t i = (size_t)v * W + u;

@@ -145,3 +145,33 @@ def test_host_validation_matches_the_rule(lib, dtype):
                     n_reject += 1
                     assert f"{names[j]} at (u={u}, v={v})" in msg, msg
     assert n_reject > 50
+
+
+def test_host_validation_of_large_planes_in_parallel(lib):
+    """Planes large enough for the threaded check (6 x 1024 x 768 elements):
+    a bad value anywhere is found and reported as the first bad pixel, and
+    valid planes pass."""
+    W, H = 1024, 768
+    base = [np.full((H, W), 0.25 if j % 2 == 0 else 2.0, np.float32) for j in range(6)]
+    desc = dfl.df_keyframe_desc(W, H, dfl.DF_F32)
+    out = C.c_void_p()
+
+    def create(planes):
+        st = lib.df_keyframe_create(C.byref(desc), *[p.ctypes.data for p in planes], 0, None,
+                                    C.byref(out))
+        if st == dfl.DF_OK:
+            lib.df_keyframe_destroy(out)
+        return st, dfl.df_last_error()
+
+    st, msg = create(base)
+    assert not (st == dfl.DF_EINVAL and "invalid network input" in msg), msg
+    for j, (v, u), val in [(5, (H - 2, W - 1), np.inf), (1, (700, 3), 0.0), (0, (383, 512), np.nan),
+                           (3, (10, 1000), -1.0)]:
+        planes = [b.copy() for b in base]
+        planes[j][v, u] = val
+        planes[2][H - 1, 5] = np.nan  # a later pixel (row H - 1) of an earlier plane
+        st, msg = create(planes)
+        assert st == dfl.DF_EINVAL and "invalid network input" in msg, msg
+        names = ["mu_net", "var_net", "gx", "var_gx", "gy", "var_gy"]
+        first = min([(v, u, j), (H - 1, 5, 2)])
+        assert f"{names[first[2]]} at (u={first[1]}, v={first[0]})" in msg, msg
