@@ -33,7 +33,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mpixel·iter/s"
-WORKLOAD = "sequence-640x480-100f-10x5-fp32"
+WORKLOAD = "sequence-640x480-100f-10x5-fp32"  # the default sequence workload
+
+
+def sequence_name(args) -> str:
+    """Name of the sequence workload a run measures (WORKLOAD by default)."""
+    return (f"sequence-{args.width}x{args.height}-{args.frames}f-"
+            f"{args.n_gn}x{args.n_pcg}-fp32")
 SCALE_STEPS = {"fixed": 0, "alternate": 1, "joint": 2}  # DF_SCALE_* values
 ALG_BYTES_PER_PCG_PX = 56  # canonical streaming model of one PCG iteration
 ALG_BYTES_PER_GN_PX = 56   # scale step + re-weighting / assembly per GN iteration
@@ -51,8 +57,14 @@ def parse():
     ap.add_argument("--width", type=int, default=640)
     ap.add_argument("--height", type=int, default=480)
     ap.add_argument("--frames", type=int, default=100)
-    ap.add_argument("--n-gn", type=int, default=10)
-    ap.add_argument("--n-pcg", type=int, default=5)
+    ap.add_argument("--n-gn", type=int, default=None,
+                    help="Gauss-Newton iterations per solve (default: the workload's, 10)")
+    ap.add_argument("--n-pcg", type=int, default=None,
+                    help="PCG iterations per GN iteration (default: the workload's, 5 for the "
+                         "sequence, 3 for the keyframe workloads)")
+    ap.add_argument("--loss", choices=["huber", "lsq", "tukey"], default="huber",
+                    help="robust loss: Huber (delta 1.345, the default), least squares, or "
+                         "Tukey's biweight (c 4.685)")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -78,7 +90,23 @@ def parse():
                     help="batch64: keep the default launch shape instead of autotuning it")
     ap.add_argument("--rate", type=float, default=600.0, help="serving: frames/s offered")
     ap.add_argument("--requests", type=int, default=1200, help="serving: frames per run")
-    return ap.parse_args()
+    args = ap.parse_args()
+    keyframes = args.workload in ("batch64", "precision")
+    if args.n_gn is None:
+        args.n_gn = 10
+    if args.n_pcg is None:
+        args.n_pcg = 3 if keyframes else 5
+    return args
+
+
+# (delta, loss code) of each --loss choice: the C ABI's df_solve_params
+# fields and the oracle's keyword arguments take the same values
+LOSSES = {"huber": (1.345, 0), "lsq": (0.0, 0), "tukey": (4.685, 1)}
+
+
+def loss_params(args):
+    delta, loss = LOSSES[args.loss]
+    return {"delta": delta, "loss": loss}
 
 
 def dist_env():
@@ -150,6 +178,8 @@ def traffic_key(args, workload: str) -> str:
     key = f"solve_{args.solver}_{workload}"
     if getattr(args, "scale_step", "alternate") != "alternate":
         key += f"_{args.scale_step}"
+    if getattr(args, "loss", "huber") != "huber":
+        key += f"_{args.loss}"
     if args.mode != "auto":
         key += f"_{args.mode}"
     for flag in ("max_ctas", "vec", "tile_rows"):
@@ -253,7 +283,7 @@ def run_reference(args, ws, rank):
         view.mu_s, view.var_s = mus[f % args.frames], vs[f % args.frames]
         t0 = time.perf_counter()
         xr, t, _ = o.optimise(view, x0=x, t0=t, n_gn=args.n_gn, n_pcg=args.n_pcg,
-                               scale_step=SCALE_STEPS[args.scale_step])
+                               scale_step=SCALE_STEPS[args.scale_step], **loss_params(args))
         dt = time.perf_counter() - t0
         x = xr.ravel()
         f += 1
@@ -268,8 +298,8 @@ def run_reference(args, ws, rank):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "width": args.width, "height": args.height,
-                   "frames_per_step": 1, "n_gn": args.n_gn, "n_pcg": args.n_pcg,
+        "config": {"workload": sequence_name(args), "width": args.width, "height": args.height,
+                   "frames_per_step": 1, "n_gn": args.n_gn, "n_pcg": args.n_pcg, "loss": args.loss,
                    "scale_step": args.scale_step},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -296,7 +326,7 @@ def cpu_baseline(args, kf, mus, vs):
     while True:
         view.mu_s, view.var_s = mus[n % args.frames], vs[n % args.frames]
         xr, t, _ = o.optimise(view, x0=x, t0=t, n_gn=args.n_gn, n_pcg=args.n_pcg,
-                               scale_step=SCALE_STEPS[args.scale_step])
+                               scale_step=SCALE_STEPS[args.scale_step], **loss_params(args))
         x = xr.ravel()
         n += 1
         el = time.perf_counter() - t_start
@@ -506,14 +536,15 @@ def run_mvs(args, ws, rank, dev, torch, dfl, replicas, synth):
 
 def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     """Batched / large-keyframe workloads: one solve of all keyframes per step."""
+    n_gn, n_pcg = args.n_gn, args.n_pcg
     if args.workload == "batch64":
         shapes = synth.batch_shapes(64, replicas.rank_seed(args.seed, rank))
-        dt_name, n_gn, n_pcg = "f32", 10, 3
-        name = "batch64-uneven-10x3-fp32"
+        dt_name = "f32"
+        name = f"batch64-uneven-{n_gn}x{n_pcg}-fp32"
     else:
         shapes = [(1920, 1440)]
-        dt_name, n_gn, n_pcg = args.cnn_dtype, 10, 3
-        name = f"keyframe-1920x1440-10x3-{dt_name}"
+        dt_name = args.cnn_dtype
+        name = f"keyframe-1920x1440-{n_gn}x{n_pcg}-{dt_name}"
     code = {"f32": dfl.DF_F32, "bf16": dfl.DF_BF16, "f16": dfl.DF_F16}[dt_name]
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dt_name]
     base = replicas.rank_seed(args.seed, rank)
@@ -523,7 +554,7 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     outs = [torch.empty((kf.height, kf.width), dtype=torch.float32, device=dev) for kf in kfs]
     solver = {"auto": dfl.DF_SOLVER_AUTO, "launches": dfl.DF_SOLVER_LAUNCHES,
               "fused": dfl.DF_SOLVER_FUSED}[args.solver]
-    prm = dfl.df_default_params(n_gn=n_gn, n_pcg=n_pcg, solver=solver)
+    prm = dfl.df_default_params(n_gn=n_gn, n_pcg=n_pcg, solver=solver, **loss_params(args))
     stream = torch.cuda.Stream(dev)
     sptr = stream.cuda_stream
     ks = [dfl.Keyframe(kf.width, kf.height, *c, cnn_dtype=code, stream=sptr)
@@ -654,7 +685,7 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
         o = oracle.get()
         kf = kfs[0]
         t0 = time.perf_counter()
-        o.optimise(kf, n_gn=n_gn, n_pcg=n_pcg)
+        o.optimise(kf, n_gn=n_gn, n_pcg=n_pcg, **loss_params(args))
         el = time.perf_counter() - t0
         cpu = {"value": kf.width * kf.height * n_gn * n_pcg / el / 1e6, "unit": METRIC,
                "cores": 1, "kind": "oracle",
@@ -675,7 +706,8 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
             "config": {"workload": name, "keyframes": len(shapes), "pixels": px,
-                       "cnn_dtype": dt_name, "n_gn": n_gn, "n_pcg": n_pcg, "solver": args.solver,
+                       "cnn_dtype": dt_name, "n_gn": n_gn, "n_pcg": n_pcg, "loss": args.loss,
+                       "solver": args.solver,
                        "cuda_graph": used_graph, "autotuned": tuning,
                        "kernel_mode": args.mode, "max_ctas": args.max_ctas,
                        "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MB write)"},
@@ -747,7 +779,7 @@ def main():
     scale_step = {"alternate": dfl.DF_SCALE_ALTERNATE, "joint": dfl.DF_SCALE_JOINT,
                   "fixed": dfl.DF_SCALE_FIXED}[args.scale_step]
     prm = dfl.df_default_params(n_gn=args.n_gn, n_pcg=args.n_pcg, solver=solver,
-                                scale_step=scale_step)
+                                scale_step=scale_step, **loss_params(args))
     dfl.df_set_tuning(mode={"auto": 0, "streaming": 1, "resident": 2}[args.mode],
                       vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas)
     stream = torch.cuda.Stream(dev)
@@ -841,7 +873,7 @@ def main():
                          args.n_gn * ALG_BYTES_PER_GN_PX)
     peak, peak_kind = peaks()
     achieved = alg_bytes / solve_avg_s / 1e9
-    kernel_key = traffic_key(args, WORKLOAD)
+    kernel_key = traffic_key(args, sequence_name(args))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": ncu_traffic(kernel_key),
                 "peak_kind": peak_kind, "region": "df_optimise (one frame's solve)",
@@ -903,8 +935,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
-            "config": {"workload": WORKLOAD, "width": W, "height": H, "frames": F,
-                       "n_gn": args.n_gn, "n_pcg": args.n_pcg, "solver": args.solver,
+            "config": {"workload": sequence_name(args), "width": W, "height": H, "frames": F,
+                       "n_gn": args.n_gn, "n_pcg": args.n_pcg, "loss": args.loss,
+                       "solver": args.solver,
                        "scale_step": args.scale_step, "cuda_graph": bool(args.graph),
                        "kernel_mode": args.mode, "max_ctas": args.max_ctas,
                        "parallelism": f"replicas x{ws}",
