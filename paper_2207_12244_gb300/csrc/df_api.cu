@@ -2,12 +2,15 @@
 // input validation and the solve driver. Declarations and the contract of
 // every entry point are in include/deepfusion.h.
 #include <math.h>
+#include <pthread.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -156,6 +159,81 @@ float host_elem(const void *p, size_t i, int dtype) {
   return half_bits_to_float(h);
 }
 
+// ---- host worker threads for checking large host inputs --------------------
+//
+// A batch reloads the network planes of every keyframe each frame (hundreds
+// of MB). One host thread checks ~20 GB/s; the pool spreads a check over the
+// host's cores without creating threads per call. Its threads are made once,
+// detached, and wait on a condition variable; one job runs at a time, and
+// every worker acknowledges each job before run() returns, so no worker
+// touches a finished job. A process that forks gets no pool in the child
+// (the threads are not copied): there, and while another thread's job runs,
+// run() declines and the caller checks on its own thread.
+std::atomic<bool> g_pool_forked{false};
+
+class CheckPool {
+ public:
+  static CheckPool &get() {
+    static CheckPool *pool = new CheckPool();  // never destroyed: its threads live until exit
+    return *pool;
+  }
+  // f(0) .. f(parts - 1) on the pool's threads and the caller's; false (and
+  // nothing run) if the pool is unavailable or busy.
+  bool run(int parts, const std::function<void(int)> &f) {
+    if (g_pool_forked.load() || nthreads_ == 0) return false;
+    std::unique_lock<std::mutex> job(job_mu_, std::try_to_lock);
+    if (!job.owns_lock()) return false;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      fn_ = &f;
+      parts_ = parts;
+      acked_ = 0;
+      next_.store(0);
+      ++gen_;
+    }
+    wake_.notify_all();
+    for (int p = next_.fetch_add(1); p < parts; p = next_.fetch_add(1)) f(p);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [&] { return acked_ == nthreads_; });
+    return true;
+  }
+
+ private:
+  CheckPool() {
+    pthread_atfork(nullptr, nullptr, [] { g_pool_forked.store(true); });
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int n = (int)std::min(15u, hc > 1 ? hc - 1 : 0u);
+    for (int i = 0; i < n; ++i) {
+      try {
+        std::thread(&CheckPool::worker, this).detach();
+      } catch (...) {
+        break;
+      }
+      ++nthreads_;
+    }
+  }
+  void worker() {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+      wake_.wait(lk, [&] { return gen_ != seen; });
+      seen = gen_;
+      const std::function<void(int)> *fn = fn_;
+      const int parts = parts_;
+      lk.unlock();
+      for (int p = next_.fetch_add(1); p < parts; p = next_.fetch_add(1)) (*fn)(p);
+      lk.lock();
+      if (++acked_ == nthreads_) done_.notify_one();
+    }
+  }
+  std::mutex job_mu_, mu_;
+  std::condition_variable wake_, done_;
+  const std::function<void(int)> *fn_ = nullptr;
+  int parts_ = 0, acked_ = 0, nthreads_ = 0;
+  std::atomic<int> next_{0};
+  uint64_t gen_ = 0;
+};
+
 // Validity of one network plane from the bit patterns of its elements:
 // finite (any sign) for a mean, finite and > 0 for a variance. Integer tests
 // over whole rows, so the loop is a plain streaming pass (the caller's planes
@@ -204,20 +282,15 @@ bool host_inputs_ok(const void *const cnn[6], int W, int H, int dtype, char *why
       if (!ok) fast_ok.store(false, std::memory_order_relaxed);
     }
   };
+  // inputs of 1 M elements and more go to the pool in row blocks
   const long long elems = 6LL * W * H;
-  unsigned parts = 1;
-  if (elems >= (1LL << 22)) {
-    const unsigned hc = std::thread::hardware_concurrency();
-    parts = std::max(1u, std::min(16u, std::min(hc, (unsigned)H)));
+  const int parts = std::min(H, 64);
+  bool done = false;
+  if (elems >= (1LL << 20) && parts > 1) {
+    const std::function<void(int)> job = [&](int part) { check_rows(part, parts); };
+    done = CheckPool::get().run(parts, job);
   }
-  std::vector<std::thread> helpers;
-  try {
-    for (unsigned t = 1; t < parts; ++t) helpers.emplace_back(check_rows, (int)t, (int)parts);
-  } catch (...) {  // no threads to be had: the caller's thread checks the rest
-    for (unsigned t = (unsigned)helpers.size() + 1; t < parts; ++t) check_rows((int)t, (int)parts);
-  }
-  check_rows(0, (int)parts);
-  for (std::thread &th : helpers) th.join();
+  if (!done) check_rows(0, 1);
   if (fast_ok.load()) return true;
   for (int v = 0; v < H; ++v) {
     for (int u = 0; u < W; ++u) {
@@ -238,17 +311,36 @@ bool host_inputs_ok(const void *const cnn[6], int W, int H, int dtype, char *why
   return true;
 }
 
-df_status copy_cnn(df_keyframe *kf, const void *const cnn[6], cudaStream_t s) {
+// The six network planes into the keyframe's pitched planes, ordered on s.
+// Host planes go up as whole contiguous copies into the dense staging plane
+// (one f32 plane or two 16-bit planes at a time) and then into place by
+// pitched device-to-device copies: a pitched copy straight from host memory
+// moves one row per transfer and ran at ~24 GB/s on GB300, a contiguous one
+// at ~160 GB/s.
+df_status copy_cnn(df_keyframe *kf, const void *const cnn[6], int on_device, cudaStream_t s) {
   const size_t es = elem_size(kf->dtype);
-  for (int j = 0; j < 6; ++j) {
-    DF_CUDA(cudaMemcpy2DAsync(const_cast<void *>(kf->planes.cnn[j]), kf->P * es, cnn[j],
-                              kf->W * es, kf->W * es, kf->H, cudaMemcpyDefault, s));
+  const size_t row = (size_t)kf->W * es, pitch = (size_t)kf->P * es;
+  if (on_device) {
+    for (int j = 0; j < 6; ++j)
+      DF_CUDA(cudaMemcpy2DAsync(const_cast<void *>(kf->planes.cnn[j]), pitch, cnn[j], row, row,
+                                kf->H, cudaMemcpyDefault, s));
+    return DF_OK;
+  }
+  const size_t plane = row * kf->H;
+  const int per = (int)(((size_t)kf->W * kf->H * 4) / plane);  // planes per staging round
+  char *st = reinterpret_cast<char *>(kf->staging);
+  for (int j = 0; j < 6; j += per) {
+    for (int q = 0; q < per && j + q < 6; ++q)
+      DF_CUDA(cudaMemcpyAsync(st + q * plane, cnn[j + q], plane, cudaMemcpyDefault, s));
+    for (int q = 0; q < per && j + q < 6; ++q)
+      DF_CUDA(cudaMemcpy2DAsync(const_cast<void *>(kf->planes.cnn[j + q]), pitch, st + q * plane,
+                                row, row, kf->H, cudaMemcpyDeviceToDevice, s));
   }
   return DF_OK;
 }
 
 df_status load_cnn(df_keyframe *kf, const void *const cnn[6], int on_device, cudaStream_t s) {
-  df_status st = copy_cnn(kf, cnn, s);
+  df_status st = copy_cnn(kf, cnn, on_device, s);
   if (st != DF_OK) return st;
   DF_CUDA(cudaMemsetAsync(kf->planes.sc, 0, sizeof(Scalars), s));
   DF_CUDA(df::launch_init_state(kf->planes, s));

@@ -175,3 +175,72 @@ def test_host_validation_of_large_planes_in_parallel(lib):
         names = ["mu_net", "var_net", "gx", "var_gx", "gy", "var_gy"]
         first = min([(v, u, j), (H - 1, 5, 2)])
         assert f"{names[first[2]]} at (u={first[1]}, v={first[0]})" in msg, msg
+
+
+def _large_planes(W=1024, H=768, bad=None):
+    planes = [np.full((H, W), 0.25 if j % 2 == 0 else 2.0, np.float32) for j in range(6)]
+    if bad is not None:
+        j, v, u, val = bad
+        planes[j][v, u] = val
+    return planes
+
+
+def _create_status(lib, planes):
+    H, W = planes[0].shape
+    desc = dfl.df_keyframe_desc(W, H, dfl.DF_F32)
+    out = C.c_void_p()
+    st = lib.df_keyframe_create(C.byref(desc), *[p.ctypes.data for p in planes], 0, None,
+                                C.byref(out))
+    if st == dfl.DF_OK:
+        lib.df_keyframe_destroy(out)
+    return st, dfl.df_last_error()
+
+
+def test_host_validation_from_concurrent_threads(lib):
+    """Several host threads checking large planes at once (one holds the
+    worker pool, the others check on their own threads): every call reports
+    its own first bad pixel."""
+    import threading
+
+    cases = [(1, 700 - 9 * i, 3 + i, 0.0) for i in range(6)]
+    results = [None] * len(cases)
+
+    def work(i):
+        planes = _large_planes(bad=cases[i])
+        for _ in range(3):
+            st, msg = _create_status(lib, planes)
+            results[i] = (st, msg)
+
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(len(cases))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(timeout=60)
+        assert not t.is_alive()
+    for (j, v, u, _), (st, msg) in zip(cases, results):
+        assert st == dfl.DF_EINVAL and f"var_net at (u={u}, v={v})" in msg, msg
+
+
+def _forked_child_check(q):
+    lib = dfl.load()
+    st, msg = _create_status(lib, _large_planes(bad=(4, 500, 17, np.inf)))
+    q.put((st, msg))
+
+
+def test_host_validation_in_a_forked_child(lib):
+    """A child forked after the worker pool exists checks on its own thread
+    (the pool's threads are not in the child) instead of waiting for them."""
+    import multiprocessing as mp
+
+    _create_status(lib, _large_planes())  # the pool exists in this process now
+    ctx = mp.get_context("fork")
+    q = ctx.Queue()
+    p = ctx.Process(target=_forked_child_check, args=(q,))
+    p.start()
+    p.join(timeout=60)
+    alive = p.is_alive()
+    if alive:
+        p.kill()
+    assert not alive, "the forked child hung in the host check"
+    st, msg = q.get(timeout=5)
+    assert st == dfl.DF_EINVAL and "gy at (u=17, v=500)" in msg, msg
