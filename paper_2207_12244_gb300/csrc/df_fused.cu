@@ -1060,7 +1060,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
   __shared__ unsigned int s_epoch;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int G = h->G, nslots = h->nslots, nkf = h->nkf;
+  const int G = h->G, nkf = h->nkf;
   const char *hb = reinterpret_cast<const char *>(h);
   const int *warp_row = reinterpret_cast<const int *>(hb + h->off_cta_work);
   const int *cta_kf = reinterpret_cast<const int *>(hb + h->off_cta_kf);

@@ -29,7 +29,6 @@ namespace df {
 namespace {
 
 constexpr int kRThreads = 512;
-constexpr int kRWarps = kRThreads / 32;
 constexpr int kRQ = 4;
 constexpr int kHalo = 9;  // halo arrays of W floats kept in shared memory
 
