@@ -513,3 +513,49 @@ def test_frame_captured_in_a_cuda_graph(sv):
             k.close()
     finally:
         dfl.df_set_tuning()
+
+
+def test_frame_captured_with_host_buffers():
+    """Frame updates from pinned host buffers inside a CUDA graph capture take
+    the direct upload (no copy stream in a capture); replays give the eager
+    device-pointer result, also after uncaptured host updates made the
+    keyframe's copy stream."""
+    torch = torch_cuda()
+    kf, mus, vs = synth.make_sequence(96, 72, 27, n_frames=3)
+    prm = params(n_gn=4, n_pcg=3, solver=dfl.DF_SOLVER_FUSED)
+    out = torch.empty((72, 96), dtype=torch.float32, device="cuda")
+    eager = create(kf)
+    try:
+        for f in range(3):
+            eager.frame_update(to_dev(mus[f]), to_dev(vs[f]))
+            eager.optimise(prm)
+        eager.fetch_depth(out, log_space=True)
+        ref = out.clone()
+    finally:
+        eager.close()
+    mu_h = torch.from_numpy(mus[0].copy()).pin_memory()
+    var_h = torch.from_numpy(vs[0].copy()).pin_memory()
+    k = create(kf)
+    try:
+        k.frame_update(mu_h, var_h)  # uncaptured host update: the copy stream path
+        k.optimise(prm)
+        k.set_state(to_dev(kf.mu_n), 0.0)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                k.frame_update(mu_h, var_h)
+                k.optimise(prm)
+                k.fetch_depth(out, log_space=True)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        for f in range(3):
+            mu_h.copy_(torch.from_numpy(mus[f]))
+            var_h.copy_(torch.from_numpy(vs[f]))
+            g.replay()
+            torch.cuda.synchronize()  # the graph reads the pinned buffers
+        assert torch.equal(out, ref)
+    finally:
+        k.close()
