@@ -13,6 +13,10 @@ The fixtures freeze the oracle's output, so that
 * the oracle built on another host (the GPU machine is an Arm machine) can be
   checked to give the same bits as the one that wrote them.
 
+A stereo case stores one semi-dense update (Section II-B) the same way:
+the two images and the relative pose, and the oracle's depth, variance,
+decision margin, status and best step per pixel.
+
 Run from the repository root:  python tests/golden/make_golden.py
 """
 from __future__ import annotations
@@ -96,10 +100,59 @@ def write_case(o, case) -> str:
     return path
 
 
+# name, W, H, seed, baseline (m), what it covers
+STEREO_CASES = [
+    ("stereo_40x30", 40, 30, 5, 0.08,
+     "one semi-dense update (Section II-B, Eqs. 2-4): epipolar 5-point SSD search, sub-pixel "
+     "fit and variance, every rejection status"),
+]
+
+
+def _f32_list(a) -> str:
+    return " ".join(float(v).hex() for v in np.asarray(a, np.float32).astype(np.float64).ravel())
+
+
+def write_stereo_case(o, case) -> str:
+    name, W, H, seed, baseline, what = case
+    sp = synth.make_stereo_pair(W, H, seed, baseline=baseline)
+    # the geometry exactly as the C ABI takes it (float32)
+    cam = [float(np.float32(c)) for c in sp.cam]
+    R = np.asarray(sp.R, np.float32).astype(np.float64)
+    t = np.asarray(sp.t, np.float32).astype(np.float64)
+    d, v, st, bs, mg, n = o.semi_dense(sp.img_key, sp.img_ref, cam, R, t)
+    lines = [
+        f"# golden case {name}: {what}.",
+        "# Written by tests/golden/make_golden.py from oracle/ (default stereo parameters);",
+        f"# images from synth.make_stereo_pair({W}, {H}, seed={seed}, baseline={baseline}).",
+        "# Hex floats: images and geometry as float32 values, depth / variance as float64,",
+        "# the decision margin as float32; status and best step as integers.",
+        "kind stereo",
+        f"W {W}",
+        f"H {H}",
+        f"cam {_f32_list(cam)}",
+        f"R {_f32_list(R)}",
+        f"t {_f32_list(t)}",
+        f"image img_key {_hex32(sp.img_key)}",
+        f"image img_ref {_hex32(sp.img_ref)}",
+        f"expect_depth {_hex64(d)}",
+        f"expect_var {_hex64(v)}",
+        f"expect_margin {_f32_list(mg)}",
+        "expect_status " + " ".join(str(int(x)) for x in st.ravel()),
+        "expect_best " + " ".join(str(int(x)) for x in bs.ravel()),
+        f"expect_measured {n}",
+    ]
+    path = os.path.join(HERE, name + ".txt")
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    return path
+
+
 def main():
     o = oracle.get()
     for case in CASES:
         print(write_case(o, case))
+    for case in STEREO_CASES:
+        print(write_stereo_case(o, case))
 
 
 if __name__ == "__main__":
