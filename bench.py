@@ -536,6 +536,8 @@ def run_mvs(args, ws, rank, dev, torch, dfl, replicas, synth):
 
 def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     """Batched / large-keyframe workloads: one solve of all keyframes per step."""
+    import torch.distributed as dist
+
     n_gn, n_pcg = args.n_gn, args.n_pcg
     if args.workload == "batch64":
         shapes = synth.batch_shapes(64, replicas.rank_seed(args.seed, rank))
@@ -621,6 +623,8 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     with ClockSampler(dev.index) as clk:
         for _ in range(args.steps):
             flush.fill_(1.0)
+            if ws > 1:
+                dist.barrier()
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -631,6 +635,8 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             solve_ms.append(ev[0].elapsed_time(ev[1]))
+        if ws > 1:
+            dist.barrier()
     # the library counts its own launches; a replayed graph's kernels are
     # counted from the capture, once per timed replay
     launches = dfl.df_kernel_launches() - launches0 + graph_launches * args.steps
@@ -860,6 +866,8 @@ def main():
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             solve_ms.extend(a.elapsed_time(b) for a, b in ev_opt)
+        if ws > 1:
+            dist.barrier()
     # a replayed graph's kernels are counted from its capture, once per frame
     launches = dfl.df_kernel_launches() - launches0 + graph_launches * F * args.steps
     clocks = clk.summary()
