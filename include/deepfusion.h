@@ -152,7 +152,10 @@ df_status df_keyframe_reset(df_keyframe *kf, const void *mu_net, const void *var
  * the keyframe's own copy stream into a staging pair of the keyframe, so
  * that the upload overlaps the work 'stream' runs before the call (the
  * previous frame's solve); 'stream' then waits for it and moves the planes
- * into place. Under stream capture the upload goes on 'stream' itself.
+ * into place. Host buffers must therefore hold the frame's data when the
+ * call is made (as host planes must for df_keyframe_create / _reset, which
+ * check them on the host): a copy into them still pending on a stream is
+ * not waited for. Under stream capture the upload goes on 'stream' itself.
  * Errors: DF_EINVAL (null kf/pointers), DF_ECUDA. */
 df_status df_frame_update(df_keyframe *kf, const float *mu_semi, const float *var_semi,
                           int ptrs_on_device, void *stream);

@@ -290,6 +290,10 @@ def df_keyframe_reset(kf, mu_net, var_net, gx, var_gx, gy, var_gy, stream=None):
 
 
 def df_frame_update(kf, mu_semi, var_semi, stream=None):
+    """The frame's semi-dense log-depth and variance (H x W float32), both on
+    the host or both on the device. Host buffers must already hold the data
+    (they may be read before the stream reaches the call) and stay unchanged
+    until the stream has passed it."""
     on_dev = _same_side([mu_semi, var_semi], "df_frame_update")
     _check(load().df_frame_update(kf, _ptr(mu_semi)[0], _ptr(var_semi)[0], on_dev,
                                   _stream(stream, mu_semi)), "df_frame_update")
