@@ -524,8 +524,13 @@ void orc_ls_scale_fit(const orc_problem *P, double *x, double *t) {
   double s = 0.0;
   for (int i = 0; i < N; ++i) s += P->mu_n[i] - x[i];
   double c = s / (double)N;
+#if ORC_MUTANT == 13
+  c = -c;
+#endif
   for (int i = 0; i < N; ++i) x[i] += c;
+#if ORC_MUTANT != 14
   *t = *t + c;
+#endif
 }
 
 /* Accuracy measure of Section III-B (Tables I-III): among the pixels with a

@@ -20,6 +20,8 @@ What each pin fixes:
   invariances          shifts of mu_s, of (mu_n, mu_s), and transposition
   monotone             cost never increases over scale and depth steps
   no_pairwise          semi + network only: closed-form joint optimum
+  ls_scale_fit         Table II fit: a constructed offset comes back exactly;
+                       optimality, x - t kept, shift invariance
   semi_to_log          first-order log conversion vs Monte Carlo
 """
 from __future__ import annotations
@@ -413,6 +415,45 @@ def no_pairwise(o):
     assert abs(t - t1) < 1e-12 and np.allclose(x.ravel(), x1, rtol=0, atol=1e-12)
 
 
+def ls_scale_fit(o):
+    """Table II's least-squares scale fit (reading: the shift c minimising
+    sum_i (x_i + c - mu_n,i)^2 moves x and t together, so the semi-dense
+    residuals x - t - mu_s are unchanged).
+
+    Fixed by a constructed answer: x = mu_n - c0 + e with sum(e) = 0 exactly
+    (e in 1/1024 steps, paired with its negation) must come back as x + c0
+    and t0 + c0. Then, on an arbitrary x, three facts the definition fixes:
+    the fitted x has zero mean offset from mu_n (first-order optimality) and
+    a strictly smaller objective than any other shift; x - t is unchanged per
+    pixel; shifting the input x by k leaves the fitted x unchanged."""
+    W, H = 11, 7
+    kf = _noisy(W, H, 71)
+    N = W * H
+    mu_n = kf.mu_n.astype(np.float64).ravel()
+    rng = np.random.default_rng(71)
+    half = rng.integers(-200, 201, N // 2) / 1024.0
+    e = np.concatenate([half, -half, np.zeros(N - 2 * (N // 2))])
+    rng.shuffle(e)
+    c0, t0 = 0.375, -0.21
+    x_in = mu_n - c0 + e
+    xf, tf = o.ls_scale_fit(kf, x_in, t0)
+    assert np.allclose(xf.ravel(), x_in + c0, rtol=0, atol=1e-13), np.abs(xf.ravel() - x_in - c0).max()
+    assert abs(tf - (t0 + c0)) < 1e-13, (tf, t0 + c0)
+    # an arbitrary start
+    x_in = mu_n + rng.normal(0.8, 0.3, N)
+    xf, tf = o.ls_scale_fit(kf, x_in, t0)
+    xf = xf.ravel()
+    assert abs(np.sum(xf - mu_n)) < 1e-11 * N
+    obj = lambda c: np.sum((xf + c - mu_n) ** 2)
+    for h in (1e-3, -1e-3, 0.1, -0.1):
+        assert obj(h) > obj(0.0)
+    assert np.allclose(xf - tf, x_in - t0, rtol=0, atol=1e-13)
+    k = -1.7
+    xk, tk = o.ls_scale_fit(kf, x_in + k, t0)
+    assert np.allclose(xk.ravel(), xf, rtol=0, atol=1e-12)
+    assert abs(tk - (tf - k)) < 1e-12
+
+
 def semi_to_log(o):
     rng = np.random.default_rng(3)
     d = np.array([0.5, 1.0, 2.0, 4.5, -1.0, 0.0, 2.0, np.nan])
@@ -527,5 +568,6 @@ def mvs_scene(o):
 
 
 ALL = [cost_closed_form, robust_weight, dense_hessian, joint_optimum, joint_bordered, prior_only,
-       planar_recovery, huber_scipy, invariances, monotone, no_pairwise, semi_to_log, within_10pct,
+       planar_recovery, huber_scipy, invariances, monotone, no_pairwise, ls_scale_fit, semi_to_log,
+       within_10pct,
        mvs_rectified, mvs_fusion_and_interval, mvs_scene]

@@ -396,8 +396,11 @@ def test_table2_scale_ambiguous_solve_then_ls_fit(o, solver):
     try:
         k.frame_update(to_dev(kf.mu_s), to_dev(kf.var_s))
         k.optimise(prm)
-        k.scale_fit_ls()
         out = torch.empty((kf.height, kf.width), dtype=torch.float32, device="cuda")
+        k.fetch_depth(out, log_space=True)
+        t_pre = k.get_state()
+        x_pre = out.double().cpu().numpy()
+        k.scale_fit_ls()
         k.fetch_depth(out, log_space=True)
         t = k.get_state()
         x = out.double().cpu().numpy()
@@ -406,7 +409,13 @@ def test_table2_scale_ambiguous_solve_then_ls_fit(o, solver):
     xo, to, _ = oracle_solve(o, kf, prm)
     xo, to = o.ls_scale_fit(kf, xo, to)
     assert_parity(x, t, xo, to, what="table II")
-    assert abs(np.mean(kf.mu_n.astype(np.float64) - x)) < 1e-5  # the fit's defining property
+    # the fit itself, from the GPU's own pre-fit state and the definition:
+    # c = mean(mu_n - x) moves every x and t by the same c
+    c = np.mean(kf.mu_n.astype(np.float64) - x_pre)
+    assert abs(c) > 1e-2  # the scale-ambiguous solve leaves a real offset to fit
+    assert abs((t - t_pre) - c) < 1e-6, (t - t_pre, c)
+    assert np.allclose(x - x_pre, c, rtol=0, atol=1e-5)
+    assert abs(np.mean(kf.mu_n.astype(np.float64) - x)) < 1e-5
 
 
 @pytest.mark.parametrize("mode", [dfl.DF_MODE_STREAMING, dfl.DF_MODE_RESIDENT],

@@ -7,7 +7,8 @@ gradient residual, a wrong Huber weight, a flipped scale step, a wrong
 neighbour index, an inverted CG beta, a residual divided by the variance
 instead of the standard deviation, a flipped sign of the x-t coupling in
 the joint solve, a stereo variance with the wrong power of the depth step,
-a stereo sub-pixel fraction with the wrong sign.
+a stereo sub-pixel fraction with the wrong sign, a Table II scale fit
+with the wrong sign, a Table II scale fit that does not move t.
 """
 import pytest
 
@@ -27,6 +28,8 @@ MUTANTS = {
     10: "joint PCG couples x and t with the wrong sign",
     11: "stereo variance uses |dd| instead of dd^2",
     12: "stereo sub-pixel fraction has the wrong sign",
+    13: "Table II fit shifts by mean(x - mu_n)",
+    14: "Table II fit leaves t in place",
 }
 
 
