@@ -403,17 +403,23 @@ int32_t df_server_pending(const df_server *srv);
 /* The stream's current depth (as df_fetch_depth; synchronises). */
 df_status df_server_fetch_depth(df_server *srv, int32_t stream_id, float *out, int log_space,
                                 int ptr_on_device);
+/* The stream's current state (as df_keyframe_get_state: the log-depth x,
+ * H x W f32, and the log scale t of Eq. 5, either may be NULL; waits for
+ * the server's launches and synchronises). */
+df_status df_server_get_state(df_server *srv, int32_t stream_id, float *x_out, double *t_out,
+                              int ptrs_on_device);
 
 /* Largest keyframe (in pixels) df_optimise_noalloc accepts: 196608, i.e.
  * 512 x 384, or four times the 256 x 192 resolution of Section II-A. */
 #define DF_NOALLOC_MAX_PIXELS 196608
 
 /* The per-frame solve of df_optimise for callers that cannot allocate device
- * memory: code running where cudaMalloc is forbidden or unavailable, such as
- * inside a CUDA graph being captured by someone else, a real-time loop with a
- * no-allocation rule, or a host whose device memory is owned by another
- * allocator. The paper has no counterpart; this is an interface of this
- * library.
+ * memory. Some callers may not call cudaMalloc at all: a real-time loop whose
+ * rules forbid allocation after start-up (an allocation can block on the
+ * driver for milliseconds), a plugin inside a host program whose device
+ * memory is owned by that program's own allocator (which may hold nearly all
+ * of it), or a process that runs under a fixed device-memory quota. The
+ * paper has no counterpart; this is an interface of this library.
  *
  * Arguments: H x W = height x width (at most DF_NOALLOC_MAX_PIXELS pixels),
  * dense row-major f32 DEVICE buffers owned by the caller: the six network
@@ -425,16 +431,20 @@ df_status df_server_fetch_depth(df_server *srv, int32_t stream_id, float *out, i
  * launch schedule). Inputs are not checked on the device.
  *
  * It allocates nothing: its working memory (the solver vectors, FP64 partial
- * sums and scalars) is one static device array of the library, about 5.6 MB,
- * that every GPU which loads the library holds until the process exits. All
- * calls on a device share that array and it keeps the last call's contents,
- * so calls whose work overlaps on the GPU (other streams, other host
- * threads) race with each other: serialise them. The first call on each
- * device looks the array's device address up (cudaGetSymbolAddress); make
- * that first call before any stream capture. Asynchronous on 'stream'.
+ * sums and scalars) is one static device array of the library of 5,701,824
+ * bytes (5.70 MB, 5.44 MiB) that every GPU which loads the library holds
+ * until the process exits. All calls on a device share that array and it
+ * keeps the last call's contents (the scalars are cleared at the start of
+ * each call), so calls whose work overlaps on the GPU (other streams, other
+ * host threads) race with each other: serialise them. The first call on
+ * each device looks the array's device address up (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream
+ * capture. Asynchronous on 'stream'.
  * Errors: DF_EINVAL (sizes above the limit, NULL pointers, parameters),
- * DF_ENOTSUP (the joint (x, t) variant, whose extra scratch plane the array
- * does not hold; a device index beyond 63), DF_ECUDA. */
+ * DF_ENOTSUP (the joint (x, t) variant with the semi-dense term, whose extra
+ * scratch plane the array does not hold; without the semi-dense term the
+ * joint variant leaves t in place and runs as the depth step with t fixed;
+ * a device index beyond 63), DF_ECUDA. */
 df_status df_optimise_noalloc(int32_t width, int32_t height, const float *mu_net,
                               const float *var_net, const float *gx, const float *var_gx,
                               const float *gy, const float *var_gy, const float *mu_semi,
@@ -469,13 +479,20 @@ df_status df_get_tuning(df_tuning *t);
 
 /* Autotuner (paper counterpart: none): time the fused solver's candidate
  * launch shapes -- the resident kernel with all GN iterations in one launch
- * or one per launch, the streaming kernel with 1 or 4 pixels per lane and
- * 2..32 rows per warp tile -- on these keyframes (solved together as by
+ * or one per launch; the streaming kernel with 1 or 4 pixels per lane, each
+ * warp walking its whole row share or pieces of 4..64 rows, and with 1 or 2
+ * GN iterations per launch -- on these keyframes (solved together as by
  * df_optimise_batch, or alone when n = 1) with 'params'. Every trial starts
  * from the keyframes' current state, which is restored at the end. The
  * fastest shape becomes the current tuning (df_set_tuning) and is written to
- * *best, its time per solve to *best_ms. Synchronises; allocates a snapshot
- * of the keyframes' log-depth for the duration of the call. */
+ * *best, its time per solve (the median of five timed solves after an
+ * untimed one) to *best_ms. Synchronises; allocates a snapshot of the
+ * keyframes' log-depth for the duration of the call.
+ * Errors: DF_EINVAL for a NULL or repeated keyframe in the list (checked
+ * before anything is allocated or changed); a failure while taking the
+ * snapshot frees what was taken and leaves every keyframe and the tuning as
+ * they were; DF_ENOTSUP when no shape can solve the list (the states are
+ * restored and the tuning is left as it was). */
 df_status df_autotune(df_keyframe *const *kfs, int32_t n, const df_solve_params *params,
                       void *stream, df_tuning *best, float *best_ms);
 

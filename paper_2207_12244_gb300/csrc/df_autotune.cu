@@ -1,6 +1,7 @@
 // Autotuner of the fused solver's launch shape (df_autotune): times
 // candidate shapes on the caller's own keyframes, each trial starting from
 // the same state, and keeps the fastest.
+#include <algorithm>
 #include <vector>
 
 #include "df_internal.cuh"
@@ -26,30 +27,50 @@ extern "C" df_status df_autotune(df_keyframe *const *kfs, int32_t n, const df_so
   p.solver = DF_SOLVER_FUSED;
   df_status st = df::check_solve_params(&p);
   if (st != DF_OK) return st;
+  // the list is checked before anything is allocated or any state changes
+  for (int32_t j = 0; j < n; ++j) {
+    if (!kfs[j]) return df::report(DF_EINVAL, "keyframe %d is NULL", (int)j);
+    for (int32_t m = 0; m < j; ++m)
+      if (kfs[m] == kfs[j]) return df::report(DF_EINVAL, "keyframe %d appears twice", (int)j);
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   df_tuning saved;
   df_get_tuning(&saved);
-  // snapshot every keyframe's (x, t)
+  // snapshot every keyframe's (x, t); on a failure part-way, only the
+  // snapshots taken so far are freed (no keyframe has been touched yet)
   Snapshot snap;
+  auto free_snap = [&]() {
+    cudaStreamSynchronize(s);
+    for (float *q : snap.x) cudaFree(q);
+    snap.x.clear();
+    snap.t.clear();
+  };
   for (int32_t j = 0; j < n; ++j) {
     df_keyframe_desc d;
     size_t bytes = 0;
     st = df_keyframe_info(kfs[j], &d, &bytes);
-    if (st != DF_OK) return st;
+    if (st != DF_OK) {
+      free_snap();
+      return st;
+    }
     float *buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, (size_t)d.width * d.height * sizeof(float));
     if (e != cudaSuccess) {
-      for (float *q : snap.x) cudaFree(q);
+      free_snap();
       return df::report(DF_ENOMEM, "autotune snapshot: %s", cudaGetErrorString(e));
     }
-    snap.x.push_back(buf);
     double t = 0.0;
     st = df_keyframe_get_state(kfs[j], buf, &t, 0, stream);
-    if (st != DF_OK) break;
+    if (st != DF_OK) {
+      cudaFree(buf);
+      free_snap();
+      return st;
+    }
+    snap.x.push_back(buf);
     snap.t.push_back(t);
   }
   auto restore = [&]() -> df_status {
-    for (int32_t j = 0; j < n; ++j) {
+    for (size_t j = 0; j < snap.x.size(); ++j) {
       df_status r = df_keyframe_set_state(kfs[j], snap.x[j], snap.t[j], 1, stream);
       if (r != DF_OK) return r;
     }
@@ -68,46 +89,52 @@ extern "C" df_status df_autotune(df_keyframe *const *kfs, int32_t n, const df_so
   for (int vec : {1, 4})
     for (int th : {0, 4, 8, 16, 32, 64}) cand.push_back(df_tuning{1, vec, th, 0, 0, -1});
   for (int g : {1, 2}) cand.push_back(df_tuning{1, 4, 0, 0, g, -1});
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    free_snap();
+    return df::report(DF_ECUDA, "autotune: cannot create timing events");
+  }
+  // each candidate: one untimed solve, then the median of kReps timed ones
+  constexpr int kReps = 5;
   float best_t = 0.0f;
   bool have = false;
-  if (st == DF_OK) {
-    for (const df_tuning &c : cand) {
-      df_set_tuning(&c);
-      if (restore() != DF_OK) continue;
-      if (solve() != DF_OK) {  // e.g. the resident kernel cannot hold these keyframes
-        cudaStreamSynchronize(s);
-        continue;
-      }
-      float tmin = 1e30f;
-      for (int rep = 0; rep < 2; ++rep) {
-        restore();
-        cudaEventRecord(e0, s);
-        if (solve() != DF_OK) break;
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) break;
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < tmin) tmin = ms;
-      }
-      if (tmin < 1e29f && (!have || tmin < best_t)) {
-        best_t = tmin;
-        *best = c;
-        have = true;
-      }
+  for (const df_tuning &c : cand) {
+    df_set_tuning(&c);
+    if (restore() != DF_OK) continue;
+    if (solve() != DF_OK) {  // e.g. the resident kernel cannot hold these keyframes
+      cudaStreamSynchronize(s);
+      continue;
+    }
+    float ms[kReps];
+    int got = 0;
+    for (int rep = 0; rep < kReps; ++rep) {
+      if (restore() != DF_OK) break;
+      cudaEventRecord(e0, s);
+      if (solve() != DF_OK) break;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) break;
+      float v = 0.0f;
+      cudaEventElapsedTime(&v, e0, e1);
+      ms[got++] = v;
+    }
+    if (got < kReps) {
+      cudaStreamSynchronize(s);
+      continue;
+    }
+    std::sort(ms, ms + kReps);
+    const float med = ms[kReps / 2];
+    if (!have || med < best_t) {
+      best_t = med;
+      *best = c;
+      have = true;
     }
   }
   df_status rs = restore();
   cudaStreamSynchronize(s);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  for (float *q : snap.x) cudaFree(q);
-  if (st != DF_OK) {
-    df_set_tuning(&saved);
-    return st;
-  }
+  free_snap();
   if (!have) {
     df_set_tuning(&saved);
     return df::report(DF_ENOTSUP, "no launch shape could solve these keyframes");

@@ -71,9 +71,14 @@ extern "C" df_status df_optimise_noalloc(int32_t width, int32_t height, const fl
   }
   df_status st = check_solve_params(&p);
   if (st != DF_OK) return st;
-  if (p.scale_step == DF_SCALE_JOINT)
-    return report(DF_ENOTSUP, "df_optimise_noalloc has no scratch plane for DF_SCALE_JOINT");
   if (!mu_semi) p.terms &= ~DF_TERM_SEMI;
+  if (p.scale_step == DF_SCALE_JOINT) {
+    if (p.terms & DF_TERM_SEMI)
+      return report(DF_ENOTSUP, "df_optimise_noalloc has no scratch plane for DF_SCALE_JOINT");
+    // without the semi-dense term the joint system's border row is empty and
+    // t stays where it is: the depth step with t fixed is that solve
+    p.scale_step = DF_SCALE_FIXED;
+  }
   if ((p.terms & (DF_TERM_NET | DF_TERM_GRAD)) == 0)
     return report(DF_EINVAL, "terms must include NET or GRAD");
   NoallocScratch *scr = nullptr;

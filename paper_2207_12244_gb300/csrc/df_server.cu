@@ -283,4 +283,17 @@ df_status df_server_fetch_depth(df_server *s, int32_t sid, float *out, int log_s
   return DF_OK;
 }
 
+df_status df_server_get_state(df_server *s, int32_t sid, float *x_out, double *t_out,
+                              int ptrs_on_device) {
+  if (!s || sid < 0 || sid >= (int32_t)s->streams.size() || !s->streams[sid].kf)
+    return df::report(DF_EINVAL, "no such stream");
+  for (Launch &L : s->launches) cudaStreamSynchronize(L.stream);
+  df_status st = df_keyframe_get_state(s->streams[sid].kf, x_out, t_out, ptrs_on_device,
+                                       s->launches[0].stream);
+  if (st != DF_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(s->launches[0].stream);
+  if (e != cudaSuccess) return df::report(DF_ECUDA, "get state: %s", cudaGetErrorString(e));
+  return DF_OK;
+}
+
 }  // extern "C"

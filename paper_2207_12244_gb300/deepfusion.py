@@ -156,8 +156,10 @@ def load(path: Optional[str] = None) -> C.CDLL:
     L.df_server_pending.argtypes = [vp]
     L.df_server_pending.restype = C.c_int32
     L.df_server_fetch_depth.argtypes = [vp, C.c_int32, vp, C.c_int, C.c_int]
+    L.df_server_get_state.argtypes = [vp, C.c_int32, vp, C.POINTER(C.c_double), C.c_int]
     for name in ("df_server_create", "df_server_open_stream", "df_server_close_stream",
-                 "df_server_submit", "df_server_progress", "df_server_fetch_depth"):
+                 "df_server_submit", "df_server_progress", "df_server_fetch_depth",
+                 "df_server_get_state"):
         getattr(L, name).restype = C.c_int
     L.df_autotune.argtypes = [C.POINTER(vp), C.c_int32, C.POINTER(df_solve_params), vp,
                               C.POINTER(df_tuning), C.POINTER(C.c_float)]
@@ -466,21 +468,73 @@ def df_server_fetch_depth(srv, sid: int, out, log_space: bool = False):
     return out
 
 
+def df_server_get_state(srv, sid: int, x_out=None) -> float:
+    """The stream's log scale t; its log-depth x goes to x_out if given
+    (host or device, H x W float32)."""
+    p, dev = _ptr(x_out)
+    t = C.c_double(0.0)
+    _check(load().df_server_get_state(srv, int(sid), p, C.byref(t), int(dev)),
+           "df_server_get_state")
+    return t.value
+
+
+_NOALLOC_PLANES = ("mu_net", "var_net", "gx", "var_gx", "gy", "var_gy", "mu_semi", "var_semi",
+                   "x_inout")
+
+
+def _noalloc_check(width: int, height: int, bufs) -> None:
+    """Refuse buffers df_optimise_noalloc would read or write out of bounds:
+    the nine planes float32 with at least width*height elements, the scale a
+    float64 tensor with at least one element, every buffer a contiguous CUDA
+    tensor, all on one device. Metadata only: nothing is launched."""
+    import torch
+
+    n = int(width) * int(height)
+    planes, scale = bufs[:9], bufs[9]
+    if any(b is None for b in planes[:6]) or planes[8] is None or scale is None:
+        raise ValueError("df_optimise_noalloc: the network planes, x_inout and scale_log_inout "
+                         "are required")
+    if (planes[6] is None) != (planes[7] is None):
+        raise ValueError("df_optimise_noalloc: mu_semi and var_semi go together")
+    named = [(nm, b) for nm, b in zip(_NOALLOC_PLANES, planes) if b is not None]
+    for nm, b in named + [("scale_log_inout", scale)]:
+        if not isinstance(b, torch.Tensor):
+            raise TypeError(f"df_optimise_noalloc: {nm} must be a torch tensor")
+        if not b.is_contiguous():
+            raise ValueError(f"df_optimise_noalloc: {nm} must be contiguous")
+    for nm, b in named:
+        if b.dtype != torch.float32:
+            raise ValueError(f"df_optimise_noalloc: {nm} must be float32, not {b.dtype}")
+        if b.numel() < n:
+            raise ValueError(f"df_optimise_noalloc: {nm} holds {b.numel()} elements, "
+                             f"fewer than {width} x {height}")
+    if scale.dtype != torch.float64 or scale.numel() < 1:
+        raise ValueError("df_optimise_noalloc: scale_log_inout must be a float64 tensor with "
+                         "at least one element")
+    devs = {b.device for _, b in named} | {scale.device}
+    if any(d.type != "cuda" for d in devs):
+        raise ValueError("df_optimise_noalloc takes device buffers only")
+    if len(devs) != 1:
+        raise ValueError("df_optimise_noalloc: every buffer must be on one device")
+
+
 def df_optimise_noalloc(width: int, height: int, mu_net, var_net, gx, var_gx, gy, var_gy,
                         mu_semi, var_semi, x_inout, scale_log_inout,
                         params: Optional[df_solve_params] = None, stream=None):
     """The solve without device allocation: every buffer is the caller's
-    (CUDA tensors; scale_log_inout a one-element float64 tensor)."""
+    (contiguous CUDA tensors on one device: nine float32 planes of at least
+    width*height elements, scale_log_inout a float64 tensor of one element).
+    The call runs with that device current, on its current stream unless
+    'stream' is given."""
+    import torch
+
     bufs = [mu_net, var_net, gx, var_gx, gy, var_gy, mu_semi, var_semi, x_inout, scale_log_inout]
-    ptrs = []
-    for b in bufs:
-        p, dev = _ptr(b)
-        if b is not None and not dev:
-            raise ValueError("df_optimise_noalloc takes device buffers only")
-        ptrs.append(p)
-    _check(load().df_optimise_noalloc(int(width), int(height), *ptrs,
-                                      C.byref(params) if params is not None else None,
-                                      _stream(stream, x_inout)), "df_optimise_noalloc")
+    _noalloc_check(width, height, bufs)
+    ptrs = [None if b is None else b.data_ptr() for b in bufs]
+    with torch.cuda.device(x_inout.device):
+        _check(load().df_optimise_noalloc(int(width), int(height), *ptrs,
+                                          C.byref(params) if params is not None else None,
+                                          _stream(stream, x_inout)), "df_optimise_noalloc")
 
 
 def df_set_tuning(mode: int = 0, vec: int = 0, tile_rows: int = 0, max_ctas: int = 0,

@@ -244,3 +244,45 @@ def test_host_validation_in_a_forked_child(lib):
     assert not alive, "the forked child hung in the host check"
     st, msg = q.get(timeout=5)
     assert st == dfl.DF_EINVAL and "gy at (u=17, v=500)" in msg, msg
+
+
+def test_noalloc_wrapper_refuses_buffers_it_would_overrun(lib):
+    """The binding of df_optimise_noalloc checks dtypes, sizes, contiguity and
+    devices before the call: a buffer of the wrong type or too few elements
+    would be read or written out of bounds by the kernels."""
+    import torch
+
+    W, H = 8, 6
+    ok = [torch.zeros(H, W) for _ in range(9)]
+    t = torch.zeros(1, dtype=torch.float64)
+
+    def call(planes, scale):
+        dfl.df_optimise_noalloc(W, H, *planes, scale)
+
+    cases = []
+    for j in range(9):  # one plane of the wrong dtype, then one too small
+        p = list(ok)
+        p[j] = torch.zeros(H, W, dtype=torch.float16)
+        cases.append((p, t, "float32"))
+        p = list(ok)
+        p[j] = torch.zeros(H * W - 1)
+        cases.append((p, t, "fewer than"))
+    cases.append((ok, torch.zeros(1, dtype=torch.float32), "float64"))
+    cases.append((ok, torch.zeros(0, dtype=torch.float64), "float64"))
+    p = list(ok)
+    p[0] = torch.zeros(W, H).t()
+    cases.append((p, t, "contiguous"))
+    p = list(ok)
+    p[6] = None
+    cases.append((p, t, "go together"))
+    p = list(ok)
+    p[2] = None
+    cases.append((p, t, "required"))
+    p = list(ok)
+    p[4] = np.zeros((H, W), np.float32)
+    cases.append((p, t, "torch tensor"))
+    cases.append((ok, t, "device buffers only"))  # host tensors
+    for planes, scale, msg in cases:
+        with pytest.raises((ValueError, TypeError)) as e:
+            call(planes, scale)
+        assert msg in str(e.value), (msg, str(e.value))

@@ -470,6 +470,45 @@ def test_autotune_picks_a_shape_and_restores_state(o):
         dfl.df_set_tuning()
 
 
+def test_autotune_refuses_bad_lists_and_leaves_everything_as_it_was():
+    """A NULL or repeated keyframe in the list: DF_EINVAL before anything is
+    allocated or changed; the tuning and every keyframe's (x, t) stay as
+    they were, and device memory in use is unchanged."""
+    torch = torch_cuda()
+    kfs = [synth.make_keyframe(64, 48, 310 + i) for i in range(2)]
+    prm = params(n_gn=2, n_pcg=2, solver=dfl.DF_SOLVER_FUSED)
+    ks = [create(kf) for kf in kfs]
+    try:
+        for k, kf in zip(ks, kfs):
+            k.frame_update(to_dev(kf.mu_s), to_dev(kf.var_s))
+            k.optimise(prm)
+        before = []
+        for k, kf in zip(ks, kfs):
+            xb = np.empty((kf.height, kf.width), np.float32)
+            before.append((xb, k.get_state(xb)))
+        dfl.df_set_tuning(mode=1, vec=1, tile_rows=8)
+        tun0 = dfl.df_get_tuning()
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        a, b = ks[0].handle, ks[1].handle
+        for bad in ([a, None, b], [a, b, a], [None]):
+            with pytest.raises(dfl.DFError) as ei:
+                dfl.df_autotune(bad, prm)
+            assert ei.value.status == dfl.DF_EINVAL
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        tun = dfl.df_get_tuning()
+        assert (tun.mode, tun.vec, tun.tile_rows, tun.gn_per_launch) == (
+            tun0.mode, tun0.vec, tun0.tile_rows, tun0.gn_per_launch)
+        for k, (xb, tb) in zip(ks, before):
+            xa = np.empty_like(xb)
+            assert k.get_state(xa) == tb and np.array_equal(xa, xb)
+    finally:
+        for k in ks:
+            k.close()
+        dfl.df_set_tuning()
+
+
 @pytest.mark.parametrize("sv", [(dfl.DF_SOLVER_LAUNCHES, 0), (dfl.DF_SOLVER_FUSED, 2),
                                 (dfl.DF_SOLVER_FUSED, 1)], ids=["launches", "resident", "streaming"])
 def test_frame_captured_in_a_cuda_graph(sv):

@@ -1,9 +1,10 @@
 """Serving layer on the GPU: continuous batching gives each stream the result
-it gets alone; admission follows the memory budget; every frame completes
-exactly once."""
+(log-depth and scale) it gets alone, and the oracle's; admission follows the
+memory budget; every frame completes exactly once."""
 import numpy as np
 import pytest
 
+import oracle
 from gpu_util import DEPTH_RTOL, SCALE_ATOL, assert_parity, create, params, to_dev, torch_cuda
 from paper_2207_12244_gb300 import deepfusion as dfl
 from paper_2207_12244_gb300 import serving, synth
@@ -11,6 +12,12 @@ from paper_2207_12244_gb300 import serving, synth
 pytestmark = pytest.mark.gpu
 
 SIZES = [(64, 48), (96, 72), (40, 30), (128, 96), (64, 48), (80, 60)]
+
+
+@pytest.fixture(scope="module")
+def o():
+    return oracle.get()
+
 NF = 4
 
 
@@ -37,7 +44,7 @@ def _alone(kf, frames, prm):
 
 
 @pytest.mark.parametrize("batching", [True, False], ids=["batched", "plain"])
-def test_each_result_is_the_same_alone_and_in_the_mix(batching):
+def test_each_result_is_the_same_alone_and_in_the_mix(o, batching):
     torch = torch_cuda()
     prm = params(n_gn=10, n_pcg=5, solver=dfl.DF_SOLVER_AUTO)
     seqs, frames = _streams()
@@ -53,13 +60,25 @@ def test_each_result_is_the_same_alone_and_in_the_mix(batching):
         assert st.n == len(SIZES) * NF
         if batching:
             assert st.mean_batch > 1.0  # frames really were solved together
+        mode = "batched" if batching else "plain"
         for i, (kf, _, _) in enumerate(seqs):
             out = torch.empty((kf.height, kf.width), dtype=torch.float32, device="cuda")
             dfl.df_server_fetch_depth(srv, sids[i], out, log_space=True)
             x = out.double().cpu().numpy()
+            xs = torch.empty_like(out)
+            t = dfl.df_server_get_state(srv, sids[i], xs)
+            assert torch.equal(xs, out)  # the state's x is the fetched log-depth
             xa, ta = _alone(kf, frames[i], prm)
-            assert_parity(x, ta, xa, ta, rtol=DEPTH_RTOL, atol_t=SCALE_ATOL,
-                          what=f"stream {i} {'batched' if batching else 'plain'}")
+            assert t != 0.0  # the scale step moved t
+            assert_parity(x, t, xa, ta, rtol=DEPTH_RTOL, atol_t=SCALE_ATOL,
+                          what=f"stream {i} {mode}")
+        # one stream against the FP64 oracle over the same frames in order
+        i = 3
+        kf, mus, vs = seqs[i]
+        x = torch.empty((kf.height, kf.width), dtype=torch.float32, device="cuda")
+        t = dfl.df_server_get_state(srv, sids[i], x)
+        xo, to = o.optimise_sequence(kf, mus, vs, n_gn=prm.n_gn, n_pcg=prm.n_pcg)
+        assert_parity(x.double().cpu().numpy(), t, xo, to, what=f"stream {i} {mode} vs oracle")
     finally:
         dfl.df_server_destroy(srv)
 
