@@ -1,18 +1,22 @@
 #!/usr/bin/env python
 """Throughput of the per-frame keyframe re-optimisation on GB300.
 
-Workload (one "step"): a 640 x 480 FP32 keyframe re-optimised over a
-100-frame synthetic sequence. The semi-dense mask grows from 5 % to 40 % and
-variances shrink by Gaussian fusion. Each frame runs 10 Gauss-Newton x 5 PCG
-iterations. A step covers every stage of the path: keyframe (re)initialisation
-from the network planes, then per frame the semi-dense refresh, the solve
-(scale step, re-weighting / assembly, PCG) and the depth output.
+Default workload (one "step"): 64 keyframes of uneven sizes drawn from
+{320x240, 512x384, 640x480, 1280x960} (30.5 Mpixel), each its own synthetic
+scene, re-optimised together for one frame: keyframe (re)initialisation from
+the network planes, the frame's semi-dense refresh, one batched solve of
+10 Gauss-Newton x 3 PCG iterations (scale step, re-weighting / assembly,
+PCG) in one persistent launch replayed from a CUDA graph with an autotuned
+launch shape, and the depth output. Beside it the same keyframes are solved
+by the plain path, one df_optimise launch per keyframe, and both results are
+checked to agree.
 
-Metric: Mpixel.iter/s = sum over frames of H*W*n_gn*n_pcg / time / 1e6.
+Metric: Mpixel.iter/s = sum over keyframes of H*W*n_gn*n_pcg / time / 1e6.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload batch64|sequence|precision|serving|mvs]
 
-With N > 1 (torchrun, one rank per GPU) every rank solves its own sequence
+With N > 1 (torchrun, one rank per GPU) every rank solves its own keyframes
 (weak scaling, no collective on the data path); value = all ranks' units /
 max-over-ranks time.
 """
@@ -21,7 +25,9 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import multiprocessing as mp
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -74,10 +80,10 @@ def parse():
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on the fused kernel's grid")
     ap.add_argument("--vec", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
-    ap.add_argument("--workload", choices=["sequence", "batch64", "precision", "serving", "mvs"],
-                    default="sequence",
-                    help="sequence: 640x480 keyframe over 100 frames (default); batch64: 64 "
-                         "keyframes of uneven sizes in one batched solve; precision: one "
+    ap.add_argument("--workload", choices=["batch64", "sequence", "precision", "serving", "mvs"],
+                    default="batch64",
+                    help="batch64: 64 keyframes of uneven sizes in one batched solve (default); "
+                         "sequence: a 640x480 keyframe over 100 frames; precision: one "
                          "1920x1440 keyframe with reduced-precision network planes")
     ap.add_argument("--cnn-dtype", choices=["f32", "bf16", "f16"], default="bf16",
                     help="network-plane storage for --workload precision")
@@ -258,20 +264,199 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_reference(args, ws, rank):
-    """The oracle (FP64 CPU) on a bounded sample of the same workload."""
-    if rank != 0:
-        return
+L2_NOTE = "flushed between steps (256 MB write)"
+
+
+def sequence_config(args, ws):
+    """config of the sequence workload (the same in both arms)."""
+    return {"workload": sequence_name(args), "width": args.width, "height": args.height,
+            "frames": args.frames, "n_gn": args.n_gn, "n_pcg": args.n_pcg, "loss": args.loss,
+            "scale_step": args.scale_step, "parallelism": f"replicas x{ws}", "l2": L2_NOTE}
+
+
+def keyframe_shapes(args, rank):
+    """(name, [(W, H)], network-plane dtype name) of a keyframe workload."""
+    if args.workload == "batch64":
+        shapes = synth_batch_shapes(64, rank_seed(args.seed, rank))
+        return f"batch64-uneven-{args.n_gn}x{args.n_pcg}-fp32", shapes, "f32"
+    return (f"keyframe-1920x1440-{args.n_gn}x{args.n_pcg}-{args.cnn_dtype}", [(1920, 1440)],
+            args.cnn_dtype)
+
+
+def keyframe_seeds(args, rank, shapes):
+    base = rank_seed(args.seed, rank)
+    return [base + 17 * i for i in range(len(shapes))]
+
+
+def keyframes_config(args, ws, rank=0):
+    """config of the batch / large-keyframe workloads (the same in both arms)."""
+    name, shapes, dt_name = keyframe_shapes(args, rank)
+    return {"workload": name, "keyframes": len(shapes), "pixels": sum(W * H for W, H in shapes),
+            "cnn_dtype": dt_name, "n_gn": args.n_gn, "n_pcg": args.n_pcg, "loss": args.loss,
+            "parallelism": f"replicas x{ws}", "l2": L2_NOTE}
+
+
+def synth_batch_shapes(n, seed):
+    from paper_2207_12244_gb300 import synth
+
+    return synth.batch_shapes(n, seed)
+
+
+def rank_seed(base, rank):
+    from paper_2207_12244_gb300 import replicas
+
+    return replicas.rank_seed(base, rank)
+
+
+def host_cpu():
+    """(model name, usable cores) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    return f"{model or 'unknown'} ({platform.machine()})", cores
+
+
+def _shares(sizes, n_workers):
+    """Largest-first greedy split of jobs over workers (balanced work)."""
+    loads = [0] * n_workers
+    shares = [[] for _ in range(n_workers)]
+    for i in sorted(range(len(sizes)), key=lambda j: -sizes[j]):
+        w = min(range(n_workers), key=lambda k: loads[k])
+        shares[w].append(i)
+        loads[w] += sizes[i]
+    return [sh for sh in shares if sh]
+
+
+def _oracle_worker(conn, jobs, solve_kw):
+    """Pool worker: generate its keyframes once, then solve them all with the
+    oracle (single thread) whenever the parent asks; reply the busy time."""
     import oracle
     from paper_2207_12244_gb300 import synth
 
     o = oracle.get()
-    kf, mus, vs = synth.make_sequence(args.width, args.height, args.seed, args.frames)
-    px_iters = args.width * args.height * args.n_gn * args.n_pcg
+    kfs = [synth.make_keyframe(W, H, seed) for W, H, seed in jobs]
+    conn.send(0.0)
+    while True:
+        msg = conn.recv()
+        if msg is None:
+            break
+        t0 = time.perf_counter()
+        for kf in kfs:
+            o.optimise(kf, **solve_kw)
+        conn.send(time.perf_counter() - t0)
+    conn.close()
+
+
+class OraclePool:
+    """The oracle over independent keyframes on every host core: one spawned
+    process per core, each solving a fixed share of the keyframes (the
+    arithmetic of each solve is the oracle's, unchanged)."""
+
+    def __init__(self, jobs, solve_kw, n_workers):
+        import oracle
+
+        oracle.build()  # once, before the workers load it
+        ctx = mp.get_context("spawn")
+        self.shares = _shares([W * H for W, H, _ in jobs], max(1, n_workers))
+        self.procs, self.conns = [], []
+        for share in self.shares:
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, [jobs[i] for i in share], solve_kw),
+                            daemon=True)
+            p.start()
+            b.close()
+            self.procs.append(p)
+            self.conns.append(a)
+        for c in self.conns:
+            c.recv()
+
+    def solve_all(self):
+        """Wall time of one pass over every keyframe, and each worker's busy time."""
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send(1)
+        busy = [c.recv() for c in self.conns]
+        return time.perf_counter() - t0, busy
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(None)
+            except OSError:
+                pass
+        for p in self.procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.terminate()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def keyframe_pool(args, rank, n_workers=None):
+    """An OraclePool over the keyframes of a batch / large-keyframe workload."""
+    _, shapes, _ = keyframe_shapes(args, rank)
+    seeds = keyframe_seeds(args, rank, shapes)
+    jobs = [(W, H, sd) for (W, H), sd in zip(shapes, seeds)]
+    kw = dict(n_gn=args.n_gn, n_pcg=args.n_pcg, **loss_params(args))
+    model, cores = host_cpu()
+    n = min(cores, len(jobs)) if n_workers is None else n_workers
+    return OraclePool(jobs, kw, n), model, cores
+
+
+def keyframes_cpu_baseline(args, rank, passes=1):
+    """The oracle on every host core over the workload's keyframes: `passes`
+    timed passes over all of them (a batch pass is ~20 s of CPU work)."""
+    pool, model, cores = keyframe_pool(args, rank)
+    _, shapes, _ = keyframe_shapes(args, rank)
+    units = sum(W * H for W, H in shapes) * args.n_gn * args.n_pcg
+    with pool:
+        walls, busy = [], []
+        for _ in range(passes):
+            w, b = pool.solve_all()
+            walls.append(w)
+            busy.extend(b)
+    return {"value": units * passes / sum(walls) / 1e6, "unit": METRIC,
+            "cores": len(pool.shares), "kind": "oracle", "cpu_model": model, "host_cores": cores,
+            "single_thread_value": units * passes / sum(busy) / 1e6,
+            "sample": f"{passes} pass(es) over all {len(shapes)} keyframes of the workload, "
+                      f"{args.n_gn}x{args.n_pcg}, FP64 on the FP32 inputs; one spawned process "
+                      f"per core, each a fixed share of the keyframes; {sum(walls):.1f} s wall, "
+                      f"{sum(busy):.1f} s of CPU work; single_thread_value = the same work over "
+                      f"the workers' summed busy time"}
+
+
+def _sequence_reference(args, kf, mus, vs, n_frames):
+    """The oracle over the first frames of a warm-started sequence, one frame
+    per step: (per-step seconds of the timed steps)."""
+    import oracle
+
+    o = oracle.get()
     x = kf.mu_n.astype(np.float64).ravel()
     t = 0.0
     times = []
-    f = 0
 
     class _V:
         pass
@@ -280,35 +465,90 @@ def run_reference(args, ws, rank):
     for n in ("width", "height", "mu_n", "var_n", "gx", "var_gx", "gy", "var_gy"):
         setattr(view, n, getattr(kf, n))
     for step in range(args.warmup + args.steps):
-        view.mu_s, view.var_s = mus[f % args.frames], vs[f % args.frames]
+        view.mu_s, view.var_s = mus[step % n_frames], vs[step % n_frames]
         t0 = time.perf_counter()
         xr, t, _ = o.optimise(view, x0=x, t0=t, n_gn=args.n_gn, n_pcg=args.n_pcg,
                                scale_step=SCALE_STEPS[args.scale_step], **loss_params(args))
         dt = time.perf_counter() - t0
         x = xr.ravel()
-        f += 1
         if step >= args.warmup:
             times.append(dt)
-    value = px_iters * len(times) / sum(times) / 1e6
-    sample = (f"{args.steps} timed frames (after {args.warmup} warm-up) of the "
-              f"{args.width}x{args.height} sequence, {args.n_gn}x{args.n_pcg} per frame, "
-              "warm-started; one frame per step")
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": sequence_name(args), "width": args.width, "height": args.height,
-                   "frames_per_step": 1, "n_gn": args.n_gn, "n_pcg": args.n_pcg, "loss": args.loss,
-                   "scale_step": args.scale_step},
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
+    return times
+
+
+def run_reference(args, ws, rank):
+    """The reference arm: the oracle (FP64, CPU) on the same workload and
+    config as our arm, on the host cores of this machine. Rank 0 only."""
+    if rank != 0:
+        return
+    from paper_2207_12244_gb300 import synth
+
+    model, cores = host_cpu()
+    line = {"impl": "reference", "metric": METRIC, "unit": METRIC, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "l2_note": "config.l2 states how our arm times the GPU; the oracle runs on the host"}
+    if args.workload in ("batch64", "precision"):
+        line["config"] = keyframes_config(args, ws)
+        pool, model, cores = keyframe_pool(args, rank)
+        _, shapes, _ = keyframe_shapes(args, rank)
+        units = sum(W * H for W, H in shapes) * args.n_gn * args.n_pcg
+        with pool:
+            for _ in range(args.warmup):
+                pool.solve_all()
+            walls = [pool.solve_all()[0] for _ in range(args.steps)]
+        value = units * len(walls) / sum(walls) / 1e6
+        n_used = len(pool.shares)
+        sample = (f"every step: all {len(shapes)} keyframes of the workload, {args.n_gn}x"
+                  f"{args.n_pcg}, one spawned process per core with a fixed share of them")
+    elif args.workload == "mvs":  # one stereo update (first reference view) per step
+        import oracle
+
+        o = oracle.get()
+        W, H = args.width, args.height
+        p = synth.make_stereo_pair(W, H, rank_seed(args.seed, 0), baseline=0.03, view=0)
+        walls = []
+        for step in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            o.semi_dense(p.img_key, p.img_ref, p.cam, p.R, p.t)
+            if step >= args.warmup:
+                walls.append(time.perf_counter() - t0)
+        line.update({"metric": "Mpixel/s", "unit": "Mpixel/s", "config": mvs_config(args, ws)})
+        value = W * H * len(walls) / sum(walls) / 1e6
+        n_used = 1
+        sample = f"one {W}x{H} stereo update (first reference view) per step, FP64"
+    else:
+        if args.workload == "serving":  # the frames of the first 640x480 stream, in order
+            kf, mus, vs = synth.make_sequence(640, 480, rank_seed(args.seed, 0), n_frames=8)
+            n_frames = 8
+            px_iters = 640 * 480 * 10 * 5
+            args.n_gn, args.n_pcg = 10, 5
+            line["config"] = serving_config(args, ws)
+            sample = "the frames of one 640x480 stream in order, 10x5 per frame, warm-started"
+        else:
+            kf, mus, vs = synth.make_sequence(args.width, args.height, args.seed, args.frames)
+            n_frames = args.frames
+            px_iters = args.width * args.height * args.n_gn * args.n_pcg
+            line["config"] = sequence_config(args, ws)
+            sample = (f"{args.steps} timed frames (after {args.warmup} warm-up) of the "
+                      f"{args.width}x{args.height} sequence, {args.n_gn}x{args.n_pcg} per frame, "
+                      "warm-started; one frame per step (frames depend on each other)")
+        times = _sequence_reference(args, kf, mus, vs, n_frames)
+        walls = times
+        value = px_iters * len(times) / sum(times) / 1e6
+        n_used = 1
+    line.update({
+        "value": value, "ms_per_step": 1e3 * sum(walls) / len(walls),
+        "cpu_baseline": {"value": value, "unit": line["unit"], "cores": n_used, "kind": "oracle",
+                         "cpu_model": model, "host_cores": cores, "sample": sample},
+        "e2e": {"value": value, "unit": line["unit"], "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    })
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline(args, kf, mus, vs):
+    """The oracle on the sequence (frames depend on each other: one core)."""
     import oracle
 
     o = oracle.get()
@@ -333,9 +573,24 @@ def cpu_baseline(args, kf, mus, vs):
         if el >= args.cpu_seconds or n >= args.frames:
             break
     px_iters = args.width * args.height * args.n_gn * args.n_pcg * n
+    model, cores = host_cpu()
     return {"value": px_iters / el / 1e6, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "cpu_model": model, "host_cores": cores,
             "sample": f"first {n} frames of the same {args.width}x{args.height} sequence, "
-                      f"{args.n_gn}x{args.n_pcg} per frame, warm-started, {el:.1f} s single-thread"}
+                      f"{args.n_gn}x{args.n_pcg} per frame, warm-started, {el:.1f} s single-thread "
+                      "(each frame starts from the previous one's result, so one core)"}
+
+
+def mvs_config(args, ws):
+    W, H, F = args.width, args.height, min(args.frames, 8)
+    return {"workload": f"mvs-{W}x{H}-{F}views", "width": W, "height": H, "views": F,
+            "parallelism": f"replicas x{ws}", "l2": L2_NOTE}
+
+
+def serving_config(args, ws):
+    return {"workload": "serving-32streams-640x480+1280x960-poisson-10x5",
+            "offered_frames_per_s": args.rate, "frames": args.requests,
+            "budget_bytes": 40 << 30, "parallelism": f"replicas x{ws}"}
 
 
 def run_serving(args, ws, rank, dev, torch, dfl, replicas, synth):
@@ -388,9 +643,7 @@ def run_serving(args, ws, rank, dev, torch, dfl, replicas, synth):
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
-            "config": {"workload": "serving-32streams-640x480+1280x960-poisson-10x5",
-                       "offered_frames_per_s": args.rate, "frames": args.requests,
-                       "budget_bytes": 40 << 30, "parallelism": f"replicas x{ws}"},
+            "config": serving_config(args, ws),
             "update_latency_ms": {"batched": results["batched"], "plain": results["plain"],
                                   "what": "arrival (submit) to finished (event seen), host clock"},
             "e2e": None, "roofline": None, "cpu_baseline": None,
@@ -513,7 +766,9 @@ def run_mvs(args, ws, rank, dev, torch, dfl, replicas, synth):
         t0 = time.perf_counter()
         o.semi_dense(p.img_key, p.img_ref, p.cam, p.R, p.t)
         el = time.perf_counter() - t0
+        model, host_cores = host_cpu()
         cpu = {"value": W * H / el / 1e6, "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+               "cpu_model": model, "host_cores": host_cores,
                "sample": f"one {W}x{H} update (first reference view), {el:.2f} s single-thread FP64"}
     m.close()
     if rank == 0:
@@ -522,9 +777,7 @@ def run_mvs(args, ws, rank, dev, torch, dfl, replicas, synth):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (two rendered views of a textured piecewise-planar scene)",
-            "config": {"workload": name, "width": W, "height": H, "views": F,
-                       "parallelism": f"replicas x{ws}",
-                       "l2": "flushed between steps (256 MB write)"},
+            "config": mvs_config(args, ws),
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu,
             "update_latency_ms": {"p50": float(np.percentile(upd_ms, 50)),
@@ -535,22 +788,19 @@ def run_mvs(args, ws, rank, dev, torch, dfl, replicas, synth):
 
 
 def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
-    """Batched / large-keyframe workloads: one solve of all keyframes per step."""
+    """Batched / large-keyframe workloads: one solve of all keyframes per step.
+
+    For the 64-keyframe batch a second, plain leg solves the same keyframes
+    from the same state with one df_optimise launch per keyframe; both legs'
+    depth maps are compared after the timed regions."""
     import torch.distributed as dist
 
     n_gn, n_pcg = args.n_gn, args.n_pcg
-    if args.workload == "batch64":
-        shapes = synth.batch_shapes(64, replicas.rank_seed(args.seed, rank))
-        dt_name = "f32"
-        name = f"batch64-uneven-{n_gn}x{n_pcg}-fp32"
-    else:
-        shapes = [(1920, 1440)]
-        dt_name = args.cnn_dtype
-        name = f"keyframe-1920x1440-{n_gn}x{n_pcg}-{dt_name}"
+    name, shapes, dt_name = keyframe_shapes(args, rank)
     code = {"f32": dfl.DF_F32, "bf16": dfl.DF_BF16, "f16": dfl.DF_F16}[dt_name]
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dt_name]
-    base = replicas.rank_seed(args.seed, rank)
-    kfs = [synth.make_keyframe(W, H, base + 17 * i) for i, (W, H) in enumerate(shapes)]
+    seeds = keyframe_seeds(args, rank, shapes)
+    kfs = [synth.make_keyframe(W, H, sd) for (W, H), sd in zip(shapes, seeds)]
     cnn_d = [[torch.from_numpy(p).to(tdt).to(dev) for p in kf.cnn_planes] for kf in kfs]
     semi_d = [(torch.from_numpy(kf.mu_s).to(dev), torch.from_numpy(kf.var_s).to(dev)) for kf in kfs]
     outs = [torch.empty((kf.height, kf.width), dtype=torch.float32, device=dev) for kf in kfs]
@@ -565,6 +815,10 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
 
+    def forced_tuning():
+        dfl.df_set_tuning(mode={"auto": 0, "streaming": 1, "resident": 2}[args.mode],
+                          vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas)
+
     graph = None
     graph_launches = 0
     tuning = None
@@ -575,10 +829,13 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
         else:
             dfl.df_optimise_batch(handles, prm, stream=sptr)
 
-    def step(record):
+    def load_frame():
         for k, c, (ms, vs) in zip(ks, cnn_d, semi_d):
             k.reset(*c, stream=sptr)
             k.frame_update(ms, vs, stream=sptr)
+
+    def step(record):
+        load_frame()
         if record:
             ev[0].record(stream)
         solve()
@@ -684,44 +941,99 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
         e2e = {"value": units * args.steps * ws / (tot / 1e3) / 1e6, "unit": METRIC,
                "h2d_bytes_per_step": int(px * (6 * esz + 8)), "d2h_bytes_per_step": int(px * 4),
                "ms_per_step": tot / args.steps}
+
+    # the batched result of one more (untimed) step, kept for the comparison
+    with torch.cuda.stream(stream):
+        step(False)
+    torch.cuda.synchronize()
+    batched_depth = [o.clone() for o in outs]
+
+    plain = None
+    if args.workload == "batch64":
+        # the plain path: one df_optimise launch per keyframe, in list order,
+        # with the library's default launch shape (not the batch's tuning)
+        forced_tuning()
+        evk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in ks]
+
+        def plain_solve(record):
+            for j, k in enumerate(ks):
+                if record:
+                    evk[j][0].record(stream)
+                k.optimise(prm, stream=sptr)
+                if record:
+                    evk[j][1].record(stream)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                load_frame()
+                plain_solve(False)
+        torch.cuda.synchronize()
+        plain_ms, per_kf_ms = [], []
+        p_launches0 = dfl.df_kernel_launches()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            if ws > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                load_frame()
+                e0.record(stream)
+                plain_solve(True)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            plain_ms.append(e0.elapsed_time(e1))
+            per_kf_ms.extend(a.elapsed_time(b) for a, b in evk)
+        p_launches = dfl.df_kernel_launches() - p_launches0
+        # same accuracy: the plain leg's depth against the batched leg's
+        for k, o in zip(ks, outs):
+            k.fetch_depth(o, stream=sptr)
+        torch.cuda.synchronize()
+        diff = max(float(((o.double() / b.double()) - 1.0).abs().max())
+                   for o, b in zip(outs, batched_depth))
+        plain_tot = replicas.max_over_ranks(sum(plain_ms), device=dev)
+        plain = {"p50": float(np.percentile(plain_ms, 50)), "p99": float(np.percentile(plain_ms, 99)),
+                 "value": units * args.steps * ws / (plain_tot / 1e3) / 1e6, "unit": METRIC,
+                 "per_keyframe_p50": float(np.percentile(per_kf_ms, 50)),
+                 "per_keyframe_p99": float(np.percentile(per_kf_ms, 99)),
+                 "gpu_launches_per_step": p_launches / args.steps,
+                 "max_rel_depth_diff_vs_batched": diff,
+                 "same_accuracy": bool(diff <= 1e-4),
+                 "what": f"the same {len(ks)} keyframes from the same state, one df_optimise "
+                         "launch per keyframe (default launch shape), eager; p50/p99 = device "
+                         "time until all keyframes are solved; per_keyframe = one launch"}
+        if diff > 1e-4:
+            raise RuntimeError(f"plain and batched depth maps differ by {diff:.3g} (> 1e-4)")
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        import oracle
-
-        o = oracle.get()
-        kf = kfs[0]
-        t0 = time.perf_counter()
-        o.optimise(kf, n_gn=n_gn, n_pcg=n_pcg, **loss_params(args))
-        el = time.perf_counter() - t0
-        cpu = {"value": kf.width * kf.height * n_gn * n_pcg / el / 1e6, "unit": METRIC,
-               "cores": 1, "kind": "oracle",
-               "sample": f"one {kf.width}x{kf.height} keyframe of the workload, {n_gn}x{n_pcg}, "
-                         f"{el:.1f} s single-thread (FP64 on the FP32 inputs)"}
+        cpu = keyframes_cpu_baseline(args, rank)
     used_graph = graph is not None
     if used_graph:
         graph = None
         dfl.df_batch_release(handles)
-    dfl.df_set_tuning(mode={"auto": 0, "streaming": 1, "resident": 2}[args.mode],
-                      vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas)
+    forced_tuning()
     for k in ks:
         k.close()
     if rank == 0:
+        lat = {"p50": float(np.percentile(solve_ms, 50)), "p99": float(np.percentile(solve_ms, 99)),
+               "what": "one batched solve of every keyframe, device time"}
+        if plain is not None:
+            lat = {"batched": lat, "plain": plain}
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
-            "config": {"workload": name, "keyframes": len(shapes), "pixels": px,
-                       "cnn_dtype": dt_name, "n_gn": n_gn, "n_pcg": n_pcg, "loss": args.loss,
-                       "solver": args.solver,
-                       "cuda_graph": used_graph, "autotuned": tuning,
+            "config": keyframes_config(args, ws, rank),
+            "launch": {"solver": args.solver, "cuda_graph": used_graph, "autotuned": tuning,
                        "kernel_mode": args.mode, "max_ctas": args.max_ctas,
-                       "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MB write)"},
+                       "vec": args.vec, "tile_rows": args.tile_rows},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu,
-            "update_latency_ms": {"p50": float(np.percentile(solve_ms, 50)),
-                                  "p99": float(np.percentile(solve_ms, 99)),
-                                  "what": "one batched solve, device time"},
+            "update_latency_ms": lat,
             "hbm_frac": roofline["frac"],
         }
         print(json.dumps(line), flush=True)
@@ -943,13 +1255,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded piecewise-planar scenes; no dataset)",
-            "config": {"workload": sequence_name(args), "width": W, "height": H, "frames": F,
-                       "n_gn": args.n_gn, "n_pcg": args.n_pcg, "loss": args.loss,
-                       "solver": args.solver,
-                       "scale_step": args.scale_step, "cuda_graph": bool(args.graph),
+            "config": sequence_config(args, ws),
+            "launch": {"solver": args.solver, "cuda_graph": bool(args.graph),
                        "kernel_mode": args.mode, "max_ctas": args.max_ctas,
-                       "parallelism": f"replicas x{ws}",
-                       "l2": "flushed between steps (256 MB write)"},
+                       "vec": args.vec, "tile_rows": args.tile_rows},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu, "accuracy": accuracy,
             "update_latency_ms": {"p50": float(lat[0]), "p99": float(lat[1]),
