@@ -68,9 +68,9 @@ def parse():
     ap.add_argument("--n-pcg", type=int, default=None,
                     help="PCG iterations per GN iteration (default: the workload's, 5 for the "
                          "sequence, 3 for the keyframe workloads)")
-    ap.add_argument("--loss", choices=["huber", "lsq", "tukey"], default="huber",
-                    help="robust loss: Huber (delta 1.345, the default), least squares, or "
-                         "Tukey's biweight (c 4.685)")
+    ap.add_argument("--loss", choices=["huber", "lsq", "tukey", "huber-tukey"], default="huber",
+                    help="robust loss: Huber (delta 1.345, the default), least squares, "
+                         "Tukey's biweight (c 4.685), or 3 Huber GN iterations then Tukey")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -105,14 +105,19 @@ def parse():
     return args
 
 
-# (delta, loss code) of each --loss choice: the C ABI's df_solve_params
-# fields and the oracle's keyword arguments take the same values
-LOSSES = {"huber": (1.345, 0), "lsq": (0.0, 0), "tukey": (4.685, 1)}
+# (delta, loss code, Huber warm-start GN iterations) of each --loss choice:
+# the C ABI's df_solve_params fields and the oracle's keyword arguments take
+# the same values
+LOSSES = {"huber": (1.345, 0, 0), "lsq": (0.0, 0, 0), "tukey": (4.685, 1, 0),
+          "huber-tukey": (4.685, 1, 3)}
 
 
 def loss_params(args):
-    delta, loss = LOSSES[args.loss]
-    return {"delta": delta, "loss": loss}
+    delta, loss, warm = LOSSES[args.loss]
+    kw = {"delta": delta, "loss": loss}
+    if warm:
+        kw.update(warm_gn=warm, warm_delta=1.345)
+    return kw
 
 
 def dist_env():

@@ -104,6 +104,13 @@ typedef struct {
   int32_t solver;     /* DF_SOLVER_* */
   double tol;         /* > 0: end a depth step once ||r|| < tol ||b||;
                          0: fixed iteration count */
+  int32_t warm_gn;    /* the first warm_gn GN iterations use the Huber loss
+                         with threshold warm_delta, the remaining ones 'loss'
+                         with 'delta': Tukey's biweight (Section IV) is not
+                         convex, so it is started from Huber iterations;
+                         0: every iteration uses 'loss' */
+  float warm_delta;   /* Huber threshold of the warm iterations (<= 0 or +inf:
+                         least squares) */
 } df_solve_params;
 
 typedef struct {
@@ -116,7 +123,8 @@ typedef struct {
 typedef struct df_keyframe df_keyframe; /* opaque; owns its device memory */
 
 /* Fill 'p' with the paper's schedule: n_gn = 10 (Section II-C), n_pcg = 3,
- * Huber with delta = 1.345, all terms, scale step on, AUTO solver, tol = 0. */
+ * Huber with delta = 1.345, all terms, scale step on, AUTO solver, tol = 0,
+ * no warm start (warm_gn = 0, warm_delta = 1.345). */
 void df_default_params(df_solve_params *p);
 
 /* Create a keyframe from the network's per-keyframe outputs (Section II:

@@ -60,7 +60,7 @@ MVS_OK, MVS_FLAT, MVS_INTERVAL, MVS_LINE, MVS_NOSTEP, MVS_SSD, MVS_NEIGHBOUR = r
 class _Params(C.Structure):
     _fields_ = [("n_gn", C.c_int32), ("n_pcg", C.c_int32), ("delta", C.c_double),
                 ("tol", C.c_double), ("terms", C.c_int32), ("loss", C.c_int32),
-                ("scale_step", C.c_int32)]
+                ("scale_step", C.c_int32), ("warm_gn", C.c_int32), ("warm_delta", C.c_double)]
 
 
 class _Report(C.Structure):
@@ -197,12 +197,16 @@ class Oracle:
     # -- the per-frame solve -------------------------------------------------
     def optimise(self, kf, x0=None, t0: float = 0.0, n_gn: int = 10, n_pcg: int = 3,
                  delta: float = HUBER_DELTA, tol: float = 0.0, terms: int = TERMS_ALL,
-                 loss: int = LOSS_HUBER, scale_step: int = SCALE_ALTERNATE, trace: bool = False):
+                 loss: int = LOSS_HUBER, scale_step: int = SCALE_ALTERNATE, trace: bool = False,
+                 warm_gn: int = 0, warm_delta: float = HUBER_DELTA):
         """Run the schedule from (x0, t0); x0 defaults to mu_n (keyframe init).
 
         scale_step: SCALE_FIXED (t kept), SCALE_ALTERNATE (scale half, then
         depth half, per GN iteration) or SCALE_JOINT (bordered PCG in (x, t));
         True / False mean SCALE_ALTERNATE / SCALE_FIXED.
+        warm_gn: the first warm_gn GN iterations use the Huber loss with
+        threshold warm_delta, the others ``loss`` with ``delta``. The cost
+        trace is always the cost of ``loss`` with ``delta``.
 
         Returns (x [H, W] float64, t, Report[, cost trace of 2*n_gn+1 values]).
         """
@@ -210,7 +214,7 @@ class Oracle:
         x = _f64(kf.mu_n if x0 is None else x0).copy()
         t = C.c_double(float(t0))
         prm = _Params(int(n_gn), int(n_pcg), float(delta), float(tol), int(terms),
-                      int(loss), int(scale_step))
+                      int(loss), int(scale_step), int(warm_gn), float(warm_delta))
         rep = _Report()
         tr = np.zeros(2 * int(n_gn) + 1) if trace else None
         self.lib.orc_optimise(C.byref(prob), _dp(x), C.byref(t), C.byref(prm), C.byref(rep),

@@ -91,6 +91,10 @@ typedef struct {
   int32_t loss;       /* ORC_LOSS_* */
   int32_t scale_step; /* 0: t fixed; 1: scale half, then depth half, in each GN
                          iteration; 2: one PCG on the bordered system in (x, t) */
+  int32_t warm_gn;    /* the first warm_gn GN iterations use the Huber loss with
+                         threshold warm_delta (a convex start for the
+                         non-convex Tukey loss, Section IV); 0: none */
+  double warm_delta;
 } orc_params;
 
 typedef struct {
@@ -468,13 +472,25 @@ int32_t orc_optimise(const orc_problem *P, double *x, double *t,
   const int joint = prm->scale_step == 2 && (prm->terms & ORC_TERM_SEMI);
   double *ws = joint ? (double *)malloc(sizeof(double) * (size_t)N) : NULL;
   for (int k = 0; k < prm->n_gn; ++k) {
+    /* the loss of this GN iteration: Huber during the warm start */
+#if ORC_MUTANT == 15
+    const int warm = k <= prm->warm_gn && prm->warm_gn > 0;
+#else
+    const int warm = k < prm->warm_gn;
+#endif
+#if ORC_MUTANT == 16
+    const double dk = prm->delta;
+#else
+    const double dk = warm ? prm->warm_delta : prm->delta;
+#endif
+    const int32_t lk = warm ? ORC_LOSS_HUBER : prm->loss;
     if ((prm->terms & ORC_TERM_SEMI) && prm->scale_step == 1)
-      *t = orc_scale_step(P, x, *t, prm->delta, prm->loss);
+      *t = orc_scale_step(P, x, *t, dk, lk);
     if (cost_trace)
       cost_trace[2 * k + 1] = orc_cost(P, x, *t, prm->delta, prm->terms, prm->loss);
-    orc_assemble(P, x, *t, prm->delta, prm->terms, prm->loss, diag, wx, wy, b);
+    orc_assemble(P, x, *t, dk, prm->terms, lk, diag, wx, wy, b);
     if (joint) {
-      semi_weights(P, x, *t, prm->delta, prm->terms, prm->loss, ws);
+      semi_weights(P, x, *t, dk, prm->terms, lk, ws);
       iters += orc_pcg_joint(W, H, diag, wx, wy, ws, P->mu_s, b, x, t, prm->n_pcg, prm->tol, &rn);
     } else {
       iters += orc_pcg(W, H, diag, wx, wy, b, x, prm->n_pcg, prm->tol, &rn);

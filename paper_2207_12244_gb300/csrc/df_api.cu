@@ -360,8 +360,11 @@ df_status check_params(const df_solve_params *p) {
     return fail(DF_EINVAL, "unknown scale_step %d", p->scale_step);
   if (!(p->tol >= 0.0) || !isfinite(p->tol)) return fail(DF_EINVAL, "tol must be finite >= 0");
   if (isnan(p->delta)) return fail(DF_EINVAL, "delta is NaN");
+  if (p->warm_gn < 0) return fail(DF_EINVAL, "warm_gn must be >= 0");
+  if (p->warm_gn > 0 && isnan(p->warm_delta)) return fail(DF_EINVAL, "warm_delta is NaN");
   return DF_OK;
 }
+
 
 SolveCfg cfg_of(const df_solve_params *p) {
   SolveCfg c;
@@ -399,6 +402,30 @@ df_status report(df_status s, const char *fmt, ...) {
   va_end(ap);
   g_err = buf;
   return s;
+}
+
+// The schedule as (at most) two phases of whole GN iterations: the warm
+// start (Huber with warm_delta) and the rest (the requested loss). Each
+// fused launch and each launch-solver run starts its first GN iteration
+// with its own scale step, so two back-to-back solves are exactly one
+// schedule whose loss changes after warm_gn iterations.
+int split_schedule(const df_solve_params &p, df_solve_params ph[2]) {
+  if (p.warm_gn <= 0 || p.n_gn == 0) {
+    ph[0] = p;
+    ph[0].warm_gn = 0;
+    return 1;
+  }
+  const int warm = p.warm_gn < p.n_gn ? p.warm_gn : p.n_gn;
+  ph[0] = p;
+  ph[0].n_gn = warm;
+  ph[0].loss = DF_LOSS_HUBER;
+  ph[0].delta = p.warm_delta;
+  ph[0].warm_gn = 0;
+  if (warm == p.n_gn) return 1;
+  ph[1] = p;
+  ph[1].n_gn = p.n_gn - warm;
+  ph[1].warm_gn = 0;
+  return 2;
 }
 
 df_status check_solve_params(const df_solve_params *p) { return check_params(p); }
@@ -460,6 +487,8 @@ void df_default_params(df_solve_params *p) {
   p->scale_step = 1;
   p->solver = DF_SOLVER_AUTO;
   p->tol = 0.0;
+  p->warm_gn = 0;
+  p->warm_delta = 1.345f;
 }
 
 size_t df_keyframe_bytes(int32_t width, int32_t height, int32_t cnn_dtype) {
@@ -663,7 +692,7 @@ static df_status check_joint(const df_solve_params &p) {
 // need_resident: the solve runs only on a shared-memory resident plan (the
 // joint (x, t) solve); DF_ENOTSUP otherwise, before anything is launched.
 static df_status fused_one(df_keyframe *kf, const SolveCfg &c, int n_gn, int n_pcg,
-                           cudaStream_t s, bool need_resident = false) {
+                           cudaStream_t s, bool need_resident = false, bool first_phase = true) {
   if (!df::fused_supported() || !kf->plan) return fail(DF_ENOTSUP, "fused solver not available on this device");
   const df::FusedTuning tune = current_tuning();
   if (kf->plan_shape.kind < 0 || !same_tuning(tune, kf->plan_tune)) {
@@ -684,7 +713,7 @@ static df_status fused_one(df_keyframe *kf, const SolveCfg &c, int n_gn, int n_p
   for (int g0 = 0, first = 1; g0 < n_gn || first; g0 += chunk, first = 0) {
     const int m = std::min(chunk, n_gn - g0);
     DF_CUDA(df::fused_launch(kf->plan, kf->plan_shape, c, m < 0 ? 0 : m, n_pcg,
-                             g_spin_limit_ns.load(), s, first));
+                             g_spin_limit_ns.load(), s, first && first_phase));
     if (n_gn == 0) break;
   }
   return DF_OK;
@@ -738,12 +767,12 @@ static bool find_batch_plan(df_keyframe *const *kfs, int n, const df::FusedTunin
 
 static df_status fused_launches(void *dplan, const df::LaunchShape &shape,
                                 const df::FusedTuning &tune, const SolveCfg &c, int n_gn,
-                                int n_pcg, cudaStream_t s) {
+                                int n_pcg, cudaStream_t s, bool first_phase) {
   const int chunk = tune.gn_per_launch > 0 ? tune.gn_per_launch : (n_gn > 0 ? n_gn : 1);
   for (int g0 = 0, first = 1; g0 < n_gn || first; g0 += chunk, first = 0) {
     const int m = std::min(chunk, n_gn - g0);
     DF_CUDA(df::fused_launch(dplan, shape, c, m < 0 ? 0 : m, n_pcg, g_spin_limit_ns.load(), s,
-                             first));
+                             first && first_phase));
     if (n_gn == 0) break;
   }
   return DF_OK;
@@ -752,19 +781,19 @@ static df_status fused_launches(void *dplan, const df::LaunchShape &shape,
 // Fused solve of a list of keyframes in as few launches as the plan allows
 // (a list whose tiles cannot share one grid is split in halves).
 static df_status fused_many(df_keyframe *const *kfs, int n, const SolveCfg &c, int n_gn,
-                            int n_pcg, cudaStream_t s) {
+                            int n_pcg, cudaStream_t s, bool first_phase) {
   if (n <= 0) return DF_OK;
-  if (n == 1) return fused_one(kfs[0], c, n_gn, n_pcg, s);
+  if (n == 1) return fused_one(kfs[0], c, n_gn, n_pcg, s, false, first_phase);
   if (n > df::kMaxBatch) {
-    df_status st = fused_many(kfs, df::kMaxBatch, c, n_gn, n_pcg, s);
+    df_status st = fused_many(kfs, df::kMaxBatch, c, n_gn, n_pcg, s, first_phase);
     if (st != DF_OK) return st;
-    return fused_many(kfs + df::kMaxBatch, n - df::kMaxBatch, c, n_gn, n_pcg, s);
+    return fused_many(kfs + df::kMaxBatch, n - df::kMaxBatch, c, n_gn, n_pcg, s, first_phase);
   }
   const df::FusedTuning tune = current_tuning();
   void *dplan = nullptr;
   df::LaunchShape shape;
   if (find_batch_plan(kfs, n, tune, &dplan, &shape))
-    return fused_launches(dplan, shape, tune, c, n_gn, n_pcg, s);
+    return fused_launches(dplan, shape, tune, c, n_gn, n_pcg, s, first_phase);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cs);
   if (cs != cudaStreamCaptureStatusNone)
@@ -775,14 +804,15 @@ static df_status fused_many(df_keyframe *const *kfs, int n, const SolveCfg &c, i
   std::vector<char> host;
   if (!df::fused_build_plan(list.data(), n, tune, host, shape)) {
     const int h = n / 2;
-    df_status st = fused_many(kfs, h, c, n_gn, n_pcg, s);
+    df_status st = fused_many(kfs, h, c, n_gn, n_pcg, s, first_phase);
     if (st != DF_OK) return st;
-    return fused_many(kfs + h, n - h, c, n_gn, n_pcg, s);
+    return fused_many(kfs + h, n - h, c, n_gn, n_pcg, s, first_phase);
   }
   DF_CUDA(cudaMallocAsync(&dplan, host.size(), s));
   cudaError_t e = cudaMemcpyAsync(dplan, host.data(), host.size(), cudaMemcpyHostToDevice, s);
-  df_status st = e == cudaSuccess ? fused_launches(dplan, shape, tune, c, n_gn, n_pcg, s)
-                                  : cuda_fail(e, "batch plan upload");
+  df_status st = e == cudaSuccess
+                     ? fused_launches(dplan, shape, tune, c, n_gn, n_pcg, s, first_phase)
+                     : cuda_fail(e, "batch plan upload");
   cudaError_t e2 = cudaFreeAsync(dplan, s);
   if (st != DF_OK) return st;
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
@@ -827,17 +857,30 @@ static df_status prepare_many(df_keyframe *const *kfs, int n, cudaStream_t s) {
   return DF_OK;
 }
 
-static df_status optimise_one(df_keyframe *kf, const df_solve_params *p, cudaStream_t s) {
+// One phase of a keyframe's schedule (first: the PCG iteration count of the
+// report starts at zero; otherwise it continues the previous phase's).
+static df_status optimise_phase(df_keyframe *kf, const df_solve_params *p, cudaStream_t s,
+                                bool first) {
   const SolveCfg c = cfg_of(p);
   const bool joint = p->scale_step == DF_SCALE_JOINT;
   if (pick_solver(*p) == DF_SOLVER_FUSED) {
-    df_status st = fused_one(kf, c, p->n_gn, p->n_pcg, s, joint);
+    df_status st = fused_one(kf, c, p->n_gn, p->n_pcg, s, joint, first);
     // the joint solve on a streaming launch shape: the launch solver serves AUTO
     if (!(joint && st == DF_ENOTSUP && p->solver == DF_SOLVER_AUTO)) return st;
   }
-  DF_CUDA(cudaMemsetAsync(&kf->planes.sc->iters, 0, sizeof(int), s));
+  if (first) DF_CUDA(cudaMemsetAsync(&kf->planes.sc->iters, 0, sizeof(int), s));
   DF_CUDA(cudaMemsetAsync(&kf->planes.sc->stop, 0, sizeof(int), s));
   DF_CUDA(df::launch_solve_launches(kf->planes, c, p->n_gn, p->n_pcg, s));
+  return DF_OK;
+}
+
+static df_status optimise_one(df_keyframe *kf, const df_solve_params *p, cudaStream_t s) {
+  df_solve_params ph[2];
+  const int n = df::split_schedule(*p, ph);
+  for (int j = 0; j < n; ++j) {
+    df_status st = optimise_phase(kf, &ph[j], s, j == 0);
+    if (st != DF_OK) return st;
+  }
   return DF_OK;
 }
 
@@ -883,8 +926,12 @@ df_status df_optimise_batch(df_keyframe *const *kfs, int32_t n, const df_solve_p
   DeviceGuard g(kfs[0]->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (pick_solver(p) == DF_SOLVER_FUSED && p.scale_step != DF_SCALE_JOINT) {
-    st = fused_many(kfs, n, cfg_of(&p), p.n_gn, p.n_pcg, s);
-    if (st != DF_OK) return st;
+    df_solve_params ph[2];
+    const int np = df::split_schedule(p, ph);
+    for (int j = 0; j < np; ++j) {
+      st = fused_many(kfs, n, cfg_of(&ph[j]), ph[j].n_gn, ph[j].n_pcg, s, j == 0);
+      if (st != DF_OK) return st;
+    }
   } else {  // the launch solver, or the joint solve (keyframe by keyframe)
     for (int j = 0; j < n; ++j) {
       st = optimise_one(kfs[j], &p, s);

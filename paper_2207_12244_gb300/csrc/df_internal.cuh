@@ -249,6 +249,10 @@ void count_launches(unsigned n);
 // for df_last_error() and return the status; check / convert solve params.
 df_status report(df_status s, const char *fmt, ...);
 df_status check_solve_params(const df_solve_params *p);
+// The schedule split at the end of its Huber warm start: writes 1 or 2
+// phases of whole GN iterations (each with warm_gn = 0) and returns their
+// number.
+int split_schedule(const df_solve_params &p, df_solve_params ph[2]);
 SolveCfg solve_cfg(const df_solve_params *p);
 
 int launch_grid(int tiles);  // blocks for a grid-stride launch over 32x8 tiles

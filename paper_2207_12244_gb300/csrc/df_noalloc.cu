@@ -106,7 +106,12 @@ extern "C" df_status df_optimise_noalloc(int32_t width, int32_t height, const fl
   cudaError_t e = cudaMemsetAsync(&scr->sc, 0, sizeof(Scalars), s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&scr->sc.t, scale_log_inout, sizeof(double), cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = launch_solve_launches(k, solve_cfg(&p), p.n_gn, p.n_pcg, s);
+  df_solve_params ph[2];
+  const int nph = split_schedule(p, ph);  // the Huber warm start, then the rest
+  for (int j = 0; j < nph && e == cudaSuccess; ++j) {
+    if (j > 0) e = cudaMemsetAsync(&scr->sc.stop, 0, sizeof(scr->sc.stop), s);
+    if (e == cudaSuccess) e = launch_solve_launches(k, solve_cfg(&ph[j]), ph[j].n_gn, ph[j].n_pcg, s);
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(scale_log_inout, &scr->sc.t, sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return report(DF_ECUDA, "df_optimise_noalloc: %s", cudaGetErrorString(e));

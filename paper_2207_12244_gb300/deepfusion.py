@@ -35,7 +35,8 @@ class df_keyframe_desc(C.Structure):
 class df_solve_params(C.Structure):
     _fields_ = [("n_gn", C.c_int32), ("n_pcg", C.c_int32), ("delta", C.c_float),
                 ("loss", C.c_int32), ("terms", C.c_int32), ("scale_step", C.c_int32),
-                ("solver", C.c_int32), ("tol", C.c_double)]
+                ("solver", C.c_int32), ("tol", C.c_double), ("warm_gn", C.c_int32),
+                ("warm_delta", C.c_float)]
 
 
 class df_solve_report(C.Structure):

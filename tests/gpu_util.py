@@ -81,7 +81,8 @@ def oracle_solve(o, kf, prm, semi=True, x0=None, t0=0.0):
         view.var_s = None
     return o.optimise(view, x0=x0, t0=t0, n_gn=prm.n_gn, n_pcg=prm.n_pcg, delta=prm.delta,
                       tol=prm.tol, terms=prm.terms, loss=prm.loss,
-                      scale_step=int(prm.scale_step))
+                      scale_step=int(prm.scale_step), warm_gn=prm.warm_gn,
+                      warm_delta=prm.warm_delta)
 
 
 def depth_rel_err(x_gpu, x_orc):

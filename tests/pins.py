@@ -20,6 +20,9 @@ What each pin fixes:
   invariances          shifts of mu_s, of (mu_n, mu_s), and transposition
   monotone             cost never increases over scale and depth steps
   no_pairwise          semi + network only: closed-form joint optimum
+  tukey_after_huber    Huber warm start then Tukey: the ends are the plain
+                       solves; k + (n - k) iterations = two chained solves;
+                       Tukey iterations never raise the Tukey cost
   ls_scale_fit         Table II fit: a constructed offset comes back exactly;
                        optimality, x - t kept, shift invariance
   semi_to_log          first-order log conversion vs Monte Carlo
@@ -415,6 +418,37 @@ def no_pairwise(o):
     assert abs(t - t1) < 1e-12 and np.allclose(x.ravel(), x1, rtol=0, atol=1e-12)
 
 
+def tukey_after_huber(o):
+    """The Huber-then-Tukey schedule (Section IV names Tukey's loss; being
+    non-convex it is started from a Huber solve): warm_gn = n_gn is the
+    Huber solve and warm_gn = 0 the Tukey solve, bit for bit; k Huber
+    iterations followed by n - k Tukey ones equal a Huber solve of k
+    iterations continued by a Tukey solve of n - k from its (x, t); and the
+    Tukey iterations never increase the Tukey cost (IRLS on a loss concave
+    in u^2 is majorise-minimise, and truncated CG decreases the majoriser)."""
+    kf = _noisy(12, 9, 81)
+    rng = np.random.default_rng(81)
+    m = kf.var_s > 0
+    out = rng.random(kf.mu_s.shape) < 0.15  # gross semi-dense outliers
+    kf.mu_s = np.where(m & out, kf.mu_s + rng.choice([-1.5, 1.5], kf.mu_s.shape), kf.mu_s)
+    n, k = 8, 3
+    tk = dict(delta=TUKEY_C, loss=orc.LOSS_TUKEY, n_pcg=4)
+    x_h, t_h, r_h = o.optimise(kf, n_gn=n, n_pcg=4, delta=DELTA)
+    x_w, t_w, r_w = o.optimise(kf, n_gn=n, warm_gn=n, warm_delta=DELTA, **tk)
+    assert np.array_equal(x_w, x_h) and t_w == t_h and r_w.iters_done == r_h.iters_done
+    x_t, t_t, _ = o.optimise(kf, n_gn=n, **tk)
+    x_0, t_0, _ = o.optimise(kf, n_gn=n, warm_gn=0, warm_delta=0.5, **tk)
+    assert np.array_equal(x_0, x_t) and t_0 == t_t
+    x1, t1, r1 = o.optimise(kf, n_gn=k, n_pcg=4, delta=DELTA)
+    x2, t2, r2 = o.optimise(kf, x0=x1, t0=t1, n_gn=n - k, **tk)
+    xs, ts, rs, tr = o.optimise(kf, n_gn=n, warm_gn=k, warm_delta=DELTA, trace=True, **tk)
+    assert np.array_equal(xs, x2) and ts == t2
+    assert rs.iters_done == r1.iters_done + r2.iters_done
+    assert not np.array_equal(xs, x_t) and not np.array_equal(xs, x_h)
+    d = np.diff(tr[2 * k:])
+    assert np.all(d <= 1e-12 * tr[2 * k]), d.max()
+
+
 def ls_scale_fit(o):
     """Table II's least-squares scale fit (reading: the shift c minimising
     sum_i (x_i + c - mu_n,i)^2 moves x and t together, so the semi-dense
@@ -568,6 +602,7 @@ def mvs_scene(o):
 
 
 ALL = [cost_closed_form, robust_weight, dense_hessian, joint_optimum, joint_bordered, prior_only,
-       planar_recovery, huber_scipy, invariances, monotone, no_pairwise, ls_scale_fit, semi_to_log,
+       planar_recovery, huber_scipy, invariances, monotone, no_pairwise, tukey_after_huber, ls_scale_fit,
+       semi_to_log,
        within_10pct,
        mvs_rectified, mvs_fusion_and_interval, mvs_scene]

@@ -25,9 +25,10 @@ def test_status_strings_and_defaults(lib):
     assert dfl.df_status_str(dfl.DF_EINVAL) == "DF_EINVAL"
     assert dfl.df_status_str(dfl.DF_ETIMEOUT) == "DF_ETIMEOUT"
     p = dfl.df_default_params()
-    assert (p.n_gn, p.n_pcg, p.loss, p.terms, p.scale_step, p.solver, p.tol) == (
-        10, 3, dfl.DF_LOSS_HUBER, dfl.DF_TERMS_ALL, 1, dfl.DF_SOLVER_AUTO, 0.0)
-    assert abs(p.delta - 1.345) < 1e-6
+    assert (p.n_gn, p.n_pcg, p.loss, p.terms, p.scale_step, p.solver, p.tol, p.warm_gn) == (
+        10, 3, dfl.DF_LOSS_HUBER, dfl.DF_TERMS_ALL, 1, dfl.DF_SOLVER_AUTO, 0.0, 0)
+    assert abs(p.delta - 1.345) < 1e-6 and abs(p.warm_delta - 1.345) < 1e-6
+    assert C.sizeof(dfl.df_solve_params) == 48  # the C struct's layout
 
 
 def test_keyframe_bytes_and_budget(lib):
@@ -87,7 +88,8 @@ def test_null_keyframe_and_bad_params(lib):
     lib.df_keyframe_destroy(None)  # NULL-safe
     bad = [dict(n_gn=-1), dict(n_pcg=-2), dict(loss=5), dict(terms=0), dict(terms=1),
            dict(terms=8), dict(solver=9), dict(tol=-1.0), dict(tol=float("inf")),
-           dict(delta=float("nan"))]
+           dict(delta=float("nan")), dict(warm_gn=-1),
+           dict(warm_gn=2, warm_delta=float("nan"))]
     arr = (C.c_void_p * 1)(None)
     for b in bad:
         p = dfl.df_default_params(**b)

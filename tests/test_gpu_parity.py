@@ -58,8 +58,8 @@ def test_edge_sizes(o, solver, W, H):
     assert rep.iters_done == ro.iters_done
 
 
-@pytest.mark.parametrize("mode", ["l2", "huber", "tukey", "semi+net", "net+grad", "semi+grad",
-                                  "no-scale-step"])
+@pytest.mark.parametrize("mode", ["l2", "huber", "tukey", "huber-then-tukey", "semi+net",
+                                  "net+grad", "semi+grad", "no-scale-step"])
 def test_modes(o, solver, mode):
     kf = synth.make_keyframe(96, 72, 7)
     kw = dict(n_gn=6, n_pcg=5, solver=solver)
@@ -67,6 +67,8 @@ def test_modes(o, solver, mode):
         kw["delta"] = float("inf")
     elif mode == "tukey":
         kw.update(loss=dfl.DF_LOSS_TUKEY, delta=4.685)
+    elif mode == "huber-then-tukey":  # 2 Huber GN iterations, then 4 Tukey
+        kw.update(loss=dfl.DF_LOSS_TUKEY, delta=4.685, warm_gn=2, warm_delta=1.345)
     elif mode == "semi+net":
         kw["terms"] = dfl.DF_TERM_SEMI | dfl.DF_TERM_NET
     elif mode == "net+grad":
@@ -383,6 +385,38 @@ def test_barrier_wait_times_out_cleanly(mode):
         dfl.df_set_spin_limit_ns(2_000_000_000)
     again = solve(kf, prm)
     assert np.array_equal(again[0], ref[0]) and again[1] == ref[1]
+
+
+def test_huber_warm_start_is_two_chained_solves(o, solver):
+    """The Huber-then-Tukey schedule in one call equals, bit for bit, a Huber
+    solve of warm_gn iterations continued by a Tukey solve of the rest, and
+    its report counts the PCG iterations of both; warm_gn >= n_gn is the
+    Huber solve."""
+    torch = torch_cuda()
+    kf = synth.make_keyframe(100, 70, 27)
+    tk = dict(loss=dfl.DF_LOSS_TUKEY, delta=4.685, n_pcg=4, solver=solver)
+
+    def run(prms):
+        k = create(kf)
+        try:
+            k.frame_update(to_dev(kf.mu_s), to_dev(kf.var_s))
+            iters = 0
+            for prm in prms:
+                iters += k.optimise(prm, report=True).iters_done
+            out = torch.empty((kf.height, kf.width), dtype=torch.float32, device="cuda")
+            k.fetch_depth(out, log_space=True)
+            return out.cpu().numpy(), k.get_state(), iters
+        finally:
+            k.close()
+
+    x1, t1, i1 = run([params(n_gn=7, warm_gn=3, warm_delta=1.345, **tk)])
+    x2, t2, i2 = run([params(n_gn=3, n_pcg=4, solver=solver), params(n_gn=4, **tk)])
+    assert np.array_equal(x1, x2) and t1 == t2 and i1 == i2 == 28
+    xh, th, _ = run([params(n_gn=5, n_pcg=4, solver=solver)])
+    xw, tw, _ = run([params(n_gn=5, warm_gn=9, warm_delta=1.345, **tk)])
+    assert np.array_equal(xh, xw) and th == tw
+    xo, to, _ = oracle_solve(o, kf, params(n_gn=7, warm_gn=3, warm_delta=1.345, **tk))
+    assert_parity(x1.astype(np.float64), t1, xo, to, what="huber then tukey")
 
 
 def test_table2_scale_ambiguous_solve_then_ls_fit(o, solver):

@@ -8,7 +8,9 @@ neighbour index, an inverted CG beta, a residual divided by the variance
 instead of the standard deviation, a flipped sign of the x-t coupling in
 the joint solve, a stereo variance with the wrong power of the depth step,
 a stereo sub-pixel fraction with the wrong sign, a Table II scale fit
-with the wrong sign, a Table II scale fit that does not move t.
+with the wrong sign, a Table II scale fit that does not move t, a Huber
+warm start one iteration too long, a Huber warm start with the Tukey
+threshold.
 """
 import pytest
 
@@ -30,6 +32,8 @@ MUTANTS = {
     12: "stereo sub-pixel fraction has the wrong sign",
     13: "Table II fit shifts by mean(x - mu_n)",
     14: "Table II fit leaves t in place",
+    15: "Huber warm start runs one GN iteration too long",
+    16: "Huber warm start uses the Tukey threshold",
 }
 
 
