@@ -834,10 +834,14 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
         else:
             dfl.df_optimise_batch(handles, prm, stream=sptr)
 
+    mu_d = [m for m, _ in semi_d]
+    var_d = [v for _, v in semi_d]
+
     def load_frame():
-        for k, c, (ms, vs) in zip(ks, cnn_d, semi_d):
-            k.reset(*c, stream=sptr)
-            k.frame_update(ms, vs, stream=sptr)
+        # keyframe (re)initialisation from the network planes, then the
+        # frame's semi-dense planes: a few batched launches for all keyframes
+        dfl.df_keyframe_reset_batch(handles, cnn_d, stream=sptr)
+        dfl.df_frame_update_batch(handles, mu_d, var_d, stream=sptr)
 
     def step(record):
         load_frame()
@@ -846,8 +850,7 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
         solve()
         if record:
             ev[1].record(stream)
-        for k, o in zip(ks, outs):
-            k.fetch_depth(o, stream=sptr)
+        dfl.df_fetch_depth_batch(handles, outs, stream=sptr)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -923,13 +926,14 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
                   for kf in kfs]
         outs_h = [torch.empty((kf.height, kf.width), dtype=torch.float32).pin_memory() for kf in kfs]
 
+        mu_h = [m for m, _ in semi_h]
+        var_h = [v for _, v in semi_h]
+
         def step_host():
-            for k, c, (ms, vs) in zip(ks, cnn_h, semi_h):
-                k.reset(*c, stream=sptr)
-                k.frame_update(ms, vs, stream=sptr)
+            dfl.df_keyframe_reset_batch(handles, cnn_h, stream=sptr)
+            dfl.df_frame_update_batch(handles, mu_h, var_h, stream=sptr)
             solve()
-            for k, o in zip(ks, outs_h):
-                k.fetch_depth(o, stream=sptr)
+            dfl.df_fetch_depth_batch(handles, outs_h, stream=sptr)
 
         step_host()
         torch.cuda.synchronize()
@@ -993,8 +997,7 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
             per_kf_ms.extend(a.elapsed_time(b) for a, b in evk)
         p_launches = dfl.df_kernel_launches() - p_launches0
         # same accuracy: the plain leg's depth against the batched leg's
-        for k, o in zip(ks, outs):
-            k.fetch_depth(o, stream=sptr)
+        dfl.df_fetch_depth_batch(handles, outs, stream=sptr)
         torch.cuda.synchronize()
         diff = max(float(((o.double() / b.double()) - 1.0).abs().max())
                    for o, b in zip(outs, batched_depth))

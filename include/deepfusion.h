@@ -200,6 +200,35 @@ df_status df_optimise_batch(df_keyframe *const *kfs, int32_t n,
 df_status df_batch_prepare(df_keyframe *const *kfs, int32_t n, void *stream);
 df_status df_batch_release(df_keyframe *const *kfs, int32_t n);
 
+/* The per-frame bookkeeping of many keyframes at once, in one or two device
+ * passes per 24 keyframes instead of one copy or launch per plane and
+ * keyframe (paper counterpart: none; the same work as the single-keyframe
+ * calls it names). kfs: n distinct keyframes on one device (DF_EINVAL
+ * otherwise, before anything runs). Stream-ordered; the caller keeps its
+ * buffers and must not modify them until the stream reaches the call. With
+ * device pointers nothing is uploaded and the calls can be captured in a
+ * CUDA graph; with host pointers each keyframe goes through the
+ * single-keyframe call.
+ *
+ * df_keyframe_reset_batch: df_keyframe_reset of keyframe j from
+ *   planes[6j .. 6j+5] = mu_net, var_net, gx, var_gx, gy, var_gy (each
+ *   dense row-major in keyframe j's cnn_dtype): the planes are copied in,
+ *   x = mu_n and t = 0 (Section II: a keyframe starts from the network's
+ *   prediction), the semi-dense variance is cleared, and the inputs are
+ *   checked (host pointers: all before any keyframe is touched, DF_EINVAL;
+ *   device pointers: on the device, flagging the keyframe as
+ *   df_keyframe_reset does).
+ * df_frame_update_batch: df_frame_update of keyframe j from mu_semi[j],
+ *   var_semi[j] (dense f32, log space, Section II-B).
+ * df_fetch_depth_batch: df_fetch_depth of keyframe j into out[j] (dense f32:
+ *   d = exp(x), or x when log_space). */
+df_status df_keyframe_reset_batch(df_keyframe *const *kfs, int32_t n, const void *const *planes,
+                                  int ptrs_on_device, void *stream);
+df_status df_frame_update_batch(df_keyframe *const *kfs, int32_t n, const float *const *mu_semi,
+                                const float *const *var_semi, int ptrs_on_device, void *stream);
+df_status df_fetch_depth_batch(df_keyframe *const *kfs, int32_t n, float *const *out,
+                               int log_space, int ptrs_on_device, void *stream);
+
 /* Write the keyframe's depth map d = exp(x) (Eq. 5's d; log_space != 0
  * writes x = ln d instead) as H x W f32 into 'out'. */
 df_status df_fetch_depth(df_keyframe *kf, float *out, int log_space, int ptr_on_device,

@@ -16,6 +16,7 @@
 #include <thread>
 #include <vector>
 
+#include "df_batch_io.cuh"
 #include "df_fused.cuh"
 #include "df_sync.cuh"
 #include "df_internal.cuh"
@@ -983,6 +984,147 @@ df_status df_fetch_depth(df_keyframe *kf, float *out, int log_space, int ptr_on_
   DF_CUDA(df::launch_fetch(kf->planes, kf->staging, log_space, s));
   DF_CUDA(cudaMemcpyAsync(out, kf->staging, (size_t)kf->W * kf->H * 4, cudaMemcpyDeviceToHost, s));
   return DF_OK;
+}
+
+// ---- batched bookkeeping of many keyframes --------------------------------
+
+static df_status check_list(df_keyframe *const *kfs, int32_t n) {
+  if (n < 0 || (n > 0 && !kfs)) return fail(DF_EINVAL, "bad keyframe list");
+  for (int j = 0; j < n; ++j) {
+    if (!kfs[j]) return fail(DF_EINVAL, "keyframe %d is NULL", j);
+    for (int m = 0; m < j; ++m)
+      if (kfs[m] == kfs[j]) return fail(DF_EINVAL, "keyframe %d appears twice", j);
+    if (kfs[j]->device != kfs[0]->device) return fail(DF_EINVAL, "keyframes on different devices");
+  }
+  return DF_OK;
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Fill one launch's item table with keyframes [j0, j0 + m) of the list.
+extern "C++" {
+template <typename Fill>
+static df_status launch_io_chunks(df_keyframe *const *kfs, int32_t n, df::IoKind kind, int check,
+                                  int log_space, cudaStream_t s, Fill fill) {
+  for (int j0 = 0; j0 < n; j0 += df::kIoBatch) {
+    const int m = std::min(df::kIoBatch, n - j0);
+    df::IoBatch b;
+    memset(&b, 0, sizeof b);
+    b.n = m;
+    b.check = check;
+    b.log_space = log_space;
+    int rows = 0;
+    for (int q = 0; q < m; ++q) {
+      df_keyframe *kf = kfs[j0 + q];
+      df::IoItem &it = b.item[q];
+      it.W = kf->W;
+      it.H = kf->H;
+      it.P = kf->P;
+      it.dtype = kf->dtype;
+      it.x = kf->planes.x;
+      it.var_s = const_cast<float *>(kf->planes.var_s);
+      it.sc = kf->planes.sc;
+      it.row0 = rows;
+      rows += kf->H;
+      fill(j0 + q, kf, it);
+    }
+    b.total = rows;
+    DF_CUDA(df::launch_io(kind, b, s));
+  }
+  return DF_OK;
+}
+}  // extern "C++"
+
+df_status df_keyframe_reset_batch(df_keyframe *const *kfs, int32_t n, const void *const *planes,
+                                  int ptrs_on_device, void *stream) {
+  df_status st = check_list(kfs, n);
+  if (st != DF_OK) return st;
+  if (n == 0) return DF_OK;
+  if (!planes) return fail(DF_EINVAL, "planes is NULL");
+  for (int j = 0; j < 6 * n; ++j)
+    if (!planes[j]) return fail(DF_EINVAL, "network plane %d of keyframe %d is NULL", j % 6, j / 6);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!ptrs_on_device) {
+    // host planes: every keyframe's inputs are checked before any is touched,
+    // then each goes up through its staging plane
+    for (int j = 0; j < n; ++j) {
+      char why[256];
+      if (!host_inputs_ok(planes + 6 * j, kfs[j]->W, kfs[j]->H, kfs[j]->dtype, why, sizeof why))
+        return fail(DF_EINVAL, "invalid network input of keyframe %d: %s", j, why);
+    }
+    for (int j = 0; j < n; ++j) {
+      DeviceGuard g(kfs[j]->device);
+      df_keyframe *kf = kfs[j];
+      DF_CUDA(cudaMemsetAsync((void *)kf->planes.var_s, 0, (size_t)kf->P * kf->H * 4, s));
+      st = load_cnn(kf, planes + 6 * j, 0, s);
+      if (st != DF_OK) return st;
+    }
+    return DF_OK;
+  }
+  DeviceGuard g(kfs[0]->device);
+  return launch_io_chunks(kfs, n, df::IoKind::kReset, 1, 0, s,
+                          [&](int j, df_keyframe *kf, df::IoItem &it) {
+                            const size_t es = elem_size(kf->dtype);
+                            bool vec = ((size_t)kf->W * es) % 16 == 0;
+                            for (int q = 0; q < 6; ++q) {
+                              it.src[q] = planes[6 * j + q];
+                              it.dst[q] = const_cast<void *>(kf->planes.cnn[q]);
+                              vec = vec && aligned16(it.src[q]);
+                            }
+                            it.vec = vec;
+                          });
+}
+
+df_status df_frame_update_batch(df_keyframe *const *kfs, int32_t n, const float *const *mu_semi,
+                                const float *const *var_semi, int ptrs_on_device, void *stream) {
+  df_status st = check_list(kfs, n);
+  if (st != DF_OK) return st;
+  if (n == 0) return DF_OK;
+  if (!mu_semi || !var_semi) return fail(DF_EINVAL, "plane list is NULL");
+  for (int j = 0; j < n; ++j)
+    if (!mu_semi[j] || !var_semi[j]) return fail(DF_EINVAL, "semi-dense plane of keyframe %d is NULL", j);
+  if (!ptrs_on_device) {
+    // host planes: each keyframe's upload overlaps the previous solve as in
+    // df_frame_update
+    for (int j = 0; j < n; ++j) {
+      st = df_frame_update(kfs[j], mu_semi[j], var_semi[j], 0, stream);
+      if (st != DF_OK) return st;
+    }
+    return DF_OK;
+  }
+  DeviceGuard g(kfs[0]->device);
+  return launch_io_chunks(kfs, n, df::IoKind::kUpdate, 0, 0, static_cast<cudaStream_t>(stream),
+                          [&](int j, df_keyframe *kf, df::IoItem &it) {
+                            it.src[0] = mu_semi[j];
+                            it.src[1] = var_semi[j];
+                            it.dst[0] = const_cast<float *>(kf->planes.mu_s);
+                            it.dst[1] = const_cast<float *>(kf->planes.var_s);
+                            it.vec = kf->W % 4 == 0 && aligned16(mu_semi[j]) && aligned16(var_semi[j]);
+                          });
+}
+
+df_status df_fetch_depth_batch(df_keyframe *const *kfs, int32_t n, float *const *out,
+                               int log_space, int ptrs_on_device, void *stream) {
+  df_status st = check_list(kfs, n);
+  if (st != DF_OK) return st;
+  if (n == 0) return DF_OK;
+  if (!out) return fail(DF_EINVAL, "output list is NULL");
+  for (int j = 0; j < n; ++j)
+    if (!out[j]) return fail(DF_EINVAL, "output of keyframe %d is NULL", j);
+  if (!ptrs_on_device) {
+    for (int j = 0; j < n; ++j) {
+      st = df_fetch_depth(kfs[j], out[j], log_space, 0, stream);
+      if (st != DF_OK) return st;
+    }
+    return DF_OK;
+  }
+  DeviceGuard g(kfs[0]->device);
+  return launch_io_chunks(kfs, n, df::IoKind::kFetch, 0, log_space ? 1 : 0,
+                          static_cast<cudaStream_t>(stream),
+                          [&](int j, df_keyframe *kf, df::IoItem &it) {
+                            it.dst[0] = out[j];
+                            it.vec = kf->W % 4 == 0 && aligned16(out[j]);
+                          });
 }
 
 df_status df_keyframe_get_state(df_keyframe *kf, float *x_out, double *t_out,

@@ -136,6 +136,10 @@ def load(path: Optional[str] = None) -> C.CDLL:
         C.POINTER(df_solve_params), vp]
     L.df_optimise_noalloc.restype = C.c_int
     L.df_batch_prepare.argtypes = [C.POINTER(vp), i32, vp]
+    L.df_keyframe_reset_batch.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), C.c_int, vp]
+    L.df_frame_update_batch.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp),
+                                        C.c_int, vp]
+    L.df_fetch_depth_batch.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), C.c_int, C.c_int, vp]
     L.df_batch_release.argtypes = [C.POINTER(vp), i32]
     L.df_mvs_default_params.argtypes = [C.POINTER(df_mvs_params)]
     L.df_mvs_default_params.restype = None
@@ -179,7 +183,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     for name in ("df_keyframe_create", "df_keyframe_reset", "df_frame_update", "df_optimise",
                  "df_optimise_batch", "df_fetch_depth", "df_keyframe_get_state",
                  "df_keyframe_set_state", "df_cost", "df_keyframe_check", "df_keyframe_info",
-                 "df_set_memory_budget", "df_semi_to_log"):
+                 "df_set_memory_budget", "df_semi_to_log", "df_keyframe_reset_batch",
+                 "df_frame_update_batch", "df_fetch_depth_batch"):
         getattr(L, name).restype = st
     if path is None:
         _lib = L
@@ -335,6 +340,65 @@ def df_batch_prepare(kfs: Sequence, stream=None):
 def df_batch_release(kfs: Sequence):
     arr, n = _kf_array(kfs)
     _check(load().df_batch_release(arr, n), "df_batch_release")
+
+
+def _batch_buffers(kfs, lists, where: str, per_kf_dtype: bool):
+    """Check that every buffer of a batched call has its keyframe's W*H
+    elements (and, for torch tensors, the element type the call reads), all
+    on one side; returns (keyframe array, n, pointer array, on_device)."""
+    arr, n = _kf_array(kfs)
+    flat = []
+    for j, k in enumerate(kfs):
+        W, H, dt, _ = df_keyframe_info(k)
+        want = {DF_F32: 4, DF_BF16: 2, DF_F16: 2}[dt] if per_kf_dtype else 4
+        for b in lists[j]:
+            if b is None:
+                raise ValueError(f"{where}: buffer of keyframe {j} is None")
+            if _numel(b) != W * H:
+                raise ValueError(f"{where}: buffer of keyframe {j} has {_numel(b)} elements, "
+                                 f"not {W} x {H}")
+            size = b.element_size() if _is_torch(b) else b.itemsize
+            if size != want:
+                raise ValueError(f"{where}: buffer of keyframe {j} has {size}-byte elements, "
+                                 f"the keyframe needs {want}")
+            flat.append(b)
+    on_dev = _same_side(flat, where)
+    ptrs = (C.c_void_p * max(len(flat), 1))(*[_ptr(b)[0] for b in flat])
+    return arr, n, ptrs, on_dev, flat
+
+
+def df_keyframe_reset_batch(kfs: Sequence, planes: Sequence[Sequence], stream=None):
+    """df_keyframe_reset of every keyframe in one or two device passes per 24
+    keyframes: planes[j] = the six network planes of keyframe j."""
+    arr, n, ptrs, on_dev, flat = _batch_buffers(kfs, planes, "df_keyframe_reset_batch", True)
+    _check(load().df_keyframe_reset_batch(arr, n, ptrs, on_dev,
+                                          _stream(stream, flat[0] if flat else None)),
+           "df_keyframe_reset_batch")
+
+
+def df_frame_update_batch(kfs: Sequence, mu_semi: Sequence, var_semi: Sequence, stream=None):
+    """df_frame_update of every keyframe in one device pass per 24 keyframes."""
+    arr, n, ptrs, on_dev, flat = _batch_buffers(
+        kfs, [[m, v] for m, v in zip(mu_semi, var_semi)], "df_frame_update_batch", False)
+    if len(mu_semi) != n or len(var_semi) != n:
+        raise ValueError("df_frame_update_batch: one mu_semi and one var_semi per keyframe")
+    mu = (C.c_void_p * max(n, 1))(*[ptrs[2 * j] for j in range(n)])
+    var = (C.c_void_p * max(n, 1))(*[ptrs[2 * j + 1] for j in range(n)])
+    _check(load().df_frame_update_batch(arr, n, mu, var, on_dev,
+                                        _stream(stream, flat[0] if flat else None)),
+           "df_frame_update_batch")
+
+
+def df_fetch_depth_batch(kfs: Sequence, outs: Sequence, log_space: bool = False, stream=None):
+    """df_fetch_depth of every keyframe in one device pass per 24 keyframes."""
+    arr, n, ptrs, on_dev, flat = _batch_buffers(kfs, [[o] for o in outs], "df_fetch_depth_batch",
+                                                False)
+    if len(outs) != n:
+        raise ValueError("df_fetch_depth_batch: one output per keyframe")
+    _check(load().df_fetch_depth_batch(arr, n, ptrs, int(log_space), on_dev,
+                                       _stream(stream, flat[0] if flat else None)),
+           "df_fetch_depth_batch")
+    return outs
 
 
 def df_fetch_depth(kf, out, log_space: bool = False, stream=None):
