@@ -8,17 +8,19 @@
 // One launch covers up to kIoBatch keyframes, whose pointers and sizes
 // travel as a kernel parameter (no upload, so the calls can be captured in
 // a CUDA graph). The work is the flattened list of every keyframe's rows;
-// each block takes kIoRows consecutive rows of it, and its threads walk a
-// row in 16-byte vectors when the caller's rows are 16-byte aligned, else
-// element by element. The keyframe's own planes are pitched (every row
-// starts on a 256-byte boundary), the caller's are dense.
+// each warp takes one row at a time, and its lanes walk the row in 16-byte
+// vectors when the caller's rows are 16-byte aligned, else element by
+// element (a row of 320 f32 values is 80 vectors: a whole warp stays busy,
+// where a whole block per row would leave most of its threads idle). The
+// keyframe's own planes are pitched (every row starts on a 256-byte
+// boundary), the caller's are dense.
 #include "df_batch_io.cuh"
 
 namespace df {
 namespace {
 
 constexpr int kIoThreads = 256;
-constexpr int kIoRows = 2;
+constexpr int kIoWarps = kIoThreads / 32;
 
 __device__ __forceinline__ int item_of(const IoBatch &b, int row) {
   int j = 0;
@@ -70,7 +72,7 @@ __device__ bool reset_row(const IoItem &it, int v, bool check) {
   bool bad = false;
   if (it.vec) {
     const int nv = W / PER;
-    for (int c = threadIdx.x; c < nv; c += blockDim.x) {
+    for (int c = threadIdx.x & 31; c < nv; c += 32) {
       uint4 q[6];
 #pragma unroll
       for (int j = 0; j < 6; ++j)
@@ -101,7 +103,7 @@ __device__ bool reset_row(const IoItem &it, int v, bool check) {
       }
     }
   } else {
-    for (int u = threadIdx.x; u < W; u += blockDim.x) {
+    for (int u = threadIdx.x & 31; u < W; u += 32) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) copy_elem<DT>(it.dst[j], drow + u, it.src[j], srow + u);
       const float m = load_elem<DT>(it.src[0], srow + u);
@@ -131,45 +133,48 @@ __global__ void k_io_zero_scalars(IoBatch b) {
     p[q] = make_uint4(0u, 0u, 0u, 0u);
 }
 
+// The flattened row list, one row per warp at a time.
+#define IO_FOR_EACH_ROW(b, r)                                                    \
+  for (int r = blockIdx.x * kIoWarps + (threadIdx.x >> 5); r < (b).total;       \
+       r += gridDim.x * kIoWarps)
+
 __global__ void __launch_bounds__(kIoThreads) k_io_reset(IoBatch b) {
-  for (int r0 = blockIdx.x * kIoRows; r0 < b.total; r0 += gridDim.x * kIoRows) {
-    for (int r = r0; r < r0 + kIoRows && r < b.total; ++r) {
-      const IoItem &it = b.item[item_of(b, r)];
-      const int v = r - it.row0;
-      bool bad;
-      if (it.dtype == DF_BF16)
-        bad = reset_row<DF_BF16>(it, v, b.check);
-      else if (it.dtype == DF_F16)
-        bad = reset_row<DF_F16>(it, v, b.check);
-      else
-        bad = reset_row<DF_F32>(it, v, b.check);
-      if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&it.sc->flags, kFlagBadInput);
-    }
+  IO_FOR_EACH_ROW(b, r) {
+    const IoItem &it = b.item[item_of(b, r)];
+    const int v = r - it.row0;
+    bool bad;
+    if (it.dtype == DF_BF16)
+      bad = reset_row<DF_BF16>(it, v, b.check);
+    else if (it.dtype == DF_F16)
+      bad = reset_row<DF_F16>(it, v, b.check);
+    else
+      bad = reset_row<DF_F32>(it, v, b.check);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+      atomicOr(&it.sc->flags, kFlagBadInput);
   }
 }
 
 // One row of a frame update: mu_s and var_s (f32) into the keyframe's layout.
 __global__ void __launch_bounds__(kIoThreads) k_io_update(IoBatch b) {
-  for (int r0 = blockIdx.x * kIoRows; r0 < b.total; r0 += gridDim.x * kIoRows) {
-    for (int r = r0; r < r0 + kIoRows && r < b.total; ++r) {
-      const IoItem &it = b.item[item_of(b, r)];
-      const int v = r - it.row0;
-      const size_t srow = (size_t)v * it.W, drow = (size_t)v * it.P;
-      if (it.vec) {
-        for (int c = threadIdx.x; c < it.W / 4; c += blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  IO_FOR_EACH_ROW(b, r) {
+    const IoItem &it = b.item[item_of(b, r)];
+    const int v = r - it.row0;
+    const size_t srow = (size_t)v * it.W, drow = (size_t)v * it.P;
+    if (it.vec) {
+      for (int c = lane; c < it.W / 4; c += 32) {
 #pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            const float4 q = __ldcs(reinterpret_cast<const float4 *>(
-                static_cast<const float *>(it.src[j]) + srow + (size_t)4 * c));
-            *reinterpret_cast<float4 *>(static_cast<float *>(it.dst[j]) + drow + (size_t)4 * c) = q;
-          }
+        for (int j = 0; j < 2; ++j) {
+          const float4 q = __ldcs(reinterpret_cast<const float4 *>(
+              static_cast<const float *>(it.src[j]) + srow + (size_t)4 * c));
+          *reinterpret_cast<float4 *>(static_cast<float *>(it.dst[j]) + drow + (size_t)4 * c) = q;
         }
-      } else {
-        for (int u = threadIdx.x; u < it.W; u += blockDim.x) {
+      }
+    } else {
+      for (int u = lane; u < it.W; u += 32) {
 #pragma unroll
-          for (int j = 0; j < 2; ++j)
-            static_cast<float *>(it.dst[j])[drow + u] = static_cast<const float *>(it.src[j])[srow + u];
-        }
+        for (int j = 0; j < 2; ++j)
+          static_cast<float *>(it.dst[j])[drow + u] = static_cast<const float *>(it.src[j])[srow + u];
       }
     }
   }
@@ -177,30 +182,29 @@ __global__ void __launch_bounds__(kIoThreads) k_io_update(IoBatch b) {
 
 // One row of the depth output: out = exp(x) (or x), dense.
 __global__ void __launch_bounds__(kIoThreads) k_io_fetch(IoBatch b) {
-  for (int r0 = blockIdx.x * kIoRows; r0 < b.total; r0 += gridDim.x * kIoRows) {
-    for (int r = r0; r < r0 + kIoRows && r < b.total; ++r) {
-      const IoItem &it = b.item[item_of(b, r)];
-      const int v = r - it.row0;
-      const size_t srow = (size_t)v * it.P, drow = (size_t)v * it.W;
-      float *out = static_cast<float *>(it.dst[0]);
-      if (it.vec) {
-        for (int c = threadIdx.x; c < it.W / 4; c += blockDim.x) {
-          float4 q = *reinterpret_cast<const float4 *>(it.x + srow + (size_t)4 * c);
-          if (!b.log_space) q = make_float4(expf(q.x), expf(q.y), expf(q.z), expf(q.w));
-          __stcs(reinterpret_cast<float4 *>(out + drow + (size_t)4 * c), q);
-        }
-      } else {
-        for (int u = threadIdx.x; u < it.W; u += blockDim.x) {
-          const float xi = it.x[srow + u];
-          out[drow + u] = b.log_space ? xi : expf(xi);
-        }
+  const int lane = threadIdx.x & 31;
+  IO_FOR_EACH_ROW(b, r) {
+    const IoItem &it = b.item[item_of(b, r)];
+    const int v = r - it.row0;
+    const size_t srow = (size_t)v * it.P, drow = (size_t)v * it.W;
+    float *out = static_cast<float *>(it.dst[0]);
+    if (it.vec) {
+      for (int c = lane; c < it.W / 4; c += 32) {
+        float4 q = *reinterpret_cast<const float4 *>(it.x + srow + (size_t)4 * c);
+        if (!b.log_space) q = make_float4(expf(q.x), expf(q.y), expf(q.z), expf(q.w));
+        __stcs(reinterpret_cast<float4 *>(out + drow + (size_t)4 * c), q);
+      }
+    } else {
+      for (int u = lane; u < it.W; u += 32) {
+        const float xi = it.x[srow + u];
+        out[drow + u] = b.log_space ? xi : expf(xi);
       }
     }
   }
 }
 
 int io_grid(int total_rows) {
-  const int blocks = (total_rows + kIoRows - 1) / kIoRows;
+  const int blocks = (total_rows + kIoWarps - 1) / kIoWarps;
   const int cap = 152 * 8;  // a few waves of 256-thread blocks on every SM
   return blocks < 1 ? 1 : (blocks < cap ? blocks : cap);
 }
