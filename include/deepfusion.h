@@ -501,7 +501,13 @@ df_status df_optimise_noalloc(int32_t width, int32_t height, const float *mu_net
  *             whole GN iterations with the same result
  *   debug_skip_cta  test only: >= 0 makes that CTA of the next fused launches
  *             leave without arriving at its first grid barrier, so the
- *             others' bounded waits run out (DF_ETIMEOUT); -1 = off. */
+ *             others' bounded waits run out (DF_ETIMEOUT); -1 = off.
+ *   assembly  streaming kernel with 4 pixels per lane: where each GN
+ *             iteration's weights and 5-point system are assembled.
+ *             0 auto (= 2), 1 in a pass of the persistent kernel, 2 in an
+ *             ordinary kernel of its own between two persistent launches
+ *             (many warps per SM instead of 8; same arithmetic, the
+ *             reductions summed per piece). */
 typedef struct {
   int32_t mode;
   int32_t vec;
@@ -509,6 +515,7 @@ typedef struct {
   int32_t max_ctas;
   int32_t gn_per_launch;
   int32_t debug_skip_cta;
+  int32_t assembly;
 } df_tuning;
 
 df_status df_set_tuning(const df_tuning *t); /* NULL restores the defaults */

@@ -453,6 +453,8 @@ df_status df_set_tuning(const df_tuning *t) {
     if (t->gn_per_launch < 0) return fail(DF_EINVAL, "gn_per_launch must be >= 0");
     n.gn_per_launch = t->gn_per_launch;
     n.debug_skip_cta = t->debug_skip_cta;
+    if (t->assembly < 0 || t->assembly > 2) return fail(DF_EINVAL, "assembly must be 0, 1 or 2");
+    n.assembly = t->assembly;
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune = n;
@@ -468,6 +470,7 @@ df_status df_get_tuning(df_tuning *t) {
   t->max_ctas = g_tune.max_ctas;
   t->gn_per_launch = g_tune.gn_per_launch;
   t->debug_skip_cta = g_tune.debug_skip_cta;
+  t->assembly = g_tune.assembly;
   return DF_OK;
 }
 
@@ -671,7 +674,8 @@ static df::FusedTuning current_tuning() {
 
 static bool same_tuning(const df::FusedTuning &a, const df::FusedTuning &b) {
   return a.mode == b.mode && a.vec == b.vec && a.tile_rows == b.tile_rows &&
-         a.max_ctas == b.max_ctas && a.debug_skip_cta == b.debug_skip_cta;  // gn_per_launch
+         a.max_ctas == b.max_ctas && a.debug_skip_cta == b.debug_skip_cta &&
+         a.assembly == b.assembly;  // gn_per_launch
                                                                             // does not shape plans
 }
 

@@ -85,10 +85,11 @@ extern "C" df_status df_autotune(df_keyframe *const *kfs, int32_t n, const df_so
   // streaming kernel: each warp walks its whole row share (tile_rows 0) or
   // pieces of at most tile_rows rows, at both vector widths, and the whole
   // share with 1 or 2 GN iterations per launch
-  for (int g : {0, 1}) cand.push_back(df_tuning{2, 0, 0, 0, g, -1});
+  for (int g : {0, 1}) cand.push_back(df_tuning{2, 0, 0, 0, g, -1, 0});
   for (int vec : {1, 4})
-    for (int th : {0, 4, 8, 16, 32, 64}) cand.push_back(df_tuning{1, vec, th, 0, 0, -1});
-  for (int g : {1, 2}) cand.push_back(df_tuning{1, 4, 0, 0, g, -1});
+    for (int th : {0, 4, 8, 16, 32, 64}) cand.push_back(df_tuning{1, vec, th, 0, 0, -1, 0});
+  for (int g : {1, 2}) cand.push_back(df_tuning{1, 4, 0, 0, g, -1, 0});
+  cand.push_back(df_tuning{1, 4, 0, 0, 0, -1, 1});  // the assembly inside the persistent kernel
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);

@@ -68,11 +68,11 @@ struct FusedKf {
   int row_begin;   // first row of its strips in the plan's concatenated row list
   int rows;        // strips * H: a strip is one column tile (32 * VEC columns) over all rows
   int blk;         // rows per row block of its work list (H: one block, strip by strip)
-  int pad1;
+  int asm_rows;    // separate assembly kernel: rows of one piece (one strip's rows)
   int slot_begin;  // this keyframe's slots: [slot_begin, slot_end)
   int slot_end;
   int writer_cta;  // the CTA that writes the final scalars back
-  int pad;
+  int asm_p0;      // separate assembly kernel: the keyframe's first piece
   long long inbox0;  // first slot of its readers' inboxes (within a parity)
 };
 
@@ -191,7 +191,7 @@ __device__ void scale_tile(const FusedKf &K, const Geo &g, float t, const SolveC
 }
 
 // ---- ASSEMBLE: weights, 5-point system and r0 (see df_launch.cu) -----------
-template <int VEC, int DT, int LK>
+template <int VEC, int DT, int LK, bool WIDE = true>  // WIDE: also r.r and b.b
 __device__ void assemble_tile(const FusedKf &K, const Geo &g, float t, const SolveCfg &c,
                               float acc[kQ]) {
   const Planes &k = K.pl;
@@ -300,8 +300,9 @@ __device__ void assemble_tile(const FusedKf &K, const Geo &g, float t, const Sol
         d = ws + wn + wxv.v[e] + wxw.v[e] + wyv.v[e] + wy_up.v[e];
         r = rs + wn * (m - xi) + wxv.v[e] * exv.v[e] - wxw.v[e] * exw.v[e] +
             wyv.v[e] * eyv.v[e] - wy_up.v[e] * ey_up.v[e];
-        b = bs + wn * m - wxv.v[e] * gxv.v[e] + wxw.v[e] * gxw.v[e] - wyv.v[e] * gyv.v[e] +
-            wy_up.v[e] * gy_up.v[e];
+        if (WIDE)
+          b = bs + wn * m - wxv.v[e] * gxv.v[e] + wxw.v[e] * gxw.v[e] - wyv.v[e] * gyv.v[e] +
+              wy_up.v[e] * gy_up.v[e];
       }
       const float id = d > 0.0f ? __fdividef(1.0f, d) : 0.0f;
       dd.v[e] = id;
@@ -309,8 +310,10 @@ __device__ void assemble_tile(const FusedKf &K, const Geo &g, float t, const Sol
       wxo.v[e] = wxv.v[e];
       wyo.v[e] = wyv.v[e];
       acc[0] += r * (r * id);
-      acc[1] += r * r;
-      acc[2] += b * b;
+      if (WIDE) {
+        acc[1] += r * r;
+        acc[2] += b * b;
+      }
     }
     stm<VEC>(k.diag + i, dd);
     stm<VEC>(k.wx + i, wxo);
@@ -1038,6 +1041,80 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
   return rows.ensure(rows.R - 1);
 }
 
+// ---- the assembly as a kernel of its own ------------------------------------
+//
+// For streaming plans the IRLS weights, the 5-point system and r0 of each
+// Gauss-Newton iteration can run as this ordinary kernel between two
+// cooperative launches (the scale step or the previous depth step, and the
+// depth step). The persistent kernel runs every pass with one CTA of 8 warps
+// per SM, which leaves the assembly (the pass with the most arithmetic per
+// byte) bound by instruction latency; here one warp takes one piece (one
+// 128-column strip over asm_rows rows) and each SM holds several blocks of
+// 8 warps, so the loads and the arithmetic of many pieces overlap. Each
+// piece's sums (r.z; r.r and b.b when WIDE) go to its keyframe's partial-sum
+// array as double-float pairs, one entry per piece; the depth step adds them
+// in piece order, so every CTA forms the same scalars.
+constexpr int kAsmThreads = 256;
+constexpr int kAsmWarps = kAsmThreads / 32;
+constexpr int kAsmMaxPieces = kMaxPartialBlocks * kNumQ / kQ;  // float2 entries per keyframe / kQ
+
+__host__ __device__ __forceinline__ int asm_pieces_of(int W, int H, int rows) {
+  return ((W + 127) / 128) * ((H + rows - 1) / rows);
+}
+
+template <int LK, bool WIDE>
+__global__ void __launch_bounds__(kAsmThreads) k_assemble_pieces(const PlanHeader *h, SolveCfg c) {
+  const int piece = blockIdx.x * kAsmWarps + (threadIdx.x >> 5);
+  if (piece >= h->asm_pieces) return;  // whole warps leave
+  const FusedKf *kfs =
+      reinterpret_cast<const FusedKf *>(reinterpret_cast<const char *>(h) + h->off_kf);
+  // the keyframe of this piece: the last one whose first piece is <= piece
+  int lo = 0, hi = h->nkf - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (kfs[mid].asm_p0 <= piece) lo = mid; else hi = mid - 1;
+  }
+  const FusedKf &K = kfs[lo];
+  if (K.pl.sc->flags & kFlagBadInput) return;
+  const int strips = (K.pl.W + 127) / 128;
+  const int q = piece - K.asm_p0, b = q / strips, sx = q - b * strips;
+  const int r0 = b * K.asm_rows;
+  const Geo g = geo_of<4>(sx * 128, r0, min(K.asm_rows, K.pl.H - r0));
+  const float t = (float)K.pl.sc->t;
+  float acc[kQ] = {0.0f, 0.0f, 0.0f};
+  if (K.pl.dtype == DF_BF16)
+    assemble_tile<4, DF_BF16, LK, WIDE>(K, g, t, c, acc);
+  else if (K.pl.dtype == DF_F16)
+    assemble_tile<4, DF_F16, LK, WIDE>(K, g, t, c, acc);
+  else
+    assemble_tile<4, DF_F32, LK, WIDE>(K, g, t, c, acc);
+  float2 *out = reinterpret_cast<float2 *>(K.pl.partial) + (size_t)q * kQ;
+#pragma unroll
+  for (int j = 0; j < (WIDE ? kQ : 1); ++j) {
+    const ff2 sj = warp_sum_ff(ff2{acc[j], 0.0f});
+    if ((threadIdx.x & 31) == 0) __stcg(out + j, make_float2(sj.hi, sj.lo));
+  }
+}
+
+// Quantity q of a keyframe's n piece sums, added by one warp: each lane adds
+// its entries in piece order, then a fixed warp tree (valid in lane 0).
+__device__ __forceinline__ ff2 warp_piece_sum(const double *partial, int n, int q) {
+  const float2 *p = reinterpret_cast<const float2 *>(partial);
+  ff2 acc = ff2{0.0f, 0.0f};
+#pragma unroll 4
+  for (int j = threadIdx.x & 31; j < n; j += 32) {
+    const float2 v = __ldcg(p + (size_t)j * kQ + q);
+    acc = ff_add(acc, ff2{v.x, v.y});
+  }
+  return warp_sum_ff(acc);
+}
+
+// Launch modes of the persistent kernel: the whole schedule, the scale step
+// alone, or one Gauss-Newton iteration's depth step after the separate
+// assembly (with M_FS: take the next scale step's sums in its last pass;
+// with M_RR: reduce r.r in its last pass).
+enum : int { M_FULL = 0, M_SCALE = 1, M_DEPTH = 2, M_FS = 4, M_RR = 8 };
+
 struct Seg {
   double t, bb, rr;
   ff2 gam, alpha, beta;  // CG scalars (double-float)
@@ -1050,7 +1127,7 @@ constexpr int kRingSmem = kWarps * kWarpStageBytes + kWarps * kStages * 8;
 template <int VEC, int LK>
 __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     k_fused(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns,
-            int first) {
+            int first, int mode) {
   extern __shared__ __align__(128) char dyn_ring[];
   __shared__ FusedKf s_kf[kMaxSeg];
   __shared__ Seg s_seg[kMaxSeg];
@@ -1286,18 +1363,40 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     __syncthreads();
   };
 
+  const int lmode = mode & 3;
+  if (lmode == M_SCALE) {  // the scale step alone, before a separate assembly
+    if (do_scale) {
+      alive = run_pass(P_SCALE, 0, 0);
+      if (alive) scale_update(0, 1);
+    }
+    n_gn = 0;
+  }
   bool scale_pending = false;
   for (int gn = 0; gn < n_gn && alive; ++gn) {
-    if (do_scale) {
-      if (!scale_pending) {
-        alive = run_pass(P_SCALE, 0, 0);
-        if (!alive) break;
-        scale_update(0, 1);
+    if (lmode == M_DEPTH) {
+      // the assembly ran as its own kernel: this iteration's r.z (and r.r,
+      // b.b) from its pieces' sums, in piece order
+      const int nqa = wide ? 3 : 1;
+      for (int pq = warp; pq < nseg * nqa; pq += kWarps) {
+        const int sg = pq / nqa, q = pq - sg * nqa;
+        const FusedKf &K = s_kf[sg];
+        const ff2 tot =
+            warp_piece_sum(K.pl.partial, asm_pieces_of(K.pl.W, K.pl.H, K.asm_rows), q);
+        if (lane == 0) s_tot[sg][q] = tot;
       }
-      scale_pending = false;
+      __syncthreads();
+    } else {
+      if (do_scale) {
+        if (!scale_pending) {
+          alive = run_pass(P_SCALE, 0, 0);
+          if (!alive) break;
+          scale_update(0, 1);
+        }
+        scale_pending = false;
+      }
+      alive = run_pass(P_ASSEMBLE, 0, 0);
+      if (!alive) break;
     }
-    alive = run_pass(P_ASSEMBLE, 0, 0);
-    if (!alive) break;
     if (tid < nseg) {
       Seg &S = s_seg[tid];
       S.gam = s_tot[tid][0];
@@ -1329,8 +1428,8 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       if (it == n_pcg - 1) {
         // sums needed: the next scale step's two; r.r for a tolerance and
         // for the report after the launch's last GN iteration
-        const bool fs = do_scale && gn + 1 < n_gn;
-        const bool rr = c.tol > 0.0 || gn + 1 == n_gn;
+        const bool fs = lmode == M_DEPTH ? (mode & M_FS) != 0 : do_scale && gn + 1 < n_gn;
+        const bool rr = lmode == M_DEPTH ? (mode & M_RR) != 0 : c.tol > 0.0 || gn + 1 == n_gn;
         alive = run_pass(P_FINAL, it, (fs ? 1 : 0) | (rr ? 2 : 0));
         if (!alive) break;
         if (tid < nseg) {
@@ -1606,6 +1705,16 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   memcpy(base + hd->off_cta_slot, cs.data(), sizeof(int) * G);
   FusedKf *fk = reinterpret_cast<FusedKf *>(base + hd->off_kf);
   long long ib = 0;
+  // Pieces of the separate assembly kernel (VEC = 4 plans): strips of
+  // asm_rows rows, row block by row block, the strips of a block side by
+  // side. Rows per piece: about kAsmTarget pieces over the whole plan (enough
+  // warps to cover every SM a few times), at least 4 and at most 32 rows
+  // (each piece also weighs the row above it), and few enough pieces per
+  // keyframe for its partial-sum array.
+  constexpr long long kAsmTarget = 8192;
+  const int asm_rows = (int)std::min<long long>(32, std::max<long long>(4, rb[n] / kAsmTarget));
+  long long pieces = 0;
+  bool split = vec == 4 && tune.assembly != 1;
   for (int k = 0; k < n; ++k) {
     fk[k].inbox0 = ib;
     ib += (long long)(se[k] - sb[k]) * inbox_slots(se[k] - sb[k]);
@@ -1616,23 +1725,84 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
     fk[k].slot_begin = sb[k];
     fk[k].slot_end = se[k];
     fk[k].writer_cta = wc[k];
+    const int strips = (kfs[k]->W + 127) / 128, H = kfs[k]->H;
+    int ar = asm_rows;
+    if (strips > kAsmMaxPieces) {
+      split = false;
+    } else if ((long long)strips * ((H + ar - 1) / ar) > kAsmMaxPieces) {
+      const int nb = kAsmMaxPieces / strips;
+      ar = (H + nb - 1) / nb;
+    }
+    fk[k].asm_rows = ar;
+    fk[k].asm_p0 = (int)pieces;
+    pieces += asm_pieces_of(kfs[k]->W, H, ar);
   }
+  if (pieces > INT32_MAX / 2) split = false;
+  hd->asm_pieces = split ? (int)pieces : 0;
   shape.kind = kPlanStreaming;
   shape.G = G;
   shape.vec = vec;
   shape.smem = 0;
+  shape.asm_pieces = hd->asm_pieces;
   return true;
 }
 
+namespace {
+
+const void *assemble_fn(int lk, bool wide) {
+  if (lk == LK_LSQ)
+    return wide ? reinterpret_cast<const void *>(k_assemble_pieces<LK_LSQ, true>)
+                : reinterpret_cast<const void *>(k_assemble_pieces<LK_LSQ, false>);
+  if (lk == LK_TUKEY)
+    return wide ? reinterpret_cast<const void *>(k_assemble_pieces<LK_TUKEY, true>)
+                : reinterpret_cast<const void *>(k_assemble_pieces<LK_TUKEY, false>);
+  return wide ? reinterpret_cast<const void *>(k_assemble_pieces<LK_HUBER, true>)
+              : reinterpret_cast<const void *>(k_assemble_pieces<LK_HUBER, false>);
+}
+
+}  // namespace
+
+// With a separate assembly (shape.asm_pieces > 0 and a depth step to run),
+// a launch of n_gn Gauss-Newton iterations becomes: the scale step (when it
+// is on), then per iteration the assembly kernel and one depth-step launch
+// of the persistent kernel; otherwise one launch of the persistent kernel
+// runs them all.
 cudaError_t streaming_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,
                              int n_pcg, unsigned long long limit_ns, cudaStream_t s, int first) {
   PlanHeader *h = static_cast<PlanHeader *>(dplan);
   const int G = shape.G, vec = shape.vec;
-  void *args[] = {&h, const_cast<SolveCfg *>(&c), &n_gn, &n_pcg, &limit_ns, &first};
-  count_launches(1);
-  const void *fn = fused_fn(vec, loss_kind(c.loss, c.delta));
-  return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args,
-                                     vec == 4 ? (size_t)kRingSmem : 0, s);
+  const int lk = loss_kind(c.loss, c.delta);
+  const void *fn = fused_fn(vec, lk);
+  SolveCfg cc = c;
+  auto coop = [&](int mode, int ngn, int fst) {
+    void *args[] = {&h, &cc, &ngn, &n_pcg, &limit_ns, &fst, &mode};
+    count_launches(1);
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args,
+                                       vec == 4 ? (size_t)kRingSmem : 0, s);
+  };
+  if (shape.asm_pieces <= 0 || n_pcg == 0 || n_gn == 0) return coop(M_FULL, n_gn, first);
+  const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step == DF_SCALE_ALTERNATE;
+  const bool wide = c.tol > 0.0;
+  const void *afn = assemble_fn(lk, wide);
+  const int ablocks = (shape.asm_pieces + kAsmWarps - 1) / kAsmWarps;
+  int fst = first;
+  cudaError_t e = cudaSuccess;
+  if (do_scale) {
+    e = coop(M_SCALE, 0, fst);
+    fst = 0;
+  }
+  for (int g = 0; g < n_gn && e == cudaSuccess; ++g) {
+    const PlanHeader *hc = h;
+    void *aargs[] = {&hc, &cc};
+    count_launches(1);
+    e = cudaLaunchKernel(afn, dim3(ablocks), dim3(kAsmThreads), aargs, 0, s);
+    if (e != cudaSuccess) break;
+    const int mode = M_DEPTH | ((do_scale && g + 1 < n_gn) ? M_FS : 0) |
+                     ((c.tol > 0.0 || g + 1 == n_gn) ? M_RR : 0);
+    e = coop(mode, 1, fst);
+    fst = 0;
+  }
+  return e;
 }
 
 // ---- dispatch between the resident and the streaming kernels -------------

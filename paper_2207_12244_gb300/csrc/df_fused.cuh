@@ -20,6 +20,8 @@ struct FusedTuning {
   int max_ctas = 0;      // cap on the cooperative grid
   int gn_per_launch = 0; // GN iterations per launch (0: all)
   int debug_skip_cta = -1;  // test hook, see df_tuning
+  int assembly = 0;      // streaming: 0 auto (separate kernel), 1 inside the
+                         // persistent kernel, 2 separate kernel
 };
 
 // What one fused launch looks like (filled by fused_build_plan).
@@ -28,6 +30,7 @@ struct LaunchShape {
   int G = 0;      // CTAs
   int vec = 0;    // streaming tile width selector
   int smem = 0;   // dynamic shared memory per CTA (resident)
+  int asm_pieces = 0;  // streaming: pieces of the separate assembly (0: none)
 };
 
 // True when the current device can run the fused solver.

@@ -26,6 +26,8 @@ struct PlanHeader {
   int in_smem;     // resident plans: 1 = each band's input planes are staged
                    // in shared memory for the whole launch
   long long slot_stride;  // doubles per parity of the reduction slots / inboxes
+  int asm_pieces;  // streaming plans: pieces of the separate assembly kernel
+  int asm_pad;
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {

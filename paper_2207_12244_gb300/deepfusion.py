@@ -47,7 +47,7 @@ class df_solve_report(C.Structure):
 class df_tuning(C.Structure):
     _fields_ = [("mode", C.c_int32), ("vec", C.c_int32), ("tile_rows", C.c_int32),
                 ("max_ctas", C.c_int32), ("gn_per_launch", C.c_int32),
-                ("debug_skip_cta", C.c_int32)]
+                ("debug_skip_cta", C.c_int32), ("assembly", C.c_int32)]
 
 
 DF_MODE_AUTO, DF_MODE_STREAMING, DF_MODE_RESIDENT = 0, 1, 2
@@ -603,8 +603,8 @@ def df_optimise_noalloc(width: int, height: int, mu_net, var_net, gx, var_gx, gy
 
 
 def df_set_tuning(mode: int = 0, vec: int = 0, tile_rows: int = 0, max_ctas: int = 0,
-                  debug_skip_cta: int = -1, gn_per_launch: int = 0):
-    t = df_tuning(mode, vec, tile_rows, max_ctas, gn_per_launch, debug_skip_cta)
+                  debug_skip_cta: int = -1, gn_per_launch: int = 0, assembly: int = 0):
+    t = df_tuning(mode, vec, tile_rows, max_ctas, gn_per_launch, debug_skip_cta, assembly)
     _check(load().df_set_tuning(C.byref(t)), "df_set_tuning")
 
 

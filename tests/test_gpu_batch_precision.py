@@ -78,13 +78,17 @@ def test_many_small_keyframes_share_ctas(o):
            for i in range(40)]
     prm = params(n_gn=3, n_pcg=3, solver=dfl.DF_SOLVER_FUSED)
     try:
-        for m, cap in ((dfl.DF_MODE_STREAMING, 4), (dfl.DF_MODE_STREAMING, 0),
-                       (dfl.DF_MODE_RESIDENT, 0)):
-            dfl.df_set_tuning(mode=m, max_ctas=cap)
+        # (mode, grid cap, pixels per lane, assembly placement): the 4-wide
+        # streaming kernel with its assembly in a kernel of its own and in a
+        # pass of the persistent kernel
+        for m, cap, vec, asm in ((dfl.DF_MODE_STREAMING, 4, 0, 0), (dfl.DF_MODE_STREAMING, 0, 0, 0),
+                                 (dfl.DF_MODE_STREAMING, 0, 4, 2), (dfl.DF_MODE_STREAMING, 6, 4, 2),
+                                 (dfl.DF_MODE_STREAMING, 0, 4, 1), (dfl.DF_MODE_RESIDENT, 0, 0, 0)):
+            dfl.df_set_tuning(mode=m, max_ctas=cap, vec=vec, assembly=asm)
             res, _ = _batch(kfs, prm)
             for i, (kf, (x, t)) in enumerate(zip(kfs, res)):
                 xo, to, _ = oracle_solve(o, kf, prm)
-                assert_parity(x, t, xo, to, what=f"mode {m} cap {cap} item {i}")
+                assert_parity(x, t, xo, to, what=f"mode {m} cap {cap} vec {vec} asm {asm} item {i}")
     finally:
         dfl.df_set_tuning()
 

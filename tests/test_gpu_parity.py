@@ -14,12 +14,15 @@ from paper_2207_12244_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# (solver, fused kernel mode): the per-phase launches, the streaming fused
-# kernel and the shared-memory-resident fused kernel
-SOLVERS = [(dfl.DF_SOLVER_LAUNCHES, dfl.DF_MODE_AUTO),
-           (dfl.DF_SOLVER_FUSED, dfl.DF_MODE_STREAMING),
-           (dfl.DF_SOLVER_FUSED, dfl.DF_MODE_RESIDENT)]
-SOLVER_IDS = ["launches", "streaming", "resident"]
+# (solver, fused kernel mode, assembly placement): the per-phase launches,
+# the streaming fused kernel (assembly in a kernel of its own, the default,
+# or in a pass of the persistent kernel) and the shared-memory-resident
+# fused kernel
+SOLVERS = [(dfl.DF_SOLVER_LAUNCHES, dfl.DF_MODE_AUTO, 0),
+           (dfl.DF_SOLVER_FUSED, dfl.DF_MODE_STREAMING, 0),
+           (dfl.DF_SOLVER_FUSED, dfl.DF_MODE_STREAMING, 1),
+           (dfl.DF_SOLVER_FUSED, dfl.DF_MODE_RESIDENT, 0)]
+SOLVER_IDS = ["launches", "streaming", "streaming-inkernel-assembly", "resident"]
 
 
 @pytest.fixture(scope="module")
@@ -29,8 +32,8 @@ def o():
 
 @pytest.fixture(params=SOLVERS, ids=SOLVER_IDS)
 def solver(request):
-    sv, mode = request.param
-    dfl.df_set_tuning(mode=mode)
+    sv, mode, assembly = request.param
+    dfl.df_set_tuning(mode=mode, assembly=assembly)
     yield sv
     dfl.df_set_tuning()
 
