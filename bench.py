@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on the fused kernel's grid")
     ap.add_argument("--vec", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--assembly", type=int, choices=[0, 1, 2], default=0,
+                    help="streaming kernel: where each GN iteration is assembled (0 auto, "
+                         "1 a pass of the persistent kernel, 2 a kernel of its own)")
     ap.add_argument("--workload", choices=["batch64", "sequence", "precision", "serving", "mvs"],
                     default="batch64",
                     help="batch64: 64 keyframes of uneven sizes in one batched solve (default); "
@@ -193,7 +196,7 @@ def traffic_key(args, workload: str) -> str:
         key += f"_{args.loss}"
     if args.mode != "auto":
         key += f"_{args.mode}"
-    for flag in ("max_ctas", "vec", "tile_rows"):
+    for flag in ("max_ctas", "vec", "tile_rows", "assembly"):
         if getattr(args, flag, 0):
             key += f"_{flag}{getattr(args, flag)}"
     return key
@@ -822,7 +825,8 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
 
     def forced_tuning():
         dfl.df_set_tuning(mode={"auto": 0, "streaming": 1, "resident": 2}[args.mode],
-                          vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas)
+                          vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas,
+                          assembly=args.assembly)
 
     graph = None
     graph_launches = 0
@@ -843,14 +847,22 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
         dfl.df_keyframe_reset_batch(handles, cnn_d, stream=sptr)
         dfl.df_frame_update_batch(handles, mu_d, var_d, stream=sptr)
 
+    io_graphs = None  # (reset + frame update, depth output) captured with the solve
+
     def step(record):
-        load_frame()
+        if io_graphs is not None:
+            io_graphs[0].replay()
+        else:
+            load_frame()
         if record:
             ev[0].record(stream)
         solve()
         if record:
             ev[1].record(stream)
-        dfl.df_fetch_depth_batch(handles, outs, stream=sptr)
+        if io_graphs is not None:
+            io_graphs[1].replay()
+        else:
+            dfl.df_fetch_depth_batch(handles, outs, stream=sptr)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -858,13 +870,14 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     torch.cuda.synchronize()
     use_graph = args.workload == "batch64" and not args.no_graph and args.solver != "launches"
     if args.workload == "batch64" and not args.no_autotune and args.solver != "launches" \
-            and args.mode == "auto" and not (args.vec or args.tile_rows or args.max_ctas):
+            and args.mode == "auto" and not (args.vec or args.tile_rows or args.max_ctas
+                                             or args.assembly):
         # launch shape (kernel, tile rows, vector width, GN iterations per
         # launch) picked by timing the candidates on this batch
         best, best_ms = dfl.df_autotune(handles, prm, stream=sptr)
         tuning = {"mode": best.mode, "vec": best.vec, "tile_rows": best.tile_rows,
                   "max_ctas": best.max_ctas, "gn_per_launch": best.gn_per_launch,
-                  "autotune_ms": best_ms}
+                  "assembly": best.assembly, "autotune_ms": best_ms}
     if use_graph:
         # the batched solve captured once in a CUDA graph, replayed per step
         dfl.df_batch_prepare(handles, stream=sptr)
@@ -872,13 +885,22 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
             step(False)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
+        g_load = torch.cuda.CUDAGraph()
+        g_fetch = torch.cuda.CUDAGraph()
         cap0 = dfl.df_kernel_launches()
         with torch.cuda.stream(stream):
             with torch.cuda.graph(g, stream=stream):
                 dfl.df_optimise_batch(handles, prm, stream=sptr)
+            # the per-frame bookkeeping too: device buffers, so nothing is
+            # uploaded and every step replays the same launches
+            with torch.cuda.graph(g_load, stream=stream):
+                load_frame()
+            with torch.cuda.graph(g_fetch, stream=stream):
+                dfl.df_fetch_depth_batch(handles, outs, stream=sptr)
         torch.cuda.synchronize()
-        graph_launches = dfl.df_kernel_launches() - cap0  # kernels in the graph
+        graph_launches = dfl.df_kernel_launches() - cap0  # kernels in the graphs
         graph = g
+        io_graphs = (g_load, g_fetch)
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
                 step(False)
@@ -1021,6 +1043,7 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     used_graph = graph is not None
     if used_graph:
         graph = None
+        io_graphs = None
         dfl.df_batch_release(handles)
     forced_tuning()
     for k in ks:
@@ -1038,7 +1061,7 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
             "config": keyframes_config(args, ws, rank),
             "launch": {"solver": args.solver, "cuda_graph": used_graph, "autotuned": tuning,
                        "kernel_mode": args.mode, "max_ctas": args.max_ctas,
-                       "vec": args.vec, "tile_rows": args.tile_rows},
+                       "vec": args.vec, "tile_rows": args.tile_rows, "assembly": args.assembly},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu,
             "update_latency_ms": lat,
@@ -1074,7 +1097,8 @@ def main():
         dist.barrier()
     dfl.load()
     dfl.df_set_tuning(mode={"auto": 0, "streaming": 1, "resident": 2}[args.mode],
-                      vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas)
+                      vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas,
+                      assembly=args.assembly)
     if args.workload == "serving":
         run_serving(args, ws, rank, dev, torch, dfl, replicas, synth)
         if ws > 1:
@@ -1107,7 +1131,8 @@ def main():
     prm = dfl.df_default_params(n_gn=args.n_gn, n_pcg=args.n_pcg, solver=solver,
                                 scale_step=scale_step, **loss_params(args))
     dfl.df_set_tuning(mode={"auto": 0, "streaming": 1, "resident": 2}[args.mode],
-                      vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas)
+                      vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas,
+                      assembly=args.assembly)
     stream = torch.cuda.Stream(dev)
     sptr = stream.cuda_stream
     k = dfl.Keyframe(W, H, *cnn_d, stream=sptr)
@@ -1266,7 +1291,7 @@ def main():
             "config": sequence_config(args, ws),
             "launch": {"solver": args.solver, "cuda_graph": bool(args.graph),
                        "kernel_mode": args.mode, "max_ctas": args.max_ctas,
-                       "vec": args.vec, "tile_rows": args.tile_rows},
+                       "vec": args.vec, "tile_rows": args.tile_rows, "assembly": args.assembly},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu, "accuracy": accuracy,
             "update_latency_ms": {"p50": float(lat[0]), "p99": float(lat[1]),

@@ -504,10 +504,11 @@ df_status df_optimise_noalloc(int32_t width, int32_t height, const float *mu_net
  *             others' bounded waits run out (DF_ETIMEOUT); -1 = off.
  *   assembly  streaming kernel with 4 pixels per lane: where each GN
  *             iteration's weights and 5-point system are assembled.
- *             0 auto (= 2), 1 in a pass of the persistent kernel, 2 in an
- *             ordinary kernel of its own between two persistent launches
- *             (many warps per SM instead of 8; same arithmetic, the
- *             reductions summed per piece). */
+ *             1 in a pass of the persistent kernel, 2 in an ordinary kernel
+ *             of its own between two persistent launches (many warps per SM
+ *             instead of 8; same arithmetic, the reductions summed per
+ *             piece), 0 auto: 2 when each warp of the persistent kernel
+ *             walks more than 32 rows (batches), else 1. */
 typedef struct {
   int32_t mode;
   int32_t vec;

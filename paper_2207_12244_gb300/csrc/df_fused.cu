@@ -1054,12 +1054,152 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
 // piece's sums (r.z; r.r and b.b when WIDE) go to its keyframe's partial-sum
 // array as double-float pairs, one entry per piece; the depth step adds them
 // in piece order, so every CTA forms the same scalars.
-constexpr int kAsmThreads = 256;
+constexpr int kAsmThreads = 128;
 constexpr int kAsmWarps = kAsmThreads / 32;
 constexpr int kAsmMaxPieces = kMaxPartialBlocks * kNumQ / kQ;  // float2 entries per keyframe / kQ
 
 __host__ __device__ __forceinline__ int asm_pieces_of(int W, int H, int rows) {
   return ((W + 127) / 128) * ((H + rows - 1) / rows);
+}
+
+// One piece of the separate assembly: the arithmetic of assemble_tile (same
+// operations in the same order, so the same bits), with every load of a row
+// issued before any of the row's arithmetic (the plane loads do not wait
+// for the term flags or for each other), and the inputs read through the
+// read-only path (nothing here writes them).
+template <int DT, int LK, bool WIDE>
+__device__ __forceinline__ void assemble_piece(const Planes &k, const Geo &g, float t,
+                                               const SolveCfg &c, float acc[kQ]) {
+  const int lane = threadIdx.x & 31;
+  const int W = k.W, H = k.H;
+  const size_t P = k.P;
+  const bool semi = c.terms & DF_TERM_SEMI, net = c.terms & DF_TERM_NET,
+             grad = c.terms & DF_TERM_GRAD;
+  float *r_out = k.v[1];
+  size_t i = (size_t)g.r0 * P + g.col;
+  F<4> x_cur = ldr<4>(k.x + i);
+  F<4> wy_up = fzero<4>(), ey_up = fzero<4>(), gy_up = fzero<4>();
+  if (grad && g.r0 > 0) {
+    const F<4> xu = ldr<4>(k.x + i - P);
+    const F<4> gyu = ldc<4, DT>(k.cnn[4], i - P), vyu = ldc<4, DT>(k.cnn[5], i - P);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (g.col + e < W) {
+        gy_up.v[e] = gyu.v[e];
+        ey_up.v[e] = x_cur.v[e] - xu.v[e] - gyu.v[e];
+        wy_up.v[e] = robust_weight_k<LK>(ey_up.v[e], vyu.v[e], c.delta);
+      }
+    }
+  }
+  const bool has_w = g.col > 0 && g.col < W, has_e = g.col + 4 < W;
+  for (int j = 0; j < g.nrows; ++j, i += P) {
+    const int v = g.r0 + j;
+    const bool has_dn = v + 1 < H;
+    // every load of the row first
+    const F<4> x_dn = ldr<4>(k.x + (has_dn ? i + P : i));
+    const F<4> gxr = ldc<4, DT>(k.cnn[2], i), vxr = ldc<4, DT>(k.cnn[3], i);
+    const F<4> gyr = ldc<4, DT>(k.cnn[4], i), vyr = ldc<4, DT>(k.cnn[5], i);
+    const F<4> ms = ldr<4>(k.mu_s + i), vs = ldr<4>(k.var_s + i);
+    const F<4> mn = ldc<4, DT>(k.cnn[0], i), vn = ldc<4, DT>(k.cnn[1], i);
+    float xe_l = 0.0f, xw_l = 0.0f, gw_l = 0.0f, vw_l = 1.0f;
+    if (lane == 31 && has_e) xe_l = __ldg(k.x + i + 4);
+    if (lane == 0 && has_w) {
+      xw_l = __ldg(k.x + i - 1);
+      gw_l = ld_cnn<DT>(k.cnn[2], i - 1);
+      vw_l = ld_cnn<DT>(k.cnn[3], i - 1);
+    }
+    F<4> x_e;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) x_e.v[e] = x_cur.v[e + 1];
+    {
+      const float xe = shfl_dn1(x_cur.v[0]);
+      x_e.v[3] = lane == 31 ? xe_l : xe;
+    }
+    F<4> wxv = fzero<4>(), exv = fzero<4>(), gxv = fzero<4>();
+    F<4> wyv = fzero<4>(), eyv = fzero<4>(), gyv = fzero<4>();
+    if (grad) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (g.col + e < W - 1) {
+          gxv.v[e] = gxr.v[e];
+          exv.v[e] = x_e.v[e] - x_cur.v[e] - gxr.v[e];
+          wxv.v[e] = robust_weight_k<LK>(exv.v[e], vxr.v[e], c.delta);
+        }
+      }
+      if (has_dn) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (g.col + e < W) {
+            gyv.v[e] = gyr.v[e];
+            eyv.v[e] = x_dn.v[e] - x_cur.v[e] - gyr.v[e];
+            wyv.v[e] = robust_weight_k<LK>(eyv.v[e], vyr.v[e], c.delta);
+          }
+        }
+      }
+    }
+    F<4> wxw, exw, gxw;
+#pragma unroll
+    for (int e = 1; e < 4; ++e) {
+      wxw.v[e] = wxv.v[e - 1];
+      exw.v[e] = exv.v[e - 1];
+      gxw.v[e] = gxv.v[e - 1];
+    }
+    {
+      float a = shfl_up1(wxv.v[3]), b = shfl_up1(exv.v[3]), gg = shfl_up1(gxv.v[3]);
+      if (lane == 0) {
+        a = b = gg = 0.0f;
+        if (grad && has_w) {
+          gg = gw_l;
+          b = x_cur.v[0] - xw_l - gg;
+          a = robust_weight_k<LK>(b, vw_l, c.delta);
+        }
+      }
+      wxw.v[0] = a;
+      exw.v[0] = b;
+      gxw.v[0] = gg;
+    }
+    F<4> dd, rr_;  // dd holds 1 / diag
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float d = 0.0f, r = 0.0f, b = 0.0f;
+      if (g.col + e < W) {
+        const float xi = x_cur.v[e];
+        float ws = 0.0f, rs = 0.0f, bs = 0.0f;
+        if (semi && semi_valid(ms.v[e], vs.v[e])) {
+          ws = robust_weight_k<LK>(xi - t - ms.v[e], vs.v[e], c.delta);
+          rs = ws * (t + ms.v[e] - xi);
+          bs = ws * (t + ms.v[e]);
+        }
+        float wn = 0.0f, m = 0.0f;
+        if (net) {
+          m = mn.v[e];
+          wn = robust_weight_k<LK>(xi - m, vn.v[e], c.delta);
+        }
+        d = ws + wn + wxv.v[e] + wxw.v[e] + wyv.v[e] + wy_up.v[e];
+        r = rs + wn * (m - xi) + wxv.v[e] * exv.v[e] - wxw.v[e] * exw.v[e] +
+            wyv.v[e] * eyv.v[e] - wy_up.v[e] * ey_up.v[e];
+        if (WIDE)
+          b = bs + wn * m - wxv.v[e] * gxv.v[e] + wxw.v[e] * gxw.v[e] - wyv.v[e] * gyv.v[e] +
+              wy_up.v[e] * gy_up.v[e];
+      }
+      const float id = d > 0.0f ? __fdividef(1.0f, d) : 0.0f;
+      dd.v[e] = id;
+      rr_.v[e] = r;
+      acc[0] += r * (r * id);
+      if (WIDE) {
+        acc[1] += r * r;
+        acc[2] += b * b;
+      }
+    }
+    stm<4>(k.diag + i, dd);
+    stm<4>(k.wx + i, wxv);
+    stm<4>(k.wy + i, wyv);
+    stm<4>(r_out + i, rr_);
+    wy_up = wyv;
+    ey_up = eyv;
+    gy_up = gyv;
+    x_cur = x_dn;
+  }
 }
 
 template <int LK, bool WIDE>
@@ -1083,11 +1223,11 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble_pieces(const PlanHeade
   const float t = (float)K.pl.sc->t;
   float acc[kQ] = {0.0f, 0.0f, 0.0f};
   if (K.pl.dtype == DF_BF16)
-    assemble_tile<4, DF_BF16, LK, WIDE>(K, g, t, c, acc);
+    assemble_piece<DF_BF16, LK, WIDE>(K.pl, g, t, c, acc);
   else if (K.pl.dtype == DF_F16)
-    assemble_tile<4, DF_F16, LK, WIDE>(K, g, t, c, acc);
+    assemble_piece<DF_F16, LK, WIDE>(K.pl, g, t, c, acc);
   else
-    assemble_tile<4, DF_F32, LK, WIDE>(K, g, t, c, acc);
+    assemble_piece<DF_F32, LK, WIDE>(K.pl, g, t, c, acc);
   float2 *out = reinterpret_cast<float2 *>(K.pl.partial) + (size_t)q * kQ;
 #pragma unroll
   for (int j = 0; j < (WIDE ? kQ : 1); ++j) {
@@ -1711,10 +1851,15 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   // warps to cover every SM a few times), at least 4 and at most 32 rows
   // (each piece also weighs the row above it), and few enough pieces per
   // keyframe for its partial-sum array.
+  // Auto placement: a kernel of its own when the warps' shares are long
+  // (batches: ~200 rows; the assembly pass is then a large part of a GN
+  // iteration and gains most from the extra warps), the persistent kernel's
+  // pass when they are short (one large keyframe: ~18 rows per warp, where
+  // two more launches per GN iteration cost more than the pass gains).
   constexpr long long kAsmTarget = 8192;
   const int asm_rows = (int)std::min<long long>(32, std::max<long long>(4, rb[n] / kAsmTarget));
   long long pieces = 0;
-  bool split = vec == 4 && tune.assembly != 1;
+  bool split = vec == 4 && (tune.assembly == 2 || (tune.assembly == 0 && share > 32));
   for (int k = 0; k < n; ++k) {
     fk[k].inbox0 = ib;
     ib += (long long)(se[k] - sb[k]) * inbox_slots(se[k] - sb[k]);
