@@ -389,9 +389,12 @@ df_status df_semi_to_log(const float *depth, const float *var_depth, float *mu_s
  * on a pool of CUDA streams, so frames that arrive while others are being
  * solved are admitted at the next call and overlap on the device. With
  * batching = 0 every frame is solved by its own df_optimise launch in
- * arrival order (the plain baseline). Not thread-safe: one host thread
- * drives a server. Paper counterpart: none (a serving layer of this
- * library). */
+ * arrival order (the plain baseline). In batching mode each launch slot
+ * owns a device and a pinned host buffer for a batched launch's plan (room
+ * for max_batch keyframes), made by df_server_create, and a tick's frame
+ * updates go through df_frame_update_batch when all are device buffers, so
+ * a tick allocates nothing. Not thread-safe: one host thread drives a
+ * server. Paper counterpart: none (a serving layer of this library). */
 typedef struct df_server df_server;
 
 typedef struct {

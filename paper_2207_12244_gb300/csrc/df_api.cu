@@ -1003,6 +1003,57 @@ static df_status check_list(df_keyframe *const *kfs, int32_t n) {
   return DF_OK;
 }
 
+// A batched solve whose launch plan goes through caller-owned buffers: the
+// plan is built on the host into 'hplan' (pinned), copied to 'dplan' on the
+// stream and used for every phase of the schedule; no allocation. Lists that
+// cannot use them (one keyframe, not the fused solver, the joint variant,
+// more keyframes than one launch holds, a plan larger than the buffers, a
+// list that must be split) take df_optimise_batch. The buffers must not be
+// reused before the stream has passed this call.
+extern "C++" {
+namespace df {
+
+df_status optimise_batch_buffered(df_keyframe *const *kfs, int32_t n, const df_solve_params *params,
+                                  cudaStream_t s, void *dplan, size_t dcap, void *hplan,
+                                  size_t hcap) {
+  df_solve_params p;
+  if (params) {
+    p = *params;
+  } else {
+    df_default_params(&p);
+  }
+  if (n <= 1 || n > df::kMaxBatch || !dplan || !hplan || check_params(&p) != DF_OK ||
+      check_joint(p) != DF_OK || pick_solver(p) != DF_SOLVER_FUSED ||
+      p.scale_step == DF_SCALE_JOINT || check_list(kfs, n) != DF_OK)
+    return df_optimise_batch(kfs, n, params, s, nullptr);
+  DeviceGuard g(kfs[0]->device);
+  const df::FusedTuning tune = current_tuning();
+  void *dp = nullptr;
+  df::LaunchShape shape;
+  if (!find_batch_plan(kfs, n, tune, &dp, &shape)) {
+    std::vector<const Planes *> list(n);
+    for (int j = 0; j < n; ++j) list[j] = &kfs[j]->planes;
+    std::vector<char> host;
+    if (!df::fused_build_plan(list.data(), n, tune, host, shape) || host.size() > dcap ||
+        host.size() > hcap)
+      return df_optimise_batch(kfs, n, params, s, nullptr);
+    memcpy(hplan, host.data(), host.size());
+    DF_CUDA(cudaMemcpyAsync(dplan, hplan, host.size(), cudaMemcpyHostToDevice, s));
+    dp = dplan;
+  }
+  df_solve_params ph[2];
+  const int np = df::split_schedule(p, ph);
+  for (int j = 0; j < np; ++j) {
+    df_status st = fused_launches(dp, shape, tune, cfg_of(&ph[j]), ph[j].n_gn, ph[j].n_pcg, s,
+                                  j == 0);
+    if (st != DF_OK) return st;
+  }
+  return DF_OK;
+}
+
+}  // namespace df
+}  // extern "C++"
+
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Fill one launch's item table with keyframes [j0, j0 + m) of the list.

@@ -254,6 +254,12 @@ df_status check_solve_params(const df_solve_params *p);
 // number.
 int split_schedule(const df_solve_params &p, df_solve_params ph[2]);
 SolveCfg solve_cfg(const df_solve_params *p);
+// df_optimise_batch through caller-owned plan buffers (device 'dplan' of
+// dcap bytes, pinned host 'hplan' of hcap bytes): no allocation; falls back
+// to df_optimise_batch for lists that cannot use them (df_api.cu).
+df_status optimise_batch_buffered(df_keyframe *const *kfs, int32_t n, const df_solve_params *params,
+                                  cudaStream_t s, void *dplan, size_t dcap, void *hplan,
+                                  size_t hcap);
 
 int launch_grid(int tiles);  // blocks for a grid-stride launch over 32x8 tiles
 

@@ -7,6 +7,7 @@
 #include <deque>
 #include <vector>
 
+#include "df_fused.cuh"
 #include "df_internal.cuh"
 
 namespace {
@@ -38,6 +39,11 @@ struct Launch {
   bool active = false;
   int64_t t_launch = 0;
   std::vector<Req> reqs;
+  // the slot's launch plan of a batched solve, built on the host into the
+  // pinned buffer and copied to the device buffer every tick; a slot is
+  // refilled only after its previous launch has finished, so both are free
+  void *dplan = nullptr, *hplan = nullptr;
+  size_t plan_cap = 0;
 };
 
 }  // namespace
@@ -117,16 +123,30 @@ df_status start_one(df_server *s, Launch &L, bool *started) {
     if (take.empty()) return DF_OK;
   }
   std::vector<df_keyframe *> kfs;
+  std::vector<const float *> mus, vars;
+  bool all_dev = true;
   for (const Req &r : take) {
-    StreamState &st = s->streams[r.sid];
-    df_status e = df_frame_update(st.kf, r.mu, r.var, r.on_device, L.stream);
-    if (e != DF_OK) return e;
-    st.busy = true;
-    kfs.push_back(st.kf);
+    kfs.push_back(s->streams[r.sid].kf);
+    mus.push_back(r.mu);
+    vars.push_back(r.var);
+    all_dev = all_dev && r.on_device;
   }
-  df_status e = kfs.size() == 1 ? df_optimise(kfs[0], &s->cfg.params, L.stream, nullptr)
-                                : df_optimise_batch(kfs.data(), (int32_t)kfs.size(),
-                                                    &s->cfg.params, L.stream, nullptr);
+  if (all_dev && take.size() > 1) {  // every frame in device memory: one launch
+    df_status e = df_frame_update_batch(kfs.data(), (int32_t)kfs.size(), mus.data(), vars.data(),
+                                        1, L.stream);
+    if (e != DF_OK) return e;
+  } else {
+    for (const Req &r : take) {
+      df_status e = df_frame_update(s->streams[r.sid].kf, r.mu, r.var, r.on_device, L.stream);
+      if (e != DF_OK) return e;
+    }
+  }
+  for (const Req &r : take) s->streams[r.sid].busy = true;
+  df_status e = kfs.size() == 1
+                    ? df_optimise(kfs[0], &s->cfg.params, L.stream, nullptr)
+                    : df::optimise_batch_buffered(kfs.data(), (int32_t)kfs.size(), &s->cfg.params,
+                                                  L.stream, L.dplan, L.plan_cap, L.hplan,
+                                                  L.plan_cap);
   if (e != DF_OK) return e;
   cudaError_t ce = cudaEventRecord(L.done, L.stream);
   if (ce != cudaSuccess) return df::report(DF_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(ce));
@@ -155,9 +175,19 @@ df_status df_server_create(const df_server_config *cfg, df_server **out) {
   if (!s->cfg.batching) s->cfg.max_batch = 1;
   cudaGetDevice(&s->device);
   s->launches.resize(cfg->max_inflight);
+  // plan buffers for batched ticks: room for max_batch keyframes on the
+  // largest fused grid of this device
+  const size_t cap = (s->cfg.batching && s->cfg.max_batch > 1 && df::fused_supported())
+                         ? df::fused_plan_bytes(s->cfg.max_batch, df::fused_max_ctas())
+                         : 0;
   for (Launch &L : s->launches) {
     cudaError_t e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
+    if (e == cudaSuccess && cap > 0) {
+      e = cudaMalloc(&L.dplan, cap);
+      if (e == cudaSuccess) e = cudaMallocHost(&L.hplan, cap);
+      if (e == cudaSuccess) L.plan_cap = cap;
+    }
     if (e != cudaSuccess) {
       df_server_destroy(s);
       return df::report(DF_ECUDA, "server streams: %s", cudaGetErrorString(e));
@@ -176,6 +206,8 @@ void df_server_destroy(df_server *s) {
   for (Launch &L : s->launches) {
     if (L.done) cudaEventDestroy(L.done);
     if (L.stream) cudaStreamDestroy(L.stream);
+    if (L.dplan) cudaFree(L.dplan);
+    if (L.hplan) cudaFreeHost(L.hplan);
   }
   delete s;
 }
