@@ -84,10 +84,11 @@ typedef struct {
  *                     semi-dense weights), preconditioned by diag(A) and
  *                     sum ws. Not in the paper: a solver variant that needs
  *                     no alternation. Runs on the launch solver and, with a
- *                     fixed iteration count (tol = 0), on the fused solver
- *                     when the keyframe's launch shape is shared-memory
- *                     resident; otherwise DF_SOLVER_AUTO takes the launch
- *                     solver and DF_SOLVER_FUSED returns DF_ENOTSUP. Batches
+ *                     fixed iteration count (tol = 0), on the fused solver:
+ *                     the shared-memory resident kernel, or the streaming
+ *                     kernel with 4 pixels per lane and n_pcg >= 1; other
+ *                     launch shapes make DF_SOLVER_AUTO take the launch
+ *                     solver and DF_SOLVER_FUSED return DF_ENOTSUP. Batches
  *                     are solved keyframe by keyframe. */
 #define DF_SCALE_FIXED 0
 #define DF_SCALE_ALTERNATE 1

@@ -694,10 +694,11 @@ static df_status check_joint(const df_solve_params &p) {
 
 // Fused solve of one keyframe: its launch plan lives in the keyframe's own
 // allocation and is uploaded once per launch shape.
-// need_resident: the solve runs only on a shared-memory resident plan (the
-// joint (x, t) solve); DF_ENOTSUP otherwise, before anything is launched.
+// joint: the joint (x, t) solve, which runs on a shared-memory resident
+// plan, or on a streaming plan with 4 pixels per lane and at least one CG
+// iteration; DF_ENOTSUP otherwise, before anything is launched.
 static df_status fused_one(df_keyframe *kf, const SolveCfg &c, int n_gn, int n_pcg,
-                           cudaStream_t s, bool need_resident = false, bool first_phase = true) {
+                           cudaStream_t s, bool joint = false, bool first_phase = true) {
   if (!df::fused_supported() || !kf->plan) return fail(DF_ENOTSUP, "fused solver not available on this device");
   const df::FusedTuning tune = current_tuning();
   if (kf->plan_shape.kind < 0 || !same_tuning(tune, kf->plan_tune)) {
@@ -711,9 +712,10 @@ static df_status fused_one(df_keyframe *kf, const SolveCfg &c, int n_gn, int n_p
     kf->plan_shape = shape;
     kf->plan_tune = tune;
   }
-  if (need_resident && kf->plan_shape.kind != df::kPlanResident)
-    return fail(DF_ENOTSUP, "the joint (x, t) solve needs a shared-memory resident plan; this "
-                            "keyframe's launch shape streams");
+  if (joint && kf->plan_shape.kind != df::kPlanResident &&
+      (kf->plan_shape.vec != 4 || (n_pcg < 1 && n_gn > 0)))
+    return fail(DF_ENOTSUP, "the joint (x, t) solve needs a shared-memory resident plan or a "
+                            "4-wide streaming plan with at least one CG iteration");
   const int chunk = tune.gn_per_launch > 0 ? tune.gn_per_launch : (n_gn > 0 ? n_gn : 1);
   for (int g0 = 0, first = 1; g0 < n_gn || first; g0 += chunk, first = 0) {
     const int m = std::min(chunk, n_gn - g0);

@@ -646,7 +646,7 @@ struct TileRows {
 
 // Plane order of a CG pass's staged rows: the planes a halo row needs
 // (r, s, w, 1/diag, wy) first, then wx, p, x of the own rows.
-template <int KIND>
+template <int KIND, bool JOINT = false>
 struct CgIdx {
   static constexpr int R = 0;
   static constexpr int S = KIND == 2 ? 1 : 0;
@@ -657,8 +657,11 @@ struct CgIdx {
   static constexpr int WX = NH;
   static constexpr int P = KIND == 2 ? WX + 1 : 0;
   static constexpr int X = KIND == 0 ? 0 : (KIND == 1 ? WX + 1 : WX + 2);
-  static constexpr int NP = KIND == 0 ? 4 : (KIND == 1 ? 6 : 8);
+  static constexpr int NP0 = KIND == 0 ? 4 : (KIND == 1 ? 6 : 8);
+  static constexpr int WS = NP0;  // joint: the semi-dense weights (own rows only)
+  static constexpr int NP = NP0 + (JOINT ? 1 : 0);
 };
+static_assert(CgIdx<2, true>::NP <= kMaxStagePlanes, "the joint CG pass stages one more plane");
 
 template <int KIND>
 __device__ __forceinline__ RowNew<4> ring_row_new(const RowRing &ring, int s, float alpha,
@@ -700,11 +703,14 @@ __device__ __forceinline__ float ring_col_u(const RowRing &ring, int s, int idx,
   return r * id;
 }
 
-template <int KIND>
+// JOINT: w = A u - ws u_t (ut: the border's u_t, the same in every CTA), and
+// acc[2] gathers (ws, u) instead of (r, r).
+template <int KIND, bool JOINT = false>
 __device__ __forceinline__ bool tma_cg_tile(RowRing &ring, const FusedKf &K, const Geo &g, float alpha, float beta,
                             const float *r_cur, const float *s_prev, const float *w_cur,
-                            float *r_nxt, float *s_cur, float *w_nxt, float acc[kQ]) {
-  using I = CgIdx<KIND>;
+                            float *r_nxt, float *s_cur, float *w_nxt, float acc[kQ],
+                            float ut = 0.0f) {
+  using I = CgIdx<KIND, JOINT>;
   const Planes &k = K.pl;
   const int lane = threadIdx.x & 31;
   const int W = k.W, H = k.H;
@@ -718,6 +724,7 @@ __device__ __forceinline__ bool tma_cg_tile(RowRing &ring, const FusedKf &K, con
   if constexpr (KIND != 0) pl[I::X] = {k.x, 4};
   pl[I::WX] = {k.wx, 4};
   pl[I::WY] = {k.wy, 4};
+  if constexpr (JOINT) pl[I::WS] = {k.v[7], 4};
   const int jb = g.r0 > 0 ? g.r0 - 1 : g.r0;
   const int je = min(g.r0 + g.nrows, H - 1);
   TileRows<I::NP, I::NH, 0u> rows(ring, pl, g.c0, (int)P, jb, je - jb + 1, g.r0 > 0,
@@ -768,13 +775,26 @@ __device__ __forceinline__ bool tma_cg_tile(RowRing &ring, const FusedKf &K, con
       u_e.v[3] = ue;
     }
     F<4> w_new;
+    if constexpr (JOINT) {
+      const F<4> wsr = f4v(ring.f4(sc, I::WS));
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      w_new.v[e] = cur.r.v[e] - (wxr.v[e] * u_e.v[e] + wx_w.v[e] * u_w.v[e] +
-                                 wyr.v[e] * u_dn.v[e] + wy_up.v[e] * u_up.v[e]);
-      acc[0] += cur.r.v[e] * cur.u.v[e];
-      acc[1] += w_new.v[e] * cur.u.v[e];
-      acc[2] += cur.r.v[e] * cur.r.v[e];
+      for (int e = 0; e < 4; ++e) {
+        w_new.v[e] = cur.r.v[e] - (wxr.v[e] * u_e.v[e] + wx_w.v[e] * u_w.v[e] +
+                                   wyr.v[e] * u_dn.v[e] + wy_up.v[e] * u_up.v[e]) -
+                     wsr.v[e] * ut;
+        acc[0] += cur.r.v[e] * cur.u.v[e];
+        acc[1] += w_new.v[e] * cur.u.v[e];
+        acc[2] += wsr.v[e] * cur.u.v[e];
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        w_new.v[e] = cur.r.v[e] - (wxr.v[e] * u_e.v[e] + wx_w.v[e] * u_w.v[e] +
+                                   wyr.v[e] * u_dn.v[e] + wy_up.v[e] * u_up.v[e]);
+        acc[0] += cur.r.v[e] * cur.u.v[e];
+        acc[1] += w_new.v[e] * cur.u.v[e];
+        acc[2] += cur.r.v[e] * cur.r.v[e];
+      }
     }
     stm<4>(w_nxt + i, w_new);
     if constexpr (KIND != 0) {
@@ -884,7 +904,11 @@ __device__ __forceinline__ bool tma_scale_tile(RowRing &ring, const FusedKf &K, 
 // the own rows also mu_s, var_s (f32) and the other network planes
 enum : int { A_X = 0, A_GY, A_VY, A_MS, A_VS, A_MN, A_VN, A_GX, A_VX, A_NP };
 
-template <int DT, int LK>
+// JOINT: also keep ws (the semi-dense weights, the x-t coupling of the
+// bordered system) in the free work plane v[7], and sum the border's
+// S = sum ws and r_t = sum ws (x - t - mu_s) into acc[1], acc[2] (the joint
+// solve runs with a fixed iteration count: no r.r, b.b here).
+template <int DT, int LK, bool JOINT = false>
 __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &K, const Geo &g, float t,
                                   const SolveCfg &c, bool wide, float acc[kQ]) {
   const Planes &k = K.pl;
@@ -994,10 +1018,11 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
     }
     const F<4> ms = f4v(ring.f4(sc, A_MS)), vs = f4v(ring.f4(sc, A_VS));
     const F<4> mn = cnn4<DT>(ring, sc, A_MN), vn = cnn4<DT>(ring, sc, A_VN);
-    F<4> dd, rr_;
+    F<4> dd, rr_, wsv;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       float d = 0.0f, r = 0.0f, b = 0.0f;
+      wsv.v[e] = 0.0f;
       if (g.col + e < W) {
         const float xi = x_cur.v[e];
         float ws = 0.0f, rs = 0.0f, bs = 0.0f;
@@ -1005,6 +1030,11 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
           ws = robust_weight_k<LK>(xi - t - ms.v[e], vs.v[e], c.delta);
           rs = ws * (t + ms.v[e] - xi);
           bs = ws * (t + ms.v[e]);
+        }
+        if (JOINT) {
+          wsv.v[e] = ws;
+          acc[1] += ws;
+          acc[2] -= rs;  // ws (x - t - mu_s)
         }
         float wn = 0.0f, m = 0.0f;
         if (net) {
@@ -1022,7 +1052,7 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
       dd.v[e] = id;
       rr_.v[e] = r;
       acc[0] += r * (r * id);
-      if (wide) {
+      if (!JOINT && wide) {
         acc[1] += r * r;
         acc[2] += b * b;
       }
@@ -1031,6 +1061,7 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
     stm<4>(k.wx + i, wxv);
     stm<4>(k.wy + i, wyv);
     stm<4>(r_out + i, rr_);
+    if (JOINT) stm<4>(k.v[7] + i, wsv);
     rows.release();
     wy_up = wyv;
     ey_up = eyv;
@@ -1258,13 +1289,19 @@ enum : int { M_FULL = 0, M_SCALE = 1, M_DEPTH = 2, M_FS = 4, M_RR = 8 };
 struct Seg {
   double t, bb, rr;
   ff2 gam, alpha, beta;  // CG scalars (double-float)
+  // joint (x, t) solve: the border's S = sum ws and the t components of the
+  // CG vectors (r_t, u_t, w_t, p_t, s_t) and of the step (the change of t)
+  ff2 jS, jrt, jut, jwt, jpt, jst, jdt;
   int stop, iters, active, pad;
 };
 
 // dynamic shared memory of the VEC = 4 kernel: the warps' row rings + mbarriers
 constexpr int kRingSmem = kWarps * kWarpStageBytes + kWarps * kStages * 8;
 
-template <int VEC, int LK>
+// JOINT (VEC = 4 only): the joint (x, t) variant, Chronopoulos-Gear PCG on
+// the bordered normal equations; each CTA carries the border in its Seg
+// scalars, updated identically everywhere from the reduced sums.
+template <int VEC, int LK, bool JOINT = false>
 __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     k_fused(PlanHeader *h, SolveCfg c, int n_gn, int n_pcg, unsigned long long limit_ns,
             int first, int mode) {
@@ -1299,6 +1336,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       const Scalars *sc = kfs[kk].pl.sc;
       s.t = sc->t;
       s.gam = s.alpha = s.beta = ff2{0.0f, 0.0f};
+      s.jS = s.jrt = s.jut = s.jwt = s.jpt = s.jst = s.jdt = ff2{0.0f, 0.0f};
       s.bb = 0.0;
       s.rr = sc->rr;
       s.stop = 0;
@@ -1336,9 +1374,9 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     int q0 = 0, nq = kQ;
     switch (kind) {
       case P_SCALE: nq = 2; break;                                      // sum w, sum w (x - mu_s)
-      case P_ASSEMBLE: nq = wide ? 3 : 1; break;                         // r.z (r.r, b.b)
-      case P_INIT: q0 = 1; nq = 1; break;                                // (w, u)
-      case P_ITER: nq = c.tol > 0.0 ? 3 : 2; break;                      // (r, u), (w, u) (r.r)
+      case P_ASSEMBLE: nq = (JOINT || wide) ? 3 : 1; break;              // r.z (r.r, b.b | S, r_t)
+      case P_INIT: q0 = 1; nq = JOINT ? 2 : 1; break;                    // (w, u) ((ws, u))
+      case P_ITER: nq = (JOINT || c.tol > 0.0) ? 3 : 2; break;           // (r, u), (w, u) (r.r | (ws, u))
       default:                                                           // (r.r) (scale sums)
         q0 = (fin & 2) ? 0 : 1;
         nq = ((fin & 2) ? 1 : 0) + ((fin & 1) ? 2 : 0);
@@ -1375,7 +1413,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       const Geo g = geo_of<VEC>(sx * 32 * VEC, r0, nrows);
       float a[kQ] = {0.0f, 0.0f, 0.0f};
       // hi is the float nearest to a double-float value
-      const float ft = (float)S.t, fa = S.alpha.hi, fb = S.beta.hi;
+      const float ft = (float)S.t, fa = S.alpha.hi, fb = S.beta.hi, fu = S.jut.hi;
       float *R0 = K.pl.v[1], *R1 = K.pl.v[2], *S0 = K.pl.v[3], *S1 = K.pl.v[4];
       float *W0 = K.pl.v[5], *W1 = K.pl.v[6];
       float *Rc = (it & 1) ? R1 : R0, *Rn = (it & 1) ? R0 : R1;
@@ -1389,21 +1427,22 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
             break;
           case P_ASSEMBLE:
             if (K.pl.dtype == DF_BF16)
-              ok = tma_assemble_tile<DF_BF16, LK>(rg, K, g, ft, c, wide, a);
+              ok = tma_assemble_tile<DF_BF16, LK, JOINT>(rg, K, g, ft, c, wide, a);
             else if (K.pl.dtype == DF_F16)
-              ok = tma_assemble_tile<DF_F16, LK>(rg, K, g, ft, c, wide, a);
+              ok = tma_assemble_tile<DF_F16, LK, JOINT>(rg, K, g, ft, c, wide, a);
             else
-              ok = tma_assemble_tile<DF_F32, LK>(rg, K, g, ft, c, wide, a);
+              ok = tma_assemble_tile<DF_F32, LK, JOINT>(rg, K, g, ft, c, wide, a);
             break;
           case P_INIT:
-            if (!S.stop) ok = tma_cg_tile<0>(rg, K, g, 0.0f, 0.0f, R0, S0, W1, R1, S1, W0, a);
+            if (!S.stop)
+              ok = tma_cg_tile<0, JOINT>(rg, K, g, 0.0f, 0.0f, R0, S0, W1, R1, S1, W0, a, fu);
             break;
           case P_ITER:
             if (!S.stop) {
               if (it == 0)
-                ok = tma_cg_tile<1>(rg, K, g, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
+                ok = tma_cg_tile<1, JOINT>(rg, K, g, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a, fu);
               else
-                ok = tma_cg_tile<2>(rg, K, g, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a);
+                ok = tma_cg_tile<2, JOINT>(rg, K, g, fa, fb, Rc, Sp, Wc, Rn, Sc, Wn, a, fu);
             }
             break;
           default:  // P_FINAL
@@ -1503,6 +1542,19 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     __syncthreads();
   };
 
+  // The border of the joint solve moves with the iteration's alpha, beta
+  // (right after they are formed): p_t = u_t + beta p_t, s_t = w_t + beta
+  // s_t, the change of t += alpha p_t, r_t -= alpha s_t, u_t = r_t / S.
+  auto joint_border_step = [](Seg &S, bool first_it) {
+    const ff2 a = S.alpha;
+    S.jpt = first_it ? S.jut : ff_add(S.jut, ff_mul(S.beta, S.jpt));
+    S.jst = first_it ? S.jwt : ff_add(S.jwt, ff_mul(S.beta, S.jst));
+    S.jdt = ff_add(S.jdt, ff_mul(a, S.jpt));
+    S.jrt = ff_sub(S.jrt, ff_mul(a, S.jst));
+    S.jut = S.jS.hi > 0.0f ? ff_div(S.jrt, S.jS) : ff2{0.0f, 0.0f};
+  };
+  static_assert(!JOINT || VEC == 4, "the joint variant runs on the 4-wide kernel");
+
   const int lmode = mode & 3;
   if (lmode == M_SCALE) {  // the scale step alone, before a separate assembly
     if (do_scale) {
@@ -1541,7 +1593,14 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       Seg &S = s_seg[tid];
       S.gam = s_tot[tid][0];
       S.stop = 0;
-      if (c.tol > 0.0 || n_pcg == 0) {
+      if constexpr (JOINT) {
+        // border of the bordered system: S = sum ws, r_t, u_t = r_t / S
+        S.jS = s_tot[tid][1];
+        S.jrt = s_tot[tid][2];
+        S.jut = S.jS.hi > 0.0f ? ff_div(S.jrt, S.jS) : ff2{0.0f, 0.0f};
+        S.jdt = ff2{0.0f, 0.0f};
+        S.gam = ff_add(S.gam, ff_mul(S.jrt, S.jut));
+      } else if (c.tol > 0.0 || n_pcg == 0) {
         S.rr = ff_to_double(s_tot[tid][1]);
         S.bb = ff_to_double(s_tot[tid][2]);
         S.stop = (c.tol > 0.0 && sqrt(S.rr) < c.tol * sqrt(S.bb)) ? 1 : 0;
@@ -1554,12 +1613,17 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     if (tid < nseg) {
       Seg &S = s_seg[tid];
       if (!S.stop) {
-        const ff2 dl = s_tot[tid][0];  // (w0, u0)
+        ff2 dl = s_tot[tid][0];  // (w0, u0)
+        if constexpr (JOINT) {  // w_t = S u_t - (ws, u); (w, u) gains w_t u_t
+          S.jwt = ff_sub(ff_mul(S.jS, S.jut), s_tot[tid][1]);
+          dl = ff_add(dl, ff_mul(S.jwt, S.jut));
+        }
         if (S.gam.hi == 0.0f || !(dl.hi > 0.0f)) {
           S.stop = 1;
         } else {
           S.alpha = ff_div(S.gam, dl);
           S.beta = ff2{0.0f, 0.0f};
+          if constexpr (JOINT) joint_border_step(S, true);
         }
       }
     }
@@ -1574,9 +1638,15 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
         if (!alive) break;
         if (tid < nseg) {
           Seg &S = s_seg[tid];
+          if constexpr (JOINT) {  // the depth step's change of t
+            S.t += ff_to_double(S.jdt);
+            S.jdt = ff2{0.0f, 0.0f};
+          }
           if (!S.stop) {
             S.iters += 1;
-            if (rr) S.rr = ff_to_double(s_tot[tid][0]);
+            if (rr)
+              S.rr = ff_to_double(JOINT ? ff_add(s_tot[tid][0], ff_mul(S.jrt, S.jrt))
+                                        : s_tot[tid][0]);
           }
         }
         __syncthreads();
@@ -1592,8 +1662,14 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
           Seg &S = s_seg[tid];
           if (!S.stop) {
             S.iters += 1;
-            if (c.tol > 0.0) S.rr = ff_to_double(s_tot[tid][2]);
-            const ff2 gn_ = s_tot[tid][0], dl = s_tot[tid][1];
+            ff2 gn_ = s_tot[tid][0], dl = s_tot[tid][1];
+            if constexpr (JOINT) {  // border terms of (r, u) and (w, u)
+              S.jwt = ff_sub(ff_mul(S.jS, S.jut), s_tot[tid][2]);
+              gn_ = ff_add(gn_, ff_mul(S.jrt, S.jut));
+              dl = ff_add(dl, ff_mul(S.jwt, S.jut));
+            } else if (c.tol > 0.0) {
+              S.rr = ff_to_double(s_tot[tid][2]);
+            }
             if (c.tol > 0.0 && sqrt(S.rr) < c.tol * sqrt(S.bb)) {
               S.stop = 1;
             } else {
@@ -1606,6 +1682,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
                 S.beta = beta;
                 S.alpha = ff_div(gn_, denom);
                 S.gam = gn_;
+                if constexpr (JOINT) joint_border_step(S, false);
               }
             }
           }
@@ -1643,8 +1720,14 @@ DevInfo g_dev[64];
 bool g_dev_init[64] = {false};
 std::mutex g_dev_mu;
 
-// The kernel instance of a vector width and a loss kind.
-const void *fused_fn(int vec, int lk) {
+// The kernel instance of a vector width, a loss kind and the joint variant
+// (4-wide only).
+const void *fused_fn(int vec, int lk, bool joint = false) {
+  if (vec == 4 && joint) {
+    if (lk == LK_LSQ) return reinterpret_cast<const void *>(k_fused<4, LK_LSQ, true>);
+    if (lk == LK_TUKEY) return reinterpret_cast<const void *>(k_fused<4, LK_TUKEY, true>);
+    return reinterpret_cast<const void *>(k_fused<4, LK_HUBER, true>);
+  }
   if (vec == 4) {
     if (lk == LK_LSQ) return reinterpret_cast<const void *>(k_fused<4, LK_LSQ>);
     if (lk == LK_TUKEY) return reinterpret_cast<const void *>(k_fused<4, LK_TUKEY>);
@@ -1673,13 +1756,17 @@ const DevInfo &dev_info() {
     // follows the least resident of them
     d.occ[0] = d.occ[1] = 1 << 20;
     for (int lk = LK_LSQ; lk <= LK_TUKEY; ++lk) {
-      int o1 = 0, o4 = 0;
+      int o1 = 0, o4 = 0, o4j = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, fused_fn(1, lk), kThreads, 0);
       cudaFuncSetAttribute(fused_fn(4, lk), cudaFuncAttributeMaxDynamicSharedMemorySize,
                            kRingSmem);
+      cudaFuncSetAttribute(fused_fn(4, lk, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kRingSmem);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o4, fused_fn(4, lk), kThreads, kRingSmem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o4j, fused_fn(4, lk, true), kThreads,
+                                                    kRingSmem);
       d.occ[0] = std::min(d.occ[0], o1);
-      d.occ[1] = std::min(d.occ[1], o4);
+      d.occ[1] = std::min(d.occ[1], std::min(o4, o4j));
     }
     cudaGetLastError();
     g_dev[dev] = d;
@@ -1917,7 +2004,8 @@ cudaError_t streaming_launch(void *dplan, const LaunchShape &shape, const SolveC
   PlanHeader *h = static_cast<PlanHeader *>(dplan);
   const int G = shape.G, vec = shape.vec;
   const int lk = loss_kind(c.loss, c.delta);
-  const void *fn = fused_fn(vec, lk);
+  const bool joint = (c.terms & DF_TERM_SEMI) && c.scale_step == DF_SCALE_JOINT;
+  const void *fn = fused_fn(vec, lk, joint);
   SolveCfg cc = c;
   auto coop = [&](int mode, int ngn, int fst) {
     void *args[] = {&h, &cc, &ngn, &n_pcg, &limit_ns, &fst, &mode};
@@ -1925,7 +2013,8 @@ cudaError_t streaming_launch(void *dplan, const LaunchShape &shape, const SolveC
     return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args,
                                        vec == 4 ? (size_t)kRingSmem : 0, s);
   };
-  if (shape.asm_pieces <= 0 || n_pcg == 0 || n_gn == 0) return coop(M_FULL, n_gn, first);
+  if (shape.asm_pieces <= 0 || n_pcg == 0 || n_gn == 0 || joint)  // joint: the in-kernel pass
+    return coop(M_FULL, n_gn, first);
   const bool do_scale = (c.terms & DF_TERM_SEMI) && c.scale_step == DF_SCALE_ALTERNATE;
   const bool wide = c.tol > 0.0;
   const void *afn = assemble_fn(lk, wide);

@@ -20,11 +20,22 @@ def o():
     return orc.get()
 
 
-SOLVERS = [dfl.DF_SOLVER_LAUNCHES, dfl.DF_SOLVER_FUSED]
+# (solver, fused kernel mode, pixels per lane): the launch solver, the
+# resident kernel, and the streaming kernel with 4 pixels per lane
+SOLVERS = [(dfl.DF_SOLVER_LAUNCHES, dfl.DF_MODE_AUTO, 0),
+           (dfl.DF_SOLVER_FUSED, dfl.DF_MODE_RESIDENT, 0),
+           (dfl.DF_SOLVER_FUSED, dfl.DF_MODE_STREAMING, 4)]
 
 
-@pytest.mark.parametrize("solver", SOLVERS, ids=["launches", "resident"])
-@pytest.mark.parametrize("W,H", [(256, 192), (37, 23), (1, 1), (129, 3), (3, 130)])
+@pytest.fixture(params=SOLVERS, ids=["launches", "resident", "streaming"])
+def solver(request):
+    sv, mode, vec = request.param
+    dfl.df_set_tuning(mode=mode, vec=vec)
+    yield sv
+    dfl.df_set_tuning()
+
+
+@pytest.mark.parametrize("W,H", [(256, 192), (37, 23), (1, 1), (129, 3), (3, 130), (300, 41)])
 @pytest.mark.parametrize("delta", [1.345, float("inf")], ids=["huber", "l2"])
 def test_joint_matches_oracle(o, W, H, delta, solver):
     kf = synth.make_keyframe(W, H, 300 + W + H)
@@ -37,15 +48,28 @@ def test_joint_matches_oracle(o, W, H, delta, solver):
         assert abs(t) > 1e-3  # the border moved t
 
 
+def test_joint_on_the_streaming_kernel_at_1920x1440(o):
+    """A keyframe beyond the on-chip capacity: the joint solve runs on the
+    streaming kernel (4 pixels per lane, the automatic launch shape) with
+    DF_SOLVER_FUSED and matches the oracle at every pixel."""
+    kf = synth.make_keyframe(1920, 1440, 33)
+    prm = params(n_gn=10, n_pcg=3, scale_step=JOINT, solver=dfl.DF_SOLVER_FUSED)
+    x, t, rep = solve(kf, prm)
+    xo, to, ro = oracle_solve(o, kf, prm)
+    assert rep.iters_done == ro.iters_done == 30
+    assert_parity(x, t, xo, to, what="joint 1920x1440 streaming")
+    assert abs(t) > 1e-3
+
+
 def test_joint_routing(o):
     """AUTO runs the joint solve on the resident kernel, or on the launch
-    solver where the launch shape streams or a tolerance is set; FUSED is
-    refused in those cases."""
+    solver where the launch shape streams one pixel per lane or a tolerance
+    is set; FUSED is refused in those cases."""
     kf = synth.make_keyframe(96, 72, 7)
     want = oracle_solve(o, kf, params(n_gn=5, n_pcg=4, scale_step=JOINT))
     x, t, _ = solve(kf, params(n_gn=5, n_pcg=4, scale_step=JOINT, solver=dfl.DF_SOLVER_AUTO))
     assert_parity(x, t, want[0], want[1], what="joint auto")
-    dfl.df_set_tuning(mode=dfl.DF_MODE_STREAMING)
+    dfl.df_set_tuning(mode=dfl.DF_MODE_STREAMING, vec=1)
     try:
         x, t, _ = solve(kf, params(n_gn=5, n_pcg=4, scale_step=JOINT, solver=dfl.DF_SOLVER_AUTO))
         assert_parity(x, t, want[0], want[1], what="joint auto, streaming shape")
@@ -89,7 +113,6 @@ def test_long_runs_of_both_variants(o):
     assert abs(tj - tstar) < 0.1 * abs(ta - tstar)
 
 
-@pytest.mark.parametrize("solver", SOLVERS, ids=["launches", "resident"])
 def test_joint_warm_started_sequence(o, solver):
     torch = torch_cuda()
     kf, mus, vs = synth.make_sequence(128, 96, 23, n_frames=30)
