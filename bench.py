@@ -301,7 +301,7 @@ def keyframes_config(args, ws, rank=0):
     name, shapes, dt_name = keyframe_shapes(args, rank)
     return {"workload": name, "keyframes": len(shapes), "pixels": sum(W * H for W, H in shapes),
             "cnn_dtype": dt_name, "n_gn": args.n_gn, "n_pcg": args.n_pcg, "loss": args.loss,
-            "parallelism": f"replicas x{ws}", "l2": L2_NOTE}
+            "scale_step": args.scale_step, "parallelism": f"replicas x{ws}", "l2": L2_NOTE}
 
 
 def synth_batch_shapes(n, seed):
@@ -428,7 +428,8 @@ def keyframe_pool(args, rank, n_workers=None):
     _, shapes, _ = keyframe_shapes(args, rank)
     seeds = keyframe_seeds(args, rank, shapes)
     jobs = [(W, H, sd) for (W, H), sd in zip(shapes, seeds)]
-    kw = dict(n_gn=args.n_gn, n_pcg=args.n_pcg, **loss_params(args))
+    kw = dict(n_gn=args.n_gn, n_pcg=args.n_pcg, scale_step=SCALE_STEPS[args.scale_step],
+              **loss_params(args))
     model, cores = host_cpu()
     n = min(cores, len(jobs)) if n_workers is None else n_workers
     return OraclePool(jobs, kw, n), model, cores
@@ -814,7 +815,8 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     outs = [torch.empty((kf.height, kf.width), dtype=torch.float32, device=dev) for kf in kfs]
     solver = {"auto": dfl.DF_SOLVER_AUTO, "launches": dfl.DF_SOLVER_LAUNCHES,
               "fused": dfl.DF_SOLVER_FUSED}[args.solver]
-    prm = dfl.df_default_params(n_gn=n_gn, n_pcg=n_pcg, solver=solver, **loss_params(args))
+    prm = dfl.df_default_params(n_gn=n_gn, n_pcg=n_pcg, solver=solver,
+                                scale_step=SCALE_STEPS[args.scale_step], **loss_params(args))
     stream = torch.cuda.Stream(dev)
     sptr = stream.cuda_stream
     ks = [dfl.Keyframe(kf.width, kf.height, *c, cnn_dtype=code, stream=sptr)
