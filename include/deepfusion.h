@@ -512,7 +512,7 @@ df_status df_optimise_noalloc(int32_t width, int32_t height, const float *mu_net
  *             of its own between two persistent launches (many warps per SM
  *             instead of 8; same arithmetic, the reductions summed per
  *             piece), 0 auto: 2 when each warp of the persistent kernel
- *             walks more than 32 rows (batches), else 1. */
+ *             walks 56 rows or more (large batches), else 1. */
 typedef struct {
   int32_t mode;
   int32_t vec;

@@ -1007,7 +1007,9 @@ static df_status check_list(df_keyframe *const *kfs, int32_t n) {
 
 // A batched solve whose launch plan goes through caller-owned buffers: the
 // plan is built on the host into 'hplan' (pinned), copied to 'dplan' on the
-// stream and used for every phase of the schedule; no allocation. Lists that
+// stream and used for every phase of the schedule; no allocation. With
+// one_launch (and the automatic placement) the streaming kernel keeps its
+// assembly, so each phase is one cooperative launch. Lists that
 // cannot use them (one keyframe, not the fused solver, the joint variant,
 // more keyframes than one launch holds, a plan larger than the buffers, a
 // list that must be split) take df_optimise_batch. The buffers must not be
@@ -1017,7 +1019,7 @@ namespace df {
 
 df_status optimise_batch_buffered(df_keyframe *const *kfs, int32_t n, const df_solve_params *params,
                                   cudaStream_t s, void *dplan, size_t dcap, void *hplan,
-                                  size_t hcap) {
+                                  size_t hcap, bool one_launch) {
   df_solve_params p;
   if (params) {
     p = *params;
@@ -1029,7 +1031,8 @@ df_status optimise_batch_buffered(df_keyframe *const *kfs, int32_t n, const df_s
       p.scale_step == DF_SCALE_JOINT || check_list(kfs, n) != DF_OK)
     return df_optimise_batch(kfs, n, params, s, nullptr);
   DeviceGuard g(kfs[0]->device);
-  const df::FusedTuning tune = current_tuning();
+  df::FusedTuning tune = current_tuning();
+  if (one_launch && tune.assembly == 0) tune.assembly = 1;  // the assembly in the persistent kernel
   void *dp = nullptr;
   df::LaunchShape shape;
   if (!find_batch_plan(kfs, n, tune, &dp, &shape)) {

@@ -211,6 +211,15 @@ int io_grid(int total_rows) {
 
 }  // namespace
 
+void preload_io_kernels() {
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, k_io_zero_scalars);
+  cudaFuncGetAttributes(&fa, k_io_reset);
+  cudaFuncGetAttributes(&fa, k_io_update);
+  cudaFuncGetAttributes(&fa, k_io_fetch);
+  cudaGetLastError();
+}
+
 cudaError_t launch_io(IoKind kind, const IoBatch &b, cudaStream_t s) {
   if (b.n <= 0 || b.total <= 0) return cudaSuccess;
   const int grid = io_grid(b.total);

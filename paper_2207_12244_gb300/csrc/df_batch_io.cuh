@@ -37,4 +37,8 @@ enum class IoKind { kReset, kUpdate, kFetch };
 
 cudaError_t launch_io(IoKind kind, const IoBatch &b, cudaStream_t s);
 
+// Load the batched-bookkeeping kernels on the current device now rather than
+// at their first launch.
+void preload_io_kernels();
+
 }  // namespace df

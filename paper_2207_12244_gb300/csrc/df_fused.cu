@@ -47,6 +47,7 @@
 #include <mutex>
 #include <vector>
 
+#include "df_batch_io.cuh"
 #include "df_fused.cuh"
 #include "df_sync.cuh"
 #include "df_tma.cuh"
@@ -1738,6 +1739,18 @@ const void *fused_fn(int vec, int lk, bool joint = false) {
   return reinterpret_cast<const void *>(k_fused<1, LK_HUBER>);
 }
 
+// The separate assembly's instance of a loss kind (WIDE: with r.r, b.b).
+const void *assemble_fn(int lk, bool wide) {
+  if (lk == LK_LSQ)
+    return wide ? reinterpret_cast<const void *>(k_assemble_pieces<LK_LSQ, true>)
+                : reinterpret_cast<const void *>(k_assemble_pieces<LK_LSQ, false>);
+  if (lk == LK_TUKEY)
+    return wide ? reinterpret_cast<const void *>(k_assemble_pieces<LK_TUKEY, true>)
+                : reinterpret_cast<const void *>(k_assemble_pieces<LK_TUKEY, false>);
+  return wide ? reinterpret_cast<const void *>(k_assemble_pieces<LK_HUBER, true>)
+              : reinterpret_cast<const void *>(k_assemble_pieces<LK_HUBER, false>);
+}
+
 const DevInfo &dev_info() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -1767,7 +1780,14 @@ const DevInfo &dev_info() {
                                                     kRingSmem);
       d.occ[0] = std::min(d.occ[0], o1);
       d.occ[1] = std::min(d.occ[1], std::min(o4, o4j));
+      // load the kernels a solve may switch to now, not at their first
+      // launch in the middle of a run (lazy module loading can stall a
+      // launch for milliseconds)
+      cudaFuncAttributes fa;
+      cudaFuncGetAttributes(&fa, assemble_fn(lk, false));
+      cudaFuncGetAttributes(&fa, assemble_fn(lk, true));
     }
+    preload_io_kernels();
     cudaGetLastError();
     g_dev[dev] = d;
     g_dev_init[dev] = true;
@@ -1939,14 +1959,16 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   // (each piece also weighs the row above it), and few enough pieces per
   // keyframe for its partial-sum array.
   // Auto placement: a kernel of its own when the warps' shares are long
-  // (batches: ~200 rows; the assembly pass is then a large part of a GN
-  // iteration and gains most from the extra warps), the persistent kernel's
-  // pass when they are short (one large keyframe: ~18 rows per warp, where
-  // two more launches per GN iteration cost more than the pass gains).
+  // (the 64-keyframe batch: ~200 rows, 8 % faster), the persistent kernel's
+  // pass when they are shorter (one large keyframe: ~18 rows per warp,
+  // where two more launches per GN iteration cost more than the pass
+  // gains). Measured on batches of equal keyframes (10 GN x 3 or 5 PCG) the
+  // two break even at ~48 rows per warp (six 1280 x 960 keyframes) and the
+  // separate kernel is ahead from ~56 (eight 1280 x 960, or 32 of 640 x 480).
   constexpr long long kAsmTarget = 8192;
   const int asm_rows = (int)std::min<long long>(32, std::max<long long>(4, rb[n] / kAsmTarget));
   long long pieces = 0;
-  bool split = vec == 4 && (tune.assembly == 2 || (tune.assembly == 0 && share > 32));
+  bool split = vec == 4 && (tune.assembly == 2 || (tune.assembly == 0 && share >= 56));
   for (int k = 0; k < n; ++k) {
     fk[k].inbox0 = ib;
     ib += (long long)(se[k] - sb[k]) * inbox_slots(se[k] - sb[k]);
@@ -1979,20 +2001,6 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   return true;
 }
 
-namespace {
-
-const void *assemble_fn(int lk, bool wide) {
-  if (lk == LK_LSQ)
-    return wide ? reinterpret_cast<const void *>(k_assemble_pieces<LK_LSQ, true>)
-                : reinterpret_cast<const void *>(k_assemble_pieces<LK_LSQ, false>);
-  if (lk == LK_TUKEY)
-    return wide ? reinterpret_cast<const void *>(k_assemble_pieces<LK_TUKEY, true>)
-                : reinterpret_cast<const void *>(k_assemble_pieces<LK_TUKEY, false>);
-  return wide ? reinterpret_cast<const void *>(k_assemble_pieces<LK_HUBER, true>)
-              : reinterpret_cast<const void *>(k_assemble_pieces<LK_HUBER, false>);
-}
-
-}  // namespace
 
 // With a separate assembly (shape.asm_pieces > 0 and a depth step to run),
 // a launch of n_gn Gauss-Newton iterations becomes: the scale step (when it

@@ -257,9 +257,11 @@ SolveCfg solve_cfg(const df_solve_params *p);
 // df_optimise_batch through caller-owned plan buffers (device 'dplan' of
 // dcap bytes, pinned host 'hplan' of hcap bytes): no allocation; falls back
 // to df_optimise_batch for lists that cannot use them (df_api.cu).
+// one_launch: keep each phase one cooperative launch (no separate assembly
+// kernel under the automatic placement).
 df_status optimise_batch_buffered(df_keyframe *const *kfs, int32_t n, const df_solve_params *params,
                                   cudaStream_t s, void *dplan, size_t dcap, void *hplan,
-                                  size_t hcap);
+                                  size_t hcap, bool one_launch);
 
 int launch_grid(int tiles);  // blocks for a grid-stride launch over 32x8 tiles
 
