@@ -206,19 +206,22 @@ df_status df_batch_release(df_keyframe *const *kfs, int32_t n);
  * keyframe (paper counterpart: none; the same work as the single-keyframe
  * calls it names). kfs: n distinct keyframes on one device (DF_EINVAL
  * otherwise, before anything runs). Stream-ordered; the caller keeps its
- * buffers and must not modify them until the stream reaches the call. With
- * device pointers nothing is uploaded and the calls can be captured in a
- * CUDA graph; with host pointers each keyframe goes through the
- * single-keyframe call.
+ * buffers and must not modify them until the stream has passed the call.
+ * With device pointers nothing is uploaded and the calls can be captured in
+ * a CUDA graph. Host pointers into page-locked (pinned) memory are treated
+ * like device pointers: the kernels read and write them directly over the
+ * host link (so the reset's input check runs on the device and flags a
+ * keyframe rather than returning DF_EINVAL). Other host pointers go through
+ * the single-keyframe calls.
  *
  * df_keyframe_reset_batch: df_keyframe_reset of keyframe j from
  *   planes[6j .. 6j+5] = mu_net, var_net, gx, var_gx, gy, var_gy (each
  *   dense row-major in keyframe j's cnn_dtype): the planes are copied in,
  *   x = mu_n and t = 0 (Section II: a keyframe starts from the network's
  *   prediction), the semi-dense variance is cleared, and the inputs are
- *   checked (host pointers: all before any keyframe is touched, DF_EINVAL;
- *   device pointers: on the device, flagging the keyframe as
- *   df_keyframe_reset does).
+ *   checked (pageable host pointers: all before any keyframe is touched,
+ *   DF_EINVAL; device and pinned host pointers: on the device, flagging the
+ *   keyframe as df_keyframe_reset does with device pointers).
  * df_frame_update_batch: df_frame_update of keyframe j from mu_semi[j],
  *   var_semi[j] (dense f32, log space, Section II-B).
  * df_fetch_depth_batch: df_fetch_depth of keyframe j into out[j] (dense f32:

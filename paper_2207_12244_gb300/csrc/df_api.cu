@@ -1061,6 +1061,23 @@ df_status optimise_batch_buffered(df_keyframe *const *kfs, int32_t n, const df_s
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Host buffers in page-locked (pinned) memory are read and written by the
+// batched kernels directly: *out gets each one's device-side address. False
+// (and nothing changed) if any of them is pageable.
+static bool pinned_all(const void *const *p, int n, std::vector<const void *> *out) {
+  out->resize(n);
+  for (int j = 0; j < n; ++j) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p[j]) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    (*out)[j] = a.devicePointer;
+  }
+  return true;
+}
+
 // Fill one launch's item table with keyframes [j0, j0 + m) of the list.
 extern "C++" {
 template <typename Fill>
@@ -1104,9 +1121,16 @@ df_status df_keyframe_reset_batch(df_keyframe *const *kfs, int32_t n, const void
   for (int j = 0; j < 6 * n; ++j)
     if (!planes[j]) return fail(DF_EINVAL, "network plane %d of keyframe %d is NULL", j % 6, j / 6);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<const void *> mapped;
+  if (!ptrs_on_device && pinned_all(planes, 6 * n, &mapped)) {
+    // pinned host planes: the kernel reads them directly and checks them on
+    // the device, as it does device planes
+    planes = mapped.data();
+    ptrs_on_device = 1;
+  }
   if (!ptrs_on_device) {
-    // host planes: every keyframe's inputs are checked before any is touched,
-    // then each goes up through its staging plane
+    // pageable host planes: every keyframe's inputs are checked before any is
+    // touched, then each goes up through its staging plane
     for (int j = 0; j < n; ++j) {
       char why[256];
       if (!host_inputs_ok(planes + 6 * j, kfs[j]->W, kfs[j]->H, kfs[j]->dtype, why, sizeof why))
@@ -1143,6 +1167,13 @@ df_status df_frame_update_batch(df_keyframe *const *kfs, int32_t n, const float 
   if (!mu_semi || !var_semi) return fail(DF_EINVAL, "plane list is NULL");
   for (int j = 0; j < n; ++j)
     if (!mu_semi[j] || !var_semi[j]) return fail(DF_EINVAL, "semi-dense plane of keyframe %d is NULL", j);
+  std::vector<const void *> mu_m, var_m;
+  if (!ptrs_on_device && pinned_all(reinterpret_cast<const void *const *>(mu_semi), n, &mu_m) &&
+      pinned_all(reinterpret_cast<const void *const *>(var_semi), n, &var_m)) {
+    mu_semi = reinterpret_cast<const float *const *>(mu_m.data());
+    var_semi = reinterpret_cast<const float *const *>(var_m.data());
+    ptrs_on_device = 1;  // pinned: read directly by the kernel
+  }
   if (!ptrs_on_device) {
     // host planes: each keyframe's upload overlaps the previous solve as in
     // df_frame_update
@@ -1171,6 +1202,13 @@ df_status df_fetch_depth_batch(df_keyframe *const *kfs, int32_t n, float *const 
   if (!out) return fail(DF_EINVAL, "output list is NULL");
   for (int j = 0; j < n; ++j)
     if (!out[j]) return fail(DF_EINVAL, "output of keyframe %d is NULL", j);
+  std::vector<const void *> out_m;
+  std::vector<float *> out_w;
+  if (!ptrs_on_device && pinned_all(reinterpret_cast<const void *const *>(out), n, &out_m)) {
+    for (const void *q : out_m) out_w.push_back(static_cast<float *>(const_cast<void *>(q)));
+    out = out_w.data();
+    ptrs_on_device = 1;  // pinned: written directly by the kernel
+  }
   if (!ptrs_on_device) {
     for (int j = 0; j < n; ++j) {
       st = df_fetch_depth(kfs[j], out[j], log_space, 0, stream);

@@ -240,3 +240,46 @@ def test_batched_calls_refuse_bad_lists():
     finally:
         for k in ks:
             k.close()
+
+
+def test_pinned_host_buffers_are_read_and_written_directly():
+    """Pinned host buffers take the kernels' direct path: the same bits as
+    device buffers for the reset, the frame update and the depth output;
+    an invalid network value flags its keyframe on the device (the call
+    itself succeeds, as with device buffers)."""
+    torch = torch_cuda()
+    kfs, dts = _make(10, seed=700)
+    a, b = _keyframes(kfs, dts), _keyframes(kfs, dts)
+    try:
+        dev = [_planes(kf, dt) for kf, dt in zip(kfs, dts)]
+        pin = [[p.cpu().pin_memory() for p in ps] for ps in dev]
+        pin[3][1][2, 5] = -1.0  # a negative network variance in pinned memory
+        dev[3][1][2, 5] = -1.0
+        dfl.df_keyframe_reset_batch([k.handle for k in a], dev)
+        dfl.df_keyframe_reset_batch([k.handle for k in b], pin)
+        mu_p = [torch.from_numpy(np.ascontiguousarray(kf.mu_s)).pin_memory() for kf in kfs]
+        var_p = [torch.from_numpy(np.ascontiguousarray(kf.var_s)).pin_memory() for kf in kfs]
+        dfl.df_frame_update_batch([k.handle for k in a], [to_dev(kf.mu_s) for kf in kfs],
+                                  [to_dev(kf.var_s) for kf in kfs])
+        dfl.df_frame_update_batch([k.handle for k in b], mu_p, var_p)
+        prm = params(n_gn=2, n_pcg=2, solver=dfl.DF_SOLVER_FUSED)
+        dfl.df_optimise_batch([k.handle for k in a], prm)
+        dfl.df_optimise_batch([k.handle for k in b], prm)
+        dev_out = [torch.empty((kf.height, kf.width), device="cuda") for kf in kfs]
+        pin_out = [torch.empty((kf.height, kf.width)).pin_memory() for kf in kfs]
+        dfl.df_fetch_depth_batch([k.handle for k in a], dev_out)
+        dfl.df_fetch_depth_batch([k.handle for k in b], pin_out)
+        torch.cuda.synchronize()
+        for i, (d, h) in enumerate(zip(dev_out, pin_out)):
+            assert torch.equal(d.cpu(), h), i
+        for i, (ka, kb) in enumerate(zip(a, b)):
+            for k in (ka, kb):
+                if i == 3:
+                    with pytest.raises(dfl.DFError) as e:
+                        k.check()
+                    assert e.value.status == dfl.DF_EINVAL
+                else:
+                    k.check()
+    finally:
+        for k in a + b:
+            k.close()
