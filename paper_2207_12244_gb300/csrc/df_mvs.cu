@@ -119,60 +119,6 @@ struct Walk {
   float key[5];            // keyframe samples
 };
 
-// bilin without a branch: the sample is read at clamped, in-bounds
-// coordinates whatever (x, y) is, and the return value says whether (x, y)
-// was inside the image; inside, the value is bilin's, bit for bit.
-__device__ __forceinline__ bool bilin_nb(const float *__restrict__ I, int W, int H, float x, float y,
-                                         float *out) {
-  const bool in = x >= 0.0f && y >= 0.0f && x <= (float)(W - 1) && y <= (float)(H - 1);
-  const float xc = fminf(fmaxf(x, 0.0f), (float)(W - 1));  // NaN -> 0
-  const float yc = fminf(fmaxf(y, 0.0f), (float)(H - 1));
-  const int x0 = min((int)floorf(xc), W - 2), y0 = min((int)floorf(yc), H - 2);
-  const float ax = xc - (float)x0, ay = yc - (float)y0;
-  const float *r0 = I + (size_t)y0 * W + x0;
-  const float *r1 = r0 + W;
-  const float top = (1.0f - ax) * __ldg(r0) + ax * __ldg(r0 + 1);
-  const float bot = (1.0f - ax) * __ldg(r1) + ax * __ldg(r1 + 1);
-  *out = (1.0f - ay) * top + ay * bot;
-  return in;
-}
-
-// step_error of the walk, branch-free (every gather is issued whatever the
-// step's validity, so two steps' gathers can be in flight together); the
-// return value is step_error's, and for valid steps so are e, *ssd, *dj.
-__device__ __forceinline__ bool step_error_nb(const Walk &w, const MvsGeo &g,
-                                              const float *__restrict__ I1, int W, int H, int j,
-                                              float e[5], float *ssd, float *dj) {
-  const float qx = w.P0x + (float)j * w.dx, qy = w.P0y + (float)j * w.dy;
-  float d;
-  if (w.use_x) {
-    const float qt = (qx - g.cx) * g.ifx;
-    d = (g.t[0] - qt * g.t[2]) / (qt * w.a0[2] - w.a0[0]);
-  } else {
-    const float qt = (qy - g.cy) * g.ify;
-    d = (g.t[1] - qt * g.t[2]) / (qt * w.a0[2] - w.a0[1]);
-  }
-  bool ok = d > 0.0f && isfinite(d);
-  float s2 = 0.0f;
-#pragma unroll
-  for (int s = -2; s <= 2; ++s) {
-    const float sf = (float)s;
-    const float Y0 = d * (w.a0[0] + sf * w.a1[0]) + g.t[0];
-    const float Y1 = d * (w.a0[1] + sf * w.a1[1]) + g.t[1];
-    const float Y2 = d * (w.a0[2] + sf * w.a1[2]) + g.t[2];
-    ok = ok && Y2 > 0.0f;
-    const float iz = 1.0f / Y2;  // one exact reciprocal for both coordinates
-    const float pu = g.fx * Y0 * iz + g.cx, pv = g.fy * Y1 * iz + g.cy;
-    float val;
-    ok = bilin_nb(I1, W, H, pu, pv, &val) && ok;
-    e[s + 2] = val - w.key[s + 2];
-    s2 += e[s + 2] * e[s + 2];
-  }
-  *ssd = s2;
-  *dj = d;
-  return ok;
-}
-
 // Photometric error 5-vector, SSD and depth of step j (Eq. 2).
 __device__ __forceinline__ bool step_error(const Walk &w, const MvsGeo &g,
                                            const float *__restrict__ I1, int W, int H, int j,
@@ -295,25 +241,9 @@ __global__ void __launch_bounds__(kSearchThreads)
       float best = INFINITY;
       int bj = 0x7fffffff;
       const int n = ok ? w.n : 0;
-      // two steps per round (j, j + kGroup), taken in step order, so the
-      // first minimum is the one-step walk's
-      int j = lane;
-      for (; j + kGroup < n; j += 2 * kGroup) {
-        float ea[5], eb[5], sa, sb, da, db;
-        const bool oka = step_error_nb(w, g, img_ref, W, H, j, ea, &sa, &da);
-        const bool okb = step_error_nb(w, g, img_ref, W, H, j + kGroup, eb, &sb, &db);
-        if (oka && sa < best) {
-          best = sa;
-          bj = j;
-        }
-        if (okb && sb < best) {
-          best = sb;
-          bj = j + kGroup;
-        }
-      }
-      if (j < n) {
+      for (int j = lane; j < n; j += kGroup) {
         float ev[5], ssd, dj;
-        if (step_error_nb(w, g, img_ref, W, H, j, ev, &ssd, &dj) && ssd < best) {
+        if (step_error(w, g, img_ref, W, H, j, ev, &ssd, &dj) && ssd < best) {
           best = ssd;
           bj = j;
         }
