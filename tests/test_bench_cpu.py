@@ -112,3 +112,20 @@ def _args(argv):
         return bench.parse()
     finally:
         sys.argv = old
+
+
+def test_batch_reference_arm_uses_our_config_on_every_core():
+    """The default workload's reference arm: the oracle over all 64 keyframes
+    on the host's cores, with the config our arm prints (same workload keys,
+    same values)."""
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([ln for ln in out.stdout.splitlines() if ln.strip()][-1])
+    assert d["config"] == bench.keyframes_config(_args([]), 1)
+    assert d["config"]["workload"] == "batch64-uneven-10x3-fp32"
+    cb = d["cpu_baseline"]
+    assert cb["cores"] == min(cb["host_cores"], 64) and cb["cores"] >= 1
+    assert d["value"] > 0 and d["e2e"]["value"] == d["value"]
