@@ -283,3 +283,48 @@ def test_pinned_host_buffers_are_read_and_written_directly():
     finally:
         for k in a + b:
             k.close()
+
+
+def test_pinned_host_step_captured_in_a_cuda_graph():
+    """The whole per-frame step from pinned host buffers (reset, frame
+    update, batched solve, depth output) captured once and replayed: the
+    replay reads the host inputs and writes the host outputs again, equal
+    to the eager step bitwise."""
+    torch = torch_cuda()
+    kfs, dts = _make(12, seed=720)
+    pin = [[p.cpu().pin_memory() for p in _planes(kf, dt)] for kf, dt in zip(kfs, dts)]
+    mu_p = [torch.from_numpy(np.ascontiguousarray(kf.mu_s)).pin_memory() for kf in kfs]
+    var_p = [torch.from_numpy(np.ascontiguousarray(kf.var_s)).pin_memory() for kf in kfs]
+    outs = [torch.empty((kf.height, kf.width)).pin_memory() for kf in kfs]
+    prm = params(n_gn=3, n_pcg=2, solver=dfl.DF_SOLVER_FUSED)
+    ks = _keyframes(kfs, dts)
+    h = [k.handle for k in ks]
+    try:
+        s = torch.cuda.Stream()
+
+        def frame():
+            dfl.df_keyframe_reset_batch(h, pin, stream=s)
+            dfl.df_frame_update_batch(h, mu_p, var_p, stream=s)
+            dfl.df_optimise_batch(h, prm, stream=s)
+            dfl.df_fetch_depth_batch(h, outs, stream=s)
+
+        with torch.cuda.stream(s):
+            frame()
+        torch.cuda.synchronize()
+        eager = [o.clone() for o in outs]
+        dfl.df_batch_prepare(h)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                frame()
+        for o in outs:
+            o.zero_()
+        with torch.cuda.stream(s):
+            g.replay()
+        torch.cuda.synchronize()
+        for i, (e, o) in enumerate(zip(eager, outs)):
+            assert torch.equal(e, o), i
+        dfl.df_batch_release(h)
+    finally:
+        for k in ks:
+            k.close()
