@@ -44,8 +44,9 @@ WORKLOAD = "sequence-640x480-100f-10x5-fp32"  # the default sequence workload
 
 def sequence_name(args) -> str:
     """Name of the sequence workload a run measures (WORKLOAD by default)."""
+    v = "" if getattr(args, "variant", "paper") == "paper" else f"-{args.variant}"
     return (f"sequence-{args.width}x{args.height}-{args.frames}f-"
-            f"{args.n_gn}x{args.n_pcg}-fp32")
+            f"{args.n_gn}x{args.n_pcg}-fp32{v}")
 SCALE_STEPS = {"fixed": 0, "alternate": 1, "joint": 2}  # DF_SCALE_* values
 ALG_BYTES_PER_PCG_PX = 56  # canonical streaming model of one PCG iteration
 ALG_BYTES_PER_GN_PX = 56   # scale step + re-weighting / assembly per GN iteration
@@ -68,6 +69,11 @@ def parse():
     ap.add_argument("--n-pcg", type=int, default=None,
                     help="PCG iterations per GN iteration (default: the workload's, 5 for the "
                          "sequence, 3 for the keyframe workloads)")
+    ap.add_argument("--variant", choices=["paper", "table2", "table3"], default="paper",
+                    help="paper: the full cost with the alternating scale step; table2: semi-dense "
+                         "+ gradient terms with the scale fixed, then the least-squares scale fit "
+                         "to the network depth (Table II); table3: semi-dense + network terms, no "
+                         "pairwise term (Table III)")
     ap.add_argument("--loss", choices=["huber", "lsq", "tukey", "huber-tukey"], default="huber",
                     help="robust loss: Huber (delta 1.345, the default), least squares, "
                          "Tukey's biweight (c 4.685), or 3 Huber GN iterations then Tukey")
@@ -120,6 +126,19 @@ def loss_params(args):
     kw = {"delta": delta, "loss": loss}
     if warm:
         kw.update(warm_gn=warm, warm_delta=1.345)
+    return kw
+
+
+# df_solve_params.terms of each --variant (DF_TERM_SEMI = 1, NET = 2, GRAD = 4)
+VARIANT_TERMS = {"paper": 7, "table2": 5, "table3": 3}
+
+
+def method_params(args):
+    """The solve's method fields (loss, terms, scale step): the same keyword
+    arguments for df_default_params and for the oracle's optimise."""
+    kw = loss_params(args)
+    kw["terms"] = VARIANT_TERMS[args.variant]
+    kw["scale_step"] = SCALE_STEPS["fixed" if args.variant == "table2" else args.scale_step]
     return kw
 
 
@@ -189,7 +208,7 @@ def traffic_key(args, workload: str) -> str:
     the solver, the workload and every launch-shape or method flag that
     changes which kernel runs (a forced mode, grid cap, tile shape, the joint
     scale step)."""
-    key = f"solve_{args.solver}_{workload}"
+    key = f"solve_{args.solver}_{workload}"  # the workload name carries a --variant
     if getattr(args, "scale_step", "alternate") != "alternate":
         key += f"_{args.scale_step}"
     if getattr(args, "loss", "huber") != "huber":
@@ -279,15 +298,17 @@ def sequence_config(args, ws):
     """config of the sequence workload (the same in both arms)."""
     return {"workload": sequence_name(args), "width": args.width, "height": args.height,
             "frames": args.frames, "n_gn": args.n_gn, "n_pcg": args.n_pcg, "loss": args.loss,
-            "scale_step": args.scale_step, "parallelism": f"replicas x{ws}", "l2": L2_NOTE}
+            "scale_step": args.scale_step, "variant": args.variant,
+            "parallelism": f"replicas x{ws}", "l2": L2_NOTE}
 
 
 def keyframe_shapes(args, rank):
     """(name, [(W, H)], network-plane dtype name) of a keyframe workload."""
+    v = "" if args.variant == "paper" else f"-{args.variant}"
     if args.workload == "batch64":
         shapes = synth_batch_shapes(64, rank_seed(args.seed, rank))
-        return f"batch64-uneven-{args.n_gn}x{args.n_pcg}-fp32", shapes, "f32"
-    return (f"keyframe-1920x1440-{args.n_gn}x{args.n_pcg}-{args.cnn_dtype}", [(1920, 1440)],
+        return f"batch64-uneven-{args.n_gn}x{args.n_pcg}-fp32{v}", shapes, "f32"
+    return (f"keyframe-1920x1440-{args.n_gn}x{args.n_pcg}-{args.cnn_dtype}{v}", [(1920, 1440)],
             args.cnn_dtype)
 
 
@@ -301,7 +322,8 @@ def keyframes_config(args, ws, rank=0):
     name, shapes, dt_name = keyframe_shapes(args, rank)
     return {"workload": name, "keyframes": len(shapes), "pixels": sum(W * H for W, H in shapes),
             "cnn_dtype": dt_name, "n_gn": args.n_gn, "n_pcg": args.n_pcg, "loss": args.loss,
-            "scale_step": args.scale_step, "parallelism": f"replicas x{ws}", "l2": L2_NOTE}
+            "scale_step": args.scale_step, "variant": args.variant,
+            "parallelism": f"replicas x{ws}", "l2": L2_NOTE}
 
 
 def synth_batch_shapes(n, seed):
@@ -361,6 +383,8 @@ def _oracle_worker(conn, jobs, solve_kw):
     from paper_2207_12244_gb300 import synth
 
     o = oracle.get()
+    solve_kw = dict(solve_kw)
+    ls_fit = solve_kw.pop("ls_fit", False)
     kfs = [synth.make_keyframe(W, H, seed) for W, H, seed in jobs]
     conn.send(0.0)
     while True:
@@ -369,7 +393,9 @@ def _oracle_worker(conn, jobs, solve_kw):
             break
         t0 = time.perf_counter()
         for kf in kfs:
-            o.optimise(kf, **solve_kw)
+            x, t, _ = o.optimise(kf, **solve_kw)
+            if ls_fit:  # Table II: the scale fitted to the network depth
+                o.ls_scale_fit(kf, x, t)
         conn.send(time.perf_counter() - t0)
     conn.close()
 
@@ -428,8 +454,8 @@ def keyframe_pool(args, rank, n_workers=None):
     _, shapes, _ = keyframe_shapes(args, rank)
     seeds = keyframe_seeds(args, rank, shapes)
     jobs = [(W, H, sd) for (W, H), sd in zip(shapes, seeds)]
-    kw = dict(n_gn=args.n_gn, n_pcg=args.n_pcg, scale_step=SCALE_STEPS[args.scale_step],
-              **loss_params(args))
+    kw = dict(n_gn=args.n_gn, n_pcg=args.n_pcg, **method_params(args))
+    kw["ls_fit"] = args.variant == "table2"
     model, cores = host_cpu()
     n = min(cores, len(jobs)) if n_workers is None else n_workers
     return OraclePool(jobs, kw, n), model, cores
@@ -477,7 +503,9 @@ def _sequence_reference(args, kf, mus, vs, n_frames):
         view.mu_s, view.var_s = mus[step % n_frames], vs[step % n_frames]
         t0 = time.perf_counter()
         xr, t, _ = o.optimise(view, x0=x, t0=t, n_gn=args.n_gn, n_pcg=args.n_pcg,
-                               scale_step=SCALE_STEPS[args.scale_step], **loss_params(args))
+                               **method_params(args))
+        if args.variant == "table2":
+            xr, t = o.ls_scale_fit(view, xr, t)
         dt = time.perf_counter() - t0
         x = xr.ravel()
         if step >= args.warmup:
@@ -575,7 +603,9 @@ def cpu_baseline(args, kf, mus, vs):
     while True:
         view.mu_s, view.var_s = mus[n % args.frames], vs[n % args.frames]
         xr, t, _ = o.optimise(view, x0=x, t0=t, n_gn=args.n_gn, n_pcg=args.n_pcg,
-                               scale_step=SCALE_STEPS[args.scale_step], **loss_params(args))
+                               **method_params(args))
+        if args.variant == "table2":
+            xr, t = o.ls_scale_fit(view, xr, t)
         x = xr.ravel()
         n += 1
         el = time.perf_counter() - t_start
@@ -815,8 +845,8 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     outs = [torch.empty((kf.height, kf.width), dtype=torch.float32, device=dev) for kf in kfs]
     solver = {"auto": dfl.DF_SOLVER_AUTO, "launches": dfl.DF_SOLVER_LAUNCHES,
               "fused": dfl.DF_SOLVER_FUSED}[args.solver]
-    prm = dfl.df_default_params(n_gn=n_gn, n_pcg=n_pcg, solver=solver,
-                                scale_step=SCALE_STEPS[args.scale_step], **loss_params(args))
+    prm = dfl.df_default_params(n_gn=n_gn, n_pcg=n_pcg, solver=solver, **method_params(args))
+    ls_fit = args.variant == "table2"
     stream = torch.cuda.Stream(dev)
     sptr = stream.cuda_stream
     ks = [dfl.Keyframe(kf.width, kf.height, *c, cnn_dtype=code, stream=sptr)
@@ -851,6 +881,14 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
 
     io_graphs = None  # (reset + frame update, depth output) captured with the solve
 
+    def output():
+        # Table II: the scale fitted to the network depth after the
+        # scale-ambiguous solve; then the depth maps
+        if ls_fit:
+            for k in ks:
+                k.scale_fit_ls(stream=sptr)
+        dfl.df_fetch_depth_batch(handles, outs, stream=sptr)
+
     def step(record):
         if io_graphs is not None:
             io_graphs[0].replay()
@@ -864,7 +902,7 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
         if io_graphs is not None:
             io_graphs[1].replay()
         else:
-            dfl.df_fetch_depth_batch(handles, outs, stream=sptr)
+            output()
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -898,7 +936,7 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
             with torch.cuda.graph(g_load, stream=stream):
                 load_frame()
             with torch.cuda.graph(g_fetch, stream=stream):
-                dfl.df_fetch_depth_batch(handles, outs, stream=sptr)
+                output()
         torch.cuda.synchronize()
         graph_launches = dfl.df_kernel_launches() - cap0  # kernels in the graphs
         graph = g
@@ -957,6 +995,9 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
             dfl.df_keyframe_reset_batch(handles, cnn_h, stream=sptr)
             dfl.df_frame_update_batch(handles, mu_h, var_h, stream=sptr)
             solve()
+            if ls_fit:
+                for k in ks:
+                    k.scale_fit_ls(stream=sptr)
             dfl.df_fetch_depth_batch(handles, outs_h, stream=sptr)
 
         with torch.cuda.stream(stream):
@@ -975,6 +1016,9 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
                         dfl.df_keyframe_reset_batch(handles, cnn_h, stream=sptr)
                         dfl.df_frame_update_batch(handles, mu_h, var_h, stream=sptr)
                         dfl.df_optimise_batch(handles, prm, stream=sptr)
+                        if ls_fit:
+                            for k in ks:
+                                k.scale_fit_ls(stream=sptr)
                         dfl.df_fetch_depth_batch(handles, outs_h, stream=sptr)
                 torch.cuda.synchronize()
                 with torch.cuda.stream(stream):
@@ -1024,6 +1068,8 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
                 if record:
                     evk[j][0].record(stream)
                 k.optimise(prm, stream=sptr)
+                if ls_fit:
+                    k.scale_fit_ls(stream=sptr)
                 if record:
                     evk[j][1].record(stream)
 
@@ -1158,10 +1204,9 @@ def main():
     out_d = torch.empty((F, H, W), dtype=torch.float32, device=dev)
     solver = {"auto": dfl.DF_SOLVER_AUTO, "launches": dfl.DF_SOLVER_LAUNCHES,
               "fused": dfl.DF_SOLVER_FUSED}[args.solver]
-    scale_step = {"alternate": dfl.DF_SCALE_ALTERNATE, "joint": dfl.DF_SCALE_JOINT,
-                  "fixed": dfl.DF_SCALE_FIXED}[args.scale_step]
     prm = dfl.df_default_params(n_gn=args.n_gn, n_pcg=args.n_pcg, solver=solver,
-                                scale_step=scale_step, **loss_params(args))
+                                **method_params(args))
+    ls_fit = args.variant == "table2"
     dfl.df_set_tuning(mode={"auto": 0, "streaming": 1, "resident": 2}[args.mode],
                       vec=args.vec, tile_rows=args.tile_rows, max_ctas=args.max_ctas,
                       assembly=args.assembly)
@@ -1180,10 +1225,6 @@ def main():
     mu_in = torch.empty_like(mus_d[0])
     var_in = torch.empty_like(vs_d[0])
     out_fix = torch.empty((H, W), dtype=torch.float32, device=dev)
-
-    def frame_eager(f):
-        k.frame_update(mus_d[f], vs_d[f], stream=sptr)
-        k.optimise(prm, stream=sptr)
 
     def step(record_solve: bool):
         k.reset(*cnn_d, stream=sptr)
@@ -1204,6 +1245,8 @@ def main():
                 k.optimise(prm, stream=sptr)
                 if record_solve:
                     ev_opt[f][1].record(stream)
+                if ls_fit:  # Table II: the scale fitted to the network depth
+                    k.scale_fit_ls(stream=sptr)
                 k.fetch_depth(out_d[f], stream=sptr)
 
     with torch.cuda.stream(stream):
@@ -1217,6 +1260,8 @@ def main():
             with torch.cuda.graph(g, stream=stream):
                 k.frame_update(mu_in, var_in, stream=sptr)
                 k.optimise(prm, stream=sptr)
+                if ls_fit:
+                    k.scale_fit_ls(stream=sptr)
                 k.fetch_depth(out_fix, stream=sptr)
         torch.cuda.synchronize()
         graph_launches = dfl.df_kernel_launches() - cap0
@@ -1278,6 +1323,8 @@ def main():
             for f in range(F):
                 k.frame_update(mus_h[f], vs_h[f], stream=sptr)
                 k.optimise(prm, stream=sptr)
+                if ls_fit:
+                    k.scale_fit_ls(stream=sptr)
                 k.fetch_depth(out_h[f], stream=sptr)
 
         step_host()
