@@ -970,17 +970,28 @@ def run_keyframes(args, ws, rank, dev, torch, dfl, replicas, synth):
     clocks = clk.summary()
     total_ms = replicas.max_over_ranks(sum(step_ms), device=dev)
     px = sum(W * H for W, H in shapes)
-    units = px * n_gn * n_pcg
+    # the PCG iterations a step executes, from the solve reports of one more
+    # (untimed) step from the same state: all n_gn x n_pcg of them unless a
+    # depth step stops early (the diagonal system of --variant table3 is
+    # solved exactly by its first iteration)
+    with torch.cuda.stream(stream):
+        load_frame()
+        reps = dfl.df_optimise_batch(handles, prm, stream=sptr, report=True)
+    torch.cuda.synchronize()
+    iters = [int(r.iters_done) for r in reps]
+    units = sum(W * H * it for (W, H), it in zip(shapes, iters))
     value = units * args.steps * ws / (total_ms / 1e3) / 1e6
     gn_bytes = ALG_BYTES_PER_GN_PX if code == dfl.DF_F32 else ALG_BYTES_PER_GN_PX - 12
-    alg = px * (n_gn * n_pcg * ALG_BYTES_PER_PCG_PX + n_gn * gn_bytes)
+    alg = units * ALG_BYTES_PER_PCG_PX + px * n_gn * gn_bytes
     peak, peak_kind = peaks()
     solve_s = statistics.mean(solve_ms) / 1e3
     achieved = alg / solve_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": ncu_traffic(traffic_key(args, name)),
                 "peak_kind": peak_kind, "region": "df_optimise_batch (all keyframes, one frame)",
-                "alg_bytes_per_launch": alg}
+                "alg_bytes_per_launch": alg,
+                "pcg_iterations": {"nominal_per_keyframe": n_gn * n_pcg,
+                                   "executed_mean": float(np.mean(iters))}}
     e2e = None
     if not args.no_e2e:
         cnn_h = [[torch.from_numpy(p).to(tdt).pin_memory() for p in kf.cnn_planes] for kf in kfs]
@@ -1294,12 +1305,23 @@ def main():
     launches = dfl.df_kernel_launches() - launches0 + graph_launches * F * args.steps
     clocks = clk.summary()
     total_ms = replicas.max_over_ranks(sum(step_ms), device=dev)
-    units_per_step = W * H * args.n_gn * args.n_pcg * F
+    # the PCG iterations a step executes (solve reports of one more, untimed
+    # step): n_gn x n_pcg per frame unless a depth step stops early
+    iters = []
+    with torch.cuda.stream(stream):
+        k.reset(*cnn_d, stream=sptr)
+        for f in range(F):
+            k.frame_update(mus_d[f], vs_d[f], stream=sptr)
+            iters.append(int(k.optimise(prm, stream=sptr, report=True).iters_done))
+            if ls_fit:
+                k.scale_fit_ls(stream=sptr)
+    torch.cuda.synchronize()
+    units_per_step = W * H * sum(iters)
     value = units_per_step * args.steps * ws / (total_ms / 1e3) / 1e6
 
     # dominant region: the solve of one frame (all its kernels)
     solve_avg_s = statistics.mean(solve_ms) / 1e3
-    alg_bytes = W * H * (args.n_gn * args.n_pcg * ALG_BYTES_PER_PCG_PX +
+    alg_bytes = W * H * (float(np.mean(iters)) * ALG_BYTES_PER_PCG_PX +
                          args.n_gn * ALG_BYTES_PER_GN_PX)
     peak, peak_kind = peaks()
     achieved = alg_bytes / solve_avg_s / 1e9
@@ -1307,7 +1329,9 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": ncu_traffic(kernel_key),
                 "peak_kind": peak_kind, "region": "df_optimise (one frame's solve)",
-                "alg_bytes_per_launch": alg_bytes}
+                "alg_bytes_per_launch": alg_bytes,
+                "pcg_iterations": {"nominal_per_frame": args.n_gn * args.n_pcg,
+                                   "executed_mean": float(np.mean(iters))}}
     lat = np.percentile(np.array(solve_ms), [50, 99])
 
     # end to end through the public API with host (pinned) buffers
