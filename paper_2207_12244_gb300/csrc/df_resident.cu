@@ -327,7 +327,7 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     const float wyu = v > 0 ? m.WY[q - W] : m.WYT[u], eyu = v > 0 ? m.S[q - W] : m.HA[1][u];
     const float d = ws + wn + wx + wxl + wy + wyu;
     const float r = rs + wn * (mn - xq) + wx * ex - wxl * exl + wy * ey - wyu * eyu;
-    const float id = d > 0.0f ? __fdividef(1.0f, d) : 0.0f;
+    const float id = inv_diag(d);
     m.ID[q] = id;
     m.R[q] = r;
     acc[0] += r * (r * id);
