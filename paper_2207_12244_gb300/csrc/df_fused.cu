@@ -1268,15 +1268,25 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble_pieces(const PlanHeade
   }
 }
 
-// Quantity q of a keyframe's n piece sums, added by one warp: each lane adds
-// its entries in piece order, then a fixed warp tree (valid in lane 0).
-__device__ __forceinline__ ff2 warp_piece_sum(const double *partial, int n, int q) {
+// Quantity q of a keyframe's n piece sums, this warp's share of a CTA-wide
+// sum: thread tid adds entries tid, tid + kThreads, ... in order, eight loads
+// in flight at a time, then a fixed warp tree (valid in lane 0); the caller
+// adds the warps' results in warp order. Every CTA forms the same value. (One
+// warp alone walked the 5400 pieces of a 1920 x 1440 keyframe in ~40
+// dependent L2 round trips, ~28 us at the start of every depth-step launch.)
+__device__ __forceinline__ ff2 cta_piece_part(const double *partial, int n, int q) {
   const float2 *p = reinterpret_cast<const float2 *>(partial);
+  constexpr int kU = 8;
   ff2 acc = ff2{0.0f, 0.0f};
-#pragma unroll 4
-  for (int j = threadIdx.x & 31; j < n; j += 32) {
-    const float2 v = __ldcg(p + (size_t)j * kQ + q);
-    acc = ff_add(acc, ff2{v.x, v.y});
+  for (int base = threadIdx.x; base < n; base += kThreads * kU) {
+    float2 v[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      const int e = base + j * kThreads;
+      v[j] = e < n ? __ldcg(p + (size_t)e * kQ + q) : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int j = 0; j < kU; ++j) acc = ff_add(acc, ff2{v[j].x, v[j].y});
   }
   return warp_sum_ff(acc);
 }
@@ -1570,12 +1580,19 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       // the assembly ran as its own kernel: this iteration's r.z (and r.r,
       // b.b) from its pieces' sums, in piece order
       const int nqa = wide ? 3 : 1;
-      for (int pq = warp; pq < nseg * nqa; pq += kWarps) {
+      for (int pq = 0; pq < nseg * nqa; ++pq) {
         const int sg = pq / nqa, q = pq - sg * nqa;
         const FusedKf &K = s_kf[sg];
-        const ff2 tot =
-            warp_piece_sum(K.pl.partial, asm_pieces_of(K.pl.W, K.pl.H, K.asm_rows), q);
-        if (lane == 0) s_tot[sg][q] = tot;
+        const ff2 part =
+            cta_piece_part(K.pl.partial, asm_pieces_of(K.pl.W, K.pl.H, K.asm_rows), q);
+        if (lane == 0) s_acc[warp][sg][q] = part;
+      }
+      __syncthreads();
+      if (tid < nseg * nqa) {
+        const int sg = tid / nqa, q = tid - sg * nqa;
+        ff2 tot = s_acc[0][sg][q];
+        for (int w = 1; w < kWarps; ++w) tot = ff_add(tot, s_acc[w][sg][q]);
+        s_tot[sg][q] = tot;
       }
       __syncthreads();
     } else {
