@@ -1081,11 +1081,12 @@ __device__ __forceinline__ bool tma_assemble_tile(RowRing &ring, const FusedKf &
 // depth step). The persistent kernel runs every pass with one CTA of 8 warps
 // per SM, which leaves the assembly (the pass with the most arithmetic per
 // byte) bound by instruction latency; here one warp takes one piece (one
-// 128-column strip over asm_rows rows) and each SM holds several blocks of
-// 8 warps, so the loads and the arithmetic of many pieces overlap. Each
-// piece's sums (r.z; r.r and b.b when WIDE) go to its keyframe's partial-sum
-// array as double-float pairs, one entry per piece; the depth step adds them
-// in piece order, so every CTA forms the same scalars.
+// 128-column strip over asm_rows rows), each warp holds the next row's loads
+// in registers while it works on the current row (up to 170 registers:
+// three blocks of 4 warps per SM), so the loads and the arithmetic overlap.
+// Each piece's sums (r.z; r.r and b.b when WIDE) go to its keyframe's
+// partial-sum array as double-float pairs, one entry per piece; the depth
+// step adds them in a fixed order, so every CTA forms the same scalars.
 constexpr int kAsmThreads = 128;
 constexpr int kAsmWarps = kAsmThreads / 32;
 constexpr int kAsmMaxPieces = kMaxPartialBlocks * kNumQ / kQ;  // float2 entries per keyframe / kQ
@@ -1095,10 +1096,10 @@ __host__ __device__ __forceinline__ int asm_pieces_of(int W, int H, int rows) {
 }
 
 // One piece of the separate assembly: the arithmetic of assemble_tile (same
-// operations in the same order, so the same bits), with every load of a row
-// issued before any of the row's arithmetic (the plane loads do not wait
-// for the term flags or for each other), and the inputs read through the
-// read-only path (nothing here writes them).
+// operations in the same order, so the same bits), with every load of the
+// next row issued before any of this row's arithmetic (the plane loads do
+// not wait for the term flags or for each other), and the inputs read
+// through the read-only path (nothing here writes them).
 template <int DT, int LK, bool WIDE>
 __device__ __forceinline__ void assemble_piece(const Planes &k, const Geo &g, float t,
                                                const SolveCfg &c, float acc[kQ]) {
@@ -1124,22 +1125,43 @@ __device__ __forceinline__ void assemble_piece(const Planes &k, const Geo &g, fl
     }
   }
   const bool has_w = g.col > 0 && g.col < W, has_e = g.col + 4 < W;
+  // A row's inputs: x of the row below, the network planes, the semi-dense
+  // pair, and the single values past the strip's edges. The next row's are
+  // loaded before this row's arithmetic, so each warp keeps two rows of
+  // loads in flight.
+  struct RowIn {
+    F<4> x_dn, gx, vx, gy, vy, ms, vs, mn, vn;
+    float xe_l, xw_l, gw_l, vw_l;
+  };
+  auto load_row = [&](size_t ir, int vr, RowIn &R) {
+    R.x_dn = ldr<4>(k.x + (vr + 1 < H ? ir + P : ir));
+    R.gx = ldc<4, DT>(k.cnn[2], ir);
+    R.vx = ldc<4, DT>(k.cnn[3], ir);
+    R.gy = ldc<4, DT>(k.cnn[4], ir);
+    R.vy = ldc<4, DT>(k.cnn[5], ir);
+    R.ms = ldr<4>(k.mu_s + ir);
+    R.vs = ldr<4>(k.var_s + ir);
+    R.mn = ldc<4, DT>(k.cnn[0], ir);
+    R.vn = ldc<4, DT>(k.cnn[1], ir);
+    R.xe_l = R.xw_l = R.gw_l = 0.0f;
+    R.vw_l = 1.0f;
+    if (lane == 31 && has_e) R.xe_l = __ldg(k.x + ir + 4);
+    if (lane == 0 && has_w) {
+      R.xw_l = __ldg(k.x + ir - 1);
+      R.gw_l = ld_cnn<DT>(k.cnn[2], ir - 1);
+      R.vw_l = ld_cnn<DT>(k.cnn[3], ir - 1);
+    }
+  };
+  RowIn cur;
+  load_row(i, g.r0, cur);
   for (int j = 0; j < g.nrows; ++j, i += P) {
     const int v = g.r0 + j;
     const bool has_dn = v + 1 < H;
-    // every load of the row first
-    const F<4> x_dn = ldr<4>(k.x + (has_dn ? i + P : i));
-    const F<4> gxr = ldc<4, DT>(k.cnn[2], i), vxr = ldc<4, DT>(k.cnn[3], i);
-    const F<4> gyr = ldc<4, DT>(k.cnn[4], i), vyr = ldc<4, DT>(k.cnn[5], i);
-    const F<4> ms = ldr<4>(k.mu_s + i), vs = ldr<4>(k.var_s + i);
-    const F<4> mn = ldc<4, DT>(k.cnn[0], i), vn = ldc<4, DT>(k.cnn[1], i);
-    float xe_l = 0.0f, xw_l = 0.0f, gw_l = 0.0f, vw_l = 1.0f;
-    if (lane == 31 && has_e) xe_l = __ldg(k.x + i + 4);
-    if (lane == 0 && has_w) {
-      xw_l = __ldg(k.x + i - 1);
-      gw_l = ld_cnn<DT>(k.cnn[2], i - 1);
-      vw_l = ld_cnn<DT>(k.cnn[3], i - 1);
-    }
+    RowIn nxt;
+    if (j + 1 < g.nrows) load_row(i + P, v + 1, nxt);
+    const F<4> &x_dn = cur.x_dn, &gxr = cur.gx, &vxr = cur.vx, &gyr = cur.gy, &vyr = cur.vy;
+    const F<4> &ms = cur.ms, &vs = cur.vs, &mn = cur.mn, &vn = cur.vn;
+    const float xe_l = cur.xe_l, xw_l = cur.xw_l, gw_l = cur.gw_l, vw_l = cur.vw_l;
     F<4> x_e;
 #pragma unroll
     for (int e = 0; e < 3; ++e) x_e.v[e] = x_cur.v[e + 1];
@@ -1231,11 +1253,12 @@ __device__ __forceinline__ void assemble_piece(const Planes &k, const Geo &g, fl
     ey_up = eyv;
     gy_up = gyv;
     x_cur = x_dn;
+    cur = nxt;
   }
 }
 
 template <int LK, bool WIDE>
-__global__ void __launch_bounds__(kAsmThreads) k_assemble_pieces(const PlanHeader *h, SolveCfg c) {
+__global__ void __launch_bounds__(kAsmThreads, 3) k_assemble_pieces(const PlanHeader *h, SolveCfg c) {
   const int piece = blockIdx.x * kAsmWarps + (threadIdx.x >> 5);
   if (piece >= h->asm_pieces) return;  // whole warps leave
   const FusedKf *kfs =

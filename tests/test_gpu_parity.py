@@ -644,3 +644,32 @@ def test_frame_captured_with_host_buffers():
         assert torch.equal(out, ref)
     finally:
         k.close()
+
+
+def test_subnormal_variances_weigh_as_the_smallest_normal(solver):
+    """The reciprocals of the IRLS weights flush subnormal operands: a
+    variance below the smallest normal float must act exactly as that float
+    does (the weight saturates at 1 / FLT_MIN), never as 0 or a NaN. One
+    semi-dense pixel and one network-prior pixel carry such a variance, with
+    a mean equal to the prior so the huge weight meets a zero residual."""
+    import copy
+
+    kf = synth.make_keyframe(96, 72, 11)
+    p = int(np.flatnonzero(kf.var_s.ravel() > 0)[3])
+    q = (kf.width * kf.height) // 2 + 5
+    tiny, fmin = np.float32(1e-40), np.finfo(np.float32).tiny
+    assert 0 < tiny < fmin
+
+    def variant(v):
+        k2 = copy.deepcopy(kf)
+        k2.mu_s.ravel()[p] = k2.mu_n.ravel()[p]
+        k2.var_s.ravel()[p] = v
+        k2.var_n.ravel()[q] = v
+        return k2
+
+    prm = params(n_gn=4, n_pcg=4, solver=solver)
+    x_sub, t_sub, rep_sub = solve(variant(tiny), prm)
+    x_min, t_min, rep_min = solve(variant(fmin), prm)
+    assert rep_sub.flags == rep_min.flags == 0
+    assert np.isfinite(x_sub).all() and np.isfinite(t_sub)
+    assert np.array_equal(x_sub, x_min) and t_sub == t_min
