@@ -35,7 +35,6 @@ constexpr int kHalo = 9;  // halo arrays of W floats kept in shared memory
 struct ResKf {
   Planes pl;
   int cta_begin, cta_end;  // CTAs of this keyframe
-  long long inbox0;        // first slot of its CTAs' inboxes (within a parity)
 };
 
 struct ResCta {
@@ -361,7 +360,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
   __shared__ ff2 s_red[32 * kRQ];
   __shared__ ff2 s_cs[kRQ];
   __shared__ ff2 s_tot[kRQ];  // this pass's totals
-  __shared__ unsigned int s_epoch;
+  __shared__ int s_ok;
+  __shared__ SumPrev s_prev;
   __shared__ ResKf s_kf;
   __shared__ ResSeg s_seg;
 
@@ -370,7 +370,6 @@ __global__ void __launch_bounds__(kRThreads, 1)
   const char *hb = reinterpret_cast<const char *>(h);
   const ResCta *ctas = reinterpret_cast<const ResCta *>(hb + h->off_cta_work);
   const ResKf *kfs = reinterpret_cast<const ResKf *>(hb + h->off_kf);
-  Slot *slots = reinterpret_cast<Slot *>(reinterpret_cast<char *>(h) + h->off_slots);
   const ResCta me = ctas[blockIdx.x];
   if (tid == 0) {
     s_kf = kfs[me.kf];
@@ -384,8 +383,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
     s_seg.stop = 0;
     s_seg.iters = first ? 0 : sc->iters;
     s_seg.active = (sc->flags & kFlagBadInput) ? 0 : 1;
-    s_epoch = 0u;
   }
+  for (int i = tid; i < 2 * kSumQ * kSumDigits; i += kRThreads) (&s_prev.v[0][0][0])[i] = 0ull;
   __syncthreads();
   const Planes &k = s_kf.pl;
   const int W = k.W, H = k.H;
@@ -447,48 +446,50 @@ __global__ void __launch_bounds__(kRThreads, 1)
     }
   };
 
-  // partial sums -> slot -> barrier -> prefetch next halo + this keyframe's totals
-  // Reductions: every CTA pushes its double-float partials into the inbox of each
-  // CTA of its keyframe (one slot per writer); after the barrier a CTA adds
-  // its own inbox in slot order. No two CTAs read the same lines, so the
-  // sums cost one uncontended L2 round trip and are identical everywhere.
+  // partial sums -> exact sum words -> prefetch next halo + this keyframe's totals.
+  // Reductions: every CTA of a keyframe adds its double-float partials into
+  // the keyframe's fixed-point sum words (a fence first, so its band edges
+  // are visible to whoever sees the arrival) and polls them until all of the
+  // keyframe's CTAs have arrived; the total is exact and identical
+  // everywhere. No grid barrier: a keyframe's CTAs wait only for each other.
   const int nk = s_kf.cta_end - s_kf.cta_begin;
-  const int lk = (int)blockIdx.x - s_kf.cta_begin;
+  SumGroup *groups = reinterpret_cast<SumGroup *>(reinterpret_cast<char *>(h) + h->off_slots);
+  SumGroup *grp = groups + me.kf;
+  const bool skip_me = (int)blockIdx.x == h->debug_skip_cta;  // test hook: never arrive
   // nq: std::integral_constant with the number of sums this pass needs
-  // (acc[0 .. NQ-1]); narrower slots store and load half as much.
-  auto end_pass = [&](auto nq, const float *acc, int next_halo, int next_cb) -> bool {
+  // (acc[0 .. NQ-1]). post() runs on thread 0 once the totals are in s_tot,
+  // while the other warps load the next pass's halo; its writes to s_seg are
+  // visible to every thread when end_pass returns.
+  auto end_pass = [&](auto nq, const float *acc, int next_halo, int next_cb,
+                      auto &&post) -> bool {
     constexpr int NQ = decltype(nq)::value;
-    const int np = inbox_slots(nk);
-    Slot *box = slots + (size_t)parity * h->slot_stride + s_kf.inbox0;
     {
       float an[NQ];
 #pragma unroll
       for (int q = 0; q < NQ; ++q) an[q] = acc[q];
       cta_partial_sum_split<NQ>(an, s_red, s_cs);
       __syncthreads();
-      if (warp == 0) {
-        float v[8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          v[2 * q] = q < NQ ? s_cs[q].hi : 0.0f;
-          v[2 * q + 1] = q < NQ ? s_cs[q].lo : 0.0f;
-        }
-        const float4 lo = make_float4(v[0], v[1], v[2], v[3]);
-        const float4 hi = make_float4(v[4], v[5], v[6], v[7]);
-        for (int j = lane; j < nk; j += 32) {
-          float4 *dst = reinterpret_cast<float4 *>(box + (size_t)j * np + lk);
-          __stcg(dst, lo);
-          if (NQ > 2) __stcg(dst + 1, hi);
-        }
-      }
     }
-    if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
-    // warp q adds quantity q of the inbox; the other warps load the halo
-    if (warp < NQ) {
-      const ff2 tot = warp_inbox_sum_q(box + (size_t)lk * np, nk, warp);
-      if (lane == 0) s_tot[warp] = tot;
+    long long digit = 0;
+    if (warp == 0) {
+      bool ok = false;
+      if (!skip_me) {
+        sum_push<NQ>(grp, parity, s_cs);
+        ok = sum_wait<NQ>(grp, parity, nk, &s_prev, h, limit_ns, &digit);
+      }
+      if (lane == 0) s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    // warp 0 forms the totals and the pass's scalars; the other warps load
+    // the halo
+    if (warp == 0) {
+      const ff2 tot = sum_total(digit);
+      if ((lane & 7) == 0 && (lane >> 3) < NQ) s_tot[lane >> 3] = tot;
+      __syncwarp();
+      if (lane == 0) post();
     } else {
-      prefetch_halo(next_halo, next_cb, 32 * NQ);
+      prefetch_halo(next_halo, next_cb, 32);
     }
     __syncthreads();
     parity ^= 1;
@@ -508,10 +509,9 @@ __global__ void __launch_bounds__(kRThreads, 1)
       }
     }
   };
+  // thread 0: the scale step's t from the sums s_tot[qw], s_tot[qwr]
   auto scale_update = [&](int qw, int qwr) {
-    if (tid == 0 && s_seg.active && s_tot[qw].hi > 0.0f)
-      s_seg.t = ff_to_double(ff_div(s_tot[qwr], s_tot[qw]));
-    __syncthreads();
+    if (s_seg.active && s_tot[qw].hi > 0.0f) s_seg.t = ff_to_double(ff_div(s_tot[qwr], s_tot[qw]));
   };
 
   // The border of the joint solve moves with the iteration's alpha, beta
@@ -537,8 +537,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
       if (!scale_pending) {
         float acc[kRQ] = {};
         if (active) scale_partials(acc, 0, (float)s_seg.t);
-        if (!(alive = end_pass(IC<2>{}, acc, HK_X, 0))) break;
-        scale_update(0, 1);
+        if (!(alive = end_pass(IC<2>{}, acc, HK_X, 0, [&] { scale_update(0, 1); }))) break;
       }
       scale_pending = false;
     }
@@ -562,13 +561,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
       // without CG iterations; the joint solve also S and r_t
       const int next_a = n_pcg > 0 ? HK_INIT : HK_X;
       const bool wide = c.tol > 0.0 || n_pcg == 0;
-      if constexpr (JOINT) {
-        alive = end_pass(IC<4>{}, acc, next_a, 0);
-      } else {
-        alive = wide ? end_pass(IC<3>{}, acc, next_a, 0) : end_pass(IC<1>{}, acc, next_a, 0);
-      }
-      if (!alive) break;
-      if (tid == 0) {
+      auto post = [&] {
         if constexpr (JOINT) {
           // border of the bordered system: S = sum ws, r_t, u_t = r_t / S
           const ff2 S = s_tot[2], rt = s_tot[3];
@@ -589,8 +582,14 @@ __global__ void __launch_bounds__(kRThreads, 1)
             s_seg.stop = (c.tol > 0.0 && sqrt(s_seg.rr) < c.tol * sqrt(s_seg.bb)) ? 1 : 0;
           }
         }
+      };
+      if constexpr (JOINT) {
+        alive = end_pass(IC<4>{}, acc, next_a, 0, post);
+      } else {
+        alive = wide ? end_pass(IC<3>{}, acc, next_a, 0, post)
+                     : end_pass(IC<1>{}, acc, next_a, 0, post);
       }
-      __syncthreads();
+      if (!alive) break;
     }
     if (n_pcg == 0) continue;  // no depth update in this GN iteration
     {  // INIT: w0 = A u0
@@ -615,14 +614,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
       }
       // sums needed: (w0, u0); the joint solve also (ws, u0)
       const int next_i = n_pcg > 1 ? HK_ITER : HK_NONE;
-      if constexpr (JOINT) {
-        const float a2[2] = {acc[1], acc[3]};
-        alive = end_pass(IC<2>{}, a2, next_i, 0);
-      } else {
-        alive = end_pass(IC<1>{}, acc + 1, next_i, 0);
-      }
-      if (!alive) break;
-      if (tid == 0 && !s_seg.stop) {
+      auto post = [&] {
+        if (s_seg.stop) return;
         ff2 dl = s_tot[0];
         if constexpr (JOINT) {  // w_t = S u_t - (ws, u); (w, u) gains w_t u_t
           s_seg.jwt = ff_sub(ff_mul(s_seg.jS, s_seg.jut), s_tot[1]);
@@ -635,8 +628,14 @@ __global__ void __launch_bounds__(kRThreads, 1)
           s_seg.beta = ff2{0.0f, 0.0f};
           if constexpr (JOINT) joint_border_step(true);
         }
+      };
+      if constexpr (JOINT) {
+        const float a2[2] = {acc[1], acc[3]};
+        alive = end_pass(IC<2>{}, a2, next_i, 0, post);
+      } else {
+        alive = end_pass(IC<1>{}, acc + 1, next_i, 0, post);
       }
-      __syncthreads();
+      if (!alive) break;
     }
     for (int it = 0; it < n_pcg && alive; ++it) {
       const int cb = it & 1, nb = cb ^ 1;
@@ -675,14 +674,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
         // sums needed: the next scale step's two; r.r for a tolerance and
         // for the report after the last Gauss-Newton iteration
         const bool need_rr = c.tol > 0.0 || gn + 1 == n_gn;
-        if (fs && need_rr)
-          alive = end_pass(IC<3>{}, acc, HK_X, 0);
-        else if (fs)
-          alive = end_pass(IC<2>{}, acc + 1, HK_X, 0);
-        else
-          alive = end_pass(IC<1>{}, acc, HK_X, 0);
-        if (!alive) break;
-        if (tid == 0) {
+        auto post = [&] {
           if constexpr (JOINT) {  // the depth step's change of t
             s_seg.t += ff_to_double(s_seg.jdt);
             s_seg.jdt = ff2{0.0f, 0.0f};
@@ -693,15 +685,21 @@ __global__ void __launch_bounds__(kRThreads, 1)
               s_seg.rr = ff_to_double(joint ? ff_add(s_tot[0], ff_mul(s_seg.jrt, s_seg.jrt))
                                             : s_tot[0]);
           }
-        }
-        __syncthreads();
-        if (fs) {
-          if (need_rr)
-            scale_update(1, 2);
-          else
-            scale_update(0, 1);
-          scale_pending = true;
-        }
+          if (fs) {
+            if (need_rr)
+              scale_update(1, 2);
+            else
+              scale_update(0, 1);
+          }
+        };
+        if (fs && need_rr)
+          alive = end_pass(IC<3>{}, acc, HK_X, 0, post);
+        else if (fs)
+          alive = end_pass(IC<2>{}, acc + 1, HK_X, 0, post);
+        else
+          alive = end_pass(IC<1>{}, acc, HK_X, 0, post);
+        if (!alive) break;
+        if (fs) scale_pending = true;
       } else {  // ITER
         if (run) {
           for (int u = tid; u < W; u += kRThreads) {
@@ -747,15 +745,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
         const int next_kind = (it + 1 < n_pcg - 1) ? HK_ITER : HK_NONE;
         // sums needed: (r, u), (w, u); (r, r) for a tolerance; the joint
         // solve also (ws, u)
-        if constexpr (JOINT) {
-          const float a3[3] = {acc[0], acc[1], acc[3]};
-          alive = end_pass(IC<3>{}, a3, next_kind, nb);
-        } else {
-          alive = c.tol > 0.0 ? end_pass(IC<3>{}, acc, next_kind, nb)
-                              : end_pass(IC<2>{}, acc, next_kind, nb);
-        }
-        if (!alive) break;
-        if (tid == 0 && run) {
+        auto post = [&] {
+          if (!run) return;
           s_seg.iters += 1;
           ff2 gn_ = s_tot[0], dl = s_tot[1];
           if constexpr (JOINT) {  // border terms of (r, u) and (w, u)
@@ -780,8 +771,15 @@ __global__ void __launch_bounds__(kRThreads, 1)
               if constexpr (JOINT) joint_border_step(false);
             }
           }
+        };
+        if constexpr (JOINT) {
+          const float a3[3] = {acc[0], acc[1], acc[3]};
+          alive = end_pass(IC<3>{}, a3, next_kind, nb, post);
+        } else {
+          alive = c.tol > 0.0 ? end_pass(IC<3>{}, acc, next_kind, nb, post)
+                              : end_pass(IC<2>{}, acc, next_kind, nb, post);
         }
-        __syncthreads();
+        if (!alive) break;
       }
     }
   }
@@ -802,7 +800,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
       sc->stop = s_seg.stop;
     }
   }
-  grid_exit(h, G);
+  grid_exit(h, G, reinterpret_cast<unsigned long long *>(groups),
+            (long long)h->nkf * (long long)(sizeof(SumGroup) / 8));
 }
 
 // The kernel instance of a variant and a loss kind.
@@ -852,27 +851,18 @@ const ResDev &rdev() {
 
 }  // namespace
 
-// Inbox slots per parity for keyframes with nk[k] CTAs: each of a
-// keyframe's CTAs has an inbox with one slot per CTA of that keyframe.
-static size_t inbox_total(const std::vector<int> &nk) {
-  size_t s = 0;
-  for (int n : nk) s += (size_t)n * inbox_slots(n);
-  return s;
-}
-
-static size_t resident_bytes(int nkf, int G, size_t inbox) {
+// Plan bytes: header, CTA table, keyframe table, then one exact-sum group
+// per keyframe.
+static size_t resident_bytes(int nkf, int G) {
   size_t off = align16(sizeof(PlanHeader));
   off += align16(sizeof(ResCta) * (size_t)G);
   off += align16(sizeof(ResKf) * (size_t)nkf);
   off = (off + 255) & ~(size_t)255;
-  off += sizeof(Slot) * 2 * inbox;
+  off += sizeof(SumGroup) * (size_t)nkf;
   return off;
 }
 
-// Upper bound (all G CTAs on one keyframe has the largest inboxes).
-size_t resident_plan_bytes(int nkf, int G) {
-  return resident_bytes(nkf, G, (size_t)G * inbox_slots(G));
-}
+size_t resident_plan_bytes(int nkf, int G) { return resident_bytes(nkf, G); }
 
 int resident_max_ctas() { return rdev().sms; }
 
@@ -894,7 +884,8 @@ static bool resident_build_plan_with(const Planes *const *kfs, int n, const Fuse
   const ResDev &d = rdev();
   if (n < 1 || d.sms <= 0 || d.smem_optin <= 0) return false;
   const long long arrays = in_smem ? 9 + kIn : 9, halo = in_smem ? kHalo + 2 : kHalo;
-  int G_cap = d.sms;
+  // the exact-sum words count up to 255 CTAs per keyframe
+  int G_cap = std::min(d.sms, 255);
   if (tune.max_ctas > 0) G_cap = std::min(G_cap, tune.max_ctas);
   const long long avail = (long long)d.smem_optin - d.static_smem - 1024;
   long long total_px = 0;
@@ -952,18 +943,10 @@ static bool resident_build_plan_with(const Planes *const *kfs, int n, const Fuse
     }
     rk[k].cta_end = cI;
   }
-  {
-    long long ib = 0;
-    for (int k = 0; k < n; ++k) {
-      rk[k].inbox0 = ib;
-      ib += (long long)nb[k] * inbox_slots(nb[k]);
-    }
-  }
   const int stride = (band_px_max + 3) & ~3;
   const long long smem = (arrays * stride + halo * Wmax) * 4;
   if (smem > avail) return false;
-  const size_t inbox = inbox_total(nb);
-  out.assign(resident_bytes(n, G, inbox), 0);
+  out.assign(resident_bytes(n, G), 0);
   char *base = out.data();
   PlanHeader *hd = reinterpret_cast<PlanHeader *>(base);
   size_t off = align16(sizeof(PlanHeader));
@@ -978,7 +961,7 @@ static bool resident_build_plan_with(const Planes *const *kfs, int n, const Fuse
   hd->nkf = n;
   hd->G = G;
   hd->nslots = G;
-  hd->slot_stride = (long long)inbox;
+  hd->slot_stride = 0;
   hd->th = stride;  // shared-memory stride of one band array
   hd->smem_bytes = (int)smem;
   hd->in_smem = in_smem ? 1 : 0;

@@ -3,6 +3,7 @@
 // time limit, and the exit protocol that leaves the barrier words clean.
 #pragma once
 
+#include "df_exact.cuh"
 #include "df_internal.cuh"
 
 namespace df {
@@ -91,10 +92,6 @@ __device__ __forceinline__ bool grid_sync(PlanHeader *h, int G, unsigned long lo
 // totals stay double-float for the CG scalars and become doubles only where
 // an FP64 value is stored or reported. All operations are FP32 adds, so the
 // reduction is deterministic and as cheap as an FP32 one.
-struct ff2 {
-  float hi, lo;
-};
-
 __device__ __forceinline__ ff2 ff_add(ff2 a, ff2 b) {
   const float s = a.hi + b.hi;
   const float bb = s - a.hi;
@@ -223,14 +220,151 @@ __device__ __forceinline__ ff2 warp_inbox_sum_q(const Slot *box, int n, int q) {
   return warp_sum_ff(acc);
 }
 
+// ---- exact sums over the CTAs of a keyframe, without a grid barrier ---------
+//
+// Each CTA's double-float partial of a quantity is added, exactly, into a
+// fixed-point integer whose unit is 2^-149 (the smallest float step), kept as
+// eight 36-bit digits. Every finite float is m 2^(b - 149) with m < 2^24 and
+// 0 <= b <= 253, so it lands in at most two neighbouring digits; integer
+// addition is associative, so the total does not depend on the order in
+// which the CTAs arrive and every reader gets the same bits. The total of up
+// to 255 partials (each below 2^129) fits the 288 bits.
+//
+// Each digit lives in a 64-bit word that also counts its own arrivals: a
+// CTA adds (digit + 2^37) + 2^48 with one red.add per word, so bits 0..47
+// hold the biased digit sum and bits 48..63 the number of CTAs added so far.
+// A reader polls the words of a quantity until every word shows all n
+// arrivals; it needs no barrier word, and no word waits for another. The
+// words are never cleared during a launch: each CTA remembers the value at
+// which a word last completed and works with the difference (modulo 2^64).
+// Two sets alternate between consecutive reductions; a CTA can reach the
+// reduction after next on a set only after every CTA has contributed to the
+// next one, that is, after every CTA has read this one. Before its adds a
+// CTA fences, so everything it wrote in the pass (the band or tile edges its
+// neighbours read next) is visible to whoever sees its arrival.
+// One quantity of one set: the eight digit words in one 128-byte line (a
+// warp's adds and loads of a quantity are one request each; spreading the
+// words over eight lines measured slower).
+struct alignas(128) SumLine {
+  unsigned long long w[16];
+};
+// The reduction words of one keyframe: [set][quantity].
+struct SumGroup {
+  SumLine line[2][kSumQ];
+};
+__device__ __forceinline__ unsigned long long *sum_word(SumGroup *g, int set, int q, int k) {
+  return &g->line[set][q].w[k];
+}
+// What a CTA remembers of a group's words (shared memory).
+struct SumPrev {
+  unsigned long long v[2][kSumQ][kSumDigits];
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Release / acquire fence at GPU scope (lighter than the sequentially
+// consistent __threadfence): before relaxed adds it makes them a release,
+// after relaxed loads an acquire.
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// Warp-collective (one whole warp): fence, then add the NQ totals tot[] of
+// this CTA into set 'set' of group g (lane q * 8 + k adds digit k of
+// quantity q).
+template <int NQ>
+__device__ __forceinline__ void sum_push(SumGroup *g, int set, const ff2 *tot) {
+  const int lane = threadIdx.x & 31;
+  fence_acq_rel_gpu();
+  if (lane < 8 * NQ) {
+    const int q = lane >> 3, k = lane & 7;
+    const long long d = ff_digit(tot[q], k);
+    red_add_u64(sum_word(g, set, q, k), (unsigned long long)(d + (long long)kDigitBias) + kArrival);
+  }
+}
+
+// Warp-collective: wait until all n CTAs have added their NQ quantities to
+// set 'set' of g (every lane q * 8 + k < 8 NQ polls its own word with an
+// acquire load: two requests per quantity line and spin). Returns false if
+// the wait ran past limit_ns or another CTA raised the abort word (and then
+// raises it too). On success each lane q * 8 + k < 8 NQ holds digit k of
+// quantity q in *digit, prev is updated, and the warp has acquired what the
+// other CTAs wrote before their adds.
+template <int NQ>
+__device__ __forceinline__ bool sum_wait(SumGroup *g, int set, int n, SumPrev *prev,
+                                         PlanHeader *h, unsigned long long limit_ns,
+                                         long long *digit) {
+  const int lane = threadIdx.x & 31;
+  const bool act = lane < 8 * NQ;
+  const int q = lane >> 3, k = lane & 7;
+  const unsigned long long *wp = act ? sum_word(g, set, q, k) : nullptr;
+  const unsigned long long pv = act ? prev->v[set][q][k] : 0ull;
+  unsigned long long v = 0ull;
+  const unsigned long long t0 = global_ns();
+  unsigned int spins = 0;
+  bool ok = true;
+  for (;;) {
+    bool done = true;
+    if (act) {
+      v = ld_acquire_u64(wp);
+      done = ((v - pv) >> 48) == (unsigned long long)n;
+    }
+    if (__all_sync(0xffffffffu, done)) break;
+    if (((++spins) & 63u) == 0u) {
+      int bad = 0;
+      if (lane == 0) bad = (ld_acquire(&h->abort) != 0u || global_ns() - t0 > limit_ns) ? 1 : 0;
+      if (__shfl_sync(0xffffffffu, bad, 0)) {
+        ok = false;
+        break;
+      }
+    }
+  }
+  if (!ok) {
+    if (lane == 0) atomicExch(&h->abort, 1u);
+    return false;
+  }
+  if (act) {
+    prev->v[set][q][k] = v;
+    *digit = (long long)((v - pv) & (kArrival - 1ull)) - (long long)n * (long long)kDigitBias;
+  }
+  return true;
+}
+
+// Warp-collective after sum_wait: lane 8 q returns the total of quantity q.
+__device__ __forceinline__ ff2 sum_total(long long digit) {
+  const int lane = threadIdx.x & 31;
+  long long raw[kSumDigits];
+#pragma unroll
+  for (int j = 0; j < kSumDigits; ++j) raw[j] = __shfl_sync(0xffffffffu, digit, (lane & ~7) + j);
+  return digits_to_ff(raw);
+}
+
 // Called once by every CTA as its last action: the last CTA out resets the
-// barrier words (also after an abort, since every CTA does exit).
-__device__ __forceinline__ void grid_exit(PlanHeader *h, int G) {
+// barrier words (also after an abort, since every CTA does exit), and clears
+// n_sum words of exact-sum groups at 'sums' (nullptr: none).
+__device__ __forceinline__ void grid_exit(PlanHeader *h, int G, unsigned long long *sums = nullptr,
+                                          long long n_sum = 0) {
+  __shared__ int s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int done = atomicAdd(&h->exit_count, 1u) + 1u;
-    if (done == (unsigned int)G) {
+    s_last = done == (unsigned int)G ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (long long i = threadIdx.x; i < n_sum; i += blockDim.x) sums[i] = 0ull;
+    __syncthreads();
+    if (threadIdx.x == 0) {
       h->bar_count = 0u;
       h->abort = 0u;
       h->exit_count = 0u;
