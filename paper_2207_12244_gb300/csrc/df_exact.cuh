@@ -6,10 +6,11 @@
 // A finite float is m 2^(b - 149) with an integer m < 2^24 and 0 <= b <= 253
 // (subnormals: b = 0). As an integer in units of 2^-149 it has at most 277
 // bits; written in eight 36-bit digits, a float touches at most two
-// neighbouring digits. Digit sums of up to 255 CTAs' double-float partials
-// (each partial two floats) stay below 2^47 in magnitude, and their value
-// below 2^137, so integer additions of the digits are exact and the order in
-// which they happen does not change the total.
+// neighbouring digits. A CTA's double-float partial (two floats) adds less
+// than 2^37 to each digit, so the digit sums of up to 1023 CTAs stay below
+// 2^47 in magnitude: integer additions of the digits are exact and the order
+// in which they happen does not change the total. The value of such a sum is
+// below 2^139; totals beyond the float range come out as infinities.
 #pragma once
 
 #include <stdint.h>
@@ -76,12 +77,15 @@ DF_HD long long float_digit(float f, int k) {
 }
 
 // Digit k of what one CTA adds for its double-float partial t: the digits of
-// both floats; a non-finite partial adds 2^36 to digit 7 instead, more than
-// finite partials of 255 CTAs can add there (below 2^34).
+// both floats. A finite partial adds less than 2^26 to digit 7 (its floats
+// are below 2^129); a non-finite one adds 2^37 - 2^26 there instead, so the
+// digit-7 sum of up to 1023 CTAs is below 2^36 exactly when every partial
+// was finite.
+constexpr long long kNonFiniteMark = (1LL << 37) - (1LL << 26);
 DF_HD long long ff_digit(ff2 t, int k) {
   const bool finite = ((df_float_bits(t.hi) >> 23) & 0xffu) != 0xffu &&
                       ((df_float_bits(t.lo) >> 23) & 0xffu) != 0xffu;
-  if (!finite) return k == 7 ? (1LL << 36) : 0;
+  if (!finite) return k == 7 ? kNonFiniteMark : 0;
   return float_digit(t.hi, k) + float_digit(t.lo, k);
 }
 
@@ -96,10 +100,10 @@ DF_HD float scale_pow2(float x, int p) {
 }
 
 // The fixed-point total (raw digit sums dg[0..7], each |dg| < 2^47) as a
-// double-float, truncated after 48 significant bits. A digit-7 sum of 2^35
+// double-float, truncated after 48 significant bits. A digit-7 sum of 2^36
 // or more marks a non-finite partial: the total is then NaN.
 DF_HD ff2 digits_to_ff(const long long (&raw)[kSumDigits]) {
-  if (raw[7] >= (1LL << 35)) return ff2{df_bits_float(0x7fc00000), df_bits_float(0x7fc00000)};
+  if (raw[7] >= (1LL << 36)) return ff2{df_bits_float(0x7fc00000), df_bits_float(0x7fc00000)};
   long long dg[kSumDigits];
   long long c = 0;
 #pragma unroll
@@ -108,7 +112,10 @@ DF_HD ff2 digits_to_ff(const long long (&raw)[kSumDigits]) {
     dg[k] = t & kDigitMask;
     c = t >> 36;  // arithmetic: floor
   }
-  // value = c 2^288 + sum dg[k] 2^(36 k), with c = 0 or -1
+  // value = c 2^288 + sum dg[k] 2^(36 k); c = 0 or -1 unless the value is
+  // beyond 2^139 (float overflow either way)
+  if (c > 0) return ff2{df_bits_float(0x7f800000), 0.0f};
+  if (c < -1) return ff2{df_bits_float(0xff800000), 0.0f};
   const bool neg = c < 0;
   if (neg) {  // two's complement: -N = sum (mask - dg[k]) 2^(36 k) + 1
     long long cc = 1;

@@ -74,7 +74,8 @@ struct FusedKf {
   int slot_end;
   int writer_cta;  // the CTA that writes the final scalars back
   int asm_p0;      // separate assembly kernel: the keyframe's first piece
-  long long inbox0;  // first slot of its readers' inboxes (within a parity)
+  int group;       // its exact-sum words: the plan's group 'group'
+  int pad;
 };
 
 
@@ -1344,23 +1345,22 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
   __shared__ Seg s_seg[kMaxSeg];
   __shared__ ff2 s_acc[kWarps][kMaxSeg][kQ];
   __shared__ Slot s_push[kMaxSeg];
+  __shared__ SumPrev s_sumprev[kMaxSeg];
+  __shared__ int s_okseg[kMaxSeg];
   __shared__ ff2 s_tot[kMaxSeg][kQ];  // this pass's totals
   __shared__ int s_nseg;
-  __shared__ unsigned int s_epoch;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = h->G, nkf = h->nkf;
   const char *hb = reinterpret_cast<const char *>(h);
   const int *warp_row = reinterpret_cast<const int *>(hb + h->off_cta_work);
   const int *cta_kf = reinterpret_cast<const int *>(hb + h->off_cta_kf);
-  const int *cta_slot = reinterpret_cast<const int *>(hb + h->off_cta_slot);
   const FusedKf *kfs = reinterpret_cast<const FusedKf *>(hb + h->off_kf);
-  Slot *slots = reinterpret_cast<Slot *>(reinterpret_cast<char *>(h) + h->off_slots);
+  SumGroup *groups = reinterpret_cast<SumGroup *>(reinterpret_cast<char *>(h) + h->off_slots);
   const int cta = blockIdx.x;
   const int re = warp_row[(cta + 1) * kWarps];  // end of the CTA's rows
   const int wb = warp_row[cta * kWarps + warp], we = warp_row[cta * kWarps + warp + 1];
   const int th_max = h->th;
-  const int slot0 = cta_slot[cta];
 
   if (tid == 0) {
     int n = 0;
@@ -1379,8 +1379,11 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
       ++n;
     }
     s_nseg = n;
-    s_epoch = 0u;
   }
+  // every launch starts from cleared exact-sum words (the plan upload, or
+  // the last CTA out of the previous launch, leaves them zero)
+  for (int i = tid; i < kMaxSeg * 2 * kSumQ * kSumDigits; i += kThreads)
+    (&s_sumprev[0].v[0][0][0])[i] = 0ull;
   RowRing ring;
   if constexpr (VEC == 4) {
     ring.smem = dyn_ring + warp * kWarpStageBytes;
@@ -1529,38 +1532,38 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     }
     ring = rg;
     __syncthreads();
-    // Push the CTA's sum for each keyframe into the inbox of every CTA of
-    // that keyframe (one slot per writer), then read only the own inbox
-    // after the barrier: no cache line is read by more than one CTA.
-    Slot *pbox = slots + (size_t)parity * h->slot_stride;
-    if (nq > 0 && tid < nseg * 4) {
+    // Each keyframe segment's CTA sum, in warp order, then warp sg adds it to
+    // keyframe sg's exact-sum words and waits until every CTA of that
+    // keyframe has (no grid barrier: a CTA waits only for the CTAs that share
+    // its keyframes). A pass without sums still exchanges one zero, which
+    // orders its writes before the next pass's reads by the keyframe's CTAs.
+    if (tid < nseg * 4) {
       const int sg = tid >> 2, q = tid & 3;
       ff2 s = ff2{0.0f, 0.0f};
-      if (q < kQ)
+      if (q < kQ && q < nq)
         for (int w = 0; w < kWarps; ++w) s = ff_add(s, s_acc[w][sg][q]);
       s_push[sg].v[q] = s;
     }
     __syncthreads();
-    for (int sg = 0; sg < nseg && nq > 0; ++sg) {
-      const FusedKf &K = s_kf[sg];
-      const int nk = K.slot_end - K.slot_begin, l = slot0 + sg - K.slot_begin;
-      const int np = inbox_slots(nk);
-      Slot *box = pbox + K.inbox0;
-      const float4 *src = reinterpret_cast<const float4 *>(&s_push[sg]);
-      for (int j = tid; j < nk; j += kThreads) {
-        float4 *dst = reinterpret_cast<float4 *>(box + (size_t)j * np + l);
-        __stcg(dst, src[0]);
-        if (nq > 2) __stcg(dst + 1, src[1]);
+    long long digit = 0;
+    if (warp < nseg) {
+      const FusedKf &K = s_kf[warp];
+      SumGroup *grp = groups + K.group;
+      const int nk = K.slot_end - K.slot_begin;
+      bool ok = false;
+      if (cta != h->debug_skip_cta) {  // test hook: never arrive
+        const int nx = nq > 0 ? nq : 1;
+        sum_push(grp, parity, s_push[warp].v, nx);
+        ok = sum_wait(grp, parity, nk, nx, &s_sumprev[warp], h, limit_ns, &digit);
       }
+      if (lane == 0) s_okseg[warp] = ok ? 1 : 0;
     }
-    if (!grid_sync(h, G, limit_ns, &s_epoch)) return false;
-    // one warp per (keyframe, sum): the trees run side by side
-    for (int pq = warp; pq < nseg * nq; pq += kWarps) {
-      const int sg = pq / nq, q = pq - sg * nq;
-      const FusedKf &K = s_kf[sg];
-      const int nk = K.slot_end - K.slot_begin, l = slot0 + sg - K.slot_begin;
-      const ff2 tot = warp_inbox_sum_q(pbox + K.inbox0 + (size_t)l * inbox_slots(nk), nk, q);
-      if (lane == 0) s_tot[sg][q] = tot;
+    __syncthreads();
+    for (int sg = 0; sg < nseg; ++sg)
+      if (!s_okseg[sg]) return false;
+    if (warp < nseg) {
+      const ff2 tot = sum_total(digit);
+      if ((lane & 7) == 0 && (lane >> 3) < nq) s_tot[warp][lane >> 3] = tot;
     }
     __syncthreads();
     parity ^= 1;
@@ -1748,7 +1751,8 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
     }
   }
   if constexpr (VEC == 4) ring.drain();
-  grid_exit(h, G);
+  grid_exit(h, G, reinterpret_cast<unsigned long long *>(groups),
+            (long long)nkf * (long long)(sizeof(SumGroup) / 8));
 }
 
 struct DevInfo {
@@ -1849,23 +1853,18 @@ int streaming_max_ctas() {
   return d.sms * std::max(1, std::max(d.occ[0], d.occ[1]));
 }
 
-static size_t streaming_bytes(int nkf, int G, size_t inbox) {
+static size_t streaming_bytes(int nkf, int G) {
   size_t off = align16(sizeof(PlanHeader));
   off += align16(sizeof(int) * ((size_t)G * kWarps + 1));
   off += align16(sizeof(int) * (size_t)G);
   off += align16(sizeof(int) * (size_t)G);
   off += align16(sizeof(FusedKf) * (size_t)nkf);
   off = (off + 255) & ~(size_t)255;
-  off += sizeof(Slot) * 2 * inbox;
+  off += sizeof(SumGroup) * (size_t)nkf;  // one exact-sum group per keyframe
   return off;
 }
 
-// Upper bound: per parity the inboxes hold, for every keyframe with m slots,
-// m inboxes of inbox_slots(m) slots; at most (G + nkf) * inbox_slots(G + nkf).
-size_t streaming_plan_bytes(int nkf, int G) {
-  const int m = G + nkf;
-  return streaming_bytes(nkf, G, (size_t)m * inbox_slots(m));
-}
+size_t streaming_plan_bytes(int nkf, int G) { return streaming_bytes(nkf, G); }
 
 bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
                           std::vector<char> &out, LaunchShape &shape) {
@@ -1965,9 +1964,9 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   for (int k = 0; k < n; ++k)
     if (sb[k] < 0) return false;
   const int nslots = ns;
-  size_t inbox = 0;
-  for (int k = 0; k < n; ++k) inbox += (size_t)(se[k] - sb[k]) * inbox_slots(se[k] - sb[k]);
-  out.assign(streaming_bytes(n, G, inbox), 0);
+  for (int k = 0; k < n; ++k)
+    if (se[k] - sb[k] > 1023) return false;  // CTAs an exact-sum group counts
+  out.assign(streaming_bytes(n, G), 0);
   char *base = out.data();
   PlanHeader *hd = reinterpret_cast<PlanHeader *>(base);
   size_t off = align16(sizeof(PlanHeader));
@@ -1988,14 +1987,13 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   hd->ntiles = (int)R;  // rows of the work list
   hd->th = th_max;
   hd->nslots = nslots;
-  hd->slot_stride = (long long)inbox;
+  hd->slot_stride = 0;
   hd->vec = vec;
   hd->bytes = (long long)out.size();
   memcpy(base + hd->off_cta_work, wr.data(), sizeof(int) * wr.size());
   memcpy(base + hd->off_cta_kf, ck.data(), sizeof(int) * G);
   memcpy(base + hd->off_cta_slot, cs.data(), sizeof(int) * G);
   FusedKf *fk = reinterpret_cast<FusedKf *>(base + hd->off_kf);
-  long long ib = 0;
   // Pieces of the separate assembly kernel (VEC = 4 plans): strips of
   // asm_rows rows, row block by row block, the strips of a block side by
   // side. Rows per piece: about kAsmTarget pieces over the whole plan (enough
@@ -2014,8 +2012,8 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   long long pieces = 0;
   bool split = vec == 4 && (tune.assembly == 2 || (tune.assembly == 0 && share >= 56));
   for (int k = 0; k < n; ++k) {
-    fk[k].inbox0 = ib;
-    ib += (long long)(se[k] - sb[k]) * inbox_slots(se[k] - sb[k]);
+    fk[k].group = k;
+    fk[k].pad = 0;
     fk[k].pl = *kfs[k];
     fk[k].row_begin = (int)rb[k];
     fk[k].rows = (int)(rb[k + 1] - rb[k]);

@@ -474,8 +474,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
     if (warp == 0) {
       bool ok = false;
       if (!skip_me) {
-        sum_push<NQ>(grp, parity, s_cs);
-        ok = sum_wait<NQ>(grp, parity, nk, &s_prev, h, limit_ns, &digit);
+        sum_push(grp, parity, s_cs, NQ);
+        ok = sum_wait(grp, parity, nk, NQ, &s_prev, h, limit_ns, &digit);
       }
       if (lane == 0) s_ok = ok ? 1 : 0;
     }
@@ -884,8 +884,8 @@ static bool resident_build_plan_with(const Planes *const *kfs, int n, const Fuse
   const ResDev &d = rdev();
   if (n < 1 || d.sms <= 0 || d.smem_optin <= 0) return false;
   const long long arrays = in_smem ? 9 + kIn : 9, halo = in_smem ? kHalo + 2 : kHalo;
-  // the exact-sum words count up to 255 CTAs per keyframe
-  int G_cap = std::min(d.sms, 255);
+  // the exact-sum words hold up to 1023 CTAs per keyframe
+  int G_cap = std::min(d.sms, 1023);
   if (tune.max_ctas > 0) G_cap = std::min(G_cap, tune.max_ctas);
   const long long avail = (long long)d.smem_optin - d.static_smem - 1024;
   long long total_px = 0;

@@ -227,8 +227,8 @@ __device__ __forceinline__ ff2 warp_inbox_sum_q(const Slot *box, int n, int q) {
 // eight 36-bit digits. Every finite float is m 2^(b - 149) with m < 2^24 and
 // 0 <= b <= 253, so it lands in at most two neighbouring digits; integer
 // addition is associative, so the total does not depend on the order in
-// which the CTAs arrive and every reader gets the same bits. The total of up
-// to 255 partials (each below 2^129) fits the 288 bits.
+// which the CTAs arrive and every reader gets the same bits (df_exact.cuh:
+// up to 1023 CTAs per keyframe).
 //
 // Each digit lives in a 64-bit word that also counts its own arrivals: a
 // CTA adds (digit + 2^37) + 2^48 with one red.add per word, so bits 0..47
@@ -277,33 +277,31 @@ __device__ __forceinline__ void fence_acq_rel_gpu() {
   asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
-// Warp-collective (one whole warp): fence, then add the NQ totals tot[] of
-// this CTA into set 'set' of group g (lane q * 8 + k adds digit k of
-// quantity q).
-template <int NQ>
-__device__ __forceinline__ void sum_push(SumGroup *g, int set, const ff2 *tot) {
+// Warp-collective (one whole warp): fence, then add the nq (1..4) totals
+// tot[] of this CTA into set 'set' of group g (lane q * 8 + k adds digit k
+// of quantity q).
+__device__ __forceinline__ void sum_push(SumGroup *g, int set, const ff2 *tot, int nq) {
   const int lane = threadIdx.x & 31;
   fence_acq_rel_gpu();
-  if (lane < 8 * NQ) {
+  if (lane < 8 * nq) {
     const int q = lane >> 3, k = lane & 7;
     const long long d = ff_digit(tot[q], k);
     red_add_u64(sum_word(g, set, q, k), (unsigned long long)(d + (long long)kDigitBias) + kArrival);
   }
 }
 
-// Warp-collective: wait until all n CTAs have added their NQ quantities to
-// set 'set' of g (every lane q * 8 + k < 8 NQ polls its own word with an
+// Warp-collective: wait until all n CTAs have added their nq quantities to
+// set 'set' of g (every lane q * 8 + k < 8 nq polls its own word with an
 // acquire load: two requests per quantity line and spin). Returns false if
 // the wait ran past limit_ns or another CTA raised the abort word (and then
-// raises it too). On success each lane q * 8 + k < 8 NQ holds digit k of
+// raises it too). On success each lane q * 8 + k < 8 nq holds digit k of
 // quantity q in *digit, prev is updated, and the warp has acquired what the
 // other CTAs wrote before their adds.
-template <int NQ>
-__device__ __forceinline__ bool sum_wait(SumGroup *g, int set, int n, SumPrev *prev,
+__device__ __forceinline__ bool sum_wait(SumGroup *g, int set, int n, int nq, SumPrev *prev,
                                          PlanHeader *h, unsigned long long limit_ns,
                                          long long *digit) {
   const int lane = threadIdx.x & 31;
-  const bool act = lane < 8 * NQ;
+  const bool act = lane < 8 * nq;
   const int q = lane >> 3, k = lane & 7;
   const unsigned long long *wp = act ? sum_word(g, set, q, k) : nullptr;
   const unsigned long long pv = act ? prev->v[set][q][k] : 0ull;

@@ -150,3 +150,23 @@ def test_non_finite_partial_makes_the_total_nan(lib):
     # a non-finite low part too, and with many large finite partials beside it
     p = [(np.float32(3.0e38), np.float32(0.0))] * 254 + [(np.float32(1.0), np.float32(np.nan))]
     assert np.isnan(total(lib, p)[0])
+    p = [(np.float32(-3.4e38), np.float32(0.0))] * 1022 + [(np.float32(np.inf), np.float32(0.0))]
+    assert np.isnan(total(lib, p)[0])
+
+
+def test_up_to_1023_partials(lib):
+    """Plans with two CTAs per SM give a keyframe up to 304 CTAs; the digits
+    hold 1023 partials exactly."""
+    rng = np.random.default_rng(5)
+    pairs = rand_pairs(rng, 1023, 100, 127)
+    hi, lo = total(lib, pairs)
+    s = exact(pairs)
+    if abs(s) < 2 ** 128:
+        got = Fraction(float(hi)) + Fraction(float(lo))
+        assert abs(s - got) <= abs(s) * Fraction(2) ** -47
+    else:
+        assert np.isinf(hi)
+    # 1023 partials at the float maximum: the total overflows to infinity
+    mx = [(np.float32(3.4028235e38), np.float32(2.0 ** 103))] * 1023
+    assert np.isinf(total(lib, mx)[0]) and total(lib, mx)[0] > 0
+    assert np.isinf(total(lib, [(-a, -b) for a, b in mx])[0])
