@@ -186,8 +186,8 @@ def _code_only(text: str) -> str:
 
 # The sources of the fused solvers, whose launches profiles/traffic.json
 # records: the kernels, their launch plans and the device headers they use.
-FUSED_SOURCES = ("df_fused.cu", "df_fused.cuh", "df_internal.cuh", "df_resident.cu",
-                 "df_sync.cuh", "df_tma.cuh")
+FUSED_SOURCES = ("df_exact.cuh", "df_fused.cu", "df_fused.cuh", "df_internal.cuh",
+                 "df_resident.cu", "df_sync.cuh", "df_tma.cuh")
 
 
 def lib_source_hash():
