@@ -97,16 +97,17 @@ __device__ __forceinline__ Smem smem_of(float *base, int stride, int W, bool in_
 // Per-thread walk over the band's pixels q = tid, tid + T, ... with the row
 // and column kept incrementally (no integer division per pixel).
 struct Walk {
-  int q, v, u, dv, du, W;
-  __device__ __forceinline__ Walk(int W_) : W(W_) {
-    q = threadIdx.x;
+  int q, v, u, dv, du, W, step;
+  __device__ __forceinline__ Walk(int W_, int t = threadIdx.x, int step_ = kRThreads)
+      : W(W_), step(step_) {
+    q = t;
     v = q / W;
     u = q - v * W;
-    dv = kRThreads / W;
-    du = kRThreads - dv * W;
+    dv = step / W;
+    du = step - dv * W;
   }
   __device__ __forceinline__ void next() {
-    q += kRThreads;
+    q += step;
     v += dv;
     u += du;
     if (u >= W) {
@@ -248,22 +249,20 @@ __device__ void stage_inputs(const Smem &m, const Planes &k, int rb, int bp, boo
   }
 }
 
-// JOINT: also keep ws in the U array and sum the border's S = sum ws and
-// r_t = sum ws (x - t - mu_s) into acc[2], acc[3] (b.b is not formed: the
-// joint solve runs with a fixed iteration count here). SM: the inputs are
-// staged in shared memory (DT is then unused).
-template <int DT, bool JOINT, int LK, bool SM>
-__device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, float t,
-                              const SolveCfg &c, float acc[kRQ]) {
+// The assembly in two parts. assemble_pre needs only the band's x and its
+// inputs: the x-terms, the y-terms inside the band and the prior term, so
+// it can run while the previous pass's sums are still being exchanged
+// (threads t, t + nt, ...). wx, wy, ex, ey go to WX, WY, P, S (p and s are
+// free during assembly), the prior's weight wn and residual part
+// wn (mu_n - x) to ID and R.
+template <int DT, int LK, bool SM>
+__device__ void assemble_pre(const Smem &m, const Planes &k, int rb, int nr, const SolveCfg &c,
+                             int t, int nt) {
   const int W = k.W, H = k.H, bp = nr * W;
   const size_t P = k.P;
-  const bool semi = c.terms & DF_TERM_SEMI, net = c.terms & DF_TERM_NET,
-             grad = c.terms & DF_TERM_GRAD;
-  const bool has_above = rb > 0;
+  const bool net = c.terms & DF_TERM_NET, grad = c.terms & DF_TERM_GRAD;
   auto in = [&](int j, int q, size_t gi) { return band_in<SM, DT>(m, k, j, q, gi); };
-  // x of the rows above / below the band is in HA[0] / HA[4] (prefetched)
-  // step A: the band's own x- and y-terms, and the y-term above the band
-  for (Walk it(W); it.q < bp; it.next()) {
+  for (Walk it(W, t, nt); it.q < bp; it.next()) {
     const int q = it.q, u = it.u, v = it.v;
     const size_t gi = (size_t)(rb + v) * P + u;
     const float xq = m.X[q];
@@ -272,17 +271,53 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
       ex = m.X[q + 1] - xq - in(I_GX, q, gi);
       wx = robust_weight_k<LK>(ex, in(I_VX, q, gi), c.delta);
     }
-    if (grad && rb + v < H - 1) {
-      const float xs = (v < nr - 1) ? m.X[q + W] : m.HA[4][u];
-      ey = xs - xq - in(I_GY, q, gi);
+    if (grad && v < nr - 1 && rb + v < H - 1) {  // the last row's y-term needs the halo
+      ey = m.X[q + W] - xq - in(I_GY, q, gi);
       wy = robust_weight_k<LK>(ey, in(I_VY, q, gi), c.delta);
+    }
+    float wn = 0.0f, rn = 0.0f;
+    if (net) {
+      const float mn = in(I_MN, q, gi);
+      wn = robust_weight_k<LK>(xq - mn, in(I_VN, q, gi), c.delta);
+      rn = wn * (mn - xq);
     }
     m.WX[q] = wx;
     m.WY[q] = wy;
-    m.P[q] = ex;  // p and s are free during assembly: hold ex, ey
+    m.P[q] = ex;
     m.S[q] = ey;
+    m.ID[q] = wn;
+    m.R[q] = rn;
   }
+}
+
+// The rest of the assembly, once t and the x halo (HA[0] above, HA[4]
+// below) are known: the last row's y-term, the y-term above the band, the
+// semi-dense term, then 1/diag and r0 = b - A x in residual form.
+// JOINT: also keep ws in the U array and sum the border's S = sum ws and
+// r_t = sum ws (x - t - mu_s) into acc[2], acc[3] (b.b is not formed: the
+// joint solve runs with a fixed iteration count here). SM: the inputs are
+// staged in shared memory (DT is then unused).
+template <int DT, bool JOINT, int LK, bool SM>
+__device__ void assemble_post(const Smem &m, const Planes &k, int rb, int nr, float t,
+                              const SolveCfg &c, float acc[kRQ]) {
+  const int W = k.W, H = k.H, bp = nr * W;
+  const size_t P = k.P;
+  const bool semi = c.terms & DF_TERM_SEMI, net = c.terms & DF_TERM_NET,
+             grad = c.terms & DF_TERM_GRAD;
+  const bool has_above = rb > 0;
+  auto in = [&](int j, int q, size_t gi) { return band_in<SM, DT>(m, k, j, q, gi); };
   for (int u = threadIdx.x; u < W; u += kRThreads) {
+    {  // the band's last row: its y-term reaches the row below
+      const int v = nr - 1, q = v * W + u;
+      const size_t gi = (size_t)(rb + v) * P + u;
+      float wy = 0.0f, ey = 0.0f;
+      if (grad && rb + v < H - 1) {
+        ey = m.HA[4][u] - m.X[q] - in(I_GY, q, gi);
+        wy = robust_weight_k<LK>(ey, in(I_VY, q, gi), c.delta);
+      }
+      m.WY[q] = wy;
+      m.S[q] = ey;
+    }
     float wy = 0.0f, ey = 0.0f, gy = 0.0f;
     if (grad && has_above) {
       const size_t gi = (size_t)(rb - 1) * P + u;
@@ -302,7 +337,6 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
     m.HA[2][u] = gy;
   }
   __syncthreads();
-  // step B: unary terms, diagonal, residual r0 = b - A x in residual form
   for (Walk it(W); it.q < bp; it.next()) {
     const int q = it.q, u = it.u, v = it.v;
     const size_t gi = (size_t)(rb + v) * P + u;
@@ -316,26 +350,20 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
         bs = ws * (t + ms);
       }
     }
-    float wn = 0.0f, mn = 0.0f;
-    if (net) {
-      mn = in(I_MN, q, gi);
-      wn = robust_weight_k<LK>(xq - mn, in(I_VN, q, gi), c.delta);
-    }
+    const float wn = m.ID[q], rn = m.R[q];
     const float wx = m.WX[q], ex = m.P[q], wy = m.WY[q], ey = m.S[q];
     const float wxl = u > 0 ? m.WX[q - 1] : 0.0f, exl = u > 0 ? m.P[q - 1] : 0.0f;
     const float wyu = v > 0 ? m.WY[q - W] : m.WYT[u], eyu = v > 0 ? m.S[q - W] : m.HA[1][u];
     const float d = ws + wn + wx + wxl + wy + wyu;
-    const float r = rs + wn * (mn - xq) + wx * ex - wxl * exl + wy * ey - wyu * eyu;
+    const float r = rs + rn + wx * ex - wxl * exl + wy * ey - wyu * eyu;
     const float id = inv_diag(d);
-    m.ID[q] = id;
-    m.R[q] = r;
     acc[0] += r * (r * id);
     acc[1] += r * r;
     if (JOINT) {
-      m.U[q] = ws;
       acc[2] += ws;
       acc[3] -= rs;  // ws (x - t - mu_s)
     } else if (c.tol > 0.0) {
+      const float mn = net ? in(I_MN, q, gi) : 0.0f;
       const float gx = (grad && u < W - 1) ? in(I_GX, q, gi) : 0.0f;
       const float gxl = (grad && u > 0) ? in(I_GX, q - 1, gi - 1) : 0.0f;
       const float gy = (grad && rb + v < H - 1) ? in(I_GY, q, gi) : 0.0f;
@@ -343,6 +371,9 @@ __device__ void assemble_band(const Smem &m, const Planes &k, int rb, int nr, fl
       const float b = bs + wn * mn - wx * gx + wxl * gxl - wy * gy + wyu * gyu;
       acc[2] += b * b;
     }
+    m.ID[q] = id;
+    m.R[q] = r;
+    if (JOINT) m.U[q] = ws;
   }
 }
 
@@ -460,6 +491,23 @@ __global__ void __launch_bounds__(kRThreads, 1)
   // (acc[0 .. NQ-1]). post() runs on thread 0 once the totals are in s_tot,
   // while the other warps load the next pass's halo; its writes to s_seg are
   // visible to every thread when end_pass returns.
+  // The part of the next assembly that needs neither t nor the x halo, on
+  // threads t, t + nt, ... (see assemble_pre).
+  auto pre_assemble = [&](int t, int nt) {
+    if (!active) return;
+    if (in_sm)
+      assemble_pre<DF_F32, LK, true>(m, k, rb, nr, c, t, nt);
+    else if (k.dtype == DF_BF16)
+      assemble_pre<DF_BF16, LK, false>(m, k, rb, nr, c, t, nt);
+    else if (k.dtype == DF_F16)
+      assemble_pre<DF_F16, LK, false>(m, k, rb, nr, c, t, nt);
+    else
+      assemble_pre<DF_F32, LK, false>(m, k, rb, nr, c, t, nt);
+  };
+  // overlap_pre: the pass that ends here is followed by an assembly, whose
+  // first part the warps other than warp 0 run while warp 0 exchanges the
+  // sums (the pass's own reads of the band arrays are done by then).
+  bool overlap_pre = false, pre_done = false;
   auto end_pass = [&](auto nq, const float *acc, int next_halo, int next_cb,
                       auto &&post) -> bool {
     constexpr int NQ = decltype(nq)::value;
@@ -478,7 +526,11 @@ __global__ void __launch_bounds__(kRThreads, 1)
         ok = sum_wait(grp, parity, nk, NQ, &s_prev, h, limit_ns, &digit);
       }
       if (lane == 0) s_ok = ok ? 1 : 0;
+    } else if (overlap_pre) {
+      pre_assemble(tid - 32, kRThreads - 32);
     }
+    pre_done = overlap_pre;
+    overlap_pre = false;
     __syncthreads();
     if (!s_ok) return false;
     // warp 0 forms the totals and the pass's scalars; the other warps load
@@ -537,6 +589,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
       if (!scale_pending) {
         float acc[kRQ] = {};
         if (active) scale_partials(acc, 0, (float)s_seg.t);
+        overlap_pre = true;
         if (!(alive = end_pass(IC<2>{}, acc, HK_X, 0, [&] { scale_update(0, 1); }))) break;
       }
       scale_pending = false;
@@ -545,14 +598,18 @@ __global__ void __launch_bounds__(kRThreads, 1)
       float acc[kRQ] = {};
       if (active) {
         const float t = (float)s_seg.t;
+        if (!pre_done) {  // no exchange before it to hide the first part in
+          pre_assemble(tid, kRThreads);
+          __syncthreads();
+        }
         if (in_sm)
-          assemble_band<DF_F32, JOINT, LK, true>(m, k, rb, nr, t, c, acc);
+          assemble_post<DF_F32, JOINT, LK, true>(m, k, rb, nr, t, c, acc);
         else if (k.dtype == DF_BF16)
-          assemble_band<DF_BF16, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
+          assemble_post<DF_BF16, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
         else if (k.dtype == DF_F16)
-          assemble_band<DF_F16, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
+          assemble_post<DF_F16, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
         else
-          assemble_band<DF_F32, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
+          assemble_post<DF_F32, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
         __syncthreads();
         publish_edges(m.R, Rg[0], W, nr, rb, P);
         publish_edges(m.ID, IDg, W, nr, rb, P);
@@ -674,6 +731,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
         // sums needed: the next scale step's two; r.r for a tolerance and
         // for the report after the last Gauss-Newton iteration
         const bool need_rr = c.tol > 0.0 || gn + 1 == n_gn;
+        overlap_pre = gn + 1 < n_gn;  // the next Gauss-Newton iteration's assembly
         auto post = [&] {
           if constexpr (JOINT) {  // the depth step's change of t
             s_seg.t += ff_to_double(s_seg.jdt);

@@ -1,6 +1,7 @@
-// Grid-wide synchronisation shared by the persistent solvers: launch-plan
-// header, a generation-counting grid barrier whose waits give up after a
-// time limit, and the exit protocol that leaves the barrier words clean.
+// Synchronisation shared by the persistent solvers: launch-plan header,
+// double-float arithmetic, the exact per-keyframe sums whose words also
+// order the passes (their waits give up after a time limit), and the exit
+// protocol that leaves the words clean for the next launch.
 #pragma once
 
 #include "df_exact.cuh"
@@ -18,7 +19,8 @@ struct PlanHeader {
   int th;  // streaming: longest piece a warp walks at once (0: no limit);
            // resident: shared-memory stride of a band array
   int debug_skip_cta;  // test hook: this CTA leaves without arriving (-1: none)
-  unsigned int bar_count, bar_gen, exit_count, abort;
+  unsigned int bar_count, bar_gen, exit_count, abort;  // bar_*: unused (zero)
+  // off_slots: the plan's exact-sum groups, one SumGroup per keyframe
   // off_cta_work: per-CTA work table (streaming: the G * 8 + 1 warp row
   // starts; resident: one band descriptor per CTA)
   long long off_cta_work, off_cta_kf, off_cta_slot, off_kf, off_slots;
@@ -26,7 +28,7 @@ struct PlanHeader {
   int smem_bytes;  // dynamic shared memory per CTA (resident plans)
   int in_smem;     // resident plans: 1 = each band's input planes are staged
                    // in shared memory for the whole launch
-  long long slot_stride;  // doubles per parity of the reduction slots / inboxes
+  long long slot_stride;  // unused (zero)
   int asm_pieces;  // streaming plans: pieces of the separate assembly kernel
   int asm_pad;
 };
@@ -41,45 +43,6 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-// Grid barrier over the G CTAs of one cooperative launch. The arrival
-// counter only grows during a launch: the n-th barrier of a CTA waits until
-// the counter reaches n * G, so the last arriver has nothing to release and
-// the waiters see it one L2 round trip after it lands. Every wait gives up
-// after limit_ns; a CTA that gives up (or sees that another one did) raises
-// the abort word and returns false, and the caller then skips all remaining
-// work. 'epoch' is the CTA's count of barriers passed (shared memory).
-__device__ __forceinline__ bool grid_sync(PlanHeader *h, int G, unsigned long long limit_ns,
-                                          unsigned int *epoch) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0 && (int)blockIdx.x == h->debug_skip_cta) {
-    s_ok = 0;  // test hook: leave silently, the other CTAs' waits run out
-  } else if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned int target = (*epoch + 1u) * (unsigned int)G;
-    *epoch += 1u;
-    __threadfence();  // the CTA's writes (ordered before by __syncthreads) first
-    const unsigned int arrived = atomicAdd(&h->bar_count, 1u) + 1u;
-    if (arrived < target) {
-      const unsigned long long t0 = global_ns();
-      unsigned int spins = 0;
-      while (ld_acquire(&h->bar_count) < target) {
-        if (((++spins) & 63u) == 0u) {
-          if (ld_acquire(&h->abort) != 0u || global_ns() - t0 > limit_ns) {
-            ok = 0;
-            break;
-          }
-        }
-      }
-    }
-    if (ok && ld_acquire(&h->abort) != 0u) ok = 0;
-    if (!ok) atomicExch(&h->abort, 1u);
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
 }
 
 // ---- double-float reductions ------------------------------------------------
@@ -166,14 +129,10 @@ __device__ __forceinline__ ff2 ff_from_double(double d) {
   return ff2{hi, (float)(d - (double)hi)};
 }
 
-// Reduction slot: kQ double-float values padded to 32 bytes (kQ <= 4).
+// A CTA's sums of one keyframe segment: up to four double-float values.
 struct alignas(32) Slot {
   ff2 v[4];
 };
-
-// Slots a reader's inbox holds for n writers: padded to whole warps so that
-// every lane loads whole slots without bounds checks (padding stays zero).
-__host__ __device__ __forceinline__ int inbox_slots(int n) { return (n + 31) & ~31; }
 
 // A CTA's FP32 per-thread partials -> double-float CTA totals in a fixed
 // order: a warp tree per quantity, then warp q adds quantity q over the warps
@@ -196,28 +155,6 @@ __device__ __forceinline__ void cta_partial_sum_split(const float (&acc)[kQ], ff
     const ff2 t = warp_sum_ff(x);
     if (lane == 0) out[warp] = t;
   }
-}
-
-// One quantity q of an inbox of n writers, summed by one warp: every lane
-// adds its slots in slot order (issuing all its loads first), then a fixed
-// warp tree. The total is valid in lane 0, as a double-float.
-__device__ __forceinline__ ff2 warp_inbox_sum_q(const Slot *box, int n, int q) {
-  const int lane = threadIdx.x & 31;
-  const int np = inbox_slots(n);
-  constexpr int kU = 8;
-  ff2 acc = ff2{0.0f, 0.0f};
-  for (int base = 0; base < np; base += 32 * kU) {
-    float2 v[kU];
-#pragma unroll
-    for (int j = 0; j < kU; ++j) {
-      const int sl = base + lane + 32 * j;
-      v[j] = (base + 32 * j < np) ? __ldcg(reinterpret_cast<const float2 *>(&box[sl].v[q]))
-                                  : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int j = 0; j < kU; ++j) acc = ff_add(acc, ff2{v[j].x, v[j].y});
-  }
-  return warp_sum_ff(acc);
 }
 
 // ---- exact sums over the CTAs of a keyframe, without a grid barrier ---------
