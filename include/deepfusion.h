@@ -507,7 +507,7 @@ df_status df_optimise_noalloc(int32_t width, int32_t height, const float *mu_net
  *             them in one launch); the solve is split into launches of
  *             whole GN iterations with the same result
  *   debug_skip_cta  test only: >= 0 makes that CTA of the next fused launches
- *             leave without arriving at its first grid barrier, so the
+ *             leave without adding its sums of the first pass, so the
  *             others' bounded waits run out (DF_ETIMEOUT); -1 = off.
  *   assembly  streaming kernel with 4 pixels per lane: where each GN
  *             iteration's weights and 5-point system are assembled.
@@ -548,8 +548,8 @@ df_status df_get_tuning(df_tuning *t);
 df_status df_autotune(df_keyframe *const *kfs, int32_t n, const df_solve_params *params,
                       void *stream, df_tuning *best, float *best_ms);
 
-/* Upper bound on every device-side wait of the fused solver (grid
- * barriers), in nanoseconds; a wait that runs out abandons the solve and is
+/* Upper bound on every device-side wait of the fused solver (the polls of
+ * each keyframe's sum words, the waits on staged rows), in nanoseconds; a wait that runs out abandons the solve and is
  * reported as DF_ETIMEOUT. Default 2 s. */
 df_status df_set_spin_limit_ns(uint64_t ns);
 

@@ -12,7 +12,7 @@
 // gamma = r.z = 0 or when p.Ap = delta - beta gamma / alpha <= 0, or (tol > 0)
 // when ||r|| < tol ||b||.
 //
-// Passes, each ended by one grid barrier:
+// Passes, each ended by one exchange of the keyframes' sums:
 //   SCALE     scale-step partial sums (first GN iteration only)
 //   ASSEMBLE  IRLS weights of Eqs. 6-8 at (x, t), 5-point system, r0
 //   INIT      w0 = A u0
@@ -27,18 +27,20 @@
 // may span a few keyframes ("segments").
 //
 // Reductions: per tile a warp sums its FP32 per-lane partials as a
-// double-float (df_sync.cuh), per CTA the warps' sums are added in warp order
-// into one slot per (CTA, keyframe), pushed into the inbox of every CTA of
-// that keyframe; after the barrier each CTA adds its own inbox in slot
-// order. All CTAs therefore compute bitwise identical scalars, and the
-// result does not depend on timing. The CG scalars formed from the sums are
-// double-float too.
+// double-float (df_sync.cuh), per CTA the warps' sums of a keyframe segment
+// are added in warp order, and warp sg adds segment sg's sums exactly into
+// that keyframe's fixed-point sum words (df_exact.cuh), whose arrival counts
+// also end the pass: a CTA waits only for the CTAs that share its
+// keyframes, never for the whole grid. Integer addition is associative, so
+// every CTA reads bitwise identical totals and the result does not depend on
+// timing. The CG scalars formed from the sums are double-float too.
 //
-// Barrier: a generation-counting grid barrier whose waits give up after a
-// time limit (%globaltimer); a CTA that gives up raises an abort word, every
-// CTA then skips the remaining passes, the keyframes are flagged
-// kFlagTimeout and the host reports DF_ETIMEOUT. The last CTA to exit resets
-// the barrier words, so the next launch starts clean either way.
+// Waits: every poll of the sum words and every wait on a staged row gives
+// up after a time limit (%globaltimer); a CTA that gives up raises an abort
+// word, every CTA then skips the remaining passes, the keyframes are
+// flagged kFlagTimeout and the host reports DF_ETIMEOUT. The last CTA to
+// exit clears the sum and abort words, so the next launch starts clean
+// either way.
 #include <math.h>
 
 #include <string.h>
@@ -1403,7 +1405,7 @@ __global__ void __launch_bounds__(kThreads, VEC == 4 ? 1 : 2)
   bool alive = true;
   const bool wide = c.tol > 0.0 || n_pcg == 0;  // the assembly's r.r and b.b are read
 
-  // One pass over the CTA's tiles, then slots, barrier and per-keyframe sums.
+  // One pass over the CTA's tiles, then the exchange of the per-keyframe sums.
   // fin (the last x update only): bit 0 the next scale step's sums, bit 1 r.r
   auto run_pass = [&](int kind, int it, int fin) __attribute__((always_inline)) -> bool {
     // the sums this pass's consumers use: a[q0 .. q0 + nq) of the tiles'
@@ -1902,7 +1904,7 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   if (R > (long long)INT32_MAX / 2) return false;
   const int th_max = tune.tile_rows > 0 ? tune.tile_rows : 0;
   // at least min_rows rows per warp: fewer CTAs for small work (a cheaper
-  // grid barrier); VEC = 4 warps need a few rows to fill their copy ring
+  // exchange); VEC = 4 warps need a few rows to fill their copy ring
   const long long min_rows = std::max<long long>(vec == 4 ? 4 : 1, th_max);
   int G = (int)std::min<long long>(G_cap, std::max<long long>(1, (R + min_rows * kWarps - 1) /
                                                                       (min_rows * kWarps)));

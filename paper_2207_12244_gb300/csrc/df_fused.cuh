@@ -45,14 +45,14 @@ size_t fused_plan_bytes(int nkf, int G);
 // Bytes a single keyframe reserves for its own launch plan (either kernel).
 size_t fused_plan_cap_single();
 
-// Host-side plan of one launch (tiles, CTA ranges, reduction slots, barrier
+// Host-side plan of one launch (tiles, CTA ranges, exact-sum words, exit
 // words). Returns false if the keyframes cannot share one launch (then
 // split the batch).
 bool fused_build_plan(const Planes *const *kfs, int n, const FusedTuning &tune,
                       std::vector<char> &out, LaunchShape &shape);
 
 // Launch on stream s with a plan already copied to device memory 'dplan'.
-// limit_ns bounds every grid-barrier wait.
+// limit_ns bounds every device-side wait (sum words, staged rows).
 // 'first' = 1 for the first launch of a solve (the reported PCG iteration
 // count starts at 0), 0 for later launches of the same solve.
 cudaError_t fused_launch(void *dplan, const LaunchShape &shape, const SolveCfg &c, int n_gn,

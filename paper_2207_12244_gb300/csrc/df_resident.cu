@@ -1,8 +1,8 @@
 // Resident persistent solver: the same per-frame solve as df_fused.cu
 // (Section II-C: n_gn Gauss-Newton iterations alternating scale and depth;
-// Jacobi-PCG in the Chronopoulos-Gear arrangement, one grid barrier per
-// pass), for keyframes small enough that the whole solver state fits in the
-// GPU's shared memory.
+// Jacobi-PCG in the Chronopoulos-Gear arrangement, one exchange of the
+// keyframe's exact sums per pass), for keyframes small enough that the whole
+// solver state fits in the GPU's shared memory.
 //
 // Each CTA owns a band of whole rows [rb, re) of one keyframe and keeps
 // x, r, p, s, w, diag, wx, wy and u of its band in shared memory for the
@@ -50,8 +50,8 @@ struct ResSeg {
   int stop, iters, active, pad;
 };
 
-// What the halo stage arrays are loaded with right after a barrier, for the
-// pass that follows it.
+// What the halo stage arrays are loaded with right after an exchange, for
+// the pass that follows it.
 enum HaloKind : int { HK_NONE = 0, HK_X, HK_INIT, HK_ITER };
 
 // Shared-memory arrays of one band (stride BS floats each): x, r, p, s, w,
@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
           __syncthreads();
           // r and s of the band's edge rows are final: their stores drain
           // while the stencil runs (the next pass reads them after the
-          // barrier; this pass reads only the other parity's planes)
+          // exchange; this pass reads only the other parity's planes)
           publish_edges(m.R, Rg[nb], W, nr, rb, P);
           publish_edges(m.S, Sg[nb], W, nr, rb, P);
           if constexpr (JOINT)

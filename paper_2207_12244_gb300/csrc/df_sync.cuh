@@ -283,7 +283,7 @@ __device__ __forceinline__ ff2 sum_total(long long digit) {
 }
 
 // Called once by every CTA as its last action: the last CTA out resets the
-// barrier words (also after an abort, since every CTA does exit), and clears
+// abort and exit words (also after an abort, since every CTA does exit), and clears
 // n_sum words of exact-sum groups at 'sums' (nullptr: none).
 __device__ __forceinline__ void grid_exit(PlanHeader *h, int G, unsigned long long *sums = nullptr,
                                           long long n_sum = 0) {
