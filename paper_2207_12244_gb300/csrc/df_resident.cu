@@ -511,18 +511,29 @@ __global__ void __launch_bounds__(kRThreads, 1)
   auto end_pass = [&](auto nq, const float *acc, int next_halo, int next_cb,
                       auto &&post) -> bool {
     constexpr int NQ = decltype(nq)::value;
-    {
-      float an[NQ];
+    // the CTA tree: a warp tree per quantity, then warp 1 + q adds quantity
+    // q over the warps while warp 0 runs the release fence of the pass's
+    // edge stores (the barrier before orders every warp's stores first)
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) an[q] = acc[q];
-      cta_partial_sum_split<NQ>(an, s_red, s_cs);
-      __syncthreads();
+    for (int q = 0; q < NQ; ++q) {
+      const ff2 sw = warp_sum_ff(ff2{acc[q], 0.0f});
+      if (lane == 0) s_red[warp * NQ + q] = sw;
     }
+    __syncthreads();
+    if (warp == 0) {
+      fence_acq_rel_gpu();
+    } else if (warp <= NQ) {
+      const int q = warp - 1;
+      const ff2 x = lane < kRThreads / 32 ? s_red[lane * NQ + q] : ff2{0.0f, 0.0f};
+      const ff2 tq = warp_sum_ff(x);
+      if (lane == 0) s_cs[q] = tq;
+    }
+    __syncthreads();
     long long digit = 0;
     if (warp == 0) {
       bool ok = false;
       if (!skip_me) {
-        sum_push(grp, parity, s_cs, NQ);
+        sum_push(grp, parity, s_cs, NQ, false);
         ok = sum_wait(grp, parity, nk, NQ, &s_prev, h, limit_ns, &digit);
       }
       if (lane == 0) s_ok = ok ? 1 : 0;

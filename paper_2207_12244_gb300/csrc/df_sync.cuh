@@ -217,9 +217,10 @@ __device__ __forceinline__ void fence_acq_rel_gpu() {
 // Warp-collective (one whole warp): fence, then add the nq (1..4) totals
 // tot[] of this CTA into set 'set' of group g (lane q * 8 + k adds digit k
 // of quantity q).
-__device__ __forceinline__ void sum_push(SumGroup *g, int set, const ff2 *tot, int nq) {
+__device__ __forceinline__ void sum_push(SumGroup *g, int set, const ff2 *tot, int nq,
+                                         bool fence = true) {
   const int lane = threadIdx.x & 31;
-  fence_acq_rel_gpu();
+  if (fence) fence_acq_rel_gpu();  // (a caller that fenced already passes false)
   if (lane < 8 * nq) {
     const int q = lane >> 3, k = lane & 7;
     const long long d = ff_digit(tot[q], k);
