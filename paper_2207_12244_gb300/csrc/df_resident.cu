@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
                int first) {
   extern __shared__ float4 dyn_smem[];
   __shared__ ff2 s_red[32 * kRQ];
-  __shared__ ff2 s_cs[kRQ];
+  __shared__ long long s_dig[kRQ][kSumDigits];
   __shared__ ff2 s_tot[kRQ];  // this pass's totals
   __shared__ int s_ok;
   __shared__ SumPrev s_prev;
@@ -512,8 +512,9 @@ __global__ void __launch_bounds__(kRThreads, 1)
                       auto &&post) -> bool {
     constexpr int NQ = decltype(nq)::value;
     // the CTA tree: a warp tree per quantity, then warp 1 + q adds quantity
-    // q over the warps while warp 0 runs the release fence of the pass's
-    // edge stores (the barrier before orders every warp's stores first)
+    // q over the warps and writes its digits while warp 0 runs the release
+    // fence of the pass's edge stores (the barrier before orders every
+    // warp's stores first)
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const ff2 sw = warp_sum_ff(ff2{acc[q], 0.0f});
@@ -526,14 +527,15 @@ __global__ void __launch_bounds__(kRThreads, 1)
       const int q = warp - 1;
       const ff2 x = lane < kRThreads / 32 ? s_red[lane * NQ + q] : ff2{0.0f, 0.0f};
       const ff2 tq = warp_sum_ff(x);
-      if (lane == 0) s_cs[q] = tq;
+      const ff2 tb = ff2{__shfl_sync(0xffffffffu, tq.hi, 0), __shfl_sync(0xffffffffu, tq.lo, 0)};
+      if (lane < kSumDigits) s_dig[q][lane] = ff_digit(tb, lane);
     }
     __syncthreads();
     long long digit = 0;
     if (warp == 0) {
       bool ok = false;
       if (!skip_me) {
-        sum_push(grp, parity, s_cs, NQ, false);
+        sum_push_digits(grp, parity, s_dig, NQ);
         ok = sum_wait(grp, parity, nk, NQ, &s_prev, h, limit_ns, &digit);
       }
       if (lane == 0) s_ok = ok ? 1 : 0;

@@ -228,6 +228,17 @@ __device__ __forceinline__ void sum_push(SumGroup *g, int set, const ff2 *tot, i
   }
 }
 
+// Warp-collective (one whole warp): add digits d[q][k] (k < 8, q < nq) that
+// the CTA formed already (ff_digit of its totals); the caller has fenced.
+__device__ __forceinline__ void sum_push_digits(SumGroup *g, int set, const long long (*d)[kSumDigits],
+                                                int nq) {
+  const int lane = threadIdx.x & 31;
+  if (lane < 8 * nq) {
+    const int q = lane >> 3, k = lane & 7;
+    red_add_u64(sum_word(g, set, q, k), (unsigned long long)(d[q][k] + (long long)kDigitBias) + kArrival);
+  }
+}
+
 // Warp-collective: wait until all n CTAs have added their nq quantities to
 // set 'set' of g (every lane q * 8 + k < 8 nq polls its own word with an
 // acquire load: two requests per quantity line and spin). Returns false if
