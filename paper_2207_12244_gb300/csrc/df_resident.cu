@@ -118,7 +118,7 @@ struct Walk {
 };
 
 // Walks the band two pixels per step: eval(q, u, v, out) only loads from
-// shared memory, commit(q, out) stores, so the two pixels' load and
+// shared memory, commit(q, u, v, out) stores, so the two pixels' load and
 // arithmetic chains overlap (a store between them would order every later
 // shared-memory load after it). Per thread the pixels are committed in walk
 // order, so every per-thread partial sum is added in the same order as a
@@ -134,21 +134,23 @@ __device__ __forceinline__ void walk_pairs(int W, int bp, Eval &&eval, Commit &&
     T a, b;
     eval(qa, ua, va, a);
     eval(qb, ub, vb, b);
-    commit(qa, a);
-    commit(qb, b);
+    commit(qa, ua, va, a);
+    commit(qb, ub, vb, b);
   }
   if (it.q < bp) {
     T a;
     eval(it.q, it.u, it.v, a);
-    commit(it.q, a);
+    commit(it.q, it.u, it.v, a);
   }
 }
 
 // w = A u = r - N u for the band (A = diag - N; u = r / diag exactly, so
 // diag * u is r). Halo u: HA[0] above, HA[4] below; y-coupling of the row
-// above the band in WYT. Accumulates (r, u), (w, u), (r, r).
+// above the band in WYT. Accumulates (r, u), (w, u), (r, r). The band's edge
+// rows of w also go to wpub (global plane, rows rb and rb + nr - 1) as they
+// are formed, for the neighbouring bands.
 __device__ __forceinline__ void apply_band(const Smem &m, int W, int nr, int bp, bool has_below,
-                                           float acc[kRQ]) {
+                                           float acc[kRQ], float *wpub, int rb, size_t P) {
   struct Px {
     float r, uq, w;
   };
@@ -168,8 +170,9 @@ __device__ __forceinline__ void apply_band(const Smem &m, int W, int nr, int bp,
         o.r = m.R[q];
         o.w = o.r - nu;
       },
-      [&](int q, const Px &o) {
+      [&](int q, int u, int v, const Px &o) {
         m.Wv[q] = o.w;
+        if (v == 0 || v == nr - 1) __stcg(wpub + (size_t)(rb + v) * P + u, o.w);
         acc[0] += o.r * o.uq;
         acc[1] += o.w * o.uq;
         acc[2] += o.r * o.r;
@@ -299,7 +302,7 @@ __device__ void assemble_pre(const Smem &m, const Planes &k, int rb, int nr, con
 // staged in shared memory (DT is then unused).
 template <int DT, bool JOINT, int LK, bool SM>
 __device__ void assemble_post(const Smem &m, const Planes &k, int rb, int nr, float t,
-                              const SolveCfg &c, float acc[kRQ]) {
+                              const SolveCfg &c, float acc[kRQ], float *rpub, float *idpub) {
   const int W = k.W, H = k.H, bp = nr * W;
   const size_t P = k.P;
   const bool semi = c.terms & DF_TERM_SEMI, net = c.terms & DF_TERM_NET,
@@ -374,6 +377,10 @@ __device__ void assemble_post(const Smem &m, const Planes &k, int rb, int nr, fl
     m.ID[q] = id;
     m.R[q] = r;
     if (JOINT) m.U[q] = ws;
+    if (v == 0 || v == nr - 1) {  // the edge rows, for the neighbouring bands
+      __stcg(rpub + gi, r);
+      __stcg(idpub + gi, id);
+    }
   }
 }
 
@@ -616,16 +623,13 @@ __global__ void __launch_bounds__(kRThreads, 1)
           __syncthreads();
         }
         if (in_sm)
-          assemble_post<DF_F32, JOINT, LK, true>(m, k, rb, nr, t, c, acc);
+          assemble_post<DF_F32, JOINT, LK, true>(m, k, rb, nr, t, c, acc, Rg[0], IDg);
         else if (k.dtype == DF_BF16)
-          assemble_post<DF_BF16, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
+          assemble_post<DF_BF16, JOINT, LK, false>(m, k, rb, nr, t, c, acc, Rg[0], IDg);
         else if (k.dtype == DF_F16)
-          assemble_post<DF_F16, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
+          assemble_post<DF_F16, JOINT, LK, false>(m, k, rb, nr, t, c, acc, Rg[0], IDg);
         else
-          assemble_post<DF_F32, JOINT, LK, false>(m, k, rb, nr, t, c, acc);
-        __syncthreads();
-        publish_edges(m.R, Rg[0], W, nr, rb, P);
-        publish_edges(m.ID, IDg, W, nr, rb, P);
+          assemble_post<DF_F32, JOINT, LK, false>(m, k, rb, nr, t, c, acc, Rg[0], IDg);
       }
       // sums needed: r.z; r.r and b.b only for a tolerance or a report
       // without CG iterations; the joint solve also S and r_t
@@ -675,12 +679,14 @@ __global__ void __launch_bounds__(kRThreads, 1)
         } else {
           walk_pairs<float>(
               W, bp, [&](int q, int, int, float &o) { o = m.R[q] * m.ID[q]; },
-              [&](int q, float o) { m.U[q] = o; });
+              [&](int q, int, int, float o) { m.U[q] = o; });
           __syncthreads();
-          apply_band(m, W, nr, bp, has_below, acc);
+          apply_band(m, W, nr, bp, has_below, acc, Wg[0], rb, P);
         }
-        __syncthreads();
-        publish_edges(m.Wv, Wg[0], W, nr, rb, P);
+        if constexpr (JOINT) {
+          __syncthreads();
+          publish_edges(m.Wv, Wg[0], W, nr, rb, P);
+        }
       }
       // sums needed: (w0, u0); the joint solve also (ws, u0)
       const int next_i = n_pcg > 1 ? HK_ITER : HK_NONE;
@@ -729,15 +735,14 @@ __global__ void __launch_bounds__(kRThreads, 1)
                 const float si = first ? m.Wv[q] : m.Wv[q] + fb * m.S[q];
                 o.rn = r - fa * si;
               },
-              [&](int q, const Fin &o) {
+              [&](int q, int u, int v, const Fin &o) {
                 m.X[q] = o.x;
+                if (v == 0 || v == nr - 1) __stcg(k.x + (size_t)(rb + v) * P + u, o.x);
                 acc[0] += o.rn * o.rn;
               });
-        }
-        if (active) {
+        } else if (active) {
           // x may also have moved in earlier passes of a depth step that
           // stopped early: the neighbours' next assembly needs the edges
-          __syncthreads();
           publish_edges(m.X, k.x, W, nr, rb, P);
         }
         if (fs && active) scale_partials(acc, 1, (float)s_seg.t);
@@ -793,25 +798,29 @@ __global__ void __launch_bounds__(kRThreads, 1)
                 o.s = first ? m.Wv[q] : m.Wv[q] + fb * m.S[q];
                 o.r = r - fa * o.s;
               },
-              [&](int q, const Upd &o) {
+              [&](int q, int u, int v, const Upd &o) {
                 m.X[q] = o.x;
                 m.P[q] = o.p;
                 m.S[q] = o.s;
                 m.R[q] = o.r;
                 if (!joint) m.U[q] = o.r * o.id;
+                // r and s of the band's edge rows are final: they go to the
+                // other parity's planes now and drain while the stencil runs
+                // (the neighbours read them after the exchange)
+                if (v == 0 || v == nr - 1) {
+                  const size_t gi = (size_t)(rb + v) * P + u;
+                  __stcg(Rg[nb] + gi, o.r);
+                  __stcg(Sg[nb] + gi, o.s);
+                }
               });
           __syncthreads();
-          // r and s of the band's edge rows are final: their stores drain
-          // while the stencil runs (the next pass reads them after the
-          // exchange; this pass reads only the other parity's planes)
-          publish_edges(m.R, Rg[nb], W, nr, rb, P);
-          publish_edges(m.S, Sg[nb], W, nr, rb, P);
-          if constexpr (JOINT)
+          if constexpr (JOINT) {
             apply_band_joint(m, W, nr, bp, has_below, s_seg.jut.hi, acc);
-          else
-            apply_band(m, W, nr, bp, has_below, acc);
-          __syncthreads();
-          publish_edges(m.Wv, Wg[nb], W, nr, rb, P);
+            __syncthreads();
+            publish_edges(m.Wv, Wg[nb], W, nr, rb, P);
+          } else {
+            apply_band(m, W, nr, bp, has_below, acc, Wg[nb], rb, P);
+          }
         }
         const int next_kind = (it + 1 < n_pcg - 1) ? HK_ITER : HK_NONE;
         // sums needed: (r, u), (w, u); (r, r) for a tolerance; the joint
