@@ -455,31 +455,48 @@ __global__ void __launch_bounds__(kRThreads, 1)
   auto prefetch_halo = [&](int kind, int cb, int t0 = 32) {
     if (!active || kind == HK_NONE) return;
     const size_t ia = (size_t)(rb - 1) * P, ib = (size_t)(rb + nr) * P;
-    for (int u = tid - t0; u < W; u += kRThreads - t0) {
-      if (kind == HK_X) {
-        m.HA[0][u] = has_above ? __ldcg(k.x + ia + u) : 0.0f;
-        m.HA[4][u] = has_below ? __ldcg(k.x + ib + u) : 0.0f;
-      } else {
-        const float *Rc = kind == HK_INIT ? Rg[0] : Rg[cb];
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
-        if (has_above) {
-          a0 = __ldcg(Rc + ia + u);
-          a3 = __ldcg(IDg + ia + u);
-          if (kind == HK_ITER) {
-            a1 = __ldcg(Sg[cb] + ia + u);
-            a2 = __ldcg(Wg[cb] + ia + u);
+    const int nt = kRThreads - t0;
+    const float *Rc = kind == HK_INIT ? Rg[0] : Rg[cb];
+    // two columns per thread and round: both columns' loads are issued
+    // before either is stored, so a round costs one L2 round trip
+    for (int u0 = tid - t0; u0 < W; u0 += 2 * nt) {
+      float a[2][4] = {}, b[2][4] = {};
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int u = u0 + h2 * nt;
+        if (u >= W) continue;
+        if (kind == HK_X) {
+          if (has_above) a[h2][0] = __ldcg(k.x + ia + u);
+          if (has_below) b[h2][0] = __ldcg(k.x + ib + u);
+        } else {
+          if (has_above) {
+            a[h2][0] = __ldcg(Rc + ia + u);
+            a[h2][3] = __ldcg(IDg + ia + u);
+            if (kind == HK_ITER) {
+              a[h2][1] = __ldcg(Sg[cb] + ia + u);
+              a[h2][2] = __ldcg(Wg[cb] + ia + u);
+            }
+          }
+          if (has_below) {
+            b[h2][0] = __ldcg(Rc + ib + u);
+            b[h2][3] = __ldcg(IDg + ib + u);
+            if (kind == HK_ITER) {
+              b[h2][1] = __ldcg(Sg[cb] + ib + u);
+              b[h2][2] = __ldcg(Wg[cb] + ib + u);
+            }
           }
         }
-        if (has_below) {
-          b0 = __ldcg(Rc + ib + u);
-          b3 = __ldcg(IDg + ib + u);
-          if (kind == HK_ITER) {
-            b1 = __ldcg(Sg[cb] + ib + u);
-            b2 = __ldcg(Wg[cb] + ib + u);
-          }
+      }
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int u = u0 + h2 * nt;
+        if (u >= W) continue;
+        m.HA[0][u] = a[h2][0];
+        m.HA[4][u] = b[h2][0];
+        if (kind != HK_X) {
+          m.HA[1][u] = a[h2][1]; m.HA[2][u] = a[h2][2]; m.HA[3][u] = a[h2][3];
+          m.HA[5][u] = b[h2][1]; m.HA[6][u] = b[h2][2]; m.HA[7][u] = b[h2][3];
         }
-        m.HA[0][u] = a0; m.HA[1][u] = a1; m.HA[2][u] = a2; m.HA[3][u] = a3;
-        m.HA[4][u] = b0; m.HA[5][u] = b1; m.HA[6][u] = b2; m.HA[7][u] = b3;
       }
     }
   };
