@@ -93,6 +93,21 @@ def test_modes(o, solver, mode):
         assert rep.iters_done == ro.iters_done
 
 
+@pytest.mark.parametrize("n_pcg", [0, 1, 2])
+def test_short_depth_steps(o, solver, n_pcg):
+    """Depth steps of no, one and two CG iterations over three Gauss-Newton
+    iterations: the fused kernels' pass sequences without CG iteration
+    passes (the first CG pass straight into the last x update) or without
+    any depth pass (assembly after assembly, each with the scale step
+    before it), against the oracle."""
+    kf = synth.make_keyframe(100, 70, 61 + n_pcg)
+    prm = params(n_gn=3, n_pcg=n_pcg, solver=solver)
+    x, t, rep = solve(kf, prm)
+    xo, to, ro = oracle_solve(o, kf, prm)
+    assert_parity(x, t, xo, to, what=f"n_pcg={n_pcg}")
+    assert rep.iters_done == ro.iters_done
+
+
 def test_prior_only_returns_cnn_depth_bitwise(o, solver):
     kf = synth.make_keyframe(64, 48, 9)
     prm = params(terms=dfl.DF_TERM_NET, solver=solver)
