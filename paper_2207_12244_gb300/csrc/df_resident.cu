@@ -539,10 +539,15 @@ __global__ void __launch_bounds__(kRThreads, 1)
     // q over the warps and writes its digits while warp 0 runs the release
     // fence of the pass's edge stores (the barrier before orders every
     // warp's stores first)
+    {
+      ff2 sw[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const ff2 sw = warp_sum_ff(ff2{acc[q], 0.0f});
-      if (lane == 0) s_red[warp * NQ + q] = sw;
+      for (int q = 0; q < NQ; ++q) sw[q] = ff2{acc[q], 0.0f};
+      warp_sum_ff_n<NQ>(sw);
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) s_red[warp * NQ + q] = sw[q];
+      }
     }
     __syncthreads();
     if (warp == 0) {

@@ -75,6 +75,21 @@ __device__ __forceinline__ ff2 warp_sum_ff(ff2 a) {
   return a;
 }
 
+// NQ fixed-order warp trees side by side, level by level, so that their
+// shuffle and add latencies overlap (each tree's arithmetic is warp_sum_ff's);
+// results in lane 0
+template <int NQ>
+__device__ __forceinline__ void warp_sum_ff_n(ff2 (&a)[NQ]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ff2 t[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) t[q] = ff_shfl_down(a[q], o);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) a[q] = ff_add(a[q], t[q]);
+  }
+}
+
 __device__ __forceinline__ double ff_to_double(ff2 a) { return (double)a.hi + (double)a.lo; }
 
 // ---- double-float scalar arithmetic -----------------------------------------
