@@ -99,6 +99,28 @@ DF_HD float scale_pow2(float x, int p) {
   return x * df_bits_float((unsigned int)(p + 127) << 23);
 }
 
+// The double-float of a fixed-point magnitude in normalised digits (each in
+// [0, 2^36)) whose leading non-zero digit is d2 = digit K, with d1, d0 the
+// two digits below it (0 where K < 1, 2), negated if neg; truncated after 48
+// significant bits.
+DF_HD ff2 leading_to_ff(int K, unsigned long long d2, unsigned long long d1,
+                        unsigned long long d0, bool neg) {
+  // the 64 bits below and at the leading one of d2 2^72 + d1 2^36 + d0
+  const int lz = df_clz64(d2) - 28;  // leading zeros in the 36-bit digit
+  unsigned long long w = d2 << (28 + lz);
+  const int s1 = lz - 8;
+  w |= s1 >= 0 ? (d1 << s1) : (d1 >> -s1);
+  w |= d0 >> (44 - lz);
+  const int e63 = 36 * K + 35 - lz - 149;  // the leading one is 2^e63
+  float hi = scale_pow2((float)(unsigned int)(w >> 40), e63 - 23);
+  float lo = scale_pow2((float)(unsigned int)((w >> 16) & 0xffffffull), e63 - 47);
+  if (neg) {
+    hi = -hi;
+    lo = -lo;
+  }
+  return ff2{hi, lo};
+}
+
 // The fixed-point total (raw digit sums dg[0..7], each |dg| < 2^47) as a
 // double-float, truncated after 48 significant bits. A digit-7 sum of 2^36
 // or more marks a non-finite partial: the total is then NaN.
@@ -138,20 +160,7 @@ DF_HD ff2 digits_to_ff(const long long (&raw)[kSumDigits]) {
     }
   }
   if (K < 0) return ff2{0.0f, 0.0f};
-  // the 64 bits below and at the leading one of d2 2^72 + d1 2^36 + d0
-  const int lz = df_clz64(d2) - 28;  // leading zeros in the 36-bit digit
-  unsigned long long w = d2 << (28 + lz);
-  const int s1 = lz - 8;
-  w |= s1 >= 0 ? (d1 << s1) : (d1 >> -s1);
-  w |= d0 >> (44 - lz);
-  const int e63 = 36 * K + 35 - lz - 149;  // the leading one is 2^e63
-  float hi = scale_pow2((float)(unsigned int)(w >> 40), e63 - 23);
-  float lo = scale_pow2((float)(unsigned int)((w >> 16) & 0xffffffull), e63 - 47);
-  if (neg) {
-    hi = -hi;
-    lo = -lo;
-  }
-  return ff2{hi, lo};
+  return leading_to_ff(K, d2, d1, d0, neg);
 }
 
 }  // namespace df

@@ -300,13 +300,49 @@ __device__ __forceinline__ bool sum_wait(SumGroup *g, int set, int n, int nq, Su
   return true;
 }
 
-// Warp-collective after sum_wait: lane 8 q returns the total of quantity q.
+// Carry rounds over the 8-lane digit groups of a warp: each round keeps the
+// low 36 bits of every digit and adds the carry of the digit below it (lane
+// k - 1 of the group); the carry out of digit 7 goes to *c8 (lane 7). Rounds
+// repeat until every digit of every group is in [0, 2^36).
+__device__ __forceinline__ long long carry_rounds(long long d, long long *c8) {
+  const int k = threadIdx.x & 7;
+  for (;;) {
+    const long long c = d >> 36;  // floor(d / 2^36)
+    d &= kDigitMask;
+    const long long cin = __shfl_up_sync(0xffffffffu, c, 1);
+    if (k > 0) d += cin;
+    if (k == 7) *c8 += c;
+    if (!__any_sync(0xffffffffu, (d >> 36) != 0)) return d;
+  }
+}
+
+// Warp-collective after sum_wait: every lane of the group of quantity q
+// (lanes 8 q .. 8 q + 7) returns its total. The same value as digits_to_ff
+// of the group's raw digit sums (the normalised digits of an integer are
+// unique), with the carries resolved across the group's lanes in a few
+// rounds instead of one digit after another.
 __device__ __forceinline__ ff2 sum_total(long long digit) {
-  const int lane = threadIdx.x & 31;
-  long long raw[kSumDigits];
-#pragma unroll
-  for (int j = 0; j < kSumDigits; ++j) raw[j] = __shfl_sync(0xffffffffu, digit, (lane & ~7) + j);
-  return digits_to_ff(raw);
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, k = lane & 7, base = lane & ~7;
+  const bool nonfinite = __shfl_sync(full, digit, base + 7) >= (1LL << 36);
+  long long c8 = 0;
+  long long d = carry_rounds(digit, &c8);
+  const long long top = __shfl_sync(full, c8, base + 7);  // 0 or -1 unless beyond 2^139
+  const bool neg = top == -1;
+  // two's complement of negative totals: -N = sum (mask - d_k) 2^(36 k) + 1
+  if (neg) d = (kDigitMask - d) + (k == 0 ? 1 : 0);
+  long long c8n = 0;
+  d = carry_rounds(d, &c8n);
+  const unsigned gm = (__ballot_sync(full, d != 0) >> base) & 0xffu;
+  const int K = gm ? 31 - __clz(gm) : 0;
+  const unsigned long long d2 = (unsigned long long)__shfl_sync(full, d, base + K);
+  const unsigned long long d1 = (unsigned long long)__shfl_sync(full, d, base + (K >= 1 ? K - 1 : 0));
+  const unsigned long long d0 = (unsigned long long)__shfl_sync(full, d, base + (K >= 2 ? K - 2 : 0));
+  if (nonfinite) return ff2{__int_as_float(0x7fc00000), __int_as_float(0x7fc00000)};
+  if (top > 0) return ff2{__int_as_float(0x7f800000), 0.0f};
+  if (top < -1) return ff2{__int_as_float((int)0xff800000u), 0.0f};
+  if (gm == 0) return ff2{0.0f, 0.0f};
+  return leading_to_ff(K, d2, K >= 1 ? d1 : 0ull, K >= 2 ? d0 : 0ull, neg);
 }
 
 // Called once by every CTA as its last action: the last CTA out resets the

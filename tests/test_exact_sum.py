@@ -170,3 +170,44 @@ def test_up_to_1023_partials(lib):
     mx = [(np.float32(3.4028235e38), np.float32(2.0 ** 103))] * 1023
     assert np.isinf(total(lib, mx)[0]) and total(lib, mx)[0] > 0
     assert np.isinf(total(lib, [(-a, -b) for a, b in mx])[0])
+
+
+def test_carry_rounds_equal_the_sequential_carries(lib):
+    """The solvers resolve the digit sums' carries across the lanes of a
+    group in rounds; on every kind of digit-sum vector (random, every digit at
+    its extremes, carries rippling through full digits, negative totals,
+    zero, non-finite marks, overflow) the result is the sequential one."""
+    L = lib
+    for f in (L.total_by_rounds, L.total_sequential):
+        f.argtypes = [C.POINTER(C.c_longlong), C.POINTER(C.c_float)]
+
+    def both(raw):
+        a = np.ascontiguousarray(np.asarray(raw, dtype=np.int64))
+        o1, o2 = (C.c_float * 2)(), (C.c_float * 2)()
+        L.total_by_rounds(a.ctypes.data_as(C.POINTER(C.c_longlong)), o1)
+        L.total_sequential(a.ctypes.data_as(C.POINTER(C.c_longlong)), o2)
+        return (np.float32(o1[0]).tobytes() + np.float32(o1[1]).tobytes(),
+                np.float32(o2[0]).tobytes() + np.float32(o2[1]).tobytes())
+
+    rng = np.random.default_rng(7)
+    mask = (1 << 36) - 1
+    cases = [[0] * 8, [mask] * 7 + [0], [mask] * 7 + [-1], [1] + [0] * 7, [-1] + [0] * 7,
+             [0] * 7 + [1 << 36], [0] * 7 + [(1 << 35) - 1], [0] * 7 + [-(1 << 35)],
+             [mask + 1] + [mask] * 6 + [0], [-(1 << 46)] * 8, [(1 << 46) - 1] * 7 + [0]]
+    for _ in range(3000):
+        kind = rng.integers(0, 4)
+        if kind == 0:
+            raw = rng.integers(-(1 << 46), 1 << 46, 8)
+            raw[7] = rng.integers(-(1 << 34), 1 << 34)
+        elif kind == 1:
+            raw = rng.choice([0, 1, -1, mask, mask + 1, -mask], 8)
+        elif kind == 2:
+            raw = rng.integers(0, 1 << 37, 8) * rng.choice([1, -1], 8)
+            raw[5:] = 0
+        else:
+            raw = np.zeros(8, dtype=np.int64)
+            raw[rng.integers(0, 8)] = rng.integers(-(1 << 46), 1 << 46)
+        cases.append([int(v) for v in raw])
+    for raw in cases:
+        a, b = both(raw)
+        assert a == b, raw
