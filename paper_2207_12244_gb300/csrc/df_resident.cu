@@ -501,6 +501,64 @@ __global__ void __launch_bounds__(kRThreads, 1)
     }
   };
 
+  // Deferred halo (the first CG pass and the CG iterations, keyframes up to
+  // 2 x 480 pixels wide): right after the exchange, threads 32.. issue the
+  // loads of the raw halo values of up to two columns each into registers
+  // hv; they store the halo's new u into HA[0] / HA[4] only after the pass's
+  // vector update, which needs no halo, so the loads' round trip overlaps
+  // the CG scalars and that update instead of preceding them.
+  float hv[2][8];
+  bool halo_deferred = false;
+  const bool can_defer = W <= 2 * (kRThreads - 32);
+  auto halo_issue = [&](int kind, int cb) {
+    if (!active) return;
+    const size_t ia = (size_t)(rb - 1) * P, ib = (size_t)(rb + nr) * P;
+    const float *Rc = kind == HK_INIT ? Rg[0] : Rg[cb];
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) hv[h2][j] = 0.0f;
+      const int u = tid - 32 + h2 * (kRThreads - 32);
+      if (u >= W) continue;
+      if (has_above) {
+        hv[h2][0] = __ldcg(Rc + ia + u);
+        hv[h2][3] = __ldcg(IDg + ia + u);
+        if (kind == HK_ITER) {
+          hv[h2][1] = __ldcg(Sg[cb] + ia + u);
+          hv[h2][2] = __ldcg(Wg[cb] + ia + u);
+        }
+      }
+      if (has_below) {
+        hv[h2][4] = __ldcg(Rc + ib + u);
+        hv[h2][7] = __ldcg(IDg + ib + u);
+        if (kind == HK_ITER) {
+          hv[h2][5] = __ldcg(Sg[cb] + ib + u);
+          hv[h2][6] = __ldcg(Wg[cb] + ib + u);
+        }
+      }
+    }
+  };
+  // the halo's new u: r' = r - alpha (w + beta s), u' = r' / diag (CG
+  // iterations; the arithmetic of the in-place update below), or u0 = r0 /
+  // diag (the first CG pass)
+  auto halo_store = [&](bool iter, bool first_it, float fa_, float fb_) {
+    if (tid < 32) return;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int u = tid - 32 + h2 * (kRThreads - 32);
+      if (u >= W) continue;
+      if (iter) {
+        const float sa = first_it ? hv[h2][2] : hv[h2][2] + fb_ * hv[h2][1];
+        m.HA[0][u] = (hv[h2][0] - fa_ * sa) * hv[h2][3];
+        const float sb = first_it ? hv[h2][6] : hv[h2][6] + fb_ * hv[h2][5];
+        m.HA[4][u] = (hv[h2][4] - fa_ * sb) * hv[h2][7];
+      } else {
+        m.HA[0][u] = hv[h2][0] * hv[h2][3];
+        m.HA[4][u] = hv[h2][4] * hv[h2][7];
+      }
+    }
+  };
+
   // partial sums -> exact sum words -> prefetch next halo + this keyframe's totals.
   // Reductions: every CTA of a keyframe adds its double-float partials into
   // the keyframe's fixed-point sum words (a fence first, so its band edges
@@ -573,6 +631,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
     }
     pre_done = overlap_pre;
     overlap_pre = false;
+    halo_deferred = can_defer && (next_halo == HK_INIT || next_halo == HK_ITER);
     __syncthreads();
     if (!s_ok) return false;
     // warp 0 forms the totals and the pass's scalars; the other warps load
@@ -583,7 +642,10 @@ __global__ void __launch_bounds__(kRThreads, 1)
       __syncwarp();
       if (lane == 0) post();
     } else {
-      prefetch_halo(next_halo, next_cb, 32);
+      if (halo_deferred)
+        halo_issue(next_halo, next_cb);
+      else
+        prefetch_halo(next_halo, next_cb, 32);
     }
     __syncthreads();
     parity ^= 1;
@@ -691,17 +753,21 @@ __global__ void __launch_bounds__(kRThreads, 1)
     {  // INIT: w0 = A u0
       float acc[kRQ] = {};
       if (active && !s_seg.stop) {
-        for (int u = tid; u < W; u += kRThreads) {
-          m.HA[0][u] = m.HA[0][u] * m.HA[3][u];
-          m.HA[4][u] = m.HA[4][u] * m.HA[7][u];
+        if (!halo_deferred) {
+          for (int u = tid; u < W; u += kRThreads) {
+            m.HA[0][u] = m.HA[0][u] * m.HA[3][u];
+            m.HA[4][u] = m.HA[4][u] * m.HA[7][u];
+          }
         }
         if constexpr (JOINT) {
+          if (halo_deferred) halo_store(false, false, 0.0f, 0.0f);
           __syncthreads();
           apply_band_joint(m, W, nr, bp, has_below, s_seg.jut.hi, acc);
         } else {
           walk_pairs<float>(
               W, bp, [&](int q, int, int, float &o) { o = m.R[q] * m.ID[q]; },
               [&](int q, int, int, float o) { m.U[q] = o; });
+          if (halo_deferred) halo_store(false, false, 0.0f, 0.0f);
           __syncthreads();
           apply_band(m, W, nr, bp, has_below, acc, Wg[0], rb, P);
         }
@@ -800,12 +866,14 @@ __global__ void __launch_bounds__(kRThreads, 1)
         if (fs) scale_pending = true;
       } else {  // ITER
         if (run) {
-          for (int u = tid; u < W; u += kRThreads) {
-            // r' = r - alpha (w + beta s), u' = r' / diag at the halo rows
-            const float sa = first ? m.HA[2][u] : m.HA[2][u] + fb * m.HA[1][u];
-            m.HA[0][u] = (m.HA[0][u] - fa * sa) * m.HA[3][u];
-            const float sb = first ? m.HA[6][u] : m.HA[6][u] + fb * m.HA[5][u];
-            m.HA[4][u] = (m.HA[4][u] - fa * sb) * m.HA[7][u];
+          if (!halo_deferred) {
+            for (int u = tid; u < W; u += kRThreads) {
+              // r' = r - alpha (w + beta s), u' = r' / diag at the halo rows
+              const float sa = first ? m.HA[2][u] : m.HA[2][u] + fb * m.HA[1][u];
+              m.HA[0][u] = (m.HA[0][u] - fa * sa) * m.HA[3][u];
+              const float sb = first ? m.HA[6][u] : m.HA[6][u] + fb * m.HA[5][u];
+              m.HA[4][u] = (m.HA[4][u] - fa * sb) * m.HA[7][u];
+            }
           }
           struct Upd {
             float x, p, s, r, id;
@@ -835,6 +903,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
                   __stcg(Sg[nb] + gi, o.s);
                 }
               });
+          if (halo_deferred) halo_store(true, first, fa, fb);
           __syncthreads();
           if constexpr (JOINT) {
             apply_band_joint(m, W, nr, bp, has_below, s_seg.jut.hi, acc);
