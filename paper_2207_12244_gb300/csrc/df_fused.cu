@@ -1989,7 +1989,7 @@ bool streaming_build_plan(const Planes *const *kfs, int n, const FusedTuning &tu
   hd->ntiles = (int)R;  // rows of the work list
   hd->th = th_max;
   hd->nslots = nslots;
-  hd->slot_stride = 0;
+  hd->off_flags = 0;
   hd->vec = vec;
   hd->bytes = (long long)out.size();
   memcpy(base + hd->off_cta_work, wr.data(), sizeof(int) * wr.size());

@@ -31,6 +31,7 @@ namespace {
 constexpr int kRThreads = 512;
 constexpr int kRQ = 4;
 constexpr int kHalo = 9;  // halo arrays of W floats kept in shared memory
+constexpr int kFlagWords = 4;  // u64 words per CTA edge flag (one 32-byte sector)
 
 struct ResKf {
   Planes pl;
@@ -568,6 +569,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
   const int nk = s_kf.cta_end - s_kf.cta_begin;
   SumGroup *groups = reinterpret_cast<SumGroup *>(reinterpret_cast<char *>(h) + h->off_slots);
   SumGroup *grp = groups + me.kf;
+  unsigned long long *flags =
+      reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(h) + h->off_flags);
   const bool skip_me = (int)blockIdx.x == h->debug_skip_cta;  // test hook: never arrive
   // nq: std::integral_constant with the number of sums this pass needs
   // (acc[0 .. NQ-1]). post() runs on thread 0 once the totals are in s_tot,
@@ -698,6 +701,13 @@ __global__ void __launch_bounds__(kRThreads, 1)
       }
       scale_pending = false;
     }
+    // Without the joint solve, the first CG pass needs of the assembly only
+    // the neighbouring bands' edge rows of r0 and 1/diag; its sums are not
+    // used before that pass's scalars. So the assembly ends in an edge
+    // hand-off with the two neighbours instead of an exchange, and its sums
+    // travel with the first CG pass's.
+    const bool merged = !JOINT && n_pcg > 0;
+    float asm_acc[kRQ] = {};
     {  // ASSEMBLE
       float acc[kRQ] = {};
       if (active) {
@@ -741,13 +751,46 @@ __global__ void __launch_bounds__(kRThreads, 1)
           }
         }
       };
-      if constexpr (JOINT) {
-        alive = end_pass(IC<4>{}, acc, next_a, 0, post);
+      if (merged) {
+#pragma unroll
+        for (int q = 0; q < kRQ; ++q) asm_acc[q] = acc[q];
+        if (tid == 0) s_seg.stop = 0;
+        __syncthreads();  // the band's r0, 1/diag and its edge stores are done
+        if (warp == 0) {
+          bool ok = true;
+          if (active) {
+            const unsigned long long e = (unsigned long long)gn + 1ull;
+            if (lane == 0) edge_flag_raise(flags + kFlagWords * blockIdx.x, e);
+            const unsigned long long *nbr = nullptr;
+            if (lane == 0 && has_above) nbr = flags + kFlagWords * (blockIdx.x - 1);
+            if (lane == 1 && has_below) nbr = flags + kFlagWords * (blockIdx.x + 1);
+            ok = edge_flags_wait(nbr, e, h, limit_ns);
+          }
+          if (lane == 0) s_ok = ok ? 1 : 0;
+        } else if (active) {  // u0 = r0 / diag of the band, meanwhile
+          for (int q = tid - 32; q < bp; q += kRThreads - 32) m.U[q] = m.R[q] * m.ID[q];
+        }
+        halo_deferred = can_defer;
+        __syncthreads();
+        if (!s_ok) {
+          alive = false;
+          break;
+        }
+        if (halo_deferred) {
+          halo_issue(HK_INIT, 0);
+        } else {
+          prefetch_halo(HK_INIT, 0, 0);
+          __syncthreads();
+        }
       } else {
-        alive = wide ? end_pass(IC<3>{}, acc, next_a, 0, post)
-                     : end_pass(IC<1>{}, acc, next_a, 0, post);
+        if constexpr (JOINT) {
+          alive = end_pass(IC<4>{}, acc, next_a, 0, post);
+        } else {
+          alive = wide ? end_pass(IC<3>{}, acc, next_a, 0, post)
+                       : end_pass(IC<1>{}, acc, next_a, 0, post);
+        }
+        if (!alive) break;
       }
-      if (!alive) break;
     }
     if (n_pcg == 0) continue;  // no depth update in this GN iteration
     {  // INIT: w0 = A u0
@@ -764,9 +807,10 @@ __global__ void __launch_bounds__(kRThreads, 1)
           __syncthreads();
           apply_band_joint(m, W, nr, bp, has_below, s_seg.jut.hi, acc);
         } else {
-          walk_pairs<float>(
-              W, bp, [&](int q, int, int, float &o) { o = m.R[q] * m.ID[q]; },
-              [&](int q, int, int, float o) { m.U[q] = o; });
+          if (!merged)
+            walk_pairs<float>(
+                W, bp, [&](int q, int, int, float &o) { o = m.R[q] * m.ID[q]; },
+                [&](int q, int, int, float o) { m.U[q] = o; });
           if (halo_deferred) halo_store(false, false, 0.0f, 0.0f);
           __syncthreads();
           apply_band(m, W, nr, bp, has_below, acc, Wg[0], rb, P);
@@ -779,8 +823,16 @@ __global__ void __launch_bounds__(kRThreads, 1)
       // sums needed: (w0, u0); the joint solve also (ws, u0)
       const int next_i = n_pcg > 1 ? HK_ITER : HK_NONE;
       auto post = [&] {
+        if (merged) {  // the assembly's sums (its exchange's scalars)
+          s_seg.gam = s_tot[0];
+          if (c.tol > 0.0) {
+            s_seg.rr = ff_to_double(s_tot[2]);
+            s_seg.bb = ff_to_double(s_tot[3]);
+            s_seg.stop = (c.tol > 0.0 && sqrt(s_seg.rr) < c.tol * sqrt(s_seg.bb)) ? 1 : 0;
+          }
+        }
         if (s_seg.stop) return;
-        ff2 dl = s_tot[0];
+        ff2 dl = merged ? s_tot[1] : s_tot[0];
         if constexpr (JOINT) {  // w_t = S u_t - (ws, u); (w, u) gains w_t u_t
           s_seg.jwt = ff_sub(ff_mul(s_seg.jS, s_seg.jut), s_tot[1]);
           dl = ff_add(dl, ff_mul(s_seg.jwt, s_seg.jut));
@@ -796,6 +848,14 @@ __global__ void __launch_bounds__(kRThreads, 1)
       if constexpr (JOINT) {
         const float a2[2] = {acc[1], acc[3]};
         alive = end_pass(IC<2>{}, a2, next_i, 0, post);
+      } else if (merged) {  // (r0, u0) [, r0.r0, b.b] of the assembly, (w0, u0)
+        if (c.tol > 0.0) {
+          const float a4[4] = {asm_acc[0], acc[1], asm_acc[1], asm_acc[2]};
+          alive = end_pass(IC<4>{}, a4, next_i, 0, post);
+        } else {
+          const float a2[2] = {asm_acc[0], acc[1]};
+          alive = end_pass(IC<2>{}, a2, next_i, 0, post);
+        }
       } else {
         alive = end_pass(IC<1>{}, acc + 1, next_i, 0, post);
       }
@@ -972,7 +1032,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
     }
   }
   grid_exit(h, G, reinterpret_cast<unsigned long long *>(groups),
-            (long long)h->nkf * (long long)(sizeof(SumGroup) / 8));
+            (long long)h->nkf * (long long)(sizeof(SumGroup) / 8) + (long long)kFlagWords * G);
 }
 
 // The kernel instance of a variant and a loss kind.
@@ -1023,13 +1083,15 @@ const ResDev &rdev() {
 }  // namespace
 
 // Plan bytes: header, CTA table, keyframe table, then one exact-sum group
-// per keyframe.
+// per keyframe and the CTAs' edge flags (32 bytes each; the launch's last
+// CTA clears groups and flags together on its way out).
 static size_t resident_bytes(int nkf, int G) {
   size_t off = align16(sizeof(PlanHeader));
   off += align16(sizeof(ResCta) * (size_t)G);
   off += align16(sizeof(ResKf) * (size_t)nkf);
   off = (off + 255) & ~(size_t)255;
   off += sizeof(SumGroup) * (size_t)nkf;
+  off += kFlagWords * 8 * (size_t)G;
   return off;
 }
 
@@ -1127,12 +1189,12 @@ static bool resident_build_plan_with(const Planes *const *kfs, int n, const Fuse
   off += align16(sizeof(ResKf) * (size_t)n);
   off = (off + 255) & ~(size_t)255;
   hd->off_slots = (long long)off;
+  hd->off_flags = (long long)(off + sizeof(SumGroup) * (size_t)n);
   hd->kind = kPlanResident;
   hd->debug_skip_cta = tune.debug_skip_cta;
   hd->nkf = n;
   hd->G = G;
   hd->nslots = G;
-  hd->slot_stride = 0;
   hd->th = stride;  // shared-memory stride of one band array
   hd->smem_bytes = (int)smem;
   hd->in_smem = in_smem ? 1 : 0;

@@ -28,7 +28,9 @@ struct PlanHeader {
   int smem_bytes;  // dynamic shared memory per CTA (resident plans)
   int in_smem;     // resident plans: 1 = each band's input planes are staged
                    // in shared memory for the whole launch
-  long long slot_stride;  // unused (zero)
+  long long off_flags;  // resident plans: the CTAs' edge flags (four words
+                        // per CTA, the first used) right after the sum
+                        // groups; 0 in streaming plans
   int asm_pieces;  // streaming plans: pieces of the separate assembly kernel
   int asm_pad;
 };
@@ -298,6 +300,36 @@ __device__ __forceinline__ bool sum_wait(SumGroup *g, int set, int n, int nq, Su
     *digit = (long long)((v - pv) & (kArrival - 1ull)) - (long long)n * (long long)kDigitBias;
   }
   return true;
+}
+
+// Edge hand-off between neighbouring bands without a reduction: after its
+// edge stores (and a barrier of its CTA), one thread raises the CTA's flag
+// to epoch e; fence first, so that whoever sees e sees the edges.
+__device__ __forceinline__ void edge_flag_raise(unsigned long long *f, unsigned long long e) {
+  fence_acq_rel_gpu();
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(f), "l"(e) : "memory");
+}
+
+// Warp-collective (one whole warp): lanes with a non-null p wait until *p
+// reaches e (acquire loads). Bounded like sum_wait: false (abort raised)
+// once limit_ns has passed or another CTA raised the abort word.
+__device__ __forceinline__ bool edge_flags_wait(const unsigned long long *p, unsigned long long e,
+                                                PlanHeader *h, unsigned long long limit_ns) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long t0 = global_ns();
+  unsigned int spins = 0;
+  for (;;) {
+    const bool done = p == nullptr || ld_acquire_u64(p) >= e;
+    if (__all_sync(0xffffffffu, done)) return true;
+    if (((++spins) & 63u) == 0u) {
+      int bad = 0;
+      if (lane == 0) bad = (ld_acquire(&h->abort) != 0u || global_ns() - t0 > limit_ns) ? 1 : 0;
+      if (__shfl_sync(0xffffffffu, bad, 0)) {
+        if (lane == 0) atomicExch(&h->abort, 1u);
+        return false;
+      }
+    }
+  }
 }
 
 // Carry rounds over the 8-lane digit groups of a warp: each round keeps the
