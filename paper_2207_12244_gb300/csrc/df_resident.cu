@@ -990,14 +990,18 @@ __global__ void __launch_bounds__(kRThreads, 1)
           if (c.tol > 0.0 && sqrt(s_seg.rr) < c.tol * sqrt(s_seg.bb)) {
             s_seg.stop = 1;
           } else {
-            // beta = gamma / gamma_prev; p.Ap = delta - beta gamma / alpha_prev
+            // beta = gamma / gamma_prev; p.Ap = delta - beta gamma / alpha_prev,
+            // so alpha = gamma / p.Ap = gamma ag / (delta ag - gamma^2) with
+            // ag = alpha_prev gamma_prev > 0: one division after the sums
+            // arrive (beta's runs beside it) instead of three in a row
             const ff2 beta = ff_div(gn_, s_seg.gam);
-            const ff2 denom = ff_sub(dl, ff_div(ff_mul(beta, gn_), s_seg.alpha));
-            if (gn_.hi == 0.0f || !(denom.hi > 0.0f)) {
+            const ff2 ag = ff_mul(s_seg.alpha, s_seg.gam);
+            const ff2 den = ff_sub(ff_mul(dl, ag), ff_mul(gn_, gn_));
+            if (gn_.hi == 0.0f || !(den.hi > 0.0f)) {
               s_seg.stop = 1;
             } else {
               s_seg.beta = beta;
-              s_seg.alpha = ff_div(gn_, denom);
+              s_seg.alpha = ff_div(ff_mul(gn_, ag), den);
               s_seg.gam = gn_;
               if constexpr (JOINT) joint_border_step(false);
             }
