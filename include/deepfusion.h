@@ -507,8 +507,10 @@ df_status df_optimise_noalloc(int32_t width, int32_t height, const float *mu_net
  *             them in one launch); the solve is split into launches of
  *             whole GN iterations with the same result
  *   debug_skip_cta  test only: >= 0 makes that CTA of the next fused launches
- *             leave without adding its sums of the first pass, so the
- *             others' bounded waits run out (DF_ETIMEOUT); -1 = off.
+ *             leave without adding its sums of the first pass (and, in
+ *             the resident kernel, without raising its edge flag after
+ *             the assembly), so the others' bounded waits run out
+ *             (DF_ETIMEOUT); -1 = off.
  *   assembly  streaming kernel with 4 pixels per lane: where each GN
  *             iteration's weights and 5-point system are assembled.
  *             1 in a pass of the persistent kernel, 2 in an ordinary kernel
@@ -549,8 +551,9 @@ df_status df_autotune(df_keyframe *const *kfs, int32_t n, const df_solve_params 
                       void *stream, df_tuning *best, float *best_ms);
 
 /* Upper bound on every device-side wait of the fused solver (the polls of
- * each keyframe's sum words, the waits on staged rows), in nanoseconds; a wait that runs out abandons the solve and is
- * reported as DF_ETIMEOUT. Default 2 s. */
+ * each keyframe's sum words and of the neighbouring bands' edge flags, the
+ * waits on staged rows), in nanoseconds; a wait that runs out abandons the
+ * solve and is reported as DF_ETIMEOUT. Default 2 s. */
 df_status df_set_spin_limit_ns(uint64_t ns);
 
 /* Number of kernels this library has launched in this process (all devices);

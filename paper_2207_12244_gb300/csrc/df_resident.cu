@@ -571,7 +571,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
   SumGroup *grp = groups + me.kf;
   unsigned long long *flags =
       reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(h) + h->off_flags);
-  const bool skip_me = (int)blockIdx.x == h->debug_skip_cta;  // test hook: never arrive
+  // test hook: never arrive (nor raise the CTA's edge flag)
+  const bool skip_me = (int)blockIdx.x == h->debug_skip_cta;
   // nq: std::integral_constant with the number of sums this pass needs
   // (acc[0 .. NQ-1]). post() runs on thread 0 once the totals are in s_tot,
   // while the other warps load the next pass's halo; its writes to s_seg are
@@ -760,7 +761,7 @@ __global__ void __launch_bounds__(kRThreads, 1)
           bool ok = true;
           if (active) {
             const unsigned long long e = (unsigned long long)gn + 1ull;
-            if (lane == 0) edge_flag_raise(flags + kFlagWords * blockIdx.x, e);
+            if (lane == 0 && !skip_me) edge_flag_raise(flags + kFlagWords * blockIdx.x, e);
             const unsigned long long *nbr = nullptr;
             if (lane == 0 && has_above) nbr = flags + kFlagWords * (blockIdx.x - 1);
             if (lane == 1 && has_below) nbr = flags + kFlagWords * (blockIdx.x + 1);

@@ -375,14 +375,19 @@ def test_streaming_tile_shapes(o, mode):
         dfl.df_set_tuning()
 
 
+@pytest.mark.parametrize("scale", ["alternate", "fixed"])
 @pytest.mark.parametrize("mode", [dfl.DF_MODE_STREAMING, dfl.DF_MODE_RESIDENT],
                          ids=["streaming", "resident"])
-def test_barrier_wait_times_out_cleanly(mode):
-    """One CTA leaves without arriving at its first grid barrier (test
-    switch): the others' bounded waits run out, the solve reports
-    DF_ETIMEOUT, and the next solve on the same context is correct."""
+def test_barrier_wait_times_out_cleanly(mode, scale):
+    """One CTA leaves without arriving at its first exchange (test switch):
+    the others' bounded waits run out, the solve reports DF_ETIMEOUT, and
+    the next solve on the same context is correct. With the scale fixed the
+    resident kernel's first synchronisation is the assembly's edge hand-off,
+    where the CTA also withholds its flag: its neighbours' flag waits run
+    out."""
     kf = synth.make_keyframe(160, 120, 23)
-    prm = params(n_gn=2, n_pcg=3, solver=dfl.DF_SOLVER_FUSED)
+    extra = {} if scale == "alternate" else dict(scale_step=dfl.DF_SCALE_FIXED)
+    prm = params(n_gn=2, n_pcg=3, solver=dfl.DF_SOLVER_FUSED, **extra)
     ref = solve(kf, prm)
     try:
         dfl.df_set_spin_limit_ns(50_000_000)
