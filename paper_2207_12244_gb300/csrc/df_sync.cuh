@@ -196,18 +196,19 @@ __device__ __forceinline__ void cta_partial_sum_split(const float (&acc)[kQ], ff
 // next one, that is, after every CTA has read this one. Before its adds a
 // CTA fences, so everything it wrote in the pass (the band or tile edges its
 // neighbours read next) is visible to whoever sees its arrival.
-// One quantity of one set: the eight digit words in one 128-byte line (a
-// warp's adds and loads of a quantity are one request each; spreading the
-// words over eight lines measured slower).
+// Two quantities of one set share a 128-byte line, eight digit words each
+// (a warp's adds and loads of two quantities are one request each; fewer
+// lines polled and added to by all the keyframe's CTAs measured faster,
+// spreading the words over eight lines per quantity slower).
 struct alignas(128) SumLine {
   unsigned long long w[16];
 };
-// The reduction words of one keyframe: [set][quantity].
+// The reduction words of one keyframe: [set][quantity pair].
 struct SumGroup {
-  SumLine line[2][kSumQ];
+  SumLine line[2][(kSumQ + 1) / 2];
 };
 __device__ __forceinline__ unsigned long long *sum_word(SumGroup *g, int set, int q, int k) {
-  return &g->line[set][q].w[k];
+  return &g->line[set][q >> 1].w[((q & 1) << 3) + k];
 }
 // What a CTA remembers of a group's words (shared memory).
 struct SumPrev {
