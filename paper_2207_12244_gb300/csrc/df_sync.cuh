@@ -259,7 +259,7 @@ __device__ __forceinline__ void sum_push_digits(SumGroup *g, int set, const long
 
 // Warp-collective: wait until all n CTAs have added their nq quantities to
 // set 'set' of g (every lane q * 8 + k < 8 nq polls its own word with an
-// acquire load: two requests per quantity line and spin). Returns false if
+// acquire load: one request per line of two quantities and spin). Returns false if
 // the wait ran past limit_ns or another CTA raised the abort word (and then
 // raises it too). On success each lane q * 8 + k < 8 nq holds digit k of
 // quantity q in *digit, prev is updated, and the warp has acquired what the
